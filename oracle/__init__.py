@@ -1,0 +1,209 @@
+"""FP64 CPU oracle for the sparse Cholesky hot path (TEST INFRASTRUCTURE).
+
+Only the tests, ``__graft_entry__.smoke()`` and the benchmark's CPU-baseline
+leg may import this package. It restates the definitions of "GPU Accelerated
+Sparse Cholesky Factorization" (Karsavuran, Ng, Peyton) in the plainest
+form, in ``oracle.c`` (symbolic and numeric parts) and ``selinv.py``:
+
+* ``permute``           B = P A P^T                           (Sec. II, problem)
+* ``symbolic``          etree parent, column counts, struct(L) (Sec. II, etree
+                        definition; fill by symbolic elimination)
+* ``supernodes``        maximal supernode partition and tree  (Sec. II, Fig. 1)
+* ``relind``            relative indices by definition        (Sec. II-A)
+* ``factor``            left-looking column Cholesky (cmod/cdiv), FP64
+* ``solve``             forward/backward substitution          (Sec. I)
+* ``logdet``, ``spmv``, ``backward_error``, ``factor_residual``
+
+It shares no code with the CUDA library.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+from . import build as _build
+
+_lib = None
+
+
+def lib():
+    global _lib
+    if _lib is None:
+        path = _build.build()
+        L = C.CDLL(path)
+        P = C.c_void_p
+        L.orc_permute.restype = C.c_int
+        L.orc_permute.argtypes = [C.c_int32, P, P, P, P, P, P, P]
+        L.orc_sym_new.restype = C.c_void_p
+        L.orc_sym_new.argtypes = [C.c_int32, P, P]
+        L.orc_sym_nnz.restype = C.c_int64
+        L.orc_sym_nnz.argtypes = [P]
+        L.orc_sym_get.argtypes = [P, P, P, P, P]
+        L.orc_sym_free.argtypes = [P]
+        L.orc_supernodes.restype = C.c_int32
+        L.orc_supernodes.argtypes = [C.c_int32, P, P, P, P]
+        L.orc_relind.argtypes = [C.c_int32, C.c_int32, P, P, P, P, P, P, P, P]
+        L.orc_factor_new.restype = C.c_void_p
+        L.orc_factor_new.argtypes = [C.c_int32, P, P, P]
+        L.orc_factor_info.restype = C.c_int32
+        L.orc_factor_info.argtypes = [P]
+        L.orc_factor_nnz.restype = C.c_int64
+        L.orc_factor_nnz.argtypes = [P]
+        L.orc_factor_get.argtypes = [P, P, P, P]
+        L.orc_factor_free.argtypes = [P]
+        L.orc_solve.argtypes = [C.c_int32, P, P, P, P, C.c_int32, P, P]
+        L.orc_logdet.restype = C.c_double
+        L.orc_logdet.argtypes = [C.c_int32, P, P]
+        L.orc_spmv.argtypes = [C.c_int32, P, P, P, C.c_int32, P, P]
+        L.orc_backward_error.argtypes = [C.c_int32, P, P, P, C.c_int32, P, P, P]
+        L.orc_factor_residual.restype = C.c_double
+        L.orc_factor_residual.argtypes = [C.c_int32, P, P, P, P, P, P]
+        _lib = L
+    return _lib
+
+
+def _p(a):
+    return None if a is None else a.ctypes.data_as(C.c_void_p)
+
+
+def _c(a, dt):
+    return np.ascontiguousarray(a, dtype=dt)
+
+
+def permute(n, colptr, rowind, values, perm):
+    """Lower CSC of B = P A P^T (perm new->old; None = identity)."""
+    colptr = _c(colptr, np.int64); rowind = _c(rowind, np.int32)
+    values = None if values is None else _c(values, np.float64)
+    perm = None if perm is None else _c(perm, np.int32)
+    nnz = int(colptr[n])
+    bp = np.zeros(n + 1, np.int64); bi = np.zeros(max(nnz, 1), np.int32)
+    bx = np.zeros(max(nnz, 1), np.float64)
+    rc = lib().orc_permute(n, _p(colptr), _p(rowind), _p(values), _p(perm), _p(bp), _p(bi), _p(bx))
+    if rc != 0:
+        raise ValueError("perm is not a permutation")
+    return bp, bi[:nnz], (bx[:nnz] if values is not None else None)
+
+
+class Symbolic:
+    """parent, colcount, lp, li (struct(L) column by column) of B = P A P^T."""
+
+    def __init__(self, n, bcolptr, browind):
+        bcolptr = _c(bcolptr, np.int64); browind = _c(browind, np.int32)
+        h = lib().orc_sym_new(n, _p(bcolptr), _p(browind))
+        try:
+            nnz = lib().orc_sym_nnz(h)
+            self.n = n
+            self.parent = np.zeros(n, np.int32)
+            self.colcount = np.zeros(n, np.int32)
+            self.lp = np.zeros(n + 1, np.int64)
+            self.li = np.zeros(max(nnz, 1), np.int32)
+            lib().orc_sym_get(h, _p(self.parent), _p(self.colcount), _p(self.lp), _p(self.li))
+            self.li = self.li[:nnz]
+        finally:
+            lib().orc_sym_free(h)
+
+    @property
+    def nnz(self):
+        return int(self.lp[-1])
+
+    def flops(self):
+        """Factor flop count sum_j c_j^2 (c_j = nnz of column j incl. diagonal)."""
+        c = self.colcount.astype(np.int64)
+        return int((c * c).sum())
+
+    def supernodes(self):
+        ptr = np.zeros(self.n + 1, np.int32)
+        sp = np.zeros(max(self.n, 1), np.int32)
+        ns = lib().orc_supernodes(self.n, _p(self.parent), _p(self.colcount), _p(ptr), _p(sp))
+        return ptr[: ns + 1].copy(), sp[:ns].copy()
+
+    def relind(self, snode_ptr):
+        """(relind_ptr, relind_target, relind) for every (J, touched ancestor K)."""
+        ns = len(snode_ptr) - 1
+        sptr = _c(snode_ptr, np.int32)
+        npairs = C.c_int64(0); tot = C.c_int64(0)
+        L = lib()
+        L.orc_relind(self.n, ns, _p(sptr), _p(self.lp), _p(self.li), C.byref(npairs), C.byref(tot),
+                     None, None, None)
+        rp = np.zeros(npairs.value + 1, np.int64)
+        rt = np.zeros(max(npairs.value, 1), np.int32)
+        ri = np.zeros(max(tot.value, 1), np.int32)
+        L.orc_relind(self.n, ns, _p(sptr), _p(self.lp), _p(self.li), C.byref(npairs), C.byref(tot),
+                     _p(rp), _p(rt), _p(ri))
+        return rp, rt[: npairs.value], ri[: tot.value]
+
+
+class Factor:
+    """Left-looking FP64 column Cholesky of B. info = 0 or j+1 (bad pivot at j)."""
+
+    def __init__(self, n, bcolptr, browind, bvals):
+        bcolptr = _c(bcolptr, np.int64); browind = _c(browind, np.int32); bvals = _c(bvals, np.float64)
+        h = lib().orc_factor_new(n, _p(bcolptr), _p(browind), _p(bvals))
+        try:
+            self.n = n
+            self.info = lib().orc_factor_info(h)
+            nnz = lib().orc_factor_nnz(h)
+            self.lp = np.zeros(n + 1, np.int64)
+            self.li = np.zeros(max(nnz, 1), np.int32)
+            self.lx = np.zeros(max(nnz, 1), np.float64)
+            lib().orc_factor_get(h, _p(self.lp), _p(self.li), _p(self.lx))
+            self.li = self.li[:nnz]; self.lx = self.lx[:nnz]
+        finally:
+            lib().orc_factor_free(h)
+
+    def solve(self, perm, b):
+        b = np.asfortranarray(b, dtype=np.float64)
+        nrhs = 1 if b.ndim == 1 else b.shape[1]
+        x = np.zeros_like(b, order="F")
+        perm = None if perm is None else _c(perm, np.int32)
+        lib().orc_solve(self.n, _p(self.lp), _p(self.li), _p(self.lx), _p(perm), nrhs, _p(b), _p(x))
+        return x
+
+    def logdet(self):
+        return lib().orc_logdet(self.n, _p(self.lp), _p(self.lx))
+
+    def diag(self):
+        return self.lx[self.lp[:-1]]
+
+
+def spmv(n, colptr, rowind, values, x):
+    x = np.asfortranarray(x, dtype=np.float64)
+    nrhs = 1 if x.ndim == 1 else x.shape[1]
+    y = np.zeros_like(x, order="F")
+    lib().orc_spmv(n, _p(_c(colptr, np.int64)), _p(_c(rowind, np.int32)), _p(_c(values, np.float64)),
+                   nrhs, _p(x), _p(y))
+    return y
+
+
+def backward_error(n, colptr, rowind, values, b, x):
+    """Per right-hand side eta = ||b-Ax||_inf / (||A||_inf ||x||_inf + ||b||_inf)."""
+    b = np.asfortranarray(b, dtype=np.float64); x = np.asfortranarray(x, dtype=np.float64)
+    nrhs = 1 if b.ndim == 1 else b.shape[1]
+    eta = np.zeros(nrhs)
+    lib().orc_backward_error(n, _p(_c(colptr, np.int64)), _p(_c(rowind, np.int32)),
+                             _p(_c(values, np.float64)), nrhs, _p(b), _p(x), _p(eta))
+    return eta
+
+
+def factor_residual(n, bcolptr, browind, bvals, lp, li, lx):
+    """||B - L L^T||_F / ||B||_F (B = P A P^T lower CSC, L in CSC)."""
+    r = lib().orc_factor_residual(n, _p(_c(bcolptr, np.int64)), _p(_c(browind, np.int32)),
+                                  _p(_c(bvals, np.float64)), _p(_c(lp, np.int64)),
+                                  _p(_c(li, np.int32)), _p(_c(lx, np.float64)))
+    if r < 0:
+        raise ValueError("L L^T or B has an entry outside the pattern of L")
+    return r
+
+
+def reference(problem, b=None):
+    """Run the whole oracle on a gridgen problem: returns a dict of results."""
+    n = problem["n"]
+    bp, bi, bx = permute(n, problem["colptr"], problem["rowind"], problem["values"], problem["perm"])
+    sym = Symbolic(n, bp, bi)
+    fac = Factor(n, bp, bi, bx)
+    out = dict(B=(bp, bi, bx), sym=sym, fac=fac)
+    if b is not None:
+        out["x"] = fac.solve(problem["perm"], b)
+    return out
