@@ -1,0 +1,203 @@
+/*
+ * chol.h -- C ABI of the GB300 supernodal sparse Cholesky library.
+ *
+ * The library computes A = L L^T for a sparse symmetric positive definite A
+ * (Karsavuran, Ng, Peyton, "GPU Accelerated Sparse Cholesky Factorization",
+ * Sec. II: problem statement A = L L^T, elimination tree, supernodes, relative
+ * indices) with the right-looking supernodal method RL of Sec. II-A: per
+ * supernode J a dense POTRF of the diagonal block, a TRSM of the off-diagonal
+ * panel, a SYRK update matrix, and the scatter-add of that update matrix into
+ * the ancestor supernodes through relative indices. The triangular factors
+ * then give the solution (Sec. I, abstract).
+ *
+ * Conventions shared by every call
+ *   - A is passed once as a pattern: the lower triangle including the
+ *     diagonal in compressed sparse column form, 0-based, row indices sorted
+ *     ascending and unique in every column, every diagonal entry present.
+ *   - perm is new->old: row/column i of P A P^T is row/column perm[i] of A.
+ *     NULL means the identity. The library never reorders on its own.
+ *   - Host arrays passed to chol_analyze are copied; the caller keeps them.
+ *   - Device arrays (values, right-hand sides, gradients) belong to the
+ *     caller and must stay valid until the call's work on `stream` is done.
+ *   - `stream` is a cudaStream_t passed as void*; NULL is the legacy default
+ *     stream. Work is ordered on that stream only.
+ *   - Return codes: CHOL_OK (0); -k: argument k (1-based) is invalid;
+ *     +j: A is not positive definite, the first failing pivot is column j
+ *     (1-based) of P A P^T (LAPACK "info" convention); CHOL_E* below.
+ *     No call aborts, prints, traps or asserts.
+ *   - A handle is not thread-safe: calls on one handle must be serialized.
+ */
+#ifndef CHOL_H_
+#define CHOL_H_
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct chol_handle chol_handle;
+
+enum {
+  CHOL_OK = 0,
+  CHOL_ENOMEM = -1001,    /* host or device allocation failed (or over cap) */
+  CHOL_ECUDA = -1002,     /* a CUDA runtime call failed */
+  CHOL_ETIMEOUT = -1003,  /* a bounded device wait ran out */
+  CHOL_ENOCONV = -1004,   /* iterative refinement did not reach the tolerance */
+  CHOL_ESTATE = -1005,    /* call made in the wrong state (e.g. solve before factor) */
+  CHOL_ENOTSUP = -1006    /* option combination not supported */
+};
+
+enum {
+  CHOL_PREC_FP64 = 0      /* every operation in IEEE binary64 */
+};
+
+typedef struct chol_options {
+  int32_t precision;       /* CHOL_PREC_*; default CHOL_PREC_FP64 */
+  int32_t small_max_cols;  /* supernodes with at most this many columns and at   */
+  int32_t small_max_panel; /* most this many panel entries (len*cols) take the   */
+                           /* one-CTA-per-supernode kernel; default 64 / 4096    */
+  int32_t block_cols;      /* column block of the blocked large-supernode path  */
+                           /* (POTRF/TRSM/update step); default 64               */
+  int64_t device_mem_cap;  /* refuse device allocations above this many bytes;  */
+                           /* 0 = no cap (for testing the ENOMEM path)          */
+} chol_options;
+
+/* Fill *opt with the defaults. */
+void chol_default_options(chol_options* opt);
+
+/*
+ * Symbolic analysis on the host (Sec. II): forms the pattern of P A P^T,
+ * the elimination tree (parent(j) = min{i > j : L_ij != 0}), column counts,
+ * the maximal supernode partition (columns j, j+1 share a supernode iff
+ * parent(j) = j+1 and colcount(j) = colcount(j+1) + 1), the supernodal
+ * elimination tree, the row structure of every supernode, the relative
+ * indices relind(J, K) of Sec. II-A for every supernode J and every ancestor
+ * K that J updates, the level schedule and the kernel task lists.
+ *   n       matrix order, >= 0
+ *   colptr  host, n+1 entries, colptr[0] = 0, non-decreasing
+ *   rowind  host, colptr[n] entries (lower triangle incl. diagonal)
+ *   perm    host, n entries (new->old) or NULL
+ *   opt     host or NULL for defaults
+ *   out     receives a new handle (library-owned; free with chol_destroy)
+ * Errors: -1..-5 for invalid arguments (malformed CSC: -2 or -3; bad
+ * permutation: -4), CHOL_ENOMEM. No device memory is touched here: device
+ * buffers are created by the first chol_factor.
+ */
+int chol_analyze(int32_t n, const int64_t* colptr, const int32_t* rowind,
+                 const int32_t* perm, const chol_options* opt, chol_handle** out);
+
+/*
+ * Numeric factorization A = L L^T (Sec. II-A, RL): scatters the values into
+ * the supernodal panels, then, level by level of the supernodal elimination
+ * tree (leaves first), POTRF of each diagonal block, TRSM of each panel,
+ * SYRK of each update matrix U_J = L_RJ L_RJ^T and the relind scatter-add of
+ * U_J into the ancestors (pull-ordered, atomic-free, deterministic).
+ *   values  device, colptr[n] doubles in the order of the analyzed rowind
+ *   stream  cudaStream_t as void*
+ * Returns CHOL_OK, +j (not positive definite at column j of P A P^T), or an
+ * error. Synchronizes `stream` once at the end to read the status word.
+ */
+int chol_factor(chol_handle* h, const double* values, void* stream);
+
+/*
+ * Solve A X = B with the computed factor: X = P^T L^{-T} L^{-1} P B
+ * (forward substitution over the levels leaves->root, backward substitution
+ * root->leaves).
+ *   b      device, n x nrhs column-major (leading dimension n); overwritten by X
+ *   nrhs   >= 0
+ * Returns CHOL_ESTATE without a successful chol_factor. Asynchronous.
+ */
+int chol_solve(chol_handle* h, double* b, int32_t nrhs, void* stream);
+
+/*
+ * log det A = 2 sum_j log L_jj, reduced in a fixed order (deterministic).
+ *   out    host pointer to one double
+ * Synchronizes `stream`.
+ */
+int chol_logdet(chol_handle* h, double* out, void* stream);
+
+/* Sizes of the symbolic structure, for sizing the chol_get_symbolic arrays. */
+typedef struct chol_info {
+  int32_t n;
+  int32_t nsuper;          /* number of supernodes */
+  int32_t nlevels;         /* levels of the supernodal elimination tree */
+  int32_t max_cols;        /* widest supernode */
+  int64_t nnz_a;           /* entries of the lower triangle of A */
+  int64_t nnz_l;           /* entries of L (diagonal included) */
+  int64_t n_relind_pairs;  /* (J, K) pairs with relind(J, K) */
+  int64_t relind_len;      /* total relind entries */
+  int64_t panel_doubles;   /* device storage of the supernodal panels */
+  int64_t update_doubles;  /* update-matrix workspace (largest level) */
+  double flops;            /* sum_j c_j^2, c_j = nnz(L_{*,j}) incl. diagonal */
+  int32_t n_small;         /* supernodes on the one-CTA kernel */
+  int32_t n_large;         /* supernodes on the blocked path */
+} chol_info;
+
+int chol_get_info(const chol_handle* h, chol_info* info);
+
+/*
+ * Copy out the symbolic results (host arrays, sized from chol_info; any
+ * pointer may be NULL to skip it):
+ *   parent[n]            etree parent of each column of P A P^T (-1 = root)
+ *   colcount[n]          nnz(L_{*,j}) including the diagonal
+ *   snode_ptr[nsuper+1]  first column of each supernode
+ *   snode_parent[nsuper] supernodal etree parent (-1 = root)
+ *   row_ptr[nsuper+1]    offsets into rows[] (int64)
+ *   rows[]               struct(J) ascending (J's own columns first)
+ *   relind_ptr[pairs+1]  offsets into relind[] (int64); pairs are ordered by
+ *                        J ascending, then K ascending
+ *   relind_target[pairs] K of each pair
+ *   relind[]             relind(J, K): for each row i of struct(J) ∩
+ *                        struct(K), in ascending i, the distance of i from the
+ *                        bottom of struct(K) (Sec. II-A definition)
+ */
+int chol_get_symbolic(const chol_handle* h, int32_t* parent, int32_t* colcount,
+                      int32_t* snode_ptr, int32_t* snode_parent, int64_t* row_ptr,
+                      int32_t* rows, int64_t* relind_ptr, int32_t* relind_target,
+                      int32_t* relind);
+
+/*
+ * Copy the factor to the host in compressed sparse column form of L (rows of
+ * each column ascending, diagonal first): lp[n+1] (int64), li[nnz_l],
+ * lx[nnz_l]. Synchronizes `stream`. CHOL_ESTATE before a factorization.
+ */
+int chol_get_factor(chol_handle* h, int64_t* lp, int32_t* li, double* lx, void* stream);
+
+/*
+ * Per-kernel-class launch statistics (tracing). Launch counts and the
+ * algorithmic flops and bytes of every launch are always accumulated; device
+ * time is measured with CUDA events on the launching stream only for the
+ * classes whose bit is set in the mask given to chol_profile (bit k = class k
+ * of chol_kernel_class). Times of asynchronous calls are resolved when the
+ * stats are read (which synchronizes the handle's last stream).
+ */
+enum chol_kernel_class {
+  CHOL_K_SCATTER = 0, CHOL_K_SMALL, CHOL_K_POTRF, CHOL_K_TRSM, CHOL_K_GEMM, CHOL_K_SYRK,
+  CHOL_K_ASSEMBLE, CHOL_K_SOLVE_DIAG, CHOL_K_SOLVE_FUPD, CHOL_K_SOLVE_FASM, CHOL_K_SOLVE_BPANEL,
+  CHOL_K_SOLVE_BUPD, CHOL_K_PERMUTE, CHOL_K_LOGDET, CHOL_K_NCLASSES
+};
+
+typedef struct chol_kernel_stat {
+  int64_t launches;   /* kernel launches of this class */
+  double flops;       /* algorithmic floating-point operations of those launches */
+  double bytes;       /* algorithmic DRAM bytes of those launches */
+  double ms;          /* summed device time of the timed launches */
+  int64_t timed;      /* how many launches were timed */
+} chol_kernel_stat;
+
+int chol_profile(chol_handle* h, uint32_t timing_mask);
+/* out[CHOL_K_NCLASSES]; reset != 0 clears the counters after reading. */
+int chol_get_stats(chol_handle* h, chol_kernel_stat* out, int32_t reset);
+
+/* Release the handle and all its device memory. NULL is a no-op. */
+void chol_destroy(chol_handle* h);
+
+/* Static description of a return code. */
+const char* chol_strerror(int code);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* CHOL_H_ */

@@ -58,6 +58,7 @@ def lib():
         L.orc_logdet.argtypes = [C.c_int32, P, P]
         L.orc_spmv.argtypes = [C.c_int32, P, P, P, C.c_int32, P, P]
         L.orc_backward_error.argtypes = [C.c_int32, P, P, P, C.c_int32, P, P, P]
+        L.orc_factor_residual_cols.argtypes = [C.c_int32, P, P, P, P, P, P, C.c_int32, P, P]
         L.orc_factor_residual.restype = C.c_double
         L.orc_factor_residual.argtypes = [C.c_int32, P, P, P, P, P, P]
         _lib = L
@@ -195,6 +196,16 @@ def factor_residual(n, bcolptr, browind, bvals, lp, li, lx):
     if r < 0:
         raise ValueError("L L^T or B has an entry outside the pattern of L")
     return r
+
+
+def factor_residual_cols(n, bcolptr, browind, bvals, lp, li, lx, cols):
+    """Per sampled column j: ||B_{j:,j} - (L L^T)_{j:,j}||_2 / ||B_{j:,j}||_2."""
+    cols = _c(cols, np.int32)
+    out = np.zeros(len(cols))
+    lib().orc_factor_residual_cols(n, _p(_c(bcolptr, np.int64)), _p(_c(browind, np.int32)),
+                                   _p(_c(bvals, np.float64)), _p(_c(lp, np.int64)), _p(_c(li, np.int32)),
+                                   _p(_c(lx, np.float64)), len(cols), _p(cols), _p(out))
+    return out
 
 
 def reference(problem, b=None):

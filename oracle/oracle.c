@@ -478,3 +478,41 @@ double orc_factor_residual(int32_t n, const int64_t* bcolptr, const int32_t* bro
   if (bad) return -1.0;
   return sqrt(num) / sqrt(den);
 }
+
+/* Residual of selected columns: for each listed column j, the lower part
+ * r_i = B_ij - sum_k L_ik L_jk (i >= j), returned as ||r||_2 / ||B_{j:n,j}||_2.
+ * Row j of L (the k with L_jk != 0) comes from a transposed index built once. */
+void orc_factor_residual_cols(int32_t n, const int64_t* bcolptr, const int32_t* browind,
+                              const double* bvals, const int64_t* lp, const int32_t* li,
+                              const double* lx, int32_t ncols, const int32_t* cols, double* out) {
+  int64_t nnz = lp[n];
+  int64_t* rcount = (int64_t*)calloc((size_t)(n + 1), sizeof(int64_t));
+  for (int64_t t = 0; t < nnz; ++t) rcount[li[t] + 1]++;
+  for (int32_t i = 0; i < n; ++i) rcount[i + 1] += rcount[i];
+  int64_t* fill = (int64_t*)malloc(sizeof(int64_t) * (size_t)(n > 0 ? n : 1));
+  for (int32_t i = 0; i < n; ++i) fill[i] = rcount[i];
+  int64_t* rent = (int64_t*)malloc(sizeof(int64_t) * (size_t)(nnz > 0 ? nnz : 1));
+  int32_t* rcol = (int32_t*)malloc(sizeof(int32_t) * (size_t)(nnz > 0 ? nnz : 1));
+  for (int32_t k = 0; k < n; ++k)
+    for (int64_t t = lp[k]; t < lp[k + 1]; ++t) { rent[fill[li[t]]] = t; rcol[fill[li[t]]] = k; fill[li[t]]++; }
+  double* w = (double*)calloc((size_t)(n > 0 ? n : 1), sizeof(double));
+  for (int32_t q = 0; q < ncols; ++q) {
+    int32_t j = cols[q];
+    double bn = 0.0;
+    for (int64_t t = bcolptr[j]; t < bcolptr[j + 1]; ++t) { w[browind[t]] += bvals[t]; bn += bvals[t] * bvals[t]; }
+    for (int64_t e = rcount[j]; e < rcount[j + 1]; ++e) {
+      int64_t tj = rent[e];
+      int32_t k = rcol[e];
+      double ljk = lx[tj];
+      for (int64_t t = tj; t < lp[k + 1]; ++t) w[li[t]] -= lx[t] * ljk;
+    }
+    double rn = 0.0;
+    for (int64_t e = rcount[j]; e < rcount[j + 1]; ++e) {
+      int32_t k = rcol[e];
+      for (int64_t t = rent[e]; t < lp[k + 1]; ++t) { rn += w[li[t]] * w[li[t]]; w[li[t]] = 0.0; }
+    }
+    for (int64_t t = bcolptr[j]; t < bcolptr[j + 1]; ++t) { rn += w[browind[t]] * w[browind[t]]; w[browind[t]] = 0.0; }
+    out[q] = sqrt(rn) / sqrt(bn);
+  }
+  free(w); free(rcount); free(fill); free(rent); free(rcol);
+}

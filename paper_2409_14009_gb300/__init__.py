@@ -1,0 +1,282 @@
+"""GB300 supernodal sparse Cholesky: thin Python binding of the C ABI (include/chol.h).
+
+Every numeric step runs in the CUDA library ``_build/libchol.so``; this module
+only marshals arguments (NumPy arrays for host data, raw device pointers and
+CUDA streams for device data; PyTorch tensors are accepted for convenience).
+Importing works without a GPU; loading the library fails loudly if it has not
+been built (``python -m paper_2409_14009_gb300.build`` or ``__graft_entry__.build()``).
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "_build", "libchol.so")
+
+CHOL_OK = 0
+CHOL_ENOMEM = -1001
+CHOL_ECUDA = -1002
+CHOL_ETIMEOUT = -1003
+CHOL_ENOCONV = -1004
+CHOL_ESTATE = -1005
+CHOL_ENOTSUP = -1006
+CHOL_PREC_FP64 = 0
+
+EXPORTED = ["chol_default_options", "chol_analyze", "chol_factor", "chol_solve", "chol_logdet",
+            "chol_get_info", "chol_get_symbolic", "chol_get_factor", "chol_profile",
+            "chol_get_stats", "chol_destroy", "chol_strerror"]
+
+KERNEL_CLASSES = ["scatter", "small", "potrf", "trsm", "gemm", "syrk", "assemble", "solve_diag",
+                  "solve_fupd", "solve_fasm", "solve_bpanel", "solve_bupd", "permute", "logdet"]
+
+
+class chol_options(C.Structure):
+    _fields_ = [("precision", C.c_int32), ("small_max_cols", C.c_int32),
+                ("small_max_panel", C.c_int32), ("block_cols", C.c_int32),
+                ("device_mem_cap", C.c_int64)]
+
+
+class chol_info(C.Structure):
+    _fields_ = [("n", C.c_int32), ("nsuper", C.c_int32), ("nlevels", C.c_int32),
+                ("max_cols", C.c_int32), ("nnz_a", C.c_int64), ("nnz_l", C.c_int64),
+                ("n_relind_pairs", C.c_int64), ("relind_len", C.c_int64),
+                ("panel_doubles", C.c_int64), ("update_doubles", C.c_int64),
+                ("flops", C.c_double), ("n_small", C.c_int32), ("n_large", C.c_int32)]
+
+
+class chol_kernel_stat(C.Structure):
+    _fields_ = [("launches", C.c_int64), ("flops", C.c_double), ("bytes", C.c_double),
+                ("ms", C.c_double), ("timed", C.c_int64)]
+
+
+class CholError(RuntimeError):
+    def __init__(self, code, where=""):
+        self.code = code
+        super().__init__("%s: %d (%s)" % (where, code, chol_strerror(code)))
+
+
+_lib = None
+
+
+def lib():
+    """Load libchol.so (raises if it is missing: there is no fallback)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise ImportError("libchol.so is not built: run __graft_entry__.build()")
+        L = C.CDLL(LIB_PATH)
+        P = C.c_void_p
+        L.chol_default_options.argtypes = [C.POINTER(chol_options)]
+        L.chol_analyze.argtypes = [C.c_int32, P, P, P, C.POINTER(chol_options), C.POINTER(C.c_void_p)]
+        L.chol_analyze.restype = C.c_int
+        L.chol_factor.argtypes = [P, P, P]
+        L.chol_factor.restype = C.c_int
+        L.chol_solve.argtypes = [P, P, C.c_int32, P]
+        L.chol_solve.restype = C.c_int
+        L.chol_logdet.argtypes = [P, C.POINTER(C.c_double), P]
+        L.chol_logdet.restype = C.c_int
+        L.chol_get_info.argtypes = [P, C.POINTER(chol_info)]
+        L.chol_get_info.restype = C.c_int
+        L.chol_get_symbolic.argtypes = [P] + [P] * 9
+        L.chol_get_symbolic.restype = C.c_int
+        L.chol_get_factor.argtypes = [P, P, P, P, P]
+        L.chol_get_factor.restype = C.c_int
+        L.chol_profile.argtypes = [P, C.c_uint32]
+        L.chol_profile.restype = C.c_int
+        L.chol_get_stats.argtypes = [P, C.POINTER(chol_kernel_stat), C.c_int32]
+        L.chol_get_stats.restype = C.c_int
+        L.chol_destroy.argtypes = [P]
+        L.chol_destroy.restype = None
+        L.chol_strerror.argtypes = [C.c_int]
+        L.chol_strerror.restype = C.c_char_p
+        _lib = L
+    return _lib
+
+
+def _np(a, dt):
+    return None if a is None else np.ascontiguousarray(a, dtype=dt)
+
+
+def _ptr(a):
+    return None if a is None else a.ctypes.data_as(C.c_void_p)
+
+
+def _dev_ptr(x):
+    """Raw device pointer of a torch tensor or an int."""
+    if x is None:
+        return None
+    if isinstance(x, int):
+        return C.c_void_p(x)
+    return C.c_void_p(x.data_ptr())
+
+
+def _stream(s):
+    if s is None:
+        return None
+    if isinstance(s, int):
+        return C.c_void_p(s)
+    return C.c_void_p(s.cuda_stream)
+
+
+# ---- the C ABI, name for name -------------------------------------------------
+
+def chol_default_options() -> chol_options:
+    o = chol_options()
+    lib().chol_default_options(C.byref(o))
+    return o
+
+
+def chol_analyze(n, colptr, rowind, perm=None, opt=None):
+    """Returns (rc, handle)."""
+    colptr = _np(colptr, np.int64); rowind = _np(rowind, np.int32); perm = _np(perm, np.int32)
+    h = C.c_void_p()
+    rc = lib().chol_analyze(int(n), _ptr(colptr), _ptr(rowind), _ptr(perm),
+                            C.byref(opt) if opt is not None else None, C.byref(h))
+    return rc, h
+
+
+def chol_factor(h, values, stream=None) -> int:
+    return lib().chol_factor(h, _dev_ptr(values), _stream(stream))
+
+
+def chol_solve(h, b, nrhs, stream=None) -> int:
+    return lib().chol_solve(h, _dev_ptr(b), int(nrhs), _stream(stream))
+
+
+def chol_logdet(h, stream=None):
+    out = C.c_double(0.0)
+    rc = lib().chol_logdet(h, C.byref(out), _stream(stream))
+    return rc, out.value
+
+
+def chol_get_info(h) -> chol_info:
+    info = chol_info()
+    rc = lib().chol_get_info(h, C.byref(info))
+    if rc:
+        raise CholError(rc, "chol_get_info")
+    return info
+
+
+def chol_get_symbolic(h) -> dict:
+    info = chol_get_info(h)
+    n, ns = info.n, info.nsuper
+    out = dict(parent=np.zeros(n, np.int32), colcount=np.zeros(n, np.int32),
+               snode_ptr=np.zeros(ns + 1, np.int32), snode_parent=np.zeros(ns, np.int32),
+               row_ptr=np.zeros(ns + 1, np.int64), rows=np.zeros(info.nnz_l and 1, np.int32),
+               relind_ptr=np.zeros(info.n_relind_pairs + 1, np.int64),
+               relind_target=np.zeros(max(info.n_relind_pairs, 1), np.int32),
+               relind=np.zeros(max(info.relind_len, 1), np.int32))
+    # rows[] holds sum over supernodes of |struct(J)|: size it from a first call
+    rc = lib().chol_get_symbolic(h, None, None, None, None, _ptr(out["row_ptr"]), None, None, None, None)
+    if rc:
+        raise CholError(rc, "chol_get_symbolic")
+    out["rows"] = np.zeros(max(int(out["row_ptr"][-1]), 1), np.int32)
+    rc = lib().chol_get_symbolic(h, *(_ptr(out[k]) for k in (
+        "parent", "colcount", "snode_ptr", "snode_parent", "row_ptr", "rows", "relind_ptr",
+        "relind_target", "relind")))
+    if rc:
+        raise CholError(rc, "chol_get_symbolic")
+    out["rows"] = out["rows"][: int(out["row_ptr"][-1])]
+    out["relind_target"] = out["relind_target"][: info.n_relind_pairs]
+    out["relind"] = out["relind"][: info.relind_len]
+    return out
+
+
+def chol_get_factor(h, stream=None):
+    info = chol_get_info(h)
+    lp = np.zeros(info.n + 1, np.int64)
+    li = np.zeros(max(info.nnz_l, 1), np.int32)
+    lx = np.zeros(max(info.nnz_l, 1), np.float64)
+    rc = lib().chol_get_factor(h, _ptr(lp), _ptr(li), _ptr(lx), _stream(stream))
+    if rc:
+        raise CholError(rc, "chol_get_factor")
+    return lp, li[: info.nnz_l], lx[: info.nnz_l]
+
+
+def chol_profile(h, timing_mask: int) -> int:
+    return lib().chol_profile(h, int(timing_mask))
+
+
+def chol_get_stats(h, reset: bool = False) -> dict:
+    """{class name: dict(launches, flops, bytes, ms, timed)}."""
+    arr = (chol_kernel_stat * len(KERNEL_CLASSES))()
+    rc = lib().chol_get_stats(h, arr, 1 if reset else 0)
+    if rc:
+        raise CholError(rc, "chol_get_stats")
+    return {nm: dict(launches=a.launches, flops=a.flops, bytes=a.bytes, ms=a.ms, timed=a.timed)
+            for nm, a in zip(KERNEL_CLASSES, arr)}
+
+
+def chol_destroy(h) -> None:
+    lib().chol_destroy(h)
+
+
+def chol_strerror(code) -> str:
+    return lib().chol_strerror(int(code)).decode()
+
+
+# ---- convenience wrapper over torch device memory ------------------------------
+
+class SparseCholesky:
+    """Analyze once, factor many times, solve many times (device-resident).
+
+    ``values`` and right-hand sides are float64 CUDA tensors; the current
+    torch stream is used unless one is given.
+    """
+
+    def __init__(self, n, colptr, rowind, perm=None, options: chol_options | None = None):
+        rc, h = chol_analyze(n, colptr, rowind, perm, options)
+        if rc:
+            raise CholError(rc, "chol_analyze")
+        self.h = h
+        self.n = int(n)
+        self.info = chol_get_info(h)
+
+    def _st(self, stream):
+        import torch
+        return stream if stream is not None else torch.cuda.current_stream()
+
+    def factor(self, values, stream=None):
+        rc = chol_factor(self.h, values, self._st(stream))
+        if rc:
+            raise CholError(rc, "chol_factor")
+
+    def solve_(self, b, stream=None):
+        """In place: b (n x nrhs, column-major = a transposed contiguous tensor, or 1-D)."""
+        nrhs = 1 if b.dim() == 1 else b.shape[1]
+        if b.dim() == 2 and nrhs > 1 and b.stride() != (1, self.n):
+            raise ValueError("b must be column-major (n x nrhs with strides (1, n))")
+        rc = chol_solve(self.h, b, nrhs, self._st(stream))
+        if rc:
+            raise CholError(rc, "chol_solve")
+        return b
+
+    def solve(self, b, stream=None):
+        x = b.t().contiguous().t() if b.dim() == 2 else b.clone()
+        return self.solve_(x, stream)
+
+    def logdet(self, stream=None):
+        rc, v = chol_logdet(self.h, self._st(stream))
+        if rc:
+            raise CholError(rc, "chol_logdet")
+        return v
+
+    def symbolic(self):
+        return chol_get_symbolic(self.h)
+
+    def factor_csc(self, stream=None):
+        return chol_get_factor(self.h, self._st(stream))
+
+    def close(self):
+        if self.h:
+            chol_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

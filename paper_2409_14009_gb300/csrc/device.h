@@ -1,0 +1,106 @@
+// device.h -- device-side state of a handle and helpers shared by the CUDA
+// translation units.
+#pragma once
+#include <cuda_runtime.h>
+
+#include <vector>
+
+#include "internal.h"
+
+struct DeviceState {
+  int device = -1;
+  int64_t bytes = 0;            // bytes allocated so far (for the optional cap)
+  double* L = nullptr;          // supernodal panels
+  double* U = nullptr;          // update-matrix workspace (one level)
+  SnodeDev* sn = nullptr;
+  int32_t* rows = nullptr;
+  int64_t* amap = nullptr;
+  int32_t* small_list = nullptr;
+  int32_t* potrf_list = nullptr;
+  int32_t* level_snodes = nullptr;
+  TileTask* trsm = nullptr;
+  TileTask* gemm = nullptr;
+  TileTask* syrk = nullptr;
+  AsmTask* asm_tasks = nullptr;
+  AsmSeg* asm_segs = nullptr;
+  int32_t* sdiag = nullptr;
+  TileTask* fupd = nullptr;
+  TileTask* bupd = nullptr;
+  TileTask* bpanel = nullptr;
+  int32_t* perm = nullptr;
+  int32_t* status = nullptr;    // device status word (first failing column + 1)
+  int32_t* status_host = nullptr;  // pinned
+  double* part = nullptr;       // logdet partial sums (one per supernode)
+  double* scalar_host = nullptr;   // pinned
+  double* scalar_dev = nullptr;
+  // solve workspaces (grown on demand)
+  double* Y = nullptr;          // permuted right-hand sides, n x chunk
+  double* W = nullptr;          // per-level panel products, w_rows_max x chunk
+};
+
+// Right-hand sides are processed in chunks of at most this many columns.
+constexpr int kSolveChunk = 16;
+
+#define CHOL_CUDA_TRY(expr)                 \
+  do {                                      \
+    cudaError_t e_ = (expr);                \
+    if (e_ != cudaSuccess) {                \
+      return e_ == cudaErrorMemoryAllocation ? CHOL_ENOMEM : CHOL_ECUDA; \
+    }                                       \
+  } while (0)
+
+// Launch accounting: counts, algorithmic flops/bytes, and (for the classes in
+// the mask) CUDA-event timing of each launch on its stream.
+struct Profiler {
+  uint32_t mask = 0;
+  chol_kernel_stat st[CHOL_K_NCLASSES] = {};
+  struct Pending {
+    int cls;
+    cudaEvent_t a, b;
+  };
+  std::vector<Pending> pending;
+  std::vector<cudaEvent_t> pool;
+  cudaStream_t last = nullptr;
+};
+
+inline Profiler* chol_prof(chol_handle* h) {
+  if (!h->prof) h->prof = new Profiler();
+  return h->prof;
+}
+
+// RAII scope around one kernel launch.
+struct KScope {
+  Profiler* p;
+  int cls;
+  cudaStream_t st;
+  cudaEvent_t a = nullptr, b = nullptr;
+  KScope(chol_handle* h, int cls_, cudaStream_t st_, double flops, double bytes)
+      : p(chol_prof(h)), cls(cls_), st(st_) {
+    p->st[cls].launches++;
+    p->st[cls].flops += flops;
+    p->st[cls].bytes += bytes;
+    p->last = st;
+    if (p->mask & (1u << cls)) {
+      for (cudaEvent_t* e : {&a, &b}) {
+        if (!p->pool.empty()) { *e = p->pool.back(); p->pool.pop_back(); }
+        else if (cudaEventCreate(e) != cudaSuccess) { *e = nullptr; }
+      }
+      if (a && b) cudaEventRecord(a, st);
+    }
+  }
+  ~KScope() {
+    if (a && b) {
+      cudaEventRecord(b, st);
+      p->pending.push_back({cls, a, b});
+    } else {
+      if (a) p->pool.push_back(a);
+      if (b) p->pool.push_back(b);
+    }
+  }
+};
+
+void chol_prof_resolve(chol_handle* h);   // sum the pending event pairs
+void chol_prof_free(chol_handle* h);
+
+int chol_device_ensure(chol_handle* h);   // allocate and upload on first use
+int chol_dalloc(chol_handle* h, void** p, size_t bytes);

@@ -1,0 +1,571 @@
+// factor.cu -- right-looking supernodal Cholesky (RL, Sec. II-A) on the GPU.
+//
+// Level by level of the supernodal elimination tree (leaves first), every
+// supernode J of the level is factored (POTRF on the diagonal block, TRSM on
+// the off-diagonal panel, Sec. II-A), its update matrix U_J = L_RJ L_RJ^T
+// (the DSYRK of Sec. II-A) is formed in a workspace sized for the largest
+// level (the preallocated update storage of Sec. II-A), and the update
+// matrices of the level are scatter-added into their ancestors through the
+// relative indices relind(J, K) (Sec. II-A assembly).
+//
+// Kernel classes
+//   k_scatter        A's values into the zeroed panels (HBM-bound gather/scatter)
+//   k_small          one CTA per small supernode: POTRF + TRSM + SYRK in shared memory
+//   k_potrf          blocked path, diagonal block of one column step
+//   k_trsm           blocked path, row tiles below the diagonal block
+//   k_gemm_trailing  blocked path, trailing update of the panel (FP64 DFMA tiles)
+//   k_syrk           blocked path, U_J tiles (lower triangle only)
+//   k_assemble       relind scatter-add, pull-ordered: each task owns target
+//                    columns and applies its contributors in a fixed order, so
+//                    no atomics and a bitwise-deterministic result
+//   k_logdet_*       2 sum log L_jj with a fixed-order reduction
+#include <climits>
+#include <cmath>
+#include <cstring>
+
+#include "device.h"
+
+namespace {
+
+constexpr int kSmallThreads = 128;
+constexpr int kGemmThreads = 256;
+constexpr int kAsmThreads = 256;
+
+// ---------------------------------------------------------------------------
+// dense Cholesky of the first s columns of a len x s column-major block in
+// shared memory (right-looking, one column per step). A non-positive or NaN
+// pivot records column fcol+k+1 in *status (smallest wins) and poisons the
+// column with NaN so that the failure propagates without stopping the grid.
+// ---------------------------------------------------------------------------
+__device__ void dense_chol_smem(double* P, int ld, int len, int s, int fcol, int* status) {
+  for (int k = 0; k < s; ++k) {
+    __syncthreads();
+    const double d = P[k + k * ld];
+    const bool bad = !(d > 0.0);
+    const double dk = bad ? __longlong_as_double(0x7ff8000000000000LL) : sqrt(d);
+    const double inv = 1.0 / dk;
+    for (int r = k + 1 + threadIdx.x; r < len; r += blockDim.x) P[r + k * ld] *= inv;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      P[k + k * ld] = dk;
+      if (bad) atomicMin(status, fcol + k + 1);
+    }
+    // rank-1 update of the trailing columns, one thread per row
+    for (int r = k + 1 + threadIdx.x; r < len; r += blockDim.x) {
+      const double lrk = P[r + k * ld];
+      const int jmax = r < s - 1 ? r : s - 1;
+      for (int j = k + 1; j <= jmax; ++j) P[r + j * ld] -= lrk * P[j + k * ld];
+    }
+  }
+  __syncthreads();
+}
+
+__global__ void k_status_init(int* status) { *status = INT_MAX; }
+
+__global__ void k_scatter(const double* __restrict__ vals, const int64_t* __restrict__ amap,
+                          int64_t nnz, double* __restrict__ L) {
+  for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < nnz;
+       t += (int64_t)gridDim.x * blockDim.x)
+    L[amap[t]] = vals[t];
+}
+
+// One CTA per small supernode: the whole len x s panel lives in shared memory.
+__global__ void __launch_bounds__(kSmallThreads)
+k_small(const SnodeDev* __restrict__ sn, const int32_t* __restrict__ list, double* __restrict__ L,
+        double* __restrict__ U, int* status) {
+  extern __shared__ double P[];
+  const SnodeDev d = sn[list[blockIdx.x]];
+  const int len = d.len, s = d.s, b = len - s;
+  double* G = L + d.loff;
+  for (int c = 0; c < s; ++c)
+    for (int r = threadIdx.x; r < len; r += blockDim.x) P[r + c * len] = G[r + (int64_t)c * d.ld];
+  dense_chol_smem(P, len, len, s, d.f, status);
+  for (int c = 0; c < s; ++c)
+    for (int r = c + threadIdx.x; r < len; r += blockDim.x) G[r + (int64_t)c * d.ld] = P[r + c * len];
+  if (b <= 0) return;
+  // U_J = L_RJ L_RJ^T, lower triangle, column-major b x b. Flat walk over the
+  // lower triangle: column c holds rows c..b-1.
+  double* Uj = U + d.uoff;
+  const double* R = P + s;  // row u of L_RJ is R[u + k*len]
+  const int64_t total = (int64_t)b * (b + 1) / 2;
+  int c = 0;
+  int64_t cstart = 0;  // flat index of (c, c)
+  for (int64_t q = threadIdx.x; q < total; q += blockDim.x) {
+    while (q >= cstart + (b - c)) { cstart += b - c; ++c; }
+    const int u = c + (int)(q - cstart);
+    double acc = 0.0;
+    for (int k = 0; k < s; ++k) acc += R[u + k * len] * R[c + k * len];
+    Uj[u + (int64_t)c * b] = acc;
+  }
+}
+
+// Blocked path, step k0: factor the kb x kb diagonal block of each listed supernode.
+__global__ void k_potrf(const SnodeDev* __restrict__ sn, const int32_t* __restrict__ list, int k0,
+                        int nb, double* __restrict__ L, int* status) {
+  extern __shared__ double P[];
+  const SnodeDev d = sn[list[blockIdx.x]];
+  const int kb = min(nb, d.s - k0);
+  double* G = L + d.loff + k0 + (int64_t)k0 * d.ld;
+  for (int c = 0; c < kb; ++c)
+    for (int r = threadIdx.x; r < kb; r += blockDim.x) P[r + c * kb] = G[r + (int64_t)c * d.ld];
+  dense_chol_smem(P, kb, kb, kb, d.f + k0, status);
+  for (int c = 0; c < kb; ++c)
+    for (int r = c + threadIdx.x; r < kb; r += blockDim.x) G[r + (int64_t)c * d.ld] = P[r + c * kb];
+}
+
+// Blocked path, step k0: rows [r0, r0+64) of column block [k0, k0+kb) become
+// X = B L_kk^{-T} (forward substitution along each row; one thread per row).
+__global__ void __launch_bounds__(kTile)
+k_trsm(const SnodeDev* __restrict__ sn, const TileTask* __restrict__ tasks, int nb,
+       double* __restrict__ L) {
+  extern __shared__ double sm[];
+  const TileTask t = tasks[blockIdx.x];
+  const SnodeDev d = sn[t.J];
+  const int kb = min(nb, d.s - t.k0);
+  double* Lk = sm;                      // kb x kb, ld kb
+  double* X = sm + kb * kb;             // kTile x kb, ld kTile
+  double* inv = X + kTile * kb;         // kb
+  const double* Gd = L + d.loff + t.k0 + (int64_t)t.k0 * d.ld;
+  for (int c = 0; c < kb; ++c)
+    for (int r = threadIdx.x; r < kb; r += blockDim.x) Lk[r + c * kb] = Gd[r + (int64_t)c * d.ld];
+  const int nrow = min(kTile, d.len - t.r0);
+  double* Gx = L + d.loff + t.r0 + (int64_t)t.k0 * d.ld;
+  for (int c = 0; c < kb; ++c)
+    if (threadIdx.x < nrow) X[threadIdx.x + c * kTile] = Gx[threadIdx.x + (int64_t)c * d.ld];
+  __syncthreads();
+  for (int c = threadIdx.x; c < kb; c += blockDim.x) inv[c] = 1.0 / Lk[c + c * kb];
+  __syncthreads();
+  const int r = threadIdx.x;
+  if (r < nrow) {
+    for (int j = 0; j < kb; ++j) {
+      double acc = X[r + j * kTile];
+      for (int i = 0; i < j; ++i) acc -= X[r + i * kTile] * Lk[j + i * kb];
+      X[r + j * kTile] = acc * inv[j];
+    }
+    for (int c = 0; c < kb; ++c) Gx[r + (int64_t)c * d.ld] = X[r + c * kTile];
+  }
+}
+
+// ---------------------------------------------------------------------------
+// 64 x 64 FP64 tile of C (op)= A B^T with K-chunks of 16 staged in shared
+// memory; 256 threads, 4 x 4 accumulators each (rows ty+16i, cols tx+16j).
+// Only entries with (row + rdiag >= col) are written (lower triangle of the
+// global matrix). SUB: C -= A B^T, else C = A B^T.
+// ---------------------------------------------------------------------------
+template <bool SUB>
+__device__ __forceinline__ void gemm_nt_tile(const double* __restrict__ A, int64_t lda,
+                                             const double* __restrict__ B, int64_t ldb, int K,
+                                             double* __restrict__ C, int64_t ldc, int M, int N,
+                                             int rdiag) {
+  constexpr int KC = 16;
+  __shared__ double As[KC][kTile];
+  __shared__ double Bs[KC][kTile];
+  const int tid = threadIdx.x;
+  const int tx = tid & 15, ty = tid >> 4;
+  double acc[4][4];
+#pragma unroll
+  for (int i = 0; i < 4; ++i)
+#pragma unroll
+    for (int j = 0; j < 4; ++j) acc[i][j] = 0.0;
+  for (int k = 0; k < K; k += KC) {
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      const int idx = tid + kGemmThreads * q;
+      const int kk = idx >> 6, r = idx & 63;
+      const bool kin = k + kk < K;
+      As[kk][r] = (kin && r < M) ? A[r + (int64_t)(k + kk) * lda] : 0.0;
+      Bs[kk][r] = (kin && r < N) ? B[r + (int64_t)(k + kk) * ldb] : 0.0;
+    }
+    __syncthreads();
+#pragma unroll
+    for (int kk = 0; kk < KC; ++kk) {
+      double a[4], bb[4];
+#pragma unroll
+      for (int i = 0; i < 4; ++i) a[i] = As[kk][ty + 16 * i];
+#pragma unroll
+      for (int j = 0; j < 4; ++j) bb[j] = Bs[kk][tx + 16 * j];
+#pragma unroll
+      for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j) acc[i][j] = fma(a[i], bb[j], acc[i][j]);
+    }
+    __syncthreads();
+  }
+#pragma unroll
+  for (int i = 0; i < 4; ++i)
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      const int r = ty + 16 * i, c = tx + 16 * j;
+      if (r < M && c < N && r + rdiag >= c) {
+        double* p = C + r + (int64_t)c * ldc;
+        *p = SUB ? (*p - acc[i][j]) : acc[i][j];
+      }
+    }
+}
+
+// Blocked path, step k0: trailing update of the panel,
+// P[r, c] -= sum_{k in block} P[r, k] P[c, k] for r >= c, c >= k0 + kb.
+__global__ void __launch_bounds__(kGemmThreads)
+k_gemm_trailing(const SnodeDev* __restrict__ sn, const TileTask* __restrict__ tasks, int nb,
+                double* __restrict__ L) {
+  const TileTask t = tasks[blockIdx.x];
+  const SnodeDev d = sn[t.J];
+  const int kb = min(nb, d.s - t.k0);
+  double* P = L + d.loff;
+  gemm_nt_tile<true>(P + t.r0 + (int64_t)t.k0 * d.ld, d.ld, P + t.c0 + (int64_t)t.k0 * d.ld, d.ld,
+                     kb, P + t.r0 + (int64_t)t.c0 * d.ld, d.ld, min(kTile, d.len - t.r0),
+                     min(kTile, d.s - t.c0), t.r0 - t.c0);
+}
+
+// Blocked path: U_J tile = L_RJ[r0.., :] L_RJ[c0.., :]^T (lower triangle).
+__global__ void __launch_bounds__(kGemmThreads)
+k_syrk(const SnodeDev* __restrict__ sn, const TileTask* __restrict__ tasks,
+       const double* __restrict__ L, double* __restrict__ U) {
+  const TileTask t = tasks[blockIdx.x];
+  const SnodeDev d = sn[t.J];
+  const int b = d.len - d.s;
+  const double* R = L + d.loff + d.s;
+  gemm_nt_tile<false>(R + t.r0, d.ld, R + t.c0, d.ld, d.s, U + d.uoff + t.r0 + (int64_t)t.c0 * b, b,
+                      min(kTile, b - t.r0), min(kTile, b - t.c0), t.r0 - t.c0);
+}
+
+// relind scatter-add of the level's update matrices into their ancestors.
+// Task = (target K, its columns [t0, t1)); segments = contributors in J order.
+// The relative positions of the rows of U_J inside struct(K) (relind(J, K) of
+// Sec. II-A, counted from the top instead of the bottom) are found by binary
+// search in struct(K), staged in shared memory, once per segment and reused by
+// every column of the segment. Within a segment every (column c, row u) of U_J
+// hits a distinct entry of K (relind is injective); a barrier separates
+// segments, so contributions to one entry are applied in a fixed order.
+__global__ void __launch_bounds__(kAsmThreads)
+k_assemble(const AsmTask* __restrict__ tasks, const AsmSeg* __restrict__ segs,
+           const SnodeDev* __restrict__ sn, const int32_t* __restrict__ rows,
+           const double* __restrict__ U, double* __restrict__ L) {
+  extern __shared__ int32_t ssm[];
+  const AsmTask t = tasks[blockIdx.x];
+  const SnodeDev dk = sn[t.K];
+  int32_t* sK = ssm;              // struct(K), dk.len entries
+  int32_t* pos = ssm + dk.len;    // positions of rows ca.. of the current segment
+  const int32_t* rk = rows + dk.roff;
+  for (int i = threadIdx.x; i < dk.len; i += blockDim.x) sK[i] = rk[i];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  constexpr int nwarps = kAsmThreads / 32;
+  for (int g = t.seg_begin; g < t.seg_end; ++g) {
+    const AsmSeg sg = segs[g];
+    const SnodeDev dj = sn[sg.J];
+    const int b = dj.len - dj.s;
+    const int32_t* rj = rows + dj.roff + dj.s;
+    __syncthreads();   // sK loaded / previous segment finished with pos[]
+    for (int u = sg.ca + threadIdx.x; u < b; u += blockDim.x) {
+      const int32_t key = rj[u];
+      int lo = t.t0, hi = dk.len;   // rows of U_J here are >= column t0 of K
+      while (lo < hi) {
+        const int mid = (lo + hi) >> 1;
+        if (sK[mid] < key) lo = mid + 1; else hi = mid;
+      }
+      pos[u - sg.ca] = lo;
+    }
+    __syncthreads();
+    const double* Uj = U + dj.uoff;
+    for (int c = sg.ca + warp; c < sg.cb; c += nwarps) {
+      double* Lc = L + dk.loff + (int64_t)(rj[c] - dk.f) * dk.ld;
+      const double* Uc = Uj + (int64_t)c * b;
+      for (int u = c + lane; u < b; u += 32) Lc[pos[u - sg.ca]] -= Uc[u];
+    }
+  }
+}
+
+// log det: per-supernode partial sums, then one fixed-order reduction.
+__global__ void k_logdet_part(const SnodeDev* __restrict__ sn, const double* __restrict__ L,
+                              double* __restrict__ part) {
+  __shared__ double red[128];
+  const SnodeDev d = sn[blockIdx.x];
+  double acc = 0.0;
+  for (int c = threadIdx.x; c < d.s; c += blockDim.x) acc += log(L[d.loff + c + (int64_t)c * d.ld]);
+  red[threadIdx.x] = acc;
+  __syncthreads();
+  for (int w = blockDim.x / 2; w > 0; w >>= 1) {
+    if (threadIdx.x < w) red[threadIdx.x] += red[threadIdx.x + w];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) part[blockIdx.x] = red[0];
+}
+
+__global__ void k_logdet_reduce(const double* __restrict__ part, int ns, double* out) {
+  __shared__ double red[1024];
+  double acc = 0.0;
+  for (int i = threadIdx.x; i < ns; i += blockDim.x) acc += part[i];
+  red[threadIdx.x] = acc;
+  __syncthreads();
+  for (int w = blockDim.x / 2; w > 0; w >>= 1) {
+    if (threadIdx.x < w) red[threadIdx.x] += red[threadIdx.x + w];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) *out = 2.0 * red[0];
+}
+
+// Copy the panels into compressed sparse column form (diagonal first).
+__global__ void k_to_csc(const SnodeDev* __restrict__ sn, const double* __restrict__ L,
+                         const int64_t* __restrict__ lp, double* __restrict__ lx) {
+  const SnodeDev d = sn[blockIdx.x];
+  for (int c = 0; c < d.s; ++c) {
+    const int64_t base = lp[d.f + c];
+    for (int r = c + threadIdx.x; r < d.len; r += blockDim.x)
+      lx[base + (r - c)] = L[d.loff + r + (int64_t)c * d.ld];
+  }
+}
+
+template <class T>
+int upload(chol_handle* h, T** dst, const std::vector<T>& v) {
+  if (v.empty()) { *dst = nullptr; return CHOL_OK; }
+  int rc = chol_dalloc(h, (void**)dst, v.size() * sizeof(T));
+  if (rc) return rc;
+  CHOL_CUDA_TRY(cudaMemcpy(*dst, v.data(), v.size() * sizeof(T), cudaMemcpyHostToDevice));
+  return CHOL_OK;
+}
+
+inline unsigned grid1d(int64_t n, int threads) {
+  int64_t g = (n + threads - 1) / threads;
+  if (g > 152 * 32) g = 152 * 32;
+  return (unsigned)(g > 0 ? g : 1);
+}
+
+}  // namespace
+
+void chol_prof_resolve(chol_handle* h) {
+  Profiler* p = h->prof;
+  if (!p || p->pending.empty()) return;
+  cudaEventSynchronize(p->pending.back().b);
+  for (auto& q : p->pending) {
+    float ms = 0.f;
+    if (cudaEventElapsedTime(&ms, q.a, q.b) == cudaSuccess) {
+      p->st[q.cls].ms += ms;
+      p->st[q.cls].timed++;
+    }
+    p->pool.push_back(q.a);
+    p->pool.push_back(q.b);
+  }
+  p->pending.clear();
+  cudaGetLastError();
+}
+
+void chol_prof_free(chol_handle* h) {
+  Profiler* p = h->prof;
+  if (!p) return;
+  chol_prof_resolve(h);
+  for (cudaEvent_t e : p->pool) cudaEventDestroy(e);
+  delete p;
+  h->prof = nullptr;
+}
+
+extern "C" int chol_profile(chol_handle* h, uint32_t timing_mask) {
+  if (!h) return -1;
+  chol_prof_resolve(h);
+  chol_prof(h)->mask = timing_mask;
+  return CHOL_OK;
+}
+
+extern "C" int chol_get_stats(chol_handle* h, chol_kernel_stat* out, int32_t reset) {
+  if (!h) return -1;
+  if (!out) return -2;
+  chol_prof_resolve(h);
+  Profiler* p = chol_prof(h);
+  std::memcpy(out, p->st, sizeof(p->st));
+  if (reset) std::memset(p->st, 0, sizeof(p->st));
+  return CHOL_OK;
+}
+
+int chol_dalloc(chol_handle* h, void** p, size_t bytes) {
+  DeviceState* D = h->dev;
+  *p = nullptr;
+  if (bytes == 0) return CHOL_OK;
+  if (h->opt.device_mem_cap > 0 && D->bytes + (int64_t)bytes > h->opt.device_mem_cap) return CHOL_ENOMEM;
+  cudaError_t e = cudaMalloc(p, bytes);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    *p = nullptr;
+    return e == cudaErrorMemoryAllocation ? CHOL_ENOMEM : CHOL_ECUDA;
+  }
+  D->bytes += (int64_t)bytes;
+  return CHOL_OK;
+}
+
+void chol_device_free(chol_handle* h) {
+  chol_prof_free(h);
+  DeviceState* D = h->dev;
+  if (!D) return;
+  int cur = -1;
+  cudaGetDevice(&cur);
+  if (D->device >= 0) cudaSetDevice(D->device);
+  void* ptrs[] = {D->L, D->U, D->sn, D->rows, D->amap, D->small_list, D->potrf_list,
+                  D->level_snodes, D->trsm, D->gemm, D->syrk, D->asm_tasks, D->asm_segs, D->sdiag,
+                  D->fupd, D->bupd, D->bpanel, D->perm, D->status, D->part, D->scalar_dev, D->Y, D->W};
+  for (void* p : ptrs)
+    if (p) cudaFree(p);
+  if (D->status_host) cudaFreeHost(D->status_host);
+  if (D->scalar_host) cudaFreeHost(D->scalar_host);
+  if (cur >= 0) cudaSetDevice(cur);
+  delete D;
+  h->dev = nullptr;
+}
+
+int chol_device_ensure(chol_handle* h) {
+  if (h->dev) {
+    int cur = -1;
+    CHOL_CUDA_TRY(cudaGetDevice(&cur));
+    return cur == h->dev->device ? CHOL_OK : CHOL_ESTATE;
+  }
+  h->dev = new DeviceState();
+  DeviceState* D = h->dev;
+  int rc = CHOL_OK;
+  auto fail = [&](int code) {
+    chol_device_free(h);
+    return code;
+  };
+  if (cudaGetDevice(&D->device) != cudaSuccess) return fail(CHOL_ECUDA);
+  if ((rc = chol_dalloc(h, (void**)&D->L, sizeof(double) * (size_t)std::max<int64_t>(h->panel_doubles, 1)))) return fail(rc);
+  if ((rc = chol_dalloc(h, (void**)&D->U, sizeof(double) * (size_t)std::max<int64_t>(h->update_doubles, 1)))) return fail(rc);
+  if ((rc = upload(h, &D->sn, h->snodes))) return fail(rc);
+  if ((rc = upload(h, &D->rows, h->rows))) return fail(rc);
+  if ((rc = upload(h, &D->amap, h->amap))) return fail(rc);
+  if ((rc = upload(h, &D->small_list, h->small_list))) return fail(rc);
+  if ((rc = upload(h, &D->potrf_list, h->potrf_list))) return fail(rc);
+  if ((rc = upload(h, &D->level_snodes, h->level_snodes))) return fail(rc);
+  if ((rc = upload(h, &D->trsm, h->trsm_tasks))) return fail(rc);
+  if ((rc = upload(h, &D->gemm, h->gemm_tasks))) return fail(rc);
+  if ((rc = upload(h, &D->syrk, h->syrk_tasks))) return fail(rc);
+  if ((rc = upload(h, &D->asm_tasks, h->asm_tasks))) return fail(rc);
+  if ((rc = upload(h, &D->asm_segs, h->asm_segs))) return fail(rc);
+  if ((rc = upload(h, &D->sdiag, h->sdiag_list))) return fail(rc);
+  if ((rc = upload(h, &D->fupd, h->fupd_tasks))) return fail(rc);
+  if ((rc = upload(h, &D->bupd, h->bupd_tasks))) return fail(rc);
+  if ((rc = upload(h, &D->bpanel, h->bpanel_tasks))) return fail(rc);
+  if ((rc = upload(h, &D->perm, h->perm))) return fail(rc);
+  if ((rc = chol_dalloc(h, (void**)&D->status, sizeof(int32_t)))) return fail(rc);
+  if ((rc = chol_dalloc(h, (void**)&D->part, sizeof(double) * (size_t)std::max(h->ns, 1)))) return fail(rc);
+  if ((rc = chol_dalloc(h, (void**)&D->scalar_dev, sizeof(double)))) return fail(rc);
+  if (cudaMallocHost((void**)&D->status_host, sizeof(int32_t)) != cudaSuccess) return fail(CHOL_ENOMEM);
+  if (cudaMallocHost((void**)&D->scalar_host, sizeof(double)) != cudaSuccess) return fail(CHOL_ENOMEM);
+  static bool attrs_done = false;
+  if (!attrs_done) {
+    const int trsm_smem = (64 * 64 + kTile * 64 + 64) * (int)sizeof(double);
+    if (cudaFuncSetAttribute(k_trsm, cudaFuncAttributeMaxDynamicSharedMemorySize, trsm_smem) != cudaSuccess)
+      return fail(CHOL_ECUDA);
+    if (cudaFuncSetAttribute(k_assemble, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024) != cudaSuccess)
+      return fail(CHOL_ECUDA);
+    attrs_done = true;
+  }
+  return CHOL_OK;
+}
+
+extern "C" int chol_factor(chol_handle* h, const double* values, void* stream) {
+  if (!h) return -1;
+  if (!values && h->nnz_a > 0) return -2;
+  if ((int64_t)h->max_len * 2 * (int64_t)sizeof(int32_t) > 200 * 1024) return CHOL_ENOTSUP;
+  int rc = chol_device_ensure(h);
+  if (rc) return rc;
+  DeviceState* D = h->dev;
+  cudaStream_t st = (cudaStream_t)stream;
+  const int nb = h->opt.block_cols;
+  h->factored = false;
+  k_status_init<<<1, 1, 0, st>>>(D->status);
+  CHOL_CUDA_TRY(cudaMemsetAsync(D->L, 0, sizeof(double) * (size_t)h->panel_doubles, st));
+  if (h->nnz_a > 0) {
+    KScope ks(h, CHOL_K_SCATTER, st, 0.0, 24.0 * (double)h->nnz_a);
+    k_scatter<<<grid1d(h->nnz_a, 256), 256, 0, st>>>(values, D->amap, h->nnz_a, D->L);
+  }
+  for (const LevelPlan& P : h->levels) {
+    if (P.small_n > 0) {
+      KScope ks(h, CHOL_K_SMALL, st, P.small_flops, P.small_bytes);
+      k_small<<<P.small_n, kSmallThreads, sizeof(double) * P.small_max_panel, st>>>(
+          D->sn, D->small_list + P.small_b, D->L, D->U, D->status);
+    }
+    for (size_t k = 0; k < P.steps.size(); ++k) {
+      const StepRange& s = P.steps[k];
+      const int k0 = (int)k * nb;
+      if (s.potrf_n > 0) {
+        KScope ks(h, CHOL_K_POTRF, st, s.potrf_flops, 16.0 * nb * nb * s.potrf_n);
+        k_potrf<<<s.potrf_n, 128, sizeof(double) * nb * nb, st>>>(D->sn, D->potrf_list + s.potrf_b, k0, nb,
+                                                                  D->L, D->status);
+      }
+      if (s.trsm_n > 0) {
+        KScope ks(h, CHOL_K_TRSM, st, s.trsm_flops, 16.0 * kTile * nb * s.trsm_n);
+        k_trsm<<<s.trsm_n, kTile, sizeof(double) * (nb * nb + kTile * nb + nb), st>>>(
+            D->sn, D->trsm + s.trsm_b, nb, D->L);
+      }
+      if (s.gemm_n > 0) {
+        KScope ks(h, CHOL_K_GEMM, st, s.gemm_flops, 16.0 * kTile * kTile * s.gemm_n);
+        k_gemm_trailing<<<s.gemm_n, kGemmThreads, 0, st>>>(D->sn, D->gemm + s.gemm_b, nb, D->L);
+      }
+    }
+    if (P.syrk_n > 0) {
+      KScope ks(h, CHOL_K_SYRK, st, P.syrk_flops, 8.0 * kTile * kTile * P.syrk_n);
+      k_syrk<<<P.syrk_n, kGemmThreads, 0, st>>>(D->sn, D->syrk + P.syrk_b, D->L, D->U);
+    }
+    if (P.asm_n > 0) {
+      KScope ks(h, CHOL_K_ASSEMBLE, st, P.asm_entries, 24.0 * P.asm_entries);
+      k_assemble<<<P.asm_n, kAsmThreads, sizeof(int32_t) * 2 * h->max_len, st>>>(
+          D->asm_tasks + P.asm_b, D->asm_segs, D->sn, D->rows, D->U, D->L);
+    }
+  }
+  CHOL_CUDA_TRY(cudaGetLastError());
+  CHOL_CUDA_TRY(cudaMemcpyAsync(D->status_host, D->status, sizeof(int32_t), cudaMemcpyDeviceToHost, st));
+  CHOL_CUDA_TRY(cudaStreamSynchronize(st));
+  const int32_t s = *D->status_host;
+  if (s != INT_MAX) return s;
+  h->factored = true;
+  return CHOL_OK;
+}
+
+extern "C" int chol_logdet(chol_handle* h, double* out, void* stream) {
+  if (!h) return -1;
+  if (!out) return -2;
+  if (!h->factored) return CHOL_ESTATE;
+  DeviceState* D = h->dev;
+  cudaStream_t st = (cudaStream_t)stream;
+  if (h->ns > 0) {
+    KScope ks(h, CHOL_K_LOGDET, st, (double)h->n, 8.0 * h->n);
+    k_logdet_part<<<h->ns, 128, 0, st>>>(D->sn, D->L, D->part);
+    k_logdet_reduce<<<1, 1024, 0, st>>>(D->part, h->ns, D->scalar_dev);
+  } else {
+    CHOL_CUDA_TRY(cudaMemsetAsync(D->scalar_dev, 0, sizeof(double), st));
+  }
+  CHOL_CUDA_TRY(cudaGetLastError());
+  CHOL_CUDA_TRY(cudaMemcpyAsync(D->scalar_host, D->scalar_dev, sizeof(double), cudaMemcpyDeviceToHost, st));
+  CHOL_CUDA_TRY(cudaStreamSynchronize(st));
+  *out = *D->scalar_host;
+  return CHOL_OK;
+}
+
+extern "C" int chol_get_factor(chol_handle* h, int64_t* lp, int32_t* li, double* lx, void* stream) {
+  if (!h) return -1;
+  if (!h->factored) return CHOL_ESTATE;
+  DeviceState* D = h->dev;
+  cudaStream_t st = (cudaStream_t)stream;
+  std::vector<int64_t> hp(h->n + 1, 0);
+  for (int32_t j = 0; j < h->n; ++j) hp[j + 1] = hp[j] + h->colcount[j];
+  if (lp) std::memcpy(lp, hp.data(), sizeof(int64_t) * hp.size());
+  if (li) {
+    for (int32_t J = 0; J < h->ns; ++J) {
+      const SnodeDev& d = h->snodes[J];
+      for (int c = 0; c < d.s; ++c)
+        for (int r = c; r < d.len; ++r) li[hp[d.f + c] + (r - c)] = h->rows[d.roff + r];
+    }
+  }
+  if (lx && h->nnz_l > 0) {
+    int64_t* dlp = nullptr;
+    double* dlx = nullptr;
+    int rc = chol_dalloc(h, (void**)&dlp, sizeof(int64_t) * hp.size());
+    if (rc) return rc;
+    rc = chol_dalloc(h, (void**)&dlx, sizeof(double) * (size_t)h->nnz_l);
+    if (rc) { cudaFree(dlp); D->bytes -= sizeof(int64_t) * hp.size(); return rc; }
+    CHOL_CUDA_TRY(cudaMemcpyAsync(dlp, hp.data(), sizeof(int64_t) * hp.size(), cudaMemcpyHostToDevice, st));
+    k_to_csc<<<h->ns, 128, 0, st>>>(D->sn, D->L, dlp, dlx);
+    CHOL_CUDA_TRY(cudaMemcpyAsync(lx, dlx, sizeof(double) * (size_t)h->nnz_l, cudaMemcpyDeviceToHost, st));
+    CHOL_CUDA_TRY(cudaStreamSynchronize(st));
+    cudaFree(dlp);
+    cudaFree(dlx);
+    D->bytes -= (int64_t)(sizeof(int64_t) * hp.size() + sizeof(double) * (size_t)h->nnz_l);
+  }
+  return CHOL_OK;
+}

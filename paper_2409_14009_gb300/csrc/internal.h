@@ -1,0 +1,104 @@
+// internal.h -- handle layout shared by the host analysis and the CUDA driver.
+#pragma once
+#include <cstdint>
+#include <vector>
+
+#include "chol.h"
+
+// Per-supernode descriptor (device copy).
+struct SnodeDev {
+  int64_t loff;  // offset of the panel in L storage (doubles), column-major, leading dim ld
+  int64_t roff;  // offset of struct(J) in the rows[] array
+  int64_t uoff;  // offset of U_J (b x b, column-major, ld b) in the update workspace
+  int64_t wpre;  // prefix of b over the level (solve workspace offset = wpre * nrhs)
+  int32_t f;     // first column
+  int32_t s;     // number of columns
+  int32_t len;   // |struct(J)| (rows of the panel)
+  int32_t ld;    // leading dimension of the panel
+};
+
+// Blocked large-supernode task: supernode J, column step k0, tile origin (r0, c0).
+struct TileTask {
+  int32_t J, k0, r0, c0;
+};
+
+// Pull-ordered assembly: one task owns columns [t0, t1) of target supernode K and
+// applies its segments in order; a segment is the part of U_J (columns [ca, cb),
+// rows c.. b-1 of each column c) that lands there.
+struct AsmTask {
+  int32_t K, t0, t1, seg_begin, seg_end, pad0, pad1, pad2;
+};
+struct AsmSeg {
+  int32_t J, ca, cb, pad;
+};
+
+struct StepRange {
+  int32_t potrf_b, potrf_n, trsm_b, trsm_n, gemm_b, gemm_n;
+  double potrf_flops, trsm_flops, gemm_flops;
+};
+
+// Blocked triangular-solve step k0 of one level: diagonal blocks of every
+// supernode with s > k0, the row tiles below them (forward) and the column
+// tiles left of them (backward).
+struct SolveStep {
+  int32_t diag_b, diag_n, fupd_b, fupd_n, bupd_b, bupd_n;
+};
+
+struct LevelPlan {
+  int32_t snode_b, snode_n;   // all supernodes of the level (in level_snodes)
+  int32_t small_b, small_n;   // one-CTA supernodes (in small_list)
+  int32_t small_max_panel;    // largest len*s among them (shared memory sizing)
+  std::vector<StepRange> steps;
+  int32_t syrk_b, syrk_n;     // U tiles (in syrk_tasks)
+  int32_t asm_b, asm_n;       // assembly tasks
+  std::vector<SolveStep> ssteps;
+  int32_t bpanel_b, bpanel_n; // backward-solve panel column blocks (TileTask: J, c0)
+  int64_t u_doubles;          // update workspace used by this level
+  int64_t w_rows;             // sum of b over the level (solve workspace rows)
+  double small_flops, syrk_flops, asm_entries;   // algorithmic work per launch
+  double small_bytes;
+};
+
+struct DeviceState;  // defined in the CUDA driver
+struct Profiler;     // defined in the CUDA driver
+
+struct chol_handle {
+  chol_options opt;
+  int32_t n = 0;
+  int64_t nnz_a = 0;
+  std::vector<int32_t> perm, iperm;
+  // symbolic
+  std::vector<int32_t> parent, colcount;
+  int32_t ns = 0, nlevels = 0, max_cols = 0;
+  std::vector<int32_t> sptr, sparent, level;
+  std::vector<int64_t> rowptr;
+  std::vector<int32_t> rows;
+  std::vector<SnodeDev> snodes;
+  std::vector<int64_t> amap;        // entry t of A -> position in L storage
+  int64_t nnz_l = 0, panel_doubles = 0, update_doubles = 0, w_rows_max = 0;
+  double flops = 0.0;
+  // (J, K) pairs: J updates ancestor K through U_J columns [c0, c1) (J ascending, K ascending)
+  std::vector<int32_t> rel_J, rel_K, rel_c0, rel_c1;
+  int64_t relind_len = 0;           // sum over pairs of (b_J - c0)
+  int32_t max_len = 0;              // longest struct(J)
+  // schedule
+  std::vector<LevelPlan> levels;
+  std::vector<int32_t> level_snodes, small_list, potrf_list;
+  std::vector<TileTask> trsm_tasks, gemm_tasks, syrk_tasks, bpanel_tasks;
+  std::vector<int32_t> sdiag_list;             // solve: supernode per (level, step)
+  std::vector<TileTask> fupd_tasks, bupd_tasks; // solve: (J, k0, r0) / (J, k0, c0)
+  std::vector<AsmTask> asm_tasks;
+  std::vector<AsmSeg> asm_segs;
+  int32_t n_small = 0, n_large = 0;
+  // numeric state
+  bool factored = false;
+  DeviceState* dev = nullptr;
+  Profiler* prof = nullptr;
+};
+
+// Tile sizes shared by the schedule builder and the kernels.
+constexpr int kTile = 64;        // GEMM/SYRK tile edge and TRSM row block
+constexpr int kAsmCols = 64;     // assembly task width (target columns)
+constexpr int kBwdCols = 64;     // backward-solve panel column block
+
+void chol_device_free(chol_handle* h);  // CUDA side

@@ -324,3 +324,19 @@ def test_permute_rejects_bad_perm():
     bad = perm.copy(); bad[0] = bad[1]
     with pytest.raises(ValueError):
         oracle.permute(10, cp, ri, vx, bad)
+
+
+def test_sampled_column_residual_matches_dense():
+    A, cp, ri, vx, perm = random_spd(50, 0.1, 21)
+    bp, bi, bx = oracle.permute(50, cp, ri, vx, perm)
+    fac = oracle.Factor(50, bp, bi, bx)
+    lx = fac.lx * (1.0 + np.random.RandomState(2).uniform(-1e-7, 1e-7, fac.lx.shape))
+    Lp = csc_to_dense_lower(50, fac.lp, fac.li, lx)
+    P = np.eye(50)[perm]
+    B = P @ A @ P.T
+    cols = np.array([0, 7, 23, 49])
+    got = oracle.factor_residual_cols(50, bp, bi, bx, fac.lp, fac.li, lx, cols)
+    R = B - Lp @ Lp.T
+    for q, j in enumerate(cols):
+        exp = np.linalg.norm(R[j:, j]) / np.linalg.norm(B[j:, j])
+        assert got[q] == pytest.approx(exp, rel=1e-6)
