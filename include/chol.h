@@ -61,6 +61,13 @@ typedef struct chol_options {
                            /* (POTRF/TRSM/update step); default 64               */
   int64_t device_mem_cap;  /* refuse device allocations above this many bytes;  */
                            /* 0 = no cap (for testing the ENOMEM path)          */
+  double merge_growth;     /* relaxed supernode merging budget (Sec. IV setup): */
+                           /* merge adjacent (J, parent(J)) pairs, fewest added */
+                           /* explicit zeros first (ties: smaller J), while the */
+                           /* stored entries grow by at most this fraction of   */
+                           /* nnz(L); 0 = off (the maximal partition, default)  */
+  int32_t small_max_rows;  /* rows limit of the one-CTA kernel; default 128     */
+  int32_t reserved;
 } chol_options;
 
 /* Fill *opt with the defaults. */
@@ -132,6 +139,10 @@ typedef struct chol_info {
   double flops;            /* sum_j c_j^2, c_j = nnz(L_{*,j}) incl. diagonal */
   int32_t n_small;         /* supernodes on the one-CTA kernel */
   int32_t n_large;         /* supernodes on the blocked path */
+  int32_t nsuper_storage;  /* supernodes after relaxed merging (= nsuper if off) */
+  int32_t reserved;
+  int64_t nnz_stored;      /* stored factor entries incl. explicit zeros of merging */
+  double flops_stored;     /* sum over stored columns of their stored count^2 */
 } chol_info;
 
 int chol_get_info(const chol_handle* h, chol_info* info);
@@ -156,6 +167,15 @@ int chol_get_symbolic(const chol_handle* h, int32_t* parent, int32_t* colcount,
                       int32_t* snode_ptr, int32_t* snode_parent, int64_t* row_ptr,
                       int32_t* rows, int64_t* relind_ptr, int32_t* relind_target,
                       int32_t* relind);
+
+/*
+ * The storage partition actually used by the numeric kernels (the maximal
+ * partition, or the coarser one after relaxed merging): snode_ptr[nsuper_storage+1],
+ * snode_parent[nsuper_storage], row_ptr[nsuper_storage+1] and rows[] (struct of
+ * each stored supernode: union of the structures of its columns). NULL skips.
+ */
+int chol_get_partition(const chol_handle* h, int32_t* snode_ptr, int32_t* snode_parent,
+                       int64_t* row_ptr, int32_t* rows);
 
 /*
  * Copy the factor to the host in compressed sparse column form of L (rows of

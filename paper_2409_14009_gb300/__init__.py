@@ -26,7 +26,7 @@ CHOL_ENOTSUP = -1006
 CHOL_PREC_FP64 = 0
 
 EXPORTED = ["chol_default_options", "chol_analyze", "chol_factor", "chol_solve", "chol_logdet",
-            "chol_get_info", "chol_get_symbolic", "chol_get_factor", "chol_profile",
+            "chol_get_info", "chol_get_symbolic", "chol_get_partition", "chol_get_factor", "chol_profile",
             "chol_get_stats", "chol_destroy", "chol_strerror"]
 
 KERNEL_CLASSES = ["scatter", "small", "potrf", "trsm", "gemm", "syrk", "assemble", "solve_diag",
@@ -36,7 +36,8 @@ KERNEL_CLASSES = ["scatter", "small", "potrf", "trsm", "gemm", "syrk", "assemble
 class chol_options(C.Structure):
     _fields_ = [("precision", C.c_int32), ("small_max_cols", C.c_int32),
                 ("small_max_panel", C.c_int32), ("block_cols", C.c_int32),
-                ("device_mem_cap", C.c_int64)]
+                ("device_mem_cap", C.c_int64), ("merge_growth", C.c_double),
+                ("small_max_rows", C.c_int32), ("reserved", C.c_int32)]
 
 
 class chol_info(C.Structure):
@@ -44,7 +45,9 @@ class chol_info(C.Structure):
                 ("max_cols", C.c_int32), ("nnz_a", C.c_int64), ("nnz_l", C.c_int64),
                 ("n_relind_pairs", C.c_int64), ("relind_len", C.c_int64),
                 ("panel_doubles", C.c_int64), ("update_doubles", C.c_int64),
-                ("flops", C.c_double), ("n_small", C.c_int32), ("n_large", C.c_int32)]
+                ("flops", C.c_double), ("n_small", C.c_int32), ("n_large", C.c_int32),
+                ("nsuper_storage", C.c_int32), ("reserved", C.c_int32), ("nnz_stored", C.c_int64),
+                ("flops_stored", C.c_double)]
 
 
 class chol_kernel_stat(C.Structure):
@@ -82,6 +85,8 @@ def lib():
         L.chol_get_info.restype = C.c_int
         L.chol_get_symbolic.argtypes = [P] + [P] * 9
         L.chol_get_symbolic.restype = C.c_int
+        L.chol_get_partition.argtypes = [P, P, P, P, P]
+        L.chol_get_partition.restype = C.c_int
         L.chol_get_factor.argtypes = [P, P, P, P, P]
         L.chol_get_factor.restype = C.c_int
         L.chol_profile.argtypes = [P, C.c_uint32]
@@ -182,6 +187,23 @@ def chol_get_symbolic(h) -> dict:
     out["rows"] = out["rows"][: int(out["row_ptr"][-1])]
     out["relind_target"] = out["relind_target"][: info.n_relind_pairs]
     out["relind"] = out["relind"][: info.relind_len]
+    return out
+
+
+def chol_get_partition(h) -> dict:
+    """Storage partition used by the kernels (after relaxed merging, if enabled)."""
+    info = chol_get_info(h)
+    ns = info.nsuper_storage
+    out = dict(snode_ptr=np.zeros(ns + 1, np.int32), snode_parent=np.zeros(max(ns, 1), np.int32),
+               row_ptr=np.zeros(ns + 1, np.int64))
+    rc = lib().chol_get_partition(h, _ptr(out["snode_ptr"]), _ptr(out["snode_parent"]),
+                                  _ptr(out["row_ptr"]), None)
+    if rc:
+        raise CholError(rc, "chol_get_partition")
+    out["rows"] = np.zeros(max(int(out["row_ptr"][-1]), 1), np.int32)
+    lib().chol_get_partition(h, None, None, None, _ptr(out["rows"]))
+    out["rows"] = out["rows"][: int(out["row_ptr"][-1])]
+    out["snode_parent"] = out["snode_parent"][:ns]
     return out
 
 

@@ -10,6 +10,8 @@
 #include <cstring>
 #include <new>
 #include <numeric>
+#include <queue>
+#include <tuple>
 #include <stdexcept>
 
 #include "internal.h"
@@ -22,6 +24,8 @@ extern "C" void chol_default_options(chol_options* opt) {
   opt->small_max_panel = 4096;
   opt->block_cols = 64;
   opt->device_mem_cap = 0;
+  opt->merge_growth = 0.0;
+  opt->small_max_rows = 128;
 }
 
 namespace {
@@ -52,9 +56,139 @@ int validate(int32_t n, const int64_t* colptr, const int32_t* rowind, const int3
     if (opt->small_max_cols < 1 || opt->small_max_panel < 1 || opt->small_max_panel > 4096) return -5;
     if (opt->block_cols < 8 || opt->block_cols > 64) return -5;
     if (opt->device_mem_cap < 0) return -5;
+    if (!(opt->merge_growth >= 0.0) || opt->merge_growth > 100.0) return -5;
+    if (opt->small_max_rows < 1) return -5;
   }
   return 0;
 }
+
+// Supernodal elimination tree of a contiguous partition: parent of J = the
+// supernode holding parent(last column of J).
+void supernode_tree(int32_t n, const std::vector<int32_t>& sptr, const std::vector<int32_t>& parent,
+                    std::vector<int32_t>& sparent) {
+  const int32_t ns = (int32_t)sptr.size() - 1;
+  std::vector<int32_t> snode_of(n);
+  for (int32_t J = 0; J < ns; ++J)
+    for (int32_t j = sptr[J]; j < sptr[J + 1]; ++j) snode_of[j] = J;
+  sparent.assign(ns, -1);
+  for (int32_t J = 0; J < ns; ++J) {
+    int32_t p = parent[sptr[J + 1] - 1];
+    sparent[J] = p >= 0 ? snode_of[p] : -1;
+  }
+}
+
+// struct(J) for every supernode of a partition: J's columns, then the rows
+// below J of B's columns in J and of the children's structures, ascending.
+// For the maximal partition this is exactly struct(first column of J); for a
+// merged one it is the union of the structures of J's columns.
+void build_structs(int32_t n, const std::vector<int32_t>& sptr, const std::vector<int32_t>& sparent,
+                   const std::vector<int64_t>& bp, const std::vector<std::pair<int32_t, int64_t>>& ent,
+                   std::vector<int64_t>& rowptr, std::vector<int32_t>& rows) {
+  const int32_t ns = (int32_t)sptr.size() - 1;
+  std::vector<int32_t> chead(ns, -1), cnext(ns, -1);
+  for (int32_t J = ns - 1; J >= 0; --J)
+    if (sparent[J] >= 0) {
+      cnext[J] = chead[sparent[J]];
+      chead[sparent[J]] = J;
+    }
+  rowptr.assign(ns + 1, 0);
+  rows.clear();
+  std::vector<int32_t> mark(n, -1), buf;
+  for (int32_t J = 0; J < ns; ++J) {
+    const int32_t f = sptr[J], l = sptr[J + 1] - 1;
+    buf.clear();
+    for (int32_t j = f; j <= l; ++j) buf.push_back(j);
+    const size_t first_off = buf.size();
+    for (int32_t j = f; j <= l; ++j)
+      for (int64_t t = bp[j]; t < bp[j + 1]; ++t) {
+        int32_t i = ent[t].first;
+        if (i > l && mark[i] != J) { mark[i] = J; buf.push_back(i); }
+      }
+    for (int32_t C = chead[J]; C != -1; C = cnext[C])
+      for (int64_t t = rowptr[C]; t < rowptr[C + 1]; ++t) {
+        int32_t i = rows[t];
+        if (i > l && mark[i] != J) { mark[i] = J; buf.push_back(i); }
+      }
+    std::sort(buf.begin() + first_off, buf.end());
+    rows.insert(rows.end(), buf.begin(), buf.end());
+    rowptr[J + 1] = (int64_t)rows.size();
+  }
+}
+
+// Stored entries of a supernode with s columns and len rows (lower trapezoid).
+inline double stored_entries(double s, double len) { return s * len - s * (s - 1.0) / 2.0; }
+
+// Relaxed supernode merging (Sec. IV setup): repeatedly merge the adjacent pair
+// (J, P) with P = parent(J) = the next supernode in column order that adds the
+// fewest explicit zeros (ties: smaller first column of J), while the cumulative
+// added zeros stay within the budget. The merged structure is J's columns plus
+// struct(P), because struct(J) minus J's columns lies in struct(P).
+void relaxed_merge(const std::vector<int32_t>& csptr, const std::vector<int32_t>& csparent,
+                   const std::vector<int64_t>& crowptr, double budget, std::vector<int32_t>& sptr) {
+  const int32_t ns = (int32_t)csptr.size() - 1;
+  std::vector<double> s(ns), len(ns);
+  std::vector<int32_t> nxt(ns), prv(ns), rep(ns), ver(ns, 0), lastc(ns);
+  std::vector<char> alive(ns, 1);
+  for (int32_t J = 0; J < ns; ++J) {
+    s[J] = csptr[J + 1] - csptr[J];
+    len[J] = (double)(crowptr[J + 1] - crowptr[J]);
+    nxt[J] = J + 1 < ns ? J + 1 : -1;
+    prv[J] = J - 1;
+    rep[J] = J;
+    lastc[J] = J;   // canonical member holding the last column
+  }
+  auto find = [&](int32_t x) {
+    while (rep[x] != x) {
+      rep[x] = rep[rep[x]];
+      x = rep[x];
+    }
+    return x;
+  };
+  // current parent of a live supernode = representative of the canonical parent
+  // of its last canonical member
+  auto cur_parent = [&](int32_t J) {
+    const int32_t p = csparent[lastc[J]];
+    return p < 0 ? -1 : find(p);
+  };
+  auto cost = [&](int32_t J, int32_t P) {
+    return stored_entries(s[J] + s[P], s[J] + len[P]) - stored_entries(s[J], len[J]) -
+           stored_entries(s[P], len[P]);
+  };
+  typedef std::tuple<double, int32_t, int32_t, int32_t> Item;  // cost, first column, J, version
+  std::priority_queue<Item, std::vector<Item>, std::greater<Item>> pq;
+  auto push = [&](int32_t J) {
+    ++ver[J];
+    const int32_t P = nxt[J];
+    if (P >= 0 && cur_parent(J) == P) pq.push(Item(cost(J, P), csptr[J], J, ver[J]));
+  };
+  for (int32_t J = 0; J < ns; ++J) push(J);
+  double total = 0.0;
+  while (!pq.empty()) {
+    const Item it = pq.top();
+    pq.pop();
+    const int32_t J = std::get<2>(it);
+    if (!alive[J] || std::get<3>(it) != ver[J]) continue;
+    const int32_t P = nxt[J];
+    if (P < 0 || cur_parent(J) != P) continue;
+    const double c = std::get<0>(it);
+    if (total + c > budget) break;
+    total += c;
+    len[J] = s[J] + len[P];   // J absorbs P
+    s[J] += s[P];
+    lastc[J] = lastc[P];
+    alive[P] = 0;
+    rep[P] = J;
+    nxt[J] = nxt[P];
+    if (nxt[P] >= 0) prv[nxt[P]] = J;
+    push(J);
+    if (prv[J] >= 0) push(prv[J]);
+  }
+  sptr.clear();
+  for (int32_t J = 0; J < ns; ++J)
+    if (alive[J]) sptr.push_back(csptr[J]);
+  sptr.push_back(csptr[ns]);
+}
+
 
 void build(chol_handle* h, const int64_t* colptr, const int32_t* rowind) {
   const int32_t n = h->n;
@@ -128,58 +262,40 @@ void build(chol_handle* h, const int64_t* colptr, const int32_t* rowind) {
     h->nnz_l += h->colcount[j];
     h->flops += (double)h->colcount[j] * (double)h->colcount[j];
   }
-  // ---- maximal supernodes and the supernodal tree ----
-  h->sptr.clear();
+  // ---- maximal supernodes (Fig. 1): the canonical partition ----
+  h->c_sptr.clear();
   for (int32_t j = 0; j < n; ++j) {
     bool join = j > 0 && h->parent[j - 1] == j && h->colcount[j - 1] == h->colcount[j] + 1;
-    if (!join) h->sptr.push_back(j);
+    if (!join) h->c_sptr.push_back(j);
   }
-  h->sptr.push_back(n);
+  h->c_sptr.push_back(n);
+  supernode_tree(n, h->c_sptr, h->parent, h->c_sparent);
+  build_structs(n, h->c_sptr, h->c_sparent, bp, ent, h->c_rowptr, h->c_rows);
+  for (size_t J = 0; J + 1 < h->c_sptr.size(); ++J)
+    if (h->c_rowptr[J + 1] - h->c_rowptr[J] != h->colcount[h->c_sptr[J]])
+      throw std::logic_error("structure/count mismatch");
+  // ---- storage partition: canonical, or coarser after relaxed merging ----
+  if (h->opt.merge_growth > 0.0) {
+    relaxed_merge(h->c_sptr, h->c_sparent, h->c_rowptr, (double)h->nnz_l * h->opt.merge_growth, h->sptr);
+    supernode_tree(n, h->sptr, h->parent, h->sparent);
+    build_structs(n, h->sptr, h->sparent, bp, ent, h->rowptr, h->rows);
+  } else {
+    h->sptr = h->c_sptr;
+    h->sparent = h->c_sparent;
+    h->rowptr = h->c_rowptr;
+    h->rows = h->c_rows;
+  }
   const int32_t ns = (int32_t)h->sptr.size() - 1;
   h->ns = ns;
   std::vector<int32_t> snode_of(n);
   for (int32_t J = 0; J < ns; ++J)
     for (int32_t j = h->sptr[J]; j < h->sptr[J + 1]; ++j) snode_of[j] = J;
-  h->sparent.assign(ns, -1);
-  for (int32_t J = 0; J < ns; ++J) {
-    int32_t p = h->parent[h->sptr[J + 1] - 1];
-    h->sparent[J] = p >= 0 ? snode_of[p] : -1;
-  }
   std::vector<int32_t> chead(ns, -1), cnext(ns, -1);
   for (int32_t J = ns - 1; J >= 0; --J)
     if (h->sparent[J] >= 0) {
       cnext[J] = chead[h->sparent[J]];
       chead[h->sparent[J]] = J;
     }
-  // ---- struct(J): J's columns, B's rows below J, children's rows below J ----
-  h->rowptr.assign(ns + 1, 0);
-  for (int32_t J = 0; J < ns; ++J) h->rowptr[J + 1] = h->rowptr[J] + h->colcount[h->sptr[J]];
-  h->rows.assign(h->rowptr[ns], 0);
-  {
-    std::vector<int32_t> mark(n, -1);
-    for (int32_t J = 0; J < ns; ++J) {
-      int32_t f = h->sptr[J], l = h->sptr[J + 1] - 1;
-      int32_t* out = h->rows.data() + h->rowptr[J];
-      int32_t cnt = 0;
-      for (int32_t j = f; j <= l; ++j) out[cnt++] = j;
-      int32_t first_off = cnt;
-      for (int32_t j = f; j <= l; ++j)
-        for (int64_t t = bp[j]; t < bp[j + 1]; ++t) {
-          int32_t i = ent[t].first;
-          if (i > l && mark[i] != J) { mark[i] = J; out[cnt++] = i; }
-        }
-      for (int32_t C = chead[J]; C != -1; C = cnext[C]) {
-        const int32_t* cr = h->rows.data() + h->rowptr[C];
-        int32_t clen = (int32_t)(h->rowptr[C + 1] - h->rowptr[C]);
-        for (int32_t t = 0; t < clen; ++t) {
-          int32_t i = cr[t];
-          if (i > l && mark[i] != J) { mark[i] = J; out[cnt++] = i; }
-        }
-      }
-      std::sort(out + first_off, out + cnt);
-      if (cnt != h->colcount[f]) throw std::logic_error("structure/count mismatch");
-    }
-  }
   // ---- levels (height in the supernodal tree) ----
   h->level.assign(ns, 0);
   h->nlevels = ns > 0 ? 1 : 0;
@@ -191,6 +307,8 @@ void build(chol_handle* h, const int64_t* colptr, const int32_t* rowind) {
   }
   // ---- panel layout ----
   h->snodes.assign(ns, SnodeDev{});
+  h->nnz_stored = 0;
+  h->flops_stored = 0.0;
   int64_t off = 0;
   h->max_cols = 0;
   h->max_len = 0;
@@ -206,6 +324,10 @@ void build(chol_handle* h, const int64_t* colptr, const int32_t* rowind) {
     off = (off + 15) & ~int64_t(15);
     h->max_cols = std::max(h->max_cols, d.s);
     h->max_len = std::max(h->max_len, d.len);
+    for (int32_t c = 0; c < d.s; ++c) {
+      h->nnz_stored += d.len - c;
+      h->flops_stored += (double)(d.len - c) * (double)(d.len - c);
+    }
   }
   h->panel_doubles = off;
   // ---- value scatter map: A entry -> L storage position ----
@@ -272,7 +394,8 @@ void build(chol_handle* h, const int64_t* colptr, const int32_t* rowind) {
       uo += (int64_t)b * b;
       d.wpre = wo;
       wo += b;
-      bool small = d.s <= h->opt.small_max_cols && (int64_t)d.len * d.s <= h->opt.small_max_panel;
+      bool small = d.s <= h->opt.small_max_cols && (int64_t)d.len * d.s <= h->opt.small_max_panel &&
+                   d.len <= h->opt.small_max_rows;
       if (small) {
         for (int32_t j = d.f; j < d.f + d.s; ++j) P.small_flops += (double)h->colcount[j] * h->colcount[j];
         P.small_bytes += 16.0 * (double)d.len * d.s + 8.0 * (double)b * (b + 1) / 2.0;
@@ -306,7 +429,7 @@ void build(chol_handle* h, const int64_t* colptr, const int32_t* rowind) {
         for (int32_t j = 0; j < kb; ++j) st.potrf_flops += (double)(kb - j) * (kb - j);
         const double below = (double)(d.len - k0 - kb);
         st.trsm_flops += below * (double)kb * (double)kb;   // kb divisions + 2*kb(kb-1)/2 per row
-        for (int32_t r0 = k0 + kb; r0 < d.len; r0 += kTile) h->trsm_tasks.push_back({J, k0, r0, 0});
+        for (int32_t r0 = k0 + kb; r0 < d.len; r0 += kTrsmRowsHost) h->trsm_tasks.push_back({J, k0, r0, 0});
         for (int32_t c0 = k0 + kb; c0 < d.s; c0 += kTile)
           for (int32_t r0 = c0; r0 < d.len; r0 += kTile) h->gemm_tasks.push_back({J, k0, r0, c0});
         // trailing update: 2 kb flops per entry (r, c) with c in [k0+kb, s), r in [c, len)
@@ -428,18 +551,36 @@ extern "C" int chol_analyze(int32_t n, const int64_t* colptr, const int32_t* row
   return CHOL_OK;
 }
 
+namespace {
+void canonical_pairs(const chol_handle* h, std::vector<int32_t>& pj, std::vector<int32_t>& pk,
+                     std::vector<int32_t>& pc0);
+}
+
 extern "C" int chol_get_info(const chol_handle* h, chol_info* info) {
   if (!h) return -1;
   if (!info) return -2;
   std::memset(info, 0, sizeof(*info));
   info->n = h->n;
-  info->nsuper = h->ns;
+  info->nsuper = (int32_t)h->c_sptr.size() - 1;
+  info->nsuper_storage = h->ns;
+  info->nnz_stored = h->nnz_stored;
+  info->flops_stored = h->flops_stored;
   info->nlevels = h->nlevels;
   info->max_cols = h->max_cols;
   info->nnz_a = h->nnz_a;
   info->nnz_l = h->nnz_l;
-  info->n_relind_pairs = (int64_t)h->rel_J.size();
-  info->relind_len = h->relind_len;
+  {
+    std::vector<int32_t> pj, pk, pc0;
+    canonical_pairs(h, pj, pk, pc0);
+    info->n_relind_pairs = (int64_t)pj.size();
+    int64_t tot = 0;
+    for (size_t p = 0; p < pj.size(); ++p) {
+      const int32_t J = pj[p];
+      const int64_t b = (h->c_rowptr[J + 1] - h->c_rowptr[J]) - (h->c_sptr[J + 1] - h->c_sptr[J]);
+      tot += b - pc0[p];
+    }
+    info->relind_len = tot;
+  }
   info->panel_doubles = h->panel_doubles;
   info->update_doubles = h->update_doubles;
   info->flops = h->flops;
@@ -447,6 +588,33 @@ extern "C" int chol_get_info(const chol_handle* h, chol_info* info) {
   info->n_large = h->n_large;
   return CHOL_OK;
 }
+
+namespace {
+
+// (J, K) pairs of the canonical partition: K = every supernode owning a row of
+// struct(J) below J's columns, ascending; c0 = first such row's index in
+// struct(J) minus J's columns.
+void canonical_pairs(const chol_handle* h, std::vector<int32_t>& pj, std::vector<int32_t>& pk,
+                     std::vector<int32_t>& pc0) {
+  const int32_t ns = (int32_t)h->c_sptr.size() - 1;
+  std::vector<int32_t> snode_of(h->n);
+  for (int32_t J = 0; J < ns; ++J)
+    for (int32_t j = h->c_sptr[J]; j < h->c_sptr[J + 1]; ++j) snode_of[j] = J;
+  for (int32_t J = 0; J < ns; ++J) {
+    const int32_t s = h->c_sptr[J + 1] - h->c_sptr[J];
+    const int32_t* r = h->c_rows.data() + h->c_rowptr[J];
+    const int32_t len = (int32_t)(h->c_rowptr[J + 1] - h->c_rowptr[J]);
+    int32_t prevK = -1;
+    for (int32_t u = s; u < len; ++u) {
+      const int32_t K = snode_of[r[u]];
+      if (K == prevK) continue;
+      prevK = K;
+      pj.push_back(J); pk.push_back(K); pc0.push_back(u - s);
+    }
+  }
+}
+
+}  // namespace
 
 extern "C" int chol_get_symbolic(const chol_handle* h, int32_t* parent, int32_t* colcount,
                                  int32_t* snode_ptr, int32_t* snode_parent, int64_t* row_ptr,
@@ -458,35 +626,50 @@ extern "C" int chol_get_symbolic(const chol_handle* h, int32_t* parent, int32_t*
   };
   cp(parent, h->parent);
   cp(colcount, h->colcount);
+  cp(snode_ptr, h->c_sptr);
+  cp(snode_parent, h->c_sparent);
+  cp(row_ptr, h->c_rowptr);
+  cp(rows, h->c_rows);
+  if (relind_ptr || relind_target || relind) {
+    // relind(J, K) by its definition (Sec. II-A), on request: for each row i of
+    // struct(J) from the first row owned by K on (all of them lie in struct(K)),
+    // the distance of i from the bottom of struct(K).
+    std::vector<int32_t> pj, pk, pc0;
+    canonical_pairs(h, pj, pk, pc0);
+    cp(relind_target, pk);
+    std::vector<int32_t> pos(h->n, -1);
+    int64_t off = 0;
+    if (relind_ptr) relind_ptr[0] = 0;
+    for (size_t p = 0; p < pj.size(); ++p) {
+      const int32_t J = pj[p], K = pk[p];
+      const int32_t sJ = h->c_sptr[J + 1] - h->c_sptr[J];
+      const int32_t* rj = h->c_rows.data() + h->c_rowptr[J];
+      const int32_t lenJ = (int32_t)(h->c_rowptr[J + 1] - h->c_rowptr[J]);
+      const int32_t* rk = h->c_rows.data() + h->c_rowptr[K];
+      const int32_t lenK = (int32_t)(h->c_rowptr[K + 1] - h->c_rowptr[K]);
+      for (int32_t t = 0; t < lenK; ++t) pos[rk[t]] = t;
+      for (int32_t u = sJ + pc0[p]; u < lenJ; ++u) {
+        const int32_t ps = pos[rj[u]];
+        if (relind) relind[off] = ps < 0 ? -1 : lenK - 1 - ps;
+        ++off;
+      }
+      for (int32_t t = 0; t < lenK; ++t) pos[rk[t]] = -1;
+      if (relind_ptr) relind_ptr[p + 1] = off;
+    }
+  }
+  return CHOL_OK;
+}
+
+extern "C" int chol_get_partition(const chol_handle* h, int32_t* snode_ptr, int32_t* snode_parent,
+                                  int64_t* row_ptr, int32_t* rows) {
+  if (!h) return -1;
+  auto cp = [](auto* dst, const auto& v) {
+    if (dst && !v.empty()) std::memcpy(dst, v.data(), v.size() * sizeof(v[0]));
+  };
   cp(snode_ptr, h->sptr);
   cp(snode_parent, h->sparent);
   cp(row_ptr, h->rowptr);
   cp(rows, h->rows);
-  cp(relind_target, h->rel_K);
-  if (relind_ptr || relind) {
-    // relind(J, K) by its definition, computed on request: for each row i of
-    // struct(J) from the first row in K on (all of them lie in struct(K)), the
-    // distance of i from the bottom of struct(K).
-    const int64_t np = (int64_t)h->rel_J.size();
-    int64_t off = 0;
-    std::vector<int32_t> pos(h->n, -1);
-    if (relind_ptr) relind_ptr[0] = 0;
-    for (int64_t p = 0; p < np; ++p) {
-      const SnodeDev& dj = h->snodes[h->rel_J[p]];
-      const SnodeDev& dk = h->snodes[h->rel_K[p]];
-      const int32_t* rj = h->rows.data() + dj.roff;
-      const int32_t* rk = h->rows.data() + dk.roff;
-      for (int32_t t = 0; t < dk.len; ++t) pos[rk[t]] = t;
-      const int32_t b = dj.len - dj.s;
-      for (int32_t u = h->rel_c0[p]; u < b; ++u) {
-        int32_t ps = pos[rj[dj.s + u]];
-        if (relind) relind[off] = ps < 0 ? -1 : dk.len - 1 - ps;
-        ++off;
-      }
-      for (int32_t t = 0; t < dk.len; ++t) pos[rk[t]] = -1;
-      if (relind_ptr) relind_ptr[p + 1] = off;
-    }
-  }
   return CHOL_OK;
 }
 

@@ -99,50 +99,143 @@ k_small(const SnodeDev* __restrict__ sn, const int32_t* __restrict__ list, doubl
   }
 }
 
-// Blocked path, step k0: factor the kb x kb diagonal block of each listed supernode.
-__global__ void k_potrf(const SnodeDev* __restrict__ sn, const int32_t* __restrict__ list, int k0,
-                        int nb, double* __restrict__ L, int* status) {
-  extern __shared__ double P[];
+// Blocked path, step k0: factor the kb x kb (kb <= 64) diagonal block of each
+// listed supernode. Register-blocked right-looking Cholesky: 256 threads in a
+// 16 x 16 grid, thread (tx, ty) holds entries (ty + 16a, tx + 16b), a, b < 4;
+// per column k the scaled column goes through shared memory and every thread
+// applies the rank-1 update to its own entries.
+constexpr int kPotrfThreads = 256;
+__global__ void __launch_bounds__(kPotrfThreads)
+k_potrf(const SnodeDev* __restrict__ sn, const int32_t* __restrict__ list, int k0, int nb,
+        double* __restrict__ L, int* status) {
+  __shared__ double colk[64];
+  __shared__ double sdiag;
   const SnodeDev d = sn[list[blockIdx.x]];
   const int kb = min(nb, d.s - k0);
   double* G = L + d.loff + k0 + (int64_t)k0 * d.ld;
-  for (int c = 0; c < kb; ++c)
-    for (int r = threadIdx.x; r < kb; r += blockDim.x) P[r + c * kb] = G[r + (int64_t)c * d.ld];
-  dense_chol_smem(P, kb, kb, kb, d.f + k0, status);
-  for (int c = 0; c < kb; ++c)
-    for (int r = c + threadIdx.x; r < kb; r += blockDim.x) G[r + (int64_t)c * d.ld] = P[r + c * kb];
+  const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
+  double v[4][4];
+#pragma unroll
+  for (int a = 0; a < 4; ++a)
+#pragma unroll
+    for (int b = 0; b < 4; ++b) {
+      const int r = ty + 16 * a, c = tx + 16 * b;
+      v[a][b] = (r < kb && c < kb && r >= c) ? G[r + (int64_t)c * d.ld] : 0.0;
+    }
+#pragma unroll 1
+  for (int kk = 0; kk < 4; ++kk) {
+#pragma unroll
+    for (int k1 = 0; k1 < 16; ++k1) {
+      const int k = kk * 16 + k1;
+      if (k >= kb) break;
+      // pivot: held by thread (tx, ty) = (k1, k1) in slot (kk, kk)
+      if (tx == k1 && ty == k1) {
+        double dv = 0.0;
+#pragma unroll
+        for (int a = 0; a < 4; ++a)
+          if (a == kk) {
+#pragma unroll
+            for (int b = 0; b < 4; ++b)
+              if (b == kk) dv = v[a][b];
+          }
+        const bool bad = !(dv > 0.0);
+        const double dk = bad ? __longlong_as_double(0x7ff8000000000000LL) : sqrt(dv);
+        if (bad) atomicMin(status, d.f + k0 + k + 1);
+        sdiag = dk;
+      }
+      __syncthreads();
+      const double dk = sdiag;
+      const double inv = 1.0 / dk;
+      if (tx == k1) {   // column k lives in slot b = kk of these threads
+#pragma unroll
+        for (int a = 0; a < 4; ++a) {
+          const int r = ty + 16 * a;
+#pragma unroll
+          for (int b = 0; b < 4; ++b)
+            if (b == kk) {
+              if (r > k) { v[a][b] *= inv; colk[r] = v[a][b]; }
+              else if (r == k) v[a][b] = dk;
+            }
+        }
+      }
+      __syncthreads();
+#pragma unroll
+      for (int a = 0; a < 4; ++a) {
+        const int r = ty + 16 * a;
+        if (r <= k || r >= kb) continue;
+        const double lr = colk[r];
+#pragma unroll
+        for (int b = 0; b < 4; ++b) {
+          const int c = tx + 16 * b;
+          if (c > k && c <= r) v[a][b] -= lr * colk[c];
+        }
+      }
+    }
+  }
+#pragma unroll
+  for (int a = 0; a < 4; ++a)
+#pragma unroll
+    for (int b = 0; b < 4; ++b) {
+      const int r = ty + 16 * a, c = tx + 16 * b;
+      if (r < kb && c < kb && r >= c) G[r + (int64_t)c * d.ld] = v[a][b];
+    }
 }
 
-// Blocked path, step k0: rows [r0, r0+64) of column block [k0, k0+kb) become
-// X = B L_kk^{-T} (forward substitution along each row; one thread per row).
-__global__ void __launch_bounds__(kTile)
+// Blocked path, step k0: rows [r0, r0+32) of column block [k0, k0+kb) become
+// X = B L_kk^{-T}. Eight lanes share a row, lane q holding columns q + 8m; the
+// solved x_j is broadcast inside the 8-lane group with a shuffle and every lane
+// updates its own columns (no barriers in the substitution loop).
+constexpr int kTrsmThreads = 256;
+constexpr int kTrsmRows = 32;
+__global__ void __launch_bounds__(kTrsmThreads)
 k_trsm(const SnodeDev* __restrict__ sn, const TileTask* __restrict__ tasks, int nb,
        double* __restrict__ L) {
-  extern __shared__ double sm[];
+  __shared__ double Lk[64 * 65];
+  __shared__ double inv[64];
   const TileTask t = tasks[blockIdx.x];
   const SnodeDev d = sn[t.J];
   const int kb = min(nb, d.s - t.k0);
-  double* Lk = sm;                      // kb x kb, ld kb
-  double* X = sm + kb * kb;             // kTile x kb, ld kTile
-  double* inv = X + kTile * kb;         // kb
   const double* Gd = L + d.loff + t.k0 + (int64_t)t.k0 * d.ld;
-  for (int c = 0; c < kb; ++c)
-    for (int r = threadIdx.x; r < kb; r += blockDim.x) Lk[r + c * kb] = Gd[r + (int64_t)c * d.ld];
-  const int nrow = min(kTile, d.len - t.r0);
-  double* Gx = L + d.loff + t.r0 + (int64_t)t.k0 * d.ld;
-  for (int c = 0; c < kb; ++c)
-    if (threadIdx.x < nrow) X[threadIdx.x + c * kTile] = Gx[threadIdx.x + (int64_t)c * d.ld];
+  for (int q = threadIdx.x; q < kb * kb; q += blockDim.x) {
+    const int r = q % kb, c = q / kb;
+    Lk[r + c * 65] = Gd[r + (int64_t)c * d.ld];
+  }
   __syncthreads();
-  for (int c = threadIdx.x; c < kb; c += blockDim.x) inv[c] = 1.0 / Lk[c + c * kb];
+  for (int c = threadIdx.x; c < kb; c += blockDim.x) inv[c] = 1.0 / Lk[c + c * 65];
   __syncthreads();
-  const int r = threadIdx.x;
-  if (r < nrow) {
-    for (int j = 0; j < kb; ++j) {
-      double acc = X[r + j * kTile];
-      for (int i = 0; i < j; ++i) acc -= X[r + i * kTile] * Lk[j + i * kb];
-      X[r + j * kTile] = acc * inv[j];
+  const int g = threadIdx.x >> 3, q = threadIdx.x & 7;
+  const int row = t.r0 + g;
+  const bool live = row < d.len;
+  double* Gx = L + d.loff + row + (int64_t)t.k0 * d.ld;
+  double x[8];
+#pragma unroll
+  for (int m = 0; m < 8; ++m) {
+    const int c = q + 8 * m;
+    x[m] = (live && c < kb) ? Gx[(int64_t)c * d.ld] : 0.0;
+  }
+#pragma unroll
+  for (int jm = 0; jm < 8; ++jm) {
+#pragma unroll
+    for (int jq = 0; jq < 8; ++jq) {
+      const int j = jm * 8 + jq;
+      if (j < kb) {
+        const double cand = x[jm] * inv[j];
+        const double xj = __shfl_sync(0xffffffffu, cand, jq, 8);
+        if (q == jq) x[jm] = xj;
+#pragma unroll
+        for (int m = 0; m < 8; ++m) {
+          const int c = q + 8 * m;
+          if (c > j && c < kb) x[m] -= xj * Lk[c + j * 65];
+        }
+      }
     }
-    for (int c = 0; c < kb; ++c) Gx[r + (int64_t)c * d.ld] = X[r + c * kTile];
+  }
+  if (live) {
+#pragma unroll
+    for (int m = 0; m < 8; ++m) {
+      const int c = q + 8 * m;
+      if (c < kb) Gx[(int64_t)c * d.ld] = x[m];
+    }
   }
 }
 
@@ -304,15 +397,11 @@ __global__ void k_logdet_reduce(const double* __restrict__ part, int ns, double*
   if (threadIdx.x == 0) *out = 2.0 * red[0];
 }
 
-// Copy the panels into compressed sparse column form (diagonal first).
-__global__ void k_to_csc(const SnodeDev* __restrict__ sn, const double* __restrict__ L,
-                         const int64_t* __restrict__ lp, double* __restrict__ lx) {
-  const SnodeDev d = sn[blockIdx.x];
-  for (int c = 0; c < d.s; ++c) {
-    const int64_t base = lp[d.f + c];
-    for (int r = c + threadIdx.x; r < d.len; r += blockDim.x)
-      lx[base + (r - c)] = L[d.loff + r + (int64_t)c * d.ld];
-  }
+// out[t] = L[map[t]] (panel entries -> compressed sparse column order).
+__global__ void k_gather(const double* __restrict__ L, const int64_t* __restrict__ map, int64_t nnz,
+                         double* __restrict__ out) {
+  for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < nnz; t += (int64_t)gridDim.x * blockDim.x)
+    out[t] = L[map[t]];
 }
 
 template <class T>
@@ -448,9 +537,6 @@ int chol_device_ensure(chol_handle* h) {
   if (cudaMallocHost((void**)&D->scalar_host, sizeof(double)) != cudaSuccess) return fail(CHOL_ENOMEM);
   static bool attrs_done = false;
   if (!attrs_done) {
-    const int trsm_smem = (64 * 64 + kTile * 64 + 64) * (int)sizeof(double);
-    if (cudaFuncSetAttribute(k_trsm, cudaFuncAttributeMaxDynamicSharedMemorySize, trsm_smem) != cudaSuccess)
-      return fail(CHOL_ECUDA);
     if (cudaFuncSetAttribute(k_assemble, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024) != cudaSuccess)
       return fail(CHOL_ECUDA);
     attrs_done = true;
@@ -485,13 +571,12 @@ extern "C" int chol_factor(chol_handle* h, const double* values, void* stream) {
       const int k0 = (int)k * nb;
       if (s.potrf_n > 0) {
         KScope ks(h, CHOL_K_POTRF, st, s.potrf_flops, 16.0 * nb * nb * s.potrf_n);
-        k_potrf<<<s.potrf_n, 128, sizeof(double) * nb * nb, st>>>(D->sn, D->potrf_list + s.potrf_b, k0, nb,
-                                                                  D->L, D->status);
+        k_potrf<<<s.potrf_n, kPotrfThreads, 0, st>>>(D->sn, D->potrf_list + s.potrf_b, k0, nb, D->L,
+                                                     D->status);
       }
       if (s.trsm_n > 0) {
-        KScope ks(h, CHOL_K_TRSM, st, s.trsm_flops, 16.0 * kTile * nb * s.trsm_n);
-        k_trsm<<<s.trsm_n, kTile, sizeof(double) * (nb * nb + kTile * nb + nb), st>>>(
-            D->sn, D->trsm + s.trsm_b, nb, D->L);
+        KScope ks(h, CHOL_K_TRSM, st, s.trsm_flops, 16.0 * kTrsmRows * nb * s.trsm_n);
+        k_trsm<<<s.trsm_n, kTrsmThreads, 0, st>>>(D->sn, D->trsm + s.trsm_b, nb, D->L);
       }
       if (s.gemm_n > 0) {
         KScope ks(h, CHOL_K_GEMM, st, s.gemm_flops, 16.0 * kTile * kTile * s.gemm_n);
@@ -542,30 +627,61 @@ extern "C" int chol_get_factor(chol_handle* h, int64_t* lp, int32_t* li, double*
   if (!h->factored) return CHOL_ESTATE;
   DeviceState* D = h->dev;
   cudaStream_t st = (cudaStream_t)stream;
-  std::vector<int64_t> hp(h->n + 1, 0);
-  for (int32_t j = 0; j < h->n; ++j) hp[j + 1] = hp[j] + h->colcount[j];
+  const int32_t n = h->n;
+  const int32_t cns = (int32_t)h->c_sptr.size() - 1;
+  std::vector<int64_t> hp(n + 1, 0);
+  for (int32_t j = 0; j < n; ++j) hp[j + 1] = hp[j] + h->colcount[j];
   if (lp) std::memcpy(lp, hp.data(), sizeof(int64_t) * hp.size());
+  // canonical column j: rows of its maximal supernode's structure from j on
   if (li) {
-    for (int32_t J = 0; J < h->ns; ++J) {
-      const SnodeDev& d = h->snodes[J];
-      for (int c = 0; c < d.s; ++c)
-        for (int r = c; r < d.len; ++r) li[hp[d.f + c] + (r - c)] = h->rows[d.roff + r];
+    for (int32_t K = 0; K < cns; ++K) {
+      const int32_t f = h->c_sptr[K];
+      const int32_t* r = h->c_rows.data() + h->c_rowptr[K];
+      const int32_t len = (int32_t)(h->c_rowptr[K + 1] - h->c_rowptr[K]);
+      for (int32_t c = 0; c < h->c_sptr[K + 1] - f; ++c)
+        for (int32_t t = c; t < len; ++t) li[hp[f + c] + (t - c)] = r[t];
     }
   }
   if (lx && h->nnz_l > 0) {
-    int64_t* dlp = nullptr;
+    if (h->cscmap.empty()) {
+      // entry of canonical column j -> its position in the storage panel
+      h->cscmap.assign(h->nnz_l, 0);
+      std::vector<int32_t> csnode(n), pos(n, -1);
+      for (int32_t K = 0; K < cns; ++K)
+        for (int32_t j = h->c_sptr[K]; j < h->c_sptr[K + 1]; ++j) csnode[j] = K;
+      for (int32_t J = 0; J < h->ns; ++J) {
+        const SnodeDev& d = h->snodes[J];
+        const int32_t* r = h->rows.data() + d.roff;
+        for (int32_t t = 0; t < d.len; ++t) pos[r[t]] = t;
+        for (int32_t c = 0; c < d.s; ++c) {
+          const int32_t j = d.f + c, K = csnode[j];
+          const int32_t* rk = h->c_rows.data() + h->c_rowptr[K];
+          const int32_t lenk = (int32_t)(h->c_rowptr[K + 1] - h->c_rowptr[K]);
+          const int32_t ck = j - h->c_sptr[K];
+          for (int32_t t = ck; t < lenk; ++t)
+            h->cscmap[hp[j] + (t - ck)] = d.loff + (int64_t)c * d.ld + pos[rk[t]];
+        }
+        for (int32_t t = 0; t < d.len; ++t) pos[r[t]] = -1;
+      }
+    }
+    int64_t* dmap = nullptr;
     double* dlx = nullptr;
-    int rc = chol_dalloc(h, (void**)&dlp, sizeof(int64_t) * hp.size());
+    int rc = chol_dalloc(h, (void**)&dmap, sizeof(int64_t) * (size_t)h->nnz_l);
     if (rc) return rc;
     rc = chol_dalloc(h, (void**)&dlx, sizeof(double) * (size_t)h->nnz_l);
-    if (rc) { cudaFree(dlp); D->bytes -= sizeof(int64_t) * hp.size(); return rc; }
-    CHOL_CUDA_TRY(cudaMemcpyAsync(dlp, hp.data(), sizeof(int64_t) * hp.size(), cudaMemcpyHostToDevice, st));
-    k_to_csc<<<h->ns, 128, 0, st>>>(D->sn, D->L, dlp, dlx);
+    if (rc) {
+      cudaFree(dmap);
+      D->bytes -= sizeof(int64_t) * (size_t)h->nnz_l;
+      return rc;
+    }
+    CHOL_CUDA_TRY(cudaMemcpyAsync(dmap, h->cscmap.data(), sizeof(int64_t) * (size_t)h->nnz_l,
+                                  cudaMemcpyHostToDevice, st));
+    k_gather<<<grid1d(h->nnz_l, 256), 256, 0, st>>>(D->L, dmap, h->nnz_l, dlx);
     CHOL_CUDA_TRY(cudaMemcpyAsync(lx, dlx, sizeof(double) * (size_t)h->nnz_l, cudaMemcpyDeviceToHost, st));
     CHOL_CUDA_TRY(cudaStreamSynchronize(st));
-    cudaFree(dlp);
+    cudaFree(dmap);
     cudaFree(dlx);
-    D->bytes -= (int64_t)(sizeof(int64_t) * hp.size() + sizeof(double) * (size_t)h->nnz_l);
+    D->bytes -= (int64_t)(sizeof(int64_t) + sizeof(double)) * h->nnz_l;
   }
   return CHOL_OK;
 }

@@ -67,16 +67,21 @@ struct chol_handle {
   int32_t n = 0;
   int64_t nnz_a = 0;
   std::vector<int32_t> perm, iperm;
-  // symbolic
+  // symbolic: the canonical (maximal) partition of Fig. 1 ...
   std::vector<int32_t> parent, colcount;
+  std::vector<int32_t> c_sptr, c_sparent;
+  std::vector<int64_t> c_rowptr;
+  std::vector<int32_t> c_rows;
+  // ... and the storage partition the kernels use (canonical, or merged)
   int32_t ns = 0, nlevels = 0, max_cols = 0;
   std::vector<int32_t> sptr, sparent, level;
   std::vector<int64_t> rowptr;
   std::vector<int32_t> rows;
+  std::vector<int64_t> cscmap;      // canonical CSC entry -> panel position (built on request)
   std::vector<SnodeDev> snodes;
   std::vector<int64_t> amap;        // entry t of A -> position in L storage
-  int64_t nnz_l = 0, panel_doubles = 0, update_doubles = 0, w_rows_max = 0;
-  double flops = 0.0;
+  int64_t nnz_l = 0, panel_doubles = 0, update_doubles = 0, w_rows_max = 0, nnz_stored = 0;
+  double flops = 0.0, flops_stored = 0.0;
   // (J, K) pairs: J updates ancestor K through U_J columns [c0, c1) (J ascending, K ascending)
   std::vector<int32_t> rel_J, rel_K, rel_c0, rel_c1;
   int64_t relind_len = 0;           // sum over pairs of (b_J - c0)
@@ -99,6 +104,7 @@ struct chol_handle {
 // Tile sizes shared by the schedule builder and the kernels.
 constexpr int kTile = 64;        // GEMM/SYRK tile edge and TRSM row block
 constexpr int kAsmCols = 64;     // assembly task width (target columns)
-constexpr int kBwdCols = 64;     // backward-solve panel column block
+constexpr int kTrsmRowsHost = 32; // TRSM task height (rows)
+constexpr int kBwdCols = 8;      // backward-solve panel column block (one warp per column)
 
 void chol_device_free(chol_handle* h);  // CUDA side

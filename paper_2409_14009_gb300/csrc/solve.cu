@@ -37,51 +37,76 @@ __global__ void k_permute_out(const double* __restrict__ Y, const int32_t* __res
   }
 }
 
-// Triangular solve with the kb x kb diagonal block at step k0 (in place in Y).
+// Triangular solve with the kb x kb (kb <= 64) diagonal block at step k0, in
+// place in Y, for up to 16 right-hand sides. Sixteen lanes share a right-hand
+// side, lane q holding rows q + 16a; the solved entry is broadcast inside the
+// 16-lane group with a shuffle (no barriers in the substitution loop).
 template <bool TRANS>
 __global__ void __launch_bounds__(kSolveThreads)
 k_diag(const SnodeDev* __restrict__ sn, const int32_t* __restrict__ list, int k0, int nb,
        const double* __restrict__ L, double* __restrict__ Y, int n, int nrhs) {
-  extern __shared__ double sm[];
+  __shared__ double Lk[64 * 65];
+  __shared__ double inv[64];
   const SnodeDev d = sn[list[blockIdx.x]];
   const int kb = min(nb, d.s - k0);
-  double* Lk = sm;               // kb x kb
-  double* yb = sm + kb * kb;     // kb x nrhs
   const double* G = L + d.loff + k0 + (int64_t)k0 * d.ld;
   for (int q = threadIdx.x; q < kb * kb; q += blockDim.x) {
     const int r = q % kb, c = q / kb;
-    Lk[q] = G[r + (int64_t)c * d.ld];
-  }
-  double* Yb = Y + d.f + k0;
-  for (int q = threadIdx.x; q < kb * nrhs; q += blockDim.x) {
-    const int r = q % kb, c = q / kb;
-    yb[q] = Yb[r + (int64_t)c * n];
+    Lk[r + c * 65] = G[r + (int64_t)c * d.ld];
   }
   __syncthreads();
+  for (int c = threadIdx.x; c < kb; c += blockDim.x) inv[c] = 1.0 / Lk[c + c * 65];
+  __syncthreads();
+  const int rr = threadIdx.x >> 4, q = threadIdx.x & 15;
+  const bool live = rr < nrhs;
+  double* Yb = Y + d.f + k0 + (int64_t)rr * n;
+  double y[4];
+#pragma unroll
+  for (int a = 0; a < 4; ++a) {
+    const int i = q + 16 * a;
+    y[a] = (live && i < kb) ? Yb[i] : 0.0;
+  }
   if (!TRANS) {
-    for (int k = 0; k < kb; ++k) {
-      if (threadIdx.x < nrhs) yb[k + threadIdx.x * kb] /= Lk[k + k * kb];
-      __syncthreads();
-      for (int q = threadIdx.x; q < (kb - k - 1) * nrhs; q += blockDim.x) {
-        const int i = k + 1 + q % (kb - k - 1), r = q / (kb - k - 1);
-        yb[i + r * kb] -= Lk[i + k * kb] * yb[k + r * kb];
+#pragma unroll
+    for (int ka = 0; ka < 4; ++ka) {
+#pragma unroll
+      for (int kq = 0; kq < 16; ++kq) {
+        const int k = ka * 16 + kq;
+        if (k < kb) {
+          const double yk = __shfl_sync(0xffffffffu, y[ka] * inv[k], kq, 16);
+          if (q == kq) y[ka] = yk;
+#pragma unroll
+          for (int a = 0; a < 4; ++a) {
+            const int i = q + 16 * a;
+            if (i > k && i < kb) y[a] -= Lk[i + k * 65] * yk;
+          }
+        }
       }
-      __syncthreads();
     }
   } else {
-    for (int k = kb - 1; k >= 0; --k) {
-      if (threadIdx.x < nrhs) yb[k + threadIdx.x * kb] /= Lk[k + k * kb];
-      __syncthreads();
-      for (int q = threadIdx.x; q < k * nrhs; q += blockDim.x) {
-        const int i = q % k, r = q / k;
-        yb[i + r * kb] -= Lk[k + i * kb] * yb[k + r * kb];
+#pragma unroll
+    for (int ka = 3; ka >= 0; --ka) {
+#pragma unroll
+      for (int kq = 15; kq >= 0; --kq) {
+        const int k = ka * 16 + kq;
+        if (k < kb) {
+          const double yk = __shfl_sync(0xffffffffu, y[ka] * inv[k], kq, 16);
+          if (q == kq) y[ka] = yk;
+#pragma unroll
+          for (int a = 0; a < 4; ++a) {
+            const int i = q + 16 * a;
+            if (i < k) y[a] -= Lk[k + i * 65] * yk;
+          }
+        }
       }
-      __syncthreads();
     }
   }
-  for (int q = threadIdx.x; q < kb * nrhs; q += blockDim.x) {
-    const int r = q % kb, c = q / kb;
-    Yb[r + (int64_t)c * n] = yb[q];
+  if (live) {
+#pragma unroll
+    for (int a = 0; a < 4; ++a) {
+      const int i = q + 16 * a;
+      if (i < kb) Yb[i] = y[a];
+    }
   }
 }
 
@@ -270,7 +295,7 @@ extern "C" int chol_solve(chol_handle* h, double* b, int32_t nrhs, void* stream)
         const int k0 = (int)k * nb;
         if (s.diag_n > 0) {
           KScope ks(h, CHOL_K_SOLVE_DIAG, st, 0.0, 0.0);
-          k_diag<false><<<s.diag_n, kSolveThreads, sizeof(double) * (nb * nb + nb * nr), st>>>(
+          k_diag<false><<<s.diag_n, kSolveThreads, 0, st>>>(
               D->sn, D->sdiag + s.diag_b, k0, nb, D->L, D->Y, n, nr);
         }
         if (s.fupd_n > 0) {
@@ -297,7 +322,7 @@ extern "C" int chol_solve(chol_handle* h, double* b, int32_t nrhs, void* stream)
         const int k0 = k * nb;
         if (s.diag_n > 0) {
           KScope ks(h, CHOL_K_SOLVE_DIAG, st, 0.0, 0.0);
-          k_diag<true><<<s.diag_n, kSolveThreads, sizeof(double) * (nb * nb + nb * nr), st>>>(
+          k_diag<true><<<s.diag_n, kSolveThreads, 0, st>>>(
               D->sn, D->sdiag + s.diag_b, k0, nb, D->L, D->Y, n, nr);
         }
         if (s.bupd_n > 0) {

@@ -125,3 +125,36 @@ def test_symbolic_bit_exact_workloads(name):
     if p.n <= 4096:
         rp, rt, rv = sym.relind(ptr)
         assert np.array_equal(got["relind_ptr"], rp) and np.array_equal(got["relind"], rv)
+
+
+@pytest.mark.parametrize("growth", [0.02, 0.1, 0.25, 1.0])
+@pytest.mark.parametrize("case", ["2d20", "3d7", "rand"])
+def test_relaxed_merging_matches_oracle(case, growth):
+    """Sec. IV setup: the merged storage partition and the merged structures are
+    those of the plain greedy restatement in oracle.merge."""
+    from oracle.merge import merged_partition
+    P = chol()
+    if case == "2d20":
+        p = gridgen.laplacian_2d_dirichlet(20)
+    elif case == "3d7":
+        p = gridgen.laplacian_neumann_varcoef((7, 6, 7), 1e-2, 1e2, 1e-6, seed=1)
+    else:
+        A, cp, ri, vx, perm = random_spd(150, 0.03, 77)
+        p = dict(n=150, colptr=cp, rowind=ri, values=vx, perm=perm)
+    o = P.chol_default_options()
+    o.merge_growth = growth
+    rc, h = P.chol_analyze(p["n"], p["colptr"], p["rowind"], p["perm"], o)
+    assert rc == 0
+    part = P.chol_get_partition(h)
+    info = P.chol_get_info(h)
+    canon = P.chol_get_symbolic(h)
+    P.chol_destroy(h)
+    bp, bi, _ = oracle.permute(p["n"], p["colptr"], p["rowind"], None, p["perm"])
+    sym = oracle.Symbolic(p["n"], bp, bi)
+    ptr, structs = merged_partition(sym, growth)
+    assert np.array_equal(part["snode_ptr"], ptr)
+    for J, st in enumerate(structs):
+        assert part["rows"][part["row_ptr"][J]:part["row_ptr"][J + 1]].tolist() == st
+    assert info.nnz_stored <= (1.0 + growth) * info.nnz_l
+    # the canonical outputs do not change with merging
+    assert np.array_equal(canon["snode_ptr"], sym.supernodes()[0])

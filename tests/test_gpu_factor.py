@@ -17,9 +17,10 @@ from lib_fixture import chol
 pytestmark = pytest.mark.gpu
 
 
-def _opts(small_cols=64, small_panel=4096, nb=64, cap=0):
+def _opts(small_cols=64, small_panel=4096, nb=64, cap=0, merge=0.0, small_rows=128):
     o = chol().chol_default_options()
     o.small_max_cols, o.small_max_panel, o.block_cols, o.device_mem_cap = small_cols, small_panel, nb, cap
+    o.merge_growth, o.small_max_rows = merge, small_rows
     return o
 
 
@@ -143,3 +144,14 @@ def test_refactor_with_new_values():
         rc, ld = P.chol_logdet(h)
         assert abs(ld - ref["fac"].logdet()) <= 1e-12 * abs(ld)
     P.chol_destroy(h)
+
+
+@pytest.mark.parametrize("merge", [0.01, 0.05, 0.25, 1.0])
+def test_relaxed_merging_parity(merge):
+    """Merged storage partitions (explicit zeros) give the same factor on the
+    canonical pattern and the same solution."""
+    p = gridgen.laplacian_neumann_varcoef((16, 15, 14), 1e-2, 1e2, 1e-6, seed=8)
+    b = gridgen.rhs_uniform(p.n, 8, seed=8)
+    got, _ = check_parity(p, b, _opts(merge=merge), L_tol=1e-6, x_tol=1e-6)
+    assert got["info"].nsuper_storage < got["info"].nsuper
+    check_parity(gridgen.workload("2d64"), gridgen.rhs_uniform(4096, 2, seed=1), _opts(merge=merge, nb=32))
