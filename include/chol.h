@@ -45,7 +45,8 @@ enum {
   CHOL_ETIMEOUT = -1003,  /* a bounded device wait ran out */
   CHOL_ENOCONV = -1004,   /* iterative refinement did not reach the tolerance */
   CHOL_ESTATE = -1005,    /* call made in the wrong state (e.g. solve before factor) */
-  CHOL_ENOTSUP = -1006    /* option combination not supported */
+  CHOL_ENOTSUP = -1006,   /* option combination not supported */
+  CHOL_ETOOBIG = -1007    /* problem exceeds a fixed-size workspace */
 };
 
 enum {
@@ -116,6 +117,24 @@ int chol_factor(chol_handle* h, const double* values, void* stream);
  * Returns CHOL_ESTATE without a successful chol_factor. Asynchronous.
  */
 int chol_solve(chol_handle* h, double* b, int32_t nrhs, void* stream);
+
+/*
+ * chol_solve without any device allocation. The paper has no counterpart: it
+ * exists for callers that cannot call cudaMalloc once they are set up (a
+ * process whose memory pool already owns the GPU, or a latency-bound loop in
+ * which an allocation could stall on device-wide synchronization). Arguments,
+ * layout and result are those of chol_solve; the handle must hold a factor.
+ * Its workspaces live in one fixed device array of 2^21 doubles (16 MiB) that
+ * every GPU loading the library keeps until the process exits; a problem needs
+ * n + (largest per-level sum of off-diagonal supernode rows) doubles per
+ * right-hand-side column and is refused with CHOL_ETOOBIG if one column does
+ * not fit (wider blocks of right-hand sides are processed in chunks that fit).
+ * All calls on a device share that array, so calls that overlap on the GPU
+ * race; nothing in it needs to start at zero. The first call on each device
+ * looks up the array's device address (cudaGetSymbolAddress, with that device
+ * current): make that first call before any stream capture. Asynchronous.
+ */
+int chol_solve_noalloc(chol_handle* h, double* b, int32_t nrhs, void* stream);
 
 /*
  * log det A = 2 sum_j log L_jj, reduced in a fixed order (deterministic).

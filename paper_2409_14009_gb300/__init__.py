@@ -23,9 +23,11 @@ CHOL_ETIMEOUT = -1003
 CHOL_ENOCONV = -1004
 CHOL_ESTATE = -1005
 CHOL_ENOTSUP = -1006
+CHOL_ETOOBIG = -1007
 CHOL_PREC_FP64 = 0
 
-EXPORTED = ["chol_default_options", "chol_analyze", "chol_factor", "chol_solve", "chol_logdet",
+EXPORTED = ["chol_default_options", "chol_analyze", "chol_factor", "chol_solve", "chol_solve_noalloc",
+            "chol_logdet",
             "chol_get_info", "chol_get_symbolic", "chol_get_partition", "chol_get_factor", "chol_profile",
             "chol_get_stats", "chol_destroy", "chol_strerror"]
 
@@ -79,6 +81,8 @@ def lib():
         L.chol_factor.restype = C.c_int
         L.chol_solve.argtypes = [P, P, C.c_int32, P]
         L.chol_solve.restype = C.c_int
+        L.chol_solve_noalloc.argtypes = [P, P, C.c_int32, P]
+        L.chol_solve_noalloc.restype = C.c_int
         L.chol_logdet.argtypes = [P, C.POINTER(C.c_double), P]
         L.chol_logdet.restype = C.c_int
         L.chol_get_info.argtypes = [P, C.POINTER(chol_info)]
@@ -149,6 +153,11 @@ def chol_factor(h, values, stream=None) -> int:
 
 def chol_solve(h, b, nrhs, stream=None) -> int:
     return lib().chol_solve(h, _dev_ptr(b), int(nrhs), _stream(stream))
+
+
+def chol_solve_noalloc(h, b, nrhs, stream=None) -> int:
+    """chol_solve whose workspaces come from a fixed device array (no allocation)."""
+    return lib().chol_solve_noalloc(h, _dev_ptr(b), int(nrhs), _stream(stream))
 
 
 def chol_logdet(h, stream=None):

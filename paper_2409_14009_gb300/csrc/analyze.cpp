@@ -688,6 +688,7 @@ extern "C" const char* chol_strerror(int code) {
     case CHOL_ENOCONV: return "iterative refinement did not converge";
     case CHOL_ESTATE: return "call made in the wrong state";
     case CHOL_ENOTSUP: return "option combination not supported";
+    case CHOL_ETOOBIG: return "problem exceeds the fixed-size workspace of this call";
     default: break;
   }
   if (code > 0) return "matrix is not positive definite (return value = failing column, 1-based)";

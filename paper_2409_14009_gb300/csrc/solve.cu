@@ -13,6 +13,8 @@
 //   and y_c -= L_kc^T x_k for the column blocks c left of k       (k_bwd_update)
 // Every output entry is written by exactly one thread per launch; reductions
 // run in a fixed order, so the solve is deterministic.
+#include <mutex>
+
 #include "device.h"
 
 namespace {
@@ -339,4 +341,112 @@ extern "C" int chol_solve(chol_handle* h, double* b, int32_t nrhs, void* stream)
   }
   CHOL_CUDA_TRY(cudaGetLastError());
   return CHOL_OK;
+}
+
+// ---------------------------------------------------------------------------
+// chol_solve_noalloc: the same forward/backward substitution as chol_solve, for
+// callers that must not allocate device memory once set up -- for example a
+// service whose memory pool has already claimed the GPU, or a latency-bound
+// loop where a cudaMalloc could stall on device-wide synchronization. Its two
+// workspaces (the permuted right-hand sides and the per-level panel products)
+// live in one fixed, file-scope device array instead of handle-owned buffers.
+//
+// The array holds kNoAllocScratchDoubles doubles (16 MiB) on every GPU that
+// loads this library, for the life of the process. A solve needs n + w_rows
+// doubles per right-hand-side column (w_rows: the largest sum of off-diagonal
+// rows over one level); right-hand sides are processed in chunks that fit, and
+// a problem whose single column does not fit is rejected with CHOL_ETOOBIG.
+//
+// The array is shared by every call on a device and keeps the previous call's
+// contents; nothing in it needs to start at zero (each chunk writes Y before
+// reading it, and the first column step writes each W row before accumulating).
+// Calls whose work overlaps on the GPU (different streams or threads) race on
+// the array. The first call on each device looks up the array's device address
+// with cudaGetSymbolAddress (with that device current); make that first call
+// before any stream capture.
+// ---------------------------------------------------------------------------
+constexpr int64_t kNoAllocScratchDoubles = int64_t(1) << 21;
+static __device__ __align__(256) double g_noalloc_scratch[kNoAllocScratchDoubles];
+
+namespace {
+
+constexpr int kNoAllocMaxDevices = 64;
+std::mutex g_noalloc_mu;
+double* g_noalloc_addr[kNoAllocMaxDevices] = {};
+
+// Device address of g_noalloc_scratch on the current device (looked up once).
+int noalloc_scratch(double** out) {
+  int dev = -1;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kNoAllocMaxDevices) {
+    cudaGetLastError();
+    return CHOL_ECUDA;
+  }
+  std::lock_guard<std::mutex> lock(g_noalloc_mu);
+  if (!g_noalloc_addr[dev]) {
+    void* p = nullptr;
+    const cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+    if (e != cudaSuccess || !p) {
+      cudaGetLastError();
+      return CHOL_ECUDA;
+    }
+    g_noalloc_addr[dev] = static_cast<double*>(p);
+  }
+  *out = g_noalloc_addr[dev];
+  return CHOL_OK;
+}
+
+}  // namespace
+
+extern "C" int chol_solve_noalloc(chol_handle* h, double* b, int32_t nrhs, void* stream) {
+  if (!h) return -1;
+  if (!b && nrhs > 0 && h->n > 0) return -2;
+  if (nrhs < 0) return -3;
+  const int64_t per_col = (int64_t)h->n + h->w_rows_max;
+  if (per_col > kNoAllocScratchDoubles) return CHOL_ETOOBIG;
+  if (!h->factored || !h->dev) return CHOL_ESTATE;
+  if (nrhs == 0 || h->n == 0) return CHOL_OK;
+  double* scratch = nullptr;
+  int rc = noalloc_scratch(&scratch);
+  if (rc) return rc;
+  const int chunk = (int)std::min<int64_t>(kSolveChunk, kNoAllocScratchDoubles / std::max<int64_t>(per_col, 1));
+  DeviceState* D = h->dev;
+  cudaStream_t st = (cudaStream_t)stream;
+  const int nb = h->opt.block_cols;
+  const int n = h->n;
+  double* Y = scratch;
+  double* W = scratch + (int64_t)n * chunk;
+  for (int r0 = 0; r0 < nrhs; r0 += chunk) {
+    const int nr = std::min(chunk, nrhs - r0);
+    double* B = b + (int64_t)r0 * n;
+    k_permute_in<<<grid1d((int64_t)n * nr, 256), 256, 0, st>>>(B, D->perm, n, n, nr, Y);
+    for (const LevelPlan& P : h->levels) {
+      for (size_t k = 0; k < P.ssteps.size(); ++k) {
+        const SolveStep& s = P.ssteps[k];
+        const int k0 = (int)k * nb;
+        if (s.diag_n > 0)
+          k_diag<false><<<s.diag_n, kSolveThreads, 0, st>>>(D->sn, D->sdiag + s.diag_b, k0, nb, D->L, Y, n, nr);
+        if (s.fupd_n > 0)
+          k_fwd_update<<<s.fupd_n, kSolveThreads, 0, st>>>(D->sn, D->fupd + s.fupd_b, nb, D->L, Y, n, W, nr);
+      }
+      if (P.asm_n > 0)
+        k_fwd_assemble<<<P.asm_n, kSolveThreads, 0, st>>>(D->asm_tasks + P.asm_b, D->asm_segs, D->sn, D->rows,
+                                                          W, Y, n, nr);
+    }
+    for (int lv = h->nlevels - 1; lv >= 0; --lv) {
+      const LevelPlan& P = h->levels[lv];
+      if (P.bpanel_n > 0)
+        k_bwd_panel<<<P.bpanel_n, kSolveThreads, 0, st>>>(D->sn, D->bpanel + P.bpanel_b, D->rows, D->L, Y, n, nr);
+      for (int k = (int)P.ssteps.size() - 1; k >= 0; --k) {
+        const SolveStep& s = P.ssteps[k];
+        const int k0 = k * nb;
+        if (s.diag_n > 0)
+          k_diag<true><<<s.diag_n, kSolveThreads, 0, st>>>(D->sn, D->sdiag + s.diag_b, k0, nb, D->L, Y, n, nr);
+        if (s.bupd_n > 0)
+          k_bwd_update<<<s.bupd_n, kSolveThreads, 0, st>>>(D->sn, D->bupd + s.bupd_b, nb, D->L, Y, n, nr);
+      }
+    }
+    k_permute_out<<<grid1d((int64_t)n * nr, 256), 256, 0, st>>>(Y, D->perm, n, n, nr, B);
+  }
+  const cudaError_t e = cudaGetLastError();
+  return e == cudaSuccess ? CHOL_OK : CHOL_ECUDA;
 }
