@@ -160,7 +160,7 @@ def run_ours(args, rank, world, local_rank):
         import torch.distributed as dist
         dist.init_process_group("nccl")
     dev = torch.device("cuda", local_rank)
-    p = gridgen.workload("3d64")
+    p = gridgen.workload(args.workload)
     b = gridgen.rhs_uniform(p.n, NRHS, seed=2)
     opt = P.chol_default_options()
     opt.merge_growth = args.merge
@@ -255,7 +255,8 @@ def run_ours(args, rank, world, local_rank):
                 "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
                 "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
                 "data": "synthetic",
-                "config": {"workload": WORKLOAD, "nrhs": NRHS, "precision": "fp64",
+                "config": {"workload": WORKLOAD if args.workload == "3d64" else args.workload,
+                           "nrhs": NRHS, "precision": "fp64",
                            "merge_growth": args.merge, "supernodes": S.info.nsuper_storage,
                            "flops_stored_over_symbolic": S.info.flops_stored / flops,
                            "parallelism": "replicas" if world > 1 else "single",
@@ -283,6 +284,8 @@ def main():
     ap.add_argument("--cpu-grid", type=int, default=40)
     ap.add_argument("--ref-grid", type=int, default=32)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--workload", default="3d64", choices=["3d64", "3d48"],
+                    help="3d64 is the benchmark; 3d48 is the smaller case used for ncu captures")
     ap.add_argument("--merge", type=float, default=0.1,
                     help="relaxed supernode merging budget (fraction of nnz(L))")
     args = ap.parse_args()
