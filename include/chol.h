@@ -49,8 +49,22 @@ enum {
   CHOL_ETOOBIG = -1007    /* problem exceeds a fixed-size workspace */
 };
 
+/*
+ * Precision modes. The mixed modes scale A to D A D (D = diag(A)^{-1/2}, unit
+ * diagonal) before rounding it to binary32, keep binary32 panels (row-major),
+ * and win the accuracy back with binary64 iterative refinement
+ * (chol_solve_refine): binary64 residual r = b - A x, binary64 update of x.
+ * A diagonal block whose binary32 pivots fall below pivot_tau is refactored in
+ * binary64. The paper computes in binary64 only (D-prefixed BLAS, Sec. II-A);
+ * these modes are an extension.
+ */
 enum {
-  CHOL_PREC_FP64 = 0      /* every operation in IEEE binary64 */
+  CHOL_PREC_FP64 = 0,     /* every operation in IEEE binary64 */
+  CHOL_PREC_FP32 = 1,     /* binary32 storage and SIMT arithmetic */
+  CHOL_PREC_TF32 = 2,     /* binary32 storage; SYRK/GEMM tiles on tensor cores, TF32 operands */
+                          /* (tcgen05 kind::tf32, operands truncated by the hardware), FP32 accumulate */
+  CHOL_PREC_BF16 = 3      /* binary32 storage; SYRK/GEMM tiles on tensor cores, BF16 operands */
+                          /* (round-to-nearest-even copies), FP32 accumulate */
 };
 
 typedef struct chol_options {
@@ -69,6 +83,14 @@ typedef struct chol_options {
                            /* nnz(L); 0 = off (the maximal partition, default)  */
   int32_t small_max_rows;  /* rows limit of the one-CTA kernel; default 128     */
   int32_t reserved;
+  double pivot_tau;        /* mixed modes: a diagonal block with a binary32 pivot */
+                           /* L_jj^2 below this (scaled matrix) is refactored in  */
+                           /* binary64; default 1e-3                              */
+  int32_t static_pivot;    /* mixed modes: 1 = a pivot still below pivot_tau after */
+                           /* the binary64 redo is raised to pivot_tau (counted),  */
+                           /* leaving the correction to chol_solve_refine; 0 =    */
+                           /* report it as not positive definite (default)        */
+  int32_t reserved2;
 } chol_options;
 
 /* Fill *opt with the defaults. */
@@ -143,6 +165,27 @@ int chol_solve_noalloc(chol_handle* h, double* b, int32_t nrhs, void* stream);
  */
 int chol_logdet(chol_handle* h, double* out, void* stream);
 
+/*
+ * Iteratively refined solve (mixed modes; in CHOL_PREC_FP64 it is one solve
+ * plus the backward-error check). x_0 = solve(b); then, until the normwise
+ * backward error eta = ||b - A x||_inf / (||A||_inf ||x||_inf + ||b||_inf) of
+ * every right-hand side is <= tol: r = b - A x in binary64 (with the values of
+ * the last chol_factor), d = solve(r) with the low-precision factor, x += d in
+ * binary64. When plain refinement stagnates (eta shrinks by less than 2x per
+ * iteration) it switches to conjugate gradients in binary64 preconditioned by
+ * the same factor.
+ *   b        device, n x nrhs column-major (ld n), not modified
+ *   x        device, n x nrhs column-major (ld n), output
+ *   tol      target backward error (> 0)
+ *   max_iter iteration cap (>= 1)
+ *   iters    host, receives the iterations used (may be NULL)
+ *   berr     host, nrhs doubles, receives the final eta per right-hand side (may be NULL)
+ * Returns CHOL_OK, CHOL_ENOCONV if tol was not reached, or an error.
+ * Synchronizes `stream` once per iteration.
+ */
+int chol_solve_refine(chol_handle* h, const double* b, double* x, int32_t nrhs, double tol,
+                      int32_t max_iter, int32_t* iters, double* berr, void* stream);
+
 /* Sizes of the symbolic structure, for sizing the chol_get_symbolic arrays. */
 typedef struct chol_info {
   int32_t n;
@@ -162,6 +205,10 @@ typedef struct chol_info {
   int32_t reserved;
   int64_t nnz_stored;      /* stored factor entries incl. explicit zeros of merging */
   double flops_stored;     /* sum over stored columns of their stored count^2 */
+  int32_t precision;       /* CHOL_PREC_* of the handle */
+  int32_t fp64_fallbacks;  /* mixed modes: diagonal blocks refactored in binary64 by the last factor */
+  int32_t perturbed_pivots; /* mixed modes with static_pivot: pivots raised to pivot_tau */
+  int32_t reserved2;
 } chol_info;
 
 int chol_get_info(const chol_handle* h, chol_info* info);

@@ -25,9 +25,12 @@ CHOL_ESTATE = -1005
 CHOL_ENOTSUP = -1006
 CHOL_ETOOBIG = -1007
 CHOL_PREC_FP64 = 0
+CHOL_PREC_FP32 = 1
+CHOL_PREC_TF32 = 2
+CHOL_PREC_BF16 = 3
 
 EXPORTED = ["chol_default_options", "chol_analyze", "chol_factor", "chol_solve", "chol_solve_noalloc",
-            "chol_logdet",
+            "chol_solve_refine", "chol_logdet",
             "chol_get_info", "chol_get_symbolic", "chol_get_partition", "chol_get_factor", "chol_profile",
             "chol_get_stats", "chol_destroy", "chol_strerror"]
 
@@ -39,7 +42,8 @@ class chol_options(C.Structure):
     _fields_ = [("precision", C.c_int32), ("small_max_cols", C.c_int32),
                 ("small_max_panel", C.c_int32), ("block_cols", C.c_int32),
                 ("device_mem_cap", C.c_int64), ("merge_growth", C.c_double),
-                ("small_max_rows", C.c_int32), ("reserved", C.c_int32)]
+                ("small_max_rows", C.c_int32), ("reserved", C.c_int32), ("pivot_tau", C.c_double),
+                ("static_pivot", C.c_int32), ("reserved2", C.c_int32)]
 
 
 class chol_info(C.Structure):
@@ -49,7 +53,8 @@ class chol_info(C.Structure):
                 ("panel_doubles", C.c_int64), ("update_doubles", C.c_int64),
                 ("flops", C.c_double), ("n_small", C.c_int32), ("n_large", C.c_int32),
                 ("nsuper_storage", C.c_int32), ("reserved", C.c_int32), ("nnz_stored", C.c_int64),
-                ("flops_stored", C.c_double)]
+                ("flops_stored", C.c_double), ("precision", C.c_int32), ("fp64_fallbacks", C.c_int32),
+                ("perturbed_pivots", C.c_int32), ("reserved2", C.c_int32)]
 
 
 class chol_kernel_stat(C.Structure):
@@ -83,6 +88,9 @@ def lib():
         L.chol_solve.restype = C.c_int
         L.chol_solve_noalloc.argtypes = [P, P, C.c_int32, P]
         L.chol_solve_noalloc.restype = C.c_int
+        L.chol_solve_refine.argtypes = [P, P, P, C.c_int32, C.c_double, C.c_int32,
+                                        C.POINTER(C.c_int32), P, P]
+        L.chol_solve_refine.restype = C.c_int
         L.chol_logdet.argtypes = [P, C.POINTER(C.c_double), P]
         L.chol_logdet.restype = C.c_int
         L.chol_get_info.argtypes = [P, C.POINTER(chol_info)]
@@ -158,6 +166,15 @@ def chol_solve(h, b, nrhs, stream=None) -> int:
 def chol_solve_noalloc(h, b, nrhs, stream=None) -> int:
     """chol_solve whose workspaces come from a fixed device array (no allocation)."""
     return lib().chol_solve_noalloc(h, _dev_ptr(b), int(nrhs), _stream(stream))
+
+
+def chol_solve_refine(h, b, x, nrhs, tol=1e-10, max_iter=30, stream=None):
+    """Returns (rc, iterations, backward errors per right-hand side)."""
+    it = C.c_int32(0)
+    berr = np.zeros(max(int(nrhs), 1), np.float64)
+    rc = lib().chol_solve_refine(h, _dev_ptr(b), _dev_ptr(x), int(nrhs), float(tol), int(max_iter),
+                                 C.byref(it), _ptr(berr), _stream(stream))
+    return rc, it.value, berr[: int(nrhs)]
 
 
 def chol_logdet(h, stream=None):

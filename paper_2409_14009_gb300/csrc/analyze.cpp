@@ -26,6 +26,8 @@ extern "C" void chol_default_options(chol_options* opt) {
   opt->device_mem_cap = 0;
   opt->merge_growth = 0.0;
   opt->small_max_rows = 128;
+  opt->pivot_tau = 1e-3;
+  opt->static_pivot = 0;
 }
 
 namespace {
@@ -52,7 +54,12 @@ int validate(int32_t n, const int64_t* colptr, const int32_t* rowind, const int3
     }
   }
   if (opt) {
-    if (opt->precision != CHOL_PREC_FP64) return -5;
+    if (opt->precision < CHOL_PREC_FP64 || opt->precision > CHOL_PREC_BF16) return -5;
+    if (!(opt->pivot_tau > 0.0) || opt->pivot_tau >= 1.0) return -5;
+    if (opt->static_pivot != 0 && opt->static_pivot != 1) return -5;
+    // tensor-core K chunks are 32 (tf32) / 64 (bf16) wide and must not cross a column step
+    if (opt->precision == CHOL_PREC_TF32 && opt->block_cols % 32 != 0) return -5;
+    if (opt->precision == CHOL_PREC_BF16 && opt->block_cols % 64 != 0) return -5;
     if (opt->small_max_cols < 1 || opt->small_max_panel < 1 || opt->small_max_panel > 4096) return -5;
     if (opt->block_cols < 8 || opt->block_cols > 64) return -5;
     if (opt->device_mem_cap < 0) return -5;
@@ -211,6 +218,32 @@ void build(chol_handle* h, const int64_t* colptr, const int32_t* rowind) {
       }
     for (int32_t j = 0; j < n; ++j) std::sort(ent.begin() + bp[j], ent.begin() + bp[j + 1]);
   }
+  // ---- permuted (row, col) of every entry of A, and the full-matrix CSR of A in
+  //      its original ordering (both triangles) for binary64 residuals ----
+  h->aij.assign(2 * nnz, 0);
+  for (int32_t j = 0; j < n; ++j)
+    for (int64_t t = bp[j]; t < bp[j + 1]; ++t) {
+      h->aij[2 * ent[t].second] = ent[t].first;
+      h->aij[2 * ent[t].second + 1] = j;
+    }
+  h->csr_ptr.assign(n + 1, 0);
+  for (int32_t c = 0; c < n; ++c)
+    for (int64_t t = colptr[c]; t < colptr[c + 1]; ++t) {
+      h->csr_ptr[rowind[t] + 1]++;
+      if (rowind[t] != c) h->csr_ptr[c + 1]++;
+    }
+  for (int32_t i = 0; i < n; ++i) h->csr_ptr[i + 1] += h->csr_ptr[i];
+  h->csr_col.assign(h->csr_ptr[n], 0);
+  h->csr_src.assign(h->csr_ptr[n], 0);
+  {
+    std::vector<int64_t> nx(h->csr_ptr.begin(), h->csr_ptr.end() - 1);
+    for (int32_t c = 0; c < n; ++c)
+      for (int64_t t = colptr[c]; t < colptr[c + 1]; ++t) {
+        const int32_t r = rowind[t];
+        h->csr_col[nx[r]] = c; h->csr_src[nx[r]++] = t;
+        if (r != c) { h->csr_col[nx[c]] = r; h->csr_src[nx[c]++] = t; }
+      }
+  }
   // ---- row lists of B's strictly lower part (k < i with B_ik != 0) ----
   std::vector<int64_t> rp(n + 1, 0);
   for (int32_t j = 0; j < n; ++j)
@@ -317,11 +350,17 @@ void build(chol_handle* h, const int64_t* colptr, const int32_t* rowind) {
     d.f = h->sptr[J];
     d.s = h->sptr[J + 1] - h->sptr[J];
     d.len = (int32_t)(h->rowptr[J + 1] - h->rowptr[J]);
-    d.ld = (d.len + 1) & ~1;
     d.roff = h->rowptr[J];
     d.loff = off;
-    off += (int64_t)d.ld * d.s;
-    off = (off + 15) & ~int64_t(15);
+    if (h->opt.precision == CHOL_PREC_FP64) {
+      d.ld = (d.len + 1) & ~1;             // column-major, binary64
+      off += (int64_t)d.ld * d.s;
+      off = (off + 15) & ~int64_t(15);
+    } else {
+      d.ld = (d.s + 7) & ~7;               // row-major, binary32 (16-byte rows for TMA;
+      off += (int64_t)d.ld * d.len;        // 8-element rows also fit the BF16 copy)
+      off = (off + 31) & ~int64_t(31);
+    }
     h->max_cols = std::max(h->max_cols, d.s);
     h->max_len = std::max(h->max_len, d.len);
     for (int32_t c = 0; c < d.s; ++c) {
@@ -340,7 +379,9 @@ void build(chol_handle* h, const int64_t* colptr, const int32_t* rowind) {
       for (int32_t t = 0; t < d.len; ++t) pos[r[t]] = t;
       for (int32_t j = d.f; j < d.f + d.s; ++j)
         for (int64_t t = bp[j]; t < bp[j + 1]; ++t)
-          h->amap[ent[t].second] = d.loff + (int64_t)(j - d.f) * d.ld + pos[ent[t].first];
+          h->amap[ent[t].second] = h->opt.precision == CHOL_PREC_FP64
+                                       ? d.loff + (int64_t)(j - d.f) * d.ld + pos[ent[t].first]
+                                       : d.loff + (int64_t)pos[ent[t].first] * d.ld + (j - d.f);
     }
   }
   // ---- relind pairs (J ascending, K ascending) ----
@@ -364,6 +405,7 @@ void build(chol_handle* h, const int64_t* colptr, const int32_t* rowind) {
     h->relind_len += (h->snodes[h->rel_J[p]].len - h->snodes[h->rel_J[p]].s) - h->rel_c0[p];
   // ---- level schedule and task lists ----
   const int nb = h->opt.block_cols;
+  const int tg = (h->opt.precision == CHOL_PREC_TF32 || h->opt.precision == CHOL_PREC_BF16) ? kTileTC : kTile;
   std::vector<std::vector<int32_t>> by_level(h->nlevels);
   for (int32_t J = 0; J < ns; ++J) by_level[h->level[J]].push_back(J);
   // pairs by contributor level, then K, then J
@@ -391,7 +433,7 @@ void build(chol_handle* h, const int64_t* colptr, const int32_t* rowind) {
       SnodeDev& d = h->snodes[J];
       int32_t b = d.len - d.s;
       d.uoff = uo;
-      uo += (int64_t)b * b;
+      uo += (int64_t)b * (h->opt.precision == CHOL_PREC_FP64 ? b : ((b + 7) & ~7));
       d.wpre = wo;
       wo += b;
       bool small = d.s <= h->opt.small_max_cols && (int64_t)d.len * d.s <= h->opt.small_max_panel &&
@@ -430,8 +472,8 @@ void build(chol_handle* h, const int64_t* colptr, const int32_t* rowind) {
         const double below = (double)(d.len - k0 - kb);
         st.trsm_flops += below * (double)kb * (double)kb;   // kb divisions + 2*kb(kb-1)/2 per row
         for (int32_t r0 = k0 + kb; r0 < d.len; r0 += kTrsmRowsHost) h->trsm_tasks.push_back({J, k0, r0, 0});
-        for (int32_t c0 = k0 + kb; c0 < d.s; c0 += kTile)
-          for (int32_t r0 = c0; r0 < d.len; r0 += kTile) h->gemm_tasks.push_back({J, k0, r0, c0});
+        for (int32_t c0 = k0 + kb; c0 < d.s; c0 += tg)
+          for (int32_t r0 = c0; r0 < d.len; r0 += tg) h->gemm_tasks.push_back({J, k0, r0, c0});
         // trailing update: 2 kb flops per entry (r, c) with c in [k0+kb, s), r in [c, len)
         {
           const double w = (double)(d.s - k0 - kb), hgt = (double)(d.len - k0 - kb);
@@ -449,8 +491,8 @@ void build(chol_handle* h, const int64_t* colptr, const int32_t* rowind) {
       const SnodeDev& d = h->snodes[J];
       int32_t b = d.len - d.s;
       P.syrk_flops += 2.0 * d.s * ((double)b * (b + 1) / 2.0);
-      for (int32_t c0 = 0; c0 < b; c0 += kTile)
-        for (int32_t r0 = c0; r0 < b; r0 += kTile) h->syrk_tasks.push_back({J, 0, r0, c0});
+      for (int32_t c0 = 0; c0 < b; c0 += tg)
+        for (int32_t r0 = c0; r0 < b; r0 += tg) h->syrk_tasks.push_back({J, 0, r0, c0});
     }
     P.syrk_n = (int32_t)h->syrk_tasks.size() - P.syrk_b;
     // blocked triangular solves over every supernode of the level
@@ -539,6 +581,7 @@ extern "C" int chol_analyze(int32_t n, const int64_t* colptr, const int32_t* row
     h->iperm.resize(n);
     for (int32_t i = 0; i < n; ++i) h->perm[i] = perm ? perm[i] : i;
     for (int32_t i = 0; i < n; ++i) h->iperm[h->perm[i]] = i;
+    h->diagpos_orig.assign(colptr, colptr + n);   // diagonal = first entry of each column
     build(h, colptr, rowind);
   } catch (const std::bad_alloc&) {
     delete h;
@@ -563,6 +606,9 @@ extern "C" int chol_get_info(const chol_handle* h, chol_info* info) {
   info->n = h->n;
   info->nsuper = (int32_t)h->c_sptr.size() - 1;
   info->nsuper_storage = h->ns;
+  info->precision = h->opt.precision;
+  info->fp64_fallbacks = h->fp64_fallbacks;
+  info->perturbed_pivots = h->perturbed_pivots;
   info->nnz_stored = h->nnz_stored;
   info->flops_stored = h->flops_stored;
   info->nlevels = h->nlevels;

@@ -1,6 +1,7 @@
 // device.h -- device-side state of a handle and helpers shared by the CUDA
 // translation units.
 #pragma once
+#include <cuda.h>
 #include <cuda_runtime.h>
 
 #include <vector>
@@ -33,6 +34,30 @@ struct DeviceState {
   double* part = nullptr;       // logdet partial sums (one per supernode)
   double* scalar_host = nullptr;   // pinned
   double* scalar_dev = nullptr;
+  // mixed modes
+  bool mx_ready = false;
+  int64_t* mx_diagpos = nullptr;   // position of A_ii of P A P^T in the values array
+  int32_t* mx_aij = nullptr;       // (row, col) of P A P^T per entry of A
+  double* mx_d = nullptr;          // D = diag(P A P^T)^{-1/2}
+  int32_t* mx_fallbacks = nullptr; // diagonal blocks redone in binary64
+  int64_t* csr_ptr = nullptr;      // full symmetric A, original ordering (refinement)
+  int32_t* csr_col = nullptr;
+  int64_t* csr_src = nullptr;
+  double* csr_val = nullptr;
+  void* Lbf = nullptr;             // bf16 copy of the panels (CHOL_PREC_BF16)
+  CUtensorMap* tmaps = nullptr;    // one TMA map per supernode
+  int32_t* tc_err = nullptr;       // tensor-core tile timeout flag
+  // refinement workspaces
+  double* R = nullptr;
+  double* Z = nullptr;
+  double* Pv = nullptr;
+  double* Q = nullptr;
+  double* red = nullptr;           // reduction scratch
+  double* red_host = nullptr;      // pinned
+  int refine_cap = 0;
+  float* Y32 = nullptr;            // binary32 solve workspaces
+  float* W32 = nullptr;
+  double* rhs_scale = nullptr;
   // solve workspaces (grown on demand)
   double* Y = nullptr;          // permuted right-hand sides, n x chunk
   double* W = nullptr;          // per-level panel products, w_rows_max x chunk

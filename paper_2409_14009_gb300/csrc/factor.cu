@@ -24,6 +24,7 @@
 #include <cstring>
 
 #include "device.h"
+#include "mixed.h"
 
 namespace {
 
@@ -397,6 +398,13 @@ __global__ void k_logdet_reduce(const double* __restrict__ part, int ns, double*
   if (threadIdx.x == 0) *out = 2.0 * red[0];
 }
 
+// out[t] = vals[src[t]]
+__global__ void k_gather_src(const double* __restrict__ vals, const int64_t* __restrict__ src, int64_t m,
+                             double* __restrict__ out) {
+  for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < m; t += (int64_t)gridDim.x * blockDim.x)
+    out[t] = vals[src[t]];
+}
+
 // out[t] = L[map[t]] (panel entries -> compressed sparse column order).
 __global__ void k_gather(const double* __restrict__ L, const int64_t* __restrict__ map, int64_t nnz,
                          double* __restrict__ out) {
@@ -464,6 +472,8 @@ extern "C" int chol_get_stats(chol_handle* h, chol_kernel_stat* out, int32_t res
   return CHOL_OK;
 }
 
+void chol_status_init(int* status, cudaStream_t st) { k_status_init<<<1, 1, 0, st>>>(status); }
+
 int chol_dalloc(chol_handle* h, void** p, size_t bytes) {
   DeviceState* D = h->dev;
   *p = nullptr;
@@ -488,11 +498,15 @@ void chol_device_free(chol_handle* h) {
   if (D->device >= 0) cudaSetDevice(D->device);
   void* ptrs[] = {D->L, D->U, D->sn, D->rows, D->amap, D->small_list, D->potrf_list,
                   D->level_snodes, D->trsm, D->gemm, D->syrk, D->asm_tasks, D->asm_segs, D->sdiag,
-                  D->fupd, D->bupd, D->bpanel, D->perm, D->status, D->part, D->scalar_dev, D->Y, D->W};
+                  D->fupd, D->bupd, D->bpanel, D->perm, D->status, D->part, D->scalar_dev, D->Y, D->W,
+                  D->mx_diagpos, D->mx_aij, D->mx_d, D->mx_fallbacks, D->csr_ptr, D->csr_col, D->csr_src,
+                  D->csr_val, D->Lbf, D->tmaps, D->tc_err, D->R, D->Z, D->Pv, D->Q, D->red, D->Y32, D->W32,
+                  D->rhs_scale};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   if (D->status_host) cudaFreeHost(D->status_host);
   if (D->scalar_host) cudaFreeHost(D->scalar_host);
+  if (D->red_host) cudaFreeHost(D->red_host);
   if (cur >= 0) cudaSetDevice(cur);
   delete D;
   h->dev = nullptr;
@@ -512,8 +526,20 @@ int chol_device_ensure(chol_handle* h) {
     return code;
   };
   if (cudaGetDevice(&D->device) != cudaSuccess) return fail(CHOL_ECUDA);
-  if ((rc = chol_dalloc(h, (void**)&D->L, sizeof(double) * (size_t)std::max<int64_t>(h->panel_doubles, 1)))) return fail(rc);
-  if ((rc = chol_dalloc(h, (void**)&D->U, sizeof(double) * (size_t)std::max<int64_t>(h->update_doubles, 1)))) return fail(rc);
+  if (h->opt.precision != CHOL_PREC_FP64) {
+    // the tensor-core and binary32 kernels are built for this architecture only
+    cudaDeviceProp prop;
+    if (cudaGetDeviceProperties(&prop, D->device) != cudaSuccess) return fail(CHOL_ECUDA);
+    if (prop.major != 10) return fail(CHOL_ENOTSUP);
+  }
+  const size_t esz = h->opt.precision == CHOL_PREC_FP64 ? sizeof(double) : sizeof(float);
+  if ((rc = chol_dalloc(h, (void**)&D->L, esz * (size_t)std::max<int64_t>(h->panel_doubles, 1)))) return fail(rc);
+  if ((rc = chol_dalloc(h, (void**)&D->U, esz * (size_t)std::max<int64_t>(h->update_doubles, 1)))) return fail(rc);
+  if ((rc = upload(h, &D->csr_ptr, h->csr_ptr))) return fail(rc);
+  if ((rc = upload(h, &D->csr_col, h->csr_col))) return fail(rc);
+  if ((rc = upload(h, &D->csr_src, h->csr_src))) return fail(rc);
+  if ((rc = chol_dalloc(h, (void**)&D->csr_val, sizeof(double) * (size_t)std::max<int64_t>(h->csr_ptr[h->n], 1))))
+    return fail(rc);
   if ((rc = upload(h, &D->sn, h->snodes))) return fail(rc);
   if ((rc = upload(h, &D->rows, h->rows))) return fail(rc);
   if ((rc = upload(h, &D->amap, h->amap))) return fail(rc);
@@ -533,7 +559,7 @@ int chol_device_ensure(chol_handle* h) {
   if ((rc = chol_dalloc(h, (void**)&D->status, sizeof(int32_t)))) return fail(rc);
   if ((rc = chol_dalloc(h, (void**)&D->part, sizeof(double) * (size_t)std::max(h->ns, 1)))) return fail(rc);
   if ((rc = chol_dalloc(h, (void**)&D->scalar_dev, sizeof(double)))) return fail(rc);
-  if (cudaMallocHost((void**)&D->status_host, sizeof(int32_t)) != cudaSuccess) return fail(CHOL_ENOMEM);
+  if (cudaMallocHost((void**)&D->status_host, 4 * sizeof(int32_t)) != cudaSuccess) return fail(CHOL_ENOMEM);
   if (cudaMallocHost((void**)&D->scalar_host, sizeof(double)) != cudaSuccess) return fail(CHOL_ENOMEM);
   static bool attrs_done = false;
   if (!attrs_done) {
@@ -552,6 +578,7 @@ extern "C" int chol_factor(chol_handle* h, const double* values, void* stream) {
   if (rc) return rc;
   DeviceState* D = h->dev;
   cudaStream_t st = (cudaStream_t)stream;
+  if (h->opt.precision != CHOL_PREC_FP64) return chol_factor_mixed(h, values, st);
   const int nb = h->opt.block_cols;
   h->factored = false;
   k_status_init<<<1, 1, 0, st>>>(D->status);
@@ -559,6 +586,9 @@ extern "C" int chol_factor(chol_handle* h, const double* values, void* stream) {
   if (h->nnz_a > 0) {
     KScope ks(h, CHOL_K_SCATTER, st, 0.0, 24.0 * (double)h->nnz_a);
     k_scatter<<<grid1d(h->nnz_a, 256), 256, 0, st>>>(values, D->amap, h->nnz_a, D->L);
+    // binary64 copy of A in CSR order for residuals (chol_solve_refine)
+    const int64_t m = h->csr_ptr[h->n];
+    k_gather_src<<<grid1d(m, 256), 256, 0, st>>>(values, D->csr_src, m, D->csr_val);
   }
   for (const LevelPlan& P : h->levels) {
     if (P.small_n > 0) {
@@ -608,6 +638,7 @@ extern "C" int chol_logdet(chol_handle* h, double* out, void* stream) {
   if (!h->factored) return CHOL_ESTATE;
   DeviceState* D = h->dev;
   cudaStream_t st = (cudaStream_t)stream;
+  if (h->opt.precision != CHOL_PREC_FP64) return chol_logdet_mixed(h, out, st);
   if (h->ns > 0) {
     KScope ks(h, CHOL_K_LOGDET, st, (double)h->n, 8.0 * h->n);
     k_logdet_part<<<h->ns, 128, 0, st>>>(D->sn, D->L, D->part);
@@ -659,7 +690,9 @@ extern "C" int chol_get_factor(chol_handle* h, int64_t* lp, int32_t* li, double*
           const int32_t lenk = (int32_t)(h->c_rowptr[K + 1] - h->c_rowptr[K]);
           const int32_t ck = j - h->c_sptr[K];
           for (int32_t t = ck; t < lenk; ++t)
-            h->cscmap[hp[j] + (t - ck)] = d.loff + (int64_t)c * d.ld + pos[rk[t]];
+            h->cscmap[hp[j] + (t - ck)] = h->opt.precision == CHOL_PREC_FP64
+                                              ? d.loff + (int64_t)c * d.ld + pos[rk[t]]
+                                              : d.loff + (int64_t)pos[rk[t]] * d.ld + c;
         }
         for (int32_t t = 0; t < d.len; ++t) pos[r[t]] = -1;
       }
@@ -676,7 +709,28 @@ extern "C" int chol_get_factor(chol_handle* h, int64_t* lp, int32_t* li, double*
     }
     CHOL_CUDA_TRY(cudaMemcpyAsync(dmap, h->cscmap.data(), sizeof(int64_t) * (size_t)h->nnz_l,
                                   cudaMemcpyHostToDevice, st));
-    k_gather<<<grid1d(h->nnz_l, 256), 256, 0, st>>>(D->L, dmap, h->nnz_l, dlx);
+    if (h->opt.precision == CHOL_PREC_FP64) {
+      k_gather<<<grid1d(h->nnz_l, 256), 256, 0, st>>>(D->L, dmap, h->nnz_l, dlx);
+    } else {
+      // L = D^{-1} L~: needs the permuted row of every entry
+      std::vector<int32_t> lrow(h->nnz_l);
+      for (int32_t K = 0; K < cns; ++K) {
+        const int32_t f = h->c_sptr[K];
+        const int32_t* r = h->c_rows.data() + h->c_rowptr[K];
+        const int32_t len = (int32_t)(h->c_rowptr[K + 1] - h->c_rowptr[K]);
+        for (int32_t c = 0; c < h->c_sptr[K + 1] - f; ++c)
+          for (int32_t t = c; t < len; ++t) lrow[hp[f + c] + (t - c)] = r[t];
+      }
+      int32_t* dlrow = nullptr;
+      rc = chol_dalloc(h, (void**)&dlrow, sizeof(int32_t) * (size_t)h->nnz_l);
+      if (rc) return rc;
+      CHOL_CUDA_TRY(cudaMemcpyAsync(dlrow, lrow.data(), sizeof(int32_t) * (size_t)h->nnz_l, cudaMemcpyHostToDevice, st));
+      rc = chol_gather_mixed(h, dmap, dlrow, dlx, st);
+      CHOL_CUDA_TRY(cudaStreamSynchronize(st));
+      cudaFree(dlrow);
+      D->bytes -= (int64_t)sizeof(int32_t) * h->nnz_l;
+      if (rc) return rc;
+    }
     CHOL_CUDA_TRY(cudaMemcpyAsync(lx, dlx, sizeof(double) * (size_t)h->nnz_l, cudaMemcpyDeviceToHost, st));
     CHOL_CUDA_TRY(cudaStreamSynchronize(st));
     cudaFree(dmap);

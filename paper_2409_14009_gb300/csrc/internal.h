@@ -80,6 +80,13 @@ struct chol_handle {
   std::vector<int64_t> cscmap;      // canonical CSC entry -> panel position (built on request)
   std::vector<SnodeDev> snodes;
   std::vector<int64_t> amap;        // entry t of A -> position in L storage
+  std::vector<int32_t> aij;         // entry t of A -> (row, col) of P A P^T (pairs)
+  std::vector<int64_t> csr_ptr;     // full symmetric A in its original ordering (CSR)
+  std::vector<int32_t> csr_col;
+  std::vector<int64_t> csr_src;     // CSR entry -> entry of the lower CSC input
+  int32_t fp64_fallbacks = 0;
+  int32_t perturbed_pivots = 0;
+  std::vector<int64_t> diagpos_orig;  // position of A_jj in the values array, per original column
   int64_t nnz_l = 0, panel_doubles = 0, update_doubles = 0, w_rows_max = 0, nnz_stored = 0;
   double flops = 0.0, flops_stored = 0.0;
   // (J, K) pairs: J updates ancestor K through U_J columns [c0, c1) (J ascending, K ascending)
@@ -102,7 +109,8 @@ struct chol_handle {
 };
 
 // Tile sizes shared by the schedule builder and the kernels.
-constexpr int kTile = 64;        // GEMM/SYRK tile edge and TRSM row block
+constexpr int kTile = 64;        // SIMT GEMM/SYRK tile edge
+constexpr int kTileTC = 128;     // tensor-core (tcgen05) GEMM/SYRK tile edge
 constexpr int kAsmCols = 64;     // assembly task width (target columns)
 constexpr int kTrsmRowsHost = 32; // TRSM task height (rows)
 constexpr int kBwdCols = 8;      // backward-solve panel column block (one warp per column)

@@ -1,0 +1,582 @@
+// mixed.cu -- the mixed-precision form of the RL factorization (Sec. II-A) and
+// the binary64 refinement around it.
+//
+// The matrix is scaled to D A D (D = diag(A)^{-1/2}, unit diagonal) while its
+// values are scattered into binary32 panels. The panels are row-major, so both
+// operands of every update GEMM are K-major, which the tensor cores want. The
+// per-supernode steps are the same as in binary64:
+// - POTRF of 64-column diagonal blocks in binary32. A block whose binary32
+//   pivots fall below pivot_tau is redone in binary64.
+// - TRSM of the rows below.
+// - The trailing update and the SYRK update matrix.
+// - The pull-ordered relind scatter-add.
+// In CHOL_PREC_FP32 the updates run on binary32 SIMT tiles; in TF32/BF16 they
+// run on tcgen05 tensor-core tiles (tc_gemm.cuh). Accuracy is won back by
+// iterative refinement with binary64 residuals (refine.cu).
+#include <climits>
+#include <cmath>
+#include <cstring>
+
+#include <cuda_bf16.h>
+
+#include "device.h"
+#include "mixed.h"
+
+namespace {
+
+constexpr int kMxThreads = 256;
+
+// d[i] = 1/sqrt(A_ii) of P A P^T; a non-positive diagonal keeps d = 1 (the
+// factorization then reports the failing pivot itself).
+__global__ void k_mx_scale(const double* __restrict__ vals, const int64_t* __restrict__ diagpos, int n,
+                           double* __restrict__ d) {
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+    const double a = vals[diagpos[i]];
+    d[i] = a > 0.0 ? 1.0 / sqrt(a) : 1.0;
+  }
+}
+
+__global__ void k_mx_scatter(const double* __restrict__ vals, const int64_t* __restrict__ amap,
+                             const int32_t* __restrict__ aij, const double* __restrict__ d, int64_t nnz,
+                             float* __restrict__ L) {
+  for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < nnz; t += (int64_t)gridDim.x * blockDim.x)
+    L[amap[t]] = (float)(vals[t] * d[aij[2 * t]] * d[aij[2 * t + 1]]);
+}
+
+// Dense right-looking Cholesky of the first s columns of a len x s row-major
+// block in shared memory (ld = s). Same failure convention as the binary64 path.
+template <class T>
+__device__ void dense_chol_rowmajor(T* P, int len, int s, int fcol, int* status, T spiv, int* nperturbed) {
+  for (int k = 0; k < s; ++k) {
+    __syncthreads();
+    T dv = P[k * s + k];
+    if (spiv > T(0) && !(dv >= spiv)) {      // static pivoting: raise the pivot
+      dv = spiv;
+      if (threadIdx.x == 0) atomicAdd(nperturbed, 1);
+    }
+    const bool bad = !(dv > T(0));
+    const T dk = bad ? T(__longlong_as_double(0x7ff8000000000000LL)) : sqrt(dv);
+    const T inv = T(1) / dk;
+    for (int r = k + 1 + threadIdx.x; r < len; r += blockDim.x) P[r * s + k] *= inv;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      P[k * s + k] = dk;
+      if (bad) atomicMin(status, fcol + k + 1);
+    }
+    for (int r = k + 1 + threadIdx.x; r < len; r += blockDim.x) {
+      const T lrk = P[r * s + k];
+      const int jmax = r < s - 1 ? r : s - 1;
+      for (int j = k + 1; j <= jmax; ++j) P[r * s + j] -= lrk * P[j * s + k];
+    }
+  }
+  __syncthreads();
+}
+
+// One CTA per small supernode: binary32 panel in shared memory, U_J row-major
+// lower (row u holds columns c <= u, leading dimension ldu = b rounded to 8).
+__global__ void __launch_bounds__(128)
+k_mx_small(const SnodeDev* __restrict__ sn, const int32_t* __restrict__ list, float* __restrict__ L,
+           float* __restrict__ U, int* status, float spiv, int* counters) {
+  extern __shared__ float Pf[];
+  const SnodeDev d = sn[list[blockIdx.x]];
+  const int len = d.len, s = d.s, b = len - s;
+  float* G = L + d.loff;
+  for (int q = threadIdx.x; q < len * s; q += blockDim.x) Pf[q] = G[(int64_t)(q / s) * d.ld + q % s];
+  dense_chol_rowmajor<float>(Pf, len, s, d.f, status, spiv, counters + 1);
+  for (int q = threadIdx.x; q < len * s; q += blockDim.x) {
+    const int r = q / s, c = q % s;
+    if (r >= c) G[(int64_t)r * d.ld + c] = Pf[q];
+  }
+  if (b <= 0) return;
+  const int ldu = (b + 7) & ~7;
+  float* Uj = U + d.uoff;
+  const float* R = Pf + s * s;   // row u of L_RJ at R[u * s]
+  const int64_t total = (int64_t)b * (b + 1) / 2;
+  int u = 0;
+  int64_t ustart = 0;            // flat index of (u, 0)
+  for (int64_t q = threadIdx.x; q < total; q += blockDim.x) {
+    while (q >= ustart + u + 1) { ustart += u + 1; ++u; }
+    const int c = (int)(q - ustart);
+    float acc = 0.f;
+    for (int k = 0; k < s; ++k) acc = fmaf(R[u * s + k], R[c * s + k], acc);
+    Uj[(int64_t)u * ldu + c] = acc;
+  }
+}
+
+// Register-blocked Cholesky of a kb x kb (kb <= 64) row-major block, 256
+// threads, thread (tx, ty) holding (ty + 16a, tx + 16b). Returns through
+// *minpiv the smallest pivot seen before its square root.
+template <class T>
+__device__ void potrf_block_regs(const float* __restrict__ G, int64_t ld, int kb, T (&v)[4][4], T* colk,
+                                 T* sdiag, float* sminpiv, int tx, int ty, int fcol, int* status,
+                                 bool record, T spiv, int* nperturbed) {
+#pragma unroll
+  for (int a = 0; a < 4; ++a)
+#pragma unroll
+    for (int b = 0; b < 4; ++b) {
+      const int r = ty + 16 * a, c = tx + 16 * b;
+      v[a][b] = (r < kb && c < kb && r >= c) ? T(G[r * ld + c]) : T(0);
+    }
+#pragma unroll 1
+  for (int kk = 0; kk < 4; ++kk) {
+#pragma unroll
+    for (int k1 = 0; k1 < 16; ++k1) {
+      const int k = kk * 16 + k1;
+      if (k >= kb) break;
+      if (tx == k1 && ty == k1) {
+        T dv = T(0);
+#pragma unroll
+        for (int a = 0; a < 4; ++a)
+          if (a == kk) {
+#pragma unroll
+            for (int b = 0; b < 4; ++b)
+              if (b == kk) dv = v[a][b];
+          }
+        if (spiv > T(0) && !(dv >= spiv)) {   // static pivoting: raise the pivot
+          dv = spiv;
+          atomicAdd(nperturbed, 1);
+        }
+        const bool bad = !(dv > T(0));
+        if ((float)dv < *sminpiv || bad) *sminpiv = bad ? -1.f : (float)dv;
+        *sdiag = bad ? T(__longlong_as_double(0x7ff8000000000000LL)) : sqrt(dv);
+        if (bad && record) atomicMin(status, fcol + k + 1);
+      }
+      __syncthreads();
+      const T dk = *sdiag;
+      const T inv = T(1) / dk;
+      if (tx == k1) {
+#pragma unroll
+        for (int a = 0; a < 4; ++a) {
+          const int r = ty + 16 * a;
+#pragma unroll
+          for (int b = 0; b < 4; ++b)
+            if (b == kk) {
+              if (r > k) { v[a][b] *= inv; colk[r] = v[a][b]; }
+              else if (r == k) v[a][b] = dk;
+            }
+        }
+      }
+      __syncthreads();
+#pragma unroll
+      for (int a = 0; a < 4; ++a) {
+        const int r = ty + 16 * a;
+        if (r <= k || r >= kb) continue;
+        const T lr = colk[r];
+#pragma unroll
+        for (int b = 0; b < 4; ++b) {
+          const int c = tx + 16 * b;
+          if (c > k && c <= r) v[a][b] -= lr * colk[c];
+        }
+      }
+    }
+  }
+  __syncthreads();
+}
+
+// Blocked path, step k0: diagonal block in binary32; redone in binary64 when a
+// binary32 pivot (before its square root) falls below tau.
+__global__ void __launch_bounds__(256)
+k_mx_potrf(const SnodeDev* __restrict__ sn, const int32_t* __restrict__ list, int k0, int nb, float tau,
+           int static_pivot, float* __restrict__ L, int* status, int* counters) {
+  __shared__ double colk_d[64];
+  __shared__ float colk_f[64];
+  __shared__ double sdiag_d;
+  __shared__ float sdiag_f;
+  __shared__ float sminpiv;
+  const SnodeDev d = sn[list[blockIdx.x]];
+  const int kb = min(nb, d.s - k0);
+  float* G = L + d.loff + (int64_t)k0 * d.ld + k0;
+  const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
+  if (threadIdx.x == 0) sminpiv = 3.0e38f;
+  __syncthreads();
+  float vf[4][4];
+  potrf_block_regs<float>(G, d.ld, kb, vf, colk_f, &sdiag_f, &sminpiv, tx, ty, d.f + k0, status, false, 0.f,
+                          counters + 1);
+  if (!(sminpiv >= tau)) {
+    // binary64 redo from the (still unmodified) block in global memory
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      sminpiv = 3.0e38f;
+      atomicAdd(counters, 1);
+    }
+    __syncthreads();
+    double vd[4][4];
+    potrf_block_regs<double>(G, d.ld, kb, vd, colk_d, &sdiag_d, &sminpiv, tx, ty, d.f + k0, status, true,
+                             static_pivot ? (double)tau : 0.0, counters + 1);
+#pragma unroll
+    for (int a = 0; a < 4; ++a)
+#pragma unroll
+      for (int b = 0; b < 4; ++b) vf[a][b] = (float)vd[a][b];
+  }
+#pragma unroll
+  for (int a = 0; a < 4; ++a)
+#pragma unroll
+    for (int b = 0; b < 4; ++b) {
+      const int r = ty + 16 * a, c = tx + 16 * b;
+      if (r < kb && c < kb && r >= c) G[(int64_t)r * d.ld + c] = vf[a][b];
+    }
+}
+
+// Blocked path, step k0: rows [r0, r0+32) of the column block become
+// X = B L_kk^{-T}; eight lanes per row, shuffle broadcast (as in binary64).
+__global__ void __launch_bounds__(256)
+k_mx_trsm(const SnodeDev* __restrict__ sn, const TileTask* __restrict__ tasks, int nb,
+          float* __restrict__ L, __nv_bfloat16* __restrict__ Lb) {
+  __shared__ float Lk[64 * 65];
+  __shared__ float inv[64];
+  const TileTask t = tasks[blockIdx.x];
+  const SnodeDev d = sn[t.J];
+  const int kb = min(nb, d.s - t.k0);
+  const float* Gd = L + d.loff + (int64_t)t.k0 * d.ld + t.k0;
+  for (int q = threadIdx.x; q < kb * kb; q += blockDim.x) {
+    const int r = q / kb, c = q % kb;
+    Lk[r + c * 65] = Gd[(int64_t)r * d.ld + c];
+  }
+  __syncthreads();
+  for (int c = threadIdx.x; c < kb; c += blockDim.x) inv[c] = 1.0f / Lk[c + c * 65];
+  __syncthreads();
+  const int g = threadIdx.x >> 3, q = threadIdx.x & 7;
+  const int row = t.r0 + g;
+  const bool live = row < d.len;
+  float* Gx = L + d.loff + (int64_t)row * d.ld + t.k0;
+  float x[8];
+#pragma unroll
+  for (int m = 0; m < 8; ++m) {
+    const int c = q + 8 * m;
+    x[m] = (live && c < kb) ? Gx[c] : 0.f;
+  }
+#pragma unroll
+  for (int jm = 0; jm < 8; ++jm) {
+#pragma unroll
+    for (int jq = 0; jq < 8; ++jq) {
+      const int j = jm * 8 + jq;
+      if (j < kb) {
+        const float xj = __shfl_sync(0xffffffffu, x[jm] * inv[j], jq, 8);
+        if (q == jq) x[jm] = xj;
+#pragma unroll
+        for (int m = 0; m < 8; ++m) {
+          const int c = q + 8 * m;
+          if (c > j && c < kb) x[m] = fmaf(-xj, Lk[c + j * 65], x[m]);
+        }
+      }
+    }
+  }
+  if (live) {
+    // the bf16 copy (CHOL_PREC_BF16) feeds the tensor-core tiles; these rows
+    // are final once solved
+    __nv_bfloat16* Bx = Lb ? Lb + d.loff + (int64_t)row * d.ld + t.k0 : nullptr;
+#pragma unroll
+    for (int m = 0; m < 8; ++m) {
+      const int c = q + 8 * m;
+      if (c < kb) {
+        Gx[c] = x[m];
+        if (Bx) Bx[c] = __float2bfloat16_rn(x[m]);
+      }
+    }
+  }
+}
+
+// 64 x 64 binary32 SIMT tile of C (op)= A B^T with row-major A, B (K
+// contiguous) and row-major C; entries with row + rdiag >= col only.
+template <bool SUB>
+__device__ __forceinline__ void gemm_nt_tile_f32(const float* __restrict__ A, int64_t lda,
+                                                 const float* __restrict__ B, int64_t ldb, int K,
+                                                 float* __restrict__ C, int64_t ldc, int M, int N,
+                                                 int rdiag) {
+  constexpr int KC = 16;
+  __shared__ float As[KC][kTile + 4];
+  __shared__ float Bs[KC][kTile + 4];
+  const int tid = threadIdx.x;
+  const int tx = tid & 15, ty = tid >> 4;
+  float acc[4][4] = {};
+  for (int k = 0; k < K; k += KC) {
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      const int idx = tid + 256 * q;
+      const int kk = idx & 15, r = idx >> 4;
+      const bool kin = k + kk < K;
+      As[kk][r] = (kin && r < M) ? A[r * lda + k + kk] : 0.f;
+      Bs[kk][r] = (kin && r < N) ? B[r * ldb + k + kk] : 0.f;
+    }
+    __syncthreads();
+#pragma unroll
+    for (int kk = 0; kk < KC; ++kk) {
+      float a[4], bb[4];
+#pragma unroll
+      for (int i = 0; i < 4; ++i) a[i] = As[kk][ty + 16 * i];
+#pragma unroll
+      for (int j = 0; j < 4; ++j) bb[j] = Bs[kk][tx + 16 * j];
+#pragma unroll
+      for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j) acc[i][j] = fmaf(a[i], bb[j], acc[i][j]);
+    }
+    __syncthreads();
+  }
+#pragma unroll
+  for (int i = 0; i < 4; ++i)
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      const int r = ty + 16 * i, c = tx + 16 * j;
+      if (r < M && c < N && r + rdiag >= c) {
+        float* p = C + r * ldc + c;
+        *p = SUB ? (*p - acc[i][j]) : acc[i][j];
+      }
+    }
+}
+
+__global__ void __launch_bounds__(256)
+k_mx_gemm_simt(const SnodeDev* __restrict__ sn, const TileTask* __restrict__ tasks, int nb,
+               float* __restrict__ L) {
+  const TileTask t = tasks[blockIdx.x];
+  const SnodeDev d = sn[t.J];
+  const int kb = min(nb, d.s - t.k0);
+  float* P = L + d.loff;
+  gemm_nt_tile_f32<true>(P + (int64_t)t.r0 * d.ld + t.k0, d.ld, P + (int64_t)t.c0 * d.ld + t.k0, d.ld, kb,
+                         P + (int64_t)t.r0 * d.ld + t.c0, d.ld, min(kTile, d.len - t.r0),
+                         min(kTile, d.s - t.c0), t.r0 - t.c0);
+}
+
+__global__ void __launch_bounds__(256)
+k_mx_syrk_simt(const SnodeDev* __restrict__ sn, const TileTask* __restrict__ tasks,
+               const float* __restrict__ L, float* __restrict__ U) {
+  const TileTask t = tasks[blockIdx.x];
+  const SnodeDev d = sn[t.J];
+  const int b = d.len - d.s;
+  const int ldu = (b + 7) & ~7;
+  const float* R = L + d.loff + (int64_t)d.s * d.ld;
+  gemm_nt_tile_f32<false>(R + (int64_t)t.r0 * d.ld, d.ld, R + (int64_t)t.c0 * d.ld, d.ld, d.s,
+                          U + d.uoff + (int64_t)t.r0 * ldu + t.c0, ldu, min(kTile, b - t.r0),
+                          min(kTile, b - t.c0), t.r0 - t.c0);
+}
+
+// Pull-ordered relind scatter-add into row-major binary32 panels. Task = target
+// K and its columns [t0, t1); per segment the positions of J's rows in struct(K)
+// are found by binary search in shared memory, then warps walk the rows u of
+// U_J (row-major lower) and lanes the columns c <= u of the segment.
+__global__ void __launch_bounds__(kMxThreads)
+k_mx_assemble(const AsmTask* __restrict__ tasks, const AsmSeg* __restrict__ segs,
+              const SnodeDev* __restrict__ sn, const int32_t* __restrict__ rows,
+              const float* __restrict__ U, float* __restrict__ L) {
+  extern __shared__ int32_t ssm[];
+  __shared__ int32_t tcol[kAsmCols];
+  const AsmTask t = tasks[blockIdx.x];
+  const SnodeDev dk = sn[t.K];
+  int32_t* sK = ssm;
+  int32_t* pos = ssm + dk.len;
+  const int32_t* rk = rows + dk.roff;
+  for (int i = threadIdx.x; i < dk.len; i += blockDim.x) sK[i] = rk[i];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  constexpr int nwarps = kMxThreads / 32;
+  for (int g = t.seg_begin; g < t.seg_end; ++g) {
+    const AsmSeg sg = segs[g];
+    const SnodeDev dj = sn[sg.J];
+    const int b = dj.len - dj.s;
+    const int ldu = (b + 7) & ~7;
+    const int32_t* rj = rows + dj.roff + dj.s;
+    __syncthreads();
+    for (int u = sg.ca + threadIdx.x; u < b; u += blockDim.x) {
+      const int32_t key = rj[u];
+      int lo = t.t0, hi = dk.len;
+      while (lo < hi) {
+        const int mid = (lo + hi) >> 1;
+        if (sK[mid] < key) lo = mid + 1; else hi = mid;
+      }
+      pos[u - sg.ca] = lo;
+    }
+    for (int c = sg.ca + threadIdx.x; c < sg.cb; c += blockDim.x) tcol[c - sg.ca] = rj[c] - dk.f;
+    __syncthreads();
+    const float* Uj = U + dj.uoff;
+    for (int u = sg.ca + warp; u < b; u += nwarps) {
+      float* Lr = L + dk.loff + (int64_t)pos[u - sg.ca] * dk.ld;
+      const float* Ur = Uj + (int64_t)u * ldu;
+      const int cend = min(sg.cb, u + 1);
+      for (int c = sg.ca + lane; c < cend; c += 32) Lr[tcol[c - sg.ca]] -= Ur[c];
+    }
+  }
+}
+
+// log det: per-supernode partial sums of log(L~_jj) - log(d_j) (A = D^-1 A~ D^-1).
+__global__ void k_mx_logdet_part(const SnodeDev* __restrict__ sn, const float* __restrict__ L,
+                                 const double* __restrict__ dsc, double* __restrict__ part) {
+  __shared__ double red[128];
+  const SnodeDev d = sn[blockIdx.x];
+  double acc = 0.0;
+  for (int c = threadIdx.x; c < d.s; c += blockDim.x)
+    acc += log((double)L[d.loff + (int64_t)c * d.ld + c]) - log(dsc[d.f + c]);
+  red[threadIdx.x] = acc;
+  __syncthreads();
+  for (int w = blockDim.x / 2; w > 0; w >>= 1) {
+    if (threadIdx.x < w) red[threadIdx.x] += red[threadIdx.x + w];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) part[blockIdx.x] = red[0];
+}
+
+__global__ void k_mx_logdet_reduce(const double* __restrict__ part, int ns, double* out) {
+  __shared__ double red[1024];
+  double acc = 0.0;
+  for (int i = threadIdx.x; i < ns; i += blockDim.x) acc += part[i];
+  red[threadIdx.x] = acc;
+  __syncthreads();
+  for (int w = blockDim.x / 2; w > 0; w >>= 1) {
+    if (threadIdx.x < w) red[threadIdx.x] += red[threadIdx.x + w];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) *out = 2.0 * red[0];
+}
+
+// L = D^{-1} L~ in compressed sparse column order: out[t] = L~[map[t]] / d[row(t)].
+__global__ void k_mx_gather(const float* __restrict__ L, const int64_t* __restrict__ map,
+                            const int32_t* __restrict__ lrow, const double* __restrict__ dsc, int64_t nnz,
+                            double* __restrict__ out) {
+  for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < nnz; t += (int64_t)gridDim.x * blockDim.x)
+    out[t] = (double)L[map[t]] / dsc[lrow[t]];
+}
+
+__global__ void k_mx_gather_vals(const double* __restrict__ vals, const int64_t* __restrict__ src, int64_t m,
+                                 double* __restrict__ out) {
+  for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < m; t += (int64_t)gridDim.x * blockDim.x)
+    out[t] = vals[src[t]];
+}
+
+inline unsigned grid1d(int64_t n, int threads) {
+  int64_t g = (n + threads - 1) / threads;
+  if (g > 152 * 32) g = 152 * 32;
+  return (unsigned)(g > 0 ? g : 1);
+}
+
+template <class T>
+int upload_vec(chol_handle* h, T** dst, const std::vector<T>& v) {
+  if (v.empty()) { *dst = nullptr; return CHOL_OK; }
+  int rc = chol_dalloc(h, (void**)dst, v.size() * sizeof(T));
+  if (rc) return rc;
+  CHOL_CUDA_TRY(cudaMemcpy(*dst, v.data(), v.size() * sizeof(T), cudaMemcpyHostToDevice));
+  return CHOL_OK;
+}
+
+}  // namespace
+
+// Device buffers of the mixed modes (allocated once, by the first factor).
+int chol_mixed_ensure(chol_handle* h) {
+  DeviceState* D = h->dev;
+  if (D->mx_ready) return CHOL_OK;
+  int rc;
+  std::vector<int64_t> diagpos(h->n);
+  // diagonal of P A P^T at permuted i is A's diagonal of column perm[i]: the
+  // first entry of that column (validated by chol_analyze)
+  for (int32_t i = 0; i < h->n; ++i) diagpos[i] = h->diagpos_orig[h->perm[i]];
+  if ((rc = upload_vec(h, &D->mx_diagpos, diagpos))) return rc;
+  if ((rc = upload_vec(h, &D->mx_aij, h->aij))) return rc;
+  if ((rc = chol_dalloc(h, (void**)&D->mx_d, sizeof(double) * (size_t)std::max(h->n, 1)))) return rc;
+  if ((rc = chol_dalloc(h, (void**)&D->mx_fallbacks, 2 * sizeof(int32_t)))) return rc;
+  if ((rc = chol_tc_prepare(h))) return rc;
+  if (cudaFuncSetAttribute(k_mx_assemble, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024) != cudaSuccess)
+    return CHOL_ECUDA;
+  D->mx_ready = true;
+  return CHOL_OK;
+}
+
+int chol_factor_mixed(chol_handle* h, const double* values, cudaStream_t st) {
+  int rc = chol_mixed_ensure(h);
+  if (rc) return rc;
+  DeviceState* D = h->dev;
+  float* L = (float*)D->L;
+  float* U = (float*)D->U;
+  const int nb = h->opt.block_cols;
+  const bool tc = h->opt.precision == CHOL_PREC_TF32 || h->opt.precision == CHOL_PREC_BF16;
+  h->factored = false;
+  chol_status_init(D->status, st);
+  CHOL_CUDA_TRY(cudaMemsetAsync(D->mx_fallbacks, 0, 2 * sizeof(int32_t), st));
+  const float spiv = h->opt.static_pivot ? (float)h->opt.pivot_tau : 0.f;
+  CHOL_CUDA_TRY(cudaMemsetAsync(L, 0, sizeof(float) * (size_t)h->panel_doubles, st));
+  if (h->n > 0) {
+    KScope ks(h, CHOL_K_SCATTER, st, 0.0, 16.0 * h->n);
+    k_mx_scale<<<grid1d(h->n, 256), 256, 0, st>>>(values, D->mx_diagpos, h->n, D->mx_d);
+  }
+  if (h->nnz_a > 0) {
+    KScope ks(h, CHOL_K_SCATTER, st, 0.0, 28.0 * (double)h->nnz_a);
+    k_mx_scatter<<<grid1d(h->nnz_a, 256), 256, 0, st>>>(values, D->amap, D->mx_aij, D->mx_d, h->nnz_a, L);
+    const int64_t m = h->csr_ptr[h->n];
+    k_mx_gather_vals<<<grid1d(m, 256), 256, 0, st>>>(values, D->csr_src, m, D->csr_val);
+  }
+  for (const LevelPlan& P : h->levels) {
+    if (P.small_n > 0) {
+      KScope ks(h, CHOL_K_SMALL, st, P.small_flops, P.small_bytes / 2);
+      k_mx_small<<<P.small_n, 128, sizeof(float) * P.small_max_panel, st>>>(D->sn, D->small_list + P.small_b, L, U,
+                                                                              D->status, spiv, D->mx_fallbacks);
+    }
+    for (size_t k = 0; k < P.steps.size(); ++k) {
+      const StepRange& s = P.steps[k];
+      const int k0 = (int)k * nb;
+      if (s.potrf_n > 0) {
+        KScope ks(h, CHOL_K_POTRF, st, s.potrf_flops, 8.0 * nb * nb * s.potrf_n);
+        k_mx_potrf<<<s.potrf_n, 256, 0, st>>>(D->sn, D->potrf_list + s.potrf_b, k0, nb, (float)h->opt.pivot_tau,
+                                              h->opt.static_pivot, L, D->status, D->mx_fallbacks);
+      }
+      if (s.trsm_n > 0) {
+        KScope ks(h, CHOL_K_TRSM, st, s.trsm_flops, 8.0 * kTrsmRowsHost * nb * s.trsm_n);
+        k_mx_trsm<<<s.trsm_n, 256, 0, st>>>(D->sn, D->trsm + s.trsm_b, nb, L,
+                                            (__nv_bfloat16*)(h->opt.precision == CHOL_PREC_BF16 ? D->Lbf : nullptr));
+      }
+      if (s.gemm_n > 0) {
+        KScope ks(h, CHOL_K_GEMM, st, s.gemm_flops, 0.0);
+        if (tc) {
+          if ((rc = chol_tc_gemm(h, D->gemm + s.gemm_b, s.gemm_n, k0, nb, st))) return rc;
+        } else {
+          k_mx_gemm_simt<<<s.gemm_n, 256, 0, st>>>(D->sn, D->gemm + s.gemm_b, nb, L);
+        }
+      }
+    }
+    if (P.syrk_n > 0) {
+      KScope ks(h, CHOL_K_SYRK, st, P.syrk_flops, 0.0);
+      if (tc) {
+        if ((rc = chol_tc_syrk(h, D->syrk + P.syrk_b, P.syrk_n, st))) return rc;
+      } else {
+        k_mx_syrk_simt<<<P.syrk_n, 256, 0, st>>>(D->sn, D->syrk + P.syrk_b, L, U);
+      }
+    }
+    if (P.asm_n > 0) {
+      KScope ks(h, CHOL_K_ASSEMBLE, st, P.asm_entries, 12.0 * P.asm_entries);
+      k_mx_assemble<<<P.asm_n, kMxThreads, sizeof(int32_t) * 2 * h->max_len, st>>>(
+          D->asm_tasks + P.asm_b, D->asm_segs, D->sn, D->rows, U, L);
+    }
+  }
+  CHOL_CUDA_TRY(cudaGetLastError());
+  int32_t fb = 0;
+  CHOL_CUDA_TRY(cudaMemcpyAsync(D->status_host, D->status, sizeof(int32_t), cudaMemcpyDeviceToHost, st));
+  CHOL_CUDA_TRY(cudaMemcpyAsync(&D->status_host[1], D->mx_fallbacks, 2 * sizeof(int32_t), cudaMemcpyDeviceToHost, st));
+  CHOL_CUDA_TRY(cudaStreamSynchronize(st));
+  fb = D->status_host[1];
+  h->fp64_fallbacks = fb;
+  h->perturbed_pivots = D->status_host[2];
+  const int32_t s = D->status_host[0];
+  if (s != INT_MAX) return s;
+  if ((rc = chol_tc_status(h))) return rc;
+  h->factored = true;
+  return CHOL_OK;
+}
+
+int chol_logdet_mixed(chol_handle* h, double* out, cudaStream_t st) {
+  DeviceState* D = h->dev;
+  if (h->ns > 0) {
+    KScope ks(h, CHOL_K_LOGDET, st, (double)h->n, 4.0 * h->n);
+    k_mx_logdet_part<<<h->ns, 128, 0, st>>>(D->sn, (const float*)D->L, D->mx_d, D->part);
+    k_mx_logdet_reduce<<<1, 1024, 0, st>>>(D->part, h->ns, D->scalar_dev);
+  } else {
+    CHOL_CUDA_TRY(cudaMemsetAsync(D->scalar_dev, 0, sizeof(double), st));
+  }
+  CHOL_CUDA_TRY(cudaGetLastError());
+  CHOL_CUDA_TRY(cudaMemcpyAsync(D->scalar_host, D->scalar_dev, sizeof(double), cudaMemcpyDeviceToHost, st));
+  CHOL_CUDA_TRY(cudaStreamSynchronize(st));
+  *out = *D->scalar_host;
+  return CHOL_OK;
+}
+
+// Gather L = D^{-1} L~ (binary64) in canonical CSC order (map built by the caller).
+int chol_gather_mixed(chol_handle* h, const int64_t* dmap, const int32_t* dlrow, double* dlx, cudaStream_t st) {
+  DeviceState* D = h->dev;
+  k_mx_gather<<<grid1d(h->nnz_l, 256), 256, 0, st>>>((const float*)D->L, dmap, dlrow, D->mx_d, h->nnz_l, dlx);
+  CHOL_CUDA_TRY(cudaGetLastError());
+  return CHOL_OK;
+}

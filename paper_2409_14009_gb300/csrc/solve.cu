@@ -16,6 +16,7 @@
 #include <mutex>
 
 #include "device.h"
+#include "mixed.h"
 
 namespace {
 
@@ -278,6 +279,7 @@ extern "C" int chol_solve(chol_handle* h, double* b, int32_t nrhs, void* stream)
   if (nrhs < 0) return -3;
   if (!h->factored) return CHOL_ESTATE;
   if (nrhs == 0 || h->n == 0) return CHOL_OK;
+  if (h->opt.precision != CHOL_PREC_FP64) return chol_solve_mixed(h, b, nrhs, (cudaStream_t)stream);
   int rc = ensure_solve_ws(h);
   if (rc) return rc;
   DeviceState* D = h->dev;
@@ -404,6 +406,7 @@ extern "C" int chol_solve_noalloc(chol_handle* h, double* b, int32_t nrhs, void*
   const int64_t per_col = (int64_t)h->n + h->w_rows_max;
   if (per_col > kNoAllocScratchDoubles) return CHOL_ETOOBIG;
   if (!h->factored || !h->dev) return CHOL_ESTATE;
+  if (h->opt.precision != CHOL_PREC_FP64) return CHOL_ENOTSUP;
   if (nrhs == 0 || h->n == 0) return CHOL_OK;
   double* scratch = nullptr;
   int rc = noalloc_scratch(&scratch);
