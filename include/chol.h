@@ -86,10 +86,11 @@ typedef struct chol_options {
   double pivot_tau;        /* mixed modes: a diagonal block with a binary32 pivot */
                            /* L_jj^2 below this (scaled matrix) is refactored in  */
                            /* binary64; default 1e-3                              */
-  int32_t static_pivot;    /* mixed modes: 1 = a pivot still below pivot_tau after */
-                           /* the binary64 redo is raised to pivot_tau (counted),  */
-                           /* leaving the correction to chol_solve_refine; 0 =    */
-                           /* report it as not positive definite (default)        */
+  int32_t static_pivot;    /* mixed modes: 1 = a pivot d still below pivot_tau   */
+                           /* after the binary64 redo becomes max(|d|, pivot_tau)  */
+                           /* (counted), leaving the correction to               */
+                           /* chol_solve_refine; 0 = report it as not positive   */
+                           /* definite (default)                                 */
   int32_t reserved2;
 } chol_options;
 
@@ -261,7 +262,7 @@ int chol_get_factor(chol_handle* h, int64_t* lp, int32_t* li, double* lx, void* 
 enum chol_kernel_class {
   CHOL_K_SCATTER = 0, CHOL_K_SMALL, CHOL_K_POTRF, CHOL_K_TRSM, CHOL_K_GEMM, CHOL_K_SYRK,
   CHOL_K_ASSEMBLE, CHOL_K_SOLVE_DIAG, CHOL_K_SOLVE_FUPD, CHOL_K_SOLVE_FASM, CHOL_K_SOLVE_BPANEL,
-  CHOL_K_SOLVE_BUPD, CHOL_K_PERMUTE, CHOL_K_LOGDET, CHOL_K_NCLASSES
+  CHOL_K_SOLVE_BUPD, CHOL_K_PERMUTE, CHOL_K_LOGDET, CHOL_K_SOLVE_GEMV, CHOL_K_NCLASSES
 };
 
 typedef struct chol_kernel_stat {

@@ -35,7 +35,8 @@ EXPORTED = ["chol_default_options", "chol_analyze", "chol_factor", "chol_solve",
             "chol_get_stats", "chol_destroy", "chol_strerror"]
 
 KERNEL_CLASSES = ["scatter", "small", "potrf", "trsm", "gemm", "syrk", "assemble", "solve_diag",
-                  "solve_fupd", "solve_fasm", "solve_bpanel", "solve_bupd", "permute", "logdet"]
+                  "solve_fupd", "solve_fasm", "solve_bpanel", "solve_bupd", "permute", "logdet",
+                  "solve_gemv"]
 
 
 class chol_options(C.Structure):

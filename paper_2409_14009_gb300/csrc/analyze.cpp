@@ -405,6 +405,10 @@ void build(chol_handle* h, const int64_t* colptr, const int32_t* rowind) {
     h->relind_len += (h->snodes[h->rel_J[p]].len - h->snodes[h->rel_J[p]].s) - h->rel_c0[p];
   // ---- level schedule and task lists ----
   const int nb = h->opt.block_cols;
+  // solve super-step: one CTA solves this many diagonal columns. Binary64 keeps
+  // it at one 64-column block (a single SM's FP64 rate is the limit); binary32
+  // takes 256 to cut the number of dependent launches.
+  h->solve_sb = h->opt.precision == CHOL_PREC_FP64 ? 64 : kSolveSB;
   const int tg = (h->opt.precision == CHOL_PREC_TF32 || h->opt.precision == CHOL_PREC_BF16) ? kTileTC : kTile;
   std::vector<std::vector<int32_t>> by_level(h->nlevels);
   for (int32_t J = 0; J < ns; ++J) by_level[h->level[J]].push_back(J);
@@ -415,6 +419,7 @@ void build(chol_handle* h, const int64_t* colptr, const int32_t* rowind) {
   h->level_snodes.clear(); h->small_list.clear(); h->potrf_list.clear();
   h->trsm_tasks.clear(); h->gemm_tasks.clear(); h->syrk_tasks.clear();
   h->bpanel_tasks.clear(); h->sdiag_list.clear(); h->fupd_tasks.clear(); h->bupd_tasks.clear();
+  h->gemv_tasks.clear();
   h->asm_tasks.clear(); h->asm_segs.clear();
   h->n_small = h->n_large = 0;
   h->update_doubles = 0;
@@ -495,10 +500,14 @@ void build(chol_handle* h, const int64_t* colptr, const int32_t* rowind) {
         for (int32_t r0 = c0; r0 < b; r0 += tg) h->syrk_tasks.push_back({J, 0, r0, c0});
     }
     P.syrk_n = (int32_t)h->syrk_tasks.size() - P.syrk_b;
-    // blocked triangular solves over every supernode of the level
+    // blocked triangular solves over every supernode of the level: super-steps of
+    // kSolveSB columns (diagonal triangle in one CTA + updates of the rows of the
+    // diagonal block below it / of the column blocks left of it), then one panel
+    // product per level for the off-diagonal rows
     int32_t maxs_all = 0;
     for (int32_t J : Js) maxs_all = std::max(maxs_all, h->snodes[J].s);
-    for (int32_t k0 = 0; k0 < maxs_all; k0 += nb) {
+    const int32_t sb = h->solve_sb;
+    for (int32_t k0 = 0; k0 < maxs_all; k0 += sb) {
       SolveStep st{};
       st.diag_b = (int32_t)h->sdiag_list.size();
       st.fupd_b = (int32_t)h->fupd_tasks.size();
@@ -506,22 +515,28 @@ void build(chol_handle* h, const int64_t* colptr, const int32_t* rowind) {
       for (int32_t J : Js) {
         const SnodeDev& d = h->snodes[J];
         if (d.s <= k0) continue;
-        int32_t kb = std::min(nb, d.s - k0);
+        const int32_t sbk = std::min(sb, d.s - k0);
         h->sdiag_list.push_back(J);
-        for (int32_t r0 = k0 + kb; r0 < d.len; r0 += kTile) h->fupd_tasks.push_back({J, k0, r0, 0});
-        for (int32_t c0 = 0; c0 < k0; c0 += kTile) h->bupd_tasks.push_back({J, k0, 0, c0});
+        for (int32_t r0 = k0 + sbk; r0 < d.s; r0 += kSolveTileRows) h->fupd_tasks.push_back({J, k0, r0, 0});
+        for (int32_t c0 = 0; c0 < k0; c0 += kSolveTileRows) h->bupd_tasks.push_back({J, k0, 0, c0});
       }
       st.diag_n = (int32_t)h->sdiag_list.size() - st.diag_b;
       st.fupd_n = (int32_t)h->fupd_tasks.size() - st.fupd_b;
       st.bupd_n = (int32_t)h->bupd_tasks.size() - st.bupd_b;
       P.ssteps.push_back(st);
     }
+    const int32_t gemv_rows = h->opt.precision == CHOL_PREC_FP64 ? 64 : 32;
+    const int32_t bpanel_cols = h->opt.precision == CHOL_PREC_FP64 ? 8 : 64;
+    P.gemv_b = (int32_t)h->gemv_tasks.size();
     P.bpanel_b = (int32_t)h->bpanel_tasks.size();
     for (int32_t J : Js) {
       const SnodeDev& d = h->snodes[J];
-      if (d.len - d.s <= 0) continue;
-      for (int32_t c0 = 0; c0 < d.s; c0 += kBwdCols) h->bpanel_tasks.push_back({J, 0, 0, c0});
+      const int32_t b = d.len - d.s;
+      if (b <= 0) continue;
+      for (int32_t r0 = 0; r0 < b; r0 += gemv_rows) h->gemv_tasks.push_back({J, 0, r0, 0});
+      for (int32_t c0 = 0; c0 < d.s; c0 += bpanel_cols) h->bpanel_tasks.push_back({J, 0, 0, c0});
     }
+    P.gemv_n = (int32_t)h->gemv_tasks.size() - P.gemv_b;
     P.bpanel_n = (int32_t)h->bpanel_tasks.size() - P.bpanel_b;
     // assembly: group this level's pairs by target K (then J ascending)
     auto& pl = pairs_by_level[lv];

@@ -28,6 +28,7 @@ struct DeviceState {
   TileTask* fupd = nullptr;
   TileTask* bupd = nullptr;
   TileTask* bpanel = nullptr;
+  TileTask* gemv = nullptr;
   int32_t* perm = nullptr;
   int32_t* status = nullptr;    // device status word (first failing column + 1)
   int32_t* status_host = nullptr;  // pinned

@@ -52,6 +52,7 @@ struct LevelPlan {
   int32_t syrk_b, syrk_n;     // U tiles (in syrk_tasks)
   int32_t asm_b, asm_n;       // assembly tasks
   std::vector<SolveStep> ssteps;
+  int32_t gemv_b, gemv_n;     // forward-solve panel products (TileTask: J, r0)
   int32_t bpanel_b, bpanel_n; // backward-solve panel column blocks (TileTask: J, c0)
   int64_t u_doubles;          // update workspace used by this level
   int64_t w_rows;             // sum of b over the level (solve workspace rows)
@@ -99,9 +100,11 @@ struct chol_handle {
   std::vector<TileTask> trsm_tasks, gemm_tasks, syrk_tasks, bpanel_tasks;
   std::vector<int32_t> sdiag_list;             // solve: supernode per (level, step)
   std::vector<TileTask> fupd_tasks, bupd_tasks; // solve: (J, k0, r0) / (J, k0, c0)
+  std::vector<TileTask> gemv_tasks;             // solve: (J, r0) off-diagonal row tiles
   std::vector<AsmTask> asm_tasks;
   std::vector<AsmSeg> asm_segs;
   int32_t n_small = 0, n_large = 0;
+  int32_t solve_sb = 256;       // solve super-step (set by the analysis)
   // numeric state
   bool factored = false;
   DeviceState* dev = nullptr;
@@ -113,6 +116,7 @@ constexpr int kTile = 64;        // SIMT GEMM/SYRK tile edge
 constexpr int kTileTC = 128;     // tensor-core (tcgen05) GEMM/SYRK tile edge
 constexpr int kAsmCols = 64;     // assembly task width (target columns)
 constexpr int kTrsmRowsHost = 32; // TRSM task height (rows)
-constexpr int kBwdCols = 8;      // backward-solve panel column block (one warp per column)
+constexpr int kSolveSB = 256;    // largest solve super-step (columns solved inside one CTA)
+constexpr int kSolveTileRows = 64;  // solve update tiles (rows / columns)
 
 void chol_device_free(chol_handle* h);  // CUDA side

@@ -50,8 +50,8 @@ __device__ void dense_chol_rowmajor(T* P, int len, int s, int fcol, int* status,
   for (int k = 0; k < s; ++k) {
     __syncthreads();
     T dv = P[k * s + k];
-    if (spiv > T(0) && !(dv >= spiv)) {      // static pivoting: raise the pivot
-      dv = spiv;
+    if (spiv > T(0) && !(dv >= spiv)) {      // static pivoting: max(|d|, tau)
+      dv = fabs(dv) >= spiv ? T(fabs(dv)) : spiv;
       if (threadIdx.x == 0) atomicAdd(nperturbed, 1);
     }
     const bool bad = !(dv > T(0));
@@ -132,8 +132,8 @@ __device__ void potrf_block_regs(const float* __restrict__ G, int64_t ld, int kb
             for (int b = 0; b < 4; ++b)
               if (b == kk) dv = v[a][b];
           }
-        if (spiv > T(0) && !(dv >= spiv)) {   // static pivoting: raise the pivot
-          dv = spiv;
+        if (spiv > T(0) && !(dv >= spiv)) {   // static pivoting: max(|d|, tau)
+          dv = fabs(dv) >= spiv ? T(fabs(dv)) : spiv;
           atomicAdd(nperturbed, 1);
         }
         const bool bad = !(dv > T(0));

@@ -1,10 +1,6 @@
-// refine.cu -- the binary32 triangular solves of the mixed modes, and binary64
-// iterative refinement / preconditioned conjugate gradients around any factor.
-//
-// Mixed solve, x = A^{-1} b with A = D^{-1} L~ L~^T D^{-1}: the right-hand
-// sides are permuted, multiplied by D and divided by their max-norm, solved
-// with the binary32 factor (row-major panels, the same blocked schedule as the
-// binary64 solve), then multiplied back and returned in binary64.
+// refine.cu -- binary64 iterative refinement / preconditioned conjugate
+// gradients around any factor (the correction solves use the factor's own
+// precision: binary32 for the mixed modes, see solve.cu).
 //
 // Refinement works in binary64 on the original A (full CSR, the values of the
 // last factorization): r = b - A x, d = solve(r), x += d, until the normwise
@@ -29,10 +25,7 @@ inline unsigned grid1d(int64_t n, int threads) {
   return (unsigned)(g > 0 ? g : 1);
 }
 
-// ---- binary32 solve kernels (row-major panels) ------------------------------
-
-// per right-hand side: scale[r] = max_i |b_ir| (1 if zero); uses the ordering of
-// non-negative doubles as unsigned integers
+// per right-hand side: out[r] = max_i |b_ir| (ordering of non-negative doubles)
 __global__ void k_maxabs_cols(const double* __restrict__ b, int n, int nr, unsigned long long* __restrict__ out) {
   for (int r = 0; r < nr; ++r) {
     double m = 0.0;
@@ -40,230 +33,6 @@ __global__ void k_maxabs_cols(const double* __restrict__ b, int n, int nr, unsig
       m = fmax(m, fabs(b[i + (int64_t)r * n]));
     for (int o = 16; o > 0; o >>= 1) m = fmax(m, __shfl_xor_sync(0xffffffffu, m, o));
     if ((threadIdx.x & 31) == 0) atomicMax(out + r, (unsigned long long)__double_as_longlong(m));
-  }
-}
-
-__global__ void k_mx_permute_in(const double* __restrict__ B, const int32_t* __restrict__ perm,
-                                const double* __restrict__ d, const unsigned long long* __restrict__ scale_bits,
-                                int n, int nr, float* __restrict__ Y) {
-  const int64_t tot = (int64_t)n * nr;
-  for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < tot; q += (int64_t)gridDim.x * blockDim.x) {
-    const int r = (int)(q / n), i = (int)(q % n);
-    double s = __longlong_as_double((long long)scale_bits[r]);
-    if (!(s > 0.0)) s = 1.0;
-    Y[q] = (float)(B[perm[i] + (int64_t)r * n] * d[i] / s);
-  }
-}
-
-__global__ void k_mx_permute_out(const float* __restrict__ Y, const int32_t* __restrict__ perm,
-                                 const double* __restrict__ d, const unsigned long long* __restrict__ scale_bits,
-                                 int n, int nr, double* __restrict__ B) {
-  const int64_t tot = (int64_t)n * nr;
-  for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < tot; q += (int64_t)gridDim.x * blockDim.x) {
-    const int r = (int)(q / n), i = (int)(q % n);
-    double s = __longlong_as_double((long long)scale_bits[r]);
-    if (!(s > 0.0)) s = 1.0;
-    B[perm[i] + (int64_t)r * n] = (double)Y[q] * d[i] * s;
-  }
-}
-
-template <bool TRANS>
-__global__ void __launch_bounds__(kT)
-k_mx_diag(const SnodeDev* __restrict__ sn, const int32_t* __restrict__ list, int k0, int nb,
-          const float* __restrict__ L, float* __restrict__ Y, int n, int nrhs) {
-  __shared__ float Lk[64 * 65];
-  __shared__ float inv[64];
-  const SnodeDev d = sn[list[blockIdx.x]];
-  const int kb = min(nb, d.s - k0);
-  const float* G = L + d.loff + (int64_t)k0 * d.ld + k0;
-  for (int q = threadIdx.x; q < kb * kb; q += blockDim.x) {
-    const int r = q / kb, c = q % kb;
-    Lk[r + c * 65] = G[(int64_t)r * d.ld + c];
-  }
-  __syncthreads();
-  for (int c = threadIdx.x; c < kb; c += blockDim.x) inv[c] = 1.0f / Lk[c + c * 65];
-  __syncthreads();
-  const int rr = threadIdx.x >> 4, q = threadIdx.x & 15;
-  const bool live = rr < nrhs;
-  float* Yb = Y + d.f + k0 + (int64_t)rr * n;
-  float y[4];
-#pragma unroll
-  for (int a = 0; a < 4; ++a) {
-    const int i = q + 16 * a;
-    y[a] = (live && i < kb) ? Yb[i] : 0.f;
-  }
-  if (!TRANS) {
-#pragma unroll
-    for (int ka = 0; ka < 4; ++ka)
-#pragma unroll
-      for (int kq = 0; kq < 16; ++kq) {
-        const int k = ka * 16 + kq;
-        if (k < kb) {
-          const float yk = __shfl_sync(0xffffffffu, y[ka] * inv[k], kq, 16);
-          if (q == kq) y[ka] = yk;
-#pragma unroll
-          for (int a = 0; a < 4; ++a) {
-            const int i = q + 16 * a;
-            if (i > k && i < kb) y[a] = fmaf(-Lk[i + k * 65], yk, y[a]);
-          }
-        }
-      }
-  } else {
-#pragma unroll
-    for (int ka = 3; ka >= 0; --ka)
-#pragma unroll
-      for (int kq = 15; kq >= 0; --kq) {
-        const int k = ka * 16 + kq;
-        if (k < kb) {
-          const float yk = __shfl_sync(0xffffffffu, y[ka] * inv[k], kq, 16);
-          if (q == kq) y[ka] = yk;
-#pragma unroll
-          for (int a = 0; a < 4; ++a) {
-            const int i = q + 16 * a;
-            if (i < k) y[a] = fmaf(-Lk[k + i * 65], yk, y[a]);
-          }
-        }
-      }
-  }
-  if (live) {
-#pragma unroll
-    for (int a = 0; a < 4; ++a) {
-      const int i = q + 16 * a;
-      if (i < kb) Yb[i] = y[a];
-    }
-  }
-}
-
-__global__ void __launch_bounds__(kT)
-k_mx_fwd_update(const SnodeDev* __restrict__ sn, const TileTask* __restrict__ tasks, int nb,
-                const float* __restrict__ L, float* __restrict__ Y, int n, float* __restrict__ W, int nrhs) {
-  __shared__ float yk[64 * kChunk];
-  const TileTask t = tasks[blockIdx.x];
-  const SnodeDev d = sn[t.J];
-  const int kb = min(nb, d.s - t.k0);
-  for (int q = threadIdx.x; q < kb * nrhs; q += blockDim.x) {
-    const int r = q % kb, c = q / kb;
-    yk[q] = Y[d.f + t.k0 + r + (int64_t)c * n];
-  }
-  __syncthreads();
-  const int row = threadIdx.x & 63, rg = threadIdx.x >> 6;
-  const int gr = t.r0 + row;
-  if (gr >= d.len) return;
-  const float* Lr = L + d.loff + (int64_t)gr * d.ld + t.k0;
-  float acc[kChunk / 4];
-#pragma unroll
-  for (int j = 0; j < kChunk / 4; ++j) acc[j] = 0.f;
-  for (int k = 0; k < kb; ++k) {
-    const float l = Lr[k];
-#pragma unroll
-    for (int j = 0; j < kChunk / 4; ++j) {
-      const int r = rg + 4 * j;
-      if (r < nrhs) acc[j] = fmaf(l, yk[k + r * kb], acc[j]);
-    }
-  }
-  const int b = d.len - d.s;
-#pragma unroll
-  for (int j = 0; j < kChunk / 4; ++j) {
-    const int r = rg + 4 * j;
-    if (r >= nrhs) continue;
-    if (gr < d.s) {
-      Y[d.f + gr + (int64_t)r * n] -= acc[j];
-    } else {
-      float* w = W + d.wpre * nrhs + (gr - d.s) + (int64_t)r * b;
-      *w = (t.k0 == 0) ? acc[j] : (*w + acc[j]);
-    }
-  }
-}
-
-__global__ void __launch_bounds__(kT)
-k_mx_fwd_assemble(const AsmTask* __restrict__ tasks, const AsmSeg* __restrict__ segs,
-                  const SnodeDev* __restrict__ sn, const int32_t* __restrict__ rows,
-                  const float* __restrict__ W, float* __restrict__ Y, int n, int nrhs) {
-  const AsmTask t = tasks[blockIdx.x];
-  for (int g = t.seg_begin; g < t.seg_end; ++g) {
-    const AsmSeg sg = segs[g];
-    const SnodeDev dj = sn[sg.J];
-    const int b = dj.len - dj.s;
-    const int32_t* rj = rows + dj.roff + dj.s;
-    const float* Wj = W + dj.wpre * nrhs;
-    const int ncol = sg.cb - sg.ca;
-    for (int q = threadIdx.x; q < ncol * nrhs; q += blockDim.x) {
-      const int c = sg.ca + q % ncol, r = q / ncol;
-      Y[rj[c] + (int64_t)r * n] -= Wj[c + (int64_t)r * b];
-    }
-    __syncthreads();
-  }
-}
-
-__global__ void __launch_bounds__(kT)
-k_mx_bwd_panel(const SnodeDev* __restrict__ sn, const TileTask* __restrict__ tasks,
-               const int32_t* __restrict__ rows, const float* __restrict__ L, float* __restrict__ Y, int n,
-               int nrhs) {
-  const TileTask t = tasks[blockIdx.x];
-  const SnodeDev d = sn[t.J];
-  const int b = d.len - d.s;
-  const int32_t* rj = rows + d.roff + d.s;
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int cend = min(d.s, t.c0 + kBwdCols);
-  for (int c = t.c0 + warp; c < cend; c += kT / 32) {
-    const float* Lc = L + d.loff + (int64_t)d.s * d.ld + c;
-    float acc[kChunk];
-#pragma unroll
-    for (int r = 0; r < kChunk; ++r) acc[r] = 0.f;
-    for (int u = lane; u < b; u += 32) {
-      const float l = Lc[(int64_t)u * d.ld];
-      const int32_t g = rj[u];
-#pragma unroll
-      for (int r = 0; r < kChunk; ++r)
-        if (r < nrhs) acc[r] = fmaf(l, Y[g + (int64_t)r * n], acc[r]);
-    }
-#pragma unroll
-    for (int r = 0; r < kChunk; ++r) {
-      float v = acc[r];
-      for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-      acc[r] = v;
-    }
-    if (lane < nrhs) {
-      float v = 0.f;
-#pragma unroll
-      for (int r = 0; r < kChunk; ++r)
-        if (r == lane) v = acc[r];
-      Y[d.f + c + (int64_t)lane * n] -= v;
-    }
-  }
-}
-
-__global__ void __launch_bounds__(kT)
-k_mx_bwd_update(const SnodeDev* __restrict__ sn, const TileTask* __restrict__ tasks, int nb,
-                const float* __restrict__ L, float* __restrict__ Y, int n, int nrhs) {
-  __shared__ float xk[64 * kChunk];
-  const TileTask t = tasks[blockIdx.x];
-  const SnodeDev d = sn[t.J];
-  const int kb = min(nb, d.s - t.k0);
-  for (int q = threadIdx.x; q < kb * nrhs; q += blockDim.x) {
-    const int r = q % kb, c = q / kb;
-    xk[q] = Y[d.f + t.k0 + r + (int64_t)c * n];
-  }
-  __syncthreads();
-  const int col = threadIdx.x & 63, rg = threadIdx.x >> 6;
-  const int gc = t.c0 + col;
-  if (gc >= t.k0) return;
-  const float* Lc = L + d.loff + (int64_t)t.k0 * d.ld + gc;
-  float acc[kChunk / 4];
-#pragma unroll
-  for (int j = 0; j < kChunk / 4; ++j) acc[j] = 0.f;
-  for (int k = 0; k < kb; ++k) {
-    const float l = Lc[(int64_t)k * d.ld];
-#pragma unroll
-    for (int j = 0; j < kChunk / 4; ++j) {
-      const int r = rg + 4 * j;
-      if (r < nrhs) acc[j] = fmaf(l, xk[k + r * kb], acc[j]);
-    }
-  }
-#pragma unroll
-  for (int j = 0; j < kChunk / 4; ++j) {
-    const int r = rg + 4 * j;
-    if (r < nrhs) Y[d.f + gc + (int64_t)r * n] -= acc[j];
   }
 }
 
@@ -379,76 +148,6 @@ __global__ void k_ratio(const double* __restrict__ num, const double* __restrict
 }
 
 }  // namespace
-
-// Binary32 solve with the mixed-precision factor, in place on a binary64 block.
-int chol_solve_mixed(chol_handle* h, double* b, int32_t nrhs, cudaStream_t st) {
-  DeviceState* D = h->dev;
-  const int n = h->n, nb = h->opt.block_cols;
-  if (!D->Y32) {
-    int rc = chol_dalloc(h, (void**)&D->Y32, sizeof(float) * (size_t)std::max(n, 1) * kChunk);
-    if (rc) return rc;
-    rc = chol_dalloc(h, (void**)&D->W32, sizeof(float) * (size_t)std::max<int64_t>(h->w_rows_max, 1) * kChunk);
-    if (rc) return rc;
-    rc = chol_dalloc(h, (void**)&D->rhs_scale, sizeof(double) * kChunk);
-    if (rc) return rc;
-  }
-  const float* L = (const float*)D->L;
-  unsigned long long* sc = (unsigned long long*)D->rhs_scale;
-  for (int r0 = 0; r0 < nrhs; r0 += kChunk) {
-    const int nr = std::min(kChunk, nrhs - r0);
-    double* B = b + (int64_t)r0 * n;
-    CHOL_CUDA_TRY(cudaMemsetAsync(sc, 0, sizeof(double) * kChunk, st));
-    {
-      KScope ks(h, CHOL_K_PERMUTE, st, 0.0, 8.0 * n * nr);
-      k_maxabs_cols<<<grid1d(n, 256), 256, 0, st>>>(B, n, nr, sc);
-      k_mx_permute_in<<<grid1d((int64_t)n * nr, 256), 256, 0, st>>>(B, D->perm, D->mx_d, sc, n, nr, D->Y32);
-    }
-    for (const LevelPlan& P : h->levels) {
-      for (size_t k = 0; k < P.ssteps.size(); ++k) {
-        const SolveStep& s = P.ssteps[k];
-        const int k0 = (int)k * nb;
-        if (s.diag_n > 0) {
-          KScope ks(h, CHOL_K_SOLVE_DIAG, st, 0.0, 0.0);
-          k_mx_diag<false><<<s.diag_n, kT, 0, st>>>(D->sn, D->sdiag + s.diag_b, k0, nb, L, D->Y32, n, nr);
-        }
-        if (s.fupd_n > 0) {
-          KScope ks(h, CHOL_K_SOLVE_FUPD, st, 0.0, 0.0);
-          k_mx_fwd_update<<<s.fupd_n, kT, 0, st>>>(D->sn, D->fupd + s.fupd_b, nb, L, D->Y32, n, D->W32, nr);
-        }
-      }
-      if (P.asm_n > 0) {
-        KScope ks(h, CHOL_K_SOLVE_FASM, st, 0.0, 0.0);
-        k_mx_fwd_assemble<<<P.asm_n, kT, 0, st>>>(D->asm_tasks + P.asm_b, D->asm_segs, D->sn, D->rows, D->W32,
-                                                  D->Y32, n, nr);
-      }
-    }
-    for (int lv = h->nlevels - 1; lv >= 0; --lv) {
-      const LevelPlan& P = h->levels[lv];
-      if (P.bpanel_n > 0) {
-        KScope ks(h, CHOL_K_SOLVE_BPANEL, st, 0.0, 0.0);
-        k_mx_bwd_panel<<<P.bpanel_n, kT, 0, st>>>(D->sn, D->bpanel + P.bpanel_b, D->rows, L, D->Y32, n, nr);
-      }
-      for (int k = (int)P.ssteps.size() - 1; k >= 0; --k) {
-        const SolveStep& s = P.ssteps[k];
-        const int k0 = k * nb;
-        if (s.diag_n > 0) {
-          KScope ks(h, CHOL_K_SOLVE_DIAG, st, 0.0, 0.0);
-          k_mx_diag<true><<<s.diag_n, kT, 0, st>>>(D->sn, D->sdiag + s.diag_b, k0, nb, L, D->Y32, n, nr);
-        }
-        if (s.bupd_n > 0) {
-          KScope ks(h, CHOL_K_SOLVE_BUPD, st, 0.0, 0.0);
-          k_mx_bwd_update<<<s.bupd_n, kT, 0, st>>>(D->sn, D->bupd + s.bupd_b, nb, L, D->Y32, n, nr);
-        }
-      }
-    }
-    {
-      KScope ks(h, CHOL_K_PERMUTE, st, 0.0, 12.0 * n * nr);
-      k_mx_permute_out<<<grid1d((int64_t)n * nr, 256), 256, 0, st>>>(D->Y32, D->perm, D->mx_d, sc, n, nr, B);
-    }
-  }
-  CHOL_CUDA_TRY(cudaGetLastError());
-  return CHOL_OK;
-}
 
 namespace {
 

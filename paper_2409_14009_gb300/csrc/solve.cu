@@ -1,18 +1,25 @@
 // solve.cu -- forward and backward substitution with the supernodal factor.
 //
-// X = P^T L^{-T} L^{-1} P B (the triangular factors give the solution, Sec. I).
-// Forward, levels leaves->root: per column block k of each supernode J,
-//   y_k <- L_kk^{-1} y_k                                  (k_fwd_diag)
-//   y_i -= L_ik y_k for rows i of J below the block; rows of the off-diagonal
-//   panel accumulate w_J = L_RJ y_J instead             (k_fwd_update)
-// then w_J is scatter-subtracted into the ancestors' rows of y through the same
-// pull-ordered task lists as the factor's relind assembly  (k_fwd_assemble).
-// Backward, levels root->leaves:
-//   y_J -= L_RJ^T x_R (gather of already-final ancestor rows)   (k_bwd_panel)
-//   per column block k, last to first: x_k <- L_kk^{-T} y_k      (k_bwd_diag)
-//   and y_c -= L_kc^T x_k for the column blocks c left of k       (k_bwd_update)
-// Every output entry is written by exactly one thread per launch; reductions
-// run in a fixed order, so the solve is deterministic.
+// X = P^T L^{-T} L^{-1} P B: the triangular factors give the solution (Sec. I).
+// One engine serves both storage forms:
+// - binary64, column-major panels, binary64 vectors;
+// - the mixed modes' binary32 row-major panels, binary32 vectors. Here the
+//   right-hand sides are scaled by D and by their max-norm on the way in and
+//   scaled back on the way out.
+//
+// Forward, levels leaves -> root, for every supernode J of the level:
+//   - the diagonal block, in super-steps of 256 columns. One CTA solves a
+//     256 x 256 triangle in 64-column sub-blocks (k_sv_diag); many CTAs then
+//     update the rows of the diagonal block below it (k_sv_fupd).
+//   - one panel product w_J = L_RJ y_J for the off-diagonal rows (k_sv_gemv).
+//   - w_J is scatter-subtracted into the ancestors' rows of y through the
+//     factor's pull-ordered relind task lists (k_sv_fasm).
+// Backward, levels root -> leaves:
+//   - y_J -= L_RJ^T x_R, a gather of the already final ancestor rows (k_sv_bpanel).
+//   - the transposed diagonal block, super-steps last to first: one CTA
+//     solves, then many CTAs update the column blocks to the left (k_sv_bupd).
+// Every output entry is written by exactly one thread per launch and every
+// reduction runs in a fixed order, so the solve is deterministic.
 #include <mutex>
 
 #include "device.h"
@@ -20,155 +27,303 @@
 
 namespace {
 
-constexpr int kSolveThreads = 256;
+constexpr int kT = 256;
+constexpr int kSub = 64;
 
-__global__ void k_permute_in(const double* __restrict__ B, const int32_t* __restrict__ perm, int n,
-                             int64_t ldb, int nrhs, double* __restrict__ Y) {
-  const int64_t tot = (int64_t)n * nrhs;
+inline unsigned grid1d(int64_t n, int threads) {
+  int64_t g = (n + threads - 1) / threads;
+  if (g > 152 * 32) g = 152 * 32;
+  return (unsigned)(g > 0 ? g : 1);
+}
+
+// L(r, c) of supernode d in either storage form.
+template <class T, bool RM>
+__device__ __forceinline__ T lval(const T* __restrict__ P, const SnodeDev& d, int r, int c) {
+  return RM ? P[(int64_t)r * d.ld + c] : P[r + (int64_t)c * d.ld];
+}
+
+__device__ __forceinline__ double scale_of(const unsigned long long* s, int r) {
+  if (!s) return 1.0;
+  const double v = __longlong_as_double((long long)s[r]);
+  return v > 0.0 ? v : 1.0;
+}
+
+// Y = (P B) * d / scale (d, scale optional)
+template <class T>
+__global__ void k_sv_permute_in(const double* __restrict__ B, const int32_t* __restrict__ perm,
+                                const double* __restrict__ d, const unsigned long long* __restrict__ scale, int n,
+                                int nr, T* __restrict__ Y) {
+  const int64_t tot = (int64_t)n * nr;
   for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < tot; q += (int64_t)gridDim.x * blockDim.x) {
     const int r = (int)(q / n), i = (int)(q % n);
-    Y[q] = B[perm[i] + r * ldb];
+    double v = B[perm[i] + (int64_t)r * n];
+    if (d) v = v * d[i] / scale_of(scale, r);
+    Y[q] = (T)v;
   }
 }
 
-__global__ void k_permute_out(const double* __restrict__ Y, const int32_t* __restrict__ perm, int n,
-                              int64_t ldb, int nrhs, double* __restrict__ B) {
-  const int64_t tot = (int64_t)n * nrhs;
+template <class T>
+__global__ void k_sv_permute_out(const T* __restrict__ Y, const int32_t* __restrict__ perm,
+                                 const double* __restrict__ d, const unsigned long long* __restrict__ scale, int n,
+                                 int nr, double* __restrict__ B) {
+  const int64_t tot = (int64_t)n * nr;
   for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < tot; q += (int64_t)gridDim.x * blockDim.x) {
     const int r = (int)(q / n), i = (int)(q % n);
-    B[perm[i] + r * ldb] = Y[q];
+    double v = (double)Y[q];
+    if (d) v = v * d[i] * scale_of(scale, r);
+    B[perm[i] + (int64_t)r * n] = v;
   }
 }
 
-// Triangular solve with the kb x kb (kb <= 64) diagonal block at step k0, in
-// place in Y, for up to 16 right-hand sides. Sixteen lanes share a right-hand
-// side, lane q holding rows q + 16a; the solved entry is broadcast inside the
-// 16-lane group with a shuffle (no barriers in the substitution loop).
-template <bool TRANS>
-__global__ void __launch_bounds__(kSolveThreads)
-k_diag(const SnodeDev* __restrict__ sn, const int32_t* __restrict__ list, int k0, int nb,
-       const double* __restrict__ L, double* __restrict__ Y, int n, int nrhs) {
-  __shared__ double Lk[64 * 65];
-  __shared__ double inv[64];
+// per right-hand side: out[r] = max_i |b_ir| (ordering of non-negative doubles)
+__global__ void k_sv_maxabs(const double* __restrict__ b, int n, int nr, unsigned long long* __restrict__ out) {
+  for (int r = 0; r < nr; ++r) {
+    double m = 0.0;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x)
+      m = fmax(m, fabs(b[i + (int64_t)r * n]));
+    for (int o = 16; o > 0; o >>= 1) m = fmax(m, __shfl_xor_sync(0xffffffffu, m, o));
+    if ((threadIdx.x & 31) == 0) atomicMax(out + r, (unsigned long long)__double_as_longlong(m));
+  }
+}
+
+// One CTA solves the diagonal triangle of columns [k0, k0 + sbk) (sbk <= 256)
+// of every listed supernode, in place in Y. Inside: 64-column sub-blocks; each
+// is solved with 16 lanes per right-hand side (lane q holds rows q + 16a, the
+// solved entry broadcast by shuffle), then the rows of the later (forward) or
+// earlier (transposed) sub-blocks are updated by all threads.
+template <class T, bool RM, bool TRANS>
+__global__ void __launch_bounds__(kT)
+k_sv_diag(const SnodeDev* __restrict__ sn, const int32_t* __restrict__ list, int k0, int sb,
+          const T* __restrict__ L, T* __restrict__ Y, int n, int nrhs) {
+  extern __shared__ __align__(16) unsigned char sv_smem[];
+  T* ys = reinterpret_cast<T*>(sv_smem);          // kSolveSB x nrhs
+  T* Ls = ys + kSolveSB * nrhs;                   // 64 x 65
+  T* inv = Ls + kSub * 65;                        // 64
   const SnodeDev d = sn[list[blockIdx.x]];
-  const int kb = min(nb, d.s - k0);
-  const double* G = L + d.loff + k0 + (int64_t)k0 * d.ld;
-  for (int q = threadIdx.x; q < kb * kb; q += blockDim.x) {
-    const int r = q % kb, c = q / kb;
-    Lk[r + c * 65] = G[r + (int64_t)c * d.ld];
+  const T* P = L + d.loff;
+  const int sbk = min(sb, d.s - k0);
+  for (int q = threadIdx.x; q < sbk * nrhs; q += blockDim.x) {
+    const int i = q % sbk, r = q / sbk;
+    ys[i + r * kSolveSB] = Y[d.f + k0 + i + (int64_t)r * n];
   }
-  __syncthreads();
-  for (int c = threadIdx.x; c < kb; c += blockDim.x) inv[c] = 1.0 / Lk[c + c * 65];
-  __syncthreads();
+  const int nsub = (sbk + kSub - 1) / kSub;
   const int rr = threadIdx.x >> 4, q = threadIdx.x & 15;
   const bool live = rr < nrhs;
-  double* Yb = Y + d.f + k0 + (int64_t)rr * n;
-  double y[4];
-#pragma unroll
-  for (int a = 0; a < 4; ++a) {
-    const int i = q + 16 * a;
-    y[a] = (live && i < kb) ? Yb[i] : 0.0;
-  }
-  if (!TRANS) {
-#pragma unroll
-    for (int ka = 0; ka < 4; ++ka) {
-#pragma unroll
-      for (int kq = 0; kq < 16; ++kq) {
-        const int k = ka * 16 + kq;
-        if (k < kb) {
-          const double yk = __shfl_sync(0xffffffffu, y[ka] * inv[k], kq, 16);
-          if (q == kq) y[ka] = yk;
-#pragma unroll
-          for (int a = 0; a < 4; ++a) {
-            const int i = q + 16 * a;
-            if (i > k && i < kb) y[a] -= Lk[i + k * 65] * yk;
-          }
-        }
-      }
+  for (int t = 0; t < nsub; ++t) {
+    const int sub = TRANS ? nsub - 1 - t : t;
+    const int s0 = sub * kSub, kb = min(kSub, sbk - s0);
+    __syncthreads();
+    for (int e = threadIdx.x; e < kb * kb; e += blockDim.x) {
+      const int r = e % kb, c = e / kb;
+      Ls[r + c * 65] = lval<T, RM>(P, d, k0 + s0 + r, k0 + s0 + c);
     }
-  } else {
-#pragma unroll
-    for (int ka = 3; ka >= 0; --ka) {
-#pragma unroll
-      for (int kq = 15; kq >= 0; --kq) {
-        const int k = ka * 16 + kq;
-        if (k < kb) {
-          const double yk = __shfl_sync(0xffffffffu, y[ka] * inv[k], kq, 16);
-          if (q == kq) y[ka] = yk;
-#pragma unroll
-          for (int a = 0; a < 4; ++a) {
-            const int i = q + 16 * a;
-            if (i < k) y[a] -= Lk[k + i * 65] * yk;
-          }
-        }
-      }
-    }
-  }
-  if (live) {
+    __syncthreads();
+    for (int c = threadIdx.x; c < kb; c += blockDim.x) inv[c] = T(1) / Ls[c + c * 65];
+    __syncthreads();
+    T y[4];
 #pragma unroll
     for (int a = 0; a < 4; ++a) {
       const int i = q + 16 * a;
-      if (i < kb) Yb[i] = y[a];
+      y[a] = (live && i < kb) ? ys[s0 + i + rr * kSolveSB] : T(0);
     }
+    if (!TRANS) {
+#pragma unroll
+      for (int ka = 0; ka < 4; ++ka)
+#pragma unroll
+        for (int kq = 0; kq < 16; ++kq) {
+          const int k = ka * 16 + kq;
+          if (k < kb) {
+            const T yk = __shfl_sync(0xffffffffu, y[ka] * inv[k], kq, 16);
+            if (q == kq) y[ka] = yk;
+#pragma unroll
+            for (int a = 0; a < 4; ++a) {
+              const int i = q + 16 * a;
+              if (i > k && i < kb) y[a] -= Ls[i + k * 65] * yk;
+            }
+          }
+        }
+    } else {
+#pragma unroll
+      for (int ka = 3; ka >= 0; --ka)
+#pragma unroll
+        for (int kq = 15; kq >= 0; --kq) {
+          const int k = ka * 16 + kq;
+          if (k < kb) {
+            const T yk = __shfl_sync(0xffffffffu, y[ka] * inv[k], kq, 16);
+            if (q == kq) y[ka] = yk;
+#pragma unroll
+            for (int a = 0; a < 4; ++a) {
+              const int i = q + 16 * a;
+              if (i < k) y[a] -= Ls[k + i * 65] * yk;
+            }
+          }
+        }
+    }
+    if (live) {
+#pragma unroll
+      for (int a = 0; a < 4; ++a) {
+        const int i = q + 16 * a;
+        if (i < kb) ys[s0 + i + rr * kSolveSB] = y[a];
+      }
+    }
+    __syncthreads();
+    // update the rest of the super-block with the solved sub-block
+    const int lo = TRANS ? 0 : s0 + kb, hi = TRANS ? s0 : sbk;
+    const int cnt = hi - lo;
+    for (int e = threadIdx.x; e < cnt * nrhs; e += blockDim.x) {
+      const int i = lo + e % cnt, r = e / cnt;
+      T acc = T(0);
+      for (int k = 0; k < kb; ++k) {
+        const T l = TRANS ? lval<T, RM>(P, d, k0 + s0 + k, k0 + i) : lval<T, RM>(P, d, k0 + i, k0 + s0 + k);
+        acc += l * ys[s0 + k + r * kSolveSB];
+      }
+      ys[i + r * kSolveSB] -= acc;
+    }
+  }
+  __syncthreads();
+  for (int e = threadIdx.x; e < sbk * nrhs; e += blockDim.x) {
+    const int i = e % sbk, r = e / sbk;
+    Y[d.f + k0 + i + (int64_t)r * n] = ys[i + r * kSolveSB];
   }
 }
 
-// Forward update below the diagonal block of step k0, rows [r0, r0+64):
-// acc = L[rows, k0:k0+kb] y_k; rows < s update y, rows >= s build w_J.
-__global__ void __launch_bounds__(kSolveThreads)
-k_fwd_update(const SnodeDev* __restrict__ sn, const TileTask* __restrict__ tasks, int nb,
-             const double* __restrict__ L, double* __restrict__ Y, int n, double* __restrict__ W,
-             int nrhs) {
-  __shared__ double yk[64 * kSolveChunk];
+// Forward update inside the diagonal block: rows [r0, r0 + 64) (all < s) of J
+// minus L[rows, k0:k0+sbk] y[k0:k0+sbk]; 64 rows x 4 right-hand-side groups.
+template <class T, bool RM>
+__global__ void __launch_bounds__(kT)
+k_sv_fupd(const SnodeDev* __restrict__ sn, const TileTask* __restrict__ tasks, int sb, const T* __restrict__ L,
+          T* __restrict__ Y, int n, int nrhs) {
+  extern __shared__ __align__(16) unsigned char sv_smem[];
+  T* yk = reinterpret_cast<T*>(sv_smem);          // kSolveSB x nrhs
   const TileTask t = tasks[blockIdx.x];
   const SnodeDev d = sn[t.J];
-  const int kb = min(nb, d.s - t.k0);
-  for (int q = threadIdx.x; q < kb * nrhs; q += blockDim.x) {
-    const int r = q % kb, c = q / kb;
-    yk[q] = Y[d.f + t.k0 + r + (int64_t)c * n];
+  const int sbk = min(sb, d.s - t.k0);
+  for (int q = threadIdx.x; q < sbk * nrhs; q += blockDim.x) {
+    const int i = q % sbk, r = q / sbk;
+    yk[i + r * kSolveSB] = Y[d.f + t.k0 + i + (int64_t)r * n];
   }
   __syncthreads();
-  const int row = threadIdx.x & 63, rg = threadIdx.x >> 6;   // 4 rhs groups
+  const int row = threadIdx.x & 63, rg = threadIdx.x >> 6;
   const int gr = t.r0 + row;
-  if (gr >= d.len) return;
-  const double* Lr = L + d.loff + gr + (int64_t)t.k0 * d.ld;
-  double acc[kSolveChunk / 4];
+  if (gr >= d.s) return;
+  const T* P = L + d.loff;
+  T acc[kSolveChunk / 4];
 #pragma unroll
-  for (int j = 0; j < kSolveChunk / 4; ++j) acc[j] = 0.0;
-  for (int k = 0; k < kb; ++k) {
-    const double l = Lr[(int64_t)k * d.ld];
+  for (int j = 0; j < kSolveChunk / 4; ++j) acc[j] = T(0);
+  for (int k = 0; k < sbk; ++k) {
+    const T l = lval<T, RM>(P, d, gr, t.k0 + k);
 #pragma unroll
     for (int j = 0; j < kSolveChunk / 4; ++j) {
       const int r = rg + 4 * j;
-      if (r < nrhs) acc[j] = fma(l, yk[k + r * kb], acc[j]);
+      if (r < nrhs) acc[j] += l * yk[k + r * kSolveSB];
     }
   }
-  const int b = d.len - d.s;
 #pragma unroll
   for (int j = 0; j < kSolveChunk / 4; ++j) {
     const int r = rg + 4 * j;
-    if (r >= nrhs) continue;
-    if (gr < d.s) {
-      Y[d.f + gr + (int64_t)r * n] -= acc[j];
-    } else {
-      double* w = W + d.wpre * nrhs + (gr - d.s) + (int64_t)r * b;
-      *w = (t.k0 == 0) ? acc[j] : (*w + acc[j]);
+    if (r < nrhs) Y[d.f + gr + (int64_t)r * n] -= acc[j];
+  }
+}
+
+// Panel product w_J = L_RJ y_J for the off-diagonal rows [r0, r0 + kGemvRows)
+// of J. Column-major: 64 rows, a thread per (row, right-hand-side group), K
+// walked in chunks staged in shared memory. Row-major: 32 rows, a warp per 4
+// rows, lanes along K, fixed-order shuffle reduction.
+template <class T, bool RM>
+__global__ void __launch_bounds__(kT)
+k_sv_gemv(const SnodeDev* __restrict__ sn, const TileTask* __restrict__ tasks, const T* __restrict__ L,
+          const T* __restrict__ Y, int n, T* __restrict__ W, int nrhs) {
+  constexpr int KC = 256;
+  __shared__ T yk[KC * kSolveChunk];
+  const TileTask t = tasks[blockIdx.x];
+  const SnodeDev d = sn[t.J];
+  const int b = d.len - d.s;
+  const T* P = L + d.loff;
+  T* Wj = W + d.wpre * nrhs;
+  if constexpr (!RM) {
+    const int row = threadIdx.x & 63, rg = threadIdx.x >> 6;
+    const int u = t.r0 + row;
+    T acc[kSolveChunk / 4];
+#pragma unroll
+    for (int j = 0; j < kSolveChunk / 4; ++j) acc[j] = T(0);
+    for (int kc = 0; kc < d.s; kc += KC) {
+      const int kn = min(KC, d.s - kc);
+      __syncthreads();
+      for (int q = threadIdx.x; q < kn * nrhs; q += blockDim.x) {
+        const int i = q % kn, r = q / kn;
+        yk[i + r * KC] = Y[d.f + kc + i + (int64_t)r * n];
+      }
+      __syncthreads();
+      if (u < b) {
+        for (int k = 0; k < kn; ++k) {
+          const T l = lval<T, RM>(P, d, d.s + u, kc + k);
+#pragma unroll
+          for (int j = 0; j < kSolveChunk / 4; ++j) {
+            const int r = rg + 4 * j;
+            if (r < nrhs) acc[j] += l * yk[k + r * KC];
+          }
+        }
+      }
+    }
+    if (u < b) {
+#pragma unroll
+      for (int j = 0; j < kSolveChunk / 4; ++j) {
+        const int r = rg + 4 * j;
+        if (r < nrhs) Wj[u + (int64_t)r * b] = acc[j];
+      }
+    }
+  } else {
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    T acc[4][kSolveChunk];   // 4 rows per warp, 32 rows per task
+#pragma unroll
+    for (int m = 0; m < 4; ++m)
+#pragma unroll
+      for (int r = 0; r < kSolveChunk; ++r) acc[m][r] = T(0);
+    for (int kc = 0; kc < d.s; kc += KC) {
+      const int kn = min(KC, d.s - kc);
+      __syncthreads();
+      for (int q = threadIdx.x; q < kn * nrhs; q += blockDim.x) {
+        const int i = q % kn, r = q / kn;
+        yk[i + r * KC] = Y[d.f + kc + i + (int64_t)r * n];
+      }
+      __syncthreads();
+#pragma unroll
+      for (int m = 0; m < 4; ++m) {
+        const int u = t.r0 + warp * 4 + m;
+        if (u >= b) continue;
+        for (int k = lane; k < kn; k += 32) {
+          const T l = lval<T, RM>(P, d, d.s + u, kc + k);
+#pragma unroll
+          for (int r = 0; r < kSolveChunk; ++r)
+            if (r < nrhs) acc[m][r] += l * yk[k + r * KC];
+        }
+      }
+    }
+#pragma unroll
+    for (int m = 0; m < 4; ++m) {
+      const int u = t.r0 + warp * 4 + m;
+#pragma unroll
+      for (int r = 0; r < kSolveChunk; ++r) {
+        T v = acc[m][r];
+        for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+        if (lane == 0 && u < b && r < nrhs) Wj[u + (int64_t)r * b] = v;
+      }
     }
   }
 }
 
 // y[targets] -= w_J through the relind task lists (pull-ordered).
-__global__ void __launch_bounds__(kSolveThreads)
-k_fwd_assemble(const AsmTask* __restrict__ tasks, const AsmSeg* __restrict__ segs,
-               const SnodeDev* __restrict__ sn, const int32_t* __restrict__ rows,
-               const double* __restrict__ W, double* __restrict__ Y, int n, int nrhs) {
+template <class T>
+__global__ void __launch_bounds__(kT)
+k_sv_fasm(const AsmTask* __restrict__ tasks, const AsmSeg* __restrict__ segs, const SnodeDev* __restrict__ sn,
+          const int32_t* __restrict__ rows, const T* __restrict__ W, T* __restrict__ Y, int n, int nrhs) {
   const AsmTask t = tasks[blockIdx.x];
   for (int g = t.seg_begin; g < t.seg_end; ++g) {
     const AsmSeg sg = segs[g];
     const SnodeDev dj = sn[sg.J];
     const int b = dj.len - dj.s;
     const int32_t* rj = rows + dj.roff + dj.s;
-    const double* Wj = W + dj.wpre * nrhs;
+    const T* Wj = W + dj.wpre * nrhs;
     const int ncol = sg.cb - sg.ca;
     for (int q = threadIdx.x; q < ncol * nrhs; q += blockDim.x) {
       const int c = sg.ca + q % ncol, r = q / ncol;
@@ -178,71 +333,94 @@ k_fwd_assemble(const AsmTask* __restrict__ tasks, const AsmSeg* __restrict__ seg
   }
 }
 
-// Backward: y_J[c] -= sum_u L[s+u, c] x[rows[s+u]] for the 64 columns of a task.
-__global__ void __launch_bounds__(kSolveThreads)
-k_bwd_panel(const SnodeDev* __restrict__ sn, const TileTask* __restrict__ tasks,
-            const int32_t* __restrict__ rows, const double* __restrict__ L, double* __restrict__ Y,
-            int n, int nrhs) {
+// Backward panel: y_J[c] -= sum_u L(s+u, c) x[rows[s+u]] for the columns of a task.
+// Column-major: a warp per column (8 columns per task). Row-major: 64 columns
+// per task, a thread per (column, row group of 4), fixed-order combination.
+template <class T, bool RM>
+__global__ void __launch_bounds__(kT)
+k_sv_bpanel(const SnodeDev* __restrict__ sn, const TileTask* __restrict__ tasks, const int32_t* __restrict__ rows,
+            const T* __restrict__ L, T* __restrict__ Y, int n, int nrhs) {
   const TileTask t = tasks[blockIdx.x];
   const SnodeDev d = sn[t.J];
   const int b = d.len - d.s;
   const int32_t* rj = rows + d.roff + d.s;
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int cend = min(d.s, t.c0 + kBwdCols);
-  for (int c = t.c0 + warp; c < cend; c += kSolveThreads / 32) {
-    const double* Lc = L + d.loff + d.s + (int64_t)c * d.ld;
-    double acc[kSolveChunk];
+  const T* P = L + d.loff;
+  if constexpr (!RM) {
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int c = t.c0 + warp;
+    if (c >= d.s) return;
+    T acc[kSolveChunk];
 #pragma unroll
-    for (int r = 0; r < kSolveChunk; ++r) acc[r] = 0.0;
+    for (int r = 0; r < kSolveChunk; ++r) acc[r] = T(0);
     for (int u = lane; u < b; u += 32) {
-      const double l = Lc[u];
+      const T l = lval<T, RM>(P, d, d.s + u, c);
       const int32_t g = rj[u];
 #pragma unroll
       for (int r = 0; r < kSolveChunk; ++r)
-        if (r < nrhs) acc[r] = fma(l, Y[g + (int64_t)r * n], acc[r]);
+        if (r < nrhs) acc[r] += l * Y[g + (int64_t)r * n];
     }
 #pragma unroll
     for (int r = 0; r < kSolveChunk; ++r) {
-      double v = acc[r];
+      T v = acc[r];
       for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-      acc[r] = v;
+      if (lane == 0 && r < nrhs) Y[d.f + c + (int64_t)r * n] -= v;
     }
-    if (lane < nrhs) {
-      double v = 0.0;
+  } else {
+    __shared__ T part[4][64][kSolveChunk + 1];
+    const int col = threadIdx.x & 63, rg = threadIdx.x >> 6;
+    const int c = t.c0 + col;
+    T acc[kSolveChunk];
 #pragma unroll
-      for (int r = 0; r < kSolveChunk; ++r)
-        if (r == lane) v = acc[r];
-      Y[d.f + c + (int64_t)lane * n] -= v;
+    for (int r = 0; r < kSolveChunk; ++r) acc[r] = T(0);
+    if (c < d.s) {
+      for (int u = rg; u < b; u += 4) {
+        const T l = lval<T, RM>(P, d, d.s + u, c);
+        const int32_t g = rj[u];
+#pragma unroll
+        for (int r = 0; r < kSolveChunk; ++r)
+          if (r < nrhs) acc[r] += l * Y[g + (int64_t)r * n];
+      }
+    }
+#pragma unroll
+    for (int r = 0; r < kSolveChunk; ++r) part[rg][col][r] = acc[r];
+    __syncthreads();
+    if (rg == 0 && c < d.s) {
+      for (int r = 0; r < nrhs; ++r) {
+        const T v = ((part[0][col][r] + part[1][col][r]) + part[2][col][r]) + part[3][col][r];
+        Y[d.f + c + (int64_t)r * n] -= v;
+      }
     }
   }
 }
 
-// Backward update of step k0: y[c0..c0+64) -= L[k0:k0+kb, c0..c0+64)^T x_k.
-__global__ void __launch_bounds__(kSolveThreads)
-k_bwd_update(const SnodeDev* __restrict__ sn, const TileTask* __restrict__ tasks, int nb,
-             const double* __restrict__ L, double* __restrict__ Y, int n, int nrhs) {
-  __shared__ double xk[64 * kSolveChunk];
+// Backward update: y[c0..c0+64) -= L[k0:k0+sbk, c]^T x[k0:k0+sbk] for c < k0.
+template <class T, bool RM>
+__global__ void __launch_bounds__(kT)
+k_sv_bupd(const SnodeDev* __restrict__ sn, const TileTask* __restrict__ tasks, int sb, const T* __restrict__ L,
+          T* __restrict__ Y, int n, int nrhs) {
+  extern __shared__ __align__(16) unsigned char sv_smem[];
+  T* xk = reinterpret_cast<T*>(sv_smem);          // kSolveSB x nrhs
   const TileTask t = tasks[blockIdx.x];
   const SnodeDev d = sn[t.J];
-  const int kb = min(nb, d.s - t.k0);
-  for (int q = threadIdx.x; q < kb * nrhs; q += blockDim.x) {
-    const int r = q % kb, c = q / kb;
-    xk[q] = Y[d.f + t.k0 + r + (int64_t)c * n];
+  const int sbk = min(sb, d.s - t.k0);
+  for (int q = threadIdx.x; q < sbk * nrhs; q += blockDim.x) {
+    const int i = q % sbk, r = q / sbk;
+    xk[i + r * kSolveSB] = Y[d.f + t.k0 + i + (int64_t)r * n];
   }
   __syncthreads();
   const int col = threadIdx.x & 63, rg = threadIdx.x >> 6;
   const int gc = t.c0 + col;
-  if (gc >= t.k0) return;               // only the column blocks left of step k0
-  const double* Lc = L + d.loff + t.k0 + (int64_t)gc * d.ld;
-  double acc[kSolveChunk / 4];
+  if (gc >= t.k0) return;
+  const T* P = L + d.loff;
+  T acc[kSolveChunk / 4];
 #pragma unroll
-  for (int j = 0; j < kSolveChunk / 4; ++j) acc[j] = 0.0;
-  for (int k = 0; k < kb; ++k) {
-    const double l = Lc[k];
+  for (int j = 0; j < kSolveChunk / 4; ++j) acc[j] = T(0);
+  for (int k = 0; k < sbk; ++k) {
+    const T l = lval<T, RM>(P, d, t.k0 + k, gc);
 #pragma unroll
     for (int j = 0; j < kSolveChunk / 4; ++j) {
       const int r = rg + 4 * j;
-      if (r < nrhs) acc[j] = fma(l, xk[k + r * kb], acc[j]);
+      if (r < nrhs) acc[j] += l * xk[k + r * kSolveSB];
     }
   }
 #pragma unroll
@@ -252,10 +430,98 @@ k_bwd_update(const SnodeDev* __restrict__ sn, const TileTask* __restrict__ tasks
   }
 }
 
-inline unsigned grid1d(int64_t n, int threads) {
-  int64_t g = (n + threads - 1) / threads;
-  if (g > 152 * 32) g = 152 * 32;
-  return (unsigned)(g > 0 ? g : 1);
+template <class T>
+size_t diag_smem(int nr) {
+  return sizeof(T) * ((size_t)kSolveSB * nr + kSub * 65 + kSub);
+}
+
+template <class T>
+size_t blk_smem(int nr) {
+  return sizeof(T) * (size_t)kSolveSB * nr;
+}
+
+// The level schedule of one solve on a chunk of nr <= 16 right-hand sides
+// already permuted into Y (W: per-level panel products). `prof` enables the
+// per-class launch accounting (off for the no-allocation entry point).
+template <class T, bool RM>
+void solve_levels(chol_handle* h, const T* L, T* Y, T* W, int nr, cudaStream_t st, bool prof) {
+  DeviceState* D = h->dev;
+  const int n = h->n;
+  const int sb = h->solve_sb;
+  auto scope = [&](int cls) { return prof ? new KScope(h, cls, st, 0.0, 0.0) : nullptr; };
+  for (const LevelPlan& P : h->levels) {
+    for (size_t k = 0; k < P.ssteps.size(); ++k) {
+      const SolveStep& s = P.ssteps[k];
+      const int k0 = (int)k * sb;
+      if (s.diag_n > 0) {
+        KScope* ks = scope(CHOL_K_SOLVE_DIAG);
+        k_sv_diag<T, RM, false><<<s.diag_n, kT, diag_smem<T>(nr), st>>>(D->sn, D->sdiag + s.diag_b, k0, sb, L, Y, n,
+                                                                          nr);
+        delete ks;
+      }
+      if (s.fupd_n > 0) {
+        KScope* ks = scope(CHOL_K_SOLVE_FUPD);
+        k_sv_fupd<T, RM><<<s.fupd_n, kT, blk_smem<T>(nr), st>>>(D->sn, D->fupd + s.fupd_b, sb, L, Y, n, nr);
+        delete ks;
+      }
+    }
+    if (P.gemv_n > 0) {
+      KScope* ks = scope(CHOL_K_SOLVE_GEMV);
+      k_sv_gemv<T, RM><<<P.gemv_n, kT, 0, st>>>(D->sn, D->gemv + P.gemv_b, L, Y, n, W, nr);
+      delete ks;
+    }
+    if (P.asm_n > 0) {
+      KScope* ks = scope(CHOL_K_SOLVE_FASM);
+      k_sv_fasm<T><<<P.asm_n, kT, 0, st>>>(D->asm_tasks + P.asm_b, D->asm_segs, D->sn, D->rows, W, Y, n, nr);
+      delete ks;
+    }
+  }
+  for (int lv = h->nlevels - 1; lv >= 0; --lv) {
+    const LevelPlan& P = h->levels[lv];
+    if (P.bpanel_n > 0) {
+      KScope* ks = scope(CHOL_K_SOLVE_BPANEL);
+      k_sv_bpanel<T, RM><<<P.bpanel_n, kT, 0, st>>>(D->sn, D->bpanel + P.bpanel_b, D->rows, L, Y, n, nr);
+      delete ks;
+    }
+    for (int k = (int)P.ssteps.size() - 1; k >= 0; --k) {
+      const SolveStep& s = P.ssteps[k];
+      const int k0 = k * sb;
+      if (s.diag_n > 0) {
+        KScope* ks = scope(CHOL_K_SOLVE_DIAG);
+        k_sv_diag<T, RM, true><<<s.diag_n, kT, diag_smem<T>(nr), st>>>(D->sn, D->sdiag + s.diag_b, k0, sb, L, Y, n,
+                                                                         nr);
+        delete ks;
+      }
+      if (s.bupd_n > 0) {
+        KScope* ks = scope(CHOL_K_SOLVE_BUPD);
+        k_sv_bupd<T, RM><<<s.bupd_n, kT, blk_smem<T>(nr), st>>>(D->sn, D->bupd + s.bupd_b, sb, L, Y, n, nr);
+        delete ks;
+      }
+    }
+  }
+}
+
+int set_solve_attrs() {
+  static std::once_flag once;
+  static int rc = CHOL_OK;
+  std::call_once(once, [] {
+    const size_t dd = diag_smem<double>(kSolveChunk), df = diag_smem<float>(kSolveChunk);
+    const size_t bd = blk_smem<double>(kSolveChunk), bf = blk_smem<float>(kSolveChunk);
+    cudaError_t e = cudaSuccess;
+    e = e ? e : cudaFuncSetAttribute(k_sv_diag<double, false, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dd);
+    e = e ? e : cudaFuncSetAttribute(k_sv_diag<double, false, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dd);
+    e = e ? e : cudaFuncSetAttribute(k_sv_diag<float, true, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)df);
+    e = e ? e : cudaFuncSetAttribute(k_sv_diag<float, true, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)df);
+    e = e ? e : cudaFuncSetAttribute(k_sv_fupd<double, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bd);
+    e = e ? e : cudaFuncSetAttribute(k_sv_fupd<float, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bf);
+    e = e ? e : cudaFuncSetAttribute(k_sv_bupd<double, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bd);
+    e = e ? e : cudaFuncSetAttribute(k_sv_bupd<float, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bf);
+    if (e != cudaSuccess) {
+      cudaGetLastError();
+      rc = CHOL_ECUDA;
+    }
+  });
+  return rc;
 }
 
 int ensure_solve_ws(chol_handle* h) {
@@ -271,7 +537,60 @@ int ensure_solve_ws(chol_handle* h) {
   return CHOL_OK;
 }
 
+// binary64 solve of b (n x nrhs, ld n) in place with workspaces Y, W of
+// chunk columns each
+int solve_fp64(chol_handle* h, double* b, int32_t nrhs, cudaStream_t st, double* Y, double* W, int chunk,
+               bool prof) {
+  DeviceState* D = h->dev;
+  const int n = h->n;
+  for (int r0 = 0; r0 < nrhs; r0 += chunk) {
+    const int nr = std::min(chunk, nrhs - r0);
+    double* B = b + (int64_t)r0 * n;
+    KScope* ks = prof ? new KScope(h, CHOL_K_PERMUTE, st, 0.0, 24.0 * n * nr) : nullptr;
+    k_sv_permute_in<double><<<grid1d((int64_t)n * nr, 256), 256, 0, st>>>(B, D->perm, nullptr, nullptr, n, nr, Y);
+    delete ks;
+    solve_levels<double, false>(h, (const double*)D->L, Y, W, nr, st, prof);
+    ks = prof ? new KScope(h, CHOL_K_PERMUTE, st, 0.0, 24.0 * n * nr) : nullptr;
+    k_sv_permute_out<double><<<grid1d((int64_t)n * nr, 256), 256, 0, st>>>(Y, D->perm, nullptr, nullptr, n, nr, B);
+    delete ks;
+  }
+  const cudaError_t e = cudaGetLastError();
+  return e == cudaSuccess ? CHOL_OK : CHOL_ECUDA;
+}
+
 }  // namespace
+
+// Binary32 solve with the mixed-precision factor, in place on a binary64 block.
+int chol_solve_mixed(chol_handle* h, double* b, int32_t nrhs, cudaStream_t st) {
+  int rc = set_solve_attrs();
+  if (rc) return rc;
+  DeviceState* D = h->dev;
+  const int n = h->n;
+  if (!D->Y32) {
+    if ((rc = chol_dalloc(h, (void**)&D->Y32, sizeof(float) * (size_t)std::max(n, 1) * kSolveChunk))) return rc;
+    if ((rc = chol_dalloc(h, (void**)&D->W32, sizeof(float) * (size_t)std::max<int64_t>(h->w_rows_max, 1) * kSolveChunk)))
+      return rc;
+    if ((rc = chol_dalloc(h, (void**)&D->rhs_scale, sizeof(double) * kSolveChunk))) return rc;
+  }
+  unsigned long long* sc = (unsigned long long*)D->rhs_scale;
+  for (int r0 = 0; r0 < nrhs; r0 += kSolveChunk) {
+    const int nr = std::min(kSolveChunk, nrhs - r0);
+    double* B = b + (int64_t)r0 * n;
+    CHOL_CUDA_TRY(cudaMemsetAsync(sc, 0, sizeof(double) * kSolveChunk, st));
+    {
+      KScope ks(h, CHOL_K_PERMUTE, st, 0.0, 12.0 * n * nr);
+      k_sv_maxabs<<<grid1d(n, 256), 256, 0, st>>>(B, n, nr, sc);
+      k_sv_permute_in<float><<<grid1d((int64_t)n * nr, 256), 256, 0, st>>>(B, D->perm, D->mx_d, sc, n, nr, D->Y32);
+    }
+    solve_levels<float, true>(h, (const float*)D->L, D->Y32, D->W32, nr, st, true);
+    {
+      KScope ks(h, CHOL_K_PERMUTE, st, 0.0, 12.0 * n * nr);
+      k_sv_permute_out<float><<<grid1d((int64_t)n * nr, 256), 256, 0, st>>>(D->Y32, D->perm, D->mx_d, sc, n, nr, B);
+    }
+  }
+  CHOL_CUDA_TRY(cudaGetLastError());
+  return CHOL_OK;
+}
 
 extern "C" int chol_solve(chol_handle* h, double* b, int32_t nrhs, void* stream) {
   if (!h) return -1;
@@ -280,69 +599,11 @@ extern "C" int chol_solve(chol_handle* h, double* b, int32_t nrhs, void* stream)
   if (!h->factored) return CHOL_ESTATE;
   if (nrhs == 0 || h->n == 0) return CHOL_OK;
   if (h->opt.precision != CHOL_PREC_FP64) return chol_solve_mixed(h, b, nrhs, (cudaStream_t)stream);
-  int rc = ensure_solve_ws(h);
+  int rc = set_solve_attrs();
   if (rc) return rc;
+  if ((rc = ensure_solve_ws(h))) return rc;
   DeviceState* D = h->dev;
-  cudaStream_t st = (cudaStream_t)stream;
-  const int nb = h->opt.block_cols;
-  const int n = h->n;
-  for (int r0 = 0; r0 < nrhs; r0 += kSolveChunk) {
-    const int nr = std::min(kSolveChunk, nrhs - r0);
-    double* B = b + (int64_t)r0 * n;
-    {
-      KScope ks(h, CHOL_K_PERMUTE, st, 0.0, 24.0 * n * nr);
-      k_permute_in<<<grid1d((int64_t)n * nr, 256), 256, 0, st>>>(B, D->perm, n, n, nr, D->Y);
-    }
-    for (const LevelPlan& P : h->levels) {
-      for (size_t k = 0; k < P.ssteps.size(); ++k) {
-        const SolveStep& s = P.ssteps[k];
-        const int k0 = (int)k * nb;
-        if (s.diag_n > 0) {
-          KScope ks(h, CHOL_K_SOLVE_DIAG, st, 0.0, 0.0);
-          k_diag<false><<<s.diag_n, kSolveThreads, 0, st>>>(
-              D->sn, D->sdiag + s.diag_b, k0, nb, D->L, D->Y, n, nr);
-        }
-        if (s.fupd_n > 0) {
-          KScope ks(h, CHOL_K_SOLVE_FUPD, st, 0.0, 0.0);
-          k_fwd_update<<<s.fupd_n, kSolveThreads, 0, st>>>(D->sn, D->fupd + s.fupd_b, nb, D->L, D->Y, n,
-                                                           D->W, nr);
-        }
-      }
-      if (P.asm_n > 0) {
-        KScope ks(h, CHOL_K_SOLVE_FASM, st, 0.0, 0.0);
-        k_fwd_assemble<<<P.asm_n, kSolveThreads, 0, st>>>(D->asm_tasks + P.asm_b, D->asm_segs, D->sn,
-                                                          D->rows, D->W, D->Y, n, nr);
-      }
-    }
-    for (int lv = h->nlevels - 1; lv >= 0; --lv) {
-      const LevelPlan& P = h->levels[lv];
-      if (P.bpanel_n > 0) {
-        KScope ks(h, CHOL_K_SOLVE_BPANEL, st, 0.0, 0.0);
-        k_bwd_panel<<<P.bpanel_n, kSolveThreads, 0, st>>>(D->sn, D->bpanel + P.bpanel_b, D->rows, D->L,
-                                                          D->Y, n, nr);
-      }
-      for (int k = (int)P.ssteps.size() - 1; k >= 0; --k) {
-        const SolveStep& s = P.ssteps[k];
-        const int k0 = k * nb;
-        if (s.diag_n > 0) {
-          KScope ks(h, CHOL_K_SOLVE_DIAG, st, 0.0, 0.0);
-          k_diag<true><<<s.diag_n, kSolveThreads, 0, st>>>(
-              D->sn, D->sdiag + s.diag_b, k0, nb, D->L, D->Y, n, nr);
-        }
-        if (s.bupd_n > 0) {
-          KScope ks(h, CHOL_K_SOLVE_BUPD, st, 0.0, 0.0);
-          k_bwd_update<<<s.bupd_n, kSolveThreads, 0, st>>>(D->sn, D->bupd + s.bupd_b, nb, D->L, D->Y, n,
-                                                           nr);
-        }
-      }
-    }
-    {
-      KScope ks(h, CHOL_K_PERMUTE, st, 0.0, 24.0 * n * nr);
-      k_permute_out<<<grid1d((int64_t)n * nr, 256), 256, 0, st>>>(D->Y, D->perm, n, n, nr, B);
-    }
-  }
-  CHOL_CUDA_TRY(cudaGetLastError());
-  return CHOL_OK;
+  return solve_fp64(h, b, nrhs, (cudaStream_t)stream, D->Y, D->W, kSolveChunk, true);
 }
 
 // ---------------------------------------------------------------------------
@@ -361,7 +622,7 @@ extern "C" int chol_solve(chol_handle* h, double* b, int32_t nrhs, void* stream)
 //
 // The array is shared by every call on a device and keeps the previous call's
 // contents; nothing in it needs to start at zero (each chunk writes Y before
-// reading it, and the first column step writes each W row before accumulating).
+// reading it, and each level writes its W rows before reading them).
 // Calls whose work overlaps on the GPU (different streams or threads) race on
 // the array. The first call on each device looks up the array's device address
 // with cudaGetSymbolAddress (with that device current); make that first call
@@ -408,48 +669,12 @@ extern "C" int chol_solve_noalloc(chol_handle* h, double* b, int32_t nrhs, void*
   if (!h->factored || !h->dev) return CHOL_ESTATE;
   if (h->opt.precision != CHOL_PREC_FP64) return CHOL_ENOTSUP;
   if (nrhs == 0 || h->n == 0) return CHOL_OK;
-  double* scratch = nullptr;
-  int rc = noalloc_scratch(&scratch);
+  int rc = set_solve_attrs();
   if (rc) return rc;
+  double* scratch = nullptr;
+  if ((rc = noalloc_scratch(&scratch))) return rc;
   const int chunk = (int)std::min<int64_t>(kSolveChunk, kNoAllocScratchDoubles / std::max<int64_t>(per_col, 1));
-  DeviceState* D = h->dev;
-  cudaStream_t st = (cudaStream_t)stream;
-  const int nb = h->opt.block_cols;
-  const int n = h->n;
   double* Y = scratch;
-  double* W = scratch + (int64_t)n * chunk;
-  for (int r0 = 0; r0 < nrhs; r0 += chunk) {
-    const int nr = std::min(chunk, nrhs - r0);
-    double* B = b + (int64_t)r0 * n;
-    k_permute_in<<<grid1d((int64_t)n * nr, 256), 256, 0, st>>>(B, D->perm, n, n, nr, Y);
-    for (const LevelPlan& P : h->levels) {
-      for (size_t k = 0; k < P.ssteps.size(); ++k) {
-        const SolveStep& s = P.ssteps[k];
-        const int k0 = (int)k * nb;
-        if (s.diag_n > 0)
-          k_diag<false><<<s.diag_n, kSolveThreads, 0, st>>>(D->sn, D->sdiag + s.diag_b, k0, nb, D->L, Y, n, nr);
-        if (s.fupd_n > 0)
-          k_fwd_update<<<s.fupd_n, kSolveThreads, 0, st>>>(D->sn, D->fupd + s.fupd_b, nb, D->L, Y, n, W, nr);
-      }
-      if (P.asm_n > 0)
-        k_fwd_assemble<<<P.asm_n, kSolveThreads, 0, st>>>(D->asm_tasks + P.asm_b, D->asm_segs, D->sn, D->rows,
-                                                          W, Y, n, nr);
-    }
-    for (int lv = h->nlevels - 1; lv >= 0; --lv) {
-      const LevelPlan& P = h->levels[lv];
-      if (P.bpanel_n > 0)
-        k_bwd_panel<<<P.bpanel_n, kSolveThreads, 0, st>>>(D->sn, D->bpanel + P.bpanel_b, D->rows, D->L, Y, n, nr);
-      for (int k = (int)P.ssteps.size() - 1; k >= 0; --k) {
-        const SolveStep& s = P.ssteps[k];
-        const int k0 = k * nb;
-        if (s.diag_n > 0)
-          k_diag<true><<<s.diag_n, kSolveThreads, 0, st>>>(D->sn, D->sdiag + s.diag_b, k0, nb, D->L, Y, n, nr);
-        if (s.bupd_n > 0)
-          k_bwd_update<<<s.bupd_n, kSolveThreads, 0, st>>>(D->sn, D->bupd + s.bupd_b, nb, D->L, Y, n, nr);
-      }
-    }
-    k_permute_out<<<grid1d((int64_t)n * nr, 256), 256, 0, st>>>(Y, D->perm, n, n, nr, B);
-  }
-  const cudaError_t e = cudaGetLastError();
-  return e == cudaSuccess ? CHOL_OK : CHOL_ECUDA;
+  double* W = scratch + (int64_t)h->n * chunk;
+  return solve_fp64(h, b, nrhs, (cudaStream_t)stream, Y, W, chunk, false);
 }

