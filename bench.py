@@ -148,6 +148,95 @@ def backward_error(p, b, x):
     return (np.abs(r).max(axis=0) / (anorm * np.abs(x).max(axis=0) + np.abs(b).max(axis=0))).max()
 
 
+def _timed(torch, st, fn, reps):
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    out = None
+    ms = []
+    for _ in range(reps):
+        torch.cuda.synchronize()
+        e0.record(st)
+        out = fn()
+        e1.record(st)
+        torch.cuda.synchronize()
+        ms.append(e0.elapsed_time(e1))
+    return float(np.median(ms)), out
+
+
+def mixed_run(P, torch, dev, p, b, precision, merge, reps, static_pivot=0):
+    """Factor with a mixed mode, refine all right-hand sides to eta <= 1e-10."""
+    opt = P.chol_default_options()
+    opt.precision = precision
+    opt.merge_growth = merge
+    opt.static_pivot = static_pivot
+    S = P.SparseCholesky(p.n, p["colptr"], p["rowind"], p["perm"], opt)
+    st = torch.cuda.current_stream()
+    vals = torch.as_tensor(p["values"], device=dev)
+    nrhs = b.shape[1]
+    B = torch.as_tensor(np.ascontiguousarray(b.T), device=dev).t()
+    X = torch.zeros_like(B)
+    S.factor(vals)
+    P.chol_solve_refine(S.h, B, X, nrhs, 1e-10, 200)
+    fms, _ = _timed(torch, st, lambda: S.factor(vals), reps)
+    rms, res = _timed(torch, st, lambda: P.chol_solve_refine(S.h, B, X, nrhs, 1e-10, 200), reps)
+    rc, iters, berr = res
+    eta = backward_error(p, b, X.cpu().numpy())
+    info = P.chol_get_info(S.h)
+    S.close()
+    return {"precision": {1: "fp32", 2: "tf32", 3: "bf16"}[precision], "factor_ms": fms, "refine_ms": rms,
+            "total_ms": fms + rms, "refine_rc": rc, "iterations": iters, "backward_error": float(eta),
+            "fp64_fallback_blocks": info.fp64_fallbacks, "perturbed_pivots": info.perturbed_pivots}
+
+
+def mixed_vs_fp64(args, P, gridgen, torch, dev, p, b, vals, flops, factor_ms, solve_ms):
+    """Mixed precision + binary64 refinement to eta <= 1e-10 against the plain
+    binary64 factor + solve, on the benchmark workload and on the 3D 48^3 x 3
+    27-point elasticity workload (BF16/TF32 updates)."""
+    out = {}
+    best = None
+    for prec in (1, 2):
+        r = mixed_run(P, torch, dev, p, b, prec, args.merge, 3)
+        out.setdefault("3d64", {})[r["precision"]] = r
+        if r["refine_rc"] == 0 and (best is None or r["total_ms"] < best["total_ms"]):
+            best = r
+    out["3d64"]["fp64_ms"] = factor_ms + solve_ms
+    if best:
+        out["3d64"]["best"] = best["precision"]
+        out["3d64"]["speedup"] = (factor_ms + solve_ms) / best["total_ms"]
+        out["3d64"]["mixed_gflops"] = flops / (best["total_ms"] * 1e-3) / 1e9
+    if not args.skip_elasticity:
+        pe = gridgen.workload("elast48")
+        be = gridgen.rhs_uniform(pe.n, 1, seed=3)
+        opt = P.chol_default_options()
+        opt.merge_growth = args.merge
+        S = P.SparseCholesky(pe.n, pe["colptr"], pe["rowind"], pe["perm"], opt)
+        st = torch.cuda.current_stream()
+        ve = torch.as_tensor(pe["values"], device=dev)
+        Be = torch.as_tensor(np.ascontiguousarray(be.T), device=dev).t()
+        S.factor(ve)
+        f64, _ = _timed(torch, st, lambda: S.factor(ve), 1)
+        Xe = Be.clone()
+        s64, _ = _timed(torch, st, lambda: S.solve_(Xe), 1)
+        eflops = S.info.flops
+        eta64 = backward_error(pe, be, Xe.cpu().numpy())
+        S.close()
+        e = {"workload": "3D 48^3 x 3-dof 27-point elasticity-like (n=331776), 1 RHS", "flops": eflops,
+             "fp64": {"factor_ms": f64, "solve_ms": s64, "total_ms": f64 + s64, "backward_error": float(eta64),
+                      "factor_gflops": eflops / (f64 * 1e-3) / 1e9}}
+        bestm = None
+        for prec in (2, 3):
+            r = mixed_run(P, torch, dev, pe, be, prec, args.merge, 2)
+            e[r["precision"]] = r
+            if r["refine_rc"] == 0 and (bestm is None or r["total_ms"] < bestm["total_ms"]):
+                bestm = r
+        if bestm:
+            e["best"] = bestm["precision"]
+            e["speedup"] = (f64 + s64) / bestm["total_ms"]
+            e["mixed_gflops"] = eflops / (bestm["total_ms"] * 1e-3) / 1e9
+        out["elast48"] = e
+    return out
+
+
 def run_ours(args, rank, world, local_rank):
     import torch
     import __graft_entry__
@@ -231,6 +320,8 @@ def run_ours(args, rank, world, local_rank):
     f1.record(st)
     torch.cuda.synchronize()
     e2e_ms = f0.elapsed_time(f1) / args.steps
+    mixed = None if args.no_mixed else mixed_vs_fp64(args, P, gridgen, torch, dev, p, b, vals, flops,
+                                                         factor_ms, solve_ms)
     # max over ranks
     if dist:
         t = torch.tensor([ms, e2e_ms], device=dev)
@@ -268,7 +359,8 @@ def run_ours(args, rank, world, local_rank):
                         "ms_per_step": e2e_ms, "h2d_bytes_per_step": int(hv.numel() * 8 + hb.numel() * 8),
                         "d2h_bytes_per_step": int(hx.numel() * 8)},
                 "gpu_launches": launches // max(args.steps, 1) * args.steps,
-                "roofline": roof, "cpu_baseline": cpu, "clocks": clk.summary()}
+                "roofline": roof, "cpu_baseline": cpu, "clocks": clk.summary(),
+                "mixed_vs_fp64": mixed}
         print(json.dumps(line), flush=True)
     S.close()
     if dist:
@@ -284,6 +376,8 @@ def main():
     ap.add_argument("--cpu-grid", type=int, default=40)
     ap.add_argument("--ref-grid", type=int, default=32)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-mixed", action="store_true", help="skip the mixed-precision comparison")
+    ap.add_argument("--skip-elasticity", action="store_true")
     ap.add_argument("--workload", default="3d64", choices=["3d64", "3d48"],
                     help="3d64 is the benchmark; 3d48 is the smaller case used for ncu captures")
     ap.add_argument("--merge", type=float, default=0.1,
