@@ -419,7 +419,8 @@ void build(chol_handle* h, const int64_t* colptr, const int32_t* rowind) {
   h->level_snodes.clear(); h->small_list.clear(); h->potrf_list.clear();
   h->trsm_tasks.clear(); h->gemm_tasks.clear(); h->syrk_tasks.clear();
   h->bpanel_tasks.clear(); h->sdiag_list.clear(); h->fupd_tasks.clear(); h->bupd_tasks.clear();
-  h->gemv_tasks.clear();
+  h->gemv_tasks.clear(); h->bpart_tasks.clear(); h->bred_tasks.clear();
+  h->p_max = 0;
   h->asm_tasks.clear(); h->asm_segs.clear();
   h->n_small = h->n_large = 0;
   h->update_doubles = 0;
@@ -537,6 +538,24 @@ void build(chol_handle* h, const int64_t* colptr, const int32_t* rowind) {
       for (int32_t c0 = 0; c0 < d.s; c0 += bpanel_cols) h->bpanel_tasks.push_back({J, 0, 0, c0});
     }
     P.gemv_n = (int32_t)h->gemv_tasks.size() - P.gemv_b;
+    // row-major backward panel: 64-row chunks x 256-column tiles, then a reduction
+    P.bpart_b = (int32_t)h->bpart_tasks.size();
+    P.bred_b = (int32_t)h->bred_tasks.size();
+    int64_t pp = 0;
+    for (int32_t J : Js) {
+      SnodeDev& d = h->snodes[J];
+      const int32_t b = d.len - d.s;
+      d.ppre = pp;
+      if (b <= 0 || h->opt.precision == CHOL_PREC_FP64) continue;
+      const int32_t nch = (b + 63) / 64;
+      for (int32_t ch = 0; ch < nch; ++ch)
+        for (int32_t c0 = 0; c0 < d.s; c0 += 256) h->bpart_tasks.push_back({J, ch, ch * 64, c0});
+      for (int32_t c0 = 0; c0 < d.s; c0 += 256) h->bred_tasks.push_back({J, 0, 0, c0});
+      pp += (int64_t)nch * d.s;
+    }
+    P.bpart_n = (int32_t)h->bpart_tasks.size() - P.bpart_b;
+    P.bred_n = (int32_t)h->bred_tasks.size() - P.bred_b;
+    h->p_max = std::max(h->p_max, pp);
     P.bpanel_n = (int32_t)h->bpanel_tasks.size() - P.bpanel_b;
     // assembly: group this level's pairs by target K (then J ascending)
     auto& pl = pairs_by_level[lv];

@@ -29,6 +29,8 @@ struct DeviceState {
   TileTask* bupd = nullptr;
   TileTask* bpanel = nullptr;
   TileTask* gemv = nullptr;
+  TileTask* bpart = nullptr;
+  TileTask* bred = nullptr;
   int32_t* perm = nullptr;
   int32_t* status = nullptr;    // device status word (first failing column + 1)
   int32_t* status_host = nullptr;  // pinned
@@ -58,6 +60,7 @@ struct DeviceState {
   int refine_cap = 0;
   float* Y32 = nullptr;            // binary32 solve workspaces
   float* W32 = nullptr;
+  float* P32 = nullptr;             // row-major backward-panel partials
   double* rhs_scale = nullptr;
   // solve workspaces (grown on demand)
   double* Y = nullptr;          // permuted right-hand sides, n x chunk

@@ -498,7 +498,7 @@ void chol_device_free(chol_handle* h) {
   if (D->device >= 0) cudaSetDevice(D->device);
   void* ptrs[] = {D->L, D->U, D->sn, D->rows, D->amap, D->small_list, D->potrf_list,
                   D->level_snodes, D->trsm, D->gemm, D->syrk, D->asm_tasks, D->asm_segs, D->sdiag,
-                  D->fupd, D->bupd, D->bpanel, D->gemv, D->perm, D->status, D->part, D->scalar_dev, D->Y, D->W,
+                  D->fupd, D->bupd, D->bpanel, D->gemv, D->bpart, D->bred, D->P32, D->perm, D->status, D->part, D->scalar_dev, D->Y, D->W,
                   D->mx_diagpos, D->mx_aij, D->mx_d, D->mx_fallbacks, D->csr_ptr, D->csr_col, D->csr_src,
                   D->csr_val, D->Lbf, D->tmaps, D->tc_err, D->R, D->Z, D->Pv, D->Q, D->red, D->Y32, D->W32,
                   D->rhs_scale};
@@ -556,6 +556,8 @@ int chol_device_ensure(chol_handle* h) {
   if ((rc = upload(h, &D->bupd, h->bupd_tasks))) return fail(rc);
   if ((rc = upload(h, &D->bpanel, h->bpanel_tasks))) return fail(rc);
   if ((rc = upload(h, &D->gemv, h->gemv_tasks))) return fail(rc);
+  if ((rc = upload(h, &D->bpart, h->bpart_tasks))) return fail(rc);
+  if ((rc = upload(h, &D->bred, h->bred_tasks))) return fail(rc);
   if ((rc = upload(h, &D->perm, h->perm))) return fail(rc);
   if ((rc = chol_dalloc(h, (void**)&D->status, sizeof(int32_t)))) return fail(rc);
   if ((rc = chol_dalloc(h, (void**)&D->part, sizeof(double) * (size_t)std::max(h->ns, 1)))) return fail(rc);

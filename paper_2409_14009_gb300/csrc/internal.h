@@ -11,6 +11,7 @@ struct SnodeDev {
   int64_t roff;  // offset of struct(J) in the rows[] array
   int64_t uoff;  // offset of U_J (b x b, column-major, ld b) in the update workspace
   int64_t wpre;  // prefix of b over the level (solve workspace offset = wpre * nrhs)
+  int64_t ppre;  // prefix over the level of ceil(b/64) * s (backward-panel partials, row-major)
   int32_t f;     // first column
   int32_t s;     // number of columns
   int32_t len;   // |struct(J)| (rows of the panel)
@@ -53,6 +54,8 @@ struct LevelPlan {
   int32_t asm_b, asm_n;       // assembly tasks
   std::vector<SolveStep> ssteps;
   int32_t gemv_b, gemv_n;     // forward-solve panel products (TileTask: J, r0)
+  int32_t bpart_b, bpart_n;   // row-major backward panel, stage 1 (J, chunk, u0, c0)
+  int32_t bred_b, bred_n;     // row-major backward panel, stage 2 (J, c0)
   int32_t bpanel_b, bpanel_n; // backward-solve panel column blocks (TileTask: J, c0)
   int64_t u_doubles;          // update workspace used by this level
   int64_t w_rows;             // sum of b over the level (solve workspace rows)
@@ -101,6 +104,8 @@ struct chol_handle {
   std::vector<int32_t> sdiag_list;             // solve: supernode per (level, step)
   std::vector<TileTask> fupd_tasks, bupd_tasks; // solve: (J, k0, r0) / (J, k0, c0)
   std::vector<TileTask> gemv_tasks;             // solve: (J, r0) off-diagonal row tiles
+  std::vector<TileTask> bpart_tasks, bred_tasks; // solve: row-major backward panel stages
+  int64_t p_max = 0;                            // largest per-level partial-sum rows
   std::vector<AsmTask> asm_tasks;
   std::vector<AsmSeg> asm_segs;
   int32_t n_small = 0, n_large = 0;

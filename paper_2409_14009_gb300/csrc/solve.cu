@@ -97,8 +97,9 @@ k_sv_diag(const SnodeDev* __restrict__ sn, const int32_t* __restrict__ list, int
           const T* __restrict__ L, T* __restrict__ Y, int n, int nrhs) {
   extern __shared__ __align__(16) unsigned char sv_smem[];
   T* ys = reinterpret_cast<T*>(sv_smem);          // kSolveSB x nrhs
-  T* Ls = ys + kSolveSB * nrhs;                   // 64 x 65
-  T* inv = Ls + kSub * 65;                        // 64
+  T* Ls = ys + kSolveSB * nrhs;                   // 64 x 65 diagonal sub-block
+  T* Lt = Ls + kSub * 65;                         // 64 x 65 update tile
+  T* inv = Lt + kSub * 65;                        // 64
   const SnodeDev d = sn[list[blockIdx.x]];
   const T* P = L + d.loff;
   const int sbk = min(sb, d.s - k0);
@@ -167,17 +168,26 @@ k_sv_diag(const SnodeDev* __restrict__ sn, const int32_t* __restrict__ list, int
       }
     }
     __syncthreads();
-    // update the rest of the super-block with the solved sub-block
+    // update the rest of the super-block with the solved sub-block, 64 rows at a
+    // time through a staged tile (coalesced loads whatever the storage form)
     const int lo = TRANS ? 0 : s0 + kb, hi = TRANS ? s0 : sbk;
-    const int cnt = hi - lo;
-    for (int e = threadIdx.x; e < cnt * nrhs; e += blockDim.x) {
-      const int i = lo + e % cnt, r = e / cnt;
-      T acc = T(0);
-      for (int k = 0; k < kb; ++k) {
-        const T l = TRANS ? lval<T, RM>(P, d, k0 + s0 + k, k0 + i) : lval<T, RM>(P, d, k0 + i, k0 + s0 + k);
-        acc += l * ys[s0 + k + r * kSolveSB];
+    for (int t0 = lo; t0 < hi; t0 += kSub) {
+      const int rows = min(kSub, hi - t0);
+      __syncthreads();
+      for (int e = threadIdx.x; e < rows * kb; e += blockDim.x) {
+        // the contiguous index of the stored element varies fastest
+        const bool kfast = RM != TRANS;
+        const int r = kfast ? e / kb : e % rows, k = kfast ? e % kb : e / rows;
+        Lt[r + k * 65] = TRANS ? lval<T, RM>(P, d, k0 + s0 + k, k0 + t0 + r) : lval<T, RM>(P, d, k0 + t0 + r, k0 + s0 + k);
       }
-      ys[i + r * kSolveSB] -= acc;
+      __syncthreads();
+      for (int e = threadIdx.x; e < rows * nrhs; e += blockDim.x) {
+        const int r = e % rows, rr2 = e / rows;
+        T acc = T(0);
+#pragma unroll 8
+        for (int k = 0; k < kb; ++k) acc += Lt[r + k * 65] * ys[s0 + k + rr2 * kSolveSB];
+        ys[t0 + r + rr2 * kSolveSB] -= acc;
+      }
     }
   }
   __syncthreads();
@@ -393,6 +403,62 @@ k_sv_bpanel(const SnodeDev* __restrict__ sn, const TileTask* __restrict__ tasks,
   }
 }
 
+// Backward panel for row-major storage, two stages. Stage 1: a task (J, 64-row
+// chunk u0, 256-column tile c0) writes part[chunk][c] = sum over its rows of
+// L(s+u, c) x[rows[s+u]] (rows walked contiguously, coalesced). Stage 2: for
+// each column, the chunk partials are summed in chunk order and subtracted.
+template <class T>
+__global__ void __launch_bounds__(kT)
+k_sv_bpart(const SnodeDev* __restrict__ sn, const TileTask* __restrict__ tasks, const int32_t* __restrict__ rows,
+           const T* __restrict__ L, const T* __restrict__ Y, int n, T* __restrict__ part, int64_t pstride,
+           int nrhs) {
+  __shared__ T xs[kSub * kSolveChunk];
+  const TileTask t = tasks[blockIdx.x];
+  const SnodeDev d = sn[t.J];
+  const int b = d.len - d.s;
+  const int u0 = t.r0, chunk = t.k0;
+  const int nr64 = min(kSub, b - u0);
+  const int32_t* rj = rows + d.roff + d.s + u0;
+  for (int q = threadIdx.x; q < nr64 * nrhs; q += blockDim.x) {
+    const int u = q % nr64, r = q / nr64;
+    xs[u + r * kSub] = Y[rj[u] + (int64_t)r * n];
+  }
+  __syncthreads();
+  const int c = t.c0 + threadIdx.x;
+  if (c >= d.s) return;
+  const T* P = L + d.loff + (int64_t)(d.s + u0) * d.ld + c;
+  T acc[kSolveChunk];
+#pragma unroll
+  for (int r = 0; r < kSolveChunk; ++r) acc[r] = T(0);
+  for (int u = 0; u < nr64; ++u) {
+    const T l = P[(int64_t)u * d.ld];
+#pragma unroll
+    for (int r = 0; r < kSolveChunk; ++r)
+      if (r < nrhs) acc[r] += l * xs[u + r * kSub];
+  }
+  T* out = part + d.ppre + (int64_t)chunk * d.s + c;
+#pragma unroll
+  for (int r = 0; r < kSolveChunk; ++r)
+    if (r < nrhs) out[r * pstride] = acc[r];
+}
+
+template <class T>
+__global__ void __launch_bounds__(kT)
+k_sv_bred(const SnodeDev* __restrict__ sn, const TileTask* __restrict__ tasks, const T* __restrict__ part,
+          int64_t pstride, T* __restrict__ Y, int n, int nrhs) {
+  const TileTask t = tasks[blockIdx.x];
+  const SnodeDev d = sn[t.J];
+  const int c = t.c0 + threadIdx.x;
+  if (c >= d.s) return;
+  const int nchunks = (d.len - d.s + kSub - 1) / kSub;
+  for (int r = 0; r < nrhs; ++r) {
+    const T* p = part + r * pstride + d.ppre + c;
+    T acc = T(0);
+    for (int ch = 0; ch < nchunks; ++ch) acc += p[(int64_t)ch * d.s];
+    Y[d.f + c + (int64_t)r * n] -= acc;
+  }
+}
+
 // Backward update: y[c0..c0+64) -= L[k0:k0+sbk, c]^T x[k0:k0+sbk] for c < k0.
 template <class T, bool RM>
 __global__ void __launch_bounds__(kT)
@@ -432,7 +498,7 @@ k_sv_bupd(const SnodeDev* __restrict__ sn, const TileTask* __restrict__ tasks, i
 
 template <class T>
 size_t diag_smem(int nr) {
-  return sizeof(T) * ((size_t)kSolveSB * nr + kSub * 65 + kSub);
+  return sizeof(T) * ((size_t)kSolveSB * nr + 2 * kSub * 65 + kSub);
 }
 
 template <class T>
@@ -444,7 +510,7 @@ size_t blk_smem(int nr) {
 // already permuted into Y (W: per-level panel products). `prof` enables the
 // per-class launch accounting (off for the no-allocation entry point).
 template <class T, bool RM>
-void solve_levels(chol_handle* h, const T* L, T* Y, T* W, int nr, cudaStream_t st, bool prof) {
+void solve_levels(chol_handle* h, const T* L, T* Y, T* W, T* part, int nr, cudaStream_t st, bool prof) {
   DeviceState* D = h->dev;
   const int n = h->n;
   const int sb = h->solve_sb;
@@ -478,7 +544,14 @@ void solve_levels(chol_handle* h, const T* L, T* Y, T* W, int nr, cudaStream_t s
   }
   for (int lv = h->nlevels - 1; lv >= 0; --lv) {
     const LevelPlan& P = h->levels[lv];
-    if (P.bpanel_n > 0) {
+    if constexpr (RM) {
+      if (P.bpart_n > 0) {
+        KScope* ks = scope(CHOL_K_SOLVE_BPANEL);
+        k_sv_bpart<T><<<P.bpart_n, kT, 0, st>>>(D->sn, D->bpart + P.bpart_b, D->rows, L, Y, n, part, h->p_max, nr);
+        k_sv_bred<T><<<P.bred_n, kT, 0, st>>>(D->sn, D->bred + P.bred_b, part, h->p_max, Y, n, nr);
+        delete ks;
+      }
+    } else if (P.bpanel_n > 0) {
       KScope* ks = scope(CHOL_K_SOLVE_BPANEL);
       k_sv_bpanel<T, RM><<<P.bpanel_n, kT, 0, st>>>(D->sn, D->bpanel + P.bpanel_b, D->rows, L, Y, n, nr);
       delete ks;
@@ -549,7 +622,7 @@ int solve_fp64(chol_handle* h, double* b, int32_t nrhs, cudaStream_t st, double*
     KScope* ks = prof ? new KScope(h, CHOL_K_PERMUTE, st, 0.0, 24.0 * n * nr) : nullptr;
     k_sv_permute_in<double><<<grid1d((int64_t)n * nr, 256), 256, 0, st>>>(B, D->perm, nullptr, nullptr, n, nr, Y);
     delete ks;
-    solve_levels<double, false>(h, (const double*)D->L, Y, W, nr, st, prof);
+    solve_levels<double, false>(h, (const double*)D->L, Y, W, (double*)nullptr, nr, st, prof);
     ks = prof ? new KScope(h, CHOL_K_PERMUTE, st, 0.0, 24.0 * n * nr) : nullptr;
     k_sv_permute_out<double><<<grid1d((int64_t)n * nr, 256), 256, 0, st>>>(Y, D->perm, nullptr, nullptr, n, nr, B);
     delete ks;
@@ -571,6 +644,8 @@ int chol_solve_mixed(chol_handle* h, double* b, int32_t nrhs, cudaStream_t st) {
     if ((rc = chol_dalloc(h, (void**)&D->W32, sizeof(float) * (size_t)std::max<int64_t>(h->w_rows_max, 1) * kSolveChunk)))
       return rc;
     if ((rc = chol_dalloc(h, (void**)&D->rhs_scale, sizeof(double) * kSolveChunk))) return rc;
+    if ((rc = chol_dalloc(h, (void**)&D->P32, sizeof(float) * (size_t)std::max<int64_t>(h->p_max, 1) * kSolveChunk)))
+      return rc;
   }
   unsigned long long* sc = (unsigned long long*)D->rhs_scale;
   for (int r0 = 0; r0 < nrhs; r0 += kSolveChunk) {
@@ -582,7 +657,7 @@ int chol_solve_mixed(chol_handle* h, double* b, int32_t nrhs, cudaStream_t st) {
       k_sv_maxabs<<<grid1d(n, 256), 256, 0, st>>>(B, n, nr, sc);
       k_sv_permute_in<float><<<grid1d((int64_t)n * nr, 256), 256, 0, st>>>(B, D->perm, D->mx_d, sc, n, nr, D->Y32);
     }
-    solve_levels<float, true>(h, (const float*)D->L, D->Y32, D->W32, nr, st, true);
+    solve_levels<float, true>(h, (const float*)D->L, D->Y32, D->W32, D->P32, nr, st, true);
     {
       KScope ks(h, CHOL_K_PERMUTE, st, 0.0, 12.0 * n * nr);
       k_sv_permute_out<float><<<grid1d((int64_t)n * nr, 256), 256, 0, st>>>(D->Y32, D->perm, D->mx_d, sc, n, nr, B);
