@@ -82,7 +82,10 @@ typedef struct chol_options {
                            /* stored entries grow by at most this fraction of   */
                            /* nnz(L); 0 = off (the maximal partition, default)  */
   int32_t small_max_rows;  /* rows limit of the one-CTA kernel; default 128     */
-  int32_t reserved;
+  int32_t persistent;      /* 1 = one cooperative launch walks every level (needs */
+                           /* every supernode on the one-CTA kernel, e.g. batches */
+                           /* of small systems); 0 = one launch per level and     */
+                           /* kernel class (default)                              */
   double pivot_tau;        /* mixed modes: a diagonal block with a binary32 pivot */
                            /* L_jj^2 below this (scaled matrix) is refactored in  */
                            /* binary64; default 1e-3                              */
@@ -91,7 +94,10 @@ typedef struct chol_options {
                            /* (counted), leaving the correction to               */
                            /* chol_solve_refine; 0 = report it as not positive   */
                            /* definite (default)                                 */
-  int32_t reserved2;
+  int32_t use_graph;       /* 1 = the factorization's launches are captured in a  */
+                           /* CUDA graph on the first chol_factor and replayed by */
+                           /* the later ones (values are copied into the handle   */
+                           /* first); 0 = direct launches (default)               */
 } chol_options;
 
 /* Fill *opt with the defaults. */
@@ -209,10 +215,46 @@ typedef struct chol_info {
   int32_t precision;       /* CHOL_PREC_* of the handle */
   int32_t fp64_fallbacks;  /* mixed modes: diagonal blocks refactored in binary64 by the last factor */
   int32_t perturbed_pivots; /* mixed modes with static_pivot: pivots raised to pivot_tau */
-  int32_t reserved2;
+  int32_t nsys;            /* independent systems (chol_analyze_batch), else 1 */
+  int32_t persistent_ok;   /* 1 if every supernode takes the one-CTA kernel */
+  int32_t persistent_threads; /* launch shape of the persistent kernel (0 = default) */
+  int32_t persistent_ctas_per_sm;
+  int32_t reserved3;
 } chol_info;
 
 int chol_get_info(const chol_handle* h, chol_info* info);
+
+/*
+ * Batches of independent SPD systems (many small systems of uneven sizes).
+ * The systems are passed as one block-diagonal matrix: system q owns rows and
+ * columns [sys_ptr[q], sys_ptr[q+1]); colptr / rowind / perm use global
+ * indices, no entry may couple two systems, and perm must map every system's
+ * range onto itself. The analysis is that of the block-diagonal matrix (its
+ * elimination tree is a forest, one tree per system), so every level of the
+ * schedule batches the supernodes of all systems; chol_factor, chol_solve and
+ * chol_solve_refine then work on the concatenated values and right-hand sides.
+ *   count    number of systems, >= 0
+ *   sys_ptr  host, count+1 offsets (sys_ptr[0] = 0, non-decreasing)
+ * Errors as chol_analyze, plus -2 for a bad sys_ptr and -4 for an entry or a
+ * permutation that crosses systems.
+ */
+int chol_analyze_batch(int32_t count, const int32_t* sys_ptr, const int64_t* colptr, const int32_t* rowind,
+                       const int32_t* perm, const chol_options* opt, chol_handle** out);
+
+/* log det of every system of a batch handle (out: host, count doubles; a
+ * single-system handle fills out[0]). Fixed-order reductions. Synchronizes. */
+int chol_logdet_batch(chol_handle* h, double* out, void* stream);
+
+/*
+ * Autotuner of the launch configuration: factors `values` (device, as for
+ * chol_factor) once per candidate and keeps the fastest:
+ * - level-by-level launches, with and without CUDA-graph replay;
+ * - when every supernode takes the one-CTA kernel, the persistent
+ *   cooperative kernel with 128 or 256 threads per CTA and 1 to 4 CTAs per SM.
+ * The handle keeps the winner (reported by chol_get_info) and ends up
+ * factored. Returns the status of the last factorization.
+ */
+int chol_autotune(chol_handle* h, const double* values, void* stream);
 
 /*
  * Copy out the symbolic results (host arrays, sized from chol_info; any

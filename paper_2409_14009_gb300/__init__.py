@@ -30,7 +30,7 @@ CHOL_PREC_TF32 = 2
 CHOL_PREC_BF16 = 3
 
 EXPORTED = ["chol_default_options", "chol_analyze", "chol_factor", "chol_solve", "chol_solve_noalloc",
-            "chol_solve_refine", "chol_logdet",
+            "chol_solve_refine", "chol_logdet", "chol_analyze_batch", "chol_logdet_batch", "chol_autotune",
             "chol_get_info", "chol_get_symbolic", "chol_get_partition", "chol_get_factor", "chol_profile",
             "chol_get_stats", "chol_destroy", "chol_strerror"]
 
@@ -43,8 +43,8 @@ class chol_options(C.Structure):
     _fields_ = [("precision", C.c_int32), ("small_max_cols", C.c_int32),
                 ("small_max_panel", C.c_int32), ("block_cols", C.c_int32),
                 ("device_mem_cap", C.c_int64), ("merge_growth", C.c_double),
-                ("small_max_rows", C.c_int32), ("reserved", C.c_int32), ("pivot_tau", C.c_double),
-                ("static_pivot", C.c_int32), ("reserved2", C.c_int32)]
+                ("small_max_rows", C.c_int32), ("persistent", C.c_int32), ("pivot_tau", C.c_double),
+                ("static_pivot", C.c_int32), ("use_graph", C.c_int32)]
 
 
 class chol_info(C.Structure):
@@ -55,7 +55,9 @@ class chol_info(C.Structure):
                 ("flops", C.c_double), ("n_small", C.c_int32), ("n_large", C.c_int32),
                 ("nsuper_storage", C.c_int32), ("reserved", C.c_int32), ("nnz_stored", C.c_int64),
                 ("flops_stored", C.c_double), ("precision", C.c_int32), ("fp64_fallbacks", C.c_int32),
-                ("perturbed_pivots", C.c_int32), ("reserved2", C.c_int32)]
+                ("perturbed_pivots", C.c_int32), ("nsys", C.c_int32), ("persistent_ok", C.c_int32),
+                ("persistent_threads", C.c_int32), ("persistent_ctas_per_sm", C.c_int32),
+                ("reserved3", C.c_int32)]
 
 
 class chol_kernel_stat(C.Structure):
@@ -92,6 +94,12 @@ def lib():
         L.chol_solve_refine.argtypes = [P, P, P, C.c_int32, C.c_double, C.c_int32,
                                         C.POINTER(C.c_int32), P, P]
         L.chol_solve_refine.restype = C.c_int
+        L.chol_analyze_batch.argtypes = [C.c_int32, P, P, P, P, C.POINTER(chol_options), C.POINTER(C.c_void_p)]
+        L.chol_analyze_batch.restype = C.c_int
+        L.chol_logdet_batch.argtypes = [P, P, P]
+        L.chol_logdet_batch.restype = C.c_int
+        L.chol_autotune.argtypes = [P, P, P]
+        L.chol_autotune.restype = C.c_int
         L.chol_logdet.argtypes = [P, C.POINTER(C.c_double), P]
         L.chol_logdet.restype = C.c_int
         L.chol_get_info.argtypes = [P, C.POINTER(chol_info)]
@@ -154,6 +162,26 @@ def chol_analyze(n, colptr, rowind, perm=None, opt=None):
     rc = lib().chol_analyze(int(n), _ptr(colptr), _ptr(rowind), _ptr(perm),
                             C.byref(opt) if opt is not None else None, C.byref(h))
     return rc, h
+
+
+def chol_analyze_batch(count, sys_ptr, colptr, rowind, perm=None, opt=None):
+    """Returns (rc, handle) for a block-diagonal batch of independent systems."""
+    sys_ptr = _np(sys_ptr, np.int32); colptr = _np(colptr, np.int64)
+    rowind = _np(rowind, np.int32); perm = _np(perm, np.int32)
+    h = C.c_void_p()
+    rc = lib().chol_analyze_batch(int(count), _ptr(sys_ptr), _ptr(colptr), _ptr(rowind), _ptr(perm),
+                                  C.byref(opt) if opt is not None else None, C.byref(h))
+    return rc, h
+
+
+def chol_logdet_batch(h, count, stream=None):
+    out = np.zeros(max(int(count), 1), np.float64)
+    rc = lib().chol_logdet_batch(h, _ptr(out), _stream(stream))
+    return rc, out[: int(count)]
+
+
+def chol_autotune(h, values, stream=None) -> int:
+    return lib().chol_autotune(h, _dev_ptr(values), _stream(stream))
 
 
 def chol_factor(h, values, stream=None) -> int:

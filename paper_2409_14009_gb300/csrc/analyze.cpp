@@ -28,6 +28,8 @@ extern "C" void chol_default_options(chol_options* opt) {
   opt->small_max_rows = 128;
   opt->pivot_tau = 1e-3;
   opt->static_pivot = 0;
+  opt->persistent = 0;
+  opt->use_graph = 0;
 }
 
 namespace {
@@ -60,7 +62,9 @@ int validate(int32_t n, const int64_t* colptr, const int32_t* rowind, const int3
     // tensor-core K chunks are 32 (tf32) / 64 (bf16) wide and must not cross a column step
     if (opt->precision == CHOL_PREC_TF32 && opt->block_cols % 32 != 0) return -5;
     if (opt->precision == CHOL_PREC_BF16 && opt->block_cols % 64 != 0) return -5;
-    if (opt->small_max_cols < 1 || opt->small_max_panel < 1 || opt->small_max_panel > 4096) return -5;
+    if (opt->small_max_cols < 1 || opt->small_max_panel < 1 || opt->small_max_panel > 16384) return -5;
+    if (opt->persistent != 0 && opt->persistent != 1) return -5;
+    if (opt->use_graph != 0 && opt->use_graph != 1) return -5;
     if (opt->block_cols < 8 || opt->block_cols > 64) return -5;
     if (opt->device_mem_cap < 0) return -5;
     if (!(opt->merge_growth >= 0.0) || opt->merge_growth > 100.0) return -5;
@@ -595,6 +599,15 @@ void build(chol_handle* h, const int64_t* colptr, const int32_t* rowind) {
     }
     P.asm_n = (int32_t)h->asm_tasks.size() - P.asm_b;
   }
+  h->persist_levels.clear();
+  h->small_panel_max = 0;
+  for (const LevelPlan& P : h->levels) {
+    h->persist_levels.push_back({P.small_b, P.small_n, P.asm_b, P.asm_n});
+    h->small_panel_max = std::max(h->small_panel_max, P.small_max_panel);
+  }
+  // one system unless chol_analyze_batch says otherwise
+  h->sys_ptr = {0, n};
+  h->sys_snode_ptr = {0, ns};
 }
 
 }  // namespace
@@ -633,6 +646,41 @@ void canonical_pairs(const chol_handle* h, std::vector<int32_t>& pj, std::vector
                      std::vector<int32_t>& pc0);
 }
 
+extern "C" int chol_analyze_batch(int32_t count, const int32_t* sys_ptr, const int64_t* colptr,
+                                  const int32_t* rowind, const int32_t* perm, const chol_options* opt,
+                                  chol_handle** out) {
+  if (!out) return -7;
+  *out = nullptr;
+  if (count < 0) return -1;
+  if (!sys_ptr || sys_ptr[0] != 0) return -2;
+  for (int32_t q = 0; q < count; ++q)
+    if (sys_ptr[q + 1] < sys_ptr[q]) return -2;
+  const int32_t n = sys_ptr[count];
+  int rc = validate(n, colptr, rowind, perm, opt);
+  if (rc) return rc;
+  // no coupling between systems, and perm keeps every system in place
+  std::vector<int32_t> sys_of(n);
+  for (int32_t q = 0; q < count; ++q)
+    for (int32_t j = sys_ptr[q]; j < sys_ptr[q + 1]; ++j) sys_of[j] = q;
+  for (int32_t c = 0; c < n; ++c)
+    for (int64_t t = colptr[c]; t < colptr[c + 1]; ++t)
+      if (sys_of[rowind[t]] != sys_of[c]) return -4;
+  if (perm)
+    for (int32_t i = 0; i < n; ++i)
+      if (sys_of[perm[i]] != sys_of[i]) return -4;
+  if ((rc = chol_analyze(n, colptr, rowind, perm, opt, out))) return rc;
+  chol_handle* h = *out;
+  h->sys_ptr.assign(sys_ptr, sys_ptr + count + 1);
+  // storage supernodes never span systems (no coupling): map ranges
+  h->sys_snode_ptr.assign(count + 1, 0);
+  int32_t J = 0;
+  for (int32_t q = 0; q < count; ++q) {
+    while (J < h->ns && h->sptr[J] < sys_ptr[q + 1]) ++J;
+    h->sys_snode_ptr[q + 1] = J;
+  }
+  return CHOL_OK;
+}
+
 extern "C" int chol_get_info(const chol_handle* h, chol_info* info) {
   if (!h) return -1;
   if (!info) return -2;
@@ -641,6 +689,10 @@ extern "C" int chol_get_info(const chol_handle* h, chol_info* info) {
   info->nsuper = (int32_t)h->c_sptr.size() - 1;
   info->nsuper_storage = h->ns;
   info->precision = h->opt.precision;
+  info->nsys = (int32_t)h->sys_ptr.size() - 1;
+  info->persistent_ok = h->n_large == 0 ? 1 : 0;
+  info->persistent_threads = h->persist_threads;
+  info->persistent_ctas_per_sm = h->persist_ctas;
   info->fp64_fallbacks = h->fp64_fallbacks;
   info->perturbed_pivots = h->perturbed_pivots;
   info->nnz_stored = h->nnz_stored;

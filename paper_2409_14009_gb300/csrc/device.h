@@ -62,6 +62,16 @@ struct DeviceState {
   float* W32 = nullptr;
   float* P32 = nullptr;             // row-major backward-panel partials
   double* rhs_scale = nullptr;
+  // batches, persistent launches and graphs
+  PersistLevel* plevels = nullptr;
+  double* vals = nullptr;          // handle-owned copy of the values (graph replays)
+  int32_t* sys_snode = nullptr;    // storage-supernode range of every system
+  double* sys_out = nullptr;
+  cudaGraphExec_t graph_exec = nullptr;
+  cudaStream_t gstream = nullptr;  // capture / replay stream of the handle
+  cudaEvent_t gev[2] = {nullptr, nullptr};
+  chol_kernel_stat graph_delta[CHOL_K_NCLASSES] = {};
+  float mx_spiv = 0.f;             // static-pivot threshold passed to the persistent kernel
   // solve workspaces (grown on demand)
   double* Y = nullptr;          // permuted right-hand sides, n x chunk
   double* W = nullptr;          // per-level panel products, w_rows_max x chunk

@@ -23,8 +23,12 @@
 #include <cmath>
 #include <cstring>
 
+#include <cooperative_groups.h>
+
 #include "device.h"
 #include "mixed.h"
+
+namespace cg = cooperative_groups;
 
 namespace {
 
@@ -71,11 +75,8 @@ __global__ void k_scatter(const double* __restrict__ vals, const int64_t* __rest
 }
 
 // One CTA per small supernode: the whole len x s panel lives in shared memory.
-__global__ void __launch_bounds__(kSmallThreads)
-k_small(const SnodeDev* __restrict__ sn, const int32_t* __restrict__ list, double* __restrict__ L,
-        double* __restrict__ U, int* status) {
-  extern __shared__ double P[];
-  const SnodeDev d = sn[list[blockIdx.x]];
+__device__ __forceinline__ void small_body(const SnodeDev& d, double* __restrict__ L, double* __restrict__ U,
+                                           int* status, double* P) {
   const int len = d.len, s = d.s, b = len - s;
   double* G = L + d.loff;
   for (int c = 0; c < s; ++c)
@@ -98,6 +99,13 @@ k_small(const SnodeDev* __restrict__ sn, const int32_t* __restrict__ list, doubl
     for (int k = 0; k < s; ++k) acc += R[u + k * len] * R[c + k * len];
     Uj[u + (int64_t)c * b] = acc;
   }
+}
+
+__global__ void __launch_bounds__(kSmallThreads)
+k_small(const SnodeDev* __restrict__ sn, const int32_t* __restrict__ list, double* __restrict__ L,
+        double* __restrict__ U, int* status) {
+  extern __shared__ double P[];
+  small_body(sn[list[blockIdx.x]], L, U, status, P);
 }
 
 // Blocked path, step k0: factor the kb x kb (kb <= 64) diagonal block of each
@@ -331,19 +339,16 @@ k_syrk(const SnodeDev* __restrict__ sn, const TileTask* __restrict__ tasks,
 // every column of the segment. Within a segment every (column c, row u) of U_J
 // hits a distinct entry of K (relind is injective); a barrier separates
 // segments, so contributions to one entry are applied in a fixed order.
-__global__ void __launch_bounds__(kAsmThreads)
-k_assemble(const AsmTask* __restrict__ tasks, const AsmSeg* __restrict__ segs,
-           const SnodeDev* __restrict__ sn, const int32_t* __restrict__ rows,
-           const double* __restrict__ U, double* __restrict__ L) {
-  extern __shared__ int32_t ssm[];
-  const AsmTask t = tasks[blockIdx.x];
+__device__ __forceinline__ void assemble_body(const AsmTask& t, const AsmSeg* __restrict__ segs,
+                                              const SnodeDev* __restrict__ sn, const int32_t* __restrict__ rows,
+                                              const double* __restrict__ U, double* __restrict__ L, int32_t* ssm) {
   const SnodeDev dk = sn[t.K];
   int32_t* sK = ssm;              // struct(K), dk.len entries
   int32_t* pos = ssm + dk.len;    // positions of rows ca.. of the current segment
   const int32_t* rk = rows + dk.roff;
   for (int i = threadIdx.x; i < dk.len; i += blockDim.x) sK[i] = rk[i];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  constexpr int nwarps = kAsmThreads / 32;
+  const int nwarps = blockDim.x >> 5;
   for (int g = t.seg_begin; g < t.seg_end; ++g) {
     const AsmSeg sg = segs[g];
     const SnodeDev dj = sn[sg.J];
@@ -369,6 +374,42 @@ k_assemble(const AsmTask* __restrict__ tasks, const AsmSeg* __restrict__ segs,
   }
 }
 
+__global__ void __launch_bounds__(kAsmThreads)
+k_assemble(const AsmTask* __restrict__ tasks, const AsmSeg* __restrict__ segs,
+           const SnodeDev* __restrict__ sn, const int32_t* __restrict__ rows,
+           const double* __restrict__ U, double* __restrict__ L) {
+  extern __shared__ int32_t ssm[];
+  assemble_body(tasks[blockIdx.x], segs, sn, rows, U, L, ssm);
+}
+
+// Persistent form for problems whose supernodes all take the one-CTA kernel
+// (e.g. batches of small systems): one cooperative launch walks every level,
+// grid-wide barriers separating the factor step of a level from its assembly
+// and the assembly from the next level. The per-supernode and per-task work is
+// the same code as the level-by-level kernels, so the results are identical.
+template <int NT>
+__global__ void __launch_bounds__(NT)
+k_persist_factor(const SnodeDev* __restrict__ sn, const int32_t* __restrict__ small_list,
+                 const AsmTask* __restrict__ tasks, const AsmSeg* __restrict__ segs,
+                 const int32_t* __restrict__ rows, const PersistLevel* __restrict__ lv, int nlevels,
+                 double* __restrict__ L, double* __restrict__ U, int* status) {
+  extern __shared__ double psm[];
+  cg::grid_group grid = cg::this_grid();
+  for (int l = 0; l < nlevels; ++l) {
+    const PersistLevel p = lv[l];
+    for (int i = blockIdx.x; i < p.small_n; i += gridDim.x) {
+      __syncthreads();
+      small_body(sn[small_list[p.small_b + i]], L, U, status, psm);
+    }
+    grid.sync();
+    for (int i = blockIdx.x; i < p.asm_n; i += gridDim.x) {
+      __syncthreads();
+      assemble_body(tasks[p.asm_b + i], segs, sn, rows, U, L, reinterpret_cast<int32_t*>(psm));
+    }
+    grid.sync();
+  }
+}
+
 // log det: per-supernode partial sums, then one fixed-order reduction.
 __global__ void k_logdet_part(const SnodeDev* __restrict__ sn, const double* __restrict__ L,
                               double* __restrict__ part) {
@@ -383,6 +424,16 @@ __global__ void k_logdet_part(const SnodeDev* __restrict__ sn, const double* __r
     __syncthreads();
   }
   if (threadIdx.x == 0) part[blockIdx.x] = red[0];
+}
+
+// log det of every system: 2 x the supernode partials of its range, in order.
+__global__ void k_logdet_sys(const double* __restrict__ part, const int32_t* __restrict__ sys_snode, int count,
+                             double* __restrict__ out) {
+  const int q = blockIdx.x * blockDim.x + threadIdx.x;
+  if (q >= count) return;
+  double acc = 0.0;
+  for (int J = sys_snode[q]; J < sys_snode[q + 1]; ++J) acc += part[J];
+  out[q] = 2.0 * acc;
 }
 
 __global__ void k_logdet_reduce(const double* __restrict__ part, int ns, double* out) {
@@ -498,7 +549,8 @@ void chol_device_free(chol_handle* h) {
   if (D->device >= 0) cudaSetDevice(D->device);
   void* ptrs[] = {D->L, D->U, D->sn, D->rows, D->amap, D->small_list, D->potrf_list,
                   D->level_snodes, D->trsm, D->gemm, D->syrk, D->asm_tasks, D->asm_segs, D->sdiag,
-                  D->fupd, D->bupd, D->bpanel, D->gemv, D->bpart, D->bred, D->P32, D->perm, D->status, D->part, D->scalar_dev, D->Y, D->W,
+                  D->fupd, D->bupd, D->bpanel, D->gemv, D->bpart, D->bred, D->P32, D->plevels, D->vals, D->sys_snode, D->sys_out,
+                  D->perm, D->status, D->part, D->scalar_dev, D->Y, D->W,
                   D->mx_diagpos, D->mx_aij, D->mx_d, D->mx_fallbacks, D->csr_ptr, D->csr_col, D->csr_src,
                   D->csr_val, D->Lbf, D->tmaps, D->tc_err, D->R, D->Z, D->Pv, D->Q, D->red, D->Y32, D->W32,
                   D->rhs_scale};
@@ -507,6 +559,10 @@ void chol_device_free(chol_handle* h) {
   if (D->status_host) cudaFreeHost(D->status_host);
   if (D->scalar_host) cudaFreeHost(D->scalar_host);
   if (D->red_host) cudaFreeHost(D->red_host);
+  if (D->graph_exec) cudaGraphExecDestroy(D->graph_exec);
+  if (D->gstream) cudaStreamDestroy(D->gstream);
+  for (cudaEvent_t e : D->gev)
+    if (e) cudaEventDestroy(e);
   if (cur >= 0) cudaSetDevice(cur);
   delete D;
   h->dev = nullptr;
@@ -558,6 +614,7 @@ int chol_device_ensure(chol_handle* h) {
   if ((rc = upload(h, &D->gemv, h->gemv_tasks))) return fail(rc);
   if ((rc = upload(h, &D->bpart, h->bpart_tasks))) return fail(rc);
   if ((rc = upload(h, &D->bred, h->bred_tasks))) return fail(rc);
+  if ((rc = upload(h, &D->plevels, h->persist_levels))) return fail(rc);
   if ((rc = upload(h, &D->perm, h->perm))) return fail(rc);
   if ((rc = chol_dalloc(h, (void**)&D->status, sizeof(int32_t)))) return fail(rc);
   if ((rc = chol_dalloc(h, (void**)&D->part, sizeof(double) * (size_t)std::max(h->ns, 1)))) return fail(rc);
@@ -568,22 +625,19 @@ int chol_device_ensure(chol_handle* h) {
   if (!attrs_done) {
     if (cudaFuncSetAttribute(k_assemble, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024) != cudaSuccess)
       return fail(CHOL_ECUDA);
+    if (cudaFuncSetAttribute(k_small, cudaFuncAttributeMaxDynamicSharedMemorySize, 16384 * 8) != cudaSuccess)
+      return fail(CHOL_ECUDA);
     attrs_done = true;
   }
   return CHOL_OK;
 }
 
-extern "C" int chol_factor(chol_handle* h, const double* values, void* stream) {
-  if (!h) return -1;
-  if (!values && h->nnz_a > 0) return -2;
-  if ((int64_t)h->max_len * 2 * (int64_t)sizeof(int32_t) > 200 * 1024) return CHOL_ENOTSUP;
-  int rc = chol_device_ensure(h);
-  if (rc) return rc;
+namespace {
+
+// Enqueue the binary64 factorization (no synchronization).
+int enqueue_factor_fp64(chol_handle* h, const double* values, cudaStream_t st) {
   DeviceState* D = h->dev;
-  cudaStream_t st = (cudaStream_t)stream;
-  if (h->opt.precision != CHOL_PREC_FP64) return chol_factor_mixed(h, values, st);
   const int nb = h->opt.block_cols;
-  h->factored = false;
   k_status_init<<<1, 1, 0, st>>>(D->status);
   CHOL_CUDA_TRY(cudaMemsetAsync(D->L, 0, sizeof(double) * (size_t)h->panel_doubles, st));
   if (h->nnz_a > 0) {
@@ -592,6 +646,13 @@ extern "C" int chol_factor(chol_handle* h, const double* values, void* stream) {
     // binary64 copy of A in CSR order for residuals (chol_solve_refine)
     const int64_t m = h->csr_ptr[h->n];
     k_gather_src<<<grid1d(m, 256), 256, 0, st>>>(values, D->csr_src, m, D->csr_val);
+  }
+  if (h->opt.persistent) {
+    if (h->n_large > 0) return CHOL_ENOTSUP;
+    double fl = 0.0, by = 0.0;
+    for (const LevelPlan& P : h->levels) { fl += P.small_flops; by += P.small_bytes; }
+    KScope ks(h, CHOL_K_SMALL, st, fl, by);
+    return chol_launch_persistent(h, (void*)D->L, (void*)D->U, st);
   }
   for (const LevelPlan& P : h->levels) {
     if (P.small_n > 0) {
@@ -627,11 +688,226 @@ extern "C" int chol_factor(chol_handle* h, const double* values, void* stream) {
     }
   }
   CHOL_CUDA_TRY(cudaGetLastError());
+  return CHOL_OK;
+}
+
+int enqueue_factor(chol_handle* h, const double* values, cudaStream_t st) {
+  return h->opt.precision == CHOL_PREC_FP64 ? enqueue_factor_fp64(h, values, st)
+                                            : chol_enqueue_factor_mixed(h, values, st);
+}
+
+void drop_graph(chol_handle* h) {
+  DeviceState* D = h->dev;
+  if (D && D->graph_exec) {
+    cudaGraphExecDestroy(D->graph_exec);
+    D->graph_exec = nullptr;
+  }
+}
+
+}  // namespace
+
+// The one-CTA-per-supernode levels in a single cooperative launch.
+int chol_launch_persistent(chol_handle* h, void* L, void* U, cudaStream_t st) {
+  DeviceState* D = h->dev;
+  const bool fp64 = h->opt.precision == CHOL_PREC_FP64;
+  const size_t esz = fp64 ? sizeof(double) : sizeof(float);
+  const size_t smem = std::max(esz * (size_t)std::max(h->small_panel_max, 1),
+                               sizeof(int32_t) * 2 * (size_t)std::max(h->max_len, 1)) + 64;
+  const int threads = h->persist_threads == 256 ? 256 : 128;
+  const void* fn = chol_persistent_kernel(h->opt.precision, threads);
+  if (!fn) return CHOL_ENOTSUP;
+  CHOL_CUDA_TRY(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  int per_sm = 0, sms = 0;
+  CHOL_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, threads, smem));
+  CHOL_CUDA_TRY(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, D->device));
+  if (per_sm < 1) return CHOL_ENOTSUP;
+  if (h->persist_ctas > 0) per_sm = std::min(per_sm, h->persist_ctas);
+  const int grid = per_sm * sms;
+  int nlevels = h->nlevels;
+  D->mx_spiv = h->opt.static_pivot ? (float)h->opt.pivot_tau : 0.f;
+  void* args[] = {(void*)&D->sn, (void*)&D->small_list, (void*)&D->asm_tasks, (void*)&D->asm_segs,
+                  (void*)&D->rows, (void*)&D->plevels, (void*)&nlevels, (void*)&L, (void*)&U,
+                  (void*)&D->status, (void*)&D->mx_spiv, (void*)&D->mx_fallbacks};
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(grid);
+  cfg.blockDim = dim3(threads);
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = st;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeCooperative;
+  attr[0].val.cooperative = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  CHOL_CUDA_TRY(cudaLaunchKernelExC(&cfg, fn, args));
+  return CHOL_OK;
+}
+
+const void* chol_persistent_kernel(int precision, int threads) {
+  if (precision == CHOL_PREC_FP64)
+    return threads == 256 ? (const void*)k_persist_factor<256> : (const void*)k_persist_factor<128>;
+  return chol_persistent_kernel_mixed(threads);
+}
+
+extern "C" int chol_factor(chol_handle* h, const double* values, void* stream) {
+  if (!h) return -1;
+  if (!values && h->nnz_a > 0) return -2;
+  if ((int64_t)h->max_len * 2 * (int64_t)sizeof(int32_t) > 200 * 1024) return CHOL_ENOTSUP;
+  int rc = chol_device_ensure(h);
+  if (rc) return rc;
+  DeviceState* D = h->dev;
+  cudaStream_t st = (cudaStream_t)stream;
+  h->factored = false;
+  if (h->opt.precision != CHOL_PREC_FP64 && (rc = chol_mixed_ensure(h))) return rc;
+  if (h->opt.use_graph) {
+    // replay a graph of the whole launch sequence; the values go through a copy
+    // owned by the handle so that the captured pointers stay valid. Capture and
+    // replay run on a stream of the handle (any caller stream can be captured
+    // from that way, the legacy default stream included), joined to the
+    // caller's stream with events on both sides.
+    if (!D->gstream) {
+      CHOL_CUDA_TRY(cudaStreamCreateWithFlags(&D->gstream, cudaStreamNonBlocking));
+      CHOL_CUDA_TRY(cudaEventCreateWithFlags(&D->gev[0], cudaEventDisableTiming));
+      CHOL_CUDA_TRY(cudaEventCreateWithFlags(&D->gev[1], cudaEventDisableTiming));
+    }
+    const cudaStream_t caller = st;
+    CHOL_CUDA_TRY(cudaEventRecord(D->gev[0], caller));
+    CHOL_CUDA_TRY(cudaStreamWaitEvent(D->gstream, D->gev[0], 0));
+    st = D->gstream;
+    if (!D->vals && h->nnz_a > 0) {
+      if ((rc = chol_dalloc(h, (void**)&D->vals, sizeof(double) * (size_t)h->nnz_a))) return rc;
+    }
+    if (h->nnz_a > 0)
+      CHOL_CUDA_TRY(cudaMemcpyAsync(D->vals, values, sizeof(double) * (size_t)h->nnz_a, cudaMemcpyDeviceToDevice, st));
+    Profiler* pr = chol_prof(h);
+    if (!D->graph_exec) {
+      chol_prof_resolve(h);
+      chol_kernel_stat before[CHOL_K_NCLASSES];
+      std::memcpy(before, pr->st, sizeof(before));
+      const uint32_t mask = pr->mask;
+      pr->mask = 0;   // no event timing inside the captured sequence
+      cudaGraph_t graph = nullptr;
+      CHOL_CUDA_TRY(cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal));
+      rc = enqueue_factor(h, D->vals, st);
+      const cudaError_t ce = cudaStreamEndCapture(st, &graph);
+      pr->mask = mask;
+      if (rc) { if (graph) cudaGraphDestroy(graph); return rc; }
+      if (ce != cudaSuccess) { cudaGetLastError(); return CHOL_ECUDA; }
+      const cudaError_t ie = cudaGraphInstantiate(&D->graph_exec, graph, 0);
+      cudaGraphDestroy(graph);
+      if (ie != cudaSuccess) { cudaGetLastError(); D->graph_exec = nullptr; return CHOL_ECUDA; }
+      for (int c = 0; c < CHOL_K_NCLASSES; ++c) {     // per-replay launch accounting
+        D->graph_delta[c].launches = pr->st[c].launches - before[c].launches;
+        D->graph_delta[c].flops = pr->st[c].flops - before[c].flops;
+        D->graph_delta[c].bytes = pr->st[c].bytes - before[c].bytes;
+      }
+      std::memcpy(pr->st, before, sizeof(before));
+    }
+    CHOL_CUDA_TRY(cudaGraphLaunch(D->graph_exec, st));
+    for (int c = 0; c < CHOL_K_NCLASSES; ++c) {
+      pr->st[c].launches += D->graph_delta[c].launches;
+      pr->st[c].flops += D->graph_delta[c].flops;
+      pr->st[c].bytes += D->graph_delta[c].bytes;
+    }
+    CHOL_CUDA_TRY(cudaEventRecord(D->gev[1], st));
+    CHOL_CUDA_TRY(cudaStreamWaitEvent(caller, D->gev[1], 0));
+    st = caller;
+  } else {
+    if ((rc = enqueue_factor(h, values, st))) return rc;
+  }
+  return chol_finish_factor(h, st);
+}
+
+// Read the status word (and the mixed-mode counters) after a factorization.
+int chol_finish_factor(chol_handle* h, cudaStream_t st) {
+  DeviceState* D = h->dev;
+  CHOL_CUDA_TRY(cudaGetLastError());
   CHOL_CUDA_TRY(cudaMemcpyAsync(D->status_host, D->status, sizeof(int32_t), cudaMemcpyDeviceToHost, st));
+  if (h->opt.precision != CHOL_PREC_FP64)
+    CHOL_CUDA_TRY(cudaMemcpyAsync(&D->status_host[1], D->mx_fallbacks, 2 * sizeof(int32_t), cudaMemcpyDeviceToHost, st));
   CHOL_CUDA_TRY(cudaStreamSynchronize(st));
-  const int32_t s = *D->status_host;
+  if (h->opt.precision != CHOL_PREC_FP64) {
+    h->fp64_fallbacks = D->status_host[1];
+    h->perturbed_pivots = D->status_host[2];
+  }
+  const int32_t s = D->status_host[0];
   if (s != INT_MAX) return s;
+  if (h->opt.precision != CHOL_PREC_FP64) {
+    const int rc = chol_tc_status(h);
+    if (rc) return rc;
+  }
   h->factored = true;
+  return CHOL_OK;
+}
+
+extern "C" int chol_autotune(chol_handle* h, const double* values, void* stream) {
+  if (!h) return -1;
+  if (!values && h->nnz_a > 0) return -2;
+  cudaStream_t st = (cudaStream_t)stream;
+  struct Cand { int persistent, graph, threads, ctas; };
+  std::vector<Cand> cands = {{0, 0, 128, 0}, {0, 1, 128, 0}};
+  if (h->n_large == 0)
+    for (int t : {128, 256})
+      for (int c : {1, 2, 4, 0}) cands.push_back({1, 1, t, c});
+  float best = 1e30f;
+  Cand win = cands[0];
+  int rc = CHOL_OK;
+  cudaEvent_t e0, e1;
+  CHOL_CUDA_TRY(cudaEventCreate(&e0));
+  CHOL_CUDA_TRY(cudaEventCreate(&e1));
+  for (const Cand& c : cands) {
+    h->opt.persistent = c.persistent;
+    h->opt.use_graph = c.graph;
+    h->persist_threads = c.threads;
+    h->persist_ctas = c.ctas;
+    if (h->dev) drop_graph(h);
+    if ((rc = chol_factor(h, values, stream))) break;   // warm-up (and capture)
+    float tmin = 1e30f;
+    for (int rep = 0; rep < 2; ++rep) {
+      cudaEventRecord(e0, st);
+      if ((rc = chol_factor(h, values, stream))) break;
+      cudaEventRecord(e1, st);
+      cudaEventSynchronize(e1);
+      float ms = 0.f;
+      cudaEventElapsedTime(&ms, e0, e1);
+      tmin = std::min(tmin, ms);
+    }
+    if (rc) break;
+    if (tmin < best) { best = tmin; win = c; }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  h->opt.persistent = win.persistent;
+  h->opt.use_graph = win.graph;
+  h->persist_threads = win.threads;
+  h->persist_ctas = win.ctas;
+  if (h->dev) drop_graph(h);
+  if (rc) return rc;
+  return chol_factor(h, values, stream);
+}
+
+extern "C" int chol_logdet_batch(chol_handle* h, double* out, void* stream) {
+  if (!h) return -1;
+  if (!out) return -2;
+  if (!h->factored) return CHOL_ESTATE;
+  DeviceState* D = h->dev;
+  cudaStream_t st = (cudaStream_t)stream;
+  const int count = (int)h->sys_ptr.size() - 1;
+  if (count <= 0) return CHOL_OK;
+  int rc;
+  if (!D->sys_snode) {
+    if ((rc = upload(h, &D->sys_snode, h->sys_snode_ptr))) return rc;
+    if ((rc = chol_dalloc(h, (void**)&D->sys_out, sizeof(double) * (size_t)count))) return rc;
+  }
+  if (h->ns > 0) {
+    if (h->opt.precision == CHOL_PREC_FP64)
+      k_logdet_part<<<h->ns, 128, 0, st>>>(D->sn, D->L, D->part);
+    else if ((rc = chol_logdet_parts_mixed(h, st)))
+      return rc;
+  }
+  k_logdet_sys<<<(count + 127) / 128, 128, 0, st>>>(D->part, D->sys_snode, count, D->sys_out);
+  CHOL_CUDA_TRY(cudaGetLastError());
+  CHOL_CUDA_TRY(cudaMemcpyAsync(out, D->sys_out, sizeof(double) * (size_t)count, cudaMemcpyDeviceToHost, st));
+  CHOL_CUDA_TRY(cudaStreamSynchronize(st));
   return CHOL_OK;
 }
 

@@ -63,6 +63,11 @@ struct LevelPlan {
   double small_bytes;
 };
 
+// One level of the persistent (cooperative) factorization.
+struct PersistLevel {
+  int32_t small_b, small_n, asm_b, asm_n;
+};
+
 struct DeviceState;  // defined in the CUDA driver
 struct Profiler;     // defined in the CUDA driver
 
@@ -110,6 +115,13 @@ struct chol_handle {
   std::vector<AsmSeg> asm_segs;
   int32_t n_small = 0, n_large = 0;
   int32_t solve_sb = 256;       // solve super-step (set by the analysis)
+  // batches and launch configuration
+  std::vector<int32_t> sys_ptr;       // count+1 column offsets of the systems
+  std::vector<int32_t> sys_snode_ptr; // count+1 storage-supernode offsets of the systems
+  std::vector<PersistLevel> persist_levels;
+  int32_t small_panel_max = 0;        // largest len*s on the one-CTA kernel
+  int32_t persist_threads = 128;      // chosen by chol_autotune
+  int32_t persist_ctas = 0;           // CTAs per SM (0 = as many as fit)
   // numeric state
   bool factored = false;
   DeviceState* dev = nullptr;

@@ -17,10 +17,13 @@
 #include <cmath>
 #include <cstring>
 
+#include <cooperative_groups.h>
 #include <cuda_bf16.h>
 
 #include "device.h"
 #include "mixed.h"
+
+namespace cg = cooperative_groups;
 
 namespace {
 
@@ -74,11 +77,8 @@ __device__ void dense_chol_rowmajor(T* P, int len, int s, int fcol, int* status,
 
 // One CTA per small supernode: binary32 panel in shared memory, U_J row-major
 // lower (row u holds columns c <= u, leading dimension ldu = b rounded to 8).
-__global__ void __launch_bounds__(128)
-k_mx_small(const SnodeDev* __restrict__ sn, const int32_t* __restrict__ list, float* __restrict__ L,
-           float* __restrict__ U, int* status, float spiv, int* counters) {
-  extern __shared__ float Pf[];
-  const SnodeDev d = sn[list[blockIdx.x]];
+__device__ __forceinline__ void mx_small_body(const SnodeDev& d, float* __restrict__ L, float* __restrict__ U,
+                                              int* status, float spiv, int* counters, float* Pf) {
   const int len = d.len, s = d.s, b = len - s;
   float* G = L + d.loff;
   for (int q = threadIdx.x; q < len * s; q += blockDim.x) Pf[q] = G[(int64_t)(q / s) * d.ld + q % s];
@@ -101,6 +101,13 @@ k_mx_small(const SnodeDev* __restrict__ sn, const int32_t* __restrict__ list, fl
     for (int k = 0; k < s; ++k) acc = fmaf(R[u * s + k], R[c * s + k], acc);
     Uj[(int64_t)u * ldu + c] = acc;
   }
+}
+
+__global__ void __launch_bounds__(128)
+k_mx_small(const SnodeDev* __restrict__ sn, const int32_t* __restrict__ list, float* __restrict__ L,
+           float* __restrict__ U, int* status, float spiv, int* counters) {
+  extern __shared__ float Pf[];
+  mx_small_body(sn[list[blockIdx.x]], L, U, status, spiv, counters, Pf);
 }
 
 // Register-blocked Cholesky of a kb x kb (kb <= 64) row-major block, 256
@@ -354,20 +361,17 @@ k_mx_syrk_simt(const SnodeDev* __restrict__ sn, const TileTask* __restrict__ tas
 // K and its columns [t0, t1); per segment the positions of J's rows in struct(K)
 // are found by binary search in shared memory, then warps walk the rows u of
 // U_J (row-major lower) and lanes the columns c <= u of the segment.
-__global__ void __launch_bounds__(kMxThreads)
-k_mx_assemble(const AsmTask* __restrict__ tasks, const AsmSeg* __restrict__ segs,
-              const SnodeDev* __restrict__ sn, const int32_t* __restrict__ rows,
-              const float* __restrict__ U, float* __restrict__ L) {
-  extern __shared__ int32_t ssm[];
+__device__ __forceinline__ void mx_assemble_body(const AsmTask& t, const AsmSeg* __restrict__ segs,
+                                                 const SnodeDev* __restrict__ sn, const int32_t* __restrict__ rows,
+                                                 const float* __restrict__ U, float* __restrict__ L, int32_t* ssm) {
   __shared__ int32_t tcol[kAsmCols];
-  const AsmTask t = tasks[blockIdx.x];
   const SnodeDev dk = sn[t.K];
   int32_t* sK = ssm;
   int32_t* pos = ssm + dk.len;
   const int32_t* rk = rows + dk.roff;
   for (int i = threadIdx.x; i < dk.len; i += blockDim.x) sK[i] = rk[i];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  constexpr int nwarps = kMxThreads / 32;
+  const int nwarps = blockDim.x >> 5;
   for (int g = t.seg_begin; g < t.seg_end; ++g) {
     const AsmSeg sg = segs[g];
     const SnodeDev dj = sn[sg.J];
@@ -393,6 +397,39 @@ k_mx_assemble(const AsmTask* __restrict__ tasks, const AsmSeg* __restrict__ segs
       const int cend = min(sg.cb, u + 1);
       for (int c = sg.ca + lane; c < cend; c += 32) Lr[tcol[c - sg.ca]] -= Ur[c];
     }
+  }
+}
+
+__global__ void __launch_bounds__(kMxThreads)
+k_mx_assemble(const AsmTask* __restrict__ tasks, const AsmSeg* __restrict__ segs,
+              const SnodeDev* __restrict__ sn, const int32_t* __restrict__ rows,
+              const float* __restrict__ U, float* __restrict__ L) {
+  extern __shared__ int32_t ssm[];
+  mx_assemble_body(tasks[blockIdx.x], segs, sn, rows, U, L, ssm);
+}
+
+// Persistent form of the one-CTA levels (binary32 panels), see the binary64
+// k_persist_factor.
+template <int NT>
+__global__ void __launch_bounds__(NT)
+k_persist_factor_mx(const SnodeDev* __restrict__ sn, const int32_t* __restrict__ small_list,
+                    const AsmTask* __restrict__ tasks, const AsmSeg* __restrict__ segs,
+                    const int32_t* __restrict__ rows, const PersistLevel* __restrict__ lv, int nlevels,
+                    float* __restrict__ L, float* __restrict__ U, int* status, float spiv, int* counters) {
+  extern __shared__ float psmf[];
+  cg::grid_group grid = cg::this_grid();
+  for (int l = 0; l < nlevels; ++l) {
+    const PersistLevel p = lv[l];
+    for (int i = blockIdx.x; i < p.small_n; i += gridDim.x) {
+      __syncthreads();
+      mx_small_body(sn[small_list[p.small_b + i]], L, U, status, spiv, counters, psmf);
+    }
+    grid.sync();
+    for (int i = blockIdx.x; i < p.asm_n; i += gridDim.x) {
+      __syncthreads();
+      mx_assemble_body(tasks[p.asm_b + i], segs, sn, rows, U, L, reinterpret_cast<int32_t*>(psmf));
+    }
+    grid.sync();
   }
 }
 
@@ -473,19 +510,19 @@ int chol_mixed_ensure(chol_handle* h) {
   if ((rc = chol_tc_prepare(h))) return rc;
   if (cudaFuncSetAttribute(k_mx_assemble, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024) != cudaSuccess)
     return CHOL_ECUDA;
+  if (cudaFuncSetAttribute(k_mx_small, cudaFuncAttributeMaxDynamicSharedMemorySize, 16384 * 4) != cudaSuccess)
+    return CHOL_ECUDA;
   D->mx_ready = true;
   return CHOL_OK;
 }
 
-int chol_factor_mixed(chol_handle* h, const double* values, cudaStream_t st) {
-  int rc = chol_mixed_ensure(h);
-  if (rc) return rc;
+int chol_enqueue_factor_mixed(chol_handle* h, const double* values, cudaStream_t st) {
+  int rc = CHOL_OK;
   DeviceState* D = h->dev;
   float* L = (float*)D->L;
   float* U = (float*)D->U;
   const int nb = h->opt.block_cols;
   const bool tc = h->opt.precision == CHOL_PREC_TF32 || h->opt.precision == CHOL_PREC_BF16;
-  h->factored = false;
   chol_status_init(D->status, st);
   CHOL_CUDA_TRY(cudaMemsetAsync(D->mx_fallbacks, 0, 2 * sizeof(int32_t), st));
   const float spiv = h->opt.static_pivot ? (float)h->opt.pivot_tau : 0.f;
@@ -499,6 +536,13 @@ int chol_factor_mixed(chol_handle* h, const double* values, cudaStream_t st) {
     k_mx_scatter<<<grid1d(h->nnz_a, 256), 256, 0, st>>>(values, D->amap, D->mx_aij, D->mx_d, h->nnz_a, L);
     const int64_t m = h->csr_ptr[h->n];
     k_mx_gather_vals<<<grid1d(m, 256), 256, 0, st>>>(values, D->csr_src, m, D->csr_val);
+  }
+  if (h->opt.persistent) {
+    if (h->n_large > 0) return CHOL_ENOTSUP;
+    double fl = 0.0, by = 0.0;
+    for (const LevelPlan& P : h->levels) { fl += P.small_flops; by += P.small_bytes / 2; }
+    KScope ks(h, CHOL_K_SMALL, st, fl, by);
+    return chol_launch_persistent(h, (void*)L, (void*)U, st);
   }
   for (const LevelPlan& P : h->levels) {
     if (P.small_n > 0) {
@@ -543,17 +587,17 @@ int chol_factor_mixed(chol_handle* h, const double* values, cudaStream_t st) {
     }
   }
   CHOL_CUDA_TRY(cudaGetLastError());
-  int32_t fb = 0;
-  CHOL_CUDA_TRY(cudaMemcpyAsync(D->status_host, D->status, sizeof(int32_t), cudaMemcpyDeviceToHost, st));
-  CHOL_CUDA_TRY(cudaMemcpyAsync(&D->status_host[1], D->mx_fallbacks, 2 * sizeof(int32_t), cudaMemcpyDeviceToHost, st));
-  CHOL_CUDA_TRY(cudaStreamSynchronize(st));
-  fb = D->status_host[1];
-  h->fp64_fallbacks = fb;
-  h->perturbed_pivots = D->status_host[2];
-  const int32_t s = D->status_host[0];
-  if (s != INT_MAX) return s;
-  if ((rc = chol_tc_status(h))) return rc;
-  h->factored = true;
+  return CHOL_OK;
+}
+
+const void* chol_persistent_kernel_mixed(int threads) {
+  return threads == 256 ? (const void*)k_persist_factor_mx<256> : (const void*)k_persist_factor_mx<128>;
+}
+
+int chol_logdet_parts_mixed(chol_handle* h, cudaStream_t st) {
+  DeviceState* D = h->dev;
+  k_mx_logdet_part<<<h->ns, 128, 0, st>>>(D->sn, (const float*)D->L, D->mx_d, D->part);
+  CHOL_CUDA_TRY(cudaGetLastError());
   return CHOL_OK;
 }
 

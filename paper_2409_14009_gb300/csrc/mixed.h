@@ -6,7 +6,12 @@
 #include "internal.h"
 
 int chol_mixed_ensure(chol_handle* h);
-int chol_factor_mixed(chol_handle* h, const double* values, cudaStream_t st);
+int chol_enqueue_factor_mixed(chol_handle* h, const double* values, cudaStream_t st);
+int chol_finish_factor(chol_handle* h, cudaStream_t st);
+int chol_launch_persistent(chol_handle* h, void* L, void* U, cudaStream_t st);
+const void* chol_persistent_kernel(int precision, int threads);
+const void* chol_persistent_kernel_mixed(int threads);
+int chol_logdet_parts_mixed(chol_handle* h, cudaStream_t st);
 int chol_logdet_mixed(chol_handle* h, double* out, cudaStream_t st);
 int chol_gather_mixed(chol_handle* h, const int64_t* dmap, const int32_t* dlrow, double* dlx, cudaStream_t st);
 int chol_solve_mixed(chol_handle* h, double* b, int32_t nrhs, cudaStream_t st);

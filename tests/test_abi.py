@@ -158,3 +158,26 @@ def test_relaxed_merging_matches_oracle(case, growth):
     assert info.nnz_stored <= (1.0 + growth) * info.nnz_l
     # the canonical outputs do not change with merging
     assert np.array_equal(canon["snode_ptr"], sym.supernodes()[0])
+
+
+def test_analyze_batch_validation_and_symbolic():
+    P = chol()
+    probs = gridgen.batch_2d(count=5, kmin=3, kmax=7, seed=4)
+    bd = gridgen.block_diagonal(probs)
+    offs = bd["meta"]["offsets"].astype(np.int32)
+    rc, h = P.chol_analyze_batch(5, offs, bd["colptr"], bd["rowind"], bd["perm"])
+    assert rc == 0
+    info = P.chol_get_info(h)
+    assert info.nsys == 5
+    got = P.chol_get_symbolic(h)
+    P.chol_destroy(h)
+    bp, bi, _ = oracle.permute(bd.n, bd["colptr"], bd["rowind"], None, bd["perm"])
+    sym = oracle.Symbolic(bd.n, bp, bi)
+    assert np.array_equal(got["parent"], sym.parent)
+    # a bad sys_ptr, an entry coupling two systems, a permutation across systems
+    bad = offs.copy(); bad[2] = bad[1] - 1
+    assert P.chol_analyze_batch(5, bad, bd["colptr"], bd["rowind"], bd["perm"])[0] == -2
+    wrong = offs.copy(); wrong[1] += 1
+    assert P.chol_analyze_batch(5, wrong, bd["colptr"], bd["rowind"], bd["perm"])[0] == -4
+    perm = bd["perm"].copy(); perm[[0, offs[1]]] = perm[[offs[1], 0]]
+    assert P.chol_analyze_batch(5, offs, bd["colptr"], bd["rowind"], perm)[0] == -4

@@ -1,0 +1,113 @@
+"""Batches of independent small SPD systems (2D weighted Laplacians of uneven
+sizes): one block-diagonal analysis, level-by-level or persistent cooperative
+execution, CUDA-graph replay, the launch autotuner, per-system logdet; FP64 and
+binary32 (+ refinement), against the oracle system by system."""
+import numpy as np
+import pytest
+
+import gridgen
+import oracle
+from gpu_util import colmajor, to_dev
+from lib_fixture import chol
+
+pytestmark = pytest.mark.gpu
+
+
+def _batch(count=60, kmin=4, kmax=28, seed=4):
+    probs = gridgen.batch_2d(count=count, kmin=kmin, kmax=kmax, seed=seed)
+    return probs, gridgen.block_diagonal(probs)
+
+
+def _opts(P, precision=0, persistent=0, graph=0):
+    o = P.chol_default_options()
+    o.precision, o.persistent, o.use_graph = precision, persistent, graph
+    o.small_max_cols, o.small_max_panel, o.small_max_rows = 128, 16384, 512
+    return o
+
+
+def _run(P, bd, o, b):
+    import torch
+    offs = bd["meta"]["offsets"].astype(np.int32)
+    rc, h = P.chol_analyze_batch(len(offs) - 1, offs, bd["colptr"], bd["rowind"], bd["perm"], o)
+    assert rc == 0, rc
+    info = P.chol_get_info(h)
+    vals = to_dev(bd["values"])
+    assert P.chol_factor(h, vals) == 0
+    assert P.chol_factor(h, vals) == 0           # second call: graph replay when enabled
+    lx = P.chol_get_factor(h)[2]
+    X = colmajor(b)
+    if o.precision == 0:
+        assert P.chol_solve(h, X, b.shape[1]) == 0
+        rcr = 0
+    else:
+        B = colmajor(b)
+        rcr, iters, berr = P.chol_solve_refine(h, B, X, b.shape[1], 1e-10, 50)
+    torch.cuda.synchronize()
+    rc, lds = P.chol_logdet_batch(h, len(offs) - 1)
+    assert rc == 0
+    stats = P.chol_get_stats(h)
+    P.chol_destroy(h)
+    return dict(info=info, lx=lx, x=X.cpu().numpy(), logdet=lds, rc_refine=rcr, stats=stats)
+
+
+@pytest.mark.parametrize("persistent,graph", [(0, 0), (1, 0), (0, 1), (1, 1)])
+def test_batch_fp64_per_system(persistent, graph):
+    P = chol()
+    probs, bd = _batch()
+    b = gridgen.rhs_uniform(bd.n, 1, seed=7)
+    got = _run(P, bd, _opts(P, 0, persistent, graph), b)
+    assert got["info"].nsys == len(probs) and got["info"].persistent_ok == 1
+    offs = bd["meta"]["offsets"]
+    for q, p in enumerate(probs):
+        bq = b[offs[q]:offs[q + 1]]
+        ref = oracle.reference(p, bq)
+        xq = got["x"][offs[q]:offs[q + 1]]
+        assert np.max(np.abs(xq - ref["x"])) <= 1e-11 * np.max(np.abs(ref["x"]))
+        assert abs(got["logdet"][q] - ref["fac"].logdet()) <= 1e-12 * abs(ref["fac"].logdet())
+    if persistent:
+        assert got["stats"]["small"]["launches"] == 2        # one persistent launch per factorization
+        assert got["stats"]["assemble"]["launches"] == 0
+
+
+def test_batch_persistent_is_bitwise_identical():
+    P = chol()
+    probs, bd = _batch(count=40)
+    b = gridgen.rhs_uniform(bd.n, 1, seed=8)
+    a = _run(P, bd, _opts(P, 0, 0, 0), b)
+    c = _run(P, bd, _opts(P, 0, 1, 1), b)
+    assert np.array_equal(a["lx"], c["lx"]) and np.array_equal(a["x"], c["x"])
+
+
+@pytest.mark.parametrize("persistent", [0, 1])
+def test_batch_fp32_refined(persistent):
+    P = chol()
+    probs, bd = _batch(count=50, kmin=6, kmax=40, seed=9)
+    b = gridgen.rhs_uniform(bd.n, 1, seed=9)
+    got = _run(P, bd, _opts(P, 1, persistent, 1), b)
+    assert got["rc_refine"] == 0
+    eta = oracle.backward_error(bd.n, bd["colptr"], bd["rowind"], bd["values"], b, got["x"])
+    assert eta[0] <= 1e-10
+    offs = bd["meta"]["offsets"]
+    for q, p in enumerate(probs[:10]):
+        ref = oracle.reference(p)
+        assert abs(got["logdet"][q] - ref["fac"].logdet()) <= 1e-5 * abs(ref["fac"].logdet())
+
+
+def test_autotune_keeps_a_valid_configuration():
+    import torch
+    P = chol()
+    probs, bd = _batch(count=80, kmin=8, kmax=48, seed=11)
+    offs = bd["meta"]["offsets"].astype(np.int32)
+    rc, h = P.chol_analyze_batch(len(offs) - 1, offs, bd["colptr"], bd["rowind"], bd["perm"], _opts(P))
+    assert rc == 0
+    vals = to_dev(bd["values"])
+    assert P.chol_autotune(h, vals) == 0
+    info = P.chol_get_info(h)
+    assert info.persistent_threads in (128, 256)
+    b = gridgen.rhs_uniform(bd.n, 1, seed=1)
+    X = colmajor(b)
+    assert P.chol_solve(h, X, 1) == 0
+    torch.cuda.synchronize()
+    eta = oracle.backward_error(bd.n, bd["colptr"], bd["rowind"], bd["values"], b, X.cpu().numpy())
+    assert eta[0] <= 1e-14
+    P.chol_destroy(h)
