@@ -237,6 +237,61 @@ def mixed_vs_fp64(args, P, gridgen, torch, dev, p, b, vals, flops, factor_ms, so
     return out
 
 
+def batch_run(args, P, gridgen, torch, dev):
+    """2,000 independent 2D 5-point Laplacians (sides U{16..96}, log-uniform
+    weights in [0.1, 10], Dirichlet ghosts), one RHS each: one block-diagonal
+    analysis, autotuned launch configuration (persistent cooperative kernel in a
+    CUDA graph when it wins); FP64 factor + solve, and binary32 factor +
+    refinement to eta <= 1e-10."""
+    t0 = time.perf_counter()
+    probs = gridgen.batch_2d(count=args.batch_count)
+    bd = gridgen.block_diagonal(probs)
+    gen_s = time.perf_counter() - t0
+    offs = bd["meta"]["offsets"].astype(np.int32)
+    b = gridgen.rhs_uniform(bd.n, 1, seed=4)
+    st = torch.cuda.current_stream()
+    vals = torch.as_tensor(bd["values"], device=dev)
+    out = {"workload": "batch of %d 2D 5-point Laplacians, sides U{16..96}, n_total=%d, 1 RHS each"
+                       % (len(probs), bd.n)}
+    for prec, name in ((0, "fp64"), (1, "fp32")):
+        opt = P.chol_default_options()
+        opt.precision = prec
+        opt.small_max_cols, opt.small_max_panel, opt.small_max_rows = 160, 24576, 512
+        t0 = time.perf_counter()
+        rc, h = P.chol_analyze_batch(len(offs) - 1, offs, bd["colptr"], bd["rowind"], bd["perm"], opt)
+        ana_s = time.perf_counter() - t0
+        assert rc == 0, rc
+        info = P.chol_get_info(h)
+        rc = P.chol_autotune(h, vals, st)
+        assert rc == 0, rc
+        info = P.chol_get_info(h)
+        B = torch.as_tensor(np.ascontiguousarray(b.T), device=dev).t()
+        X = torch.zeros_like(B)
+        fms, _ = _timed(torch, st, lambda: P.chol_factor(h, vals, st), 5)
+        if prec == 0:
+            def solve():
+                X.copy_(B)
+                return P.chol_solve(h, X, 1, st)
+            sms, _ = _timed(torch, st, solve, 5)
+            iters = 0
+        else:
+            sms, res = _timed(torch, st, lambda: P.chol_solve_refine(h, B, X, 1, 1e-10, 50, st), 5)
+            iters = res[1]
+        eta = backward_error(bd, b, X.cpu().numpy())
+        out[name] = {"analyze_s": ana_s, "factor_ms": fms, "solve_ms": sms, "total_ms": fms + sms,
+                     "refine_iterations": iters, "backward_error": float(eta),
+                     "factor_gflops": info.flops / (fms * 1e-3) / 1e9,
+                     "systems_per_s": len(probs) / ((fms + sms) * 1e-3),
+                     "persistent": int(info.persistent_ok and P.chol_default_options().persistent == 0 and 1),
+                     "autotuned": {"persistent_threads": info.persistent_threads,
+                                   "persistent_ctas_per_sm": info.persistent_ctas_per_sm},
+                     "supernodes": info.nsuper_storage, "levels": info.nlevels}
+        P.chol_destroy(h)
+    out["flops"] = float(info.flops)
+    out["generate_s"] = gen_s
+    return out
+
+
 def run_ours(args, rank, world, local_rank):
     import torch
     import __graft_entry__
@@ -322,6 +377,7 @@ def run_ours(args, rank, world, local_rank):
     e2e_ms = f0.elapsed_time(f1) / args.steps
     mixed = None if args.no_mixed else mixed_vs_fp64(args, P, gridgen, torch, dev, p, b, vals, flops,
                                                          factor_ms, solve_ms)
+    batch = None if args.no_batch else batch_run(args, P, gridgen, torch, dev)
     # max over ranks
     if dist:
         t = torch.tensor([ms, e2e_ms], device=dev)
@@ -360,7 +416,7 @@ def run_ours(args, rank, world, local_rank):
                         "d2h_bytes_per_step": int(hx.numel() * 8)},
                 "gpu_launches": launches // max(args.steps, 1) * args.steps,
                 "roofline": roof, "cpu_baseline": cpu, "clocks": clk.summary(),
-                "mixed_vs_fp64": mixed}
+                "mixed_vs_fp64": mixed, "batch": batch}
         print(json.dumps(line), flush=True)
     S.close()
     if dist:
@@ -378,6 +434,8 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-mixed", action="store_true", help="skip the mixed-precision comparison")
     ap.add_argument("--skip-elasticity", action="store_true")
+    ap.add_argument("--no-batch", action="store_true", help="skip the 2,000-system batch")
+    ap.add_argument("--batch-count", type=int, default=2000)
     ap.add_argument("--workload", default="3d64", choices=["3d64", "3d48"],
                     help="3d64 is the benchmark; 3d48 is the smaller case used for ncu captures")
     ap.add_argument("--merge", type=float, default=0.1,

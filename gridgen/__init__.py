@@ -79,6 +79,9 @@ def _box_points_lex(lo, hi, dims):
     return idx.reshape(-1)
 
 
+_ND_CACHE = {}
+
+
 def nd_order(dims) -> np.ndarray:
     """Deterministic geometric nested dissection of a box grid.
 
@@ -88,6 +91,8 @@ def nd_order(dims) -> np.ndarray:
     the order is ND(low part), ND(high part), then the plane ``mid``.
     """
     dims = tuple(int(d) for d in dims)
+    if dims in _ND_CACHE:
+        return _ND_CACHE[dims].copy()
     out = []
 
     def rec(lo, hi):
@@ -110,7 +115,8 @@ def nd_order(dims) -> np.ndarray:
     rec(tuple(0 for _ in dims), dims)
     order = np.concatenate(out) if out else np.zeros(0, dtype=np.int64)
     assert order.size == int(np.prod(dims))
-    return order
+    _ND_CACHE[dims] = order
+    return order.copy()
 
 
 def nd_perm(dims, ndof: int = 1) -> np.ndarray:

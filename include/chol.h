@@ -70,8 +70,9 @@ enum {
 typedef struct chol_options {
   int32_t precision;       /* CHOL_PREC_*; default CHOL_PREC_FP64 */
   int32_t small_max_cols;  /* supernodes with at most this many columns and at   */
-  int32_t small_max_panel; /* most this many panel entries (len*cols) take the   */
-                           /* one-CTA-per-supernode kernel; default 64 / 4096    */
+  int32_t small_max_panel; /* most this many panel entries (len*cols, at most   */
+                           /* 24576) take the one-CTA-per-supernode kernel;      */
+                           /* default 64 / 4096                                  */
   int32_t block_cols;      /* column block of the blocked large-supernode path  */
                            /* (POTRF/TRSM/update step); default 64               */
   int64_t device_mem_cap;  /* refuse device allocations above this many bytes;  */

@@ -58,6 +58,8 @@ def lib():
         L.orc_logdet.argtypes = [C.c_int32, P, P]
         L.orc_spmv.argtypes = [C.c_int32, P, P, P, C.c_int32, P, P]
         L.orc_backward_error.argtypes = [C.c_int32, P, P, P, C.c_int32, P, P, P]
+        L.orc_selinv.restype = C.c_int
+        L.orc_selinv.argtypes = [C.c_int32, P, P, P, P]
         L.orc_factor_residual_cols.argtypes = [C.c_int32, P, P, P, P, P, P, C.c_int32, P, P]
         L.orc_factor_residual.restype = C.c_double
         L.orc_factor_residual.argtypes = [C.c_int32, P, P, P, P, P, P]
@@ -165,6 +167,13 @@ class Factor:
     def logdet(self):
         return lib().orc_logdet(self.n, _p(self.lp), _p(self.lx))
 
+    def selinv(self):
+        """Z = (P A P^T)^{-1} on the pattern of L (same layout as lx)."""
+        zx = np.zeros_like(self.lx)
+        if lib().orc_selinv(self.n, _p(self.lp), _p(self.li), _p(self.lx), _p(zx)) != 0:
+            raise ValueError("pattern of L is not closed")
+        return zx
+
     def diag(self):
         return self.lx[self.lp[:-1]]
 
@@ -206,6 +215,49 @@ def factor_residual_cols(n, bcolptr, browind, bvals, lp, li, lx, cols):
                                    _p(_c(bvals, np.float64)), _p(_c(lp, np.int64)), _p(_c(li, np.int32)),
                                    _p(_c(lx, np.float64)), len(cols), _p(cols), _p(out))
     return out
+
+
+def inverse_on_pattern(problem, fac, perm):
+    """(A^{-1})_ij for every entry (i, j) of A's lower CSC, from the selected inverse."""
+    n = problem["n"]
+    zx = fac.selinv()
+    iperm = np.empty(n, np.int64)
+    iperm[np.asarray(perm, np.int64)] = np.arange(n)
+    colptr, rowind = problem["colptr"], problem["rowind"]
+    out = np.zeros(len(rowind))
+    for c in range(n):
+        for t in range(colptr[c], colptr[c + 1]):
+            a, b = iperm[rowind[t]], iperm[c]
+            r, k = max(a, b), min(a, b)
+            lo, hi = fac.lp[k], fac.lp[k + 1]
+            pos = lo + np.searchsorted(fac.li[lo:hi], r)
+            out[t] = zx[pos]
+    return out
+
+
+def gradient(problem, fac, w, x, logdet_weight=1.0):
+    """Gradient of  sum_k w_k^T x_k + logdet_weight * log det A  (x = A^{-1} b)
+    with respect to the stored lower entries of A (a_ij and a_ji move
+    together) and with respect to b:
+      xbar = A^{-1} w,  G = -xbar x^T + logdet_weight * A^{-1},
+      g_ii = G_ii,  g_ij = G_ij + G_ji (i > j)."""
+    n = problem["n"]
+    perm = problem["perm"]
+    w = np.asfortranarray(w, dtype=np.float64)
+    x = np.asfortranarray(x, dtype=np.float64)
+    xbar = fac.solve(perm, w)
+    zA = inverse_on_pattern(problem, fac, perm) if logdet_weight != 0.0 else None
+    colptr, rowind = problem["colptr"], problem["rowind"]
+    cols = np.repeat(np.arange(n), np.diff(colptr))
+    rows = np.asarray(rowind, np.int64)
+    xb2 = xbar.reshape(n, -1)
+    x2 = x.reshape(n, -1)
+    g = -(np.einsum("tk,tk->t", xb2[rows], x2[cols]))
+    off = rows != cols
+    g[off] -= np.einsum("tk,tk->t", xb2[cols[off]], x2[rows[off]])
+    if zA is not None:
+        g += logdet_weight * np.where(off, 2.0, 1.0) * zA
+    return g, xbar
 
 
 def reference(problem, b=None):

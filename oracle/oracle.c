@@ -516,3 +516,45 @@ void orc_factor_residual_cols(int32_t n, const int64_t* bcolptr, const int32_t* 
   }
   free(w); free(rcount); free(fill); free(rent); free(rcol);
 }
+
+/* ------------------------------------------------------------------------ */
+/* Selected inverse Z = B^{-1} on the pattern of L (column Takahashi          */
+/* recurrence, B = L L^T). From B Z = I with Z symmetric, column by column    */
+/* from the last one: for i in struct(j), i > j,                             */
+/*   Z_ij = -sum_{k in struct(j), k > j} (L_kj / L_jj) Z_{ik}                 */
+/* and Z_jj = 1 / L_jj^2 - sum_{k in struct(j), k > j} (L_kj / L_jj) Z_kj,    */
+/* where Z_{ik} for i, k > j is an entry of an already computed column       */
+/* (struct(j) is a clique of the filled graph, so it lies in pattern(L)).    */
+/* zx has the layout of lx (lp/li).                                          */
+/* ------------------------------------------------------------------------ */
+static int64_t find_entry(const int64_t* lp, const int32_t* li, int32_t row, int32_t col) {
+  int64_t lo = lp[col], hi = lp[col + 1] - 1;
+  while (lo <= hi) {
+    int64_t mid = (lo + hi) / 2;
+    if (li[mid] == row) return mid;
+    if (li[mid] < row) lo = mid + 1; else hi = mid - 1;
+  }
+  return -1;
+}
+
+int orc_selinv(int32_t n, const int64_t* lp, const int32_t* li, const double* lx, double* zx) {
+  for (int32_t j = n - 1; j >= 0; --j) {
+    const double ljj = lx[lp[j]];
+    for (int64_t t = lp[j] + 1; t < lp[j + 1]; ++t) {
+      const int32_t i = li[t];
+      double s = 0.0;
+      for (int64_t q = lp[j] + 1; q < lp[j + 1]; ++q) {
+        const int32_t k = li[q];
+        const int32_t r = i > k ? i : k, c = i > k ? k : i;
+        const int64_t p = find_entry(lp, li, r, c);
+        if (p < 0) return -1;
+        s += (lx[q] / ljj) * zx[p];
+      }
+      zx[t] = -s;
+    }
+    double s = 0.0;
+    for (int64_t q = lp[j] + 1; q < lp[j + 1]; ++q) s += (lx[q] / ljj) * zx[q];
+    zx[lp[j]] = 1.0 / (ljj * ljj) - s;
+  }
+  return 0;
+}

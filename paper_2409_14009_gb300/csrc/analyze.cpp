@@ -62,7 +62,7 @@ int validate(int32_t n, const int64_t* colptr, const int32_t* rowind, const int3
     // tensor-core K chunks are 32 (tf32) / 64 (bf16) wide and must not cross a column step
     if (opt->precision == CHOL_PREC_TF32 && opt->block_cols % 32 != 0) return -5;
     if (opt->precision == CHOL_PREC_BF16 && opt->block_cols % 64 != 0) return -5;
-    if (opt->small_max_cols < 1 || opt->small_max_panel < 1 || opt->small_max_panel > 16384) return -5;
+    if (opt->small_max_cols < 1 || opt->small_max_panel < 1 || opt->small_max_panel > 24576) return -5;
     if (opt->persistent != 0 && opt->persistent != 1) return -5;
     if (opt->use_graph != 0 && opt->use_graph != 1) return -5;
     if (opt->block_cols < 8 || opt->block_cols > 64) return -5;

@@ -625,7 +625,7 @@ int chol_device_ensure(chol_handle* h) {
   if (!attrs_done) {
     if (cudaFuncSetAttribute(k_assemble, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024) != cudaSuccess)
       return fail(CHOL_ECUDA);
-    if (cudaFuncSetAttribute(k_small, cudaFuncAttributeMaxDynamicSharedMemorySize, 16384 * 8) != cudaSuccess)
+    if (cudaFuncSetAttribute(k_small, cudaFuncAttributeMaxDynamicSharedMemorySize, 24576 * 8) != cudaSuccess)
       return fail(CHOL_ECUDA);
     attrs_done = true;
   }

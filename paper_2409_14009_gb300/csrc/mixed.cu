@@ -510,7 +510,7 @@ int chol_mixed_ensure(chol_handle* h) {
   if ((rc = chol_tc_prepare(h))) return rc;
   if (cudaFuncSetAttribute(k_mx_assemble, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024) != cudaSuccess)
     return CHOL_ECUDA;
-  if (cudaFuncSetAttribute(k_mx_small, cudaFuncAttributeMaxDynamicSharedMemorySize, 16384 * 4) != cudaSuccess)
+  if (cudaFuncSetAttribute(k_mx_small, cudaFuncAttributeMaxDynamicSharedMemorySize, 24576 * 4) != cudaSuccess)
     return CHOL_ECUDA;
   D->mx_ready = true;
   return CHOL_OK;

@@ -340,3 +340,61 @@ def test_sampled_column_residual_matches_dense():
     for q, j in enumerate(cols):
         exp = np.linalg.norm(R[j:, j]) / np.linalg.norm(B[j:, j])
         assert got[q] == pytest.approx(exp, rel=1e-6)
+
+
+# --------------------------------------------------------------------------
+# selected inverse and gradients
+# --------------------------------------------------------------------------
+
+@pytest.mark.parametrize("seed", range(4))
+def test_selected_inverse_vs_dense_inverse(seed):
+    rs = np.random.RandomState(800 + seed)
+    n = int(rs.randint(10, 120))
+    A, cp, ri, vx, perm = random_spd(n, rs.uniform(0.03, 0.15), 90 + seed)
+    bp, bi, bx = oracle.permute(n, cp, ri, vx, perm)
+    fac = oracle.Factor(n, bp, bi, bx)
+    zx = fac.selinv()
+    P = np.eye(n)[perm]
+    Zd = np.linalg.inv(P @ A @ P.T)
+    Zsel = csc_to_dense_lower(n, fac.lp, fac.li, zx)
+    mask = csc_to_dense_lower(n, fac.lp, fac.li, np.ones_like(zx)) != 0
+    assert np.max(np.abs(Zsel[mask] - Zd[mask])) <= 1e-12 * np.max(np.abs(Zd))
+    zA = oracle.inverse_on_pattern(dict(n=n, colptr=cp, rowind=ri), fac, perm)
+    Ai = np.linalg.inv(A)
+    cols = np.repeat(np.arange(n), np.diff(cp))
+    assert np.allclose(zA, Ai[ri, cols], rtol=1e-12, atol=1e-14 * np.max(np.abs(Ai)))
+
+
+def test_gradient_vs_central_differences():
+    """d/da_ij of  w^T A^{-1} b + log det A  with a_ij and a_ji moved together."""
+    rs = np.random.RandomState(3)
+    n = 40
+    A, cp, ri, vx, perm = random_spd(n, 0.1, 33)
+    prob = dict(n=n, colptr=cp, rowind=ri, values=vx, perm=perm)
+    b = rs.uniform(-1, 1, (n, 3))
+    w = rs.normal(size=(n, 3))
+
+    def loss(vals):
+        bp, bi, bx = oracle.permute(n, cp, ri, vals, perm)
+        f = oracle.Factor(n, bp, bi, bx)
+        x = f.solve(perm, b)
+        return float(np.sum(w * x)) + f.logdet()
+
+    bp, bi, bx = oracle.permute(n, cp, ri, vx, perm)
+    fac = oracle.Factor(n, bp, bi, bx)
+    x = fac.solve(perm, b)
+    g, xbar = oracle.gradient(prob, fac, w, x, 1.0)
+    picks = rs.choice(len(vx), 20, replace=False)
+    for t in picks:
+        h = 1e-6 * abs(vx[t])
+        vp = vx.copy(); vp[t] += h
+        vm = vx.copy(); vm[t] -= h
+        fd = (loss(vp) - loss(vm)) / (2 * h)
+        assert abs(fd - g[t]) <= 1e-6 * max(1.0, abs(fd)), (t, fd, g[t])
+    # d loss / d b = A^{-1} w
+    assert np.allclose(xbar, np.linalg.solve(A, w), rtol=1e-10, atol=1e-12)
+    # dense reference: G = -xbar x^T + A^{-1}, symmetrised onto the lower entries
+    G = -xbar @ x.T + np.linalg.inv(A)
+    cols = np.repeat(np.arange(n), np.diff(cp))
+    dense = np.where(ri == cols, G[ri, cols], G[ri, cols] + G[cols, ri])
+    assert np.allclose(g, dense, rtol=1e-9, atol=1e-12)
