@@ -348,6 +348,44 @@ def laplacian_2d_dirichlet_weighted(k: int, rng: SplitMix64, lo: float = 0.1, hi
                    meta=dict(kind="laplacian_2d_dirichlet_weighted", k=k, lo=lo, hi=hi))
 
 
+def laplacian_dirichlet_weighted(dims, rng: SplitMix64, lo: float, hi: float) -> Problem:
+    """Grid Laplacian (2D 5-point / 3D 7-point) with log-uniform conductances in
+    [lo, hi] and Dirichlet ghost edges: edge order node in natural order, then
+    for axis 0..d-1 the (-1, +1) neighbours; an in-grid neighbour is drawn from
+    its +1 side only, an out-of-grid neighbour is a ghost whose conductance
+    goes to A_ii only. A_ii = sum of incident conductances (ghosts included)."""
+    dims = tuple(int(d) for d in dims)
+    d = len(dims)
+    n = int(np.prod(dims))
+    idx, coords = _grid_coords(dims)
+    offs = []
+    for a in range(d):
+        for sgn in (-1, 1):
+            o = [0] * d
+            o[a] = sgn
+            offs.append(tuple(o))
+    nb_all = np.stack([_offset_index(dims, coords, o) for o in offs], axis=1)
+    pos = np.array([o[a] > 0 for o in offs for a in [next(i for i in range(d) if o[i] != 0)]])
+    draw = (nb_all < 0) | pos[None, :]
+    w = np.zeros(nb_all.shape)
+    w[draw] = rng.log_uniform(int(draw.sum()), lo, hi)
+    diag = (w * (nb_all < 0)).sum(axis=1)
+    edge = (nb_all >= 0) & pos[None, :]
+    R, C, V = [idx], [idx], []
+    for o in range(len(offs)):
+        e = edge[:, o]
+        if not e.any():
+            continue
+        i = nb_all[e, o]; j = idx[e]
+        diag[j] += w[e, o]
+        np.add.at(diag, i, w[e, o])
+        R.append(i); C.append(j); V.append(-w[e, o])
+    V.insert(0, diag)
+    colptr, rowind, vals = coo_to_lower_csc(n, np.concatenate(R), np.concatenate(C), np.concatenate(V))
+    return Problem(n=n, colptr=colptr, rowind=rowind, values=vals, perm=nd_perm(dims),
+                   meta=dict(kind="laplacian_dirichlet_weighted", dims=dims, lo=lo, hi=hi))
+
+
 def batch_2d(count: int = 2000, kmin: int = 16, kmax: int = 96, seed: int = 4):
     """Independent weighted 2D Laplacians; side k_s ~ U{kmin..kmax} drawn first."""
     rng = SplitMix64(seed)
@@ -394,5 +432,7 @@ def workload(name: str) -> Problem:
     if name == "elast48":
         return elasticity_27pt(48, 1.0, 1e6, seed=3)
     if name == "3d48":
-        return laplacian_neumann_varcoef((48, 48, 48), 1e-2, 1e2, 1e-6, seed=5)
+        # the differentiable-solve workload: Dirichlet-anchored (ghost edges), so
+        # finite differences of log det and w^T x are well posed
+        return laplacian_dirichlet_weighted((48, 48, 48), SplitMix64(5), 1e-2, 1e2)
     raise KeyError(name)

@@ -194,6 +194,32 @@ int chol_logdet(chol_handle* h, double* out, void* stream);
 int chol_solve_refine(chol_handle* h, const double* b, double* x, int32_t nrhs, double tol,
                       int32_t max_iter, int32_t* iters, double* berr, void* stream);
 
+/*
+ * Selected inverse: zvals[t] = (A^{-1})_ij for every stored entry t = (i, j)
+ * of the analyzed lower pattern of A (device, colptr[n] doubles). Computed
+ * once per factorization, supernode by supernode from the root down (dense
+ * blocks: T = L_JJ^{-1}, Uhat = L_RJ T, Z_RJ = -Z_RR Uhat with Z_RR gathered
+ * from the ancestors through the relative positions, Z_JJ = T^T T -
+ * Uhat^T Z_RJ). CHOL_PREC_FP64 handles only (else CHOL_ENOTSUP). Asynchronous.
+ */
+int chol_selected_inverse(chol_handle* h, double* zvals, void* stream);
+
+/*
+ * Adjoint of x = A^{-1} b and log det A for the loss
+ *   l = sum_k w_k^T x_k + logdet_weight * log det A,   X = A^{-1} B.
+ * Gives dl/dB = Xbar = A^{-1} W and the gradient with respect to the stored
+ * lower entries of A (a_ij and a_ji move together):
+ *   G = -Xbar X^T + logdet_weight A^{-1},  g_ii = G_ii,  g_ij = G_ij + G_ji.
+ *   w     device, n x nrhs column-major (ld n)
+ *   x     device, n x nrhs, the solution X of the forward solve
+ *   bbar  device, n x nrhs output (dl/dB), or NULL (not returned)
+ *   grad  device, colptr[n] doubles output, in the order of the analyzed rowind
+ * Reuses the factor: two triangular solves, plus the selected inverse when
+ * logdet_weight != 0. CHOL_PREC_FP64 handles only. Asynchronous.
+ */
+int chol_adjoint(chol_handle* h, const double* w, const double* x, int32_t nrhs, double logdet_weight,
+                 double* bbar, double* grad, void* stream);
+
 /* Sizes of the symbolic structure, for sizing the chol_get_symbolic arrays. */
 typedef struct chol_info {
   int32_t n;

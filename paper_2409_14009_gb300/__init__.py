@@ -31,6 +31,7 @@ CHOL_PREC_BF16 = 3
 
 EXPORTED = ["chol_default_options", "chol_analyze", "chol_factor", "chol_solve", "chol_solve_noalloc",
             "chol_solve_refine", "chol_logdet", "chol_analyze_batch", "chol_logdet_batch", "chol_autotune",
+            "chol_selected_inverse", "chol_adjoint",
             "chol_get_info", "chol_get_symbolic", "chol_get_partition", "chol_get_factor", "chol_profile",
             "chol_get_stats", "chol_destroy", "chol_strerror"]
 
@@ -100,6 +101,10 @@ def lib():
         L.chol_logdet_batch.restype = C.c_int
         L.chol_autotune.argtypes = [P, P, P]
         L.chol_autotune.restype = C.c_int
+        L.chol_selected_inverse.argtypes = [P, P, P]
+        L.chol_selected_inverse.restype = C.c_int
+        L.chol_adjoint.argtypes = [P, P, P, C.c_int32, C.c_double, P, P, P]
+        L.chol_adjoint.restype = C.c_int
         L.chol_logdet.argtypes = [P, C.POINTER(C.c_double), P]
         L.chol_logdet.restype = C.c_int
         L.chol_get_info.argtypes = [P, C.POINTER(chol_info)]
@@ -204,6 +209,15 @@ def chol_solve_refine(h, b, x, nrhs, tol=1e-10, max_iter=30, stream=None):
     rc = lib().chol_solve_refine(h, _dev_ptr(b), _dev_ptr(x), int(nrhs), float(tol), int(max_iter),
                                  C.byref(it), _ptr(berr), _stream(stream))
     return rc, it.value, berr[: int(nrhs)]
+
+
+def chol_selected_inverse(h, zvals, stream=None) -> int:
+    return lib().chol_selected_inverse(h, _dev_ptr(zvals), _stream(stream))
+
+
+def chol_adjoint(h, w, x, nrhs, logdet_weight, bbar, grad, stream=None) -> int:
+    return lib().chol_adjoint(h, _dev_ptr(w), _dev_ptr(x), int(nrhs), float(logdet_weight), _dev_ptr(bbar),
+                              _dev_ptr(grad), _stream(stream))
 
 
 def chol_logdet(h, stream=None):
@@ -332,7 +346,13 @@ class SparseCholesky:
         return b
 
     def solve(self, b, stream=None):
-        x = b.t().contiguous().t() if b.dim() == 2 else b.clone()
+        """Returns a new column-major tensor; b is left untouched."""
+        import torch
+        if b.dim() == 2:
+            x = torch.empty_strided(tuple(b.shape), (1, b.shape[0]), dtype=b.dtype, device=b.device)
+            x.copy_(b)
+        else:
+            x = b.clone()
         return self.solve_(x, stream)
 
     def logdet(self, stream=None):

@@ -629,6 +629,8 @@ extern "C" int chol_analyze(int32_t n, const int64_t* colptr, const int32_t* row
     for (int32_t i = 0; i < n; ++i) h->perm[i] = perm ? perm[i] : i;
     for (int32_t i = 0; i < n; ++i) h->iperm[h->perm[i]] = i;
     h->diagpos_orig.assign(colptr, colptr + n);   // diagonal = first entry of each column
+    h->a_colptr.assign(colptr, colptr + n + 1);
+    h->a_rowind.assign(rowind, rowind + colptr[n]);
     build(h, colptr, rowind);
   } catch (const std::bad_alloc&) {
     delete h;

@@ -72,6 +72,17 @@ struct DeviceState {
   cudaEvent_t gev[2] = {nullptr, nullptr};
   chol_kernel_stat graph_delta[CHOL_K_NCLASSES] = {};
   float mx_spiv = 0.f;             // static-pivot threshold passed to the persistent kernel
+  // selected inverse and adjoint
+  double* Zp = nullptr;            // Z = (P A P^T)^{-1} on the pattern of L, panel layout
+  double* Tw = nullptr;            // L_JJ^{-1}
+  double* Ww = nullptr;
+  double* Uh = nullptr;            // L_RJ L_JJ^{-1}
+  double* Zrr = nullptr;           // Z_RR gathered from the ancestors
+  void* pairs = nullptr;
+  int32_t* a_col = nullptr;        // column / row of every stored entry of A
+  int32_t* a_row = nullptr;
+  double* adj_xb = nullptr;
+  int adj_cap = 0;
   // solve workspaces (grown on demand)
   double* Y = nullptr;          // permuted right-hand sides, n x chunk
   double* W = nullptr;          // per-level panel products, w_rows_max x chunk

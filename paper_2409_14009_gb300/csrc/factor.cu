@@ -550,7 +550,7 @@ void chol_device_free(chol_handle* h) {
   void* ptrs[] = {D->L, D->U, D->sn, D->rows, D->amap, D->small_list, D->potrf_list,
                   D->level_snodes, D->trsm, D->gemm, D->syrk, D->asm_tasks, D->asm_segs, D->sdiag,
                   D->fupd, D->bupd, D->bpanel, D->gemv, D->bpart, D->bred, D->P32, D->plevels, D->vals, D->sys_snode, D->sys_out,
-                  D->perm, D->status, D->part, D->scalar_dev, D->Y, D->W,
+                  D->Zp, D->Tw, D->Ww, D->Uh, D->Zrr, D->pairs, D->a_col, D->a_row, D->adj_xb, D->perm, D->status, D->part, D->scalar_dev, D->Y, D->W,
                   D->mx_diagpos, D->mx_aij, D->mx_d, D->mx_fallbacks, D->csr_ptr, D->csr_col, D->csr_src,
                   D->csr_val, D->Lbf, D->tmaps, D->tc_err, D->R, D->Z, D->Pv, D->Q, D->red, D->Y32, D->W32,
                   D->rhs_scale};
@@ -757,6 +757,7 @@ extern "C" int chol_factor(chol_handle* h, const double* values, void* stream) {
   DeviceState* D = h->dev;
   cudaStream_t st = (cudaStream_t)stream;
   h->factored = false;
+  h->selinv_valid = false;
   if (h->opt.precision != CHOL_PREC_FP64 && (rc = chol_mixed_ensure(h))) return rc;
   if (h->opt.use_graph) {
     // replay a graph of the whole launch sequence; the values go through a copy

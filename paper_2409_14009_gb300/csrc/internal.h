@@ -94,6 +94,10 @@ struct chol_handle {
   std::vector<int32_t> csr_col;
   std::vector<int64_t> csr_src;     // CSR entry -> entry of the lower CSC input
   int32_t fp64_fallbacks = 0;
+  std::vector<int64_t> a_colptr;    // the analyzed pattern of A (for gradients)
+  std::vector<int32_t> a_rowind;
+  std::vector<int32_t> pair_begin;  // first (J, K) pair of every supernode
+  bool selinv_valid = false;        // selected inverse of the current factor computed
   int32_t perturbed_pivots = 0;
   std::vector<int64_t> diagpos_orig;  // position of A_jj in the values array, per original column
   int64_t nnz_l = 0, panel_doubles = 0, update_doubles = 0, w_rows_max = 0, nnz_stored = 0;

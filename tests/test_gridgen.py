@@ -59,3 +59,18 @@ def test_batch_block_diagonal():
     assert bd.n == sum(p.n for p in probs)
     assert sorted(bd["perm"].tolist()) == list(range(bd.n))
     assert all(3 <= p["meta"]["k"] <= 6 for p in probs)
+
+
+def test_dirichlet_weighted_3d_is_spd_and_sized():
+    p = gridgen.laplacian_dirichlet_weighted((4, 3, 5), gridgen.SplitMix64(1), 1e-2, 1e2)
+    A = np.zeros((p.n, p.n))
+    for j in range(p.n):
+        for t in range(p["colptr"][j], p["colptr"][j + 1]):
+            A[p["rowind"][t], j] = A[j, p["rowind"][t]] = p["values"][t]
+    assert np.linalg.eigvalsh(A).min() > 0
+    # 7-point: n diagonals + edges along each axis
+    edges = (3 * 3 * 5) + (4 * 2 * 5) + (4 * 3 * 4)
+    assert int(p["colptr"][-1]) == p.n + edges
+    # row sums equal the ghost conductances (>= 0), strictly positive on the boundary
+    rs = A.sum(axis=1)
+    assert np.all(rs >= -1e-12) and rs[0] > 0
