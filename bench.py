@@ -282,14 +282,51 @@ def batch_run(args, P, gridgen, torch, dev):
                      "refine_iterations": iters, "backward_error": float(eta),
                      "factor_gflops": info.flops / (fms * 1e-3) / 1e9,
                      "systems_per_s": len(probs) / ((fms + sms) * 1e-3),
-                     "persistent": int(info.persistent_ok and P.chol_default_options().persistent == 0 and 1),
-                     "autotuned": {"persistent_threads": info.persistent_threads,
+                     "autotuned": {"persistent": bool(info.launch_mode & 1), "graph": bool(info.launch_mode & 2),
+                                   "persistent_threads": info.persistent_threads,
                                    "persistent_ctas_per_sm": info.persistent_ctas_per_sm},
                      "supernodes": info.nsuper_storage, "levels": info.nlevels}
         P.chol_destroy(h)
     out["flops"] = float(info.flops)
     out["generate_s"] = gen_s
     return out
+
+
+def adjoint_run(args, P, gridgen, torch, dev):
+    """Differentiable solve: 3D 48^3 7-point Dirichlet Laplacian (n=110,592),
+    conductances log-uniform in [1e-2, 1e2], 16 RHS; loss = sum w^T x + log det A.
+    Forward = factor + 16-RHS solve + logdet; backward = chol_adjoint (two
+    triangular solves + selected inverse + per-nonzero gradient)."""
+    p = gridgen.workload("3d48")
+    b = gridgen.rhs_uniform(p.n, 16, seed=5)
+    w = gridgen.rhs_normal(p.n, 16, seed=6)
+    opt = P.chol_default_options()
+    opt.merge_growth = args.merge
+    S = P.SparseCholesky(p.n, p["colptr"], p["rowind"], p["perm"], opt)
+    st = torch.cuda.current_stream()
+    vals = torch.as_tensor(p["values"], device=dev)
+    B = torch.as_tensor(np.ascontiguousarray(b.T), device=dev).t()
+    W = torch.as_tensor(np.ascontiguousarray(w.T), device=dev).t()
+    X = torch.empty_like(B)
+    bbar = torch.empty_like(B)
+    grad = torch.empty(len(p["rowind"]), dtype=torch.float64, device=dev)
+
+    def forward():
+        S.factor(vals)
+        X.copy_(B)
+        S.solve_(X)
+        return S.logdet()
+
+    def backward():
+        return P.chol_adjoint(S.h, W, X, 16, 1.0, bbar, grad, st)
+
+    forward(); backward()
+    fms, _ = _timed(torch, st, forward, 3)
+    bms, rc = _timed(torch, st, lambda: (forward(), backward())[1], 3)
+    S.close()
+    return {"workload": "3D 48^3 7-point Dirichlet Laplacian (n=110592), 16 RHS, loss = sum w^T x + log det A",
+            "forward_ms": fms, "forward_plus_backward_ms": bms, "backward_ms": bms - fms, "rc": rc,
+            "factor_flops": float(S.info.flops)}
 
 
 def run_ours(args, rank, world, local_rank):
@@ -378,6 +415,7 @@ def run_ours(args, rank, world, local_rank):
     mixed = None if args.no_mixed else mixed_vs_fp64(args, P, gridgen, torch, dev, p, b, vals, flops,
                                                          factor_ms, solve_ms)
     batch = None if args.no_batch else batch_run(args, P, gridgen, torch, dev)
+    adjoint = None if args.no_adjoint else adjoint_run(args, P, gridgen, torch, dev)
     # max over ranks
     if dist:
         t = torch.tensor([ms, e2e_ms], device=dev)
@@ -416,7 +454,7 @@ def run_ours(args, rank, world, local_rank):
                         "d2h_bytes_per_step": int(hx.numel() * 8)},
                 "gpu_launches": launches // max(args.steps, 1) * args.steps,
                 "roofline": roof, "cpu_baseline": cpu, "clocks": clk.summary(),
-                "mixed_vs_fp64": mixed, "batch": batch}
+                "mixed_vs_fp64": mixed, "batch": batch, "adjoint": adjoint}
         print(json.dumps(line), flush=True)
     S.close()
     if dist:
@@ -436,6 +474,7 @@ def main():
     ap.add_argument("--skip-elasticity", action="store_true")
     ap.add_argument("--no-batch", action="store_true", help="skip the 2,000-system batch")
     ap.add_argument("--batch-count", type=int, default=2000)
+    ap.add_argument("--no-adjoint", action="store_true", help="skip the differentiable-solve workload")
     ap.add_argument("--workload", default="3d64", choices=["3d64", "3d48"],
                     help="3d64 is the benchmark; 3d48 is the smaller case used for ncu captures")
     ap.add_argument("--merge", type=float, default=0.1,

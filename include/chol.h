@@ -246,7 +246,7 @@ typedef struct chol_info {
   int32_t persistent_ok;   /* 1 if every supernode takes the one-CTA kernel */
   int32_t persistent_threads; /* launch shape of the persistent kernel (0 = default) */
   int32_t persistent_ctas_per_sm;
-  int32_t reserved3;
+  int32_t launch_mode;     /* bit 0: persistent kernel in use, bit 1: CUDA-graph replay */
 } chol_info;
 
 int chol_get_info(const chol_handle* h, chol_info* info);

@@ -58,7 +58,7 @@ class chol_info(C.Structure):
                 ("flops_stored", C.c_double), ("precision", C.c_int32), ("fp64_fallbacks", C.c_int32),
                 ("perturbed_pivots", C.c_int32), ("nsys", C.c_int32), ("persistent_ok", C.c_int32),
                 ("persistent_threads", C.c_int32), ("persistent_ctas_per_sm", C.c_int32),
-                ("reserved3", C.c_int32)]
+                ("launch_mode", C.c_int32)]
 
 
 class chol_kernel_stat(C.Structure):

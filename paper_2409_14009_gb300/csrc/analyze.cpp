@@ -423,6 +423,7 @@ void build(chol_handle* h, const int64_t* colptr, const int32_t* rowind) {
   h->level_snodes.clear(); h->small_list.clear(); h->potrf_list.clear();
   h->trsm_tasks.clear(); h->gemm_tasks.clear(); h->syrk_tasks.clear();
   h->bpanel_tasks.clear(); h->sdiag_list.clear(); h->fupd_tasks.clear(); h->bupd_tasks.clear();
+  h->ssmall_list.clear();
   h->gemv_tasks.clear(); h->bpart_tasks.clear(); h->bred_tasks.clear();
   h->p_max = 0;
   h->asm_tasks.clear(); h->asm_segs.clear();
@@ -509,8 +510,16 @@ void build(chol_handle* h, const int64_t* colptr, const int32_t* rowind) {
     // kSolveSB columns (diagonal triangle in one CTA + updates of the rows of the
     // diagonal block below it / of the column blocks left of it), then one panel
     // product per level for the off-diagonal rows
+    auto warp_solved = [&](int32_t J) {
+      return h->snodes[J].s <= kSolveSmallCols && h->snodes[J].len <= kSolveSmallRows;
+    };
+    P.ssmall_b = (int32_t)h->ssmall_list.size();
+    for (int32_t J : Js)
+      if (warp_solved(J)) h->ssmall_list.push_back(J);
+    P.ssmall_n = (int32_t)h->ssmall_list.size() - P.ssmall_b;
     int32_t maxs_all = 0;
-    for (int32_t J : Js) maxs_all = std::max(maxs_all, h->snodes[J].s);
+    for (int32_t J : Js)
+      if (!warp_solved(J)) maxs_all = std::max(maxs_all, h->snodes[J].s);
     const int32_t sb = h->solve_sb;
     for (int32_t k0 = 0; k0 < maxs_all; k0 += sb) {
       SolveStep st{};
@@ -519,7 +528,7 @@ void build(chol_handle* h, const int64_t* colptr, const int32_t* rowind) {
       st.bupd_b = (int32_t)h->bupd_tasks.size();
       for (int32_t J : Js) {
         const SnodeDev& d = h->snodes[J];
-        if (d.s <= k0) continue;
+        if (d.s <= k0 || warp_solved(J)) continue;
         const int32_t sbk = std::min(sb, d.s - k0);
         h->sdiag_list.push_back(J);
         for (int32_t r0 = k0 + sbk; r0 < d.s; r0 += kSolveTileRows) h->fupd_tasks.push_back({J, k0, r0, 0});
@@ -537,7 +546,7 @@ void build(chol_handle* h, const int64_t* colptr, const int32_t* rowind) {
     for (int32_t J : Js) {
       const SnodeDev& d = h->snodes[J];
       const int32_t b = d.len - d.s;
-      if (b <= 0) continue;
+      if (b <= 0 || warp_solved(J)) continue;
       for (int32_t r0 = 0; r0 < b; r0 += gemv_rows) h->gemv_tasks.push_back({J, 0, r0, 0});
       for (int32_t c0 = 0; c0 < d.s; c0 += bpanel_cols) h->bpanel_tasks.push_back({J, 0, 0, c0});
     }
@@ -550,7 +559,7 @@ void build(chol_handle* h, const int64_t* colptr, const int32_t* rowind) {
       SnodeDev& d = h->snodes[J];
       const int32_t b = d.len - d.s;
       d.ppre = pp;
-      if (b <= 0 || h->opt.precision == CHOL_PREC_FP64) continue;
+      if (b <= 0 || h->opt.precision == CHOL_PREC_FP64 || warp_solved(J)) continue;
       const int32_t nch = (b + 63) / 64;
       for (int32_t ch = 0; ch < nch; ++ch)
         for (int32_t c0 = 0; c0 < d.s; c0 += 256) h->bpart_tasks.push_back({J, ch, ch * 64, c0});
@@ -695,6 +704,7 @@ extern "C" int chol_get_info(const chol_handle* h, chol_info* info) {
   info->persistent_ok = h->n_large == 0 ? 1 : 0;
   info->persistent_threads = h->persist_threads;
   info->persistent_ctas_per_sm = h->persist_ctas;
+  info->launch_mode = (h->opt.persistent ? 1 : 0) | (h->opt.use_graph ? 2 : 0);
   info->fp64_fallbacks = h->fp64_fallbacks;
   info->perturbed_pivots = h->perturbed_pivots;
   info->nnz_stored = h->nnz_stored;

@@ -25,6 +25,7 @@ struct DeviceState {
   AsmTask* asm_tasks = nullptr;
   AsmSeg* asm_segs = nullptr;
   int32_t* sdiag = nullptr;
+  int32_t* ssmall = nullptr;
   TileTask* fupd = nullptr;
   TileTask* bupd = nullptr;
   TileTask* bpanel = nullptr;

@@ -550,7 +550,7 @@ void chol_device_free(chol_handle* h) {
   void* ptrs[] = {D->L, D->U, D->sn, D->rows, D->amap, D->small_list, D->potrf_list,
                   D->level_snodes, D->trsm, D->gemm, D->syrk, D->asm_tasks, D->asm_segs, D->sdiag,
                   D->fupd, D->bupd, D->bpanel, D->gemv, D->bpart, D->bred, D->P32, D->plevels, D->vals, D->sys_snode, D->sys_out,
-                  D->Zp, D->Tw, D->Ww, D->Uh, D->Zrr, D->pairs, D->a_col, D->a_row, D->adj_xb, D->perm, D->status, D->part, D->scalar_dev, D->Y, D->W,
+                  D->ssmall, D->Zp, D->Tw, D->Ww, D->Uh, D->Zrr, D->pairs, D->a_col, D->a_row, D->adj_xb, D->perm, D->status, D->part, D->scalar_dev, D->Y, D->W,
                   D->mx_diagpos, D->mx_aij, D->mx_d, D->mx_fallbacks, D->csr_ptr, D->csr_col, D->csr_src,
                   D->csr_val, D->Lbf, D->tmaps, D->tc_err, D->R, D->Z, D->Pv, D->Q, D->red, D->Y32, D->W32,
                   D->rhs_scale};
@@ -608,6 +608,7 @@ int chol_device_ensure(chol_handle* h) {
   if ((rc = upload(h, &D->asm_tasks, h->asm_tasks))) return fail(rc);
   if ((rc = upload(h, &D->asm_segs, h->asm_segs))) return fail(rc);
   if ((rc = upload(h, &D->sdiag, h->sdiag_list))) return fail(rc);
+  if ((rc = upload(h, &D->ssmall, h->ssmall_list))) return fail(rc);
   if ((rc = upload(h, &D->fupd, h->fupd_tasks))) return fail(rc);
   if ((rc = upload(h, &D->bupd, h->bupd_tasks))) return fail(rc);
   if ((rc = upload(h, &D->bpanel, h->bpanel_tasks))) return fail(rc);

@@ -53,6 +53,7 @@ struct LevelPlan {
   int32_t syrk_b, syrk_n;     // U tiles (in syrk_tasks)
   int32_t asm_b, asm_n;       // assembly tasks
   std::vector<SolveStep> ssteps;
+  int32_t ssmall_b, ssmall_n; // supernodes solved by one warp each (in ssmall_list)
   int32_t gemv_b, gemv_n;     // forward-solve panel products (TileTask: J, r0)
   int32_t bpart_b, bpart_n;   // row-major backward panel, stage 1 (J, chunk, u0, c0)
   int32_t bred_b, bred_n;     // row-major backward panel, stage 2 (J, c0)
@@ -111,6 +112,7 @@ struct chol_handle {
   std::vector<int32_t> level_snodes, small_list, potrf_list;
   std::vector<TileTask> trsm_tasks, gemm_tasks, syrk_tasks, bpanel_tasks;
   std::vector<int32_t> sdiag_list;             // solve: supernode per (level, step)
+  std::vector<int32_t> ssmall_list;            // solve: one-warp supernodes per level
   std::vector<TileTask> fupd_tasks, bupd_tasks; // solve: (J, k0, r0) / (J, k0, c0)
   std::vector<TileTask> gemv_tasks;             // solve: (J, r0) off-diagonal row tiles
   std::vector<TileTask> bpart_tasks, bred_tasks; // solve: row-major backward panel stages
@@ -138,6 +140,8 @@ constexpr int kTileTC = 128;     // tensor-core (tcgen05) GEMM/SYRK tile edge
 constexpr int kAsmCols = 64;     // assembly task width (target columns)
 constexpr int kTrsmRowsHost = 32; // TRSM task height (rows)
 constexpr int kSolveSB = 256;    // largest solve super-step (columns solved inside one CTA)
+constexpr int kSolveSmallCols = 32;   // supernodes solved by one warp: s <= 32 and
+constexpr int kSolveSmallRows = 256;  // len <= 256
 constexpr int kSolveTileRows = 64;  // solve update tiles (rows / columns)
 
 void chol_device_free(chol_handle* h);  // CUDA side

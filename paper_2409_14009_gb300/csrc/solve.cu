@@ -496,6 +496,72 @@ k_sv_bupd(const SnodeDev* __restrict__ sn, const TileTask* __restrict__ tasks, i
   }
 }
 
+// Small supernodes (s <= 32, len <= 256), one warp each. Forward: lane i holds
+// y_i of the current right-hand side; the solved entry is broadcast by shuffle;
+// then w_J = L_RJ y_J with lanes along the off-diagonal rows.
+template <class T, bool RM>
+__global__ void __launch_bounds__(kT)
+k_sv_small_fwd(const SnodeDev* __restrict__ sn, const int32_t* __restrict__ list, int count,
+               const T* __restrict__ L, T* __restrict__ Y, int n, T* __restrict__ W, int nrhs) {
+  const int wid = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
+  if (wid >= count) return;
+  const SnodeDev d = sn[list[wid]];
+  const T* P = L + d.loff;
+  const int b = d.len - d.s;
+  T* Wj = W + d.wpre * nrhs;
+  for (int r = 0; r < nrhs; ++r) {
+    T y = lane < d.s ? Y[d.f + lane + (int64_t)r * n] : T(0);
+    for (int k = 0; k < d.s; ++k) {
+      const T yk = __shfl_sync(0xffffffffu, y, k) / lval<T, RM>(P, d, k, k);
+      if (lane == k) y = yk;
+      if (lane > k && lane < d.s) y -= lval<T, RM>(P, d, lane, k) * yk;
+    }
+    if (lane < d.s) Y[d.f + lane + (int64_t)r * n] = y;
+    T acc[kSolveSmallRows / 32];
+#pragma unroll
+    for (int c = 0; c < kSolveSmallRows / 32; ++c) acc[c] = T(0);
+    for (int k = 0; k < d.s; ++k) {
+      const T yk = __shfl_sync(0xffffffffu, y, k);
+#pragma unroll
+      for (int c = 0; c < kSolveSmallRows / 32; ++c) {
+        const int u = lane + 32 * c;
+        if (u < b) acc[c] += lval<T, RM>(P, d, d.s + u, k) * yk;
+      }
+    }
+#pragma unroll
+    for (int c = 0; c < kSolveSmallRows / 32; ++c) {
+      const int u = lane + 32 * c;
+      if (u < b) Wj[u + (int64_t)r * b] = acc[c];
+    }
+  }
+}
+
+// Backward for the same supernodes: lane k gathers t_k = sum_u L(s+u, k) x[rows[s+u]]
+// (ancestor rows are final), then the transposed diagonal solve with shuffles.
+template <class T, bool RM>
+__global__ void __launch_bounds__(kT)
+k_sv_small_bwd(const SnodeDev* __restrict__ sn, const int32_t* __restrict__ list, int count,
+               const int32_t* __restrict__ rows, const T* __restrict__ L, T* __restrict__ Y, int n, int nrhs) {
+  const int wid = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
+  if (wid >= count) return;
+  const SnodeDev d = sn[list[wid]];
+  const T* P = L + d.loff;
+  const int b = d.len - d.s;
+  const int32_t* rj = rows + d.roff + d.s;
+  for (int r = 0; r < nrhs; ++r) {
+    T t = T(0);
+    if (lane < d.s)
+      for (int u = 0; u < b; ++u) t += lval<T, RM>(P, d, d.s + u, lane) * Y[rj[u] + (int64_t)r * n];
+    T y = lane < d.s ? Y[d.f + lane + (int64_t)r * n] - t : T(0);
+    for (int k = d.s - 1; k >= 0; --k) {
+      const T xk = __shfl_sync(0xffffffffu, y, k) / lval<T, RM>(P, d, k, k);
+      if (lane == k) y = xk;
+      if (lane < k) y -= lval<T, RM>(P, d, k, lane) * xk;
+    }
+    if (lane < d.s) Y[d.f + lane + (int64_t)r * n] = y;
+  }
+}
+
 template <class T>
 size_t diag_smem(int nr) {
   return sizeof(T) * ((size_t)kSolveSB * nr + 2 * kSub * 65 + kSub);
@@ -516,6 +582,12 @@ void solve_levels(chol_handle* h, const T* L, T* Y, T* W, T* part, int nr, cudaS
   const int sb = h->solve_sb;
   auto scope = [&](int cls) { return prof ? new KScope(h, cls, st, 0.0, 0.0) : nullptr; };
   for (const LevelPlan& P : h->levels) {
+    if (P.ssmall_n > 0) {
+      KScope* ks = scope(CHOL_K_SOLVE_DIAG);
+      k_sv_small_fwd<T, RM><<<(P.ssmall_n + 7) / 8, kT, 0, st>>>(D->sn, D->ssmall + P.ssmall_b, P.ssmall_n, L, Y, n,
+                                                                 W, nr);
+      delete ks;
+    }
     for (size_t k = 0; k < P.ssteps.size(); ++k) {
       const SolveStep& s = P.ssteps[k];
       const int k0 = (int)k * sb;
@@ -554,6 +626,12 @@ void solve_levels(chol_handle* h, const T* L, T* Y, T* W, T* part, int nr, cudaS
     } else if (P.bpanel_n > 0) {
       KScope* ks = scope(CHOL_K_SOLVE_BPANEL);
       k_sv_bpanel<T, RM><<<P.bpanel_n, kT, 0, st>>>(D->sn, D->bpanel + P.bpanel_b, D->rows, L, Y, n, nr);
+      delete ks;
+    }
+    if (P.ssmall_n > 0) {
+      KScope* ks = scope(CHOL_K_SOLVE_DIAG);
+      k_sv_small_bwd<T, RM><<<(P.ssmall_n + 7) / 8, kT, 0, st>>>(D->sn, D->ssmall + P.ssmall_b, P.ssmall_n, D->rows,
+                                                                 L, Y, n, nr);
       delete ks;
     }
     for (int k = (int)P.ssteps.size() - 1; k >= 0; --k) {
