@@ -43,16 +43,20 @@ struct GenGemm {
   int amode, bmode, lower_c;
 };
 
-__global__ void __launch_bounds__(kGT) k_gen_gemm(GenGemm g) {
+// Grouped form: one CTA per (descriptor, tile i, tile j) entry of a task list,
+// so the GEMMs of every supernode of a level run in one launch.
+struct GemmTile {
+  int32_t desc, ti, tj, pad;
+};
+
+__device__ __forceinline__ void gen_gemm_tile(const GenGemm& g, int i0, int j0) {
   constexpr int KC = 16;
   __shared__ double As[KC][kGTile + 1];
   __shared__ double Bs[KC][kGTile + 1];
-  const int i0 = blockIdx.x * kGTile, j0 = blockIdx.y * kGTile;
-  if (g.lower_c && i0 + kGTile - 1 < j0) return;
   const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
   int kbeg = 0, kend = g.K;
-  if (g.amode == 1) kend = min(kend, i0 + kGTile);          // A(i,k) = 0 for k > i
-  if (g.bmode == 1) kbeg = (j0 / KC) * KC;                   // B(k,j) = 0 for k < j
+  if (g.amode == 1) kend = min(kend, i0 + kGTile);
+  if (g.bmode == 1) kbeg = (j0 / KC) * KC;
   double acc[4][4] = {};
   for (int k = kbeg; k < kend; k += KC) {
 #pragma unroll
@@ -97,10 +101,26 @@ __global__ void __launch_bounds__(kGT) k_gen_gemm(GenGemm g) {
     }
 }
 
+__global__ void __launch_bounds__(kGT)
+k_gen_gemm_grouped(const GenGemm* __restrict__ descs, const GemmTile* __restrict__ tiles) {
+  const GemmTile t = tiles[blockIdx.x];
+  const GenGemm g = descs[t.desc];
+  gen_gemm_tile(g, t.ti * kGTile, t.tj * kGTile);
+}
+
+struct InvTask {
+  const double* src;
+  int64_t lds;
+  double* dst;
+  int64_t ldt;
+  int32_t kb, pad;
+};
+
 // Inverse of a kb x kb (kb <= 64) lower-triangular block (column-major,
 // leading dimensions lds / ldt): thread j computes column j of the inverse by
 // forward substitution on the unit vector e_j.
-__global__ void k_inv64(const double* __restrict__ Lsrc, int64_t lds, int kb, double* __restrict__ T, int64_t ldt) {
+__device__ __forceinline__ void inv64_body(const double* __restrict__ Lsrc, int64_t lds, int kb,
+                                           double* __restrict__ T, int64_t ldt) {
   __shared__ double Ls[64 * 65];
   for (int e = threadIdx.x; e < kb * kb; e += blockDim.x) {
     const int r = e % kb, c = e / kb;
@@ -120,22 +140,30 @@ __global__ void k_inv64(const double* __restrict__ Lsrc, int64_t lds, int kb, do
   for (int i = 0; i < kb; ++i) T[i + j * ldt] = i >= j ? x[i] : 0.0;
 }
 
-// Z_RR of supernode J (lower, column-major b x b) gathered from the ancestors'
-// Z panels: one block per (J, K) pair, positions of J's rows in struct(K) found
-// by binary search in shared memory.
-struct PairDev {
-  int32_t K, c0, c1, pad;
+__global__ void k_inv64_grouped(const InvTask* __restrict__ tasks) {
+  const InvTask t = tasks[blockIdx.x];
+  inv64_body(t.src, t.lds, t.kb, t.dst, t.ldt);
+}
+
+struct LevelPair {
+  int32_t J, K, c0, c1;
 };
 
+// Z_RR of every supernode J of a level (lower, column-major b x b, stored in the
+// update workspace at U_J's place), gathered from the ancestors' Z panels: one
+// block per (J, K) pair, the positions of J's rows in struct(K) found by binary
+// search in shared memory.
 __global__ void __launch_bounds__(kGT)
-k_gather_zrr(const PairDev* __restrict__ pairs, SnodeDev dj, const SnodeDev* __restrict__ sn,
-             const int32_t* __restrict__ rows, const double* __restrict__ Z, double* __restrict__ ZRR) {
-  extern __shared__ int32_t gsm[];
-  const PairDev pr = pairs[blockIdx.x];
+k_gather_zrr_level(const LevelPair* __restrict__ pairs, const SnodeDev* __restrict__ sn,
+                   const int32_t* __restrict__ rows, const double* __restrict__ Z, double* __restrict__ U) {
+  extern __shared__ int32_t gsm2[];
+  const LevelPair pr = pairs[blockIdx.x];
+  const SnodeDev dj = sn[pr.J];
   const SnodeDev dk = sn[pr.K];
   const int b = dj.len - dj.s;
-  int32_t* sK = gsm;
-  int32_t* pos = gsm + dk.len;
+  double* ZRR = U + dj.uoff;
+  int32_t* sK = gsm2;
+  int32_t* pos = gsm2 + dk.len;
   const int32_t* rk = rows + dk.roff;
   const int32_t* rj = rows + dj.roff + dj.s;
   for (int i = threadIdx.x; i < dk.len; i += blockDim.x) sK[i] = rk[i];
@@ -186,12 +214,6 @@ inline unsigned grid1d(int64_t n, int threads) {
   return (unsigned)(g > 0 ? g : 1);
 }
 
-void gemm(cudaStream_t st, const GenGemm& g) {
-  if (g.M <= 0 || g.N <= 0) return;
-  dim3 grid((g.M + kGTile - 1) / kGTile, (g.N + kGTile - 1) / kGTile);
-  k_gen_gemm<<<grid, kGT, 0, st>>>(g);
-}
-
 GenGemm mk(const double* A, int64_t ar, int64_t ac, const double* B, int64_t br, int64_t bc, double* C, int64_t cr,
            int64_t cc, int M, int N, int K, double alpha, double beta, int amode = 0, int bmode = 0, int lower = 0) {
   GenGemm g;
@@ -213,78 +235,217 @@ int ensure_adjoint(chol_handle* h) {
   DeviceState* D = h->dev;
   if (D->Zp) return CHOL_OK;
   int rc;
-  int32_t maxs = 0, maxb = 0;
-  for (const SnodeDev& d : h->snodes) {
-    maxs = std::max(maxs, d.s);
-    maxb = std::max(maxb, d.len - d.s);
-  }
-  const size_t ms = std::max(maxs, 1), mb = std::max(maxb, 1);
   if ((rc = chol_dalloc(h, (void**)&D->Zp, sizeof(double) * (size_t)std::max<int64_t>(h->panel_doubles, 1)))) return rc;
-  if ((rc = chol_dalloc(h, (void**)&D->Tw, sizeof(double) * ms * ms))) return rc;
-  if ((rc = chol_dalloc(h, (void**)&D->Ww, sizeof(double) * ms * 64))) return rc;
-  if ((rc = chol_dalloc(h, (void**)&D->Uh, sizeof(double) * mb * ms))) return rc;
-  if ((rc = chol_dalloc(h, (void**)&D->Zrr, sizeof(double) * mb * mb))) return rc;
-  std::vector<PairDev> pairs(h->rel_J.size());
-  for (size_t p = 0; p < pairs.size(); ++p) pairs[p] = {h->rel_K[p], h->rel_c0[p], h->rel_c1[p], 0};
-  if ((rc = upload_v(h, (PairDev**)&D->pairs, pairs))) return rc;
-  h->pair_begin.assign(h->ns + 1, 0);
-  for (size_t p = 0; p < h->rel_J.size(); ++p) h->pair_begin[h->rel_J[p] + 1]++;
-  for (int32_t J = 0; J < h->ns; ++J) h->pair_begin[J + 1] += h->pair_begin[J];
   // column index of every stored entry of A (original ordering)
   std::vector<int32_t> colidx(h->nnz_a), rowidx(h->nnz_a);
   for (int32_t c = 0; c < h->n; ++c)
     for (int64_t t = h->a_colptr[c]; t < h->a_colptr[c + 1]; ++t) colidx[t] = c;
   if ((rc = upload_v(h, &D->a_col, colidx))) return rc;
   if ((rc = upload_v(h, &D->a_row, h->a_rowind))) return rc;
-  CHOL_CUDA_TRY(cudaFuncSetAttribute(k_gather_zrr, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024));
   return CHOL_OK;
 }
 
-// Selected inverse into D->Zp (once per factorization).
+// Level plan of the selected inverse (built once, on first use).
+struct SiStep {
+  int32_t inv_b, inv_n, g1_b, g1_n, g2_b, g2_n;
+};
+struct SiLevel {
+  int64_t t_doubles;                    // T workspace of the level (zeroed first)
+  std::vector<SiStep> steps;            // the L_JJ^{-1} recurrence, batched
+  int32_t uh_b, uh_n, zrj_b, zrj_n, zjj1_b, zjj1_n, zjj2_b, zjj2_n;
+  int32_t pair_b, pair_n;
+};
+
+struct SiPlan {
+  std::vector<SiLevel> levels;
+  std::vector<GenGemm> descs;
+  std::vector<GemmTile> tiles;
+  std::vector<InvTask> invs;
+  std::vector<LevelPair> pairs;
+  GenGemm* d_descs = nullptr;
+  GemmTile* d_tiles = nullptr;
+  InvTask* d_invs = nullptr;
+  LevelPair* d_pairs = nullptr;
+};
+
+int32_t add_gemm(SiPlan& pl, const GenGemm& g) {
+  // returns the number of tiles added
+  if (g.M <= 0 || g.N <= 0) return 0;
+  const int32_t d = (int32_t)pl.descs.size();
+  pl.descs.push_back(g);
+  int32_t cnt = 0;
+  for (int ti = 0; ti * kGTile < g.M; ++ti)
+    for (int tj = 0; tj * kGTile < g.N; ++tj) {
+      if (g.lower_c && ti * kGTile + kGTile - 1 < tj * kGTile) continue;
+      pl.tiles.push_back({d, ti, tj, 0});
+      ++cnt;
+    }
+  return cnt;
+}
+
+int build_si_plan(chol_handle* h) {
+  DeviceState* D = h->dev;
+  if (D->si_plan) return CHOL_OK;
+  SiPlan* pl = new SiPlan();
+  const double* L = D->L;
+  double* Z = D->Zp;
+  int64_t tmax = 0, hmax = 0, wmax = 0;
+  // per-level offsets of T (s^2), Uhat (b s) and W (s x 64)
+  std::vector<int64_t> toff(h->ns), hoff(h->ns), woff(h->ns);
+  for (const LevelPlan& P : h->levels) {
+    int64_t t = 0, u = 0, w = 0;
+    for (int32_t q = 0; q < P.snode_n; ++q) {
+      const int32_t J = h->level_snodes[P.snode_b + q];
+      const SnodeDev& d = h->snodes[J];
+      toff[J] = t; hoff[J] = u; woff[J] = w;
+      t += (int64_t)d.s * d.s;
+      u += (int64_t)(d.len - d.s) * d.s;
+      w += (int64_t)d.s * 64;
+    }
+    tmax = std::max(tmax, t); hmax = std::max(hmax, u); wmax = std::max(wmax, w);
+  }
+  int rc;
+  if ((rc = chol_dalloc(h, (void**)&D->Tw, sizeof(double) * (size_t)std::max<int64_t>(tmax, 1)))) return rc;
+  if ((rc = chol_dalloc(h, (void**)&D->Uh, sizeof(double) * (size_t)std::max<int64_t>(hmax, 1)))) return rc;
+  if ((rc = chol_dalloc(h, (void**)&D->Ww, sizeof(double) * (size_t)std::max<int64_t>(wmax, 1)))) return rc;
+  std::vector<std::vector<int64_t>> pairs_of(h->ns);
+  for (size_t p = 0; p < h->rel_J.size(); ++p) pairs_of[h->rel_J[p]].push_back((int64_t)p);
+  for (int lv = h->nlevels - 1; lv >= 0; --lv) {
+    const LevelPlan& P = h->levels[lv];
+    SiLevel sl{};
+    std::vector<int32_t> Js(h->level_snodes.begin() + P.snode_b, h->level_snodes.begin() + P.snode_b + P.snode_n);
+    int maxnbk = 0;
+    int64_t tl = 0;
+    for (int32_t J : Js) {
+      maxnbk = std::max(maxnbk, (h->snodes[J].s + 63) / 64);
+      tl += (int64_t)h->snodes[J].s * h->snodes[J].s;
+    }
+    sl.t_doubles = tl;
+    // T = L_JJ^{-1}: block columns right to left, step q handles block nbk-1-q
+    for (int q = 0; q < maxnbk; ++q) {
+      SiStep st{};
+      st.inv_b = (int32_t)pl->invs.size();
+      for (int32_t J : Js) {
+        const SnodeDev& d = h->snodes[J];
+        const int nbk = (d.s + 63) / 64;
+        if (q >= nbk) continue;
+        const int k0 = 64 * (nbk - 1 - q), kb = std::min(64, d.s - k0);
+        double* T = D->Tw + toff[J];
+        pl->invs.push_back({L + d.loff + k0 + (int64_t)k0 * d.ld, d.ld, T + k0 + (int64_t)k0 * d.s, d.s, kb, 0});
+      }
+      st.inv_n = (int32_t)pl->invs.size() - st.inv_b;
+      st.g1_b = (int32_t)pl->tiles.size();
+      for (int32_t J : Js) {
+        const SnodeDev& d = h->snodes[J];
+        const int nbk = (d.s + 63) / 64;
+        if (q >= nbk) continue;
+        const int k0 = 64 * (nbk - 1 - q), kb = std::min(64, d.s - k0), m = d.s - (k0 + kb);
+        if (m <= 0) continue;
+        double* T = D->Tw + toff[J];
+        add_gemm(*pl, mk(T + (k0 + kb) + (int64_t)(k0 + kb) * d.s, 1, d.s, L + d.loff + (k0 + kb) + (int64_t)k0 * d.ld,
+                         1, d.ld, D->Ww + woff[J], 1, m, m, kb, m, 1.0, 0.0, 1, 0, 0));
+      }
+      st.g1_n = (int32_t)pl->tiles.size() - st.g1_b;
+      st.g2_b = (int32_t)pl->tiles.size();
+      for (int32_t J : Js) {
+        const SnodeDev& d = h->snodes[J];
+        const int nbk = (d.s + 63) / 64;
+        if (q >= nbk) continue;
+        const int k0 = 64 * (nbk - 1 - q), kb = std::min(64, d.s - k0), m = d.s - (k0 + kb);
+        if (m <= 0) continue;
+        double* T = D->Tw + toff[J];
+        add_gemm(*pl, mk(D->Ww + woff[J], 1, m, T + k0 + (int64_t)k0 * d.s, 1, d.s, T + (k0 + kb) + (int64_t)k0 * d.s, 1,
+                         d.s, m, kb, kb, -1.0, 0.0, 0, 1, 0));
+      }
+      st.g2_n = (int32_t)pl->tiles.size() - st.g2_b;
+      sl.steps.push_back(st);
+    }
+    // Uhat = L_RJ T
+    sl.uh_b = (int32_t)pl->tiles.size();
+    for (int32_t J : Js) {
+      const SnodeDev& d = h->snodes[J];
+      const int b = d.len - d.s;
+      if (b > 0)
+        add_gemm(*pl, mk(L + d.loff + d.s, 1, d.ld, D->Tw + toff[J], 1, d.s, D->Uh + hoff[J], 1, b, b, d.s, d.s, 1.0,
+                         0.0, 0, 1, 0));
+    }
+    sl.uh_n = (int32_t)pl->tiles.size() - sl.uh_b;
+    // Z_RR gather pairs
+    sl.pair_b = (int32_t)pl->pairs.size();
+    for (int32_t J : Js)
+      for (int64_t p : pairs_of[J]) pl->pairs.push_back({J, h->rel_K[p], h->rel_c0[p], h->rel_c1[p]});
+    sl.pair_n = (int32_t)pl->pairs.size() - sl.pair_b;
+    // Z_RJ = -Z_RR Uhat  (Z_RR at U_J's place in the update workspace)
+    sl.zrj_b = (int32_t)pl->tiles.size();
+    for (int32_t J : Js) {
+      const SnodeDev& d = h->snodes[J];
+      const int b = d.len - d.s;
+      if (b > 0)
+        add_gemm(*pl, mk(D->U + d.uoff, 1, b, D->Uh + hoff[J], 1, b, Z + d.loff + d.s, 1, d.ld, b, d.s, b, -1.0, 0.0, 2,
+                         0, 0));
+    }
+    sl.zrj_n = (int32_t)pl->tiles.size() - sl.zrj_b;
+    // Z_JJ = T^T T, then -= Uhat^T Z_RJ
+    sl.zjj1_b = (int32_t)pl->tiles.size();
+    for (int32_t J : Js) {
+      const SnodeDev& d = h->snodes[J];
+      double* T = D->Tw + toff[J];
+      add_gemm(*pl, mk(T, d.s, 1, T, 1, d.s, Z + d.loff, 1, d.ld, d.s, d.s, d.s, 1.0, 0.0, 0, 0, 1));
+    }
+    sl.zjj1_n = (int32_t)pl->tiles.size() - sl.zjj1_b;
+    sl.zjj2_b = (int32_t)pl->tiles.size();
+    for (int32_t J : Js) {
+      const SnodeDev& d = h->snodes[J];
+      const int b = d.len - d.s;
+      if (b > 0)
+        add_gemm(*pl, mk(D->Uh + hoff[J], b, 1, Z + d.loff + d.s, 1, d.ld, Z + d.loff, 1, d.ld, d.s, d.s, b, -1.0, 1.0, 0,
+                         0, 1));
+    }
+    sl.zjj2_n = (int32_t)pl->tiles.size() - sl.zjj2_b;
+    pl->levels.push_back(std::move(sl));
+  }
+  auto up = [&](auto** dst, const auto& v) -> int {
+    if (v.empty()) return CHOL_OK;
+    int r = chol_dalloc(h, (void**)dst, v.size() * sizeof(v[0]));
+    if (r) return r;
+    CHOL_CUDA_TRY(cudaMemcpy(*dst, v.data(), v.size() * sizeof(v[0]), cudaMemcpyHostToDevice));
+    return CHOL_OK;
+  };
+  if ((rc = up(&pl->d_descs, pl->descs))) return rc;
+  if ((rc = up(&pl->d_tiles, pl->tiles))) return rc;
+  if ((rc = up(&pl->d_invs, pl->invs))) return rc;
+  if ((rc = up(&pl->d_pairs, pl->pairs))) return rc;
+  D->si_plan = pl;
+  CHOL_CUDA_TRY(cudaFuncSetAttribute(k_gather_zrr_level, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024));
+  return CHOL_OK;
+}
+
+// Selected inverse into D->Zp (once per factorization), level by level from the
+// root, every supernode of a level at once.
 int selinv(chol_handle* h, cudaStream_t st) {
   if (h->selinv_valid) return CHOL_OK;
   int rc = ensure_adjoint(h);
   if (rc) return rc;
+  if ((rc = build_si_plan(h))) return rc;
   DeviceState* D = h->dev;
-  const double* L = D->L;
-  double* Z = D->Zp;
-  const PairDev* pairs = (const PairDev*)D->pairs;
-  for (int32_t J = h->ns - 1; J >= 0; --J) {
-    const SnodeDev& d = h->snodes[J];
-    const int s = d.s, b = d.len - d.s;
-    const int64_t ld = d.ld;
-    const double* Lp = L + d.loff;
-    double* Zp = Z + d.loff;
-    double* T = D->Tw;
-    CHOL_CUDA_TRY(cudaMemsetAsync(T, 0, sizeof(double) * (size_t)s * s, st));
-    // T = L_JJ^{-1}, block columns right to left:
-    // T_kk = inv(L_kk), T_{>k,k} = -T_{>k,>k} L_{>k,k} T_kk
-    const int nbk = (s + 63) / 64;
-    for (int k = nbk - 1; k >= 0; --k) {
-      const int k0 = 64 * k, kb = std::min(64, s - k0);
-      k_inv64<<<1, 64, 0, st>>>(Lp + k0 + k0 * ld, ld, kb, T + k0 + (int64_t)k0 * s, s);
-      const int m = s - (k0 + kb);
-      if (m > 0) {
-        gemm(st, mk(T + (k0 + kb) + (int64_t)(k0 + kb) * s, 1, s, Lp + (k0 + kb) + (int64_t)k0 * ld, 1, ld, D->Ww, 1, m,
-                    m, kb, m, 1.0, 0.0, 1, 0, 0));
-        gemm(st, mk(D->Ww, 1, m, T + k0 + (int64_t)k0 * s, 1, s, T + (k0 + kb) + (int64_t)k0 * s, 1, s, m, kb, kb, -1.0,
-                    0.0, 0, 1, 0));
-      }
+  SiPlan* pl = (SiPlan*)D->si_plan;
+  auto launch = [&](int32_t b, int32_t n) {
+    if (n > 0) k_gen_gemm_grouped<<<n, kGT, 0, st>>>(pl->d_descs, pl->d_tiles + b);
+  };
+  for (const SiLevel& sl : pl->levels) {
+    CHOL_CUDA_TRY(cudaMemsetAsync(D->Tw, 0, sizeof(double) * (size_t)sl.t_doubles, st));
+    for (const SiStep& q : sl.steps) {
+      if (q.inv_n > 0) k_inv64_grouped<<<q.inv_n, 64, 0, st>>>(pl->d_invs + q.inv_b);
+      launch(q.g1_b, q.g1_n);
+      launch(q.g2_b, q.g2_n);
     }
-    if (b > 0) {
-      // Uhat = L_RJ T   (b x s)
-      gemm(st, mk(Lp + s, 1, ld, T, 1, s, D->Uh, 1, b, b, s, s, 1.0, 0.0, 0, 1, 0));
-      // Z_RR from the ancestors
-      const int np = h->pair_begin[J + 1] - h->pair_begin[J];
-      if (np > 0)
-        k_gather_zrr<<<np, kGT, sizeof(int32_t) * 2 * h->max_len, st>>>(pairs + h->pair_begin[J], d, D->sn, D->rows, Z,
-                                                                         D->Zrr);
-      // Z_RJ = -Z_RR Uhat
-      gemm(st, mk(D->Zrr, 1, b, D->Uh, 1, b, Zp + s, 1, ld, b, s, b, -1.0, 0.0, 2, 0, 0));
-    }
-    // Z_JJ = T^T T - Uhat^T Z_RJ  (lower)
-    gemm(st, mk(T, s, 1, T, 1, s, Zp, 1, ld, s, s, s, 1.0, 0.0, 0, 0, 1));
-    if (b > 0) gemm(st, mk(D->Uh, b, 1, Zp + s, 1, ld, Zp, 1, ld, s, s, b, -1.0, 1.0, 0, 0, 1));
+    launch(sl.uh_b, sl.uh_n);
+    if (sl.pair_n > 0)
+      k_gather_zrr_level<<<sl.pair_n, kGT, sizeof(int32_t) * 2 * h->max_len, st>>>(pl->d_pairs + sl.pair_b, D->sn,
+                                                                                   D->rows, D->Zp, D->U);
+    launch(sl.zrj_b, sl.zrj_n);
+    launch(sl.zjj1_b, sl.zjj1_n);
+    launch(sl.zjj2_b, sl.zjj2_n);
   }
   CHOL_CUDA_TRY(cudaGetLastError());
   h->selinv_valid = true;
@@ -292,6 +453,17 @@ int selinv(chol_handle* h, cudaStream_t st) {
 }
 
 }  // namespace
+
+void chol_adjoint_free(chol_handle* h) {
+  DeviceState* D = h->dev;
+  if (!D || !D->si_plan) return;
+  SiPlan* pl = (SiPlan*)D->si_plan;
+  void* ptrs[] = {pl->d_descs, pl->d_tiles, pl->d_invs, pl->d_pairs};
+  for (void* p : ptrs)
+    if (p) cudaFree(p);
+  delete pl;
+  D->si_plan = nullptr;
+}
 
 extern "C" int chol_selected_inverse(chol_handle* h, double* zvals, void* stream) {
   if (!h) return -1;

@@ -10,6 +10,7 @@
 
 struct DeviceState {
   int device = -1;
+  int sms = 152;                // streaming multiprocessors of the device
   int64_t bytes = 0;            // bytes allocated so far (for the optional cap)
   double* L = nullptr;          // supernodal panels
   double* U = nullptr;          // update-matrix workspace (one level)
@@ -78,11 +79,10 @@ struct DeviceState {
   double* Tw = nullptr;            // L_JJ^{-1}
   double* Ww = nullptr;
   double* Uh = nullptr;            // L_RJ L_JJ^{-1}
-  double* Zrr = nullptr;           // Z_RR gathered from the ancestors
-  void* pairs = nullptr;
   int32_t* a_col = nullptr;        // column / row of every stored entry of A
   int32_t* a_row = nullptr;
   double* adj_xb = nullptr;
+  void* si_plan = nullptr;         // level plan of the selected inverse (adjoint.cu)
   int adj_cap = 0;
   // solve workspaces (grown on demand)
   double* Y = nullptr;          // permuted right-hand sides, n x chunk

@@ -547,10 +547,11 @@ void chol_device_free(chol_handle* h) {
   int cur = -1;
   cudaGetDevice(&cur);
   if (D->device >= 0) cudaSetDevice(D->device);
+  chol_adjoint_free(h);
   void* ptrs[] = {D->L, D->U, D->sn, D->rows, D->amap, D->small_list, D->potrf_list,
                   D->level_snodes, D->trsm, D->gemm, D->syrk, D->asm_tasks, D->asm_segs, D->sdiag,
                   D->fupd, D->bupd, D->bpanel, D->gemv, D->bpart, D->bred, D->P32, D->plevels, D->vals, D->sys_snode, D->sys_out,
-                  D->ssmall, D->Zp, D->Tw, D->Ww, D->Uh, D->Zrr, D->pairs, D->a_col, D->a_row, D->adj_xb, D->perm, D->status, D->part, D->scalar_dev, D->Y, D->W,
+                  D->ssmall, D->Zp, D->Tw, D->Ww, D->Uh, D->a_col, D->a_row, D->adj_xb, D->perm, D->status, D->part, D->scalar_dev, D->Y, D->W,
                   D->mx_diagpos, D->mx_aij, D->mx_d, D->mx_fallbacks, D->csr_ptr, D->csr_col, D->csr_src,
                   D->csr_val, D->Lbf, D->tmaps, D->tc_err, D->R, D->Z, D->Pv, D->Q, D->red, D->Y32, D->W32,
                   D->rhs_scale};
@@ -582,6 +583,7 @@ int chol_device_ensure(chol_handle* h) {
     return code;
   };
   if (cudaGetDevice(&D->device) != cudaSuccess) return fail(CHOL_ECUDA);
+  if (cudaDeviceGetAttribute(&D->sms, cudaDevAttrMultiProcessorCount, D->device) != cudaSuccess) return fail(CHOL_ECUDA);
   if (h->opt.precision != CHOL_PREC_FP64) {
     // the tensor-core and binary32 kernels are built for this architecture only
     cudaDeviceProp prop;

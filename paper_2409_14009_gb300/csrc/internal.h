@@ -97,7 +97,6 @@ struct chol_handle {
   int32_t fp64_fallbacks = 0;
   std::vector<int64_t> a_colptr;    // the analyzed pattern of A (for gradients)
   std::vector<int32_t> a_rowind;
-  std::vector<int32_t> pair_begin;  // first (J, K) pair of every supernode
   bool selinv_valid = false;        // selected inverse of the current factor computed
   int32_t perturbed_pivots = 0;
   std::vector<int64_t> diagpos_orig;  // position of A_jj in the values array, per original column

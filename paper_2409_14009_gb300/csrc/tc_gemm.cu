@@ -22,7 +22,7 @@ typedef CUresult (*EncodeTiledFn)(CUtensorMap*, CUtensorMapDataType, cuuint32_t,
 template <int KIND>
 __global__ void __launch_bounds__(tc::kThreads, 1)
 k_tc_trailing(const CUtensorMap* __restrict__ maps, const TileTask* __restrict__ tasks,
-              const SnodeDev* __restrict__ sn, int nb, float* __restrict__ L, int* err) {
+              const SnodeDev* __restrict__ sn, int nb, float* __restrict__ L, int stages, int* err) {
   extern __shared__ uint8_t smem[];
   const TileTask t = tasks[blockIdx.x];
   const SnodeDev d = sn[t.J];
@@ -39,14 +39,14 @@ k_tc_trailing(const CUtensorMap* __restrict__ maps, const TileTask* __restrict__
   job.n = min(tc::kTileN, d.s - t.c0);
   job.rdiag = t.r0 - t.c0;
   job.sub = true;
-  tc::tile_body<KIND>(job, smem, err);
+  tc::tile_body<KIND>(job, smem, stages, err);
 }
 
 // U_J tile (row-major lower, leading dimension b rounded to 8) = L_RJ L_RJ^T.
 template <int KIND>
 __global__ void __launch_bounds__(tc::kThreads, 1)
 k_tc_syrk(const CUtensorMap* __restrict__ maps, const TileTask* __restrict__ tasks,
-          const SnodeDev* __restrict__ sn, float* __restrict__ U, int* err) {
+          const SnodeDev* __restrict__ sn, float* __restrict__ U, int stages, int* err) {
   extern __shared__ uint8_t smem[];
   const TileTask t = tasks[blockIdx.x];
   const SnodeDev d = sn[t.J];
@@ -64,7 +64,7 @@ k_tc_syrk(const CUtensorMap* __restrict__ maps, const TileTask* __restrict__ tas
   job.n = min(tc::kTileN, b - t.c0);
   job.rdiag = t.r0 - t.c0;
   job.sub = false;
-  tc::tile_body<KIND>(job, smem, err);
+  tc::tile_body<KIND>(job, smem, stages, err);
 }
 
 }  // namespace
@@ -113,26 +113,30 @@ int chol_tc_prepare(chol_handle* h) {
   const void* kernels[] = {(const void*)k_tc_trailing<0>, (const void*)k_tc_trailing<1>, (const void*)k_tc_syrk<0>,
                            (const void*)k_tc_syrk<1>};
   for (const void* k : kernels)
-    CHOL_CUDA_TRY(cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, tc::kSmemBytes));
+    CHOL_CUDA_TRY(cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, tc::kSmemMax));
   return CHOL_OK;
 }
 
 int chol_tc_gemm(chol_handle* h, const TileTask* tasks, int n, int k0, int nb, cudaStream_t st) {
   (void)k0;
   DeviceState* D = h->dev;
+  const int ns = tc::stages_for(n, D->sms);
+  const int sm = tc::smem_bytes(ns);
   if (h->opt.precision == CHOL_PREC_TF32)
-    k_tc_trailing<0><<<n, tc::kThreads, tc::kSmemBytes, st>>>(D->tmaps, tasks, D->sn, nb, (float*)D->L, D->tc_err);
+    k_tc_trailing<0><<<n, tc::kThreads, sm, st>>>(D->tmaps, tasks, D->sn, nb, (float*)D->L, ns, D->tc_err);
   else
-    k_tc_trailing<1><<<n, tc::kThreads, tc::kSmemBytes, st>>>(D->tmaps, tasks, D->sn, nb, (float*)D->L, D->tc_err);
+    k_tc_trailing<1><<<n, tc::kThreads, sm, st>>>(D->tmaps, tasks, D->sn, nb, (float*)D->L, ns, D->tc_err);
   return CHOL_OK;
 }
 
 int chol_tc_syrk(chol_handle* h, const TileTask* tasks, int n, cudaStream_t st) {
   DeviceState* D = h->dev;
+  const int ns = tc::stages_for(n, D->sms);
+  const int sm = tc::smem_bytes(ns);
   if (h->opt.precision == CHOL_PREC_TF32)
-    k_tc_syrk<0><<<n, tc::kThreads, tc::kSmemBytes, st>>>(D->tmaps, tasks, D->sn, (float*)D->U, D->tc_err);
+    k_tc_syrk<0><<<n, tc::kThreads, sm, st>>>(D->tmaps, tasks, D->sn, (float*)D->U, ns, D->tc_err);
   else
-    k_tc_syrk<1><<<n, tc::kThreads, tc::kSmemBytes, st>>>(D->tmaps, tasks, D->sn, (float*)D->U, D->tc_err);
+    k_tc_syrk<1><<<n, tc::kThreads, sm, st>>>(D->tmaps, tasks, D->sn, (float*)D->U, ns, D->tc_err);
   return CHOL_OK;
 }
 

@@ -4,13 +4,17 @@
 // One CTA computes one 128 x 128 tile D = A B^T, where A and B are 128-row slices
 // of a row-major panel (K contiguous, i.e. both operands K-major):
 // - TMA loads 128-byte-wide K chunks (32 binary32 / 64 bf16 elements per row) with
-//   the 128-byte swizzle into a 4-stage shared-memory ring. Rows or columns past
-//   the panel read as zeros (out-of-bounds fill).
+//   the 128-byte swizzle into a shared-memory ring of 2 or 6 stages (chosen per
+//   launch: 2 stages leave room for three CTAs per SM when the launch has tiles
+//   for all of them, 6 give one CTA a deeper pipeline when it does not). Rows or
+//   columns past the panel read as zeros (out-of-bounds fill).
 // - One thread issues tcgen05.mma (kind::tf32 or kind::f16 with bf16 operands)
 //   into a 128 x 128 binary32 accumulator in tensor memory and releases each
 //   stage with tcgen05.commit.
-// - Four warps read the accumulator back with tcgen05.ld and apply the masked
-//   epilogue (overwrite for U, subtract for the panel).
+// - Four warps read the accumulator back with tcgen05.ld (32 columns per load)
+//   and apply the masked epilogue (overwrite for U, subtract for the panel),
+//   with 16-byte loads and stores where a 32-column run is entirely in the
+//   mask; the C values of a run are loaded before the accumulator read.
 // Every wait is bounded: on a timeout the CTA records an error code, stops
 // issuing, waits (bounded) for its own copies in flight, frees its tensor memory
 // and returns.
@@ -21,13 +25,18 @@
 
 namespace tc {
 
-constexpr int kStages = 4;
+constexpr int kMaxStages = 6;
+constexpr int kFewStages = 2;
 constexpr int kTileM = 128;
 constexpr int kTileN = 128;
 constexpr int kChunkBytes = 128;                   // K extent of one stage, per row
 constexpr int kOperandBytes = kTileM * kChunkBytes;   // 16 KiB per operand per stage
 constexpr int kStageBytes = 2 * kOperandBytes;
-constexpr int kSmemBytes = kStages * kStageBytes + 1024;   // + alignment slack
+constexpr int kSmemMax = kMaxStages * kStageBytes + 1024;   // + alignment slack
+__host__ __device__ constexpr int smem_bytes(int stages) { return stages * kStageBytes + 1024; }
+// Stages for a launch of `tiles` CTAs on `sms` SMs: 2 (three CTAs per SM) when
+// every SM gets at least two tiles, else the deep ring.
+inline int stages_for(int tiles, int sms) { return tiles >= 2 * sms ? kFewStages : kMaxStages; }
 constexpr int kThreads = 128;
 constexpr int kTmemCols = 128;
 
@@ -125,6 +134,21 @@ __device__ __forceinline__ void tmem_ld8(uint32_t taddr, float (&v)[8]) {
   for (int i = 0; i < 8; ++i) v[i] = __uint_as_float(r[i]);
 }
 
+__device__ __forceinline__ void tmem_ld32(uint32_t taddr, float (&v)[32]) {
+  uint32_t r[32];
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15, "
+      "%16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31}, [%32];"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]), "=r"(r[8]),
+        "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]), "=r"(r[16]),
+        "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]), "=r"(r[24]),
+        "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+      : "r"(taddr));
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+  for (int i = 0; i < 32; ++i) v[i] = __uint_as_float(r[i]);
+}
+
 // Geometry of one tile: operand rows a_row / b_row in the panel's tensor map,
 // K range [k_begin, k_end), output C (row-major, ldc) with m x n valid entries,
 // entry (i, j) written only when i + rdiag >= j; SUB: C -= D, else C = D.
@@ -140,9 +164,9 @@ struct TileJob {
 // The CTA body. KIND 0: tf32 operands (32 elements per 128-byte chunk, K = 8 per
 // MMA); KIND 1: bf16 operands (64 per chunk, K = 16 per MMA).
 template <int KIND>
-__device__ __forceinline__ void tile_body(const TileJob& job, uint8_t* smem_raw, int* err) {
-  __shared__ __align__(8) uint64_t full_bar[kStages];
-  __shared__ __align__(8) uint64_t empty_bar[kStages];
+__device__ __forceinline__ void tile_body(const TileJob& job, uint8_t* smem_raw, int kStages, int* err) {
+  __shared__ __align__(8) uint64_t full_bar[kMaxStages];
+  __shared__ __align__(8) uint64_t empty_bar[kMaxStages];
   __shared__ __align__(8) uint64_t accum_bar;
   __shared__ uint32_t tmem_slot;
   __shared__ int abort_flag;
@@ -228,15 +252,31 @@ __device__ __forceinline__ void tile_body(const TileJob& job, uint8_t* smem_raw,
   if (acc_ready) {
     const int row = warp * 32 + lane;
     const uint32_t trow = tmem + ((uint32_t)(warp * 32) << 16);
-    for (int cb = 0; cb < kTileN / 8; ++cb) {
-      if (cb * 8 >= job.n) break;                       // uniform across the CTA
-      float v[8];
-      tmem_ld8(trow + (uint32_t)(cb * 8), v);
-      if (row < job.m) {
-        float* crow = job.C + (int64_t)row * job.ldc;
+    float* crow = job.C + (int64_t)row * job.ldc;
+    for (int cb = 0; cb < kTileN / 32; ++cb) {
+      const int c0 = cb * 32;
+      if (c0 >= job.n) break;                            // uniform across the CTA
+      // the whole run is inside the tile and the mask, and 16-byte aligned
+      const bool full = row < job.m && c0 + 32 <= job.n && row + job.rdiag >= c0 + 31 &&
+                        (reinterpret_cast<uintptr_t>(crow + c0) & 15u) == 0;
+      float4 c[8];
+      if (job.sub && full) {
 #pragma unroll
-        for (int j = 0; j < 8; ++j) {
-          const int col = cb * 8 + j;
+        for (int q = 0; q < 8; ++q) c[q] = reinterpret_cast<const float4*>(crow + c0)[q];
+      }
+      float v[32];
+      tmem_ld32(trow + (uint32_t)c0, v);
+      if (full) {
+#pragma unroll
+        for (int q = 0; q < 8; ++q) {
+          float4 o = make_float4(v[4 * q], v[4 * q + 1], v[4 * q + 2], v[4 * q + 3]);
+          if (job.sub) o = make_float4(c[q].x - o.x, c[q].y - o.y, c[q].z - o.z, c[q].w - o.w);
+          reinterpret_cast<float4*>(crow + c0)[q] = o;
+        }
+      } else if (row < job.m) {
+#pragma unroll
+        for (int j = 0; j < 32; ++j) {
+          const int col = c0 + j;
           if (col < job.n && row + job.rdiag >= col) {
             if (job.sub) crow[col] -= v[j];
             else crow[col] = v[j];

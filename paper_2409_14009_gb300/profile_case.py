@@ -1,0 +1,74 @@
+"""One factorization (and optionally one solve or one adjoint) of a named
+synthetic workload, for running under a profiler.
+
+    python -m paper_2409_14009_gb300.profile_case --grid elast:32 --precision bf16
+    python -m paper_2409_14009_gb300.profile_case --grid neumann:48 --adjoint
+
+Grids: ``neumann:k`` (7-point variable-coefficient k^3 Laplacian, Neumann,
+shift 1e-6), ``dirichlet:k`` (7-point weighted k^3 Laplacian with Dirichlet
+ghosts), ``elast:k`` (27-point 3-dof elasticity on a k^3 grid). The CUDA
+library must already be built (``paper_2409_14009_gb300/build.py``).
+"""
+import argparse
+import sys
+import os
+
+sys.path.insert(0, os.path.dirname(os.path.dirname(os.path.abspath(__file__))))
+
+import numpy as np  # noqa: E402
+import torch  # noqa: E402
+
+import gridgen  # noqa: E402
+import paper_2409_14009_gb300 as P  # noqa: E402
+
+PRECISIONS = {"fp64": P.CHOL_PREC_FP64, "fp32": P.CHOL_PREC_FP32, "tf32": P.CHOL_PREC_TF32,
+              "bf16": P.CHOL_PREC_BF16}
+
+
+def make(grid: str):
+    kind, k = grid.split(":")
+    k = int(k)
+    if kind == "neumann":
+        return gridgen.laplacian_neumann_varcoef((k, k, k), 1e-2, 1e2, 1e-6, seed=2)
+    if kind == "dirichlet":
+        return gridgen.laplacian_dirichlet_weighted((k, k, k), gridgen.SplitMix64(5), 1e-2, 1e2)
+    if kind == "elast":
+        return gridgen.elasticity_27pt(k, 1.0, 1e6, seed=3)
+    raise SystemExit(f"unknown grid {grid}")
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--grid", default="neumann:48")
+    ap.add_argument("--precision", default="fp64", choices=sorted(PRECISIONS))
+    ap.add_argument("--merge", type=float, default=0.1)
+    ap.add_argument("--factors", type=int, default=1, help="factorizations to run")
+    ap.add_argument("--nrhs", type=int, default=0, help="solve with this many right-hand sides")
+    ap.add_argument("--adjoint", action="store_true", help="run one adjoint (selected inverse + gradient)")
+    a = ap.parse_args()
+    p = make(a.grid)
+    o = P.chol_default_options()
+    o.precision = PRECISIONS[a.precision]
+    o.merge_growth = a.merge
+    S = P.SparseCholesky(p.n, p["colptr"], p["rowind"], p["perm"], o)
+    vals = torch.as_tensor(p["values"], device="cuda")
+    for _ in range(a.factors):
+        S.factor(vals)
+    if a.nrhs:
+        b = torch.as_tensor(gridgen.rhs_uniform(p.n, a.nrhs, seed=7), device="cuda")
+        S.solve(b)
+    if a.adjoint:
+        b = torch.as_tensor(gridgen.rhs_uniform(p.n, 1, seed=7), device="cuda")
+        x = S.solve(b)
+        w = torch.ones_like(x)
+        bbar = torch.empty_like(x)
+        grad = torch.empty(len(p["rowind"]), dtype=torch.float64, device="cuda")
+        rc = P.chol_adjoint(S.h, w, x, 1, 1.0, bbar, grad)
+        if rc:
+            raise P.CholError(rc, "chol_adjoint")
+    torch.cuda.synchronize()
+    print(f"ok n={p.n} flops={S.info.flops:.4g} panels={S.info.panel_doubles * (8 if a.precision == 'fp64' else 4) / 1e9:.3f} GB")
+
+
+if __name__ == "__main__":
+    main()
