@@ -95,6 +95,22 @@ class ClockSampler:
                 "samples": len(sm)}
 
 
+def max_over_ranks(dist, values, device):
+    """Element-wise maximum of per-rank timings (every rank gets the result)."""
+    import torch
+    if dist is None:
+        return [float(v) for v in values]
+    t = torch.tensor([float(v) for v in values], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return [float(v) for v in t.tolist()]
+
+
+def replica_throughput(flops_per_replica, world, ms_max):
+    """Whole-job GFLOP/s of `world` independent replicas, each doing one step of
+    `flops_per_replica` flops, finishing within the slowest rank's `ms_max`."""
+    return flops_per_replica * world / (ms_max * 1e-3) / 1e9
+
+
 def _cpu_cores():
     try:
         return len(os.sched_getaffinity(0))
@@ -416,11 +432,7 @@ def run_ours(args, rank, world, local_rank):
                                                          factor_ms, solve_ms)
     batch = None if args.no_batch else batch_run(args, P, gridgen, torch, dev)
     adjoint = None if args.no_adjoint else adjoint_run(args, P, gridgen, torch, dev)
-    # max over ranks
-    if dist:
-        t = torch.tensor([ms, e2e_ms], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms, e2e_ms = float(t[0]), float(t[1])
+    ms, e2e_ms = max_over_ranks(dist, [ms, e2e_ms], dev)
     if rank == 0:
         dom = max(("gemm", "syrk"), key=lambda k: stats[k]["ms"])
         ds = stats[dom]
@@ -436,7 +448,7 @@ def run_ours(args, rank, world, local_rank):
             cpu = {"value": v, "unit": "GFLOP/s", "cores": 1, "kind": "oracle",
                    "sample": "oracle FP64 factor+solve(8 RHS), same generator on a %d^3 grid (n=%d), %.1f s"
                              % (args.cpu_grid, n, dt)}
-        line = {"metric": METRIC, "value": flops * world / (ms * 1e-3) / 1e9, "unit": "GFLOP/s",
+        line = {"metric": METRIC, "value": replica_throughput(flops, world, ms), "unit": "GFLOP/s",
                 "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
                 "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
                 "data": "synthetic",
@@ -449,7 +461,7 @@ def run_ours(args, rank, world, local_rank):
                 "factor_ms": factor_ms, "solve_ms": solve_ms,
                 "factor_gflops": flops / (factor_ms * 1e-3) / 1e9, "flops": flops,
                 "backward_error": float(eta), "logdet": ld[0],
-                "e2e": {"value": flops * world / (e2e_ms * 1e-3) / 1e9, "unit": "GFLOP/s",
+                "e2e": {"value": replica_throughput(flops, world, e2e_ms), "unit": "GFLOP/s",
                         "ms_per_step": e2e_ms, "h2d_bytes_per_step": int(hv.numel() * 8 + hb.numel() * 8),
                         "d2h_bytes_per_step": int(hx.numel() * 8)},
                 "gpu_launches": launches // max(args.steps, 1) * args.steps,

@@ -197,10 +197,13 @@ int chol_solve_refine(chol_handle* h, const double* b, double* x, int32_t nrhs, 
 /*
  * Selected inverse: zvals[t] = (A^{-1})_ij for every stored entry t = (i, j)
  * of the analyzed lower pattern of A (device, colptr[n] doubles). Computed
- * once per factorization, supernode by supernode from the root down (dense
- * blocks: T = L_JJ^{-1}, Uhat = L_RJ T, Z_RJ = -Z_RR Uhat with Z_RR gathered
- * from the ancestors through the relative positions, Z_JJ = T^T T -
- * Uhat^T Z_RJ). CHOL_PREC_FP64 handles only (else CHOL_ENOTSUP). Asynchronous.
+ * once per factorization, level by level of the supernodal tree from the
+ * root down, every supernode of a level at once (dense blocks: T = L_JJ^{-1},
+ * Uhat = L_RJ T, Z_RJ = -Z_RR Uhat with Z_RR gathered from the ancestors
+ * through the relative positions, Z_JJ = T^T T - Uhat^T Z_RJ). The first call
+ * builds the level plan and its workspaces (largest level's sum of s^2,
+ * b s and 64 s doubles). CHOL_PREC_FP64 handles only (else CHOL_ENOTSUP).
+ * Asynchronous.
  */
 int chol_selected_inverse(chol_handle* h, double* zvals, void* stream);
 
