@@ -424,6 +424,8 @@ int build_si_plan(chol_handle* h) {
 // root, every supernode of a level at once.
 int selinv(chol_handle* h, cudaStream_t st) {
   if (h->selinv_valid) return CHOL_OK;
+  // the Z_RR gather stages struct(K) and the positions in shared memory
+  if ((int64_t)h->max_len * 2 * (int64_t)sizeof(int32_t) > 200 * 1024) return CHOL_ENOTSUP;
   int rc = ensure_adjoint(h);
   if (rc) return rc;
   if ((rc = build_si_plan(h))) return rc;

@@ -7,6 +7,8 @@
 // update matrix of J into its ancestor K. On top of those the level schedule
 // and the task lists of the CUDA kernels are built once, here, on the host.
 #include <algorithm>
+#include <limits>
+#include <array>
 #include <cstring>
 #include <new>
 #include <numeric>
@@ -413,7 +415,8 @@ void build(chol_handle* h, const int64_t* colptr, const int32_t* rowind) {
   // it at one 64-column block (a single SM's FP64 rate is the limit); binary32
   // takes 256 to cut the number of dependent launches.
   h->solve_sb = h->opt.precision == CHOL_PREC_FP64 ? 64 : kSolveSB;
-  const int tg = (h->opt.precision == CHOL_PREC_TF32 || h->opt.precision == CHOL_PREC_BF16) ? kTileTC : kTile;
+  const bool tc_modes = h->opt.precision == CHOL_PREC_TF32 || h->opt.precision == CHOL_PREC_BF16;
+  const int tg = tc_modes ? kTileTC : kTile;
   std::vector<std::vector<int32_t>> by_level(h->nlevels);
   for (int32_t J = 0; J < ns; ++J) by_level[h->level[J]].push_back(J);
   // pairs by contributor level, then K, then J
@@ -470,9 +473,11 @@ void build(chol_handle* h, const int64_t* colptr, const int32_t* rowind) {
     for (int32_t k0 = 0; k0 < maxs; k0 += nb) {
       StepRange st{};
       st.potrf_b = (int32_t)h->potrf_list.size();
-      st.potrf_flops = st.trsm_flops = st.gemm_flops = 0.0;
+      st.potrf_flops = st.trsm_flops = st.gemm_flops = st.ogemm_flops = 0.0;
       st.trsm_b = (int32_t)h->trsm_tasks.size();
       st.gemm_b = (int32_t)h->gemm_tasks.size();
+      // tensor-core modes: the outer block holding this step, [ob, ob + kTcOuter)
+      const int32_t ob = (k0 / kTcOuter) * kTcOuter;
       for (int32_t J : large) {
         const SnodeDev& d = h->snodes[J];
         if (d.s <= k0) continue;
@@ -483,17 +488,35 @@ void build(chol_handle* h, const int64_t* colptr, const int32_t* rowind) {
         const double below = (double)(d.len - k0 - kb);
         st.trsm_flops += below * (double)kb * (double)kb;   // kb divisions + 2*kb(kb-1)/2 per row
         for (int32_t r0 = k0 + kb; r0 < d.len; r0 += kTrsmRowsHost) h->trsm_tasks.push_back({J, k0, r0, 0});
-        for (int32_t c0 = k0 + kb; c0 < d.s; c0 += tg)
+        // the step's own trailing update covers columns [k0+kb, cend)
+        const int32_t cend = tc_modes ? std::min(d.s, ob + kTcOuter) : d.s;
+        for (int32_t c0 = k0 + kb; c0 < cend; c0 += tg)
           for (int32_t r0 = c0; r0 < d.len; r0 += tg) h->gemm_tasks.push_back({J, k0, r0, c0});
-        // trailing update: 2 kb flops per entry (r, c) with c in [k0+kb, s), r in [c, len)
+        // trailing update: 2 kb flops per entry (r, c) with c in [k0+kb, cend), r in [c, len)
         {
-          const double w = (double)(d.s - k0 - kb), hgt = (double)(d.len - k0 - kb);
+          const double w = (double)(cend - k0 - kb), hgt = (double)(d.len - k0 - kb);
           st.gemm_flops += 2.0 * kb * (w * hgt - w * (w - 1.0) / 2.0);
         }
       }
       st.potrf_n = (int32_t)h->potrf_list.size() - st.potrf_b;
       st.trsm_n = (int32_t)h->trsm_tasks.size() - st.trsm_b;
       st.gemm_n = (int32_t)h->gemm_tasks.size() - st.gemm_b;
+      // after the last step of an outer block: the columns right of it, K = the block
+      st.ogemm_b = (int32_t)h->gemm_tasks.size();
+      st.ok0 = ob;
+      st.okb = kTcOuter;
+      if (tc_modes && (k0 + nb) % kTcOuter == 0) {
+        const int32_t oend = ob + kTcOuter;
+        for (int32_t J : large) {
+          const SnodeDev& d = h->snodes[J];
+          if (d.s <= oend) continue;
+          for (int32_t c0 = oend; c0 < d.s; c0 += tg)
+            for (int32_t r0 = c0; r0 < d.len; r0 += tg) h->gemm_tasks.push_back({J, ob, r0, c0});
+          const double w = (double)(d.s - oend), hgt = (double)(d.len - oend);
+          st.ogemm_flops += 2.0 * kTcOuter * (w * hgt - w * (w - 1.0) / 2.0);
+        }
+      }
+      st.ogemm_n = (int32_t)h->gemm_tasks.size() - st.ogemm_b;
       P.steps.push_back(st);
     }
     P.syrk_b = (int32_t)h->syrk_tasks.size();
@@ -578,15 +601,18 @@ void build(chol_handle* h, const int64_t* colptr, const int32_t* rowind) {
     });
     P.asm_b = (int32_t)h->asm_tasks.size();
     P.asm_entries = 0.0;
+    std::vector<AsmTask> warp_tasks;   // placed after the level's CTA tasks
     size_t q = 0;
     while (q < pl.size()) {
       int32_t K = h->rel_K[pl[q]];
       size_t q1 = q;
       while (q1 < pl.size() && h->rel_K[pl[q1]] == K) ++q1;
       const SnodeDev& dk = h->snodes[K];
+      const int32_t* rk = h->rows.data() + dk.roff;
       for (int32_t t0 = 0; t0 < dk.s; t0 += kAsmCols) {
         int32_t t1 = std::min(dk.s, t0 + kAsmCols);
-        AsmTask task{K, t0, t1, (int32_t)h->asm_segs.size(), 0, 0, 0, 0};
+        // the segments of this column tile
+        std::vector<std::array<int32_t, 3>> tile_segs;
         for (size_t z = q; z < q1; ++z) {
           int64_t p = pl[z];
           const SnodeDev& dj = h->snodes[h->rel_J[p]];
@@ -596,22 +622,48 @@ void build(chol_handle* h, const int64_t* colptr, const int32_t* rowind) {
           int32_t ce = ca;
           while (ce < cb && rj[dj.s + ce] - dk.f < t1) ++ce;
           if (ce > ca) {
-            h->asm_segs.push_back({h->rel_J[p], ca, ce, 0});
+            tile_segs.push_back({h->rel_J[p], ca, ce});
             const double bj = dj.len - dj.s;
             for (int32_t c = ca; c < ce; ++c) P.asm_entries += bj - c;
           }
         }
-        task.seg_end = (int32_t)h->asm_segs.size();
-        if (task.seg_end > task.seg_begin) h->asm_tasks.push_back(task);
+        if (tile_segs.empty()) continue;
+        // split the row positions [t0, len) of K into chunks; a segment's rows
+        // in a chunk are those between the chunk's first and next row indices
+        for (int32_t p0 = t0; p0 < dk.len; p0 += kAsmPos) {
+          const int32_t p1 = std::min(dk.len, p0 + kAsmPos);
+          const int32_t r0 = rk[p0];
+          const int32_t r1 = p1 < dk.len ? rk[p1] : std::numeric_limits<int32_t>::max();
+          AsmTask task{K, t0, t1, (int32_t)h->asm_segs.size(), 0, p0, p1, 0};
+          int64_t entries = 0;
+          for (const auto& sgm : tile_segs) {
+            const SnodeDev& dj = h->snodes[sgm[0]];
+            const int32_t* ro = h->rows.data() + dj.roff + dj.s;
+            const int32_t b = dj.len - dj.s;
+            const int32_t ua = (int32_t)(std::lower_bound(ro + sgm[1], ro + b, r0) - ro);
+            const int32_t ub = (int32_t)(std::lower_bound(ro + ua, ro + b, r1) - ro);
+            if (ub > ua) {
+              h->asm_segs.push_back({sgm[0], sgm[1], sgm[2], ua, ub, 0});
+              entries += (int64_t)(ub - ua) * (sgm[2] - sgm[1]);
+            }
+          }
+          task.seg_end = (int32_t)h->asm_segs.size();
+          if (task.seg_end > task.seg_begin) {
+            if (p1 - p0 <= kAsmWarpPos && entries <= kAsmWarpEntries) warp_tasks.push_back(task);
+            else h->asm_tasks.push_back(task);
+          }
+        }
       }
       q = q1;
     }
     P.asm_n = (int32_t)h->asm_tasks.size() - P.asm_b;
+    P.asmw_n = (int32_t)warp_tasks.size();
+    h->asm_tasks.insert(h->asm_tasks.end(), warp_tasks.begin(), warp_tasks.end());
   }
   h->persist_levels.clear();
   h->small_panel_max = 0;
   for (const LevelPlan& P : h->levels) {
-    h->persist_levels.push_back({P.small_b, P.small_n, P.asm_b, P.asm_n});
+    h->persist_levels.push_back({P.small_b, P.small_n, P.asm_b, P.asm_n, P.asmw_n, 0});
     h->small_panel_max = std::max(h->small_panel_max, P.small_max_panel);
   }
   // one system unless chol_analyze_batch says otherwise

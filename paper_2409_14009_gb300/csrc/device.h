@@ -139,6 +139,8 @@ struct KScope {
       if (a && b) cudaEventRecord(a, st);
     }
   }
+  // the scope holds `n` launches instead of one
+  void launches(int n) { p->st[cls].launches += n - 1; }
   ~KScope() {
     if (a && b) {
       cudaEventRecord(b, st);

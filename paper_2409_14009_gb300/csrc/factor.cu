@@ -27,6 +27,7 @@
 
 #include "device.h"
 #include "mixed.h"
+#include "assemble.cuh"
 
 namespace cg = cooperative_groups;
 
@@ -331,22 +332,25 @@ k_syrk(const SnodeDev* __restrict__ sn, const TileTask* __restrict__ tasks,
                       min(kTile, b - t.r0), min(kTile, b - t.c0), t.r0 - t.c0);
 }
 
-// relind scatter-add of the level's update matrices into their ancestors.
-// Task = (target K, its columns [t0, t1)); segments = contributors in J order.
-// The relative positions of the rows of U_J inside struct(K) (relind(J, K) of
-// Sec. II-A, counted from the top instead of the bottom) are found by binary
-// search in struct(K), staged in shared memory, once per segment and reused by
-// every column of the segment. Within a segment every (column c, row u) of U_J
-// hits a distinct entry of K (relind is injective); a barrier separates
-// segments, so contributions to one entry are applied in a fixed order.
+// Assembly of one task: for every segment (in J order) the rows ua..ub-1 of
+// U_J are located in struct(K) by binary search over the task's position range
+// (staged in shared memory), then a warp per column of the segment subtracts
+// 32 rows at a time, kAsmUnroll (column, row chunk) items in flight per warp
+// with all loads issued before the stores. Every entry of U_J hits a distinct
+// entry of K (relind is injective) and a barrier separates segments, so the
+// contributions to one entry are applied in a fixed order.
+constexpr int kAsmUnroll = 4;
+
 __device__ __forceinline__ void assemble_body(const AsmTask& t, const AsmSeg* __restrict__ segs,
                                               const SnodeDev* __restrict__ sn, const int32_t* __restrict__ rows,
                                               const double* __restrict__ U, double* __restrict__ L, int32_t* ssm) {
+  __shared__ int32_t tcol[kAsmCols];
   const SnodeDev dk = sn[t.K];
-  int32_t* sK = ssm;              // struct(K), dk.len entries
-  int32_t* pos = ssm + dk.len;    // positions of rows ca.. of the current segment
-  const int32_t* rk = rows + dk.roff;
-  for (int i = threadIdx.x; i < dk.len; i += blockDim.x) sK[i] = rk[i];
+  const int np = t.p1 - t.p0;
+  int32_t* sK = ssm;              // struct(K) at positions p0 .. p1-1
+  int32_t* pos = ssm + kAsmPos;   // positions of rows ua .. ub-1 of the current segment
+  const int32_t* rk = rows + dk.roff + t.p0;
+  for (int i = threadIdx.x; i < np; i += blockDim.x) sK[i] = rk[i];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int nwarps = blockDim.x >> 5;
   for (int g = t.seg_begin; g < t.seg_end; ++g) {
@@ -354,22 +358,46 @@ __device__ __forceinline__ void assemble_body(const AsmTask& t, const AsmSeg* __
     const SnodeDev dj = sn[sg.J];
     const int b = dj.len - dj.s;
     const int32_t* rj = rows + dj.roff + dj.s;
-    __syncthreads();   // sK loaded / previous segment finished with pos[]
-    for (int u = sg.ca + threadIdx.x; u < b; u += blockDim.x) {
-      const int32_t key = rj[u];
-      int lo = t.t0, hi = dk.len;   // rows of U_J here are >= column t0 of K
+    const int nu = sg.ub - sg.ua, w = sg.cb - sg.ca;
+    __syncthreads();   // sK loaded / previous segment finished with pos[] and tcol[]
+    for (int i = threadIdx.x; i < nu; i += blockDim.x) {
+      const int32_t key = rj[sg.ua + i];
+      int lo = 0, hi = np;
       while (lo < hi) {
         const int mid = (lo + hi) >> 1;
         if (sK[mid] < key) lo = mid + 1; else hi = mid;
       }
-      pos[u - sg.ca] = lo;
+      pos[i] = t.p0 + lo;
     }
+    for (int c = threadIdx.x; c < w; c += blockDim.x) tcol[c] = rj[sg.ca + c] - dk.f;
     __syncthreads();
     const double* Uj = U + dj.uoff;
-    for (int c = sg.ca + warp; c < sg.cb; c += nwarps) {
-      double* Lc = L + dk.loff + (int64_t)(rj[c] - dk.f) * dk.ld;
-      const double* Uc = Uj + (int64_t)c * b;
-      for (int u = c + lane; u < b; u += 32) Lc[pos[u - sg.ca]] -= Uc[u];
+    double* Lk = L + dk.loff;
+    const int nch = (nu + 31) >> 5;
+    const int items = w * nch;   // (column, 32-row chunk) pairs
+    for (int i0 = warp; i0 < items; i0 += nwarps * kAsmUnroll) {
+      double v[kAsmUnroll], l[kAsmUnroll];
+      int64_t off[kAsmUnroll];
+#pragma unroll
+      for (int q = 0; q < kAsmUnroll; ++q) {
+        const int i = i0 + q * nwarps;
+        off[q] = -1;
+        if (i < items) {
+          const int cc = i / nch;
+          const int c = sg.ca + cc;
+          const int u = sg.ua + (i - cc * nch) * 32 + lane;
+          if (u < sg.ub && u >= c) {
+            off[q] = (int64_t)tcol[cc] * dk.ld + pos[u - sg.ua];
+            v[q] = Uj[(int64_t)c * b + u];
+          }
+        }
+      }
+#pragma unroll
+      for (int q = 0; q < kAsmUnroll; ++q)
+        if (off[q] >= 0) l[q] = Lk[off[q]];
+#pragma unroll
+      for (int q = 0; q < kAsmUnroll; ++q)
+        if (off[q] >= 0) Lk[off[q]] = l[q] - v[q];
     }
   }
 }
@@ -405,6 +433,15 @@ k_persist_factor(const SnodeDev* __restrict__ sn, const int32_t* __restrict__ sm
     for (int i = blockIdx.x; i < p.asm_n; i += gridDim.x) {
       __syncthreads();
       assemble_body(tasks[p.asm_b + i], segs, sn, rows, U, L, reinterpret_cast<int32_t*>(psm));
+    }
+    {
+      // warp-sized tasks: one per warp of the grid, each warp in its own slice
+      __syncthreads();
+      int32_t* wsm = reinterpret_cast<int32_t*>(psm) + (threadIdx.x >> 5) * 2 * kAsmWarpPos;
+      const int nw = NT / 32;
+      for (int i = blockIdx.x * nw + (threadIdx.x >> 5); i < p.asmw_n; i += gridDim.x * nw)
+        assemble_warp_task<double, false>(tasks[p.asm_b + p.asm_n + i], segs, sn, rows, U, L, wsm,
+                                          wsm + kAsmWarpPos);
     }
     grid.sync();
   }
@@ -684,10 +721,15 @@ int enqueue_factor_fp64(chol_handle* h, const double* values, cudaStream_t st) {
       KScope ks(h, CHOL_K_SYRK, st, P.syrk_flops, 8.0 * kTile * kTile * P.syrk_n);
       k_syrk<<<P.syrk_n, kGemmThreads, 0, st>>>(D->sn, D->syrk + P.syrk_b, D->L, D->U);
     }
-    if (P.asm_n > 0) {
+    if (P.asm_n + P.asmw_n > 0) {
       KScope ks(h, CHOL_K_ASSEMBLE, st, P.asm_entries, 24.0 * P.asm_entries);
-      k_assemble<<<P.asm_n, kAsmThreads, sizeof(int32_t) * 2 * h->max_len, st>>>(
-          D->asm_tasks + P.asm_b, D->asm_segs, D->sn, D->rows, D->U, D->L);
+      ks.launches((P.asm_n > 0) + (P.asmw_n > 0));
+      if (P.asm_n > 0)
+        k_assemble<<<P.asm_n, kAsmThreads, sizeof(int32_t) * 2 * kAsmPos, st>>>(
+            D->asm_tasks + P.asm_b, D->asm_segs, D->sn, D->rows, D->U, D->L);
+      if (P.asmw_n > 0)
+        k_assemble_warp<double, false><<<(P.asmw_n + 7) / 8, 256, 0, st>>>(
+            D->asm_tasks + P.asm_b + P.asm_n, P.asmw_n, D->asm_segs, D->sn, D->rows, D->U, D->L);
     }
   }
   CHOL_CUDA_TRY(cudaGetLastError());
@@ -715,7 +757,7 @@ int chol_launch_persistent(chol_handle* h, void* L, void* U, cudaStream_t st) {
   const bool fp64 = h->opt.precision == CHOL_PREC_FP64;
   const size_t esz = fp64 ? sizeof(double) : sizeof(float);
   const size_t smem = std::max(esz * (size_t)std::max(h->small_panel_max, 1),
-                               sizeof(int32_t) * 2 * (size_t)std::max(h->max_len, 1)) + 64;
+                               sizeof(int32_t) * 2 * (size_t)std::max(kAsmPos, 8 * kAsmWarpPos)) + 64;
   const int threads = h->persist_threads == 256 ? 256 : 128;
   const void* fn = chol_persistent_kernel(h->opt.precision, threads);
   if (!fn) return CHOL_ENOTSUP;
@@ -754,7 +796,6 @@ const void* chol_persistent_kernel(int precision, int threads) {
 extern "C" int chol_factor(chol_handle* h, const double* values, void* stream) {
   if (!h) return -1;
   if (!values && h->nnz_a > 0) return -2;
-  if ((int64_t)h->max_len * 2 * (int64_t)sizeof(int32_t) > 200 * 1024) return CHOL_ENOTSUP;
   int rc = chol_device_ensure(h);
   if (rc) return rc;
   DeviceState* D = h->dev;

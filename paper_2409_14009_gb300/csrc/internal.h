@@ -23,19 +23,27 @@ struct TileTask {
   int32_t J, k0, r0, c0;
 };
 
-// Pull-ordered assembly: one task owns columns [t0, t1) of target supernode K and
-// applies its segments in order; a segment is the part of U_J (columns [ca, cb),
-// rows c.. b-1 of each column c) that lands there.
+// Pull-ordered assembly: one task owns columns [t0, t1) and row positions
+// [p0, p1) of target supernode K (disjoint entries of K across tasks) and
+// applies its segments in order; a segment is the part of U_J that lands
+// there: columns [ca, cb), rows [ua, ub) (entries with row >= column only).
+// The positions of a (K, column tile) pair are split into chunks of at most
+// kAsmPos; the first chunk starts at t0 and holds every segment's columns.
 struct AsmTask {
-  int32_t K, t0, t1, seg_begin, seg_end, pad0, pad1, pad2;
+  int32_t K, t0, t1, seg_begin, seg_end, p0, p1, pad;
 };
 struct AsmSeg {
-  int32_t J, ca, cb, pad;
+  int32_t J, ca, cb, ua, ub, pad;
 };
 
+// One column step of the blocked large-supernode path. In the tensor-core
+// modes the trailing update is blocked twice: the step's own update (gemm_*)
+// stays inside its kTcOuter-wide column block, and after the last step of a
+// block the columns right of it are updated once with K = the block's width
+// (ogemm_*, K range starting at ok0).
 struct StepRange {
-  int32_t potrf_b, potrf_n, trsm_b, trsm_n, gemm_b, gemm_n;
-  double potrf_flops, trsm_flops, gemm_flops;
+  int32_t potrf_b, potrf_n, trsm_b, trsm_n, gemm_b, gemm_n, ogemm_b, ogemm_n, ok0, okb;
+  double potrf_flops, trsm_flops, gemm_flops, ogemm_flops;
 };
 
 // Blocked triangular-solve step k0 of one level: diagonal blocks of every
@@ -51,7 +59,8 @@ struct LevelPlan {
   int32_t small_max_panel;    // largest len*s among them (shared memory sizing)
   std::vector<StepRange> steps;
   int32_t syrk_b, syrk_n;     // U tiles (in syrk_tasks)
-  int32_t asm_b, asm_n;       // assembly tasks
+  int32_t asm_b, asm_n;       // assembly tasks, one CTA each
+  int32_t asmw_n;             // then (from asm_b + asm_n) small tasks, one warp each
   std::vector<SolveStep> ssteps;
   int32_t ssmall_b, ssmall_n; // supernodes solved by one warp each (in ssmall_list)
   int32_t gemv_b, gemv_n;     // forward-solve panel products (TileTask: J, r0)
@@ -66,7 +75,7 @@ struct LevelPlan {
 
 // One level of the persistent (cooperative) factorization.
 struct PersistLevel {
-  int32_t small_b, small_n, asm_b, asm_n;
+  int32_t small_b, small_n, asm_b, asm_n, asmw_n, pad;
 };
 
 struct DeviceState;  // defined in the CUDA driver
@@ -136,7 +145,11 @@ struct chol_handle {
 // Tile sizes shared by the schedule builder and the kernels.
 constexpr int kTile = 64;        // SIMT GEMM/SYRK tile edge
 constexpr int kTileTC = 128;     // tensor-core (tcgen05) GEMM/SYRK tile edge
+constexpr int kTcOuter = 256;    // outer column block of the tensor-core trailing update
 constexpr int kAsmCols = 64;     // assembly task width (target columns)
+constexpr int kAsmPos = 1024;    // assembly task height (row positions of the target)
+constexpr int kAsmWarpPos = 256;       // warp-sized assembly tasks: at most this many positions
+constexpr int kAsmWarpEntries = 4096;  // ... and this many entries over all segments
 constexpr int kTrsmRowsHost = 32; // TRSM task height (rows)
 constexpr int kSolveSB = 256;    // largest solve super-step (columns solved inside one CTA)
 constexpr int kSolveSmallCols = 32;   // supernodes solved by one warp: s <= 32 and

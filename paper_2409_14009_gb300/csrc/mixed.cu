@@ -22,6 +22,7 @@
 
 #include "device.h"
 #include "mixed.h"
+#include "assemble.cuh"
 
 namespace cg = cooperative_groups;
 
@@ -357,19 +358,23 @@ k_mx_syrk_simt(const SnodeDev* __restrict__ sn, const TileTask* __restrict__ tas
                           min(kTile, b - t.c0), t.r0 - t.c0);
 }
 
-// Pull-ordered relind scatter-add into row-major binary32 panels. Task = target
-// K and its columns [t0, t1); per segment the positions of J's rows in struct(K)
-// are found by binary search in shared memory, then warps walk the rows u of
-// U_J (row-major lower) and lanes the columns c <= u of the segment.
+// Binary32 assembly of one task (row-major U_J and panels). Row positions as in
+// the binary64 kernel; the segment's columns are spread over groups of 4, 8, 16
+// or 32 lanes (the smallest that covers them, twice for 33..64 columns), so a
+// warp covers 32 / group rows per pass and issues kMxAsmUnroll passes' loads
+// before their stores.
+constexpr int kMxAsmUnroll = 4;
+
 __device__ __forceinline__ void mx_assemble_body(const AsmTask& t, const AsmSeg* __restrict__ segs,
                                                  const SnodeDev* __restrict__ sn, const int32_t* __restrict__ rows,
                                                  const float* __restrict__ U, float* __restrict__ L, int32_t* ssm) {
   __shared__ int32_t tcol[kAsmCols];
   const SnodeDev dk = sn[t.K];
+  const int np = t.p1 - t.p0;
   int32_t* sK = ssm;
-  int32_t* pos = ssm + dk.len;
-  const int32_t* rk = rows + dk.roff;
-  for (int i = threadIdx.x; i < dk.len; i += blockDim.x) sK[i] = rk[i];
+  int32_t* pos = ssm + kAsmPos;
+  const int32_t* rk = rows + dk.roff + t.p0;
+  for (int i = threadIdx.x; i < np; i += blockDim.x) sK[i] = rk[i];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int nwarps = blockDim.x >> 5;
   for (int g = t.seg_begin; g < t.seg_end; ++g) {
@@ -378,24 +383,50 @@ __device__ __forceinline__ void mx_assemble_body(const AsmTask& t, const AsmSeg*
     const int b = dj.len - dj.s;
     const int ldu = (b + 7) & ~7;
     const int32_t* rj = rows + dj.roff + dj.s;
+    const int nu = sg.ub - sg.ua, w = sg.cb - sg.ca;
     __syncthreads();
-    for (int u = sg.ca + threadIdx.x; u < b; u += blockDim.x) {
-      const int32_t key = rj[u];
-      int lo = t.t0, hi = dk.len;
+    for (int i = threadIdx.x; i < nu; i += blockDim.x) {
+      const int32_t key = rj[sg.ua + i];
+      int lo = 0, hi = np;
       while (lo < hi) {
         const int mid = (lo + hi) >> 1;
         if (sK[mid] < key) lo = mid + 1; else hi = mid;
       }
-      pos[u - sg.ca] = lo;
+      pos[i] = t.p0 + lo;
     }
-    for (int c = sg.ca + threadIdx.x; c < sg.cb; c += blockDim.x) tcol[c - sg.ca] = rj[c] - dk.f;
+    for (int c = threadIdx.x; c < w; c += blockDim.x) tcol[c] = rj[sg.ca + c] - dk.f;
     __syncthreads();
     const float* Uj = U + dj.uoff;
-    for (int u = sg.ca + warp; u < b; u += nwarps) {
-      float* Lr = L + dk.loff + (int64_t)pos[u - sg.ca] * dk.ld;
-      const float* Ur = Uj + (int64_t)u * ldu;
-      const int cend = min(sg.cb, u + 1);
-      for (int c = sg.ca + lane; c < cend; c += 32) Lr[tcol[c - sg.ca]] -= Ur[c];
+    float* Lk = L + dk.loff;
+    const int gs = w <= 4 ? 4 : w <= 8 ? 8 : w <= 16 ? 16 : 32;   // lanes per row
+    const int gsh = gs == 4 ? 2 : gs == 8 ? 3 : gs == 16 ? 4 : 5;
+    const int rpw = 32 >> gsh;                                   // rows per warp pass
+    const int nc = w > 32 ? 2 : 1;                               // column chunks per row
+    const int sub = lane >> gsh, cl = lane & (gs - 1);
+    const int items = nu * nc;                                   // (row, column chunk) pairs
+    for (int i0 = warp * rpw; i0 < items; i0 += nwarps * rpw * kMxAsmUnroll) {
+      float v[kMxAsmUnroll], l[kMxAsmUnroll];
+      int64_t off[kMxAsmUnroll];
+#pragma unroll
+      for (int q = 0; q < kMxAsmUnroll; ++q) {
+        const int i = i0 + q * nwarps * rpw + sub;
+        off[q] = -1;
+        if (i < items) {
+          const int ui = nc == 2 ? (i >> 1) : i;
+          const int cc = (nc == 2 ? (i & 1) * 32 : 0) + cl;
+          const int u = sg.ua + ui, c = sg.ca + cc;
+          if (cc < w && c <= u) {
+            off[q] = (int64_t)pos[ui] * dk.ld + tcol[cc];
+            v[q] = Uj[(int64_t)u * ldu + c];
+          }
+        }
+      }
+#pragma unroll
+      for (int q = 0; q < kMxAsmUnroll; ++q)
+        if (off[q] >= 0) l[q] = Lk[off[q]];
+#pragma unroll
+      for (int q = 0; q < kMxAsmUnroll; ++q)
+        if (off[q] >= 0) Lk[off[q]] = l[q] - v[q];
     }
   }
 }
@@ -428,6 +459,14 @@ k_persist_factor_mx(const SnodeDev* __restrict__ sn, const int32_t* __restrict__
     for (int i = blockIdx.x; i < p.asm_n; i += gridDim.x) {
       __syncthreads();
       mx_assemble_body(tasks[p.asm_b + i], segs, sn, rows, U, L, reinterpret_cast<int32_t*>(psmf));
+    }
+    {
+      __syncthreads();
+      int32_t* wsm = reinterpret_cast<int32_t*>(psmf) + (threadIdx.x >> 5) * 2 * kAsmWarpPos;
+      const int nw = NT / 32;
+      for (int i = blockIdx.x * nw + (threadIdx.x >> 5); i < p.asmw_n; i += gridDim.x * nw)
+        assemble_warp_task<float, true>(tasks[p.asm_b + p.asm_n + i], segs, sn, rows, U, L, wsm,
+                                        wsm + kAsmWarpPos);
     }
     grid.sync();
   }
@@ -566,10 +605,14 @@ int chol_enqueue_factor_mixed(chol_handle* h, const double* values, cudaStream_t
       if (s.gemm_n > 0) {
         KScope ks(h, CHOL_K_GEMM, st, s.gemm_flops, 0.0);
         if (tc) {
-          if ((rc = chol_tc_gemm(h, D->gemm + s.gemm_b, s.gemm_n, k0, nb, st))) return rc;
+          if ((rc = chol_tc_gemm(h, D->gemm + s.gemm_b, s.gemm_n, nb, 1, st))) return rc;
         } else {
           k_mx_gemm_simt<<<s.gemm_n, 256, 0, st>>>(D->sn, D->gemm + s.gemm_b, nb, L);
         }
+      }
+      if (s.ogemm_n > 0) {
+        KScope ks(h, CHOL_K_GEMM, st, s.ogemm_flops, 0.0);
+        if ((rc = chol_tc_gemm(h, D->gemm + s.ogemm_b, s.ogemm_n, s.okb, 0, st))) return rc;
       }
     }
     if (P.syrk_n > 0) {
@@ -580,10 +623,15 @@ int chol_enqueue_factor_mixed(chol_handle* h, const double* values, cudaStream_t
         k_mx_syrk_simt<<<P.syrk_n, 256, 0, st>>>(D->sn, D->syrk + P.syrk_b, L, U);
       }
     }
-    if (P.asm_n > 0) {
+    if (P.asm_n + P.asmw_n > 0) {
       KScope ks(h, CHOL_K_ASSEMBLE, st, P.asm_entries, 12.0 * P.asm_entries);
-      k_mx_assemble<<<P.asm_n, kMxThreads, sizeof(int32_t) * 2 * h->max_len, st>>>(
-          D->asm_tasks + P.asm_b, D->asm_segs, D->sn, D->rows, U, L);
+      ks.launches((P.asm_n > 0) + (P.asmw_n > 0));
+      if (P.asm_n > 0)
+        k_mx_assemble<<<P.asm_n, kMxThreads, sizeof(int32_t) * 2 * kAsmPos, st>>>(
+            D->asm_tasks + P.asm_b, D->asm_segs, D->sn, D->rows, U, L);
+      if (P.asmw_n > 0)
+        k_assemble_warp<float, true><<<(P.asmw_n + 7) / 8, 256, 0, st>>>(
+            D->asm_tasks + P.asm_b + P.asm_n, P.asmw_n, D->asm_segs, D->sn, D->rows, U, L);
     }
   }
   CHOL_CUDA_TRY(cudaGetLastError());

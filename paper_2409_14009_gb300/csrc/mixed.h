@@ -18,7 +18,7 @@ int chol_solve_mixed(chol_handle* h, double* b, int32_t nrhs, cudaStream_t st);
 void chol_status_init(int* status, cudaStream_t st);
 
 int chol_tc_prepare(chol_handle* h);
-int chol_tc_gemm(chol_handle* h, const TileTask* tasks, int n, int k0, int nb, cudaStream_t st);
+int chol_tc_gemm(chol_handle* h, const TileTask* tasks, int n, int nb, int inner, cudaStream_t st);
 int chol_tc_syrk(chol_handle* h, const TileTask* tasks, int n, cudaStream_t st);
 int chol_tc_status(chol_handle* h);
 void chol_adjoint_free(chol_handle* h);

@@ -328,6 +328,7 @@ __global__ void __launch_bounds__(kT)
 k_sv_fasm(const AsmTask* __restrict__ tasks, const AsmSeg* __restrict__ segs, const SnodeDev* __restrict__ sn,
           const int32_t* __restrict__ rows, const T* __restrict__ W, T* __restrict__ Y, int n, int nrhs) {
   const AsmTask t = tasks[blockIdx.x];
+  if (t.p0 != t.t0) return;   // only the first position chunk of a column tile holds the columns
   for (int g = t.seg_begin; g < t.seg_end; ++g) {
     const AsmSeg sg = segs[g];
     const SnodeDev dj = sn[sg.J];
@@ -608,9 +609,11 @@ void solve_levels(chol_handle* h, const T* L, T* Y, T* W, T* part, int nr, cudaS
       k_sv_gemv<T, RM><<<P.gemv_n, kT, 0, st>>>(D->sn, D->gemv + P.gemv_b, L, Y, n, W, nr);
       delete ks;
     }
-    if (P.asm_n > 0) {
+    if (P.asm_n + P.asmw_n > 0) {
+      // the CTA-sized and the warp-sized assembly tasks of the level, contiguous
       KScope* ks = scope(CHOL_K_SOLVE_FASM);
-      k_sv_fasm<T><<<P.asm_n, kT, 0, st>>>(D->asm_tasks + P.asm_b, D->asm_segs, D->sn, D->rows, W, Y, n, nr);
+      k_sv_fasm<T><<<P.asm_n + P.asmw_n, kT, 0, st>>>(D->asm_tasks + P.asm_b, D->asm_segs, D->sn, D->rows, W, Y,
+                                                      n, nr);
       delete ks;
     }
   }

@@ -18,15 +18,19 @@ typedef CUresult (*EncodeTiledFn)(CUtensorMap*, CUtensorMapDataType, cuuint32_t,
                                   const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
                                   CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
 
-// Trailing update of a panel at column step k0 (C -= A B^T on the lower part).
+// Trailing update of a panel (C -= A B^T on the lower part) with K range
+// [k0, k0 + nb). inner = 1: a column step's own update, whose columns stop at
+// the end of the kTcOuter-wide block holding k0; inner = 0: the update of the
+// columns right of a finished outer block (K = the block).
 template <int KIND>
 __global__ void __launch_bounds__(tc::kThreads, 1)
 k_tc_trailing(const CUtensorMap* __restrict__ maps, const TileTask* __restrict__ tasks,
-              const SnodeDev* __restrict__ sn, int nb, float* __restrict__ L, int stages, int* err) {
+              const SnodeDev* __restrict__ sn, int nb, int inner, float* __restrict__ L, int stages, int* err) {
   extern __shared__ uint8_t smem[];
   const TileTask t = tasks[blockIdx.x];
   const SnodeDev d = sn[t.J];
   const int kb = min(nb, d.s - t.k0);
+  const int cend = inner ? min(d.s, (t.k0 / kTcOuter + 1) * kTcOuter) : d.s;
   tc::TileJob job;
   job.map = maps + t.J;
   job.a_row = t.r0;
@@ -36,7 +40,7 @@ k_tc_trailing(const CUtensorMap* __restrict__ maps, const TileTask* __restrict__
   job.C = L + d.loff + (int64_t)t.r0 * d.ld + t.c0;
   job.ldc = d.ld;
   job.m = min(tc::kTileM, d.len - t.r0);
-  job.n = min(tc::kTileN, d.s - t.c0);
+  job.n = min(tc::kTileN, cend - t.c0);
   job.rdiag = t.r0 - t.c0;
   job.sub = true;
   tc::tile_body<KIND>(job, smem, stages, err);
@@ -117,15 +121,14 @@ int chol_tc_prepare(chol_handle* h) {
   return CHOL_OK;
 }
 
-int chol_tc_gemm(chol_handle* h, const TileTask* tasks, int n, int k0, int nb, cudaStream_t st) {
-  (void)k0;
+int chol_tc_gemm(chol_handle* h, const TileTask* tasks, int n, int nb, int inner, cudaStream_t st) {
   DeviceState* D = h->dev;
   const int ns = tc::stages_for(n, D->sms);
   const int sm = tc::smem_bytes(ns);
   if (h->opt.precision == CHOL_PREC_TF32)
-    k_tc_trailing<0><<<n, tc::kThreads, sm, st>>>(D->tmaps, tasks, D->sn, nb, (float*)D->L, ns, D->tc_err);
+    k_tc_trailing<0><<<n, tc::kThreads, sm, st>>>(D->tmaps, tasks, D->sn, nb, inner, (float*)D->L, ns, D->tc_err);
   else
-    k_tc_trailing<1><<<n, tc::kThreads, sm, st>>>(D->tmaps, tasks, D->sn, nb, (float*)D->L, ns, D->tc_err);
+    k_tc_trailing<1><<<n, tc::kThreads, sm, st>>>(D->tmaps, tasks, D->sn, nb, inner, (float*)D->L, ns, D->tc_err);
   return CHOL_OK;
 }
 
