@@ -141,10 +141,14 @@ int chol_factor(chol_handle* h, const double* values, void* stream);
 /*
  * Solve A X = B with the computed factor: X = P^T L^{-T} L^{-1} P B
  * (forward substitution over the levels leaves->root, backward substitution
- * root->leaves).
+ * root->leaves; the diagonal triangles of a level in one cooperative launch).
  *   b      device, n x nrhs column-major (leading dimension n); overwritten by X
  *   nrhs   >= 0
- * Returns CHOL_ESTATE without a successful chol_factor. Asynchronous.
+ * Returns CHOL_ESTATE without a successful chol_factor. Asynchronous. The
+ * blocks of a triangle wait (bounded) for the blocks they depend on; a wait
+ * that runs out leaves X invalid and is reported as CHOL_ETIMEOUT by the next
+ * chol_factor or chol_solve_refine on the handle. Calls on one handle must not
+ * overlap on the GPU (they share workspaces).
  */
 int chol_solve(chol_handle* h, double* b, int32_t nrhs, void* stream);
 

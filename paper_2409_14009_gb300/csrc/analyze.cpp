@@ -414,7 +414,6 @@ void build(chol_handle* h, const int64_t* colptr, const int32_t* rowind) {
   // solve super-step: one CTA solves this many diagonal columns. Binary64 keeps
   // it at one 64-column block (a single SM's FP64 rate is the limit); binary32
   // takes 256 to cut the number of dependent launches.
-  h->solve_sb = h->opt.precision == CHOL_PREC_FP64 ? 64 : kSolveSB;
   const bool tc_modes = h->opt.precision == CHOL_PREC_TF32 || h->opt.precision == CHOL_PREC_BF16;
   const int tg = tc_modes ? kTileTC : kTile;
   std::vector<std::vector<int32_t>> by_level(h->nlevels);
@@ -425,7 +424,7 @@ void build(chol_handle* h, const int64_t* colptr, const int32_t* rowind) {
   h->levels.assign(h->nlevels, LevelPlan{});
   h->level_snodes.clear(); h->small_list.clear(); h->potrf_list.clear();
   h->trsm_tasks.clear(); h->gemm_tasks.clear(); h->syrk_tasks.clear();
-  h->bpanel_tasks.clear(); h->sdiag_list.clear(); h->fupd_tasks.clear(); h->bupd_tasks.clear();
+  h->bpanel_tasks.clear(); h->tri_items.clear(); h->tri_nflags = 0;
   h->ssmall_list.clear();
   h->gemv_tasks.clear(); h->bpart_tasks.clear(); h->bred_tasks.clear();
   h->p_max = 0;
@@ -529,10 +528,10 @@ void build(chol_handle* h, const int64_t* colptr, const int32_t* rowind) {
         for (int32_t r0 = c0; r0 < b; r0 += tg) h->syrk_tasks.push_back({J, 0, r0, c0});
     }
     P.syrk_n = (int32_t)h->syrk_tasks.size() - P.syrk_b;
-    // blocked triangular solves over every supernode of the level: super-steps of
-    // kSolveSB columns (diagonal triangle in one CTA + updates of the rows of the
-    // diagonal block below it / of the column blocks left of it), then one panel
-    // product per level for the off-diagonal rows
+    // triangular solves over every supernode of the level: the diagonal
+    // triangles as 64-row blocks in dependency order (one cooperative launch per
+    // level and direction), then one panel product per level for the
+    // off-diagonal rows; small supernodes take one warp each
     auto warp_solved = [&](int32_t J) {
       return h->snodes[J].s <= kSolveSmallCols && h->snodes[J].len <= kSolveSmallRows;
     };
@@ -540,28 +539,14 @@ void build(chol_handle* h, const int64_t* colptr, const int32_t* rowind) {
     for (int32_t J : Js)
       if (warp_solved(J)) h->ssmall_list.push_back(J);
     P.ssmall_n = (int32_t)h->ssmall_list.size() - P.ssmall_b;
-    int32_t maxs_all = 0;
-    for (int32_t J : Js)
-      if (!warp_solved(J)) maxs_all = std::max(maxs_all, h->snodes[J].s);
-    const int32_t sb = h->solve_sb;
-    for (int32_t k0 = 0; k0 < maxs_all; k0 += sb) {
-      SolveStep st{};
-      st.diag_b = (int32_t)h->sdiag_list.size();
-      st.fupd_b = (int32_t)h->fupd_tasks.size();
-      st.bupd_b = (int32_t)h->bupd_tasks.size();
-      for (int32_t J : Js) {
-        const SnodeDev& d = h->snodes[J];
-        if (d.s <= k0 || warp_solved(J)) continue;
-        const int32_t sbk = std::min(sb, d.s - k0);
-        h->sdiag_list.push_back(J);
-        for (int32_t r0 = k0 + sbk; r0 < d.s; r0 += kSolveTileRows) h->fupd_tasks.push_back({J, k0, r0, 0});
-        for (int32_t c0 = 0; c0 < k0; c0 += kSolveTileRows) h->bupd_tasks.push_back({J, k0, 0, c0});
-      }
-      st.diag_n = (int32_t)h->sdiag_list.size() - st.diag_b;
-      st.fupd_n = (int32_t)h->fupd_tasks.size() - st.fupd_b;
-      st.bupd_n = (int32_t)h->bupd_tasks.size() - st.bupd_b;
-      P.ssteps.push_back(st);
+    P.tri_b = (int32_t)h->tri_items.size();
+    for (int32_t J : Js) {
+      if (warp_solved(J)) continue;
+      const int32_t nb = (h->snodes[J].s + 63) / 64;
+      for (int32_t i = 0; i < nb; ++i) h->tri_items.push_back({J, i, nb, h->tri_nflags});
+      h->tri_nflags += nb;
     }
+    P.tri_n = (int32_t)h->tri_items.size() - P.tri_b;
     const int32_t gemv_rows = h->opt.precision == CHOL_PREC_FP64 ? 64 : 32;
     const int32_t bpanel_cols = h->opt.precision == CHOL_PREC_FP64 ? 8 : 64;
     P.gemv_b = (int32_t)h->gemv_tasks.size();

@@ -25,10 +25,11 @@ struct DeviceState {
   TileTask* syrk = nullptr;
   AsmTask* asm_tasks = nullptr;
   AsmSeg* asm_segs = nullptr;
-  int32_t* sdiag = nullptr;
+  TriItemHost* tri = nullptr;   // solve: diagonal-triangle items
+  int32_t* tri_flags = nullptr; // solve: one flag per diagonal block (zeroed once)
+  int32_t* tri_sync = nullptr;  // solve: {epoch, CTAs done} of the triangle launches
+  int32_t* sv_err = nullptr;    // solve: set when a bounded wait gave up
   int32_t* ssmall = nullptr;
-  TileTask* fupd = nullptr;
-  TileTask* bupd = nullptr;
   TileTask* bpanel = nullptr;
   TileTask* gemv = nullptr;
   TileTask* bpart = nullptr;

@@ -586,8 +586,8 @@ void chol_device_free(chol_handle* h) {
   if (D->device >= 0) cudaSetDevice(D->device);
   chol_adjoint_free(h);
   void* ptrs[] = {D->L, D->U, D->sn, D->rows, D->amap, D->small_list, D->potrf_list,
-                  D->level_snodes, D->trsm, D->gemm, D->syrk, D->asm_tasks, D->asm_segs, D->sdiag,
-                  D->fupd, D->bupd, D->bpanel, D->gemv, D->bpart, D->bred, D->P32, D->plevels, D->vals, D->sys_snode, D->sys_out,
+                  D->level_snodes, D->trsm, D->gemm, D->syrk, D->asm_tasks, D->asm_segs, D->tri,
+                  D->tri_flags, D->tri_sync, D->sv_err, D->bpanel, D->gemv, D->bpart, D->bred, D->P32, D->plevels, D->vals, D->sys_snode, D->sys_out,
                   D->ssmall, D->Zp, D->Tw, D->Ww, D->Uh, D->a_col, D->a_row, D->adj_xb, D->perm, D->status, D->part, D->scalar_dev, D->Y, D->W,
                   D->mx_diagpos, D->mx_aij, D->mx_d, D->mx_fallbacks, D->csr_ptr, D->csr_col, D->csr_src,
                   D->csr_val, D->Lbf, D->tmaps, D->tc_err, D->R, D->Z, D->Pv, D->Q, D->red, D->Y32, D->W32,
@@ -646,10 +646,15 @@ int chol_device_ensure(chol_handle* h) {
   if ((rc = upload(h, &D->syrk, h->syrk_tasks))) return fail(rc);
   if ((rc = upload(h, &D->asm_tasks, h->asm_tasks))) return fail(rc);
   if ((rc = upload(h, &D->asm_segs, h->asm_segs))) return fail(rc);
-  if ((rc = upload(h, &D->sdiag, h->sdiag_list))) return fail(rc);
+  if ((rc = upload(h, &D->tri, h->tri_items))) return fail(rc);
+  if ((rc = chol_dalloc(h, (void**)&D->tri_flags, sizeof(int32_t) * (size_t)std::max(h->tri_nflags, 1)))) return fail(rc);
+  if ((rc = chol_dalloc(h, (void**)&D->tri_sync, sizeof(int32_t) * 2))) return fail(rc);
+  if ((rc = chol_dalloc(h, (void**)&D->sv_err, sizeof(int32_t)))) return fail(rc);
+  if (cudaMemset(D->tri_flags, 0, sizeof(int32_t) * (size_t)std::max(h->tri_nflags, 1)) != cudaSuccess ||
+      cudaMemset(D->tri_sync, 0, sizeof(int32_t) * 2) != cudaSuccess ||
+      cudaMemset(D->sv_err, 0, sizeof(int32_t)) != cudaSuccess)
+    return fail(CHOL_ECUDA);
   if ((rc = upload(h, &D->ssmall, h->ssmall_list))) return fail(rc);
-  if ((rc = upload(h, &D->fupd, h->fupd_tasks))) return fail(rc);
-  if ((rc = upload(h, &D->bupd, h->bupd_tasks))) return fail(rc);
   if ((rc = upload(h, &D->bpanel, h->bpanel_tasks))) return fail(rc);
   if ((rc = upload(h, &D->gemv, h->gemv_tasks))) return fail(rc);
   if ((rc = upload(h, &D->bpart, h->bpart_tasks))) return fail(rc);
@@ -878,6 +883,10 @@ int chol_finish_factor(chol_handle* h, cudaStream_t st) {
   if (s != INT_MAX) return s;
   if (h->opt.precision != CHOL_PREC_FP64) {
     const int rc = chol_tc_status(h);
+    if (rc) return rc;
+  }
+  {
+    const int rc = chol_solve_status(h);
     if (rc) return rc;
   }
   h->factored = true;

@@ -49,8 +49,10 @@ struct StepRange {
 // Blocked triangular-solve step k0 of one level: diagonal blocks of every
 // supernode with s > k0, the row tiles below them (forward) and the column
 // tiles left of them (backward).
-struct SolveStep {
-  int32_t diag_b, diag_n, fupd_b, fupd_n, bupd_b, bupd_n;
+// Triangular solve of one 64-row block of a supernode's diagonal triangle:
+// supernode J, processing index i of nb blocks, flag index of block 0.
+struct TriItemHost {
+  int32_t J, i, nb, fbase;
 };
 
 struct LevelPlan {
@@ -61,7 +63,7 @@ struct LevelPlan {
   int32_t syrk_b, syrk_n;     // U tiles (in syrk_tasks)
   int32_t asm_b, asm_n;       // assembly tasks, one CTA each
   int32_t asmw_n;             // then (from asm_b + asm_n) small tasks, one warp each
-  std::vector<SolveStep> ssteps;
+  int32_t tri_b, tri_n;       // diagonal-triangle solve items (in tri_items), dependency order
   int32_t ssmall_b, ssmall_n; // supernodes solved by one warp each (in ssmall_list)
   int32_t gemv_b, gemv_n;     // forward-solve panel products (TileTask: J, r0)
   int32_t bpart_b, bpart_n;   // row-major backward panel, stage 1 (J, chunk, u0, c0)
@@ -119,16 +121,15 @@ struct chol_handle {
   std::vector<LevelPlan> levels;
   std::vector<int32_t> level_snodes, small_list, potrf_list;
   std::vector<TileTask> trsm_tasks, gemm_tasks, syrk_tasks, bpanel_tasks;
-  std::vector<int32_t> sdiag_list;             // solve: supernode per (level, step)
+  std::vector<TriItemHost> tri_items;          // solve: diagonal-triangle blocks per level
+  int32_t tri_nflags = 0;                      // solve: one flag per 64-row diagonal block
   std::vector<int32_t> ssmall_list;            // solve: one-warp supernodes per level
-  std::vector<TileTask> fupd_tasks, bupd_tasks; // solve: (J, k0, r0) / (J, k0, c0)
   std::vector<TileTask> gemv_tasks;             // solve: (J, r0) off-diagonal row tiles
   std::vector<TileTask> bpart_tasks, bred_tasks; // solve: row-major backward panel stages
   int64_t p_max = 0;                            // largest per-level partial-sum rows
   std::vector<AsmTask> asm_tasks;
   std::vector<AsmSeg> asm_segs;
   int32_t n_small = 0, n_large = 0;
-  int32_t solve_sb = 256;       // solve super-step (set by the analysis)
   // batches and launch configuration
   std::vector<int32_t> sys_ptr;       // count+1 column offsets of the systems
   std::vector<int32_t> sys_snode_ptr; // count+1 storage-supernode offsets of the systems
@@ -151,9 +152,7 @@ constexpr int kAsmPos = 1024;    // assembly task height (row positions of the t
 constexpr int kAsmWarpPos = 256;       // warp-sized assembly tasks: at most this many positions
 constexpr int kAsmWarpEntries = 4096;  // ... and this many entries over all segments
 constexpr int kTrsmRowsHost = 32; // TRSM task height (rows)
-constexpr int kSolveSB = 256;    // largest solve super-step (columns solved inside one CTA)
 constexpr int kSolveSmallCols = 32;   // supernodes solved by one warp: s <= 32 and
 constexpr int kSolveSmallRows = 256;  // len <= 256
-constexpr int kSolveTileRows = 64;  // solve update tiles (rows / columns)
 
 void chol_device_free(chol_handle* h);  // CUDA side

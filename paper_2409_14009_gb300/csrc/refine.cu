@@ -290,5 +290,9 @@ extern "C" int chol_solve_refine(chol_handle* h, const double* b, double* x, int
   CHOL_CUDA_TRY(cudaGetLastError());
   if (iters) *iters = it;
   if (berr) std::memcpy(berr, eta.data(), sizeof(double) * nrhs);
+  {
+    const int rc = chol_solve_status(h);
+    if (rc) return rc;
+  }
   return done() ? CHOL_OK : CHOL_ENOCONV;
 }

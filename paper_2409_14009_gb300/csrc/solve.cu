@@ -8,16 +8,16 @@
 //   scaled back on the way out.
 //
 // Forward, levels leaves -> root, for every supernode J of the level:
-//   - the diagonal block, in super-steps of 256 columns. One CTA solves a
-//     256 x 256 triangle in 64-column sub-blocks (k_sv_diag); many CTAs then
-//     update the rows of the diagonal block below it (k_sv_fupd).
+//   - the diagonal triangle, as 64-row blocks in one cooperative launch per
+//     level (k_sv_tri): a block accumulates the products with the blocks
+//     already solved as their flags are published, then substitutes.
 //   - one panel product w_J = L_RJ y_J for the off-diagonal rows (k_sv_gemv).
 //   - w_J is scatter-subtracted into the ancestors' rows of y through the
 //     factor's pull-ordered relind task lists (k_sv_fasm).
+//   Supernodes with s <= 32 and len <= 256 take one warp each instead.
 // Backward, levels root -> leaves:
 //   - y_J -= L_RJ^T x_R, a gather of the already final ancestor rows (k_sv_bpanel).
-//   - the transposed diagonal block, super-steps last to first: one CTA
-//     solves, then many CTAs update the column blocks to the left (k_sv_bupd).
+//   - the transposed diagonal triangle, blocks last to first (k_sv_tri).
 // Every output entry is written by exactly one thread per launch and every
 // reduction runs in a fixed order, so the solve is deterministic.
 #include <mutex>
@@ -86,152 +86,200 @@ __global__ void k_sv_maxabs(const double* __restrict__ b, int n, int nr, unsigne
   }
 }
 
-// One CTA solves the diagonal triangle of columns [k0, k0 + sbk) (sbk <= 256)
-// of every listed supernode, in place in Y. Inside: 64-column sub-blocks; each
-// is solved with 16 lanes per right-hand side (lane q holds rows q + 16a, the
-// solved entry broadcast by shuffle), then the rows of the later (forward) or
-// earlier (transposed) sub-blocks are updated by all threads.
+// Diagonal triangles of every (non-warp) supernode of a level in one
+// cooperative launch. Item (J, i) owns the 64-row block blk of L_JJ (blk = i
+// forward, nb-1-i transposed); the items of J are listed in dependency order.
+// A CTA takes items blockIdx.x, blockIdx.x + gridDim.x, ...; for each it
+// accumulates the products with the blocks already solved (forward: blocks
+// j < blk, L(blk, j) y_j; transposed: blocks j > blk, L(j, blk)^T x_j) as
+// their flags are published, then solves its own 64 x 64 triangle by
+// substitution (16 lanes per right-hand side, the solved entry broadcast by
+// shuffle), writes its rows of Y and publishes its flag. Waits point only to
+// items with smaller indices and every CTA is resident (cooperative launch),
+// so the smallest unfinished item can always proceed. Each wait is bounded;
+// one that gives up sets *err and carries on (the result is then invalid).
+// Flags hold the value epoch + 1 of the launch that published them; the last
+// CTA to finish advances the device-side epoch, so no reset is needed between
+// launches (also when they are replayed from a CUDA graph). Every entry of Y is
+// computed by one thread in a fixed order: the solve is deterministic.
+struct TriItem {
+  int32_t J, i, nb, fbase;
+};
+
+__device__ __forceinline__ int ld_acquire(const int* p) {
+  int v;
+  asm volatile("ld.acquire.gpu.global.b32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+  return v;
+}
+
+__device__ __forceinline__ void st_release(int* p, int v) {
+  asm volatile("st.release.gpu.global.b32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+
+constexpr long long kTriMaxPolls = 1ll << 24;   // about two seconds with the back-off below
+
+template <class T>
+size_t tri_smem(int nr) {
+  // ys (64 x nr), yi (64 x nr), Ls (64 x 65), Lt (64 x 65; later the k-group
+  // partial sums, 4 x 64 x nr), inv (64)
+  return sizeof(T) * ((size_t)2 * kSub * nr + 2 * kSub * 65 + kSub);
+}
+
 template <class T, bool RM, bool TRANS>
 __global__ void __launch_bounds__(kT)
-k_sv_diag(const SnodeDev* __restrict__ sn, const int32_t* __restrict__ list, int k0, int sb,
-          const T* __restrict__ L, T* __restrict__ Y, int n, int nrhs) {
+k_sv_tri(const SnodeDev* __restrict__ sn, const TriItem* __restrict__ items, int nitems, const T* __restrict__ L,
+         T* __restrict__ Y, int n, int nrhs, int* __restrict__ flags, int* __restrict__ sync, int* __restrict__ err) {
   extern __shared__ __align__(16) unsigned char sv_smem[];
-  T* ys = reinterpret_cast<T*>(sv_smem);          // kSolveSB x nrhs
-  T* Ls = ys + kSolveSB * nrhs;                   // 64 x 65 diagonal sub-block
-  T* Lt = Ls + kSub * 65;                         // 64 x 65 update tile
-  T* inv = Lt + kSub * 65;                        // 64
-  const SnodeDev d = sn[list[blockIdx.x]];
-  const T* P = L + d.loff;
-  const int sbk = min(sb, d.s - k0);
-  for (int q = threadIdx.x; q < sbk * nrhs; q += blockDim.x) {
-    const int i = q % sbk, r = q / sbk;
-    ys[i + r * kSolveSB] = Y[d.f + k0 + i + (int64_t)r * n];
-  }
-  const int nsub = (sbk + kSub - 1) / kSub;
-  const int rr = threadIdx.x >> 4, q = threadIdx.x & 15;
-  const bool live = rr < nrhs;
-  for (int t = 0; t < nsub; ++t) {
-    const int sub = TRANS ? nsub - 1 - t : t;
-    const int s0 = sub * kSub, kb = min(kSub, sbk - s0);
-    __syncthreads();
-    for (int e = threadIdx.x; e < kb * kb; e += blockDim.x) {
-      const int r = e % kb, c = e / kb;
-      Ls[r + c * 65] = lval<T, RM>(P, d, k0 + s0 + r, k0 + s0 + c);
+  T* ys = reinterpret_cast<T*>(sv_smem);   // a solved block j, 64 x nrhs
+  T* yi = ys + kSub * nrhs;                 // this block's right-hand sides, 64 x nrhs
+  T* Ls = yi + kSub * nrhs;                 // diagonal tile, 64 x 65
+  T* Lt = Ls + kSub * 65;                   // tile of the last dependency, 64 x 65
+  T* red = Lt;                              // then: k-group partial sums, 4 x 64 x nrhs
+  T* inv = Lt + kSub * 65;                  // 64
+  __shared__ int target;
+  if (threadIdx.x == 0) target = ld_acquire(sync) + 1;
+  __syncthreads();
+  const int tgt = target;
+  const int tid = threadIdx.x, r = tid & 63, g = tid >> 6;
+  constexpr bool kfast = RM != TRANS;       // the stored-contiguous index of a product tile is k
+  for (int it = blockIdx.x; it < nitems; it += gridDim.x) {
+    const TriItem item = items[it];
+    const SnodeDev d = sn[item.J];
+    const T* P = L + d.loff;
+    const int blk = TRANS ? item.nb - 1 - item.i : item.i;
+    const int i0 = blk * kSub, kb = min(kSub, d.s - i0);
+    // stage the diagonal tile and the last dependency's tile before waiting
+    for (int e = tid; e < kb * kb; e += kT) {
+      const int rr = RM ? e / kb : e % kb, cc = RM ? e % kb : e / kb;
+      Ls[rr + cc * 65] = lval<T, RM>(P, d, i0 + rr, i0 + cc);
     }
-    __syncthreads();
-    for (int c = threadIdx.x; c < kb; c += blockDim.x) inv[c] = T(1) / Ls[c + c * 65];
-    __syncthreads();
-    T y[4];
-#pragma unroll
-    for (int a = 0; a < 4; ++a) {
-      const int i = q + 16 * a;
-      y[a] = (live && i < kb) ? ys[s0 + i + rr * kSolveSB] : T(0);
+    if (item.i > 0) {
+      const int jl = TRANS ? blk + 1 : blk - 1, jl0 = jl * kSub, jlb = min(kSub, d.s - jl0);
+      for (int e = tid; e < kb * jlb; e += kT) {
+        const int rr = kfast ? e / jlb : e % kb, k = kfast ? e % jlb : e / kb;
+        Lt[rr + k * 65] = TRANS ? lval<T, RM>(P, d, jl0 + k, i0 + rr) : lval<T, RM>(P, d, i0 + rr, jl0 + k);
+      }
     }
-    if (!TRANS) {
+    T acc[kSolveChunk];
 #pragma unroll
-      for (int ka = 0; ka < 4; ++ka)
+    for (int m = 0; m < kSolveChunk; ++m) acc[m] = T(0);
+    const int ka = g * 16;                  // this thread's k range within a tile
+    for (int q = 0; q < item.i; ++q) {
+      const int j = TRANS ? item.nb - 1 - q : q;       // an already solved block
+      const int j0 = j * kSub, jb = min(kSub, d.s - j0);
+      if (tid == 0) {
+        long long polls = 0;
+        while (ld_acquire(flags + item.fbase + j) != tgt) {
+          if (++polls > kTriMaxPolls) { atomicExch(err, 1); break; }
+          __nanosleep(100);
+        }
+        __threadfence();
+      }
+      __syncthreads();   // also: the previous tile is done with ys
+      for (int e = tid; e < jb * nrhs; e += kT) {
+        const int k = e % jb, rr = e / jb;
+        ys[k + rr * kSub] = __ldcg(Y + d.f + j0 + k + (int64_t)rr * n);
+      }
+      __syncthreads();
+      if (r < kb) {
+        const int kz = min(jb, ka + 16);
+        if (q + 1 < item.i) {
+          const int row = i0 + r;
+          for (int k = ka; k < kz; ++k) {
+            const T l = TRANS ? lval<T, RM>(P, d, j0 + k, row) : lval<T, RM>(P, d, row, j0 + k);
 #pragma unroll
-        for (int kq = 0; kq < 16; ++kq) {
-          const int k = ka * 16 + kq;
-          if (k < kb) {
-            const T yk = __shfl_sync(0xffffffffu, y[ka] * inv[k], kq, 16);
-            if (q == kq) y[ka] = yk;
+            for (int m = 0; m < kSolveChunk; ++m)
+              if (m < nrhs) acc[m] += l * ys[k + m * kSub];
+          }
+        } else {
+          for (int k = ka; k < kz; ++k) {
+            const T l = Lt[r + k * 65];
 #pragma unroll
-            for (int a = 0; a < 4; ++a) {
-              const int i = q + 16 * a;
-              if (i > k && i < kb) y[a] -= Ls[i + k * 65] * yk;
-            }
+            for (int m = 0; m < kSolveChunk; ++m)
+              if (m < nrhs) acc[m] += l * ys[k + m * kSub];
           }
         }
-    } else {
-#pragma unroll
-      for (int ka = 3; ka >= 0; --ka)
-#pragma unroll
-        for (int kq = 15; kq >= 0; --kq) {
-          const int k = ka * 16 + kq;
-          if (k < kb) {
-            const T yk = __shfl_sync(0xffffffffu, y[ka] * inv[k], kq, 16);
-            if (q == kq) y[ka] = yk;
-#pragma unroll
-            for (int a = 0; a < 4; ++a) {
-              const int i = q + 16 * a;
-              if (i < k) y[a] -= Ls[k + i * 65] * yk;
-            }
-          }
-        }
+      }
     }
-    if (live) {
+    __syncthreads();   // Lt is free: it now holds the partial sums
+#pragma unroll
+    for (int m = 0; m < kSolveChunk; ++m)
+      if (m < nrhs) red[(g * kSub + r) + m * 4 * kSub] = acc[m];
+    __syncthreads();
+    // right-hand sides of this block minus the accumulated products (fixed order)
+    for (int e = tid; e < kb * nrhs; e += kT) {
+      const int rr = e % kb, m = e / kb;
+      const T* pr = red + m * 4 * kSub + rr;
+      const T sum = ((pr[0] + pr[kSub]) + pr[2 * kSub]) + pr[3 * kSub];
+      yi[rr + m * kSub] = Y[d.f + i0 + rr + (int64_t)m * n] - sum;
+    }
+    for (int c = tid; c < kb; c += kT) inv[c] = T(1) / Ls[c + c * 65];
+    __syncthreads();
+    // substitution: 16 lanes per right-hand side, lane q holds rows q + 16a;
+    // every lane takes part in the shuffles, only live ones write
+    const int rr = tid >> 4, q = tid & 15;
+    const bool live = rr < nrhs;
+    {
+      T y[4];
 #pragma unroll
       for (int a = 0; a < 4; ++a) {
         const int i = q + 16 * a;
-        if (i < kb) ys[s0 + i + rr * kSolveSB] = y[a];
+        y[a] = (live && i < kb) ? yi[i + rr * kSub] : T(0);
+      }
+      if (!TRANS) {
+#pragma unroll
+        for (int ka = 0; ka < 4; ++ka)
+#pragma unroll
+          for (int kq = 0; kq < 16; ++kq) {
+            const int k = ka * 16 + kq;
+            if (k < kb) {
+              const T yk = __shfl_sync(0xffffffffu, y[ka] * inv[k], kq, 16);
+              if (q == kq) y[ka] = yk;
+#pragma unroll
+              for (int a = 0; a < 4; ++a) {
+                const int i = q + 16 * a;
+                if (i > k && i < kb) y[a] -= Ls[i + k * 65] * yk;
+              }
+            }
+          }
+      } else {
+#pragma unroll
+        for (int ka = 3; ka >= 0; --ka)
+#pragma unroll
+          for (int kq = 15; kq >= 0; --kq) {
+            const int k = ka * 16 + kq;
+            if (k < kb) {
+              const T yk = __shfl_sync(0xffffffffu, y[ka] * inv[k], kq, 16);
+              if (q == kq) y[ka] = yk;
+#pragma unroll
+              for (int a = 0; a < 4; ++a) {
+                const int i = q + 16 * a;
+                if (i < k) y[a] -= Ls[k + i * 65] * yk;
+              }
+            }
+          }
+      }
+      if (live) {
+#pragma unroll
+        for (int a = 0; a < 4; ++a) {
+          const int i = q + 16 * a;
+          if (i < kb) Y[d.f + i0 + i + (int64_t)rr * n] = y[a];
+        }
       }
     }
+    __threadfence();
     __syncthreads();
-    // update the rest of the super-block with the solved sub-block, 64 rows at a
-    // time through a staged tile (coalesced loads whatever the storage form)
-    const int lo = TRANS ? 0 : s0 + kb, hi = TRANS ? s0 : sbk;
-    for (int t0 = lo; t0 < hi; t0 += kSub) {
-      const int rows = min(kSub, hi - t0);
-      __syncthreads();
-      for (int e = threadIdx.x; e < rows * kb; e += blockDim.x) {
-        // the contiguous index of the stored element varies fastest
-        const bool kfast = RM != TRANS;
-        const int r = kfast ? e / kb : e % rows, k = kfast ? e % kb : e / rows;
-        Lt[r + k * 65] = TRANS ? lval<T, RM>(P, d, k0 + s0 + k, k0 + t0 + r) : lval<T, RM>(P, d, k0 + t0 + r, k0 + s0 + k);
-      }
-      __syncthreads();
-      for (int e = threadIdx.x; e < rows * nrhs; e += blockDim.x) {
-        const int r = e % rows, rr2 = e / rows;
-        T acc = T(0);
-#pragma unroll 8
-        for (int k = 0; k < kb; ++k) acc += Lt[r + k * 65] * ys[s0 + k + rr2 * kSolveSB];
-        ys[t0 + r + rr2 * kSolveSB] -= acc;
-      }
-    }
+    if (tid == 0) st_release(flags + item.fbase + blk, tgt);
   }
+  // the last CTA to finish advances the epoch for the next launch
   __syncthreads();
-  for (int e = threadIdx.x; e < sbk * nrhs; e += blockDim.x) {
-    const int i = e % sbk, r = e / sbk;
-    Y[d.f + k0 + i + (int64_t)r * n] = ys[i + r * kSolveSB];
-  }
-}
-
-// Forward update inside the diagonal block: rows [r0, r0 + 64) (all < s) of J
-// minus L[rows, k0:k0+sbk] y[k0:k0+sbk]; 64 rows x 4 right-hand-side groups.
-template <class T, bool RM>
-__global__ void __launch_bounds__(kT)
-k_sv_fupd(const SnodeDev* __restrict__ sn, const TileTask* __restrict__ tasks, int sb, const T* __restrict__ L,
-          T* __restrict__ Y, int n, int nrhs) {
-  extern __shared__ __align__(16) unsigned char sv_smem[];
-  T* yk = reinterpret_cast<T*>(sv_smem);          // kSolveSB x nrhs
-  const TileTask t = tasks[blockIdx.x];
-  const SnodeDev d = sn[t.J];
-  const int sbk = min(sb, d.s - t.k0);
-  for (int q = threadIdx.x; q < sbk * nrhs; q += blockDim.x) {
-    const int i = q % sbk, r = q / sbk;
-    yk[i + r * kSolveSB] = Y[d.f + t.k0 + i + (int64_t)r * n];
-  }
-  __syncthreads();
-  const int row = threadIdx.x & 63, rg = threadIdx.x >> 6;
-  const int gr = t.r0 + row;
-  if (gr >= d.s) return;
-  const T* P = L + d.loff;
-  T acc[kSolveChunk / 4];
-#pragma unroll
-  for (int j = 0; j < kSolveChunk / 4; ++j) acc[j] = T(0);
-  for (int k = 0; k < sbk; ++k) {
-    const T l = lval<T, RM>(P, d, gr, t.k0 + k);
-#pragma unroll
-    for (int j = 0; j < kSolveChunk / 4; ++j) {
-      const int r = rg + 4 * j;
-      if (r < nrhs) acc[j] += l * yk[k + r * kSolveSB];
+  if (tid == 0) {
+    __threadfence();
+    if (atomicAdd(sync + 1, 1) == (int)gridDim.x - 1) {
+      atomicExch(sync + 1, 0);
+      __threadfence();
+      atomicAdd(sync, 1);
     }
-  }
-#pragma unroll
-  for (int j = 0; j < kSolveChunk / 4; ++j) {
-    const int r = rg + 4 * j;
-    if (r < nrhs) Y[d.f + gr + (int64_t)r * n] -= acc[j];
   }
 }
 
@@ -460,43 +508,6 @@ k_sv_bred(const SnodeDev* __restrict__ sn, const TileTask* __restrict__ tasks, c
   }
 }
 
-// Backward update: y[c0..c0+64) -= L[k0:k0+sbk, c]^T x[k0:k0+sbk] for c < k0.
-template <class T, bool RM>
-__global__ void __launch_bounds__(kT)
-k_sv_bupd(const SnodeDev* __restrict__ sn, const TileTask* __restrict__ tasks, int sb, const T* __restrict__ L,
-          T* __restrict__ Y, int n, int nrhs) {
-  extern __shared__ __align__(16) unsigned char sv_smem[];
-  T* xk = reinterpret_cast<T*>(sv_smem);          // kSolveSB x nrhs
-  const TileTask t = tasks[blockIdx.x];
-  const SnodeDev d = sn[t.J];
-  const int sbk = min(sb, d.s - t.k0);
-  for (int q = threadIdx.x; q < sbk * nrhs; q += blockDim.x) {
-    const int i = q % sbk, r = q / sbk;
-    xk[i + r * kSolveSB] = Y[d.f + t.k0 + i + (int64_t)r * n];
-  }
-  __syncthreads();
-  const int col = threadIdx.x & 63, rg = threadIdx.x >> 6;
-  const int gc = t.c0 + col;
-  if (gc >= t.k0) return;
-  const T* P = L + d.loff;
-  T acc[kSolveChunk / 4];
-#pragma unroll
-  for (int j = 0; j < kSolveChunk / 4; ++j) acc[j] = T(0);
-  for (int k = 0; k < sbk; ++k) {
-    const T l = lval<T, RM>(P, d, t.k0 + k, gc);
-#pragma unroll
-    for (int j = 0; j < kSolveChunk / 4; ++j) {
-      const int r = rg + 4 * j;
-      if (r < nrhs) acc[j] += l * xk[k + r * kSolveSB];
-    }
-  }
-#pragma unroll
-  for (int j = 0; j < kSolveChunk / 4; ++j) {
-    const int r = rg + 4 * j;
-    if (r < nrhs) Y[d.f + gc + (int64_t)r * n] -= acc[j];
-  }
-}
-
 // Small supernodes (s <= 32, len <= 256), one warp each. Forward: lane i holds
 // y_i of the current right-hand side; the solved entry is broadcast by shuffle;
 // then w_J = L_RJ y_J with lanes along the off-diagonal rows.
@@ -563,24 +574,35 @@ k_sv_small_bwd(const SnodeDev* __restrict__ sn, const int32_t* __restrict__ list
   }
 }
 
-template <class T>
-size_t diag_smem(int nr) {
-  return sizeof(T) * ((size_t)kSolveSB * nr + 2 * kSub * 65 + kSub);
-}
-
-template <class T>
-size_t blk_smem(int nr) {
-  return sizeof(T) * (size_t)kSolveSB * nr;
-}
-
 // The level schedule of one solve on a chunk of nr <= 16 right-hand sides
 // already permuted into Y (W: per-level panel products). `prof` enables the
 // per-class launch accounting (off for the no-allocation entry point).
+// Resident CTAs per SM of each triangle kernel per chunk width (set once).
+int g_tri_per_sm[2][2][kSolveChunk + 1] = {};   // [binary32][transposed][nr]
+
+template <class T, bool RM, bool TRANS>
+int launch_tri(chol_handle* h, const LevelPlan& P, const T* L, T* Y, int nr, cudaStream_t st) {
+  DeviceState* D = h->dev;
+  const int per_sm = g_tri_per_sm[sizeof(T) == 4][TRANS][nr];
+  if (per_sm < 1) return CHOL_ENOTSUP;
+  const int grid = std::min(P.tri_n, per_sm * D->sms);
+  const TriItem* items = reinterpret_cast<const TriItem*>(D->tri) + P.tri_b;
+  int nitems = P.tri_n, n = h->n;
+  void* args[] = {(void*)&D->sn, (void*)&items, (void*)&nitems, (void*)&L, (void*)&Y, (void*)&n, (void*)&nr,
+                  (void*)&D->tri_flags, (void*)&D->tri_sync, (void*)&D->sv_err};
+  const cudaError_t e = cudaLaunchCooperativeKernel((const void*)k_sv_tri<T, RM, TRANS>, dim3(grid), dim3(kT), args,
+                                                    tri_smem<T>(nr), st);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    return CHOL_ECUDA;
+  }
+  return CHOL_OK;
+}
+
 template <class T, bool RM>
-void solve_levels(chol_handle* h, const T* L, T* Y, T* W, T* part, int nr, cudaStream_t st, bool prof) {
+int solve_levels(chol_handle* h, const T* L, T* Y, T* W, T* part, int nr, cudaStream_t st, bool prof) {
   DeviceState* D = h->dev;
   const int n = h->n;
-  const int sb = h->solve_sb;
   auto scope = [&](int cls) { return prof ? new KScope(h, cls, st, 0.0, 0.0) : nullptr; };
   for (const LevelPlan& P : h->levels) {
     if (P.ssmall_n > 0) {
@@ -589,20 +611,11 @@ void solve_levels(chol_handle* h, const T* L, T* Y, T* W, T* part, int nr, cudaS
                                                                  W, nr);
       delete ks;
     }
-    for (size_t k = 0; k < P.ssteps.size(); ++k) {
-      const SolveStep& s = P.ssteps[k];
-      const int k0 = (int)k * sb;
-      if (s.diag_n > 0) {
-        KScope* ks = scope(CHOL_K_SOLVE_DIAG);
-        k_sv_diag<T, RM, false><<<s.diag_n, kT, diag_smem<T>(nr), st>>>(D->sn, D->sdiag + s.diag_b, k0, sb, L, Y, n,
-                                                                          nr);
-        delete ks;
-      }
-      if (s.fupd_n > 0) {
-        KScope* ks = scope(CHOL_K_SOLVE_FUPD);
-        k_sv_fupd<T, RM><<<s.fupd_n, kT, blk_smem<T>(nr), st>>>(D->sn, D->fupd + s.fupd_b, sb, L, Y, n, nr);
-        delete ks;
-      }
+    if (P.tri_n > 0) {
+      KScope* ks = scope(CHOL_K_SOLVE_DIAG);
+      const int rc = launch_tri<T, RM, false>(h, P, L, Y, nr, st);
+      delete ks;
+      if (rc) return rc;
     }
     if (P.gemv_n > 0) {
       KScope* ks = scope(CHOL_K_SOLVE_GEMV);
@@ -637,39 +650,32 @@ void solve_levels(chol_handle* h, const T* L, T* Y, T* W, T* part, int nr, cudaS
                                                                  L, Y, n, nr);
       delete ks;
     }
-    for (int k = (int)P.ssteps.size() - 1; k >= 0; --k) {
-      const SolveStep& s = P.ssteps[k];
-      const int k0 = k * sb;
-      if (s.diag_n > 0) {
-        KScope* ks = scope(CHOL_K_SOLVE_DIAG);
-        k_sv_diag<T, RM, true><<<s.diag_n, kT, diag_smem<T>(nr), st>>>(D->sn, D->sdiag + s.diag_b, k0, sb, L, Y, n,
-                                                                         nr);
-        delete ks;
-      }
-      if (s.bupd_n > 0) {
-        KScope* ks = scope(CHOL_K_SOLVE_BUPD);
-        k_sv_bupd<T, RM><<<s.bupd_n, kT, blk_smem<T>(nr), st>>>(D->sn, D->bupd + s.bupd_b, sb, L, Y, n, nr);
-        delete ks;
-      }
+    if (P.tri_n > 0) {
+      KScope* ks = scope(CHOL_K_SOLVE_DIAG);
+      const int rc = launch_tri<T, RM, true>(h, P, L, Y, nr, st);
+      delete ks;
+      if (rc) return rc;
     }
   }
+  return CHOL_OK;
 }
 
 int set_solve_attrs() {
   static std::once_flag once;
   static int rc = CHOL_OK;
   std::call_once(once, [] {
-    const size_t dd = diag_smem<double>(kSolveChunk), df = diag_smem<float>(kSolveChunk);
-    const size_t bd = blk_smem<double>(kSolveChunk), bf = blk_smem<float>(kSolveChunk);
+    const size_t dd = tri_smem<double>(kSolveChunk), df = tri_smem<float>(kSolveChunk);
+    const void* kd[2] = {(const void*)k_sv_tri<double, false, false>, (const void*)k_sv_tri<double, false, true>};
+    const void* kf[2] = {(const void*)k_sv_tri<float, true, false>, (const void*)k_sv_tri<float, true, true>};
     cudaError_t e = cudaSuccess;
-    e = e ? e : cudaFuncSetAttribute(k_sv_diag<double, false, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dd);
-    e = e ? e : cudaFuncSetAttribute(k_sv_diag<double, false, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dd);
-    e = e ? e : cudaFuncSetAttribute(k_sv_diag<float, true, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)df);
-    e = e ? e : cudaFuncSetAttribute(k_sv_diag<float, true, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)df);
-    e = e ? e : cudaFuncSetAttribute(k_sv_fupd<double, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bd);
-    e = e ? e : cudaFuncSetAttribute(k_sv_fupd<float, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bf);
-    e = e ? e : cudaFuncSetAttribute(k_sv_bupd<double, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bd);
-    e = e ? e : cudaFuncSetAttribute(k_sv_bupd<float, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bf);
+    for (int t = 0; t < 2; ++t) {
+      e = e ? e : cudaFuncSetAttribute(kd[t], cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dd);
+      e = e ? e : cudaFuncSetAttribute(kf[t], cudaFuncAttributeMaxDynamicSharedMemorySize, (int)df);
+      for (int nr = 1; nr <= kSolveChunk; ++nr) {
+        e = e ? e : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&g_tri_per_sm[0][t][nr], kd[t], kT, tri_smem<double>(nr));
+        e = e ? e : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&g_tri_per_sm[1][t][nr], kf[t], kT, tri_smem<float>(nr));
+      }
+    }
     if (e != cudaSuccess) {
       cudaGetLastError();
       rc = CHOL_ECUDA;
@@ -703,7 +709,8 @@ int solve_fp64(chol_handle* h, double* b, int32_t nrhs, cudaStream_t st, double*
     KScope* ks = prof ? new KScope(h, CHOL_K_PERMUTE, st, 0.0, 24.0 * n * nr) : nullptr;
     k_sv_permute_in<double><<<grid1d((int64_t)n * nr, 256), 256, 0, st>>>(B, D->perm, nullptr, nullptr, n, nr, Y);
     delete ks;
-    solve_levels<double, false>(h, (const double*)D->L, Y, W, (double*)nullptr, nr, st, prof);
+    const int rc = solve_levels<double, false>(h, (const double*)D->L, Y, W, (double*)nullptr, nr, st, prof);
+    if (rc) return rc;
     ks = prof ? new KScope(h, CHOL_K_PERMUTE, st, 0.0, 24.0 * n * nr) : nullptr;
     k_sv_permute_out<double><<<grid1d((int64_t)n * nr, 256), 256, 0, st>>>(Y, D->perm, nullptr, nullptr, n, nr, B);
     delete ks;
@@ -738,13 +745,27 @@ int chol_solve_mixed(chol_handle* h, double* b, int32_t nrhs, cudaStream_t st) {
       k_sv_maxabs<<<grid1d(n, 256), 256, 0, st>>>(B, n, nr, sc);
       k_sv_permute_in<float><<<grid1d((int64_t)n * nr, 256), 256, 0, st>>>(B, D->perm, D->mx_d, sc, n, nr, D->Y32);
     }
-    solve_levels<float, true>(h, (const float*)D->L, D->Y32, D->W32, D->P32, nr, st, true);
+    if ((rc = solve_levels<float, true>(h, (const float*)D->L, D->Y32, D->W32, D->P32, nr, st, true))) return rc;
     {
       KScope ks(h, CHOL_K_PERMUTE, st, 0.0, 12.0 * n * nr);
       k_sv_permute_out<float><<<grid1d((int64_t)n * nr, 256), 256, 0, st>>>(D->Y32, D->perm, D->mx_d, sc, n, nr, B);
     }
   }
   CHOL_CUDA_TRY(cudaGetLastError());
+  return CHOL_OK;
+}
+
+// CHOL_ETIMEOUT if a triangle launch gave up waiting since the last check
+// (for callers that have synchronized with the solves).
+int chol_solve_status(chol_handle* h) {
+  DeviceState* D = h->dev;
+  if (!D || !D->sv_err) return CHOL_OK;
+  int32_t e = 0;
+  CHOL_CUDA_TRY(cudaMemcpy(&e, D->sv_err, sizeof(int32_t), cudaMemcpyDeviceToHost));
+  if (e != 0) {
+    CHOL_CUDA_TRY(cudaMemset(D->sv_err, 0, sizeof(int32_t)));
+    return CHOL_ETIMEOUT;
+  }
   return CHOL_OK;
 }
 
