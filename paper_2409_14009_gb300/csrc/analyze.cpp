@@ -537,7 +537,10 @@ void build(chol_handle* h, const int64_t* colptr, const int32_t* rowind) {
     };
     P.ssmall_b = (int32_t)h->ssmall_list.size();
     for (int32_t J : Js)
-      if (warp_solved(J)) h->ssmall_list.push_back(J);
+      if (warp_solved(J) && h->snodes[J].s <= 8) h->ssmall_list.push_back(J);
+    P.ssmall8_n = (int32_t)h->ssmall_list.size() - P.ssmall_b;
+    for (int32_t J : Js)
+      if (warp_solved(J) && h->snodes[J].s > 8) h->ssmall_list.push_back(J);
     P.ssmall_n = (int32_t)h->ssmall_list.size() - P.ssmall_b;
     P.tri_b = (int32_t)h->tri_items.size();
     for (int32_t J : Js) {

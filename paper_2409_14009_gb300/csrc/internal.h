@@ -64,7 +64,8 @@ struct LevelPlan {
   int32_t asm_b, asm_n;       // assembly tasks, one CTA each
   int32_t asmw_n;             // then (from asm_b + asm_n) small tasks, one warp each
   int32_t tri_b, tri_n;       // diagonal-triangle solve items (in tri_items), dependency order
-  int32_t ssmall_b, ssmall_n; // supernodes solved by one warp each (in ssmall_list)
+  int32_t ssmall_b, ssmall_n; // supernodes solved by one warp each (in ssmall_list),
+  int32_t ssmall8_n;          // the first ssmall8_n of them with s <= 8
   int32_t gemv_b, gemv_n;     // forward-solve panel products (TileTask: J, r0)
   int32_t bpart_b, bpart_n;   // row-major backward panel, stage 1 (J, chunk, u0, c0)
   int32_t bred_b, bred_n;     // row-major backward panel, stage 2 (J, c0)

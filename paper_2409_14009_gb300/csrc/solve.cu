@@ -370,13 +370,19 @@ k_sv_gemv(const SnodeDev* __restrict__ sn, const TileTask* __restrict__ tasks, c
   }
 }
 
-// y[targets] -= w_J through the relind task lists (pull-ordered).
+// y[targets] -= w_J through the relind task lists (pull-ordered), one warp per
+// task: only the first position chunk of a column tile holds the segments'
+// columns; segments are applied in order (the same y entries can appear in
+// several), so each entry receives its contributions in a fixed order.
 template <class T>
 __global__ void __launch_bounds__(kT)
-k_sv_fasm(const AsmTask* __restrict__ tasks, const AsmSeg* __restrict__ segs, const SnodeDev* __restrict__ sn,
-          const int32_t* __restrict__ rows, const T* __restrict__ W, T* __restrict__ Y, int n, int nrhs) {
-  const AsmTask t = tasks[blockIdx.x];
-  if (t.p0 != t.t0) return;   // only the first position chunk of a column tile holds the columns
+k_sv_fasm(const AsmTask* __restrict__ tasks, int ntasks, const AsmSeg* __restrict__ segs,
+          const SnodeDev* __restrict__ sn, const int32_t* __restrict__ rows, const T* __restrict__ W,
+          T* __restrict__ Y, int n, int nrhs) {
+  const int i = blockIdx.x * (kT / 32) + (threadIdx.x >> 5), lane = threadIdx.x & 31;
+  if (i >= ntasks) return;
+  const AsmTask t = tasks[i];
+  if (t.p0 != t.t0) return;
   for (int g = t.seg_begin; g < t.seg_end; ++g) {
     const AsmSeg sg = segs[g];
     const SnodeDev dj = sn[sg.J];
@@ -384,11 +390,11 @@ k_sv_fasm(const AsmTask* __restrict__ tasks, const AsmSeg* __restrict__ segs, co
     const int32_t* rj = rows + dj.roff + dj.s;
     const T* Wj = W + dj.wpre * nrhs;
     const int ncol = sg.cb - sg.ca;
-    for (int q = threadIdx.x; q < ncol * nrhs; q += blockDim.x) {
+    for (int q = lane; q < ncol * nrhs; q += 32) {
       const int c = sg.ca + q % ncol, r = q / ncol;
       Y[rj[c] + (int64_t)r * n] -= Wj[c + (int64_t)r * b];
     }
-    __syncthreads();
+    __syncwarp();
   }
 }
 
@@ -508,10 +514,13 @@ k_sv_bred(const SnodeDev* __restrict__ sn, const TileTask* __restrict__ tasks, c
   }
 }
 
-// Small supernodes (s <= 32, len <= 256), one warp each. Forward: lane i holds
-// y_i of the current right-hand side; the solved entry is broadcast by shuffle;
-// then w_J = L_RJ y_J with lanes along the off-diagonal rows.
-template <class T, bool RM>
+// Small supernodes (s <= 32, len <= 256), one warp each. Lane i holds row i of
+// the diagonal block in registers (loaded once, with the reciprocal pivots), so
+// the substitution chain is shuffles and FMAs only. Forward: the solved entry
+// is broadcast by shuffle; then w_J = L_RJ y_J with lanes along the
+// off-diagonal rows. S bounds s (8 or 32), which sizes the register copy of
+// the row.
+template <class T, bool RM, int S>
 __global__ void __launch_bounds__(kT)
 k_sv_small_fwd(const SnodeDev* __restrict__ sn, const int32_t* __restrict__ list, int count,
                const T* __restrict__ L, T* __restrict__ Y, int n, T* __restrict__ W, int nrhs) {
@@ -521,12 +530,19 @@ k_sv_small_fwd(const SnodeDev* __restrict__ sn, const int32_t* __restrict__ list
   const T* P = L + d.loff;
   const int b = d.len - d.s;
   T* Wj = W + d.wpre * nrhs;
+  T lrow[S];   // L(lane, k), k < lane (s <= S)
+#pragma unroll
+  for (int k = 0; k < S; ++k) lrow[k] = (k < lane && lane < d.s) ? lval<T, RM>(P, d, lane, k) : T(0);
+  const T rdiag = lane < d.s ? T(1) / lval<T, RM>(P, d, lane, lane) : T(0);
   for (int r = 0; r < nrhs; ++r) {
     T y = lane < d.s ? Y[d.f + lane + (int64_t)r * n] : T(0);
-    for (int k = 0; k < d.s; ++k) {
-      const T yk = __shfl_sync(0xffffffffu, y, k) / lval<T, RM>(P, d, k, k);
-      if (lane == k) y = yk;
-      if (lane > k && lane < d.s) y -= lval<T, RM>(P, d, lane, k) * yk;
+#pragma unroll
+    for (int k = 0; k < S; ++k) {
+      if (k < d.s) {   // uniform across the warp
+        const T yk = __shfl_sync(0xffffffffu, y * rdiag, k);
+        if (lane == k) y = yk;
+        if (lane > k) y -= lrow[k] * yk;
+      }
     }
     if (lane < d.s) Y[d.f + lane + (int64_t)r * n] = y;
     T acc[kSolveSmallRows / 32];
@@ -549,8 +565,9 @@ k_sv_small_fwd(const SnodeDev* __restrict__ sn, const int32_t* __restrict__ list
 }
 
 // Backward for the same supernodes: lane k gathers t_k = sum_u L(s+u, k) x[rows[s+u]]
-// (ancestor rows are final), then the transposed diagonal solve with shuffles.
-template <class T, bool RM>
+// (ancestor rows are final; four rows' loads in flight), then the transposed
+// diagonal solve with shuffles, lane i holding column i of the block.
+template <class T, bool RM, int S>
 __global__ void __launch_bounds__(kT)
 k_sv_small_bwd(const SnodeDev* __restrict__ sn, const int32_t* __restrict__ list, int count,
                const int32_t* __restrict__ rows, const T* __restrict__ L, T* __restrict__ Y, int n, int nrhs) {
@@ -560,15 +577,33 @@ k_sv_small_bwd(const SnodeDev* __restrict__ sn, const int32_t* __restrict__ list
   const T* P = L + d.loff;
   const int b = d.len - d.s;
   const int32_t* rj = rows + d.roff + d.s;
+  T lcol[S];   // L(k, lane), k > lane (s <= S)
+#pragma unroll
+  for (int k = 0; k < S; ++k) lcol[k] = (k > lane && k < d.s) ? lval<T, RM>(P, d, k, lane) : T(0);
+  const T rdiag = lane < d.s ? T(1) / lval<T, RM>(P, d, lane, lane) : T(0);
   for (int r = 0; r < nrhs; ++r) {
     T t = T(0);
-    if (lane < d.s)
-      for (int u = 0; u < b; ++u) t += lval<T, RM>(P, d, d.s + u, lane) * Y[rj[u] + (int64_t)r * n];
+    if (lane < d.s) {
+      for (int u0 = 0; u0 < b; u0 += 4) {
+        T lv[4], xv[4];
+#pragma unroll
+        for (int uu = 0; uu < 4; ++uu) {
+          const int u = u0 + uu;
+          lv[uu] = u < b ? lval<T, RM>(P, d, d.s + u, lane) : T(0);
+          xv[uu] = u < b ? Y[rj[u] + (int64_t)r * n] : T(0);
+        }
+#pragma unroll
+        for (int uu = 0; uu < 4; ++uu) t += lv[uu] * xv[uu];
+      }
+    }
     T y = lane < d.s ? Y[d.f + lane + (int64_t)r * n] - t : T(0);
-    for (int k = d.s - 1; k >= 0; --k) {
-      const T xk = __shfl_sync(0xffffffffu, y, k) / lval<T, RM>(P, d, k, k);
-      if (lane == k) y = xk;
-      if (lane < k) y -= lval<T, RM>(P, d, k, lane) * xk;
+#pragma unroll
+    for (int k = S - 1; k >= 0; --k) {
+      if (k < d.s) {   // uniform across the warp
+        const T xk = __shfl_sync(0xffffffffu, y * rdiag, k);
+        if (lane == k) y = xk;
+        if (lane < k) y -= lcol[k] * xk;
+      }
     }
     if (lane < d.s) Y[d.f + lane + (int64_t)r * n] = y;
   }
@@ -606,9 +641,14 @@ int solve_levels(chol_handle* h, const T* L, T* Y, T* W, T* part, int nr, cudaSt
   auto scope = [&](int cls) { return prof ? new KScope(h, cls, st, 0.0, 0.0) : nullptr; };
   for (const LevelPlan& P : h->levels) {
     if (P.ssmall_n > 0) {
+      // supernodes with s <= 8 first, then the wider ones
       KScope* ks = scope(CHOL_K_SOLVE_DIAG);
-      k_sv_small_fwd<T, RM><<<(P.ssmall_n + 7) / 8, kT, 0, st>>>(D->sn, D->ssmall + P.ssmall_b, P.ssmall_n, L, Y, n,
-                                                                 W, nr);
+      const int n8 = P.ssmall8_n, nw = P.ssmall_n - P.ssmall8_n;
+      if (n8 > 0)
+        k_sv_small_fwd<T, RM, 8><<<(n8 + 7) / 8, kT, 0, st>>>(D->sn, D->ssmall + P.ssmall_b, n8, L, Y, n, W, nr);
+      if (nw > 0)
+        k_sv_small_fwd<T, RM, 32><<<(nw + 7) / 8, kT, 0, st>>>(D->sn, D->ssmall + P.ssmall_b + n8, nw, L, Y, n, W, nr);
+      if (ks) ks->launches((n8 > 0) + (nw > 0));
       delete ks;
     }
     if (P.tri_n > 0) {
@@ -625,8 +665,9 @@ int solve_levels(chol_handle* h, const T* L, T* Y, T* W, T* part, int nr, cudaSt
     if (P.asm_n + P.asmw_n > 0) {
       // the CTA-sized and the warp-sized assembly tasks of the level, contiguous
       KScope* ks = scope(CHOL_K_SOLVE_FASM);
-      k_sv_fasm<T><<<P.asm_n + P.asmw_n, kT, 0, st>>>(D->asm_tasks + P.asm_b, D->asm_segs, D->sn, D->rows, W, Y,
-                                                      n, nr);
+      const int nt = P.asm_n + P.asmw_n;
+      k_sv_fasm<T><<<(nt + kT / 32 - 1) / (kT / 32), kT, 0, st>>>(D->asm_tasks + P.asm_b, nt, D->asm_segs, D->sn,
+                                                                  D->rows, W, Y, n, nr);
       delete ks;
     }
   }
@@ -646,8 +687,13 @@ int solve_levels(chol_handle* h, const T* L, T* Y, T* W, T* part, int nr, cudaSt
     }
     if (P.ssmall_n > 0) {
       KScope* ks = scope(CHOL_K_SOLVE_DIAG);
-      k_sv_small_bwd<T, RM><<<(P.ssmall_n + 7) / 8, kT, 0, st>>>(D->sn, D->ssmall + P.ssmall_b, P.ssmall_n, D->rows,
-                                                                 L, Y, n, nr);
+      const int n8 = P.ssmall8_n, nw = P.ssmall_n - P.ssmall8_n;
+      if (n8 > 0)
+        k_sv_small_bwd<T, RM, 8><<<(n8 + 7) / 8, kT, 0, st>>>(D->sn, D->ssmall + P.ssmall_b, n8, D->rows, L, Y, n, nr);
+      if (nw > 0)
+        k_sv_small_bwd<T, RM, 32><<<(nw + 7) / 8, kT, 0, st>>>(D->sn, D->ssmall + P.ssmall_b + n8, nw, D->rows, L, Y,
+                                                                n, nr);
+      if (ks) ks->launches((n8 > 0) + (nw > 0));
       delete ks;
     }
     if (P.tri_n > 0) {
