@@ -337,8 +337,14 @@ int chol_get_factor(chol_handle* h, int64_t* lp, int32_t* li, double* lx, void* 
  */
 enum chol_kernel_class {
   CHOL_K_SCATTER = 0, CHOL_K_SMALL, CHOL_K_POTRF, CHOL_K_TRSM, CHOL_K_GEMM, CHOL_K_SYRK,
-  CHOL_K_ASSEMBLE, CHOL_K_SOLVE_DIAG, CHOL_K_SOLVE_FUPD, CHOL_K_SOLVE_FASM, CHOL_K_SOLVE_BPANEL,
-  CHOL_K_SOLVE_BUPD, CHOL_K_PERMUTE, CHOL_K_LOGDET, CHOL_K_SOLVE_GEMV, CHOL_K_NCLASSES
+  CHOL_K_ASSEMBLE, CHOL_K_SOLVE_DIAG,
+  CHOL_K_SELINV_INV,     /* selected inverse: L_JJ^{-1} (block inverses and their products) */
+  CHOL_K_SOLVE_FASM, CHOL_K_SOLVE_BPANEL,
+  CHOL_K_SELINV_GEMM,    /* selected inverse: Uhat, Z_RJ and Z_JJ products */
+  CHOL_K_PERMUTE, CHOL_K_LOGDET, CHOL_K_SOLVE_GEMV,
+  CHOL_K_SELINV_GATHER,  /* selected inverse: Z_RR gathered from the ancestors */
+  CHOL_K_ADJOINT,        /* per-entry gradient */
+  CHOL_K_NCLASSES
 };
 
 typedef struct chol_kernel_stat {

@@ -36,8 +36,8 @@ EXPORTED = ["chol_default_options", "chol_analyze", "chol_factor", "chol_solve",
             "chol_get_stats", "chol_destroy", "chol_strerror"]
 
 KERNEL_CLASSES = ["scatter", "small", "potrf", "trsm", "gemm", "syrk", "assemble", "solve_diag",
-                  "solve_fupd", "solve_fasm", "solve_bpanel", "solve_bupd", "permute", "logdet",
-                  "solve_gemv"]
+                  "selinv_inv", "solve_fasm", "solve_bpanel", "selinv_gemm", "permute", "logdet",
+                  "solve_gemv", "selinv_gather", "adjoint"]
 
 
 class chol_options(C.Structure):

@@ -58,21 +58,32 @@ __device__ __forceinline__ void gen_gemm_tile(const GenGemm& g, int i0, int j0) 
   if (g.amode == 1) kend = min(kend, i0 + kGTile);
   if (g.bmode == 1) kbeg = (j0 / KC) * KC;
   double acc[4][4] = {};
+  // the thread -> element map of each operand follows its contiguous index
+  const bool bkf = g.br == 1 && g.bc != 1;
   for (int k = kbeg; k < kend; k += KC) {
+    // symmetric A: the chunk reads its stored transpose wholly above the diagonal
+    const bool akf = g.amode == 2 ? (k >= i0 + kGTile ? g.ar == 1 : (g.ac == 1 && g.ar != 1))
+                                  : (g.ac == 1 && g.ar != 1);
 #pragma unroll
     for (int q = 0; q < 4; ++q) {
       const int idx = tid + kGT * q;
-      const int kk = idx >> 6, r = idx & 63;
-      const int kg = k + kk;
-      const int ia = i0 + r, jb = j0 + r;
-      double av = 0.0, bv = 0.0;
-      if (kg < g.K && ia < g.M) {
-        if (g.amode == 0 || (g.amode == 1 && kg <= ia)) av = g.A[ia * g.ar + kg * g.ac];
-        else if (g.amode == 2) av = kg <= ia ? g.A[ia * g.ar + kg * g.ac] : g.A[kg * g.ar + ia * g.ac];
+      {
+        const int kk = akf ? (idx & 15) : (idx >> 6), r = akf ? (idx >> 4) : (idx & 63);
+        const int kg = k + kk, ia = i0 + r;
+        double av = 0.0;
+        if (kg < g.K && ia < g.M) {
+          if (g.amode == 0 || (g.amode == 1 && kg <= ia)) av = g.A[ia * g.ar + kg * g.ac];
+          else if (g.amode == 2) av = kg <= ia ? g.A[ia * g.ar + kg * g.ac] : g.A[kg * g.ar + ia * g.ac];
+        }
+        As[kk][r] = av;
       }
-      if (kg < g.K && jb < g.N && (g.bmode == 0 || jb <= kg)) bv = g.B[kg * g.br + jb * g.bc];
-      As[kk][r] = av;
-      Bs[kk][r] = bv;
+      {
+        const int kk = bkf ? (idx & 15) : (idx >> 6), r = bkf ? (idx >> 4) : (idx & 63);
+        const int kg = k + kk, jb = j0 + r;
+        double bv = 0.0;
+        if (kg < g.K && jb < g.N && (g.bmode == 0 || jb <= kg)) bv = g.B[kg * g.br + jb * g.bc];
+        Bs[kk][r] = bv;
+      }
     }
     __syncthreads();
 #pragma unroll
@@ -248,13 +259,24 @@ int ensure_adjoint(chol_handle* h) {
 // Level plan of the selected inverse (built once, on first use).
 struct SiStep {
   int32_t inv_b, inv_n, g1_b, g1_n, g2_b, g2_n;
+  double flops;                         // algorithmic flops of the step
 };
 struct SiLevel {
   int64_t t_doubles;                    // T workspace of the level (zeroed first)
   std::vector<SiStep> steps;            // the L_JJ^{-1} recurrence, batched
   int32_t uh_b, uh_n, zrj_b, zrj_n, zjj1_b, zjj1_n, zjj2_b, zjj2_n;
   int32_t pair_b, pair_n;
+  double gemm_flops;                    // Uhat, Z_RJ and Z_JJ products
 };
+
+// Algorithmic flops of a descriptor: 2 M N K, halved for a triangular operand
+// and for a triangular output.
+double gemm_flops(const GenGemm& g) {
+  double f = 2.0 * g.M * (double)g.N * g.K;
+  if (g.amode == 1 || g.bmode == 1) f *= 0.5;
+  if (g.lower_c) f *= 0.5;
+  return f;
+}
 
 struct SiPlan {
   std::vector<SiLevel> levels;
@@ -268,9 +290,9 @@ struct SiPlan {
   LevelPair* d_pairs = nullptr;
 };
 
-int32_t add_gemm(SiPlan& pl, const GenGemm& g) {
-  // returns the number of tiles added
-  if (g.M <= 0 || g.N <= 0) return 0;
+double add_gemm(SiPlan& pl, const GenGemm& g) {
+  // returns the algorithmic flops added
+  if (g.M <= 0 || g.N <= 0) return 0.0;
   const int32_t d = (int32_t)pl.descs.size();
   pl.descs.push_back(g);
   int32_t cnt = 0;
@@ -280,7 +302,7 @@ int32_t add_gemm(SiPlan& pl, const GenGemm& g) {
       pl.tiles.push_back({d, ti, tj, 0});
       ++cnt;
     }
-  return cnt;
+  return gemm_flops(g);
 }
 
 int build_si_plan(chol_handle* h) {
@@ -290,7 +312,7 @@ int build_si_plan(chol_handle* h) {
   const double* L = D->L;
   double* Z = D->Zp;
   int64_t tmax = 0, hmax = 0, wmax = 0;
-  // per-level offsets of T (s^2), Uhat (b s) and W (s x 64)
+  // per-level offsets of T (s^2), Uhat (b s) and W (s^2 / 2)
   std::vector<int64_t> toff(h->ns), hoff(h->ns), woff(h->ns);
   for (const LevelPlan& P : h->levels) {
     int64_t t = 0, u = 0, w = 0;
@@ -300,7 +322,7 @@ int build_si_plan(chol_handle* h) {
       toff[J] = t; hoff[J] = u; woff[J] = w;
       t += (int64_t)d.s * d.s;
       u += (int64_t)(d.len - d.s) * d.s;
-      w += (int64_t)d.s * 64;
+      w += ((int64_t)d.s * d.s + 1) / 2;   // B A^{-1} of one doubling step: at most s^2 / 2
     }
     tmax = std::max(tmax, t); hmax = std::max(hmax, u); wmax = std::max(wmax, w);
   }
@@ -321,42 +343,48 @@ int build_si_plan(chol_handle* h) {
       tl += (int64_t)h->snodes[J].s * h->snodes[J].s;
     }
     sl.t_doubles = tl;
-    // T = L_JJ^{-1}: block columns right to left, step q handles block nbk-1-q
-    for (int q = 0; q < maxnbk; ++q) {
+    // T = L_JJ^{-1} by recursive doubling: first every 64 x 64 diagonal block
+    // is inverted (all at once), then blocks of size bs = 64, 128, ... are
+    // combined pairwise, [A 0; B C]^{-1} = [A^{-1} 0; -C^{-1} B A^{-1} C^{-1}],
+    // W = B A^{-1} then the off-diagonal block = -C^{-1} W, every pair of every
+    // supernode of the level in one launch per product
+    {
       SiStep st{};
       st.inv_b = (int32_t)pl->invs.size();
       for (int32_t J : Js) {
         const SnodeDev& d = h->snodes[J];
-        const int nbk = (d.s + 63) / 64;
-        if (q >= nbk) continue;
-        const int k0 = 64 * (nbk - 1 - q), kb = std::min(64, d.s - k0);
         double* T = D->Tw + toff[J];
-        pl->invs.push_back({L + d.loff + k0 + (int64_t)k0 * d.ld, d.ld, T + k0 + (int64_t)k0 * d.s, d.s, kb, 0});
+        for (int k0 = 0; k0 < d.s; k0 += 64) {
+          const int kb = std::min(64, d.s - k0);
+          pl->invs.push_back({L + d.loff + k0 + (int64_t)k0 * d.ld, d.ld, T + k0 + (int64_t)k0 * d.s, d.s, kb, 0});
+          st.flops += (double)kb * kb * kb / 3.0;
+        }
       }
       st.inv_n = (int32_t)pl->invs.size() - st.inv_b;
+      st.g1_b = st.g2_b = (int32_t)pl->tiles.size();
+      sl.steps.push_back(st);
+    }
+    for (int bs = 64; bs < maxnbk * 64; bs *= 2) {
+      SiStep st{};
+      st.inv_b = (int32_t)pl->invs.size();
+      std::vector<GenGemm> g2s;
       st.g1_b = (int32_t)pl->tiles.size();
       for (int32_t J : Js) {
         const SnodeDev& d = h->snodes[J];
-        const int nbk = (d.s + 63) / 64;
-        if (q >= nbk) continue;
-        const int k0 = 64 * (nbk - 1 - q), kb = std::min(64, d.s - k0), m = d.s - (k0 + kb);
-        if (m <= 0) continue;
         double* T = D->Tw + toff[J];
-        add_gemm(*pl, mk(T + (k0 + kb) + (int64_t)(k0 + kb) * d.s, 1, d.s, L + d.loff + (k0 + kb) + (int64_t)k0 * d.ld,
-                         1, d.ld, D->Ww + woff[J], 1, m, m, kb, m, 1.0, 0.0, 1, 0, 0));
+        double* Wp = D->Ww + woff[J];
+        for (int i0 = 0; i0 + bs < d.s; i0 += 2 * bs) {
+          const int c0 = i0 + bs, mc = std::min(c0 + bs, d.s) - c0;
+          st.flops += add_gemm(*pl, mk(L + d.loff + c0 + (int64_t)i0 * d.ld, 1, d.ld, T + i0 + (int64_t)i0 * d.s, 1, d.s,
+                                       Wp, 1, mc, mc, bs, bs, 1.0, 0.0, 0, 1, 0));
+          g2s.push_back(mk(T + c0 + (int64_t)c0 * d.s, 1, d.s, Wp, 1, mc, T + c0 + (int64_t)i0 * d.s, 1, d.s, mc, bs, mc,
+                           -1.0, 0.0, 1, 0, 0));
+          Wp += (int64_t)mc * bs;
+        }
       }
       st.g1_n = (int32_t)pl->tiles.size() - st.g1_b;
       st.g2_b = (int32_t)pl->tiles.size();
-      for (int32_t J : Js) {
-        const SnodeDev& d = h->snodes[J];
-        const int nbk = (d.s + 63) / 64;
-        if (q >= nbk) continue;
-        const int k0 = 64 * (nbk - 1 - q), kb = std::min(64, d.s - k0), m = d.s - (k0 + kb);
-        if (m <= 0) continue;
-        double* T = D->Tw + toff[J];
-        add_gemm(*pl, mk(D->Ww + woff[J], 1, m, T + k0 + (int64_t)k0 * d.s, 1, d.s, T + (k0 + kb) + (int64_t)k0 * d.s, 1,
-                         d.s, m, kb, kb, -1.0, 0.0, 0, 1, 0));
-      }
+      for (const GenGemm& g : g2s) st.flops += add_gemm(*pl, g);
       st.g2_n = (int32_t)pl->tiles.size() - st.g2_b;
       sl.steps.push_back(st);
     }
@@ -366,7 +394,7 @@ int build_si_plan(chol_handle* h) {
       const SnodeDev& d = h->snodes[J];
       const int b = d.len - d.s;
       if (b > 0)
-        add_gemm(*pl, mk(L + d.loff + d.s, 1, d.ld, D->Tw + toff[J], 1, d.s, D->Uh + hoff[J], 1, b, b, d.s, d.s, 1.0,
+        sl.gemm_flops += add_gemm(*pl, mk(L + d.loff + d.s, 1, d.ld, D->Tw + toff[J], 1, d.s, D->Uh + hoff[J], 1, b, b, d.s, d.s, 1.0,
                          0.0, 0, 1, 0));
     }
     sl.uh_n = (int32_t)pl->tiles.size() - sl.uh_b;
@@ -381,7 +409,7 @@ int build_si_plan(chol_handle* h) {
       const SnodeDev& d = h->snodes[J];
       const int b = d.len - d.s;
       if (b > 0)
-        add_gemm(*pl, mk(D->U + d.uoff, 1, b, D->Uh + hoff[J], 1, b, Z + d.loff + d.s, 1, d.ld, b, d.s, b, -1.0, 0.0, 2,
+        sl.gemm_flops += add_gemm(*pl, mk(D->U + d.uoff, 1, b, D->Uh + hoff[J], 1, b, Z + d.loff + d.s, 1, d.ld, b, d.s, b, -1.0, 0.0, 2,
                          0, 0));
     }
     sl.zrj_n = (int32_t)pl->tiles.size() - sl.zrj_b;
@@ -390,7 +418,7 @@ int build_si_plan(chol_handle* h) {
     for (int32_t J : Js) {
       const SnodeDev& d = h->snodes[J];
       double* T = D->Tw + toff[J];
-      add_gemm(*pl, mk(T, d.s, 1, T, 1, d.s, Z + d.loff, 1, d.ld, d.s, d.s, d.s, 1.0, 0.0, 0, 0, 1));
+      sl.gemm_flops += add_gemm(*pl, mk(T, d.s, 1, T, 1, d.s, Z + d.loff, 1, d.ld, d.s, d.s, d.s, 1.0, 0.0, 0, 0, 1));
     }
     sl.zjj1_n = (int32_t)pl->tiles.size() - sl.zjj1_b;
     sl.zjj2_b = (int32_t)pl->tiles.size();
@@ -398,7 +426,7 @@ int build_si_plan(chol_handle* h) {
       const SnodeDev& d = h->snodes[J];
       const int b = d.len - d.s;
       if (b > 0)
-        add_gemm(*pl, mk(D->Uh + hoff[J], b, 1, Z + d.loff + d.s, 1, d.ld, Z + d.loff, 1, d.ld, d.s, d.s, b, -1.0, 1.0, 0,
+        sl.gemm_flops += add_gemm(*pl, mk(D->Uh + hoff[J], b, 1, Z + d.loff + d.s, 1, d.ld, Z + d.loff, 1, d.ld, d.s, d.s, b, -1.0, 1.0, 0,
                          0, 1));
     }
     sl.zjj2_n = (int32_t)pl->tiles.size() - sl.zjj2_b;
@@ -437,17 +465,25 @@ int selinv(chol_handle* h, cudaStream_t st) {
   for (const SiLevel& sl : pl->levels) {
     CHOL_CUDA_TRY(cudaMemsetAsync(D->Tw, 0, sizeof(double) * (size_t)sl.t_doubles, st));
     for (const SiStep& q : sl.steps) {
+      KScope ks(h, CHOL_K_SELINV_INV, st, q.flops, 0.0);
+      ks.launches((q.inv_n > 0) + (q.g1_n > 0) + (q.g2_n > 0));
       if (q.inv_n > 0) k_inv64_grouped<<<q.inv_n, 64, 0, st>>>(pl->d_invs + q.inv_b);
       launch(q.g1_b, q.g1_n);
       launch(q.g2_b, q.g2_n);
     }
-    launch(sl.uh_b, sl.uh_n);
-    if (sl.pair_n > 0)
+    if (sl.pair_n > 0) {
+      KScope ks(h, CHOL_K_SELINV_GATHER, st, 0.0, 0.0);
       k_gather_zrr_level<<<sl.pair_n, kGT, sizeof(int32_t) * 2 * h->max_len, st>>>(pl->d_pairs + sl.pair_b, D->sn,
                                                                                    D->rows, D->Zp, D->U);
-    launch(sl.zrj_b, sl.zrj_n);
-    launch(sl.zjj1_b, sl.zjj1_n);
-    launch(sl.zjj2_b, sl.zjj2_n);
+    }
+    {
+      KScope ks(h, CHOL_K_SELINV_GEMM, st, sl.gemm_flops, 0.0);
+      ks.launches((sl.uh_n > 0) + (sl.zrj_n > 0) + (sl.zjj1_n > 0) + (sl.zjj2_n > 0));
+      launch(sl.uh_b, sl.uh_n);
+      launch(sl.zrj_b, sl.zrj_n);
+      launch(sl.zjj1_b, sl.zjj1_n);
+      launch(sl.zjj2_b, sl.zjj2_n);
+    }
   }
   CHOL_CUDA_TRY(cudaGetLastError());
   h->selinv_valid = true;
@@ -510,10 +546,12 @@ extern "C" int chol_adjoint(chol_handle* h, const double* w, const double* x, in
     if ((rc = chol_solve(h, xb, nrhs, (void*)st))) return rc;
   }
   if (logdet_weight != 0.0 && (rc = selinv(h, st))) return rc;
-  if (h->nnz_a > 0)
+  if (h->nnz_a > 0) {
+    KScope ks(h, CHOL_K_ADJOINT, st, 4.0 * nrhs * (double)h->nnz_a, 0.0);
     k_adj_grad<<<grid1d(h->nnz_a, 256), 256, 0, st>>>(D->a_row, D->a_col, D->amap,
                                                       logdet_weight != 0.0 ? D->Zp : nullptr, logdet_weight, xb, x,
                                                       h->n, nrhs, h->nnz_a, grad);
+  }
   CHOL_CUDA_TRY(cudaGetLastError());
   return CHOL_OK;
 }

@@ -28,6 +28,7 @@
 #include "device.h"
 #include "mixed.h"
 #include "assemble.cuh"
+#include "potrf.cuh"
 
 namespace cg = cooperative_groups;
 
@@ -110,85 +111,18 @@ k_small(const SnodeDev* __restrict__ sn, const int32_t* __restrict__ list, doubl
 }
 
 // Blocked path, step k0: factor the kb x kb (kb <= 64) diagonal block of each
-// listed supernode. Register-blocked right-looking Cholesky: 256 threads in a
-// 16 x 16 grid, thread (tx, ty) holds entries (ty + 16a, tx + 16b), a, b < 4;
-// per column k the scaled column goes through shared memory and every thread
-// applies the rank-1 update to its own entries.
-constexpr int kPotrfThreads = 256;
+// listed supernode (packed right-looking Cholesky, potrf.cuh).
+constexpr int kPotrfThreads = kPkThreads;
 __global__ void __launch_bounds__(kPotrfThreads)
 k_potrf(const SnodeDev* __restrict__ sn, const int32_t* __restrict__ list, int k0, int nb,
         double* __restrict__ L, int* status) {
   __shared__ double colk[64];
-  __shared__ double sdiag;
+  __shared__ double sinv;
   const SnodeDev d = sn[list[blockIdx.x]];
   const int kb = min(nb, d.s - k0);
   double* G = L + d.loff + k0 + (int64_t)k0 * d.ld;
-  const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
-  double v[4][4];
-#pragma unroll
-  for (int a = 0; a < 4; ++a)
-#pragma unroll
-    for (int b = 0; b < 4; ++b) {
-      const int r = ty + 16 * a, c = tx + 16 * b;
-      v[a][b] = (r < kb && c < kb && r >= c) ? G[r + (int64_t)c * d.ld] : 0.0;
-    }
-#pragma unroll 1
-  for (int kk = 0; kk < 4; ++kk) {
-#pragma unroll
-    for (int k1 = 0; k1 < 16; ++k1) {
-      const int k = kk * 16 + k1;
-      if (k >= kb) break;
-      // pivot: held by thread (tx, ty) = (k1, k1) in slot (kk, kk)
-      if (tx == k1 && ty == k1) {
-        double dv = 0.0;
-#pragma unroll
-        for (int a = 0; a < 4; ++a)
-          if (a == kk) {
-#pragma unroll
-            for (int b = 0; b < 4; ++b)
-              if (b == kk) dv = v[a][b];
-          }
-        const bool bad = !(dv > 0.0);
-        const double dk = bad ? __longlong_as_double(0x7ff8000000000000LL) : sqrt(dv);
-        if (bad) atomicMin(status, d.f + k0 + k + 1);
-        sdiag = dk;
-      }
-      __syncthreads();
-      const double dk = sdiag;
-      const double inv = 1.0 / dk;
-      if (tx == k1) {   // column k lives in slot b = kk of these threads
-#pragma unroll
-        for (int a = 0; a < 4; ++a) {
-          const int r = ty + 16 * a;
-#pragma unroll
-          for (int b = 0; b < 4; ++b)
-            if (b == kk) {
-              if (r > k) { v[a][b] *= inv; colk[r] = v[a][b]; }
-              else if (r == k) v[a][b] = dk;
-            }
-        }
-      }
-      __syncthreads();
-#pragma unroll
-      for (int a = 0; a < 4; ++a) {
-        const int r = ty + 16 * a;
-        if (r <= k || r >= kb) continue;
-        const double lr = colk[r];
-#pragma unroll
-        for (int b = 0; b < 4; ++b) {
-          const int c = tx + 16 * b;
-          if (c > k && c <= r) v[a][b] -= lr * colk[c];
-        }
-      }
-    }
-  }
-#pragma unroll
-  for (int a = 0; a < 4; ++a)
-#pragma unroll
-    for (int b = 0; b < 4; ++b) {
-      const int r = ty + 16 * a, c = tx + 16 * b;
-      if (r < kb && c < kb && r >= c) G[r + (int64_t)c * d.ld] = v[a][b];
-    }
+  potrf_block<double, false, double>(G, d.ld, kb, 0.0, nullptr, nullptr, status, true, d.f + k0, colk, &sinv,
+                                     -INFINITY);
 }
 
 // Blocked path, step k0: rows [r0, r0+32) of column block [k0, k0+kb) become

@@ -23,6 +23,7 @@
 #include "device.h"
 #include "mixed.h"
 #include "assemble.cuh"
+#include "potrf.cuh"
 
 namespace cg = cooperative_groups;
 
@@ -111,118 +112,32 @@ k_mx_small(const SnodeDev* __restrict__ sn, const int32_t* __restrict__ list, fl
   mx_small_body(sn[list[blockIdx.x]], L, U, status, spiv, counters, Pf);
 }
 
-// Register-blocked Cholesky of a kb x kb (kb <= 64) row-major block, 256
-// threads, thread (tx, ty) holding (ty + 16a, tx + 16b). Returns through
-// *minpiv the smallest pivot seen before its square root.
-template <class T>
-__device__ void potrf_block_regs(const float* __restrict__ G, int64_t ld, int kb, T (&v)[4][4], T* colk,
-                                 T* sdiag, float* sminpiv, int tx, int ty, int fcol, int* status,
-                                 bool record, T spiv, int* nperturbed) {
-#pragma unroll
-  for (int a = 0; a < 4; ++a)
-#pragma unroll
-    for (int b = 0; b < 4; ++b) {
-      const int r = ty + 16 * a, c = tx + 16 * b;
-      v[a][b] = (r < kb && c < kb && r >= c) ? T(G[r * ld + c]) : T(0);
-    }
-#pragma unroll 1
-  for (int kk = 0; kk < 4; ++kk) {
-#pragma unroll
-    for (int k1 = 0; k1 < 16; ++k1) {
-      const int k = kk * 16 + k1;
-      if (k >= kb) break;
-      if (tx == k1 && ty == k1) {
-        T dv = T(0);
-#pragma unroll
-        for (int a = 0; a < 4; ++a)
-          if (a == kk) {
-#pragma unroll
-            for (int b = 0; b < 4; ++b)
-              if (b == kk) dv = v[a][b];
-          }
-        if (spiv > T(0) && !(dv >= spiv)) {   // static pivoting: max(|d|, tau)
-          dv = fabs(dv) >= spiv ? T(fabs(dv)) : spiv;
-          atomicAdd(nperturbed, 1);
-        }
-        const bool bad = !(dv > T(0));
-        if ((float)dv < *sminpiv || bad) *sminpiv = bad ? -1.f : (float)dv;
-        *sdiag = bad ? T(__longlong_as_double(0x7ff8000000000000LL)) : sqrt(dv);
-        if (bad && record) atomicMin(status, fcol + k + 1);
-      }
-      __syncthreads();
-      const T dk = *sdiag;
-      const T inv = T(1) / dk;
-      if (tx == k1) {
-#pragma unroll
-        for (int a = 0; a < 4; ++a) {
-          const int r = ty + 16 * a;
-#pragma unroll
-          for (int b = 0; b < 4; ++b)
-            if (b == kk) {
-              if (r > k) { v[a][b] *= inv; colk[r] = v[a][b]; }
-              else if (r == k) v[a][b] = dk;
-            }
-        }
-      }
-      __syncthreads();
-#pragma unroll
-      for (int a = 0; a < 4; ++a) {
-        const int r = ty + 16 * a;
-        if (r <= k || r >= kb) continue;
-        const T lr = colk[r];
-#pragma unroll
-        for (int b = 0; b < 4; ++b) {
-          const int c = tx + 16 * b;
-          if (c > k && c <= r) v[a][b] -= lr * colk[c];
-        }
-      }
-    }
-  }
-  __syncthreads();
-}
-
-// Blocked path, step k0: diagonal block in binary32; redone in binary64 when a
+// Blocked path, step k0: diagonal block in binary32 (packed right-looking
+// Cholesky, potrf.cuh); redone in binary64 from the unmodified block when a
 // binary32 pivot (before its square root) falls below tau.
-__global__ void __launch_bounds__(256)
+__global__ void __launch_bounds__(kPkThreads)
 k_mx_potrf(const SnodeDev* __restrict__ sn, const int32_t* __restrict__ list, int k0, int nb, float tau,
            int static_pivot, float* __restrict__ L, int* status, int* counters) {
   __shared__ double colk_d[64];
   __shared__ float colk_f[64];
-  __shared__ double sdiag_d;
-  __shared__ float sdiag_f;
+  __shared__ double sinv_d;
+  __shared__ float sinv_f;
   __shared__ float sminpiv;
   const SnodeDev d = sn[list[blockIdx.x]];
   const int kb = min(nb, d.s - k0);
   float* G = L + d.loff + (int64_t)k0 * d.ld + k0;
-  const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
   if (threadIdx.x == 0) sminpiv = 3.0e38f;
   __syncthreads();
-  float vf[4][4];
-  potrf_block_regs<float>(G, d.ld, kb, vf, colk_f, &sdiag_f, &sminpiv, tx, ty, d.f + k0, status, false, 0.f,
-                          counters + 1);
-  if (!(sminpiv >= tau)) {
-    // binary64 redo from the (still unmodified) block in global memory
-    __syncthreads();
+  if (!potrf_block<float, true, float>(G, d.ld, kb, 0.f, counters + 1, &sminpiv, status, false, d.f + k0, colk_f,
+                                       &sinv_f, tau)) {
     if (threadIdx.x == 0) {
       sminpiv = 3.0e38f;
       atomicAdd(counters, 1);
     }
     __syncthreads();
-    double vd[4][4];
-    potrf_block_regs<double>(G, d.ld, kb, vd, colk_d, &sdiag_d, &sminpiv, tx, ty, d.f + k0, status, true,
-                             static_pivot ? (double)tau : 0.0, counters + 1);
-#pragma unroll
-    for (int a = 0; a < 4; ++a)
-#pragma unroll
-      for (int b = 0; b < 4; ++b) vf[a][b] = (float)vd[a][b];
+    potrf_block<double, true, float>(G, d.ld, kb, static_pivot ? (double)tau : 0.0, counters + 1, nullptr, status,
+                                     true, d.f + k0, colk_d, &sinv_d, -INFINITY);
   }
-#pragma unroll
-  for (int a = 0; a < 4; ++a)
-#pragma unroll
-    for (int b = 0; b < 4; ++b) {
-      const int r = ty + 16 * a, c = tx + 16 * b;
-      if (r < kb && c < kb && r >= c) G[(int64_t)r * d.ld + c] = vf[a][b];
-    }
 }
 
 // Blocked path, step k0: rows [r0, r0+32) of the column block become

@@ -1,0 +1,111 @@
+// potrf.cuh -- Cholesky of one kb x kb (kb <= 64) diagonal block in one CTA of
+// 256 threads (the diagonal POTRF of a column step of the blocked path, Sec.
+// II-A).
+//
+// The lower triangle is enumerated column by column, e = off(c) + (r - c) with
+// off(c) = c kb - c (c - 1) / 2, and entry e lives in register slot e / 256 of
+// thread e % 256. Right-looking, one column per step: the owner of (k, k) takes
+// the square root, the owners of column k scale it into shared memory, and the
+// owners of every later column subtract the rank-1 term. The entries still
+// being updated at step k are exactly those with e >= off(k + 1), a suffix of
+// the enumeration, so whole warps drop out as the factorization advances and
+// no arithmetic instruction is issued for finished entries. That matters most
+// for binary64, where a warp-wide DFMA occupies the FP64 pipe for many cycles
+// whether or not its lanes are active.
+#pragma once
+#include <cstdint>
+
+constexpr int kPkThreads = 256;
+constexpr int kPkSlots = 9;   // ceil(64 * 65 / 2 / 256)
+
+__device__ __forceinline__ int pk_off(int c, int kb) { return c * kb - (c * (c - 1)) / 2; }
+
+// (r, c) of entry e of the packed lower triangle of a kb x kb block.
+__device__ __forceinline__ void pk_coord(int e, int kb, int& r, int& c) {
+  const float fk = (float)kb + 0.5f;
+  int cc = (int)(fk - sqrtf(fmaxf(fk * fk - 2.0f * (float)e, 0.0f)));
+  cc = max(0, min(cc, kb - 1));
+  while (cc > 0 && pk_off(cc, kb) > e) --cc;
+  while (cc + 1 < kb && pk_off(cc + 1, kb) <= e) ++cc;
+  c = cc;
+  r = cc + (e - pk_off(cc, kb));
+}
+
+// Factor the block at G (row-major with leading dimension ld if RM, else
+// column-major) in arithmetic T, reading and writing the storage type GT.
+//   spiv       > 0: static pivoting, a pivot below spiv becomes max(|d|, spiv)
+//              (counted in *nperturbed)
+//   sminpiv    shared, receives the smallest pivot seen (-1 for a non-positive
+//              or NaN one); may be null
+//   status     when `record`, a non-positive or NaN pivot records column
+//              fcol + k + 1 (smallest wins) and the column becomes NaN
+//   colk, sinv shared scratch: 64 entries and one
+//   accept     the factor is stored back to G unless a pivot (before its
+//              square root) fell below this value (needs sminpiv); the
+//              return value, uniform across the CTA, says whether it was
+template <class T, bool RM, class GT>
+__device__ bool potrf_block(GT* __restrict__ G, int64_t ld, int kb, T spiv, int* nperturbed, float* sminpiv,
+                            int* status, bool record, int fcol, T* colk, T* sinv, float accept) {
+  const int tid = threadIdx.x;
+  const int E = kb * (kb + 1) / 2;
+  T v[kPkSlots];
+  int rr[kPkSlots], cc[kPkSlots];
+#pragma unroll
+  for (int q = 0; q < kPkSlots; ++q) {
+    const int e = tid + kPkThreads * q;
+    if (e < E) {
+      pk_coord(e, kb, rr[q], cc[q]);
+      v[q] = (T)(RM ? G[(int64_t)rr[q] * ld + cc[q]] : G[rr[q] + (int64_t)cc[q] * ld]);
+    } else {
+      rr[q] = 0;
+      cc[q] = -1;   // never in a column that is scaled or updated
+      v[q] = T(0);
+    }
+  }
+  for (int k = 0; k < kb; ++k) {
+    const int ek = pk_off(k, kb);
+    if (tid == (ek & (kPkThreads - 1))) {
+      const int qk = ek / kPkThreads;
+      T dv = T(0);
+#pragma unroll
+      for (int q = 0; q < kPkSlots; ++q)
+        if (q == qk) dv = v[q];
+      if (spiv > T(0) && !(dv >= spiv)) {
+        dv = fabs(dv) >= spiv ? T(fabs(dv)) : spiv;
+        atomicAdd(nperturbed, 1);
+      }
+      const bool bad = !(dv > T(0));
+      if (sminpiv && ((float)dv < *sminpiv || bad)) *sminpiv = bad ? -1.f : (float)dv;
+      if (bad && record) atomicMin(status, fcol + k + 1);
+      const T dk = bad ? T(__longlong_as_double(0x7ff8000000000000LL)) : sqrt(dv);
+#pragma unroll
+      for (int q = 0; q < kPkSlots; ++q)
+        if (q == qk) v[q] = dk;
+      *sinv = T(1) / dk;
+    }
+    __syncthreads();
+    const T inv = *sinv;
+#pragma unroll
+    for (int q = 0; q < kPkSlots; ++q)
+      if (cc[q] == k && rr[q] > k) {
+        v[q] *= inv;
+        colk[rr[q]] = v[q];
+      }
+    __syncthreads();
+    const int act = pk_off(k + 1, kb);   // entries e >= act are still being updated
+#pragma unroll
+    for (int q = 0; q < kPkSlots; ++q)
+      if (tid + kPkThreads * q >= act && tid + kPkThreads * q < E) v[q] -= colk[rr[q]] * colk[cc[q]];
+  }
+  __syncthreads();
+  const bool ok = !(sminpiv && !(*sminpiv >= accept));
+  if (ok) {
+#pragma unroll
+    for (int q = 0; q < kPkSlots; ++q)
+      if (tid + kPkThreads * q < E) {
+        if (RM) G[(int64_t)rr[q] * ld + cc[q]] = (GT)v[q];
+        else G[rr[q] + (int64_t)cc[q] * ld] = (GT)v[q];
+      }
+  }
+  return ok;
+}

@@ -155,3 +155,45 @@ def test_relaxed_merging_parity(merge):
     got, _ = check_parity(p, b, _opts(merge=merge), L_tol=1e-6, x_tol=1e-6)
     assert got["info"].nsuper_storage < got["info"].nsuper
     check_parity(gridgen.workload("2d64"), gridgen.rhs_uniform(4096, 2, seed=1), _opts(merge=merge, nb=32))
+
+
+@pytest.mark.parametrize("nrhs", [5, 11, 17])
+def test_solve_rhs_counts_and_chunks(nrhs):
+    # 5 and 11: partial right-hand-side groups inside one chunk; 17: two chunks
+    # (16 + 1). Forced blocked kernels give diagonal triangles of several 64-row
+    # blocks, so the flag-ordered triangle solve runs with many blocks per level.
+    p = gridgen.laplacian_neumann_varcoef((16, 15, 14), 1e-2, 1e2, 1e-3, seed=9)
+    b = gridgen.rhs_normal(p.n, nrhs, seed=nrhs)
+    check_parity(p, b, _opts(2, 64, 64, merge=0.2), L_tol=1e-8, x_tol=1e-8)
+
+
+def test_solve_replays_from_a_cuda_graph():
+    # the triangle launches keep their flag epoch on the device, so a captured
+    # solve replays correctly with new right-hand sides
+    import torch
+    from gpu_util import colmajor, to_dev
+    P = chol()
+    p = gridgen.laplacian_neumann_varcoef((14, 14, 14), 1e-2, 1e2, 1e-3, seed=10)
+    rc, h = P.chol_analyze(p.n, p["colptr"], p["rowind"], p["perm"], _opts(2, 64, 64))
+    assert rc == 0
+    try:
+        st = torch.cuda.Stream()
+        with torch.cuda.stream(st):
+            vals = to_dev(p["values"])
+            assert P.chol_factor(h, vals, st) == 0
+            X = colmajor(gridgen.rhs_uniform(p.n, 2, seed=1))
+            assert P.chol_solve(h, X, 2, st) == 0       # workspaces exist before capture
+        st.synchronize()
+        g = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(g, stream=st):
+            assert P.chol_solve(h, X, 2, st) == 0
+        for seed in (2, 3, 4):
+            b = gridgen.rhs_uniform(p.n, 2, seed=seed)
+            X.copy_(colmajor(b))
+            g.replay()
+            torch.cuda.synchronize()
+            x = X.cpu().numpy()
+            ref = oracle.reference(p, b)
+            assert np.max(np.abs(x - ref["x"])) <= 1e-8 * np.max(np.abs(ref["x"]))
+    finally:
+        P.chol_destroy(h)
