@@ -41,15 +41,18 @@ struct GenGemm {
   int M, N, K;
   double alpha, beta;
   int amode, bmode, lower_c;
+  int ksplit, kchunk;   // K split over ksplit CTAs of kchunk (a multiple of 16) each
+  int64_t part;         // split: first partial tile of this product in the workspace
 };
 
 // Grouped form: one CTA per (descriptor, tile i, tile j) entry of a task list,
 // so the GEMMs of every supernode of a level run in one launch.
 struct GemmTile {
-  int32_t desc, ti, tj, pad;
+  int32_t desc, ti, tj, kc;   // product, output tile, K chunk
 };
 
-__device__ __forceinline__ void gen_gemm_tile(const GenGemm& g, int i0, int j0) {
+__device__ __forceinline__ void gen_gemm_tile(const GenGemm& g, int i0, int j0, int kc, double* __restrict__ part_ws,
+                                              int64_t tile_idx) {
   constexpr int KC = 16;
   __shared__ double As[KC][kGTile + 1];
   __shared__ double Bs[KC][kGTile + 1];
@@ -57,6 +60,10 @@ __device__ __forceinline__ void gen_gemm_tile(const GenGemm& g, int i0, int j0) 
   int kbeg = 0, kend = g.K;
   if (g.amode == 1) kend = min(kend, i0 + kGTile);
   if (g.bmode == 1) kbeg = (j0 / KC) * KC;
+  if (g.ksplit > 1) {
+    kbeg = max(kbeg, kc * g.kchunk);
+    kend = min(kend, (kc + 1) * g.kchunk);
+  }
   double acc[4][4] = {};
   // the thread -> element map of each operand follows its contiguous index
   const bool bkf = g.br == 1 && g.bc != 1;
@@ -71,7 +78,7 @@ __device__ __forceinline__ void gen_gemm_tile(const GenGemm& g, int i0, int j0) 
         const int kk = akf ? (idx & 15) : (idx >> 6), r = akf ? (idx >> 4) : (idx & 63);
         const int kg = k + kk, ia = i0 + r;
         double av = 0.0;
-        if (kg < g.K && ia < g.M) {
+        if (kg < kend && ia < g.M) {
           if (g.amode == 0 || (g.amode == 1 && kg <= ia)) av = g.A[ia * g.ar + kg * g.ac];
           else if (g.amode == 2) av = kg <= ia ? g.A[ia * g.ar + kg * g.ac] : g.A[kg * g.ar + ia * g.ac];
         }
@@ -81,7 +88,7 @@ __device__ __forceinline__ void gen_gemm_tile(const GenGemm& g, int i0, int j0) 
         const int kk = bkf ? (idx & 15) : (idx >> 6), r = bkf ? (idx >> 4) : (idx & 63);
         const int kg = k + kk, jb = j0 + r;
         double bv = 0.0;
-        if (kg < g.K && jb < g.N && (g.bmode == 0 || jb <= kg)) bv = g.B[kg * g.br + jb * g.bc];
+        if (kg < kend && jb < g.N && (g.bmode == 0 || jb <= kg)) bv = g.B[kg * g.br + jb * g.bc];
         Bs[kk][r] = bv;
       }
     }
@@ -100,6 +107,15 @@ __device__ __forceinline__ void gen_gemm_tile(const GenGemm& g, int i0, int j0) 
     }
     __syncthreads();
   }
+  if (g.ksplit > 1) {
+    // partial tile (row-major 64 x 64), summed by k_gen_reduce
+    double* pp = part_ws + g.part + (tile_idx * g.ksplit + kc) * (kGTile * kGTile);
+#pragma unroll
+    for (int i = 0; i < 4; ++i)
+#pragma unroll
+      for (int j = 0; j < 4; ++j) pp[(ty + 16 * i) * kGTile + tx + 16 * j] = acc[i][j];
+    return;
+  }
 #pragma unroll
   for (int i = 0; i < 4; ++i)
 #pragma unroll
@@ -112,11 +128,32 @@ __device__ __forceinline__ void gen_gemm_tile(const GenGemm& g, int i0, int j0) 
     }
 }
 
-__global__ void __launch_bounds__(kGT)
-k_gen_gemm_grouped(const GenGemm* __restrict__ descs, const GemmTile* __restrict__ tiles) {
+__global__ void __launch_bounds__(kGT, 3)
+k_gen_gemm_grouped(const GenGemm* __restrict__ descs, const GemmTile* __restrict__ tiles,
+                   double* __restrict__ part_ws) {
   const GemmTile t = tiles[blockIdx.x];
   const GenGemm g = descs[t.desc];
-  gen_gemm_tile(g, t.ti * kGTile, t.tj * kGTile);
+  const int64_t ntj = (g.N + kGTile - 1) / kGTile;
+  gen_gemm_tile(g, t.ti * kGTile, t.tj * kGTile, t.kc, part_ws, t.ti * ntj + t.tj);
+}
+
+// Split products: C = beta C + alpha sum_kc partial(kc), the partials added in
+// chunk order (deterministic); one CTA per output tile.
+__global__ void __launch_bounds__(kGT)
+k_gen_reduce(const GenGemm* __restrict__ descs, const GemmTile* __restrict__ tiles,
+             const double* __restrict__ part_ws) {
+  const GemmTile t = tiles[blockIdx.x];
+  const GenGemm g = descs[t.desc];
+  const int64_t ntj = (g.N + kGTile - 1) / kGTile;
+  const double* pp = part_ws + g.part + (t.ti * ntj + t.tj) * g.ksplit * (kGTile * kGTile);
+  for (int e = threadIdx.x; e < kGTile * kGTile; e += kGT) {
+    const int r = t.ti * kGTile + e / kGTile, c = t.tj * kGTile + e % kGTile;
+    if (r >= g.M || c >= g.N || (g.lower_c && r < c)) continue;
+    double acc = 0.0;
+    for (int kc = 0; kc < g.ksplit; ++kc) acc += pp[(int64_t)kc * (kGTile * kGTile) + e];
+    double* p = g.C + r * g.cr + c * g.cc;
+    *p = (g.beta == 0.0 ? 0.0 : g.beta * *p) + g.alpha * acc;
+  }
 }
 
 struct InvTask {
@@ -156,14 +193,20 @@ __global__ void k_inv64_grouped(const InvTask* __restrict__ tasks) {
   inv64_body(t.src, t.lds, t.kb, t.dst, t.ldt);
 }
 
+// One gather task: the part of pair (J, K) with J's off-diagonal rows
+// u in [u0, u1) (at most kGatherRows of them).
 struct LevelPair {
-  int32_t J, K, c0, c1;
+  int32_t J, K, c0, c1, u0, u1;
 };
+constexpr int kGatherRows = 512;
+constexpr int kGatherUnroll = 4;
 
 // Z_RR of every supernode J of a level (lower, column-major b x b, stored in the
-// update workspace at U_J's place), gathered from the ancestors' Z panels: one
-// block per (J, K) pair, the positions of J's rows in struct(K) found by binary
-// search in shared memory.
+// update workspace at U_J's place), gathered from the ancestors' Z panels. A
+// task covers columns [c0, c1) of J's pair with K and a chunk of rows: it
+// stages struct(K) in shared memory, finds the positions of its rows by binary
+// search, then a warp per column copies 32 rows at a time, kGatherUnroll
+// (column, row chunk) items in flight per warp. Tasks write disjoint entries.
 __global__ void __launch_bounds__(kGT)
 k_gather_zrr_level(const LevelPair* __restrict__ pairs, const SnodeDev* __restrict__ sn,
                    const int32_t* __restrict__ rows, const double* __restrict__ Z, double* __restrict__ U) {
@@ -179,20 +222,41 @@ k_gather_zrr_level(const LevelPair* __restrict__ pairs, const SnodeDev* __restri
   const int32_t* rj = rows + dj.roff + dj.s;
   for (int i = threadIdx.x; i < dk.len; i += blockDim.x) sK[i] = rk[i];
   __syncthreads();
-  for (int u = pr.c0 + threadIdx.x; u < b; u += blockDim.x) {
-    const int32_t key = rj[u];
+  const int nu = pr.u1 - pr.u0;
+  for (int i = threadIdx.x; i < nu; i += blockDim.x) {
+    const int32_t key = rj[pr.u0 + i];
     int lo = 0, hi = dk.len;
     while (lo < hi) {
       const int mid = (lo + hi) >> 1;
       if (sK[mid] < key) lo = mid + 1; else hi = mid;
     }
-    pos[u - pr.c0] = lo;
+    pos[i] = lo;
   }
   __syncthreads();
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  for (int c = pr.c0 + warp; c < pr.c1; c += kGT / 32) {
-    const double* Zc = Z + dk.loff + (int64_t)(rj[c] - dk.f) * dk.ld;
-    for (int u = c + lane; u < b; u += 32) ZRR[u + (int64_t)c * b] = Zc[pos[u - pr.c0]];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = kGT / 32;
+  const int nch = (nu + 31) >> 5, w = pr.c1 - pr.c0;
+  const int items = w * nch;
+  for (int i0 = warp; i0 < items; i0 += nw * kGatherUnroll) {
+    double v[kGatherUnroll];
+    int64_t dst[kGatherUnroll];
+#pragma unroll
+    for (int q = 0; q < kGatherUnroll; ++q) {
+      const int i = i0 + q * nw;
+      dst[q] = -1;
+      if (i < items) {
+        const int cc = i / nch;
+        const int c = pr.c0 + cc;
+        const int ui = (i - cc * nch) * 32 + lane;
+        const int u = pr.u0 + ui;
+        if (ui < nu && u >= c) {
+          v[q] = Z[dk.loff + (int64_t)(rj[c] - dk.f) * dk.ld + pos[ui]];
+          dst[q] = u + (int64_t)c * b;
+        }
+      }
+    }
+#pragma unroll
+    for (int q = 0; q < kGatherUnroll; ++q)
+      if (dst[q] >= 0) ZRR[dst[q]] = v[q];
   }
 }
 
@@ -230,6 +294,7 @@ GenGemm mk(const double* A, int64_t ar, int64_t ac, const double* B, int64_t br,
   GenGemm g;
   g.A = A; g.ar = ar; g.ac = ac; g.B = B; g.br = br; g.bc = bc; g.C = C; g.cr = cr; g.cc = cc;
   g.M = M; g.N = N; g.K = K; g.alpha = alpha; g.beta = beta; g.amode = amode; g.bmode = bmode; g.lower_c = lower;
+  g.ksplit = 1; g.kchunk = K; g.part = 0;
   return g;
 }
 
@@ -257,14 +322,21 @@ int ensure_adjoint(chol_handle* h) {
 }
 
 // Level plan of the selected inverse (built once, on first use).
+// Products launched together: their tiles (incl. K chunks) and, for the split
+// ones, the output tiles of the reduction.
+struct Group {
+  int32_t tb = 0, tn = 0, rb = 0, rn = 0;
+  double flops = 0.0;
+};
 struct SiStep {
-  int32_t inv_b, inv_n, g1_b, g1_n, g2_b, g2_n;
+  int32_t inv_b, inv_n;
+  Group g1, g2;
   double flops;                         // algorithmic flops of the step
 };
 struct SiLevel {
   int64_t t_doubles;                    // T workspace of the level (zeroed first)
   std::vector<SiStep> steps;            // the L_JJ^{-1} recurrence, batched
-  int32_t uh_b, uh_n, zrj_b, zrj_n, zjj1_b, zjj1_n, zjj2_b, zjj2_n;
+  Group uh, zrj, zjj1, zjj2;
   int32_t pair_b, pair_n;
   double gemm_flops;                    // Uhat, Z_RJ and Z_JJ products
 };
@@ -281,28 +353,66 @@ double gemm_flops(const GenGemm& g) {
 struct SiPlan {
   std::vector<SiLevel> levels;
   std::vector<GenGemm> descs;
-  std::vector<GemmTile> tiles;
+  std::vector<GemmTile> tiles, rtiles;
   std::vector<InvTask> invs;
   std::vector<LevelPair> pairs;
+  int64_t part_max = 0;                 // partial-tile workspace (doubles)
   GenGemm* d_descs = nullptr;
   GemmTile* d_tiles = nullptr;
+  GemmTile* d_rtiles = nullptr;
   InvTask* d_invs = nullptr;
   LevelPair* d_pairs = nullptr;
+  double* d_part = nullptr;
 };
 
-double add_gemm(SiPlan& pl, const GenGemm& g) {
-  // returns the algorithmic flops added
-  if (g.M <= 0 || g.N <= 0) return 0.0;
-  const int32_t d = (int32_t)pl.descs.size();
-  pl.descs.push_back(g);
-  int32_t cnt = 0;
-  for (int ti = 0; ti * kGTile < g.M; ++ti)
-    for (int tj = 0; tj * kGTile < g.N; ++tj) {
-      if (g.lower_c && ti * kGTile + kGTile - 1 < tj * kGTile) continue;
-      pl.tiles.push_back({d, ti, tj, 0});
-      ++cnt;
+// Emit the tiles of products launched together. When the group has fewer
+// than two output tiles per SM, products with K > 256 are split over up to
+// ceil(2 SMs / tiles) K chunks (of at least 128): each chunk writes a partial
+// tile to the workspace and a second launch adds them in chunk order.
+Group emit_group(SiPlan& pl, const std::vector<GenGemm>& gs, int sms) {
+  Group gr;
+  gr.tb = (int32_t)pl.tiles.size();
+  gr.rb = (int32_t)pl.rtiles.size();
+  auto out_tiles = [](const GenGemm& g) {
+    int64_t n = 0;
+    for (int ti = 0; ti * kGTile < g.M; ++ti)
+      for (int tj = 0; tj * kGTile < g.N; ++tj)
+        if (!g.lower_c || ti * kGTile + kGTile - 1 >= tj * kGTile) ++n;
+    return n;
+  };
+  int64_t nt = 0;
+  for (const GenGemm& g : gs)
+    if (g.M > 0 && g.N > 0) nt += out_tiles(g);
+  const int64_t target = 2 * (int64_t)sms;
+  int64_t part = 0;
+  for (GenGemm g : gs) {
+    if (g.M <= 0 || g.N <= 0) continue;
+    gr.flops += gemm_flops(g);
+    int ks = 1;
+    if (nt > 0 && nt < target && g.K > 256)
+      ks = (int)std::min<int64_t>((g.K + 127) / 128, (target + nt - 1) / nt);
+    if (ks > 1) {
+      g.kchunk = (((g.K + ks - 1) / ks) + 15) / 16 * 16;
+      ks = (g.K + g.kchunk - 1) / g.kchunk;
     }
-  return gemm_flops(g);
+    g.ksplit = ks;
+    if (ks == 1) g.kchunk = g.K;
+    g.part = part;
+    const int32_t d = (int32_t)pl.descs.size();
+    pl.descs.push_back(g);
+    const int ntj = (g.N + kGTile - 1) / kGTile;
+    for (int ti = 0; ti * kGTile < g.M; ++ti)
+      for (int tj = 0; tj < ntj; ++tj) {
+        if (g.lower_c && ti * kGTile + kGTile - 1 < tj * kGTile) continue;
+        for (int kc = 0; kc < ks; ++kc) pl.tiles.push_back({d, ti, tj, kc});
+        if (ks > 1) pl.rtiles.push_back({d, ti, tj, 0});
+      }
+    if (ks > 1) part += (int64_t)((g.M + kGTile - 1) / kGTile) * ntj * ks * kGTile * kGTile;
+  }
+  gr.tn = (int32_t)pl.tiles.size() - gr.tb;
+  gr.rn = (int32_t)pl.rtiles.size() - gr.rb;
+  pl.part_max = std::max(pl.part_max, part);
+  return gr;
 }
 
 int build_si_plan(chol_handle* h) {
@@ -361,75 +471,80 @@ int build_si_plan(chol_handle* h) {
         }
       }
       st.inv_n = (int32_t)pl->invs.size() - st.inv_b;
-      st.g1_b = st.g2_b = (int32_t)pl->tiles.size();
       sl.steps.push_back(st);
     }
     for (int bs = 64; bs < maxnbk * 64; bs *= 2) {
       SiStep st{};
       st.inv_b = (int32_t)pl->invs.size();
-      std::vector<GenGemm> g2s;
-      st.g1_b = (int32_t)pl->tiles.size();
+      std::vector<GenGemm> g1s, g2s;
       for (int32_t J : Js) {
         const SnodeDev& d = h->snodes[J];
         double* T = D->Tw + toff[J];
         double* Wp = D->Ww + woff[J];
         for (int i0 = 0; i0 + bs < d.s; i0 += 2 * bs) {
           const int c0 = i0 + bs, mc = std::min(c0 + bs, d.s) - c0;
-          st.flops += add_gemm(*pl, mk(L + d.loff + c0 + (int64_t)i0 * d.ld, 1, d.ld, T + i0 + (int64_t)i0 * d.s, 1, d.s,
-                                       Wp, 1, mc, mc, bs, bs, 1.0, 0.0, 0, 1, 0));
+          g1s.push_back(mk(L + d.loff + c0 + (int64_t)i0 * d.ld, 1, d.ld, T + i0 + (int64_t)i0 * d.s, 1, d.s, Wp, 1, mc,
+                           mc, bs, bs, 1.0, 0.0, 0, 1, 0));
           g2s.push_back(mk(T + c0 + (int64_t)c0 * d.s, 1, d.s, Wp, 1, mc, T + c0 + (int64_t)i0 * d.s, 1, d.s, mc, bs, mc,
                            -1.0, 0.0, 1, 0, 0));
           Wp += (int64_t)mc * bs;
         }
       }
-      st.g1_n = (int32_t)pl->tiles.size() - st.g1_b;
-      st.g2_b = (int32_t)pl->tiles.size();
-      for (const GenGemm& g : g2s) st.flops += add_gemm(*pl, g);
-      st.g2_n = (int32_t)pl->tiles.size() - st.g2_b;
+      st.g1 = emit_group(*pl, g1s, D->sms);
+      st.g2 = emit_group(*pl, g2s, D->sms);
+      st.flops = st.g1.flops + st.g2.flops;
       sl.steps.push_back(st);
     }
     // Uhat = L_RJ T
-    sl.uh_b = (int32_t)pl->tiles.size();
+    std::vector<GenGemm> gs;
     for (int32_t J : Js) {
       const SnodeDev& d = h->snodes[J];
       const int b = d.len - d.s;
       if (b > 0)
-        sl.gemm_flops += add_gemm(*pl, mk(L + d.loff + d.s, 1, d.ld, D->Tw + toff[J], 1, d.s, D->Uh + hoff[J], 1, b, b, d.s, d.s, 1.0,
-                         0.0, 0, 1, 0));
+        gs.push_back(mk(L + d.loff + d.s, 1, d.ld, D->Tw + toff[J], 1, d.s, D->Uh + hoff[J], 1, b, b, d.s, d.s, 1.0,
+                        0.0, 0, 1, 0));
     }
-    sl.uh_n = (int32_t)pl->tiles.size() - sl.uh_b;
+    sl.uh = emit_group(*pl, gs, D->sms);
     // Z_RR gather pairs
     sl.pair_b = (int32_t)pl->pairs.size();
     for (int32_t J : Js)
-      for (int64_t p : pairs_of[J]) pl->pairs.push_back({J, h->rel_K[p], h->rel_c0[p], h->rel_c1[p]});
+      for (int64_t p : pairs_of[J]) {
+        const SnodeDev& d = h->snodes[J];
+        const int32_t b = d.len - d.s;
+        // rows u >= c0 of J are the ones in K (and later ancestors' rows are
+        // in struct(K) too); chunks of kGatherRows
+        for (int32_t u0 = h->rel_c0[p]; u0 < b; u0 += kGatherRows)
+          pl->pairs.push_back({J, h->rel_K[p], h->rel_c0[p], h->rel_c1[p], u0, std::min(b, u0 + kGatherRows)});
+      }
     sl.pair_n = (int32_t)pl->pairs.size() - sl.pair_b;
     // Z_RJ = -Z_RR Uhat  (Z_RR at U_J's place in the update workspace)
-    sl.zrj_b = (int32_t)pl->tiles.size();
+    gs.clear();
     for (int32_t J : Js) {
       const SnodeDev& d = h->snodes[J];
       const int b = d.len - d.s;
       if (b > 0)
-        sl.gemm_flops += add_gemm(*pl, mk(D->U + d.uoff, 1, b, D->Uh + hoff[J], 1, b, Z + d.loff + d.s, 1, d.ld, b, d.s, b, -1.0, 0.0, 2,
-                         0, 0));
+        gs.push_back(mk(D->U + d.uoff, 1, b, D->Uh + hoff[J], 1, b, Z + d.loff + d.s, 1, d.ld, b, d.s, b, -1.0, 0.0, 2,
+                        0, 0));
     }
-    sl.zrj_n = (int32_t)pl->tiles.size() - sl.zrj_b;
+    sl.zrj = emit_group(*pl, gs, D->sms);
     // Z_JJ = T^T T, then -= Uhat^T Z_RJ
-    sl.zjj1_b = (int32_t)pl->tiles.size();
+    gs.clear();
     for (int32_t J : Js) {
       const SnodeDev& d = h->snodes[J];
       double* T = D->Tw + toff[J];
-      sl.gemm_flops += add_gemm(*pl, mk(T, d.s, 1, T, 1, d.s, Z + d.loff, 1, d.ld, d.s, d.s, d.s, 1.0, 0.0, 0, 0, 1));
+      gs.push_back(mk(T, d.s, 1, T, 1, d.s, Z + d.loff, 1, d.ld, d.s, d.s, d.s, 1.0, 0.0, 0, 0, 1));
     }
-    sl.zjj1_n = (int32_t)pl->tiles.size() - sl.zjj1_b;
-    sl.zjj2_b = (int32_t)pl->tiles.size();
+    sl.zjj1 = emit_group(*pl, gs, D->sms);
+    gs.clear();
     for (int32_t J : Js) {
       const SnodeDev& d = h->snodes[J];
       const int b = d.len - d.s;
       if (b > 0)
-        sl.gemm_flops += add_gemm(*pl, mk(D->Uh + hoff[J], b, 1, Z + d.loff + d.s, 1, d.ld, Z + d.loff, 1, d.ld, d.s, d.s, b, -1.0, 1.0, 0,
-                         0, 1));
+        gs.push_back(mk(D->Uh + hoff[J], b, 1, Z + d.loff + d.s, 1, d.ld, Z + d.loff, 1, d.ld, d.s, d.s, b, -1.0, 1.0, 0,
+                        0, 1));
     }
-    sl.zjj2_n = (int32_t)pl->tiles.size() - sl.zjj2_b;
+    sl.zjj2 = emit_group(*pl, gs, D->sms);
+    sl.gemm_flops = sl.uh.flops + sl.zrj.flops + sl.zjj1.flops + sl.zjj2.flops;
     pl->levels.push_back(std::move(sl));
   }
   auto up = [&](auto** dst, const auto& v) -> int {
@@ -441,6 +556,8 @@ int build_si_plan(chol_handle* h) {
   };
   if ((rc = up(&pl->d_descs, pl->descs))) return rc;
   if ((rc = up(&pl->d_tiles, pl->tiles))) return rc;
+  if ((rc = up(&pl->d_rtiles, pl->rtiles))) return rc;
+  if (pl->part_max > 0 && (rc = chol_dalloc(h, (void**)&pl->d_part, sizeof(double) * (size_t)pl->part_max))) return rc;
   if ((rc = up(&pl->d_invs, pl->invs))) return rc;
   if ((rc = up(&pl->d_pairs, pl->pairs))) return rc;
   D->si_plan = pl;
@@ -453,36 +570,38 @@ int build_si_plan(chol_handle* h) {
 int selinv(chol_handle* h, cudaStream_t st) {
   if (h->selinv_valid) return CHOL_OK;
   // the Z_RR gather stages struct(K) and the positions in shared memory
-  if ((int64_t)h->max_len * 2 * (int64_t)sizeof(int32_t) > 200 * 1024) return CHOL_ENOTSUP;
+  if ((int64_t)(h->max_len + kGatherRows) * (int64_t)sizeof(int32_t) > 200 * 1024) return CHOL_ENOTSUP;
   int rc = ensure_adjoint(h);
   if (rc) return rc;
   if ((rc = build_si_plan(h))) return rc;
   DeviceState* D = h->dev;
   SiPlan* pl = (SiPlan*)D->si_plan;
-  auto launch = [&](int32_t b, int32_t n) {
-    if (n > 0) k_gen_gemm_grouped<<<n, kGT, 0, st>>>(pl->d_descs, pl->d_tiles + b);
+  auto launch = [&](const Group& gr) {
+    if (gr.tn > 0) k_gen_gemm_grouped<<<gr.tn, kGT, 0, st>>>(pl->d_descs, pl->d_tiles + gr.tb, pl->d_part);
+    if (gr.rn > 0) k_gen_reduce<<<gr.rn, kGT, 0, st>>>(pl->d_descs, pl->d_rtiles + gr.rb, pl->d_part);
   };
+  auto nl = [](const Group& gr) { return (gr.tn > 0) + (gr.rn > 0); };
   for (const SiLevel& sl : pl->levels) {
     CHOL_CUDA_TRY(cudaMemsetAsync(D->Tw, 0, sizeof(double) * (size_t)sl.t_doubles, st));
     for (const SiStep& q : sl.steps) {
       KScope ks(h, CHOL_K_SELINV_INV, st, q.flops, 0.0);
-      ks.launches((q.inv_n > 0) + (q.g1_n > 0) + (q.g2_n > 0));
+      ks.launches((q.inv_n > 0) + nl(q.g1) + nl(q.g2));
       if (q.inv_n > 0) k_inv64_grouped<<<q.inv_n, 64, 0, st>>>(pl->d_invs + q.inv_b);
-      launch(q.g1_b, q.g1_n);
-      launch(q.g2_b, q.g2_n);
+      launch(q.g1);
+      launch(q.g2);
     }
     if (sl.pair_n > 0) {
       KScope ks(h, CHOL_K_SELINV_GATHER, st, 0.0, 0.0);
-      k_gather_zrr_level<<<sl.pair_n, kGT, sizeof(int32_t) * 2 * h->max_len, st>>>(pl->d_pairs + sl.pair_b, D->sn,
+      k_gather_zrr_level<<<sl.pair_n, kGT, sizeof(int32_t) * (h->max_len + kGatherRows), st>>>(pl->d_pairs + sl.pair_b, D->sn,
                                                                                    D->rows, D->Zp, D->U);
     }
     {
       KScope ks(h, CHOL_K_SELINV_GEMM, st, sl.gemm_flops, 0.0);
-      ks.launches((sl.uh_n > 0) + (sl.zrj_n > 0) + (sl.zjj1_n > 0) + (sl.zjj2_n > 0));
-      launch(sl.uh_b, sl.uh_n);
-      launch(sl.zrj_b, sl.zrj_n);
-      launch(sl.zjj1_b, sl.zjj1_n);
-      launch(sl.zjj2_b, sl.zjj2_n);
+      ks.launches(nl(sl.uh) + nl(sl.zrj) + nl(sl.zjj1) + nl(sl.zjj2));
+      launch(sl.uh);
+      launch(sl.zrj);
+      launch(sl.zjj1);
+      launch(sl.zjj2);
     }
   }
   CHOL_CUDA_TRY(cudaGetLastError());
@@ -496,7 +615,7 @@ void chol_adjoint_free(chol_handle* h) {
   DeviceState* D = h->dev;
   if (!D || !D->si_plan) return;
   SiPlan* pl = (SiPlan*)D->si_plan;
-  void* ptrs[] = {pl->d_descs, pl->d_tiles, pl->d_invs, pl->d_pairs};
+  void* ptrs[] = {pl->d_descs, pl->d_tiles, pl->d_rtiles, pl->d_invs, pl->d_pairs, pl->d_part};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   delete pl;

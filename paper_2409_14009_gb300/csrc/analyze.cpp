@@ -487,15 +487,27 @@ void build(chol_handle* h, const int64_t* colptr, const int32_t* rowind) {
         const double below = (double)(d.len - k0 - kb);
         st.trsm_flops += below * (double)kb * (double)kb;   // kb divisions + 2*kb(kb-1)/2 per row
         for (int32_t r0 = k0 + kb; r0 < d.len; r0 += kTrsmRowsHost) h->trsm_tasks.push_back({J, k0, r0, 0});
-        // the step's own trailing update covers columns [k0+kb, cend)
-        const int32_t cend = tc_modes ? std::min(d.s, ob + kTcOuter) : d.s;
-        for (int32_t c0 = k0 + kb; c0 < cend; c0 += tg)
-          for (int32_t r0 = c0; r0 < d.len; r0 += tg) h->gemm_tasks.push_back({J, k0, r0, c0});
         // trailing update: 2 kb flops per entry (r, c) with c in [k0+kb, cend), r in [c, len)
+        const int32_t cend = tc_modes ? std::min(d.s, ob + kTcOuter) : d.s;
         {
           const double w = (double)(cend - k0 - kb), hgt = (double)(d.len - k0 - kb);
           st.gemm_flops += 2.0 * kb * (w * hgt - w * (w - 1.0) / 2.0);
         }
+      }
+      // the step's own trailing update covers columns [k0+kb, cend) of each
+      // supernode: first column tiles of all supernodes, then the others
+      for (int pass = 0; pass < 2; ++pass) {
+        for (int32_t J : large) {
+          const SnodeDev& d = h->snodes[J];
+          if (d.s <= k0) continue;
+          const int32_t kb = std::min(nb, d.s - k0);
+          const int32_t cend = tc_modes ? std::min(d.s, ob + kTcOuter) : d.s;
+          for (int32_t c0 = k0 + kb; c0 < cend; c0 += tg) {
+            if ((pass == 0) != (c0 == k0 + kb)) continue;
+            for (int32_t r0 = c0; r0 < d.len; r0 += tg) h->gemm_tasks.push_back({J, k0, r0, c0});
+          }
+        }
+        if (pass == 0) st.gemm_next = (int32_t)h->gemm_tasks.size() - st.gemm_b;
       }
       st.potrf_n = (int32_t)h->potrf_list.size() - st.potrf_b;
       st.trsm_n = (int32_t)h->trsm_tasks.size() - st.trsm_b;

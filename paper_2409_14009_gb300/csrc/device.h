@@ -73,6 +73,9 @@ struct DeviceState {
   cudaGraphExec_t graph_exec = nullptr;
   cudaStream_t gstream = nullptr;  // capture / replay stream of the handle
   cudaEvent_t gev[2] = {nullptr, nullptr};
+  cudaStream_t lstream = nullptr;  // side stream of the lookahead trailing updates (lowest priority)
+  cudaStream_t hstream = nullptr;  // critical path of the blocked levels (highest priority)
+  cudaEvent_t lev[3] = {nullptr, nullptr, nullptr};   // panel final / rest done / fork-join
   chol_kernel_stat graph_delta[CHOL_K_NCLASSES] = {};
   float mx_spiv = 0.f;             // static-pivot threshold passed to the persistent kernel
   // selected inverse and adjoint

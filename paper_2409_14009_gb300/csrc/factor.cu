@@ -45,18 +45,24 @@ constexpr int kAsmThreads = 256;
 // column with NaN so that the failure propagates without stopping the grid.
 // ---------------------------------------------------------------------------
 __device__ void dense_chol_smem(double* P, int ld, int len, int s, int fcol, int* status) {
+  __shared__ double srk;
   for (int k = 0; k < s; ++k) {
     __syncthreads();
-    const double d = P[k + k * ld];
-    const bool bad = !(d > 0.0);
-    const double dk = bad ? __longlong_as_double(0x7ff8000000000000LL) : sqrt(d);
-    const double inv = 1.0 / dk;
-    for (int r = k + 1 + threadIdx.x; r < len; r += blockDim.x) P[r + k * ld] *= inv;
-    __syncthreads();
     if (threadIdx.x == 0) {
+      // the pivot's root once, by one thread (FP64 sqrt and division are long
+      // dependent sequences on the narrow FP64 pipe)
+      const double d = P[k + k * ld];
+      const bool bad = !(d > 0.0);
+      double dk, rk;
+      pivot_root(d, bad, dk, rk);
       P[k + k * ld] = dk;
+      srk = rk;
       if (bad) atomicMin(status, fcol + k + 1);
     }
+    __syncthreads();
+    const double inv = srk;
+    for (int r = k + 1 + threadIdx.x; r < len; r += blockDim.x) P[r + k * ld] *= inv;
+    __syncthreads();
     // rank-1 update of the trailing columns, one thread per row
     for (int r = k + 1 + threadIdx.x; r < len; r += blockDim.x) {
       const double lrk = P[r + k * ld];
@@ -166,8 +172,9 @@ k_trsm(const SnodeDev* __restrict__ sn, const TileTask* __restrict__ tasks, int 
         const double cand = x[jm] * inv[j];
         const double xj = __shfl_sync(0xffffffffu, cand, jq, 8);
         if (q == jq) x[jm] = xj;
+        // columns q + 8m with m < jm are already solved: not even issued
 #pragma unroll
-        for (int m = 0; m < 8; ++m) {
+        for (int m = jm; m < 8; ++m) {
           const int c = q + 8 * m;
           if (c > j && c < kb) x[m] -= xj * Lk[c + j * 65];
         }
@@ -454,7 +461,7 @@ inline unsigned grid1d(int64_t n, int threads) {
 void chol_prof_resolve(chol_handle* h) {
   Profiler* p = h->prof;
   if (!p || p->pending.empty()) return;
-  cudaEventSynchronize(p->pending.back().b);
+  for (auto& q : p->pending) cudaEventSynchronize(q.b);   // launches may be on several streams
   for (auto& q : p->pending) {
     float ms = 0.f;
     if (cudaEventElapsedTime(&ms, q.a, q.b) == cudaSuccess) {
@@ -533,6 +540,10 @@ void chol_device_free(chol_handle* h) {
   if (D->red_host) cudaFreeHost(D->red_host);
   if (D->graph_exec) cudaGraphExecDestroy(D->graph_exec);
   if (D->gstream) cudaStreamDestroy(D->gstream);
+  if (D->lstream) cudaStreamDestroy(D->lstream);
+  if (D->hstream) cudaStreamDestroy(D->hstream);
+  for (cudaEvent_t e : D->lev)
+    if (e) cudaEventDestroy(e);
   for (cudaEvent_t e : D->gev)
     if (e) cudaEventDestroy(e);
   if (cur >= 0) cudaSetDevice(cur);
@@ -554,6 +565,19 @@ int chol_device_ensure(chol_handle* h) {
     return code;
   };
   if (cudaGetDevice(&D->device) != cudaSuccess) return fail(CHOL_ECUDA);
+  {
+    // the lookahead's critical path (POTRF, TRSM, next column block) runs on a
+    // highest-priority stream so that its CTAs are placed ahead of the side
+    // stream's trailing tiles
+    int lo = 0, hi = 0;
+    if (cudaDeviceGetStreamPriorityRange(&lo, &hi) != cudaSuccess ||
+        cudaStreamCreateWithPriority(&D->hstream, cudaStreamNonBlocking, hi) != cudaSuccess ||
+        cudaStreamCreateWithPriority(&D->lstream, cudaStreamNonBlocking, lo) != cudaSuccess ||
+        cudaEventCreateWithFlags(&D->lev[0], cudaEventDisableTiming) != cudaSuccess ||
+        cudaEventCreateWithFlags(&D->lev[1], cudaEventDisableTiming) != cudaSuccess ||
+        cudaEventCreateWithFlags(&D->lev[2], cudaEventDisableTiming) != cudaSuccess)
+      return fail(CHOL_ECUDA);
+  }
   if (cudaDeviceGetAttribute(&D->sms, cudaDevAttrMultiProcessorCount, D->device) != cudaSuccess) return fail(CHOL_ECUDA);
   if (h->opt.precision != CHOL_PREC_FP64) {
     // the tensor-core and binary32 kernels are built for this architecture only
@@ -633,12 +657,27 @@ int enqueue_factor_fp64(chol_handle* h, const double* values, cudaStream_t st) {
     KScope ks(h, CHOL_K_SMALL, st, fl, by);
     return chol_launch_persistent(h, (void*)D->L, (void*)D->U, st);
   }
+  // levels with blocked supernodes run on the high-priority stream (forked from
+  // and joined back to the caller's stream)
+  const cudaStream_t caller = st;
+  if (h->n_large > 0) {
+    CHOL_CUDA_TRY(cudaEventRecord(D->lev[2], caller));
+    CHOL_CUDA_TRY(cudaStreamWaitEvent(D->hstream, D->lev[2], 0));
+    st = D->hstream;
+  }
   for (const LevelPlan& P : h->levels) {
     if (P.small_n > 0) {
       KScope ks(h, CHOL_K_SMALL, st, P.small_flops, P.small_bytes);
       k_small<<<P.small_n, kSmallThreads, sizeof(double) * P.small_max_panel, st>>>(
           D->sn, D->small_list + P.small_b, D->L, D->U, D->status);
     }
+    // One-step lookahead: the trailing tiles of step k other than the next
+    // block column ("rest") run on the side stream, beside the POTRF and TRSM
+    // of step k + 1 on the main stream. Before step k + 1's own trailing tiles,
+    // the main stream waits for step k's rest (they share tiles); the side
+    // stream keeps the rests in order. Each tile still receives its updates in
+    // step order, so the result is the same as without lookahead.
+    bool rest_pending = false;
     for (size_t k = 0; k < P.steps.size(); ++k) {
       const StepRange& s = P.steps[k];
       const int k0 = (int)k * nb;
@@ -651,11 +690,31 @@ int enqueue_factor_fp64(chol_handle* h, const double* values, cudaStream_t st) {
         KScope ks(h, CHOL_K_TRSM, st, s.trsm_flops, 16.0 * kTrsmRows * nb * s.trsm_n);
         k_trsm<<<s.trsm_n, kTrsmThreads, 0, st>>>(D->sn, D->trsm + s.trsm_b, nb, D->L);
       }
+      const int nrest = s.gemm_n - s.gemm_next;
+      if (nrest > 0) {
+        CHOL_CUDA_TRY(cudaEventRecord(D->lev[0], st));   // step k's panel is final
+        CHOL_CUDA_TRY(cudaStreamWaitEvent(D->lstream, D->lev[0], 0));
+      }
+      if (rest_pending) {
+        CHOL_CUDA_TRY(cudaStreamWaitEvent(st, D->lev[1], 0));   // step k-1's rest
+        rest_pending = false;
+      }
       if (s.gemm_n > 0) {
-        KScope ks(h, CHOL_K_GEMM, st, s.gemm_flops, 16.0 * kTile * kTile * s.gemm_n);
-        k_gemm_trailing<<<s.gemm_n, kGemmThreads, 0, st>>>(D->sn, D->gemm + s.gemm_b, nb, D->L);
+        const double frac = (double)s.gemm_next / s.gemm_n;
+        if (s.gemm_next > 0) {
+          KScope ks(h, CHOL_K_GEMM, st, s.gemm_flops * frac, 16.0 * kTile * kTile * s.gemm_next);
+          k_gemm_trailing<<<s.gemm_next, kGemmThreads, 0, st>>>(D->sn, D->gemm + s.gemm_b, nb, D->L);
+        }
+        if (nrest > 0) {
+          KScope ks(h, CHOL_K_GEMM, D->lstream, s.gemm_flops * (1.0 - frac), 16.0 * kTile * kTile * nrest);
+          k_gemm_trailing<<<nrest, kGemmThreads, 0, D->lstream>>>(D->sn, D->gemm + s.gemm_b + s.gemm_next, nb,
+                                                                  D->L);
+          CHOL_CUDA_TRY(cudaEventRecord(D->lev[1], D->lstream));
+          rest_pending = true;
+        }
       }
     }
+    if (rest_pending) CHOL_CUDA_TRY(cudaStreamWaitEvent(st, D->lev[1], 0));   // join before SYRK
     if (P.syrk_n > 0) {
       KScope ks(h, CHOL_K_SYRK, st, P.syrk_flops, 8.0 * kTile * kTile * P.syrk_n);
       k_syrk<<<P.syrk_n, kGemmThreads, 0, st>>>(D->sn, D->syrk + P.syrk_b, D->L, D->U);
@@ -670,6 +729,10 @@ int enqueue_factor_fp64(chol_handle* h, const double* values, cudaStream_t st) {
         k_assemble_warp<double, false><<<(P.asmw_n + 7) / 8, 256, 0, st>>>(
             D->asm_tasks + P.asm_b + P.asm_n, P.asmw_n, D->asm_segs, D->sn, D->rows, D->U, D->L);
     }
+  }
+  if (st != caller) {
+    CHOL_CUDA_TRY(cudaEventRecord(D->lev[2], st));
+    CHOL_CUDA_TRY(cudaStreamWaitEvent(caller, D->lev[2], 0));
   }
   CHOL_CUDA_TRY(cudaGetLastError());
   return CHOL_OK;

@@ -41,8 +41,13 @@ struct AsmSeg {
 // stays inside its kTcOuter-wide column block, and after the last step of a
 // block the columns right of it are updated once with K = the block's width
 // (ogemm_*, K range starting at ok0).
+// binary64: the step's trailing tiles are ordered with the first column tile
+// of every supernode first (gemm_next of them: the next step's block column),
+// then the rest, so the rest can run beside the next POTRF and TRSM
+// (one-step lookahead).
 struct StepRange {
   int32_t potrf_b, potrf_n, trsm_b, trsm_n, gemm_b, gemm_n, ogemm_b, ogemm_n, ok0, okb;
+  int32_t gemm_next;
   double potrf_flops, trsm_flops, gemm_flops, ogemm_flops;
 };
 

@@ -177,7 +177,7 @@ k_mx_trsm(const SnodeDev* __restrict__ sn, const TileTask* __restrict__ tasks, i
         const float xj = __shfl_sync(0xffffffffu, x[jm] * inv[j], jq, 8);
         if (q == jq) x[jm] = xj;
 #pragma unroll
-        for (int m = 0; m < 8; ++m) {
+        for (int m = jm; m < 8; ++m) {
           const int c = q + 8 * m;
           if (c > j && c < kb) x[m] = fmaf(-xj, Lk[c + j * 65], x[m]);
         }

@@ -31,6 +31,34 @@ __device__ __forceinline__ void pk_coord(int e, int kb, int& r, int& c) {
   r = cc + (e - pk_off(cc, kb));
 }
 
+// Square root of a pivot and its reciprocal. binary32: the library functions.
+// binary64: on this GPU every FP64 instruction of the serial pivot chain holds
+// the narrow FP64 pipe for many cycles, and sqrt plus a division expand to
+// long dependent sequences; instead the reciprocal square root starts from the
+// binary32 estimate and takes two Newton-Raphson steps y <- y (3 - d y^2) / 2
+// (each roughly doubles the correct bits: ~23 -> ~46 -> full precision, within
+// a few ulps), then sqrt(d) = d y. Pivots outside the binary32 normal range
+// take sqrt and a division.
+__device__ __forceinline__ void pivot_root(float d, bool bad, float& root, float& rroot) {
+  root = bad ? __int_as_float(0x7fc00000) : sqrtf(d);
+  rroot = 1.0f / root;
+}
+__device__ __forceinline__ void pivot_root(double d, bool bad, double& root, double& rroot) {
+  if (bad) {
+    root = __longlong_as_double(0x7ff8000000000000LL);
+    rroot = root;
+  } else if (d > 1e-30 && d < 1e30) {
+    double y = (double)rsqrtf((float)d);
+    y = y * fma(-0.5 * d, y * y, 1.5);
+    y = y * fma(-0.5 * d, y * y, 1.5);
+    root = d * y;
+    rroot = y;
+  } else {
+    root = sqrt(d);
+    rroot = 1.0 / root;
+  }
+}
+
 // Factor the block at G (row-major with leading dimension ld if RM, else
 // column-major) in arithmetic T, reading and writing the storage type GT.
 //   spiv       > 0: static pivoting, a pivot below spiv becomes max(|d|, spiv)
@@ -77,11 +105,12 @@ __device__ bool potrf_block(GT* __restrict__ G, int64_t ld, int kb, T spiv, int*
       const bool bad = !(dv > T(0));
       if (sminpiv && ((float)dv < *sminpiv || bad)) *sminpiv = bad ? -1.f : (float)dv;
       if (bad && record) atomicMin(status, fcol + k + 1);
-      const T dk = bad ? T(__longlong_as_double(0x7ff8000000000000LL)) : sqrt(dv);
+      T dk, rk;
+      pivot_root(dv, bad, dk, rk);
 #pragma unroll
       for (int q = 0; q < kPkSlots; ++q)
         if (q == qk) v[q] = dk;
-      *sinv = T(1) / dk;
+      *sinv = rk;
     }
     __syncthreads();
     const T inv = *sinv;

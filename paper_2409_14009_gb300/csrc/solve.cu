@@ -153,6 +153,7 @@ k_sv_tri(const SnodeDev* __restrict__ sn, const TriItem* __restrict__ items, int
       const int rr = RM ? e / kb : e % kb, cc = RM ? e % kb : e / kb;
       Ls[rr + cc * 65] = lval<T, RM>(P, d, i0 + rr, i0 + cc);
     }
+    for (int c = tid; c < kb; c += kT) inv[c] = T(1) / lval<T, RM>(P, d, i0 + c, i0 + c);
     if (item.i > 0) {
       const int jl = TRANS ? blk + 1 : blk - 1, jl0 = jl * kSub, jlb = min(kSub, d.s - jl0);
       for (int e = tid; e < kb * jlb; e += kT) {
@@ -213,13 +214,13 @@ k_sv_tri(const SnodeDev* __restrict__ sn, const TriItem* __restrict__ items, int
       const T sum = ((pr[0] + pr[kSub]) + pr[2 * kSub]) + pr[3 * kSub];
       yi[rr + m * kSub] = Y[d.f + i0 + rr + (int64_t)m * n] - sum;
     }
-    for (int c = tid; c < kb; c += kT) inv[c] = T(1) / Ls[c + c * 65];
     __syncthreads();
     // substitution: 16 lanes per right-hand side, lane q holds rows q + 16a;
-    // every lane takes part in the shuffles, only live ones write
+    // warps without a live right-hand side skip it, the others take part in the
+    // shuffles with all lanes and only live ones write
     const int rr = tid >> 4, q = tid & 15;
     const bool live = rr < nrhs;
-    {
+    if ((tid >> 5) * 2 < nrhs) {
       T y[4];
 #pragma unroll
       for (int a = 0; a < 4; ++a) {
@@ -236,7 +237,7 @@ k_sv_tri(const SnodeDev* __restrict__ sn, const TriItem* __restrict__ items, int
               const T yk = __shfl_sync(0xffffffffu, y[ka] * inv[k], kq, 16);
               if (q == kq) y[ka] = yk;
 #pragma unroll
-              for (int a = 0; a < 4; ++a) {
+              for (int a = ka; a < 4; ++a) {   // rows of earlier slots are solved
                 const int i = q + 16 * a;
                 if (i > k && i < kb) y[a] -= Ls[i + k * 65] * yk;
               }
@@ -252,7 +253,7 @@ k_sv_tri(const SnodeDev* __restrict__ sn, const TriItem* __restrict__ items, int
               const T yk = __shfl_sync(0xffffffffu, y[ka] * inv[k], kq, 16);
               if (q == kq) y[ka] = yk;
 #pragma unroll
-              for (int a = 0; a < 4; ++a) {
+              for (int a = 0; a <= ka; ++a) {  // rows of later slots are solved
                 const int i = q + 16 * a;
                 if (i < k) y[a] -= Ls[k + i * 65] * yk;
               }
