@@ -516,15 +516,26 @@ void build(chol_handle* h, const int64_t* colptr, const int32_t* rowind) {
       st.ogemm_b = (int32_t)h->gemm_tasks.size();
       st.ok0 = ob;
       st.okb = kTcOuter;
+      st.ogemm_next = 0;
       if (tc_modes && (k0 + nb) % kTcOuter == 0) {
         const int32_t oend = ob + kTcOuter;
         for (int32_t J : large) {
           const SnodeDev& d = h->snodes[J];
           if (d.s <= oend) continue;
-          for (int32_t c0 = oend; c0 < d.s; c0 += tg)
-            for (int32_t r0 = c0; r0 < d.len; r0 += tg) h->gemm_tasks.push_back({J, ob, r0, c0});
           const double w = (double)(d.s - oend), hgt = (double)(d.len - oend);
           st.ogemm_flops += 2.0 * kTcOuter * (w * hgt - w * (w - 1.0) / 2.0);
+        }
+        // first column tiles (the next step's block column) of every supernode first
+        for (int pass = 0; pass < 2; ++pass) {
+          for (int32_t J : large) {
+            const SnodeDev& d = h->snodes[J];
+            if (d.s <= oend) continue;
+            for (int32_t c0 = oend; c0 < d.s; c0 += tg) {
+              if ((pass == 0) != (c0 == oend)) continue;
+              for (int32_t r0 = c0; r0 < d.len; r0 += tg) h->gemm_tasks.push_back({J, ob, r0, c0});
+            }
+          }
+          if (pass == 0) st.ogemm_next = (int32_t)h->gemm_tasks.size() - st.ogemm_b;
         }
       }
       st.ogemm_n = (int32_t)h->gemm_tasks.size() - st.ogemm_b;

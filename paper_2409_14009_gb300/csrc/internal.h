@@ -47,7 +47,7 @@ struct AsmSeg {
 // (one-step lookahead).
 struct StepRange {
   int32_t potrf_b, potrf_n, trsm_b, trsm_n, gemm_b, gemm_n, ogemm_b, ogemm_n, ok0, okb;
-  int32_t gemm_next;
+  int32_t gemm_next, ogemm_next;
   double potrf_flops, trsm_flops, gemm_flops, ogemm_flops;
 };
 

@@ -498,12 +498,30 @@ int chol_enqueue_factor_mixed(chol_handle* h, const double* values, cudaStream_t
     KScope ks(h, CHOL_K_SMALL, st, fl, by);
     return chol_launch_persistent(h, (void*)L, (void*)U, st);
   }
+  // levels with blocked supernodes: critical path on the high-priority stream
+  const cudaStream_t caller = st;
+  if (h->n_large > 0) {
+    CHOL_CUDA_TRY(cudaEventRecord(D->lev[2], caller));
+    CHOL_CUDA_TRY(cudaStreamWaitEvent(D->hstream, D->lev[2], 0));
+    st = D->hstream;
+  }
+  // trailing tiles of a step, in-block (K = nb) or outer (K = kTcOuter)
+  auto gemm = [&](const TileTask* tasks, int n, bool outer, double flops, cudaStream_t s2) -> int {
+    if (n <= 0) return CHOL_OK;
+    KScope ks(h, CHOL_K_GEMM, s2, flops, 0.0);
+    if (tc) return chol_tc_gemm(h, tasks, n, outer ? kTcOuter : nb, outer ? 0 : 1, s2);
+    k_mx_gemm_simt<<<n, 256, 0, s2>>>(D->sn, tasks, nb, L);
+    return CHOL_OK;
+  };
   for (const LevelPlan& P : h->levels) {
     if (P.small_n > 0) {
       KScope ks(h, CHOL_K_SMALL, st, P.small_flops, P.small_bytes / 2);
       k_mx_small<<<P.small_n, 128, sizeof(float) * P.small_max_panel, st>>>(D->sn, D->small_list + P.small_b, L, U,
                                                                               D->status, spiv, D->mx_fallbacks);
     }
+    // one-step lookahead as in the binary64 factor: each step's in-block and
+    // outer trailing tiles past the next block column run on the side stream
+    bool rest_pending = false;
     for (size_t k = 0; k < P.steps.size(); ++k) {
       const StepRange& s = P.steps[k];
       const int k0 = (int)k * nb;
@@ -517,19 +535,29 @@ int chol_enqueue_factor_mixed(chol_handle* h, const double* values, cudaStream_t
         k_mx_trsm<<<s.trsm_n, 256, 0, st>>>(D->sn, D->trsm + s.trsm_b, nb, L,
                                             (__nv_bfloat16*)(h->opt.precision == CHOL_PREC_BF16 ? D->Lbf : nullptr));
       }
-      if (s.gemm_n > 0) {
-        KScope ks(h, CHOL_K_GEMM, st, s.gemm_flops, 0.0);
-        if (tc) {
-          if ((rc = chol_tc_gemm(h, D->gemm + s.gemm_b, s.gemm_n, nb, 1, st))) return rc;
-        } else {
-          k_mx_gemm_simt<<<s.gemm_n, 256, 0, st>>>(D->sn, D->gemm + s.gemm_b, nb, L);
-        }
+      const int irest = s.gemm_n - s.gemm_next, orest = s.ogemm_n - s.ogemm_next;
+      if (irest + orest > 0) {
+        CHOL_CUDA_TRY(cudaEventRecord(D->lev[0], st));   // step k's panel is final
+        CHOL_CUDA_TRY(cudaStreamWaitEvent(D->lstream, D->lev[0], 0));
       }
-      if (s.ogemm_n > 0) {
-        KScope ks(h, CHOL_K_GEMM, st, s.ogemm_flops, 0.0);
-        if ((rc = chol_tc_gemm(h, D->gemm + s.ogemm_b, s.ogemm_n, s.okb, 0, st))) return rc;
+      if (rest_pending) {
+        CHOL_CUDA_TRY(cudaStreamWaitEvent(st, D->lev[1], 0));
+        rest_pending = false;
+      }
+      const double fi = s.gemm_n > 0 ? (double)s.gemm_next / s.gemm_n : 0.0;
+      const double fo = s.ogemm_n > 0 ? (double)s.ogemm_next / s.ogemm_n : 0.0;
+      if ((rc = gemm(D->gemm + s.gemm_b, s.gemm_next, false, s.gemm_flops * fi, st))) return rc;
+      if ((rc = gemm(D->gemm + s.ogemm_b, s.ogemm_next, true, s.ogemm_flops * fo, st))) return rc;
+      if (irest + orest > 0) {
+        if ((rc = gemm(D->gemm + s.gemm_b + s.gemm_next, irest, false, s.gemm_flops * (1.0 - fi), D->lstream)))
+          return rc;
+        if ((rc = gemm(D->gemm + s.ogemm_b + s.ogemm_next, orest, true, s.ogemm_flops * (1.0 - fo), D->lstream)))
+          return rc;
+        CHOL_CUDA_TRY(cudaEventRecord(D->lev[1], D->lstream));
+        rest_pending = true;
       }
     }
+    if (rest_pending) CHOL_CUDA_TRY(cudaStreamWaitEvent(st, D->lev[1], 0));   // join before SYRK
     if (P.syrk_n > 0) {
       KScope ks(h, CHOL_K_SYRK, st, P.syrk_flops, 0.0);
       if (tc) {
@@ -548,6 +576,10 @@ int chol_enqueue_factor_mixed(chol_handle* h, const double* values, cudaStream_t
         k_assemble_warp<float, true><<<(P.asmw_n + 7) / 8, 256, 0, st>>>(
             D->asm_tasks + P.asm_b + P.asm_n, P.asmw_n, D->asm_segs, D->sn, D->rows, U, L);
     }
+  }
+  if (st != caller) {
+    CHOL_CUDA_TRY(cudaEventRecord(D->lev[2], st));
+    CHOL_CUDA_TRY(cudaStreamWaitEvent(caller, D->lev[2], 0));
   }
   CHOL_CUDA_TRY(cudaGetLastError());
   return CHOL_OK;
