@@ -116,7 +116,7 @@ __device__ __forceinline__ void st_release(int* p, int v) {
   asm volatile("st.release.gpu.global.b32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
 }
 
-constexpr long long kTriMaxPolls = 1ll << 24;   // about two seconds with the back-off below
+constexpr long long kTriMaxPolls = 1ll << 24;   // seconds, with the back-off below
 
 template <class T>
 size_t tri_smem(int nr) {
@@ -154,6 +154,11 @@ k_sv_tri(const SnodeDev* __restrict__ sn, const TriItem* __restrict__ items, int
       Ls[rr + cc * 65] = lval<T, RM>(P, d, i0 + rr, i0 + cc);
     }
     for (int c = tid; c < kb; c += kT) inv[c] = T(1) / lval<T, RM>(P, d, i0 + c, i0 + c);
+    // this block's right-hand sides (written by earlier launches only)
+    for (int e = tid; e < kb * nrhs; e += kT) {
+      const int rr = e % kb, m = e / kb;
+      yi[rr + m * kSub] = Y[d.f + i0 + rr + (int64_t)m * n];
+    }
     if (item.i > 0) {
       const int jl = TRANS ? blk + 1 : blk - 1, jl0 = jl * kSub, jlb = min(kSub, d.s - jl0);
       for (int e = tid; e < kb * jlb; e += kT) {
@@ -172,9 +177,8 @@ k_sv_tri(const SnodeDev* __restrict__ sn, const TriItem* __restrict__ items, int
         long long polls = 0;
         while (ld_acquire(flags + item.fbase + j) != tgt) {
           if (++polls > kTriMaxPolls) { atomicExch(err, 1); break; }
-          __nanosleep(100);
+          if (polls > 4096) __nanosleep(100);   // spin first: the hand-off is on the critical path
         }
-        __threadfence();
       }
       __syncthreads();   // also: the previous tile is done with ys
       for (int e = tid; e < jb * nrhs; e += kT) {
@@ -185,12 +189,21 @@ k_sv_tri(const SnodeDev* __restrict__ sn, const TriItem* __restrict__ items, int
       if (r < kb) {
         const int kz = min(jb, ka + 16);
         if (q + 1 < item.i) {
+          // an earlier tile, straight from the panel: all 16 loads issued
+          // before the products
           const int row = i0 + r;
-          for (int k = ka; k < kz; ++k) {
-            const T l = TRANS ? lval<T, RM>(P, d, j0 + k, row) : lval<T, RM>(P, d, row, j0 + k);
+          T lv[16];
+#pragma unroll
+          for (int kk = 0; kk < 16; ++kk) {
+            const int k = ka + kk;
+            lv[kk] = k < kz ? (TRANS ? lval<T, RM>(P, d, j0 + k, row) : lval<T, RM>(P, d, row, j0 + k)) : T(0);
+          }
+#pragma unroll
+          for (int kk = 0; kk < 16; ++kk) {
+            if (ka + kk >= kz) break;
 #pragma unroll
             for (int m = 0; m < kSolveChunk; ++m)
-              if (m < nrhs) acc[m] += l * ys[k + m * kSub];
+              if (m < nrhs) acc[m] += lv[kk] * ys[ka + kk + m * kSub];
           }
         } else {
           for (int k = ka; k < kz; ++k) {
@@ -212,7 +225,7 @@ k_sv_tri(const SnodeDev* __restrict__ sn, const TriItem* __restrict__ items, int
       const int rr = e % kb, m = e / kb;
       const T* pr = red + m * 4 * kSub + rr;
       const T sum = ((pr[0] + pr[kSub]) + pr[2 * kSub]) + pr[3 * kSub];
-      yi[rr + m * kSub] = Y[d.f + i0 + rr + (int64_t)m * n] - sum;
+      yi[rr + m * kSub] -= sum;
     }
     __syncthreads();
     // substitution: 16 lanes per right-hand side, lane q holds rows q + 16a;
@@ -268,9 +281,11 @@ k_sv_tri(const SnodeDev* __restrict__ sn, const TriItem* __restrict__ items, int
         }
       }
     }
-    __threadfence();
-    __syncthreads();
-    if (tid == 0) st_release(flags + item.fbase + blk, tgt);
+    __syncthreads();   // every thread's rows of Y are written (CTA order) ...
+    if (tid == 0) {
+      __threadfence();  // ... and made visible at GPU scope before the flag
+      st_release(flags + item.fbase + blk, tgt);
+    }
   }
   // the last CTA to finish advances the epoch for the next launch
   __syncthreads();
@@ -293,7 +308,7 @@ __global__ void __launch_bounds__(kT)
 k_sv_gemv(const SnodeDev* __restrict__ sn, const TileTask* __restrict__ tasks, const T* __restrict__ L,
           const T* __restrict__ Y, int n, T* __restrict__ W, int nrhs) {
   constexpr int KC = 256;
-  __shared__ T yk[KC * kSolveChunk];
+  __shared__ __align__(16) T yk[KC * kSolveChunk];
   const TileTask t = tasks[blockIdx.x];
   const SnodeDev d = sn[t.J];
   const int b = d.len - d.s;
@@ -332,6 +347,10 @@ k_sv_gemv(const SnodeDev* __restrict__ sn, const TileTask* __restrict__ tasks, c
       }
     }
   } else {
+    // binary32 row-major panels: a lane covers 4 consecutive columns (one
+    // 16-byte load; rows start 32-byte aligned), 128 columns per warp pass, two
+    // passes per staged chunk: 8 loads of 16 bytes in flight per lane
+    static_assert(sizeof(T) == 4, "row-major panels are binary32");
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     T acc[4][kSolveChunk];   // 4 rows per warp, 32 rows per task
 #pragma unroll
@@ -345,16 +364,37 @@ k_sv_gemv(const SnodeDev* __restrict__ sn, const TileTask* __restrict__ tasks, c
         const int i = q % kn, r = q / kn;
         yk[i + r * KC] = Y[d.f + kc + i + (int64_t)r * n];
       }
+      for (int q = kn + threadIdx.x; q < KC; q += blockDim.x)   // zero tail: full 4-column groups
+        for (int r = 0; r < nrhs; ++r) yk[q + r * KC] = T(0);
       __syncthreads();
+      float4 lv[4][2];
 #pragma unroll
       for (int m = 0; m < 4; ++m) {
         const int u = t.r0 + warp * 4 + m;
-        if (u >= b) continue;
-        for (int k = lane; k < kn; k += 32) {
-          const T l = lval<T, RM>(P, d, d.s + u, kc + k);
+        const float* row = reinterpret_cast<const float*>(P) + (int64_t)(d.s + u) * d.ld + kc;
 #pragma unroll
-          for (int r = 0; r < kSolveChunk; ++r)
-            if (r < nrhs) acc[m][r] += l * yk[k + r * KC];
+        for (int h = 0; h < 2; ++h) {
+          const int k = 4 * lane + 128 * h;
+          if (u < b && k + 3 < kn) {
+            lv[m][h] = *reinterpret_cast<const float4*>(row + k);
+          } else {
+            lv[m][h].x = (u < b && k < kn) ? row[k] : 0.f;
+            lv[m][h].y = (u < b && k + 1 < kn) ? row[k + 1] : 0.f;
+            lv[m][h].z = (u < b && k + 2 < kn) ? row[k + 2] : 0.f;
+            lv[m][h].w = 0.f;
+          }
+        }
+      }
+#pragma unroll
+      for (int h = 0; h < 2; ++h) {
+        const int k = 4 * lane + 128 * h;
+#pragma unroll
+        for (int r = 0; r < kSolveChunk; ++r) {
+          if (r >= nrhs) break;
+          const float4 y4 = *reinterpret_cast<const float4*>(reinterpret_cast<const float*>(yk) + k + r * KC);
+#pragma unroll
+          for (int m = 0; m < 4; ++m)
+            acc[m][r] += lv[m][h].x * y4.x + lv[m][h].y * y4.y + lv[m][h].z * y4.z + lv[m][h].w * y4.w;
         }
       }
     }
