@@ -99,7 +99,19 @@ typedef struct chol_options {
                            /* CUDA graph on the first chol_factor and replayed by */
                            /* the later ones (values are copied into the handle   */
                            /* first); 0 = direct launches (default)               */
+  int32_t update_mode;     /* CHOL_UPDATE_RL (default): each supernode's update  */
+                           /* matrix U_J = L_RJ L_RJ^T is formed in a workspace   */
+                           /* and assembled into its ancestors by relative index  */
+                           /* (Sec. II-A, RL), bitwise reproducible.              */
+                           /* CHOL_UPDATE_RLB: the update products are subtracted */
+                           /* straight into the ancestors' panels block by block  */
+                           /* (the right-looking blocked variant, Sec. II-B): no  */
+                           /* update workspace, atomic adds, so results agree to  */
+                           /* rounding but not bit for bit between runs.         */
+                           /* CHOL_PREC_FP64 and persistent = 0 only.            */
 } chol_options;
+
+enum { CHOL_UPDATE_RL = 0, CHOL_UPDATE_RLB = 1 };
 
 /* Fill *opt with the defaults. */
 void chol_default_options(chol_options* opt);

@@ -28,6 +28,8 @@ CHOL_PREC_FP64 = 0
 CHOL_PREC_FP32 = 1
 CHOL_PREC_TF32 = 2
 CHOL_PREC_BF16 = 3
+CHOL_UPDATE_RL = 0
+CHOL_UPDATE_RLB = 1
 
 EXPORTED = ["chol_default_options", "chol_analyze", "chol_factor", "chol_solve", "chol_solve_noalloc",
             "chol_solve_refine", "chol_logdet", "chol_analyze_batch", "chol_logdet_batch", "chol_autotune",
@@ -45,7 +47,7 @@ class chol_options(C.Structure):
                 ("small_max_panel", C.c_int32), ("block_cols", C.c_int32),
                 ("device_mem_cap", C.c_int64), ("merge_growth", C.c_double),
                 ("small_max_rows", C.c_int32), ("persistent", C.c_int32), ("pivot_tau", C.c_double),
-                ("static_pivot", C.c_int32), ("use_graph", C.c_int32)]
+                ("static_pivot", C.c_int32), ("use_graph", C.c_int32), ("update_mode", C.c_int32)]
 
 
 class chol_info(C.Structure):

@@ -420,6 +420,13 @@ int build_si_plan(chol_handle* h) {
   if (D->si_plan) return CHOL_OK;
   SiPlan* pl = new SiPlan();
   const double* L = D->L;
+  // Z_RR of a level lives in the update workspace, at U_J's place; an RLB
+  // handle has none, so it gets its own
+  if (h->update_doubles < h->update_doubles_rl && !D->zrr_ws) {
+    const int rz = chol_dalloc(h, (void**)&D->zrr_ws, sizeof(double) * (size_t)h->update_doubles_rl);
+    if (rz) { delete pl; return rz; }
+  }
+  double* ZRR = D->zrr_ws ? D->zrr_ws : D->U;
   double* Z = D->Zp;
   int64_t tmax = 0, hmax = 0, wmax = 0;
   // per-level offsets of T (s^2), Uhat (b s) and W (s^2 / 2)
@@ -523,7 +530,7 @@ int build_si_plan(chol_handle* h) {
       const SnodeDev& d = h->snodes[J];
       const int b = d.len - d.s;
       if (b > 0)
-        gs.push_back(mk(D->U + d.uoff, 1, b, D->Uh + hoff[J], 1, b, Z + d.loff + d.s, 1, d.ld, b, d.s, b, -1.0, 0.0, 2,
+        gs.push_back(mk(ZRR + d.uoff, 1, b, D->Uh + hoff[J], 1, b, Z + d.loff + d.s, 1, d.ld, b, d.s, b, -1.0, 0.0, 2,
                         0, 0));
     }
     sl.zrj = emit_group(*pl, gs, D->sms);
@@ -593,7 +600,7 @@ int selinv(chol_handle* h, cudaStream_t st) {
     if (sl.pair_n > 0) {
       KScope ks(h, CHOL_K_SELINV_GATHER, st, 0.0, 0.0);
       k_gather_zrr_level<<<sl.pair_n, kGT, sizeof(int32_t) * (h->max_len + kGatherRows), st>>>(pl->d_pairs + sl.pair_b, D->sn,
-                                                                                   D->rows, D->Zp, D->U);
+                                                                                   D->rows, D->Zp, D->zrr_ws ? D->zrr_ws : D->U);
     }
     {
       KScope ks(h, CHOL_K_SELINV_GEMM, st, sl.gemm_flops, 0.0);

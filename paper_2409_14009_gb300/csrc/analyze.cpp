@@ -32,6 +32,7 @@ extern "C" void chol_default_options(chol_options* opt) {
   opt->static_pivot = 0;
   opt->persistent = 0;
   opt->use_graph = 0;
+  opt->update_mode = CHOL_UPDATE_RL;
 }
 
 namespace {
@@ -67,6 +68,10 @@ int validate(int32_t n, const int64_t* colptr, const int32_t* rowind, const int3
     if (opt->small_max_cols < 1 || opt->small_max_panel < 1 || opt->small_max_panel > 24576) return -5;
     if (opt->persistent != 0 && opt->persistent != 1) return -5;
     if (opt->use_graph != 0 && opt->use_graph != 1) return -5;
+    if (opt->update_mode != CHOL_UPDATE_RL && opt->update_mode != CHOL_UPDATE_RLB) return -5;
+    if (opt->update_mode == CHOL_UPDATE_RLB &&
+        (opt->precision != CHOL_PREC_FP64 || opt->persistent || opt->small_max_rows > kRlbSmallRows))
+      return -5;
     if (opt->block_cols < 8 || opt->block_cols > 64) return -5;
     if (opt->device_mem_cap < 0) return -5;
     if (!(opt->merge_growth >= 0.0) || opt->merge_growth > 100.0) return -5;
@@ -406,6 +411,9 @@ void build(chol_handle* h, const int64_t* colptr, const int32_t* rowind) {
     }
   }
   const int64_t np = (int64_t)h->rel_J.size();
+  h->pair_beg.assign(ns + 1, 0);
+  for (int64_t p = 0; p < np; ++p) h->pair_beg[h->rel_J[p] + 1]++;
+  for (int32_t J = 0; J < ns; ++J) h->pair_beg[J + 1] += h->pair_beg[J];
   h->relind_len = 0;
   for (int64_t p = 0; p < np; ++p)
     h->relind_len += (h->snodes[h->rel_J[p]].len - h->snodes[h->rel_J[p]].s) - h->rel_c0[p];
@@ -431,6 +439,7 @@ void build(chol_handle* h, const int64_t* colptr, const int32_t* rowind) {
   h->asm_tasks.clear(); h->asm_segs.clear();
   h->n_small = h->n_large = 0;
   h->update_doubles = 0;
+  h->update_doubles_rl = 0;
   h->w_rows_max = 0;
   for (int32_t lv = 0; lv < h->nlevels; ++lv) {
     LevelPlan& P = h->levels[lv];
@@ -465,7 +474,8 @@ void build(chol_handle* h, const int64_t* colptr, const int32_t* rowind) {
     P.small_n = (int32_t)h->small_list.size() - P.small_b;
     P.u_doubles = uo;
     P.w_rows = wo;
-    h->update_doubles = std::max(h->update_doubles, uo);
+    h->update_doubles_rl = std::max(h->update_doubles_rl, uo);
+    if (h->opt.update_mode == CHOL_UPDATE_RL) h->update_doubles = std::max(h->update_doubles, uo);
     h->w_rows_max = std::max(h->w_rows_max, wo);
     int32_t maxs = 0;
     for (int32_t J : large) maxs = std::max(maxs, h->snodes[J].s);

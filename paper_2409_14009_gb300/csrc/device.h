@@ -26,6 +26,9 @@ struct DeviceState {
   AsmTask* asm_tasks = nullptr;
   AsmSeg* asm_segs = nullptr;
   TriItemHost* tri = nullptr;   // solve: diagonal-triangle items
+  int4* rlb_pairs = nullptr;    // RLB: (K, c0, c1, -) of every (J, K) pair, J-major
+  int32_t* rlb_pbeg = nullptr;  // RLB: first pair of every supernode
+  double* zrr_ws = nullptr;     // adjoint: Z_RR workspace when there is no update workspace (RLB)
   int32_t* tri_flags = nullptr; // solve: one flag per diagonal block (zeroed once)
   int32_t* tri_sync = nullptr;  // solve: {epoch, CTAs done} of the triangle launches
   int32_t* sv_err = nullptr;    // solve: set when a bounded wait gave up

@@ -73,6 +73,16 @@ __device__ void dense_chol_smem(double* P, int ld, int len, int s, int fcol, int
   __syncthreads();
 }
 
+// Position of global row `key` in the sorted row structure rk[0, len).
+__device__ __forceinline__ int row_position(const int32_t* __restrict__ rk, int len, int32_t key) {
+  int lo = 0, hi = len;
+  while (lo < hi) {
+    const int mid = (lo + hi) >> 1;
+    if (rk[mid] < key) lo = mid + 1; else hi = mid;
+  }
+  return lo;
+}
+
 __global__ void k_status_init(int* status) { *status = INT_MAX; }
 
 __global__ void k_scatter(const double* __restrict__ vals, const int64_t* __restrict__ amap,
@@ -114,6 +124,48 @@ k_small(const SnodeDev* __restrict__ sn, const int32_t* __restrict__ list, doubl
         double* __restrict__ U, int* status) {
   extern __shared__ double P[];
   small_body(sn[list[blockIdx.x]], L, U, status, P);
+}
+
+// RLB form of the one-CTA kernel: after the factorization in shared memory,
+// every entry (u, c), u >= c, of L_RJ L_RJ^T is subtracted straight from the
+// ancestor owning column c, pair by pair (row positions found once per pair).
+__global__ void __launch_bounds__(kSmallThreads)
+k_small_rlb(const SnodeDev* __restrict__ sn, const int32_t* __restrict__ list, const int4* __restrict__ pairs,
+            const int32_t* __restrict__ pbeg, const int32_t* __restrict__ rows, double* __restrict__ L,
+            int* status) {
+  extern __shared__ double P[];
+  __shared__ int32_t pos[kRlbSmallRows];
+  const int32_t J = list[blockIdx.x];
+  const SnodeDev d = sn[J];
+  const int len = d.len, s = d.s, b = len - s;
+  double* G = L + d.loff;
+  for (int c = 0; c < s; ++c)
+    for (int r = threadIdx.x; r < len; r += blockDim.x) P[r + c * len] = G[r + (int64_t)c * d.ld];
+  dense_chol_smem(P, len, len, s, d.f, status);
+  for (int c = 0; c < s; ++c)
+    for (int r = c + threadIdx.x; r < len; r += blockDim.x) G[r + (int64_t)c * d.ld] = P[r + c * len];
+  if (b <= 0) return;
+  const double* R = P + s;   // row u of L_RJ is R[u + k*len]
+  const int32_t* rj = rows + d.roff + s;
+  for (int p = pbeg[J]; p < pbeg[J + 1]; ++p) {
+    const int4 pr = pairs[p];
+    const SnodeDev dk = sn[pr.x];
+    __syncthreads();
+    for (int u = pr.y + threadIdx.x; u < b; u += blockDim.x)
+      pos[u - pr.y] = row_position(rows + dk.roff, dk.len, rj[u]);
+    __syncthreads();
+    // entries of columns [c0, c1), rows c..b-1: flat walk
+    const int64_t total = (int64_t)(pr.z - pr.y) * b - ((int64_t)pr.z * (pr.z - 1) - (int64_t)pr.y * (pr.y - 1)) / 2;
+    int c = pr.y;
+    int64_t cstart = 0;   // flat index of (c, c)
+    for (int64_t q = threadIdx.x; q < total; q += blockDim.x) {
+      while (q >= cstart + (b - c)) { cstart += b - c; ++c; }
+      const int u = c + (int)(q - cstart);
+      double acc = 0.0;
+      for (int k = 0; k < s; ++k) acc += R[u + k * len] * R[c + k * len];
+      atomicAdd(L + dk.loff + pos[u - pr.y] + (int64_t)(rj[c] - dk.f) * dk.ld, -acc);
+    }
+  }
 }
 
 // Blocked path, step k0: factor the kb x kb (kb <= 64) diagonal block of each
@@ -196,17 +248,14 @@ k_trsm(const SnodeDev* __restrict__ sn, const TileTask* __restrict__ tasks, int 
 // Only entries with (row + rdiag >= col) are written (lower triangle of the
 // global matrix). SUB: C -= A B^T, else C = A B^T.
 // ---------------------------------------------------------------------------
-template <bool SUB>
-__device__ __forceinline__ void gemm_nt_tile(const double* __restrict__ A, int64_t lda,
-                                             const double* __restrict__ B, int64_t ldb, int K,
-                                             double* __restrict__ C, int64_t ldc, int M, int N,
-                                             int rdiag) {
+__device__ __forceinline__ void gemm_nt_core(const double* __restrict__ A, int64_t lda,
+                                             const double* __restrict__ B, int64_t ldb, int K, int M, int N,
+                                             double (&acc)[4][4]) {
   constexpr int KC = 16;
   __shared__ double As[KC][kTile];
   __shared__ double Bs[KC][kTile];
   const int tid = threadIdx.x;
   const int tx = tid & 15, ty = tid >> 4;
-  double acc[4][4];
 #pragma unroll
   for (int i = 0; i < 4; ++i)
 #pragma unroll
@@ -235,6 +284,16 @@ __device__ __forceinline__ void gemm_nt_tile(const double* __restrict__ A, int64
     }
     __syncthreads();
   }
+}
+
+template <bool SUB>
+__device__ __forceinline__ void gemm_nt_tile(const double* __restrict__ A, int64_t lda,
+                                             const double* __restrict__ B, int64_t ldb, int K,
+                                             double* __restrict__ C, int64_t ldc, int M, int N,
+                                             int rdiag) {
+  double acc[4][4];
+  gemm_nt_core(A, lda, B, ldb, K, M, N, acc);
+  const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
 #pragma unroll
   for (int i = 0; i < 4; ++i)
 #pragma unroll
@@ -271,6 +330,51 @@ k_syrk(const SnodeDev* __restrict__ sn, const TileTask* __restrict__ tasks,
   const double* R = L + d.loff + d.s;
   gemm_nt_tile<false>(R + t.r0, d.ld, R + t.c0, d.ld, d.s, U + d.uoff + t.r0 + (int64_t)t.c0 * b, b,
                       min(kTile, b - t.r0), min(kTile, b - t.c0), t.r0 - t.c0);
+}
+
+// RLB (Sec. II-B): the tile (rows r0.., columns c0..) of L_RJ L_RJ^T is
+// subtracted straight from the ancestors' panels instead of being stored. The
+// tile's columns fall into the (J, K) pairs of J (runs of J's rows owned by one
+// ancestor K, in column order); for each pair the tile's rows are located in
+// struct(K) (J's rows from the pair's first on all lie in it, and a run of
+// consecutive global rows lands on consecutive positions), then every entry
+// with row >= column is subtracted with an atomic add. Supernodes of a level
+// update shared ancestors concurrently, so the order of the additions, and the
+// rounding, varies from run to run.
+__global__ void __launch_bounds__(kGemmThreads)
+k_syrk_rlb(const SnodeDev* __restrict__ sn, const TileTask* __restrict__ tasks, const int4* __restrict__ pairs,
+           const int32_t* __restrict__ pbeg, const int32_t* __restrict__ rows, double* __restrict__ L) {
+  __shared__ int32_t pos[kTile];
+  const TileTask t = tasks[blockIdx.x];
+  const SnodeDev d = sn[t.J];
+  const int b = d.len - d.s;
+  const double* R = L + d.loff + d.s;
+  const int M = min(kTile, b - t.r0), N = min(kTile, b - t.c0);
+  double acc[4][4];
+  gemm_nt_core(R + t.r0, d.ld, R + t.c0, d.ld, d.s, M, N, acc);
+  const int32_t* rj = rows + d.roff + d.s;
+  const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
+  for (int p = pbeg[t.J]; p < pbeg[t.J + 1]; ++p) {
+    const int4 pr = pairs[p];   // (K, first column, end column, -)
+    if (pr.z <= t.c0) continue;
+    if (pr.y >= t.c0 + N) break;
+    const SnodeDev dk = sn[pr.x];
+    __syncthreads();   // the previous pair is done with pos
+    for (int i = threadIdx.x; i < M; i += blockDim.x) {
+      const int u = t.r0 + i;
+      pos[i] = u >= pr.y ? row_position(rows + dk.roff, dk.len, rj[u]) : -1;
+    }
+    __syncthreads();
+#pragma unroll
+    for (int i = 0; i < 4; ++i)
+#pragma unroll
+      for (int j = 0; j < 4; ++j) {
+        const int r = ty + 16 * i, c = tx + 16 * j;
+        const int u = t.r0 + r, cg = t.c0 + c;
+        if (r < M && c < N && u >= cg && cg >= pr.y && cg < pr.z)
+          atomicAdd(L + dk.loff + pos[r] + (int64_t)(rj[cg] - dk.f) * dk.ld, -acc[i][j]);
+      }
+  }
 }
 
 // Assembly of one task: for every segment (in J order) the rows ua..ub-1 of
@@ -527,7 +631,7 @@ void chol_device_free(chol_handle* h) {
   if (D->device >= 0) cudaSetDevice(D->device);
   chol_adjoint_free(h);
   void* ptrs[] = {D->L, D->U, D->sn, D->rows, D->amap, D->small_list, D->potrf_list,
-                  D->level_snodes, D->trsm, D->gemm, D->syrk, D->asm_tasks, D->asm_segs, D->tri,
+                  D->level_snodes, D->trsm, D->gemm, D->syrk, D->asm_tasks, D->asm_segs, D->tri, D->rlb_pairs, D->rlb_pbeg, D->zrr_ws,
                   D->tri_flags, D->tri_sync, D->sv_err, D->bpanel, D->gemv, D->bpart, D->bred, D->P32, D->plevels, D->vals, D->sys_snode, D->sys_out,
                   D->ssmall, D->Zp, D->Tw, D->Ww, D->Uh, D->a_col, D->a_row, D->adj_xb, D->perm, D->status, D->part, D->scalar_dev, D->Y, D->W,
                   D->mx_diagpos, D->mx_aij, D->mx_d, D->mx_fallbacks, D->csr_ptr, D->csr_col, D->csr_src,
@@ -605,6 +709,12 @@ int chol_device_ensure(chol_handle* h) {
   if ((rc = upload(h, &D->asm_tasks, h->asm_tasks))) return fail(rc);
   if ((rc = upload(h, &D->asm_segs, h->asm_segs))) return fail(rc);
   if ((rc = upload(h, &D->tri, h->tri_items))) return fail(rc);
+  if (h->opt.update_mode == CHOL_UPDATE_RLB) {
+    std::vector<int4> pr(h->rel_J.size());
+    for (size_t p = 0; p < pr.size(); ++p) pr[p] = make_int4(h->rel_K[p], h->rel_c0[p], h->rel_c1[p], 0);
+    if ((rc = upload(h, &D->rlb_pairs, pr))) return fail(rc);
+    if ((rc = upload(h, &D->rlb_pbeg, h->pair_beg))) return fail(rc);
+  }
   if ((rc = chol_dalloc(h, (void**)&D->tri_flags, sizeof(int32_t) * (size_t)std::max(h->tri_nflags, 1)))) return fail(rc);
   if ((rc = chol_dalloc(h, (void**)&D->tri_sync, sizeof(int32_t) * 2))) return fail(rc);
   if ((rc = chol_dalloc(h, (void**)&D->sv_err, sizeof(int32_t)))) return fail(rc);
@@ -666,10 +776,15 @@ int enqueue_factor_fp64(chol_handle* h, const double* values, cudaStream_t st) {
     st = D->hstream;
   }
   for (const LevelPlan& P : h->levels) {
+    const bool rlb = h->opt.update_mode == CHOL_UPDATE_RLB;
     if (P.small_n > 0) {
       KScope ks(h, CHOL_K_SMALL, st, P.small_flops, P.small_bytes);
-      k_small<<<P.small_n, kSmallThreads, sizeof(double) * P.small_max_panel, st>>>(
-          D->sn, D->small_list + P.small_b, D->L, D->U, D->status);
+      if (rlb)
+        k_small_rlb<<<P.small_n, kSmallThreads, sizeof(double) * P.small_max_panel, st>>>(
+            D->sn, D->small_list + P.small_b, D->rlb_pairs, D->rlb_pbeg, D->rows, D->L, D->status);
+      else
+        k_small<<<P.small_n, kSmallThreads, sizeof(double) * P.small_max_panel, st>>>(
+            D->sn, D->small_list + P.small_b, D->L, D->U, D->status);
     }
     // One-step lookahead: the trailing tiles of step k other than the next
     // block column ("rest") run on the side stream, beside the POTRF and TRSM
@@ -717,9 +832,13 @@ int enqueue_factor_fp64(chol_handle* h, const double* values, cudaStream_t st) {
     if (rest_pending) CHOL_CUDA_TRY(cudaStreamWaitEvent(st, D->lev[1], 0));   // join before SYRK
     if (P.syrk_n > 0) {
       KScope ks(h, CHOL_K_SYRK, st, P.syrk_flops, 8.0 * kTile * kTile * P.syrk_n);
-      k_syrk<<<P.syrk_n, kGemmThreads, 0, st>>>(D->sn, D->syrk + P.syrk_b, D->L, D->U);
+      if (rlb)
+        k_syrk_rlb<<<P.syrk_n, kGemmThreads, 0, st>>>(D->sn, D->syrk + P.syrk_b, D->rlb_pairs, D->rlb_pbeg, D->rows,
+                                                       D->L);
+      else
+        k_syrk<<<P.syrk_n, kGemmThreads, 0, st>>>(D->sn, D->syrk + P.syrk_b, D->L, D->U);
     }
-    if (P.asm_n + P.asmw_n > 0) {
+    if (!rlb && P.asm_n + P.asmw_n > 0) {
       KScope ks(h, CHOL_K_ASSEMBLE, st, P.asm_entries, 24.0 * P.asm_entries);
       ks.launches((P.asm_n > 0) + (P.asmw_n > 0));
       if (P.asm_n > 0)

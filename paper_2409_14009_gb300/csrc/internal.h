@@ -121,6 +121,8 @@ struct chol_handle {
   double flops = 0.0, flops_stored = 0.0;
   // (J, K) pairs: J updates ancestor K through U_J columns [c0, c1) (J ascending, K ascending)
   std::vector<int32_t> rel_J, rel_K, rel_c0, rel_c1;
+  std::vector<int32_t> pair_beg;    // first (J, K) pair of every supernode (pairs are J-major)
+  int64_t update_doubles_rl = 0;    // the RL update workspace (also sizes the Z_RR gathers)
   int64_t relind_len = 0;           // sum over pairs of (b_J - c0)
   int32_t max_len = 0;              // longest struct(J)
   // schedule
@@ -160,5 +162,6 @@ constexpr int kAsmWarpEntries = 4096;  // ... and this many entries over all seg
 constexpr int kTrsmRowsHost = 32; // TRSM task height (rows)
 constexpr int kSolveSmallCols = 32;   // supernodes solved by one warp: s <= 32 and
 constexpr int kSolveSmallRows = 256;  // len <= 256
+constexpr int kRlbSmallRows = 1024;   // RLB: rows of a supernode on the one-CTA kernel (small_max_rows cap)
 
 void chol_device_free(chol_handle* h);  // CUDA side

@@ -28,6 +28,25 @@ def test_exports_every_declared_symbol():
         assert nm in P.EXPORTED, nm
 
 
+def test_update_mode_validation():
+    P = chol()
+    A = np.eye(3) * 2.0
+    cp, ri, _ = lower_csc_from_dense(A)
+    o = P.chol_default_options()
+    assert o.update_mode == P.CHOL_UPDATE_RL
+    o.update_mode = 2
+    assert P.chol_analyze(3, cp, ri, None, o)[0] == -5
+    o.update_mode = P.CHOL_UPDATE_RLB
+    rc, h = P.chol_analyze(3, cp, ri, None, o)
+    assert rc == 0
+    P.chol_destroy(h)
+    o.precision = P.CHOL_PREC_FP32          # RLB is binary64 only
+    assert P.chol_analyze(3, cp, ri, None, o)[0] == -5
+    o.precision = P.CHOL_PREC_FP64
+    o.persistent = 1                        # ... and not in the persistent launch
+    assert P.chol_analyze(3, cp, ri, None, o)[0] == -5
+
+
 def test_strerror_and_defaults():
     P = chol()
     assert "success" in P.chol_strerror(0)
