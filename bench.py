@@ -308,6 +308,28 @@ def batch_run(args, P, gridgen, torch, dev):
     return out
 
 
+def rlb_run(args, P, torch, dev, p, b, vals, flops, rl_factor_ms, rl_u_doubles):
+    """The right-looking blocked update (no update workspace) on the bench
+    workload: FP64 factor + 8-RHS solve, timed like the RL factor."""
+    opt = P.chol_default_options()
+    opt.merge_growth = args.merge
+    opt.update_mode = P.CHOL_UPDATE_RLB
+    S = P.SparseCholesky(p.n, p["colptr"], p["rowind"], p["perm"], opt)
+    st = torch.cuda.current_stream()
+    B = torch.as_tensor(np.ascontiguousarray(b.T), device=dev).t()
+    X = torch.empty_like(B)
+    S.factor(vals)
+    fms, _ = _timed(torch, st, lambda: S.factor(vals), 3)
+    X.copy_(B)
+    S.solve_(X)
+    torch.cuda.synchronize()
+    eta = backward_error(p, b, X.cpu().numpy())
+    out = {"factor_ms": fms, "factor_gflops": flops / (fms * 1e-3) / 1e9, "backward_error": float(eta),
+           "rl_factor_ms": rl_factor_ms, "update_workspace_bytes_saved": int(rl_u_doubles * 8)}
+    S.close()
+    return out
+
+
 def adjoint_run(args, P, gridgen, torch, dev):
     """Differentiable solve: 3D 48^3 7-point Dirichlet Laplacian (n=110,592),
     conductances log-uniform in [1e-2, 1e2], 16 RHS; loss = sum w^T x + log det A.
@@ -432,6 +454,8 @@ def run_ours(args, rank, world, local_rank):
                                                          factor_ms, solve_ms)
     batch = None if args.no_batch else batch_run(args, P, gridgen, torch, dev)
     adjoint = None if args.no_adjoint else adjoint_run(args, P, gridgen, torch, dev)
+    rlb = None if args.no_rlb else rlb_run(args, P, torch, dev, p, b, vals, flops, factor_ms,
+                                           S.info.update_doubles)
     ms, e2e_ms = max_over_ranks(dist, [ms, e2e_ms], dev)
     if rank == 0:
         dom = max(("gemm", "syrk"), key=lambda k: stats[k]["ms"])
@@ -466,7 +490,7 @@ def run_ours(args, rank, world, local_rank):
                         "d2h_bytes_per_step": int(hx.numel() * 8)},
                 "gpu_launches": launches // max(args.steps, 1) * args.steps,
                 "roofline": roof, "cpu_baseline": cpu, "clocks": clk.summary(),
-                "mixed_vs_fp64": mixed, "batch": batch, "adjoint": adjoint}
+                "mixed_vs_fp64": mixed, "batch": batch, "adjoint": adjoint, "rlb": rlb}
         print(json.dumps(line), flush=True)
     S.close()
     if dist:
@@ -487,6 +511,7 @@ def main():
     ap.add_argument("--no-batch", action="store_true", help="skip the 2,000-system batch")
     ap.add_argument("--batch-count", type=int, default=2000)
     ap.add_argument("--no-adjoint", action="store_true", help="skip the differentiable-solve workload")
+    ap.add_argument("--no-rlb", action="store_true", help="skip the right-looking blocked (RLB) factor")
     ap.add_argument("--workload", default="3d64", choices=["3d64", "3d48"],
                     help="3d64 is the benchmark; 3d48 is the smaller case used for ncu captures")
     ap.add_argument("--merge", type=float, default=0.1,
