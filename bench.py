@@ -269,9 +269,10 @@ def batch_run(args, P, gridgen, torch, dev):
     vals = torch.as_tensor(bd["values"], device=dev)
     out = {"workload": "batch of %d 2D 5-point Laplacians, sides U{16..96}, n_total=%d, 1 RHS each"
                        % (len(probs), bd.n)}
-    for prec, name in ((0, "fp64"), (1, "fp32")):
+    for prec, name, mode in ((0, "fp64", 0), (0, "fp64_rlb", 1), (1, "fp32", 0)):
         opt = P.chol_default_options()
         opt.precision = prec
+        opt.update_mode = mode   # fp64_rlb: updates straight into the ancestors, no assembly pass
         opt.small_max_cols, opt.small_max_panel, opt.small_max_rows = 160, 24576, 512
         t0 = time.perf_counter()
         rc, h = P.chol_analyze_batch(len(offs) - 1, offs, bd["colptr"], bd["rowind"], bd["perm"], opt)
@@ -283,7 +284,8 @@ def batch_run(args, P, gridgen, torch, dev):
         info = P.chol_get_info(h)
         B = torch.as_tensor(np.ascontiguousarray(b.T), device=dev).t()
         X = torch.zeros_like(B)
-        fms, _ = _timed(torch, st, lambda: P.chol_factor(h, vals, st), 5)
+        fms, rcs = _timed(torch, st, lambda: P.chol_factor(h, vals, st), 5)
+        assert rcs == 0, rcs
         if prec == 0:
             def solve():
                 X.copy_(B)

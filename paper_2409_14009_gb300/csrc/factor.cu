@@ -740,6 +740,8 @@ int chol_device_ensure(chol_handle* h) {
       return fail(CHOL_ECUDA);
     if (cudaFuncSetAttribute(k_small, cudaFuncAttributeMaxDynamicSharedMemorySize, 24576 * 8) != cudaSuccess)
       return fail(CHOL_ECUDA);
+    if (cudaFuncSetAttribute(k_small_rlb, cudaFuncAttributeMaxDynamicSharedMemorySize, 24576 * 8) != cudaSuccess)
+      return fail(CHOL_ECUDA);
     attrs_done = true;
   }
   return CHOL_OK;
@@ -761,7 +763,7 @@ int enqueue_factor_fp64(chol_handle* h, const double* values, cudaStream_t st) {
     k_gather_src<<<grid1d(m, 256), 256, 0, st>>>(values, D->csr_src, m, D->csr_val);
   }
   if (h->opt.persistent) {
-    if (h->n_large > 0) return CHOL_ENOTSUP;
+    if (h->n_large > 0 || h->opt.update_mode != CHOL_UPDATE_RL) return CHOL_ENOTSUP;
     double fl = 0.0, by = 0.0;
     for (const LevelPlan& P : h->levels) { fl += P.small_flops; by += P.small_bytes; }
     KScope ks(h, CHOL_K_SMALL, st, fl, by);
@@ -1015,7 +1017,7 @@ extern "C" int chol_autotune(chol_handle* h, const double* values, void* stream)
   cudaStream_t st = (cudaStream_t)stream;
   struct Cand { int persistent, graph, threads, ctas; };
   std::vector<Cand> cands = {{0, 0, 128, 0}, {0, 1, 128, 0}};
-  if (h->n_large == 0)
+  if (h->n_large == 0 && h->opt.update_mode == CHOL_UPDATE_RL)   // the persistent kernel assembles through U
     for (int t : {128, 256})
       for (int c : {1, 2, 4, 0}) cands.push_back({1, 1, t, c});
   float best = 1e30f;

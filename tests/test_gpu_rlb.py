@@ -82,3 +82,32 @@ def test_rlb_selected_inverse_matches_rl():
         finally:
             P.chol_destroy(h)
     assert np.max(np.abs(zs[0] - zs[1])) <= 1e-10 * np.max(np.abs(zs[0]))
+
+
+def test_rlb_batch_with_large_small_panels_and_graph():
+    # one-CTA supernodes with panels above the default 48 KB of shared memory,
+    # direct launches and graph replay
+    import torch
+    P = chol()
+    probs = gridgen.batch_2d(count=30, kmin=20, kmax=60, seed=11)
+    bd = gridgen.block_diagonal(probs)
+    offs = bd["meta"]["offsets"].astype(np.int32)
+    b = gridgen.rhs_uniform(bd.n, 1, seed=2)
+    ref = oracle.reference(bd, b)
+    for graph in (0, 1):
+        o = _opts(160, 24576, 64, small_rows=512)
+        o.use_graph = graph
+        rc, h = P.chol_analyze_batch(len(offs) - 1, offs, bd["colptr"], bd["rowind"], bd["perm"], o)
+        assert rc == 0
+        try:
+            st = torch.cuda.current_stream()
+            vals = to_dev(bd["values"])
+            for _ in range(2):   # capture, then replay
+                assert P.chol_factor(h, vals, st) == 0
+            X = colmajor(b)
+            assert P.chol_solve(h, X, 1, st) == 0
+            torch.cuda.synchronize()
+            x = X.cpu().numpy()
+            assert np.max(np.abs(x - ref["x"])) <= 1e-10 * np.max(np.abs(ref["x"]))
+        finally:
+            P.chol_destroy(h)
