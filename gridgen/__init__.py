@@ -313,6 +313,39 @@ def elasticity_27pt(k: int, lo: float = 1.0, hi: float = 1e6, seed: int = 3) -> 
                    meta=dict(kind="elasticity_27pt", k=k, lo=lo, hi=hi, seed=seed))
 
 
+def irregular_3d(k: int, keep: float = 0.35, seed: int = 12, lo: float = 0.1, hi: float = 10.0,
+                 shift: float = 1e-2) -> Problem:
+    """A Laplacian with irregular structure on a k^3 grid of nodes: every
+    27-point edge is kept with probability `keep` (one uniform draw per edge,
+    edge order as in elasticity_27pt), a kept edge gets a weight log-uniform in
+    [lo, hi], A_ii = sum of incident weights + shift (SPD). The pattern has no
+    geometric ordering: perm is the identity (order it with chol_order_nd)."""
+    dims = (k, k, k)
+    n = k ** 3
+    idx, coords = _grid_coords(dims)
+    offs = _offsets_27()
+    pos = np.array([_is_positive(o) for o in offs])
+    nb = np.stack([_offset_index(dims, coords, o) for o in offs], axis=1)
+    cand = (nb >= 0) & pos[None, :]
+    rng = SplitMix64(seed)
+    m = int(cand.sum())
+    u = rng.uniform(m)
+    w = rng.log_uniform(m, lo, hi)
+    ii = np.broadcast_to(idx[:, None], nb.shape)[cand]
+    jj = nb[cand]
+    kept = u < keep
+    ii, jj, w = ii[kept], jj[kept], w[kept]
+    diag = np.full(n, shift)
+    np.add.at(diag, ii, w)
+    np.add.at(diag, jj, w)
+    R = np.concatenate([idx, np.maximum(ii, jj)])
+    C = np.concatenate([idx, np.minimum(ii, jj)])
+    V = np.concatenate([diag, -w])
+    colptr, rowind, vals = coo_to_lower_csc(n, R, C, V)
+    return Problem(n=n, colptr=colptr, rowind=rowind, values=vals, perm=np.arange(n, dtype=np.int32),
+                   meta=dict(kind="irregular_3d", k=k, keep=keep, seed=seed))
+
+
 def laplacian_2d_dirichlet_weighted(k: int, rng: SplitMix64, lo: float = 0.1, hi: float = 10.0) -> Problem:
     """5-point Laplacian with log-uniform edge weights and Dirichlet ghost edges.
 

@@ -35,7 +35,7 @@ EXPORTED = ["chol_default_options", "chol_analyze", "chol_factor", "chol_solve",
             "chol_solve_refine", "chol_logdet", "chol_analyze_batch", "chol_logdet_batch", "chol_autotune",
             "chol_selected_inverse", "chol_adjoint",
             "chol_get_info", "chol_get_symbolic", "chol_get_partition", "chol_get_factor", "chol_profile",
-            "chol_get_stats", "chol_destroy", "chol_strerror"]
+            "chol_get_stats", "chol_destroy", "chol_strerror", "chol_order_nd"]
 
 KERNEL_CLASSES = ["scatter", "small", "potrf", "trsm", "gemm", "syrk", "assemble", "solve_diag",
                   "selinv_inv", "solve_fasm", "solve_bpanel", "selinv_gemm", "permute", "logdet",
@@ -169,6 +169,14 @@ def chol_analyze(n, colptr, rowind, perm=None, opt=None):
     rc = lib().chol_analyze(int(n), _ptr(colptr), _ptr(rowind), _ptr(perm),
                             C.byref(opt) if opt is not None else None, C.byref(h))
     return rc, h
+
+
+def chol_order_nd(n, colptr, rowind):
+    """Nested dissection ordering of a lower-triangle CSC pattern: returns (rc, perm)."""
+    colptr = _np(colptr, np.int64); rowind = _np(rowind, np.int32)
+    perm = np.zeros(max(int(n), 1), np.int32)
+    rc = lib().chol_order_nd(int(n), _ptr(colptr), _ptr(rowind), _ptr(perm))
+    return rc, perm[: int(n)]
 
 
 def chol_analyze_batch(count, sys_ptr, colptr, rowind, perm=None, opt=None):

@@ -111,3 +111,29 @@ def test_rlb_batch_with_large_small_panels_and_graph():
             assert np.max(np.abs(x - ref["x"])) <= 1e-10 * np.max(np.abs(ref["x"]))
         finally:
             P.chol_destroy(h)
+
+
+def test_rlb_autotune_never_picks_the_persistent_kernel():
+    # the persistent kernel reads the update workspace, which RLB does not have
+    import torch
+    P = chol()
+    probs = gridgen.batch_2d(count=60, kmin=8, kmax=40, seed=5)
+    bd = gridgen.block_diagonal(probs)
+    offs = bd["meta"]["offsets"].astype(np.int32)
+    o = _opts()
+    o.update_mode = P.CHOL_UPDATE_RLB
+    rc, h = P.chol_analyze_batch(len(offs) - 1, offs, bd["colptr"], bd["rowind"], bd["perm"], o)
+    assert rc == 0
+    try:
+        vals = to_dev(bd["values"])
+        assert P.chol_autotune(h, vals) == 0
+        assert P.chol_get_info(h).launch_mode & 1 == 0
+        b = gridgen.rhs_uniform(bd.n, 1, seed=4)
+        X = colmajor(b)
+        assert P.chol_factor(h, vals) == 0
+        assert P.chol_solve(h, X, 1) == 0
+        torch.cuda.synchronize()
+        eta = oracle.backward_error(bd.n, bd["colptr"], bd["rowind"], bd["values"], b, X.cpu().numpy())
+        assert eta[0] <= 1e-14
+    finally:
+        P.chol_destroy(h)
