@@ -116,16 +116,19 @@ enum { CHOL_UPDATE_RL = 0, CHOL_UPDATE_RLB = 1 };
 /*
  * A fill-reducing ordering for a general sparsity pattern (host only). The
  * paper orders its matrices with METIS nested dissection (Sec. IV); this is a
- * self-contained nested dissection: connected components separately, parts
- * above 64 vertices split by the middle level of a breadth-first level
- * structure rooted at a pseudo-peripheral vertex (sides first, separator
- * last), small parts by minimum degree. Deterministic.
+ * self-contained nested dissection: connected components separately; parts
+ * above 64 vertices split by the smaller of two vertex separators (the
+ * minimum vertex cover of a multilevel edge bisection's cut, and the trimmed
+ * middle level of a breadth-first level structure from a pseudo-peripheral
+ * vertex), sides first and separator last; small parts by minimum degree.
+ * Deterministic; O(nnz log n) time, O(nnz) memory.
  *   n       matrix order, >= 0
  *   colptr  host, n+1 entries (lower triangle incl. diagonal, as chol_analyze)
  *   rowind  host, colptr[n] entries
  *   perm    host, n entries, receives the ordering (new -> old), ready for
  *           chol_analyze
- * Errors: -1..-4 for invalid arguments, CHOL_ENOMEM.
+ * Errors: -1..-4 for invalid arguments (a row index above the diagonal or
+ * out of range is -3), CHOL_ENOMEM.
  */
 int chol_order_nd(int32_t n, const int64_t* colptr, const int32_t* rowind, int32_t* perm);
 
