@@ -584,7 +584,7 @@ void build(chol_handle* h, const int64_t* colptr, const int32_t* rowind) {
     }
     P.tri_n = (int32_t)h->tri_items.size() - P.tri_b;
     const int32_t gemv_rows = h->opt.precision == CHOL_PREC_FP64 ? 64 : 32;
-    const int32_t bpanel_cols = h->opt.precision == CHOL_PREC_FP64 ? 8 : 64;
+    const int32_t bpanel_cols = h->opt.precision == CHOL_PREC_FP64 ? 16 : 64;
     P.gemv_b = (int32_t)h->gemv_tasks.size();
     P.bpanel_b = (int32_t)h->bpanel_tasks.size();
     for (int32_t J : Js) {

@@ -300,9 +300,14 @@ k_sv_tri(const SnodeDev* __restrict__ sn, const TriItem* __restrict__ items, int
 }
 
 // Panel product w_J = L_RJ y_J for the off-diagonal rows [r0, r0 + kGemvRows)
-// of J. Column-major: 64 rows, a thread per (row, right-hand-side group), K
-// walked in chunks staged in shared memory. Row-major: 32 rows, a warp per 4
-// rows, lanes along K, fixed-order shuffle reduction.
+// of J, y_J staged in shared memory in chunks of KC columns.
+// Column-major (binary64): 64 rows per task. The 8 warps split each chunk's
+// columns (warp w takes k = w mod 8); a lane holds rows lane and lane + 32 and
+// walks four of its columns at a time, so 8 independent 8-byte loads are in
+// flight per lane, each warp load a contiguous 256 bytes. The warps' partial
+// sums are then combined in warp order through shared memory.
+// Row-major (binary32): 32 rows, a warp per 4 rows, lanes along K,
+// fixed-order shuffle reduction.
 template <class T, bool RM>
 __global__ void __launch_bounds__(kT)
 k_sv_gemv(const SnodeDev* __restrict__ sn, const TileTask* __restrict__ tasks, const T* __restrict__ L,
@@ -315,11 +320,16 @@ k_sv_gemv(const SnodeDev* __restrict__ sn, const TileTask* __restrict__ tasks, c
   const T* P = L + d.loff;
   T* Wj = W + d.wpre * nrhs;
   if constexpr (!RM) {
-    const int row = threadIdx.x & 63, rg = threadIdx.x >> 6;
-    const int u = t.r0 + row;
-    T acc[kSolveChunk / 4];
+    constexpr int NW = kT / 32;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int u0 = t.r0 + lane, u1 = u0 + 32;
+    const bool in0 = u0 < b, in1 = u1 < b;
+    const T* col0 = P + d.s + u0;   // L(s + u0, k) = col0[k * ld]
+    T acc[2][kSolveChunk];
 #pragma unroll
-    for (int j = 0; j < kSolveChunk / 4; ++j) acc[j] = T(0);
+    for (int h = 0; h < 2; ++h)
+#pragma unroll
+      for (int r = 0; r < kSolveChunk; ++r) acc[h][r] = T(0);
     for (int kc = 0; kc < d.s; kc += KC) {
       const int kn = min(KC, d.s - kc);
       __syncthreads();
@@ -327,23 +337,54 @@ k_sv_gemv(const SnodeDev* __restrict__ sn, const TileTask* __restrict__ tasks, c
         const int i = q % kn, r = q / kn;
         yk[i + r * KC] = Y[d.f + kc + i + (int64_t)r * n];
       }
+      for (int q = kn + threadIdx.x; q < KC; q += blockDim.x)   // zero tail: masked columns read 0
+        for (int r = 0; r < nrhs; ++r) yk[q + r * KC] = T(0);
       __syncthreads();
-      if (u < b) {
-        for (int k = 0; k < kn; ++k) {
-          const T l = lval<T, RM>(P, d, d.s + u, kc + k);
+      for (int k4 = warp; k4 < kn; k4 += 4 * NW) {
+        T l[4][2];
 #pragma unroll
-          for (int j = 0; j < kSolveChunk / 4; ++j) {
-            const int r = rg + 4 * j;
-            if (r < nrhs) acc[j] += l * yk[k + r * KC];
+        for (int j = 0; j < 4; ++j) {
+          const int k = k4 + j * NW;
+          const T* c = col0 + (int64_t)(kc + k) * d.ld;
+          l[j][0] = (k < kn && in0) ? c[0] : T(0);
+          l[j][1] = (k < kn && in1) ? c[32] : T(0);
+        }
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+          const int k = min(k4 + j * NW, KC - 1);   // l = 0 past kn
+#pragma unroll
+          for (int r = 0; r < kSolveChunk; ++r) {
+            if (r >= nrhs) break;
+            const T y = yk[k + r * KC];
+            acc[0][r] += l[j][0] * y;
+            acc[1][r] += l[j][1] * y;
           }
         }
       }
     }
-    if (u < b) {
+    // combine the warps' partials in warp order, four right-hand sides a round
+    T* red = yk;   // NW x 64 rows x 4
+    for (int r0 = 0; r0 < nrhs; r0 += 4) {
+      __syncthreads();
 #pragma unroll
-      for (int j = 0; j < kSolveChunk / 4; ++j) {
-        const int r = rg + 4 * j;
-        if (r < nrhs) Wj[u + (int64_t)r * b] = acc[j];
+      for (int q = 0; q < 4; ++q) {
+        if (r0 + q >= nrhs) break;
+        T v0 = T(0), v1 = T(0);
+#pragma unroll
+        for (int r = 0; r < kSolveChunk; ++r)
+          if (r == r0 + q) { v0 = acc[0][r]; v1 = acc[1][r]; }
+        red[(warp * 64 + lane) * 4 + q] = v0;
+        red[(warp * 64 + lane + 32) * 4 + q] = v1;
+      }
+      __syncthreads();
+      for (int e = threadIdx.x; e < 64 * 4; e += blockDim.x) {
+        const int row = e >> 2, q = e & 3;
+        const int u = t.r0 + row;
+        if (r0 + q >= nrhs || u >= b) continue;
+        T v = T(0);
+#pragma unroll
+        for (int w = 0; w < NW; ++w) v += red[(w * 64 + row) * 4 + q];
+        Wj[u + (int64_t)(r0 + q) * b] = v;
       }
     }
   } else {
@@ -440,8 +481,12 @@ k_sv_fasm(const AsmTask* __restrict__ tasks, int ntasks, const AsmSeg* __restric
 }
 
 // Backward panel: y_J[c] -= sum_u L(s+u, c) x[rows[s+u]] for the columns of a task.
-// Column-major: a warp per column (8 columns per task). Row-major: 64 columns
-// per task, a thread per (column, row group of 4), fixed-order combination.
+// Column-major (binary64): 16 columns per task, two per warp. The gathered
+// x[rows[s+u]] of a 256-row chunk are staged in shared memory once for the
+// task; a lane walks rows lane, lane + 32, ... of both its columns, four rows
+// at a time (8 independent loads in flight, each warp load a contiguous 256
+// bytes), then a fixed shuffle tree sums the lanes. Row-major: 64 columns per
+// task, a thread per (column, row group of 4), fixed-order combination.
 template <class T, bool RM>
 __global__ void __launch_bounds__(kT)
 k_sv_bpanel(const SnodeDev* __restrict__ sn, const TileTask* __restrict__ tasks, const int32_t* __restrict__ rows,
@@ -452,24 +497,58 @@ k_sv_bpanel(const SnodeDev* __restrict__ sn, const TileTask* __restrict__ tasks,
   const int32_t* rj = rows + d.roff + d.s;
   const T* P = L + d.loff;
   if constexpr (!RM) {
+    constexpr int CH = 256;
+    __shared__ T xs[CH * kSolveChunk];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int c = t.c0 + warp;
-    if (c >= d.s) return;
-    T acc[kSolveChunk];
+    const int c0 = t.c0 + 2 * warp;
+    const bool in0 = c0 < d.s, in1 = c0 + 1 < d.s;
+    const T* colA = P + d.s + (int64_t)c0 * d.ld;   // L(s + u, c0) = colA[u]
+    const T* colB = colA + d.ld;
+    T acc[2][kSolveChunk];
 #pragma unroll
-    for (int r = 0; r < kSolveChunk; ++r) acc[r] = T(0);
-    for (int u = lane; u < b; u += 32) {
-      const T l = lval<T, RM>(P, d, d.s + u, c);
-      const int32_t g = rj[u];
+    for (int h = 0; h < 2; ++h)
 #pragma unroll
-      for (int r = 0; r < kSolveChunk; ++r)
-        if (r < nrhs) acc[r] += l * Y[g + (int64_t)r * n];
+      for (int r = 0; r < kSolveChunk; ++r) acc[h][r] = T(0);
+    for (int ub = 0; ub < b; ub += CH) {
+      const int un = min(CH, b - ub);
+      __syncthreads();
+      for (int q = threadIdx.x; q < un * nrhs; q += blockDim.x) {
+        const int i = q % un, r = q / un;
+        xs[i + r * CH] = Y[rj[ub + i] + (int64_t)r * n];
+      }
+      __syncthreads();
+      for (int i4 = lane; i4 < un; i4 += 128) {
+        T l[4][2];
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+          const int i = i4 + 32 * j;
+          l[j][0] = (i < un && in0) ? colA[ub + i] : T(0);
+          l[j][1] = (i < un && in1) ? colB[ub + i] : T(0);
+        }
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+          const int i = i4 + 32 * j;
+          if (i >= un) break;
+#pragma unroll
+          for (int r = 0; r < kSolveChunk; ++r) {
+            if (r >= nrhs) break;
+            const T x = xs[i + r * CH];
+            acc[0][r] += l[j][0] * x;
+            acc[1][r] += l[j][1] * x;
+          }
+        }
+      }
     }
 #pragma unroll
     for (int r = 0; r < kSolveChunk; ++r) {
-      T v = acc[r];
-      for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-      if (lane == 0 && r < nrhs) Y[d.f + c + (int64_t)r * n] -= v;
+      if (r >= nrhs) break;
+      T v0 = acc[0][r], v1 = acc[1][r];
+      for (int o = 16; o > 0; o >>= 1) {
+        v0 += __shfl_xor_sync(0xffffffffu, v0, o);
+        v1 += __shfl_xor_sync(0xffffffffu, v1, o);
+      }
+      if (lane == 0 && in0) Y[d.f + c0 + (int64_t)r * n] -= v0;
+      if (lane == 0 && in1) Y[d.f + c0 + 1 + (int64_t)r * n] -= v1;
     }
   } else {
     __shared__ T part[4][64][kSolveChunk + 1];
