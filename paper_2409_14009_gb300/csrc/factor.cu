@@ -198,9 +198,20 @@ k_trsm(const SnodeDev* __restrict__ sn, const TileTask* __restrict__ tasks, int 
   const SnodeDev d = sn[t.J];
   const int kb = min(nb, d.s - t.k0);
   const double* Gd = L + d.loff + t.k0 + (int64_t)t.k0 * d.ld;
-  for (int q = threadIdx.x; q < kb * kb; q += blockDim.x) {
-    const int r = q % kb, c = q / kb;
-    Lk[r + c * 65] = Gd[r + (int64_t)c * d.ld];
+  {
+    // stage the diagonal block: all 16 loads of a thread issued before the
+    // stores (column-major source: consecutive threads read consecutive rows)
+    double v[16];
+#pragma unroll
+    for (int i = 0; i < 16; ++i) {
+      const int q = threadIdx.x + kTrsmThreads * i, r = q & 63, c = q >> 6;
+      v[i] = (r < kb && c < kb) ? Gd[r + (int64_t)c * d.ld] : 0.0;
+    }
+#pragma unroll
+    for (int i = 0; i < 16; ++i) {
+      const int q = threadIdx.x + kTrsmThreads * i;
+      Lk[(q & 63) + (q >> 6) * 65] = v[i];
+    }
   }
   __syncthreads();
   for (int c = threadIdx.x; c < kb; c += blockDim.x) inv[c] = 1.0 / Lk[c + c * 65];

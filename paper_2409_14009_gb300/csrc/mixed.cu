@@ -112,29 +112,22 @@ k_mx_small(const SnodeDev* __restrict__ sn, const int32_t* __restrict__ list, fl
   mx_small_body(sn[list[blockIdx.x]], L, U, status, spiv, counters, Pf);
 }
 
-// Blocked path, step k0: diagonal block in binary32 (packed right-looking
-// Cholesky, potrf.cuh); redone in binary64 from the unmodified block when a
-// binary32 pivot (before its square root) falls below tau.
+// Blocked path, step k0: diagonal block in binary32 (8-column panels on a
+// shared-memory copy, potrf.cuh); redone in binary64 (packed right-looking
+// Cholesky) from the unmodified block when a binary32 pivot (before its square
+// root) falls below tau.
 __global__ void __launch_bounds__(kPkThreads)
 k_mx_potrf(const SnodeDev* __restrict__ sn, const int32_t* __restrict__ list, int k0, int nb, float tau,
            int static_pivot, float* __restrict__ L, int* status, int* counters) {
   __shared__ double colk_d[64];
-  __shared__ float colk_f[64];
+  __shared__ float As[64 * kPwLd];
   __shared__ double sinv_d;
-  __shared__ float sinv_f;
-  __shared__ float sminpiv;
+  __shared__ int accepted;
   const SnodeDev d = sn[list[blockIdx.x]];
   const int kb = min(nb, d.s - k0);
   float* G = L + d.loff + (int64_t)k0 * d.ld + k0;
-  if (threadIdx.x == 0) sminpiv = 3.0e38f;
-  __syncthreads();
-  if (!potrf_block<float, true, float>(G, d.ld, kb, 0.f, counters + 1, &sminpiv, status, false, d.f + k0, colk_f,
-                                       &sinv_f, tau)) {
-    if (threadIdx.x == 0) {
-      sminpiv = 3.0e38f;
-      atomicAdd(counters, 1);
-    }
-    __syncthreads();
+  if (!potrf_panels_f32(G, d.ld, kb, tau, As, &accepted)) {
+    if (threadIdx.x == 0) atomicAdd(counters, 1);
     potrf_block<double, true, float>(G, d.ld, kb, static_pivot ? (double)tau : 0.0, counters + 1, nullptr, status,
                                      true, d.f + k0, colk_d, &sinv_d, -INFINITY);
   }
@@ -151,9 +144,20 @@ k_mx_trsm(const SnodeDev* __restrict__ sn, const TileTask* __restrict__ tasks, i
   const SnodeDev d = sn[t.J];
   const int kb = min(nb, d.s - t.k0);
   const float* Gd = L + d.loff + (int64_t)t.k0 * d.ld + t.k0;
-  for (int q = threadIdx.x; q < kb * kb; q += blockDim.x) {
-    const int r = q / kb, c = q % kb;
-    Lk[r + c * 65] = Gd[(int64_t)r * d.ld + c];
+  {
+    // stage the diagonal block: all 16 loads of a thread issued before the
+    // stores (row-major source: consecutive threads read consecutive columns)
+    float v[16];
+#pragma unroll
+    for (int i = 0; i < 16; ++i) {
+      const int q = threadIdx.x + 256 * i, r = q >> 6, c = q & 63;
+      v[i] = (r < kb && c < kb) ? Gd[(int64_t)r * d.ld + c] : 0.f;
+    }
+#pragma unroll
+    for (int i = 0; i < 16; ++i) {
+      const int q = threadIdx.x + 256 * i;
+      Lk[(q >> 6) + (q & 63) * 65] = v[i];
+    }
   }
   __syncthreads();
   for (int c = threadIdx.x; c < kb; c += blockDim.x) inv[c] = 1.0f / Lk[c + c * 65];

@@ -138,3 +138,107 @@ __device__ bool potrf_block(GT* __restrict__ G, int64_t ld, int kb, T spiv, int*
   }
   return ok;
 }
+
+// A CTA of kPkThreads factors a kb x kb (kb <= 64) binary32 block, row-major
+// with leading dimension ld, in 8-column panels on a shared-memory copy (As:
+// 64 rows of 65 floats):
+// - staging: every thread issues its 16 loads before storing any, so the
+//   block arrives in about one memory latency;
+// - panel (warp 0): lane l holds rows c0 + l and c0 + l + 32 of the panel's 8
+//   columns in registers; right-looking, one column at a time, with the pivot
+//   and the column entries L(c0 + jj, k) passed by shuffles;
+// - trailing update (all warps): entry (r, j), c0 + w <= j <= r, subtracts
+//   the panel's w products L(r, k) L(j, k) in column order; a thread owns row
+//   r = c0 + w + tid / 4 and every fourth column of it.
+// Per entry this is exactly the arithmetic of potrf_block (the same fused
+// multiply-subtracts, scalings and pivot roots, in the same column order), so
+// the factor is bitwise the same; the difference is 2 CTA barriers per panel
+// instead of 2 per column, and no per-slot bookkeeping. Returns (uniformly
+// across the CTA) whether every pivot before its square root was >= accept,
+// with a NaN or non-positive pivot failing; the factor is stored back only
+// then, so a failed block is left unmodified.
+constexpr int kPwLd = 65;
+__device__ __forceinline__ bool potrf_panels_f32(float* __restrict__ G, int64_t ld, int kb, float accept,
+                                                 float* __restrict__ As, int* sok) {
+  const int tid = threadIdx.x;
+  {
+    float v[16];
+#pragma unroll
+    for (int i = 0; i < 16; ++i) {
+      const int q = tid + kPkThreads * i, r = q >> 6, c = q & 63;
+      v[i] = (r < kb && c <= r) ? G[(int64_t)r * ld + c] : 0.f;
+    }
+#pragma unroll
+    for (int i = 0; i < 16; ++i) {
+      const int q = tid + kPkThreads * i;
+      As[(q >> 6) * kPwLd + (q & 63)] = v[i];
+    }
+  }
+  if (tid == 0) *sok = 1;
+  __syncthreads();
+  const int lane = tid & 31;
+  for (int c0 = 0; c0 < kb; c0 += 8) {
+    const int w = min(8, kb - c0), c1 = c0 + w;
+    if (tid < 32) {
+      const int ra = c0 + lane, rb = ra + 32;
+      float xa[8], xb[8];
+#pragma unroll
+      for (int t = 0; t < 8; ++t) {
+        xa[t] = ra < 64 ? As[ra * kPwLd + c0 + t] : 0.f;
+        xb[t] = rb < 64 ? As[rb * kPwLd + c0 + t] : 0.f;
+      }
+      bool ok = true;
+#pragma unroll
+      for (int kk = 0; kk < 8; ++kk) {
+        if (kk < w) {
+          const float dk = __shfl_sync(0xffffffffu, xa[kk], kk);
+          const bool bad = !(dk > 0.f);
+          ok = ok && !bad && dk >= accept;
+          float root, rroot;
+          pivot_root(dk, bad, root, rroot);
+          const int rk = c0 + kk;
+          xa[kk] = ra == rk ? root : (ra > rk ? xa[kk] * rroot : xa[kk]);
+          xb[kk] = xb[kk] * rroot;   // rb >= c0 + 32 > rk
+#pragma unroll
+          for (int jj = kk + 1; jj < 8; ++jj) {
+            const float cj = __shfl_sync(0xffffffffu, xa[kk], jj);   // L(c0 + jj, rk)
+            xa[jj] = fmaf(-xa[kk], cj, xa[jj]);
+            xb[jj] = fmaf(-xb[kk], cj, xb[jj]);
+          }
+        }
+      }
+#pragma unroll
+      for (int t = 0; t < 8; ++t) {
+        if (ra < 64) As[ra * kPwLd + c0 + t] = xa[t];
+        if (rb < 64) As[rb * kPwLd + c0 + t] = xb[t];
+      }
+      if (lane == 0 && !ok) *sok = 0;
+    }
+    __syncthreads();
+    const int r = c1 + (tid >> 2);
+    if (r < kb) {
+      float lr[8];
+#pragma unroll
+      for (int t = 0; t < 8; ++t) lr[t] = t < w ? As[r * kPwLd + c0 + t] : 0.f;
+      float* Ar = As + r * kPwLd;
+      for (int j = c1 + (tid & 3); j <= r; j += 4) {
+        const float* Aj = As + j * kPwLd + c0;
+        float acc = Ar[j];
+#pragma unroll
+        for (int t = 0; t < 8; ++t)
+          if (t < w) acc = fmaf(-lr[t], Aj[t], acc);
+        Ar[j] = acc;
+      }
+    }
+    __syncthreads();
+  }
+  const bool ok = *sok != 0;
+  if (ok) {
+#pragma unroll
+    for (int i = 0; i < 16; ++i) {
+      const int q = tid + kPkThreads * i, r = q >> 6, c = q & 63;
+      if (r < kb && c <= r) G[(int64_t)r * ld + c] = As[r * kPwLd + c];
+    }
+  }
+  return ok;
+}

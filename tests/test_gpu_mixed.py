@@ -25,10 +25,12 @@ RES_TOL = {"fp32": 1e-5, "tf32": 1e-2, "bf16": 5e-2}
 L_TOL_2D = {"fp32": 1e-4, "tf32": 5e-2, "bf16": 2e-1}
 
 
-def _run(problem, mode, b, merge=0.0, tau=1e-3, nb=64, small_rows=128, max_iter=200, static_pivot=0):
+def _run(problem, mode, b, merge=0.0, tau=1e-3, nb=64, small_rows=128, max_iter=200, static_pivot=0, extra=None):
     import torch
     P = chol()
     o = P.chol_default_options()
+    for k, v in (extra or {}).items():
+        setattr(o, k, v)
     o.precision = MODES[mode]
     o.merge_growth = merge
     o.pivot_tau = tau
@@ -105,6 +107,23 @@ def test_3d_varcoef_mixed_refined(mode, merge):
 def test_elasticity_mixed_refined(mode):
     p = gridgen.elasticity_27pt(7, seed=3)
     _check(p, mode, nrhs=1, merge=0.05, small_rows=64)
+
+
+@pytest.mark.parametrize("n", [31, 32, 33, 64, 65, 100, 129])
+def test_fp32_blocked_diagonal_blocks_of_every_width(n):
+    # the small-supernode kernel is off, so every diagonal block, the full
+    # 64-wide ones and the ragged last one (1 to 64 columns), goes through the
+    # blocked binary32 POTRF
+    from helpers import lower_csc_from_dense
+    rs = np.random.RandomState(n)
+    M = rs.normal(size=(n, n))
+    A = M @ M.T + n * np.eye(n)
+    cp, ri, vx = lower_csc_from_dense(A)
+    prob = dict(n=n, colptr=cp, rowind=ri, values=vx, perm=np.arange(n, dtype=np.int32))
+    got, ferr, rel, ref = _check(prob, "fp32", nrhs=2, extra=dict(small_max_cols=1, small_max_panel=1))
+    assert got["info"].fp64_fallbacks == 0
+    assert got["stats"]["potrf"]["launches"] == (n + 63) // 64
+    assert ferr <= 1e-5, ferr
 
 
 def test_fp64_fallback_blocks_are_counted_and_exact():
