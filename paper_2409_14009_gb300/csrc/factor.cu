@@ -169,18 +169,18 @@ k_small_rlb(const SnodeDev* __restrict__ sn, const int32_t* __restrict__ list, c
 }
 
 // Blocked path, step k0: factor the kb x kb (kb <= 64) diagonal block of each
-// listed supernode (packed right-looking Cholesky, potrf.cuh).
+// listed supernode (8-column panels on a shared-memory copy, potrf.cuh); a
+// non-positive pivot records its column in *status.
 constexpr int kPotrfThreads = kPkThreads;
 __global__ void __launch_bounds__(kPotrfThreads)
 k_potrf(const SnodeDev* __restrict__ sn, const int32_t* __restrict__ list, int k0, int nb,
         double* __restrict__ L, int* status) {
-  __shared__ double colk[64];
-  __shared__ double sinv;
+  __shared__ double As[64 * kPwLd];
+  __shared__ int sok;
   const SnodeDev d = sn[list[blockIdx.x]];
   const int kb = min(nb, d.s - k0);
   double* G = L + d.loff + k0 + (int64_t)k0 * d.ld;
-  potrf_block<double, false, double>(G, d.ld, kb, 0.0, nullptr, nullptr, status, true, d.f + k0, colk, &sinv,
-                                     -INFINITY);
+  potrf_panels<double, false>(G, d.ld, kb, -INFINITY, As, &sok, status, true, d.f + k0);
 }
 
 // Blocked path, step k0: rows [r0, r0+32) of column block [k0, k0+kb) become

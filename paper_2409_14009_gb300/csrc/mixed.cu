@@ -126,7 +126,7 @@ k_mx_potrf(const SnodeDev* __restrict__ sn, const int32_t* __restrict__ list, in
   const SnodeDev d = sn[list[blockIdx.x]];
   const int kb = min(nb, d.s - k0);
   float* G = L + d.loff + (int64_t)k0 * d.ld + k0;
-  if (!potrf_panels_f32(G, d.ld, kb, tau, As, &accepted)) {
+  if (!potrf_panels<float, true>(G, d.ld, kb, tau, As, &accepted, status, false, d.f + k0)) {
     if (threadIdx.x == 0) atomicAdd(counters, 1);
     potrf_block<double, true, float>(G, d.ld, kb, static_pivot ? (double)tau : 0.0, counters + 1, nullptr, status,
                                      true, d.f + k0, colk_d, &sinv_d, -INFINITY);

@@ -139,9 +139,9 @@ __device__ bool potrf_block(GT* __restrict__ G, int64_t ld, int kb, T spiv, int*
   return ok;
 }
 
-// A CTA of kPkThreads factors a kb x kb (kb <= 64) binary32 block, row-major
-// with leading dimension ld, in 8-column panels on a shared-memory copy (As:
-// 64 rows of 65 floats):
+// A CTA of kPkThreads factors a kb x kb (kb <= 64) block, row-major with
+// leading dimension ld if RM, else column-major, in 8-column panels on a
+// shared-memory copy (As: 64 rows of 65 entries):
 // - staging: every thread issues its 16 loads before storing any, so the
 //   block arrives in about one memory latency;
 // - panel (warp 0): lane l holds rows c0 + l and c0 + l + 32 of the panel's 8
@@ -153,25 +153,37 @@ __device__ bool potrf_block(GT* __restrict__ G, int64_t ld, int kb, T spiv, int*
 // Per entry this is exactly the arithmetic of potrf_block (the same fused
 // multiply-subtracts, scalings and pivot roots, in the same column order), so
 // the factor is bitwise the same; the difference is 2 CTA barriers per panel
-// instead of 2 per column, and no per-slot bookkeeping. Returns (uniformly
-// across the CTA) whether every pivot before its square root was >= accept,
-// with a NaN or non-positive pivot failing; the factor is stored back only
-// then, so a failed block is left unmodified.
+// instead of 2 per column, and no per-slot bookkeeping.
+//   accept   a pivot (before its square root) below it, or a NaN or
+//            non-positive one, rejects the block: nothing is stored back and
+//            the return value (uniform across the CTA) is false; -INFINITY
+//            accepts every block
+//   record   a non-positive or NaN pivot records column fcol + k + 1 in
+//            *status (smallest wins); its column becomes NaN
+//   sok      shared scratch word
 constexpr int kPwLd = 65;
-__device__ __forceinline__ bool potrf_panels_f32(float* __restrict__ G, int64_t ld, int kb, float accept,
-                                                 float* __restrict__ As, int* sok) {
+template <class T>
+__device__ __forceinline__ T fmsub(T a, T b, T c) {   // c - a b, one rounding
+  if constexpr (sizeof(T) == 8) return fma(-a, b, c);
+  else return fmaf(-a, b, c);
+}
+template <class T, bool RM>
+__device__ __forceinline__ bool potrf_panels(T* __restrict__ G, int64_t ld, int kb, float accept, T* __restrict__ As,
+                                             int* sok, int* status, bool record, int fcol) {
   const int tid = threadIdx.x;
   {
-    float v[16];
+    T v[16];
 #pragma unroll
     for (int i = 0; i < 16; ++i) {
-      const int q = tid + kPkThreads * i, r = q >> 6, c = q & 63;
-      v[i] = (r < kb && c <= r) ? G[(int64_t)r * ld + c] : 0.f;
+      const int q = tid + kPkThreads * i;
+      const int r = RM ? q >> 6 : q & 63, c = RM ? q & 63 : q >> 6;   // coalesced either way
+      v[i] = (r < kb && c <= r) ? (RM ? G[(int64_t)r * ld + c] : G[r + (int64_t)c * ld]) : T(0);
     }
 #pragma unroll
     for (int i = 0; i < 16; ++i) {
       const int q = tid + kPkThreads * i;
-      As[(q >> 6) * kPwLd + (q & 63)] = v[i];
+      const int r = RM ? q >> 6 : q & 63, c = RM ? q & 63 : q >> 6;
+      As[r * kPwLd + c] = v[i];
     }
   }
   if (tid == 0) *sok = 1;
@@ -181,29 +193,31 @@ __device__ __forceinline__ bool potrf_panels_f32(float* __restrict__ G, int64_t 
     const int w = min(8, kb - c0), c1 = c0 + w;
     if (tid < 32) {
       const int ra = c0 + lane, rb = ra + 32;
-      float xa[8], xb[8];
+      T xa[8], xb[8];
 #pragma unroll
       for (int t = 0; t < 8; ++t) {
-        xa[t] = ra < 64 ? As[ra * kPwLd + c0 + t] : 0.f;
-        xb[t] = rb < 64 ? As[rb * kPwLd + c0 + t] : 0.f;
+        xa[t] = ra < 64 ? As[ra * kPwLd + c0 + t] : T(0);
+        xb[t] = rb < 64 ? As[rb * kPwLd + c0 + t] : T(0);
       }
       bool ok = true;
+      const bool check = accept > -INFINITY;
 #pragma unroll
       for (int kk = 0; kk < 8; ++kk) {
         if (kk < w) {
-          const float dk = __shfl_sync(0xffffffffu, xa[kk], kk);
-          const bool bad = !(dk > 0.f);
-          ok = ok && !bad && dk >= accept;
-          float root, rroot;
+          const T dk = __shfl_sync(0xffffffffu, xa[kk], kk);
+          const bool bad = !(dk > T(0));
+          ok = ok && (!check || (!bad && (float)dk >= accept));
+          if (bad && record && lane == 0) atomicMin(status, fcol + c0 + kk + 1);
+          T root, rroot;
           pivot_root(dk, bad, root, rroot);
           const int rk = c0 + kk;
           xa[kk] = ra == rk ? root : (ra > rk ? xa[kk] * rroot : xa[kk]);
           xb[kk] = xb[kk] * rroot;   // rb >= c0 + 32 > rk
 #pragma unroll
           for (int jj = kk + 1; jj < 8; ++jj) {
-            const float cj = __shfl_sync(0xffffffffu, xa[kk], jj);   // L(c0 + jj, rk)
-            xa[jj] = fmaf(-xa[kk], cj, xa[jj]);
-            xb[jj] = fmaf(-xb[kk], cj, xb[jj]);
+            const T cj = __shfl_sync(0xffffffffu, xa[kk], jj);   // L(c0 + jj, rk)
+            xa[jj] = fmsub(xa[kk], cj, xa[jj]);
+            xb[jj] = fmsub(xb[kk], cj, xb[jj]);
           }
         }
       }
@@ -217,16 +231,16 @@ __device__ __forceinline__ bool potrf_panels_f32(float* __restrict__ G, int64_t 
     __syncthreads();
     const int r = c1 + (tid >> 2);
     if (r < kb) {
-      float lr[8];
+      T lr[8];
 #pragma unroll
-      for (int t = 0; t < 8; ++t) lr[t] = t < w ? As[r * kPwLd + c0 + t] : 0.f;
-      float* Ar = As + r * kPwLd;
+      for (int t = 0; t < 8; ++t) lr[t] = t < w ? As[r * kPwLd + c0 + t] : T(0);
+      T* Ar = As + r * kPwLd;
       for (int j = c1 + (tid & 3); j <= r; j += 4) {
-        const float* Aj = As + j * kPwLd + c0;
-        float acc = Ar[j];
+        const T* Aj = As + j * kPwLd + c0;
+        T acc = Ar[j];
 #pragma unroll
         for (int t = 0; t < 8; ++t)
-          if (t < w) acc = fmaf(-lr[t], Aj[t], acc);
+          if (t < w) acc = fmsub(lr[t], Aj[t], acc);
         Ar[j] = acc;
       }
     }
@@ -236,8 +250,12 @@ __device__ __forceinline__ bool potrf_panels_f32(float* __restrict__ G, int64_t 
   if (ok) {
 #pragma unroll
     for (int i = 0; i < 16; ++i) {
-      const int q = tid + kPkThreads * i, r = q >> 6, c = q & 63;
-      if (r < kb && c <= r) G[(int64_t)r * ld + c] = As[r * kPwLd + c];
+      const int q = tid + kPkThreads * i;
+      const int r = RM ? q >> 6 : q & 63, c = RM ? q & 63 : q >> 6;
+      if (r < kb && c <= r) {
+        if (RM) G[(int64_t)r * ld + c] = As[r * kPwLd + c];
+        else G[r + (int64_t)c * ld] = As[r * kPwLd + c];
+      }
     }
   }
   return ok;
