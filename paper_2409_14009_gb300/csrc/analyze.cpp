@@ -479,6 +479,8 @@ void build(chol_handle* h, const int64_t* colptr, const int32_t* rowind) {
     h->w_rows_max = std::max(h->w_rows_max, wo);
     int32_t maxs = 0;
     for (int32_t J : large) maxs = std::max(maxs, h->snodes[J].s);
+    // binary64 TRSM tasks are half as tall: each CTA's substitution is DFMA-bound
+    const int32_t trsm_rows = h->opt.precision == CHOL_PREC_FP64 ? kTrsmRowsHost / 2 : kTrsmRowsHost;
     for (int32_t k0 = 0; k0 < maxs; k0 += nb) {
       StepRange st{};
       st.potrf_b = (int32_t)h->potrf_list.size();
@@ -496,7 +498,7 @@ void build(chol_handle* h, const int64_t* colptr, const int32_t* rowind) {
         for (int32_t j = 0; j < kb; ++j) st.potrf_flops += (double)(kb - j) * (kb - j);
         const double below = (double)(d.len - k0 - kb);
         st.trsm_flops += below * (double)kb * (double)kb;   // kb divisions + 2*kb(kb-1)/2 per row
-        for (int32_t r0 = k0 + kb; r0 < d.len; r0 += kTrsmRowsHost) h->trsm_tasks.push_back({J, k0, r0, 0});
+        for (int32_t r0 = k0 + kb; r0 < d.len; r0 += trsm_rows) h->trsm_tasks.push_back({J, k0, r0, 0});
         // trailing update: 2 kb flops per entry (r, c) with c in [k0+kb, cend), r in [c, len)
         const int32_t cend = tc_modes ? std::min(d.s, ob + kTcOuter) : d.s;
         {

@@ -183,12 +183,12 @@ k_potrf(const SnodeDev* __restrict__ sn, const int32_t* __restrict__ list, int k
   potrf_panels<double, false>(G, d.ld, kb, -INFINITY, As, &sok, status, true, d.f + k0);
 }
 
-// Blocked path, step k0: rows [r0, r0+32) of column block [k0, k0+kb) become
+// Blocked path, step k0: rows [r0, r0 + kTrsmRows) of column block [k0, k0+kb) become
 // X = B L_kk^{-T}. Eight lanes share a row, lane q holding columns q + 8m; the
 // solved x_j is broadcast inside the 8-lane group with a shuffle and every lane
 // updates its own columns (no barriers in the substitution loop).
-constexpr int kTrsmThreads = 256;
-constexpr int kTrsmRows = 32;
+constexpr int kTrsmThreads = 128;   // 8 lanes per row
+constexpr int kTrsmRows = 16;
 __global__ void __launch_bounds__(kTrsmThreads)
 k_trsm(const SnodeDev* __restrict__ sn, const TileTask* __restrict__ tasks, int nb,
        double* __restrict__ L) {
@@ -199,16 +199,17 @@ k_trsm(const SnodeDev* __restrict__ sn, const TileTask* __restrict__ tasks, int 
   const int kb = min(nb, d.s - t.k0);
   const double* Gd = L + d.loff + t.k0 + (int64_t)t.k0 * d.ld;
   {
-    // stage the diagonal block: all 16 loads of a thread issued before the
+    // stage the diagonal block: all loads of a thread issued before the
     // stores (column-major source: consecutive threads read consecutive rows)
-    double v[16];
+    constexpr int kIt = 64 * 64 / kTrsmThreads;
+    double v[kIt];
 #pragma unroll
-    for (int i = 0; i < 16; ++i) {
+    for (int i = 0; i < kIt; ++i) {
       const int q = threadIdx.x + kTrsmThreads * i, r = q & 63, c = q >> 6;
       v[i] = (r < kb && c < kb) ? Gd[r + (int64_t)c * d.ld] : 0.0;
     }
 #pragma unroll
-    for (int i = 0; i < 16; ++i) {
+    for (int i = 0; i < kIt; ++i) {
       const int q = threadIdx.x + kTrsmThreads * i;
       Lk[(q & 63) + (q >> 6) * 65] = v[i];
     }

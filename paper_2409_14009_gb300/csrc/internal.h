@@ -159,7 +159,7 @@ constexpr int kAsmCols = 64;     // assembly task width (target columns)
 constexpr int kAsmPos = 1024;    // assembly task height (row positions of the target)
 constexpr int kAsmWarpPos = 256;       // warp-sized assembly tasks: at most this many positions
 constexpr int kAsmWarpEntries = 4096;  // ... and this many entries over all segments
-constexpr int kTrsmRowsHost = 32; // TRSM task height (rows)
+constexpr int kTrsmRowsHost = 32; // TRSM task height (rows; binary64 tasks take half)
 constexpr int kSolveSmallCols = 32;   // supernodes solved by one warp: s <= 32 and
 constexpr int kSolveSmallRows = 256;  // len <= 256
 constexpr int kRlbSmallRows = 1024;   // RLB: rows of a supernode on the one-CTA kernel (small_max_rows cap)
