@@ -365,10 +365,16 @@ struct SiPlan {
   double* d_part = nullptr;
 };
 
-// Emit the tiles of products launched together. When the group has fewer
-// than two output tiles per SM, products with K > 256 are split over up to
-// ceil(2 SMs / tiles) K chunks (of at least 128): each chunk writes a partial
-// tile to the workspace and a second launch adds them in chunk order.
+// Emit the tiles of products launched together. Products with K > 256 may be
+// split over K chunks (of at least 128): each chunk writes a partial tile to
+// the workspace and a second launch adds them in chunk order. The split factor
+// is chosen per group for the fill of whole waves of resident CTAs (tiles of
+// unequal cost counted alike): a small group is spread over the SMs, and a
+// group of, say, 384 tiles on 456 CTA slots, which would leave some SMs idle
+// for a third of the launch, becomes 7 x 384 = 5.9 waves. Only groups below
+// two waves are split, and a split must gain at least 8% of fill to pay for
+// its partial tiles.
+constexpr int kGenCtasPerSm = 3;   // __launch_bounds__ of k_gen_gemm_grouped
 Group emit_group(SiPlan& pl, const std::vector<GenGemm>& gs, int sms) {
   Group gr;
   gr.tb = (int32_t)pl.tiles.size();
@@ -380,17 +386,33 @@ Group emit_group(SiPlan& pl, const std::vector<GenGemm>& gs, int sms) {
         if (!g.lower_c || ti * kGTile + kGTile - 1 >= tj * kGTile) ++n;
     return n;
   };
+  const int64_t slots = (int64_t)kGenCtasPerSm * sms;
+  auto split_of = [](const GenGemm& g, int ks) {
+    return g.K > 256 ? (int)std::min<int64_t>(ks, (g.K + 127) / 128) : 1;
+  };
+  auto fill = [&](int ks) {
+    int64_t t = 0;
+    for (const GenGemm& g : gs)
+      if (g.M > 0 && g.N > 0) t += out_tiles(g) * split_of(g, ks);
+    return t == 0 ? 1.0 : (double)t / ((double)((t + slots - 1) / slots) * (double)slots);
+  };
   int64_t nt = 0;
   for (const GenGemm& g : gs)
     if (g.M > 0 && g.N > 0) nt += out_tiles(g);
-  const int64_t target = 2 * (int64_t)sms;
+  int ksel = 1;
+  double best = fill(1);
+  const double base = best;
+  // from two waves on, tiles of unequal cost already even out the tail
+  for (int ks = 2; ks <= 32 && nt < 2 * slots; ++ks) {
+    const double f = fill(ks);
+    if (f > best + 0.02) { best = f; ksel = ks; }
+  }
+  if (best < base + 0.08) ksel = 1;
   int64_t part = 0;
   for (GenGemm g : gs) {
     if (g.M <= 0 || g.N <= 0) continue;
     gr.flops += gemm_flops(g);
-    int ks = 1;
-    if (nt > 0 && nt < target && g.K > 256)
-      ks = (int)std::min<int64_t>((g.K + 127) / 128, (target + nt - 1) / nt);
+    int ks = split_of(g, ksel);
     if (ks > 1) {
       g.kchunk = (((g.K + ks - 1) / ks) + 15) / 16 * 16;
       ks = (g.K + g.kchunk - 1) / g.kchunk;
