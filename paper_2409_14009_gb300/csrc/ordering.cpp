@@ -220,7 +220,19 @@ int64_t cut_of(const WGraph& g, const std::vector<int8_t>& where) {
 // Fiduccia-Mattheyses passes on a two-way cut: single vertex moves by best
 // gain (edge weight to the other side minus to its own), each vertex moved at
 // most once a pass, no side heavier than `maxside`; each pass is rolled back to
-// its best prefix (smallest cut, then best balance).
+// its best prefix (smallest cut, then best balance). The candidates of each
+// side sit in a binary heap ordered by (gain, then smallest vertex); an entry
+// whose vertex changed since it was pushed is skipped when it reaches the top.
+struct FmItem {
+  int64_t gain;
+  int32_t v;
+  uint32_t stamp;
+};
+struct FmOrder {   // max-heap: larger gain first, then the smaller vertex
+  bool operator()(const FmItem& a, const FmItem& b) const {
+    return a.gain != b.gain ? a.gain < b.gain : a.v > b.v;
+  }
+};
 void fm_refine(const WGraph& g, std::vector<int8_t>& where, int64_t maxside, int passes) {
   const int32_t n = g.n;
   std::vector<int64_t> id(n, 0), ed(n, 0);
@@ -233,7 +245,9 @@ void fm_refine(const WGraph& g, std::vector<int8_t>& where, int64_t maxside, int
   for (int32_t v = 0; v < n; ++v) cut += ed[v];
   cut /= 2;
   std::vector<char> locked(n, 0);
+  std::vector<uint32_t> stamp(n, 0);
   std::vector<int32_t> moves;
+  std::vector<FmItem> hv[2];
   auto move = [&](int32_t v) {
     const int s = where[v];
     where[v] = (int8_t)(1 - s);
@@ -247,40 +261,54 @@ void fm_refine(const WGraph& g, std::vector<int8_t>& where, int64_t maxside, int
       else { id[u] -= g.ew[t]; ed[u] += g.ew[t]; }
     }
   };
+  auto push = [&](int32_t v) {
+    auto& h = hv[where[v]];
+    h.push_back({ed[v] - id[v], v, stamp[v]});
+    std::push_heap(h.begin(), h.end(), FmOrder());
+  };
+  // the live top of side s, or null
+  auto top = [&](int s) -> const FmItem* {
+    auto& h = hv[s];
+    while (!h.empty()) {
+      const FmItem& f = h.front();
+      if (f.stamp == stamp[f.v] && !locked[f.v] && where[f.v] == s && ed[f.v] > 0) return &h.front();
+      std::pop_heap(h.begin(), h.end(), FmOrder());
+      h.pop_back();
+    }
+    return nullptr;
+  };
   const int limit = std::max(30, std::min(300, n / 50));
   for (int pass = 0; pass < passes; ++pass) {
-    std::set<std::pair<int64_t, int32_t>> q[2];   // (-gain, v) of unlocked boundary vertices
     std::fill(locked.begin(), locked.end(), 0);
+    hv[0].clear();
+    hv[1].clear();
     for (int32_t v = 0; v < n; ++v)
-      if (ed[v] > 0) q[where[v]].insert({id[v] - ed[v], v});
+      if (ed[v] > 0) { ++stamp[v]; push(v); }
     moves.clear();
     int64_t best_cut = cut, best_imb = std::llabs(w[0] - w[1]);
     size_t best_len = 0;
     int since = 0;
     while (since < limit) {
       int side = -1;
+      const FmItem* pick = nullptr;
       for (int s = 0; s < 2; ++s) {
-        if (q[s].empty()) continue;
-        const int32_t v = q[s].begin()->second;
-        if (w[1 - s] + g.vw[v] > maxside) continue;   // would unbalance
-        if (w[s] > maxside) { side = s; break; }        // must shed weight
-        if (side < 0 || q[s].begin()->first < q[side].begin()->first ||
-            (q[s].begin()->first == q[side].begin()->first && w[s] > w[side]))
-          side = s;
+        const FmItem* f = top(s);
+        if (!f) continue;
+        if (w[1 - s] + g.vw[f->v] > maxside) continue;   // would unbalance
+        if (w[s] > maxside) { side = s; pick = f; break; } // must shed weight
+        if (side < 0 || f->gain > pick->gain || (f->gain == pick->gain && w[s] > w[side])) { side = s; pick = f; }
       }
       if (side < 0) break;
-      const int32_t v = q[side].begin()->second;
-      q[side].erase(q[side].begin());
+      const int32_t v = pick->v;
+      std::pop_heap(hv[side].begin(), hv[side].end(), FmOrder());
+      hv[side].pop_back();
       locked[v] = 1;
-      // neighbours' keys change: take them out before the move, back after
-      for (int64_t t = g.ptr[v]; t < g.ptr[v + 1]; ++t) {
-        const int32_t u = g.adj[t];
-        if (!locked[u] && ed[u] > 0) q[where[u]].erase({id[u] - ed[u], u});
-      }
       move(v);
       for (int64_t t = g.ptr[v]; t < g.ptr[v + 1]; ++t) {
         const int32_t u = g.adj[t];
-        if (!locked[u] && ed[u] > 0) q[where[u]].insert({id[u] - ed[u], u});
+        if (locked[u]) continue;
+        ++stamp[u];   // older entries of u are stale
+        if (ed[u] > 0) push(u);
       }
       moves.push_back(v);
       const int64_t imb = std::llabs(w[0] - w[1]);
