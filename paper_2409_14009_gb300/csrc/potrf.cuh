@@ -1,17 +1,20 @@
 // potrf.cuh -- Cholesky of one kb x kb (kb <= 64) diagonal block in one CTA of
 // 256 threads (the diagonal POTRF of a column step of the blocked path, Sec.
-// II-A).
+// II-A). Two routines with the same per-entry arithmetic:
 //
-// The lower triangle is enumerated column by column, e = off(c) + (r - c) with
-// off(c) = c kb - c (c - 1) / 2, and entry e lives in register slot e / 256 of
-// thread e % 256. Right-looking, one column per step: the owner of (k, k) takes
-// the square root, the owners of column k scale it into shared memory, and the
-// owners of every later column subtract the rank-1 term. The entries still
-// being updated at step k are exactly those with e >= off(k + 1), a suffix of
-// the enumeration, so whole warps drop out as the factorization advances and
-// no arithmetic instruction is issued for finished entries. That matters most
-// for binary64, where a warp-wide DFMA occupies the FP64 pipe for many cycles
-// whether or not its lanes are active.
+// potrf_panels (the diagonal POTRF of both precisions) stages the block in
+// shared memory and works in 8-column panels: one warp factors a panel in
+// registers, all warps apply its rank-8 update to the trailing triangle.
+//
+// potrf_block (the binary64 redo of a rejected binary32 block, with static
+// pivoting) keeps the lower triangle in registers, enumerated column by
+// column, e = off(c) + (r - c) with off(c) = c kb - c (c - 1) / 2; entry e lives
+// in register slot e / 256 of thread e % 256. Right-looking, one column per
+// step: the owner of (k, k) takes the square root, the owners of column k scale
+// it into shared memory, and the owners of every later column subtract the
+// rank-1 term. The entries still being updated at step k are exactly those
+// with e >= off(k + 1), a suffix of the enumeration, so whole warps drop out as
+// the factorization advances.
 #pragma once
 #include <cstdint>
 
