@@ -429,6 +429,9 @@ void build(chol_handle* h, const int64_t* colptr, const int32_t* rowind) {
   // pairs by contributor level, then K, then J
   std::vector<std::vector<int64_t>> pairs_by_level(h->nlevels);
   for (int64_t p = 0; p < np; ++p) pairs_by_level[h->level[h->rel_J[p]]].push_back(p);
+  std::vector<int64_t> kcount(ns, 0), sorted;   // scratch of the per-level sort by K
+  std::vector<int32_t> touched;
+  std::vector<std::array<int32_t, 3>> tile_segs;  // scratch: segments of one column tile
   h->levels.assign(h->nlevels, LevelPlan{});
   h->level_snodes.clear(); h->small_list.clear(); h->potrf_list.clear();
   h->trsm_tasks.clear(); h->gemm_tasks.clear(); h->syrk_tasks.clear();
@@ -618,10 +621,24 @@ void build(chol_handle* h, const int64_t* colptr, const int32_t* rowind) {
     P.bpanel_n = (int32_t)h->bpanel_tasks.size() - P.bpanel_b;
     // assembly: group this level's pairs by target K (then J ascending)
     auto& pl = pairs_by_level[lv];
-    std::stable_sort(pl.begin(), pl.end(), [&](int64_t a, int64_t b) {
-      if (h->rel_K[a] != h->rel_K[b]) return h->rel_K[a] < h->rel_K[b];
-      return h->rel_J[a] < h->rel_J[b];
-    });
+    {
+      // pl is in J order already (pairs are generated by J), so a stable
+      // counting sort by K gives (K, then J) order
+      touched.clear();
+      for (int64_t pz : pl)
+        if (kcount[h->rel_K[pz]]++ == 0) touched.push_back(h->rel_K[pz]);
+      std::sort(touched.begin(), touched.end());
+      int64_t off = 0;
+      for (int32_t K : touched) {
+        const int64_t c = kcount[K];
+        kcount[K] = off;
+        off += c;
+      }
+      sorted.resize(pl.size());
+      for (int64_t pz : pl) sorted[kcount[h->rel_K[pz]]++] = pz;
+      pl.swap(sorted);
+      for (int32_t K : touched) kcount[K] = 0;
+    }
     P.asm_b = (int32_t)h->asm_tasks.size();
     P.asm_entries = 0.0;
     std::vector<AsmTask> warp_tasks;   // placed after the level's CTA tasks
@@ -635,7 +652,7 @@ void build(chol_handle* h, const int64_t* colptr, const int32_t* rowind) {
       for (int32_t t0 = 0; t0 < dk.s; t0 += kAsmCols) {
         int32_t t1 = std::min(dk.s, t0 + kAsmCols);
         // the segments of this column tile
-        std::vector<std::array<int32_t, 3>> tile_segs;
+        tile_segs.clear();
         for (size_t z = q; z < q1; ++z) {
           int64_t p = pl[z];
           const SnodeDev& dj = h->snodes[h->rel_J[p]];
