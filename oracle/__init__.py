@@ -47,6 +47,8 @@ def lib():
         L.orc_relind.argtypes = [C.c_int32, C.c_int32, P, P, P, P, P, P, P, P]
         L.orc_factor_new.restype = C.c_void_p
         L.orc_factor_new.argtypes = [C.c_int32, P, P, P]
+        L.orc_factor_new_mt.restype = C.c_void_p
+        L.orc_factor_new_mt.argtypes = [C.c_int32, P, P, P, P, P, P, C.c_int32]
         L.orc_factor_info.restype = C.c_int32
         L.orc_factor_info.argtypes = [P]
         L.orc_factor_nnz.restype = C.c_int64
@@ -139,11 +141,23 @@ class Symbolic:
 
 
 class Factor:
-    """Left-looking FP64 column Cholesky of B. info = 0 or j+1 (bad pivot at j)."""
+    """Left-looking FP64 column Cholesky of B. info = 0 or j+1 (bad pivot at j).
 
-    def __init__(self, n, bcolptr, browind, bvals):
+    threads = 1: the serial loops, pattern found on the fly. threads != 1: the
+    same cmod/cdiv loops in parallel over the columns of each elimination-tree
+    height (0 = all cores), on the pattern of the symbolic factor; the result
+    agrees with the serial one up to the order of the cmod sums.
+    """
+
+    def __init__(self, n, bcolptr, browind, bvals, threads=1):
         bcolptr = _c(bcolptr, np.int64); browind = _c(browind, np.int32); bvals = _c(bvals, np.float64)
-        h = lib().orc_factor_new(n, _p(bcolptr), _p(browind), _p(bvals))
+        if threads == 1:
+            h = lib().orc_factor_new(n, _p(bcolptr), _p(browind), _p(bvals))
+        else:
+            sym = Symbolic(n, bcolptr, browind)
+            li = sym.li if sym.li.size else np.zeros(1, np.int32)
+            h = lib().orc_factor_new_mt(n, _p(bcolptr), _p(browind), _p(bvals), _p(sym.parent), _p(sym.lp),
+                                        _p(li), int(threads))
         try:
             self.n = n
             self.info = lib().orc_factor_info(h)
@@ -260,12 +274,13 @@ def gradient(problem, fac, w, x, logdet_weight=1.0):
     return g, xbar
 
 
-def reference(problem, b=None):
-    """Run the whole oracle on a gridgen problem: returns a dict of results."""
+def reference(problem, b=None, threads=1):
+    """Run the whole oracle on a gridgen problem: returns a dict of results
+    (threads != 1: the multi-threaded numeric factor, 0 = all cores)."""
     n = problem["n"]
     bp, bi, bx = permute(n, problem["colptr"], problem["rowind"], problem["values"], problem["perm"])
     sym = Symbolic(n, bp, bi)
-    fac = Factor(n, bp, bi, bx)
+    fac = Factor(n, bp, bi, bx, threads=threads)
     out = dict(B=(bp, bi, bx), sym=sym, fac=fac)
     if b is not None:
         out["x"] = fac.solve(problem["perm"], b)

@@ -323,6 +323,151 @@ void* orc_factor_new(int32_t n, const int64_t* bcolptr, const int32_t* browind, 
   return f;
 }
 
+/* ------------------------------------------------------------------------ */
+/* The same numeric loops, multi-threaded (timing variant of the baseline).  */
+/* Column j needs exactly the columns k < j with L_jk != 0, all of which are */
+/* descendants of j in the elimination tree; so the columns of one etree     */
+/* height are independent and are factored in parallel (OpenMP, one dense    */
+/* accumulator per thread), heights in increasing order. A height with fewer */
+/* columns than threads (the chains of the top separators, where most of the */
+/* flops are) splits each column's cmod terms over the threads instead, and  */
+/* adds their accumulators in thread order. The pattern comes                */
+/* from the symbolic factor (lp, li: the output of orc_sym_new), and the     */
+/* columns k that update column j are walked in increasing k, so the result  */
+/* matches orc_factor_new up to the order of the cmod sums. Without OpenMP   */
+/* it runs on one thread. info = smallest j + 1 with a non-positive pivot.   */
+/* ------------------------------------------------------------------------ */
+#ifdef _OPENMP
+#include <omp.h>
+#endif
+void* orc_factor_new_mt(int32_t n, const int64_t* bcolptr, const int32_t* browind, const double* bvals,
+                        const int32_t* parent, const int64_t* lp, const int32_t* li, int32_t nthreads) {
+  orc_num* f = (orc_num*)calloc(1, sizeof(orc_num));
+  f->n = n;
+  size_t nn = (size_t)(n > 0 ? n : 1);
+  int64_t nnz = lp[n];
+  f->lp = (int64_t*)malloc(sizeof(int64_t) * (size_t)(n + 1));
+  memcpy(f->lp, lp, sizeof(int64_t) * (size_t)(n + 1));
+  f->li = (int32_t*)malloc(sizeof(int32_t) * (size_t)(nnz > 0 ? nnz : 1));
+  memcpy(f->li, li, sizeof(int32_t) * (size_t)nnz);
+  f->lx = (double*)calloc((size_t)(nnz > 0 ? nnz : 1), sizeof(double));
+  /* row lists: for row j, the columns k < j with L_jk != 0 (ascending) and */
+  /* the position of L_jk in column k                                       */
+  int64_t* rp = (int64_t*)calloc(nn + 1, sizeof(int64_t));
+  for (int32_t k = 0; k < n; ++k)
+    for (int64_t q = lp[k] + 1; q < lp[k + 1]; ++q) rp[li[q] + 1]++;
+  for (int32_t j = 0; j < n; ++j) rp[j + 1] += rp[j];
+  int32_t* rk = (int32_t*)malloc(sizeof(int32_t) * (size_t)(rp[n] > 0 ? rp[n] : 1));
+  int64_t* rq = (int64_t*)malloc(sizeof(int64_t) * (size_t)(rp[n] > 0 ? rp[n] : 1));
+  int64_t* fill = (int64_t*)malloc(sizeof(int64_t) * nn);
+  for (int32_t j = 0; j < n; ++j) fill[j] = rp[j];
+  for (int32_t k = 0; k < n; ++k)            /* k ascending: lists come out sorted */
+    for (int64_t q = lp[k] + 1; q < lp[k + 1]; ++q) {
+      int64_t z = fill[li[q]]++;
+      rk[z] = k;
+      rq[z] = q;
+    }
+  /* etree heights (children before parents: parent[j] > j) */
+  int32_t* height = (int32_t*)calloc(nn, sizeof(int32_t));
+  int32_t maxh = 0;
+  for (int32_t j = 0; j < n; ++j) {
+    if (parent[j] >= 0 && height[parent[j]] < height[j] + 1) height[parent[j]] = height[j] + 1;
+    if (height[j] > maxh) maxh = height[j];
+  }
+  int64_t* hp = (int64_t*)calloc((size_t)maxh + 2, sizeof(int64_t));
+  for (int32_t j = 0; j < n; ++j) hp[height[j] + 1]++;
+  for (int32_t h = 0; h <= maxh; ++h) hp[h + 1] += hp[h];
+  int32_t* byh = (int32_t*)malloc(sizeof(int32_t) * nn);
+  for (int32_t h = 0; h <= maxh; ++h) fill[h] = hp[h];
+  for (int32_t j = 0; j < n; ++j) byh[fill[height[j]]++] = j;
+  int nt = 1;
+#ifdef _OPENMP
+  nt = nthreads > 0 ? nthreads : omp_get_max_threads();
+#endif
+  double* wall = (double*)calloc(nn * (size_t)nt, sizeof(double));
+  int32_t first_bad = INT32_MAX;   /* smallest j + 1 with a non-positive pivot */
+  for (int32_t h = 0; h <= maxh && n > 0; ++h) {
+    if (hp[h + 1] - hp[h] >= nt) {
+      /* many columns at this height: one column per thread at a time */
+#ifdef _OPENMP
+#pragma omp parallel for schedule(dynamic, 16) num_threads(nt) reduction(min : first_bad)
+#endif
+      for (int64_t z = hp[h]; z < hp[h + 1]; ++z) {
+        int tid = 0;
+#ifdef _OPENMP
+        tid = omp_get_thread_num();
+#endif
+        double* w = wall + (size_t)tid * nn;
+        int32_t j = byh[z];
+        for (int64_t t = bcolptr[j]; t < bcolptr[j + 1]; ++t) w[browind[t]] += bvals[t];
+        for (int64_t e = rp[j]; e < rp[j + 1]; ++e) {          /* cmod(j, k) */
+          int32_t k = rk[e];
+          int64_t q0 = rq[e];
+          double ljk = f->lx[q0];
+          for (int64_t q = q0; q < lp[k + 1]; ++q) w[li[q]] -= f->lx[q] * ljk;
+        }
+        double d = w[j];                                        /* cdiv(j) */
+        if (!(d > 0.0) && j + 1 < first_bad) first_bad = j + 1;
+        double ljj = sqrt(d);
+        f->lx[lp[j]] = ljj;
+        w[j] = 0.0;
+        for (int64_t q = lp[j] + 1; q < lp[j + 1]; ++q) {
+          f->lx[q] = w[li[q]] / ljj;
+          w[li[q]] = 0.0;
+        }
+      }
+    } else {
+      /* few columns (the chains of the top separators): each column's cmod */
+      /* terms are split over the threads in fixed contiguous ranges, every */
+      /* thread sums its range into its own accumulator, and the            */
+      /* accumulators are added over the column's pattern in thread order   */
+      for (int64_t z = hp[h]; z < hp[h + 1]; ++z) {
+        int32_t j = byh[z];
+        int64_t e0 = rp[j], e1 = rp[j + 1];
+#ifdef _OPENMP
+#pragma omp parallel num_threads(nt)
+#endif
+        {
+          int tid = 0, nth = 1;
+#ifdef _OPENMP
+          tid = omp_get_thread_num();
+          nth = omp_get_num_threads();
+#endif
+          double* w = wall + (size_t)tid * nn;
+          int64_t a = e0 + (e1 - e0) * tid / nth, b = e0 + (e1 - e0) * (tid + 1) / nth;
+          for (int64_t e = a; e < b; ++e) {
+            int32_t k = rk[e];
+            int64_t q0 = rq[e];
+            double ljk = f->lx[q0];
+            for (int64_t q = q0; q < lp[k + 1]; ++q) w[li[q]] -= f->lx[q] * ljk;
+          }
+        }
+        double* w0 = wall;
+        for (int t = 1; t < nt; ++t) {
+          double* wt = wall + (size_t)t * nn;
+          for (int64_t q = lp[j]; q < lp[j + 1]; ++q) {
+            w0[li[q]] += wt[li[q]];
+            wt[li[q]] = 0.0;
+          }
+        }
+        for (int64_t t = bcolptr[j]; t < bcolptr[j + 1]; ++t) w0[browind[t]] += bvals[t];
+        double d = w0[j];
+        if (!(d > 0.0) && j + 1 < first_bad) first_bad = j + 1;
+        double ljj = sqrt(d);
+        f->lx[lp[j]] = ljj;
+        w0[j] = 0.0;
+        for (int64_t q = lp[j] + 1; q < lp[j + 1]; ++q) {
+          f->lx[q] = w0[li[q]] / ljj;
+          w0[li[q]] = 0.0;
+        }
+      }
+    }
+  }
+  f->info = first_bad == INT32_MAX ? 0 : first_bad;
+  free(rp); free(rk); free(rq); free(fill); free(height); free(hp); free(byh); free(wall);
+  return f;
+}
+
 int32_t orc_factor_info(void* h) { return ((orc_num*)h)->info; }
 int64_t orc_factor_nnz(void* h) { orc_num* f = (orc_num*)h; return f->lp[f->n]; }
 void orc_factor_get(void* h, int64_t* lp, int32_t* li, double* lx) {

@@ -398,3 +398,44 @@ def test_gradient_vs_central_differences():
     cols = np.repeat(np.arange(n), np.diff(cp))
     dense = np.where(ri == cols, G[ri, cols], G[ri, cols] + G[cols, ri])
     assert np.allclose(g, dense, rtol=1e-9, atol=1e-12)
+
+
+# --------------------------------------------------------------------------
+# the multi-threaded timing variant of the oracle's numeric loops
+# --------------------------------------------------------------------------
+
+def _threaded_vs_serial(n, cp, ri, vx, perm, threads):
+    bp, bi, bx = oracle.permute(n, cp, ri, vx, perm)
+    a = oracle.Factor(n, bp, bi, bx)
+    b = oracle.Factor(n, bp, bi, bx, threads=threads)
+    assert a.info == b.info
+    if a.info == 0:
+        assert np.array_equal(a.lp, b.lp) and np.array_equal(a.li, b.li)
+        scale = np.maximum.reduceat(np.abs(a.lx), a.lp[:-1]) if n else np.zeros(0)
+        err = np.maximum.reduceat(np.abs(a.lx - b.lx), a.lp[:-1]) if n else np.zeros(0)
+        # the cmod sums run in another order: rounding differences only, far
+        # below what a dropped or misplaced term would cause
+        assert np.all(err <= 1e-10 * scale)
+        assert oracle.factor_residual(n, bp, bi, bx, b.lp, b.li, b.lx) <= 1e-13
+    return a, b
+
+
+@pytest.mark.parametrize("threads", [0, 3])
+def test_threaded_factor_matches_serial(threads):
+    for seed in (1, 2, 3):
+        A, cp, ri, vx, p = random_spd(120, 0.04, seed)
+        _threaded_vs_serial(120, cp, ri, vx, p, threads)
+    g = gridgen.laplacian_neumann_varcoef((9, 8, 7), 1e-2, 1e2, 1e-3, seed=4)
+    _threaded_vs_serial(g.n, g["colptr"], g["rowind"], g["values"], g["perm"], threads)
+    q = gridgen.block_diagonal([gridgen.laplacian_2d_dirichlet(k) for k in (3, 11, 6)])
+    _threaded_vs_serial(q.n, q["colptr"], q["rowind"], q["values"], q["perm"], threads)
+
+
+def test_threaded_factor_reports_the_first_bad_pivot():
+    # two independent failing columns at the same etree height: the smaller wins
+    A = np.diag([4.0, -3.0, 2.0, 1.0, 5.0, -1.0, 2.0])
+    cp, ri, vx = lower_csc_from_dense(A)
+    _, b = _threaded_vs_serial(7, cp, ri, vx, None, 0)
+    assert b.info == 2
+    cp, ri, vx = lower_csc_from_dense(np.zeros((0, 0)))
+    assert oracle.Factor(0, np.zeros(1, np.int64), np.zeros(0, np.int32), np.zeros(0), threads=0).info == 0
