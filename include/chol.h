@@ -121,7 +121,9 @@ enum { CHOL_UPDATE_RL = 0, CHOL_UPDATE_RLB = 1 };
  * minimum vertex cover of a multilevel edge bisection's cut, and the trimmed
  * middle level of a breadth-first level structure from a pseudo-peripheral
  * vertex), sides first and separator last; small parts by minimum degree.
- * Deterministic; O(nnz log n) time, O(nnz) memory.
+ * Deterministic: the ordering does not depend on the number of host threads
+ * (large independent parts of the recursion run on threads of their own, up
+ * to the hardware concurrency). O(nnz log n) work, O(nnz) memory.
  *   n       matrix order, >= 0
  *   colptr  host, n+1 entries (lower triangle incl. diagonal, as chol_analyze)
  *   rowind  host, colptr[n] entries

@@ -36,7 +36,7 @@ def _compile(src):
         cmd = [NVCC, *ARCH, "-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC",
                "-I", INC, "-I", CSRC, "-c", path, "-o", obj]
     else:
-        cmd = [NVCC, "-O2", "-std=c++17", "-Xcompiler", "-fPIC", "-x", "c++",
+        cmd = [NVCC, "-O2", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-pthread", "-x", "c++",
                "-I", INC, "-I", CSRC, "-c", path, "-o", obj]
     r = subprocess.run(cmd, capture_output=True, text=True)
     if r.returncode != 0:
@@ -55,7 +55,7 @@ def build(force: bool = False, verbose: bool = False) -> str:
     with ThreadPoolExecutor(max_workers=max(2, len(srcs))) as ex:
         objs = list(ex.map(_compile, srcs))
     tmp = LIB + ".%d.tmp" % os.getpid()
-    cmd = [NVCC, *ARCH, "-shared", "-o", tmp, *objs, "-cudart", "static"]
+    cmd = [NVCC, *ARCH, "-shared", "-o", tmp, *objs, "-cudart", "static", "-lpthread"]
     r = subprocess.run(cmd, capture_output=True, text=True)
     if r.returncode != 0:
         raise RuntimeError("link failed: %s\n%s\n%s" % (" ".join(cmd), r.stdout, r.stderr))

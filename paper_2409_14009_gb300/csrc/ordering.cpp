@@ -18,12 +18,19 @@
 // - parts of at most kNdLeaf vertices are ordered by minimum degree on their
 //   own subgraph (exact degrees, eliminated vertices' neighbours joined into
 //   cliques).
-// Host only; deterministic (every tie goes to the smallest vertex index).
+// Host only; deterministic (every tie goes to the smallest vertex index), and
+// independent of the number of threads: large independent parts of the
+// recursion run on threads of their own, their outputs joined in order.
 #include <algorithm>
+#include <atomic>
 #include <climits>
 #include <cstdint>
 #include <cstdlib>
+#include <exception>
+#include <memory>
 #include <set>
+#include <system_error>
+#include <thread>
 #include <vector>
 
 #include "internal.h"
@@ -58,10 +65,27 @@ Graph build_graph(int32_t n, const int64_t* colptr, const int32_t* rowind) {
   return g;
 }
 
+// State shared by the dissection, which may run on several threads: a part
+// (a set of vertices) is worked on by one thread at a time and parts are
+// disjoint, so lvl_of and loc are only touched at the part's own vertices;
+// part tags (unique per part) are read at neighbours too, hence atomic.
+struct Shared {
+  explicit Shared(int32_t n) : part(new std::atomic<int32_t>[n]), lvl_of(n, -1), loc(n, -1) {
+    for (int32_t v = 0; v < n; ++v) part[v].store(0, std::memory_order_relaxed);
+  }
+  std::unique_ptr<std::atomic<int32_t>[]> part;
+  std::vector<int32_t> lvl_of, loc;
+  std::atomic<int32_t> next_tag{1};
+  std::atomic<int> spare_threads{0};   // threads that may still be started
+  int32_t tag_of(int32_t v) const { return part[v].load(std::memory_order_relaxed); }
+  void set_tag(int32_t v, int32_t t) { part[v].store(t, std::memory_order_relaxed); }
+};
+
 // Breadth-first search from `root` inside the part marked `part == tag`;
 // returns the vertices in visiting order and their levels.
-void bfs(const Graph& g, const std::vector<int32_t>& part, int32_t tag, int32_t root, std::vector<int32_t>& order,
-         std::vector<int32_t>& level, std::vector<int32_t>& lvl_of) {
+void bfs(const Graph& g, Shared& sh, int32_t tag, int32_t root, std::vector<int32_t>& order,
+         std::vector<int32_t>& level) {
+  std::vector<int32_t>& lvl_of = sh.lvl_of;
   order.clear();
   level.clear();
   order.push_back(root);
@@ -71,7 +95,7 @@ void bfs(const Graph& g, const std::vector<int32_t>& part, int32_t tag, int32_t 
     level.push_back(lvl_of[v]);
     for (int64_t t = g.ptr[v]; t < g.ptr[v + 1]; ++t) {
       const int32_t w = g.adj[t];
-      if (part[w] == tag && lvl_of[w] < 0) {
+      if (sh.tag_of(w) == tag && lvl_of[w] < 0) {
         lvl_of[w] = lvl_of[v] + 1;
         order.push_back(w);
       }
@@ -127,17 +151,20 @@ struct WGraph {
   std::vector<int32_t> adj, ew, vw;   // neighbours, edge weights, vertex weights
 };
 
-// the subgraph induced by `verts` (local index i is verts[i]); `loc` is a
-// global -> local scratch map holding -1 outside the call
-WGraph subgraph(const Graph& g, const std::vector<int32_t>& verts, std::vector<int32_t>& loc) {
+// the subgraph induced by `verts`, the part tagged `tag` (local index i is
+// verts[i]); sh.loc is a global -> local scratch map, read only at the part's
+// own vertices and reset to -1 before returning
+WGraph subgraph(const Graph& g, const std::vector<int32_t>& verts, Shared& sh, int32_t tag) {
+  std::vector<int32_t>& loc = sh.loc;
   WGraph s;
   s.n = (int32_t)verts.size();
   for (int32_t i = 0; i < s.n; ++i) loc[verts[i]] = i;
   s.ptr.assign(s.n + 1, 0);
   for (int32_t i = 0; i < s.n; ++i) {
     for (int64_t t = g.ptr[verts[i]]; t < g.ptr[verts[i] + 1]; ++t) {
-      const int32_t w = loc[g.adj[t]];
-      if (w >= 0) { s.adj.push_back(w); s.ew.push_back(1); }
+      if (sh.tag_of(g.adj[t]) != tag) continue;
+      s.adj.push_back(loc[g.adj[t]]);
+      s.ew.push_back(1);
     }
     s.ptr[i + 1] = (int64_t)s.adj.size();
   }
@@ -535,10 +562,31 @@ bool level_separator(const WGraph& g, std::vector<int8_t>& where) {
   return true;
 }
 
+// A side of at least this many vertices may go to its own thread.
+constexpr size_t kNdThreadMin = 4096;
+
+void dissect(const Graph& g, Shared& sh, int32_t tag, std::vector<int32_t> verts, std::vector<int32_t>& out);
+
+// Order one side of a split (possibly several components, each on its own).
+void order_side(const Graph& g, Shared& sh, const std::vector<int32_t>& side, std::vector<int32_t>& out) {
+  const int32_t stag = sh.next_tag.fetch_add(1);
+  for (int32_t v : side) sh.set_tag(v, stag);
+  for (int32_t v : side) sh.lvl_of[v] = -1;
+  std::vector<int32_t> comp, clev;
+  for (int32_t s : side) {
+    if (sh.tag_of(s) != stag) continue;   // already placed in a component
+    const int32_t ctag = sh.next_tag.fetch_add(1);
+    bfs(g, sh, stag, s, comp, clev);
+    for (int32_t v : comp) sh.set_tag(v, ctag);
+    dissect(g, sh, ctag, comp, out);
+  }
+}
+
 // Order the vertices of part `tag` (all connected), appending to `out`.
-void dissect(const Graph& g, std::vector<int32_t>& part, int32_t& next_tag, int32_t tag, std::vector<int32_t> verts,
-             std::vector<int32_t>& out, std::vector<int32_t>& lvl_of, std::vector<int32_t>& loc) {
-  (void)tag;
+// The two sides of a split are independent: the second may run on a thread
+// of its own (its output is appended after the first side's), so the
+// ordering is the same with any number of threads.
+void dissect(const Graph& g, Shared& sh, int32_t tag, std::vector<int32_t> verts, std::vector<int32_t>& out) {
   if ((int)verts.size() <= kNdLeaf) {
     min_degree(g, verts, out);
     return;
@@ -547,7 +595,7 @@ void dissect(const Graph& g, std::vector<int32_t>& part, int32_t& next_tag, int3
   // two candidate separators, the smaller one wins
   std::vector<int8_t> where, lw;
   {
-    const WGraph s = subgraph(g, verts, loc);
+    const WGraph s = subgraph(g, verts, sh, tag);
     ml_bisect(s, where);
     cover_cut(s, where);
     if (level_separator(s, lw) &&
@@ -563,21 +611,38 @@ void dissect(const Graph& g, std::vector<int32_t>& part, int32_t& next_tag, int3
     else out.insert(out.end(), verts.begin(), verts.end());
     return;
   }
-  // each side may have several components: order each on its own
-  for (std::vector<int32_t>* side : {&a, &b}) {
-    const int32_t stag = next_tag++;
-    for (int32_t v : *side) part[v] = stag;
-    for (int32_t v : *side) lvl_of[v] = -1;
-    std::vector<int32_t> comp, clev;
-    for (int32_t s : *side) {
-      if (part[s] != stag) continue;   // already placed in a component
-      const int32_t ctag = next_tag++;
-      bfs(g, part, stag, s, comp, clev, lvl_of);
-      for (int32_t v : comp) part[v] = ctag;
-      dissect(g, part, next_tag, ctag, comp, out, lvl_of, loc);
-    }
+  bool spawn = false;
+  if (b.size() >= kNdThreadMin && a.size() >= kNdThreadMin) {
+    int spare = sh.spare_threads.load();
+    while (spare > 0 && !sh.spare_threads.compare_exchange_weak(spare, spare - 1)) {}
+    spawn = spare > 0;
   }
-  for (int32_t v : sep) part[v] = -2;   // ordered
+  if (spawn) {
+    std::vector<int32_t> out_b;
+    std::exception_ptr err;
+    std::thread t([&] {
+      try {
+        order_side(g, sh, b, out_b);
+      } catch (...) {
+        err = std::current_exception();
+      }
+    });
+    try {
+      order_side(g, sh, a, out);
+    } catch (...) {
+      t.join();
+      sh.spare_threads.fetch_add(1);
+      throw;
+    }
+    t.join();
+    sh.spare_threads.fetch_add(1);
+    if (err) std::rethrow_exception(err);
+    out.insert(out.end(), out_b.begin(), out_b.end());
+  } else {
+    order_side(g, sh, a, out);
+    order_side(g, sh, b, out);
+  }
+  for (int32_t v : sep) sh.set_tag(v, -2);   // ordered
   out.insert(out.end(), sep.begin(), sep.end());
 }
 
@@ -597,21 +662,25 @@ extern "C" int chol_order_nd(int32_t n, const int64_t* colptr, const int32_t* ro
   }
   try {
     const Graph g = build_graph(n, colptr, rowind);
-    std::vector<int32_t> part(n, 0), lvl_of(n, -1), loc(n, -1), out;
+    Shared sh(n);
+    const unsigned hw = std::thread::hardware_concurrency();
+    sh.spare_threads.store(hw > 1 ? (int)hw - 1 : 0);
+    std::vector<int32_t> out;
     out.reserve(n);
-    int32_t next_tag = 1;
     // connected components of the whole graph, each dissected on its own
     std::vector<int32_t> comp, clev;
     for (int32_t s = 0; s < n; ++s) {
-      if (part[s] != 0) continue;
-      const int32_t ctag = next_tag++;
-      bfs(g, part, 0, s, comp, clev, lvl_of);
-      for (int32_t v : comp) part[v] = ctag;
-      dissect(g, part, next_tag, ctag, comp, out, lvl_of, loc);
+      if (sh.tag_of(s) != 0) continue;
+      const int32_t ctag = sh.next_tag.fetch_add(1);
+      bfs(g, sh, 0, s, comp, clev);
+      for (int32_t v : comp) sh.set_tag(v, ctag);
+      dissect(g, sh, ctag, comp, out);
     }
     if ((int32_t)out.size() != n) return CHOL_ESTATE;   // cannot happen: every vertex is placed once
     std::copy(out.begin(), out.end(), perm);
   } catch (const std::bad_alloc&) {
+    return CHOL_ENOMEM;
+  } catch (const std::system_error&) {   // a thread could not be started
     return CHOL_ENOMEM;
   }
   return CHOL_OK;

@@ -52,6 +52,14 @@ def test_deterministic():
     assert np.array_equal(_order(q.n, q["colptr"], q["rowind"]), _order(q.n, q["colptr"], q["rowind"]))
 
 
+def test_deterministic_with_threads():
+    # large enough for the two sides of the top splits to run on their own threads
+    q = gridgen.irregular_3d(30, seed=2)
+    first = _order(q.n, q["colptr"], q["rowind"])
+    for _ in range(4):
+        assert np.array_equal(first, _order(q.n, q["colptr"], q["rowind"]))
+
+
 def test_rejects_bad_input():
     P = chol()
     cp = np.array([0, 2, 3], np.int64)
