@@ -1,8 +1,10 @@
 """Matrix Market input for user-supplied matrices.
 
 read_symmetric(path) reads a `%%MatrixMarket matrix coordinate real symmetric`
-file (1-based entries of the lower or upper triangle) and returns the lower
-triangle in CSC form, as chol_analyze takes it: (n, colptr int64, rowind int32,
+file (1-based entries of the lower or upper triangle), or a `general` file
+holding both triangles of a symmetric matrix (the lower one is kept after a
+check that every entry has its mirror with an equal value), and returns the
+lower triangle in CSC form, as chol_analyze takes it: (n, colptr int64, rowind int32,
 values float64), rows sorted within each column, duplicates summed, every
 diagonal entry present (explicit zeros where the file has none).
 read_perm(path) reads a permutation (one 0- or 1-based index per line; 1-based
@@ -19,8 +21,9 @@ def read_symmetric(path):
             raise ValueError("not a coordinate Matrix Market file: %s" % path)
         if header[3] not in ("real", "integer", "double"):
             raise ValueError("values must be real (got %s)" % header[3])
-        if header[4] != "symmetric":
-            raise ValueError("the matrix must be stored as symmetric (got %s)" % header[4])
+        if header[4] not in ("symmetric", "general"):
+            raise ValueError("the matrix must be symmetric (got %s storage)" % header[4])
+        general = header[4] == "general"
         line = f.readline()
         while line.startswith("%"):
             line = f.readline()
@@ -35,6 +38,18 @@ def read_symmetric(path):
     v = data[:, 2].astype(np.float64)
     if nnz and (i.min() < 0 or j.min() < 0 or i.max() >= n or j.max() >= n):
         raise ValueError("entry index out of range")
+    if general:
+        lo, up = i > j, i < j
+        kl = np.sort(i[lo] * n + j[lo])
+        ku = np.sort(j[up] * n + i[up])   # mirrored into the lower triangle
+        if not np.array_equal(kl, ku):
+            raise ValueError("general storage: the pattern is not symmetric")
+        vl = v[lo][np.argsort(i[lo] * n + j[lo], kind="stable")]
+        vu = v[up][np.argsort(j[up] * n + i[up], kind="stable")]
+        if vl.size and np.max(np.abs(vl - vu)) > 1e-12 * max(1.0, float(np.max(np.abs(v)))):
+            raise ValueError("general storage: the values are not symmetric")
+        keep = i >= j
+        i, j, v = i[keep], j[keep], v[keep]
     r = np.maximum(i, j)
     c = np.minimum(i, j)
     # every diagonal entry present

@@ -3,7 +3,8 @@
     python -m paper_2409_14009_gb300.run_matrix --mtx A.mtx [--perm p.txt]
     python -m paper_2409_14009_gb300.run_matrix --irregular 40
 
-The matrix comes from a Matrix Market file (coordinate real symmetric) or from
+The matrix comes from a Matrix Market file (coordinate, real or integer; symmetric
+storage, or general storage of a symmetric matrix) or from
 the synthetic irregular generator (a k^3-node 27-point pattern with random
 edges dropped). Without --perm it is ordered by chol_order_nd (nested
 dissection on the graph). Prints one JSON line: sizes, ordering, analysis and
@@ -33,7 +34,7 @@ PRECISIONS = {"fp64": P.CHOL_PREC_FP64, "fp32": P.CHOL_PREC_FP32, "tf32": P.CHOL
 def main(argv=None):
     ap = argparse.ArgumentParser()
     src = ap.add_mutually_exclusive_group(required=True)
-    src.add_argument("--mtx", help="Matrix Market file (coordinate real symmetric)")
+    src.add_argument("--mtx", help="Matrix Market file (coordinate; symmetric, or general holding a symmetric matrix)")
     src.add_argument("--irregular", type=int, help="synthetic irregular pattern on a k^3 grid of nodes")
     ap.add_argument("--perm", help="ordering file (new -> old, one index per line)")
     ap.add_argument("--precision", default="fp64", choices=sorted(PRECISIONS))

@@ -129,7 +129,18 @@ def test_matrix_market_round_trip(tmp_path):
     h = os.path.join(tmp_path, "p.txt")
     np.savetxt(h, [3, 1, 2], fmt="%d")
     assert list(mmio.read_perm(h)) == [2, 0, 1]
-    with open(os.path.join(tmp_path, "c.mtx"), "w") as fh:
-        fh.write("%%MatrixMarket matrix coordinate real general\n2 2 1\n1 1 1.0\n")
+    # general storage of a symmetric matrix: both triangles, the lower one kept
+    with open(os.path.join(tmp_path, "g.mtx"), "w") as fh:
+        fh.write("%%MatrixMarket matrix coordinate real general\n3 3 5\n")
+        fh.write("1 1 4.0\n3 1 -1.0\n1 3 -1.0\n2 2 2.0\n3 3 5.0\n")
+    n, cp, ri, v = mmio.read_symmetric(os.path.join(tmp_path, "g.mtx"))
+    assert n == 3 and list(cp) == [0, 2, 3, 4] and list(ri) == [0, 2, 1, 2] and list(v) == [4.0, -1.0, 2.0, 5.0]
+    for body in ("3 3 2\n1 1 1.0\n2 1 1.0\n", "3 3 3\n1 1 1.0\n2 1 1.0\n1 2 2.0\n"):
+        with open(os.path.join(tmp_path, "c.mtx"), "w") as fh:   # not symmetric: pattern, then values
+            fh.write("%%MatrixMarket matrix coordinate real general\n" + body)
+        with pytest.raises(ValueError):
+            mmio.read_symmetric(os.path.join(tmp_path, "c.mtx"))
+    with open(os.path.join(tmp_path, "h.mtx"), "w") as fh:
+        fh.write("%%MatrixMarket matrix coordinate real hermitian\n2 2 1\n1 1 1.0\n")
     with pytest.raises(ValueError):
-        mmio.read_symmetric(os.path.join(tmp_path, "c.mtx"))
+        mmio.read_symmetric(os.path.join(tmp_path, "h.mtx"))
