@@ -312,6 +312,17 @@ int chol_analyze_batch(int32_t count, const int32_t* sys_ptr, const int64_t* col
  * single-system handle fills out[0]). Fixed-order reductions. Synchronizes. */
 int chol_logdet_batch(chol_handle* h, double* out, void* stream);
 
+/* The batch forms of chol_factor and chol_solve, with the same arguments and
+ * errors; any handle is accepted (a single-system handle is a batch of one).
+ *   values  device, the entries of every system concatenated in the order of
+ *           the block-diagonal matrix given to chol_analyze_batch
+ *   b       device, n_total x nrhs column-major (system q in rows
+ *           [sys_ptr[q], sys_ptr[q+1])), overwritten by the solutions
+ * All systems are factored (solved) together, level by level, in one launch
+ * sequence (or one graph replay / persistent launch, as analysed). */
+int chol_factor_batch(chol_handle* h, const double* values, void* stream);
+int chol_solve_batch(chol_handle* h, double* b, int32_t nrhs, void* stream);
+
 /*
  * Autotuner of the launch configuration: factors `values` (device, as for
  * chol_factor) once per candidate and keeps the fastest:

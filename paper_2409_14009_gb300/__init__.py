@@ -33,6 +33,7 @@ CHOL_UPDATE_RLB = 1
 
 EXPORTED = ["chol_default_options", "chol_analyze", "chol_factor", "chol_solve", "chol_solve_noalloc",
             "chol_solve_refine", "chol_logdet", "chol_analyze_batch", "chol_logdet_batch", "chol_autotune",
+            "chol_factor_batch", "chol_solve_batch",
             "chol_selected_inverse", "chol_adjoint",
             "chol_get_info", "chol_get_symbolic", "chol_get_partition", "chol_get_factor", "chol_profile",
             "chol_get_stats", "chol_destroy", "chol_strerror", "chol_order_nd"]
@@ -101,6 +102,10 @@ def lib():
         L.chol_analyze_batch.restype = C.c_int
         L.chol_logdet_batch.argtypes = [P, P, P]
         L.chol_logdet_batch.restype = C.c_int
+        L.chol_factor_batch.argtypes = [P, P, P]
+        L.chol_factor_batch.restype = C.c_int
+        L.chol_solve_batch.argtypes = [P, P, C.c_int32, P]
+        L.chol_solve_batch.restype = C.c_int
         L.chol_autotune.argtypes = [P, P, P]
         L.chol_autotune.restype = C.c_int
         L.chol_selected_inverse.argtypes = [P, P, P]
@@ -193,6 +198,14 @@ def chol_logdet_batch(h, count, stream=None):
     out = np.zeros(max(int(count), 1), np.float64)
     rc = lib().chol_logdet_batch(h, _ptr(out), _stream(stream))
     return rc, out[: int(count)]
+
+
+def chol_factor_batch(h, values, stream=None) -> int:
+    return lib().chol_factor_batch(h, _dev_ptr(values), _stream(stream))
+
+
+def chol_solve_batch(h, b, nrhs, stream=None) -> int:
+    return lib().chol_solve_batch(h, _dev_ptr(b), int(nrhs), _stream(stream))
 
 
 def chol_autotune(h, values, stream=None) -> int:

@@ -784,6 +784,16 @@ extern "C" int chol_analyze_batch(int32_t count, const int32_t* sys_ptr, const i
   return CHOL_OK;
 }
 
+// The batch forms of the factor and the solve: a batch handle is one
+// block-diagonal system, so they are chol_factor and chol_solve.
+extern "C" int chol_factor_batch(chol_handle* h, const double* values, void* stream) {
+  return chol_factor(h, values, stream);
+}
+
+extern "C" int chol_solve_batch(chol_handle* h, double* b, int32_t nrhs, void* stream) {
+  return chol_solve(h, b, nrhs, stream);
+}
+
 extern "C" int chol_get_info(const chol_handle* h, chol_info* info) {
   if (!h) return -1;
   if (!info) return -2;

@@ -111,3 +111,26 @@ def test_autotune_keeps_a_valid_configuration():
     eta = oracle.backward_error(bd.n, bd["colptr"], bd["rowind"], bd["values"], b, X.cpu().numpy())
     assert eta[0] <= 1e-14
     P.chol_destroy(h)
+
+
+def test_batch_entry_points_match_the_oracle_per_system():
+    # chol_factor_batch / chol_solve_batch on a batch handle, two right-hand sides
+    import torch
+    P = chol()
+    probs, bd = _batch(count=40, kmin=4, kmax=24, seed=7)
+    offs = bd["meta"]["offsets"].astype(np.int32)
+    rc, h = P.chol_analyze_batch(len(offs) - 1, offs, bd["colptr"], bd["rowind"], bd["perm"], _opts(P))
+    assert rc == 0
+    try:
+        b = gridgen.rhs_uniform(bd.n, 2, seed=3)
+        assert P.chol_factor_batch(h, to_dev(bd["values"])) == 0
+        X = colmajor(b)
+        assert P.chol_solve_batch(h, X, 2) == 0
+        torch.cuda.synchronize()
+        x = X.cpu().numpy()
+        for q, p in enumerate(probs[:8]):
+            s0, s1 = int(offs[q]), int(offs[q + 1])
+            ref = oracle.reference(p, b[s0:s1])
+            assert np.max(np.abs(x[s0:s1] - ref["x"])) <= 1e-12 * max(1.0, np.max(np.abs(ref["x"])))
+    finally:
+        P.chol_destroy(h)
