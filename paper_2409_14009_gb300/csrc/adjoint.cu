@@ -652,6 +652,7 @@ void chol_adjoint_free(chol_handle* h) {
 }
 
 extern "C" int chol_selected_inverse(chol_handle* h, double* zvals, void* stream) {
+  NvtxRange nvtx_range("chol_selected_inverse");
   if (!h) return -1;
   if (!zvals && h->nnz_a > 0) return -2;
   if (!h->factored) return CHOL_ESTATE;
@@ -667,6 +668,7 @@ extern "C" int chol_selected_inverse(chol_handle* h, double* zvals, void* stream
 
 extern "C" int chol_adjoint(chol_handle* h, const double* w, const double* x, int32_t nrhs, double logdet_weight,
                             double* bbar, double* grad, void* stream) {
+  NvtxRange nvtx_range("chol_adjoint");
   if (!h) return -1;
   if (!w && nrhs > 0) return -2;
   if (!x && nrhs > 0) return -3;

@@ -715,6 +715,7 @@ void build(chol_handle* h, const int64_t* colptr, const int32_t* rowind) {
 
 extern "C" int chol_analyze(int32_t n, const int64_t* colptr, const int32_t* rowind,
                             const int32_t* perm, const chol_options* opt, chol_handle** out) {
+  NvtxRange nvtx_range("chol_analyze");
   if (!out) return -6;
   *out = nullptr;
   int rc = validate(n, colptr, rowind, perm, opt);

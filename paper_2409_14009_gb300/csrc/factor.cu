@@ -790,6 +790,7 @@ int enqueue_factor_fp64(chol_handle* h, const double* values, cudaStream_t st) {
     st = D->hstream;
   }
   for (const LevelPlan& P : h->levels) {
+    NvtxRange nvtx_level("level", (long long)(&P - h->levels.data()));
     const bool rlb = h->opt.update_mode == CHOL_UPDATE_RLB;
     if (P.small_n > 0) {
       KScope ks(h, CHOL_K_SMALL, st, P.small_flops, P.small_bytes);
@@ -929,6 +930,7 @@ const void* chol_persistent_kernel(int precision, int threads) {
 }
 
 extern "C" int chol_factor(chol_handle* h, const double* values, void* stream) {
+  NvtxRange nvtx_range("chol_factor");
   if (!h) return -1;
   if (!values && h->nnz_a > 0) return -2;
   int rc = chol_device_ensure(h);
@@ -1024,6 +1026,7 @@ int chol_finish_factor(chol_handle* h, cudaStream_t st) {
 }
 
 extern "C" int chol_autotune(chol_handle* h, const double* values, void* stream) {
+  NvtxRange nvtx_range("chol_autotune");
   if (!h) return -1;
   if (!values && h->nnz_a > 0) return -2;
   cudaStream_t st = (cudaStream_t)stream;

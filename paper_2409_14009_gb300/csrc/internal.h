@@ -5,6 +5,24 @@
 
 #include "chol.h"
 
+#include <cstdio>
+#include <nvtx3/nvToolsExt.h>
+
+// An NVTX range over a scope, on the host timeline of the calling thread, so
+// that timeline tools and ncu's --nvtx filters can select a phase (e.g. one
+// level of one factorization). A no-op unless such a tool is attached.
+struct NvtxRange {
+  explicit NvtxRange(const char* name) { nvtxRangePushA(name); }
+  NvtxRange(const char* prefix, long long index) {
+    char buf[48];
+    std::snprintf(buf, sizeof(buf), "%s %lld", prefix, index);
+    nvtxRangePushA(buf);
+  }
+  ~NvtxRange() { nvtxRangePop(); }
+  NvtxRange(const NvtxRange&) = delete;
+  NvtxRange& operator=(const NvtxRange&) = delete;
+};
+
 // Per-supernode descriptor (device copy).
 struct SnodeDev {
   int64_t loff;  // offset of the panel in L storage (doubles), column-major, leading dim ld

@@ -518,6 +518,7 @@ int chol_enqueue_factor_mixed(chol_handle* h, const double* values, cudaStream_t
     return CHOL_OK;
   };
   for (const LevelPlan& P : h->levels) {
+    NvtxRange nvtx_level("level", (long long)(&P - h->levels.data()));
     if (P.small_n > 0) {
       KScope ks(h, CHOL_K_SMALL, st, P.small_flops, P.small_bytes / 2);
       k_mx_small<<<P.small_n, 128, sizeof(float) * P.small_max_panel, st>>>(D->sn, D->small_list + P.small_b, L, U,

@@ -180,6 +180,7 @@ int correction_solve(chol_handle* h, double* v, int nrhs, cudaStream_t st) {
 
 extern "C" int chol_solve_refine(chol_handle* h, const double* b, double* x, int32_t nrhs, double tol,
                                  int32_t max_iter, int32_t* iters, double* berr, void* stream) {
+  NvtxRange nvtx_range("chol_solve_refine");
   if (!h) return -1;
   if (!b && nrhs > 0) return -2;
   if (!x && nrhs > 0) return -3;

@@ -759,6 +759,8 @@ int solve_levels(chol_handle* h, const T* L, T* Y, T* W, T* part, int nr, cudaSt
   DeviceState* D = h->dev;
   const int n = h->n;
   auto scope = [&](int cls) { return prof ? new KScope(h, cls, st, 0.0, 0.0) : nullptr; };
+  {   // forward pass (an NVTX range over the scope; early returns pop it)
+  NvtxRange nvtx_forward("forward");
   for (const LevelPlan& P : h->levels) {
     if (P.ssmall_n > 0) {
       // supernodes with s <= 8 first, then the wider ones
@@ -791,6 +793,8 @@ int solve_levels(chol_handle* h, const T* L, T* Y, T* W, T* part, int nr, cudaSt
       delete ks;
     }
   }
+  }
+  NvtxRange nvtx_backward("backward");
   for (int lv = h->nlevels - 1; lv >= 0; --lv) {
     const LevelPlan& P = h->levels[lv];
     if constexpr (RM) {
@@ -936,6 +940,7 @@ int chol_solve_status(chol_handle* h) {
 }
 
 extern "C" int chol_solve(chol_handle* h, double* b, int32_t nrhs, void* stream) {
+  NvtxRange nvtx_range("chol_solve");
   if (!h) return -1;
   if (!b && nrhs > 0 && h->n > 0) return -2;
   if (nrhs < 0) return -3;
