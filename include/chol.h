@@ -109,6 +109,15 @@ typedef struct chol_options {
                            /* update workspace, atomic adds, so results agree to  */
                            /* rounding but not bit for bit between runs.         */
                            /* CHOL_PREC_FP64 and persistent = 0 only.            */
+  int64_t wait_polls;      /* bounded device waits of the triangle solve give up */
+                           /* after this many polls of a flag (the solve is then */
+                           /* invalid and chol_check_waits reports              */
+                           /* CHOL_ETIMEOUT); 0 = default 2^24 (seconds)        */
+  int32_t test_unreachable_flags; /* testing the failure path only: 1 = the   */
+                           /* triangle solve's dependent blocks wait for a flag  */
+                           /* value that no block publishes, so every such wait  */
+                           /* runs out after wait_polls polls; 0 = off (default) */
+  int32_t reserved_opt;
 } chol_options;
 
 enum { CHOL_UPDATE_RL = 0, CHOL_UPDATE_RLB = 1 };
@@ -178,12 +187,26 @@ int chol_factor(chol_handle* h, const double* values, void* stream);
  *   b      device, n x nrhs column-major (leading dimension n); overwritten by X
  *   nrhs   >= 0
  * Returns CHOL_ESTATE without a successful chol_factor. Asynchronous. The
- * blocks of a triangle wait (bounded) for the blocks they depend on; a wait
- * that runs out leaves X invalid and is reported as CHOL_ETIMEOUT by the next
- * chol_factor or chol_solve_refine on the handle. Calls on one handle must not
- * overlap on the GPU (they share workspaces).
+ * blocks of a triangle wait (bounded, chol_options.wait_polls) for the blocks
+ * they depend on; a wait that runs out leaves X invalid and is reported as
+ * CHOL_ETIMEOUT by chol_check_waits, or by the next chol_factor or
+ * chol_solve_refine on the handle. Calls on one handle must not overlap on the
+ * GPU (they share workspaces). CHOL_ESTATE if the current device is not the
+ * one the handle was factored on.
  */
 int chol_solve(chol_handle* h, double* b, int32_t nrhs, void* stream);
+
+/*
+ * Report the bounded waits of the solves enqueued so far on this handle
+ * (chol_solve, chol_solve_batch, chol_solve_noalloc, and the solves inside
+ * chol_solve_refine). Synchronizes `stream` (the stream the solves ran on),
+ * then returns CHOL_ETIMEOUT if any wait of a diagonal-triangle block gave up
+ * since the last check (the solutions of those calls are invalid) and clears
+ * the record; CHOL_OK otherwise. CHOL_ESTATE without a factorization on the
+ * current device. The paper's solves are host-driven library calls with no
+ * device-side waits; this check belongs to the cooperative triangle kernel.
+ */
+int chol_check_waits(chol_handle* h, void* stream);
 
 /*
  * chol_solve without any device allocation. The paper has no counterpart: it
@@ -199,7 +222,11 @@ int chol_solve(chol_handle* h, double* b, int32_t nrhs, void* stream);
  * All calls on a device share that array, so calls that overlap on the GPU
  * race; nothing in it needs to start at zero. The first call on each device
  * looks up the array's device address (cudaGetSymbolAddress, with that device
- * current): make that first call before any stream capture. Asynchronous.
+ * current), and again after the device's context was replaced (cudaDeviceReset):
+ * make that first call before any stream capture. The device the handle was
+ * factored on must be current (CHOL_ESTATE otherwise). Returns CHOL_ENOTSUP
+ * for a mixed-precision handle. A bounded wait that runs out is reported by
+ * chol_check_waits. Asynchronous.
  */
 int chol_solve_noalloc(chol_handle* h, double* b, int32_t nrhs, void* stream);
 

@@ -3,7 +3,9 @@
 Only the tests, ``__graft_entry__.smoke()`` and the benchmark's CPU-baseline
 leg may import this package. It restates the definitions of "GPU Accelerated
 Sparse Cholesky Factorization" (Karsavuran, Ng, Peyton) in the plainest
-form, in ``oracle.c`` (symbolic and numeric parts) and ``selinv.py``:
+form, in ``oracle.c`` (symbolic and numeric parts, the selected inverse) and
+in this module (the inverse on the pattern of A and the loss gradient), plus
+``merge.py`` (relaxed supernode merging):
 
 * ``permute``           B = P A P^T                           (Sec. II, problem)
 * ``symbolic``          etree parent, column counts, struct(L) (Sec. II, etree
@@ -13,6 +15,8 @@ form, in ``oracle.c`` (symbolic and numeric parts) and ``selinv.py``:
 * ``factor``            left-looking column Cholesky (cmod/cdiv), FP64
 * ``solve``             forward/backward substitution          (Sec. I)
 * ``logdet``, ``spmv``, ``backward_error``, ``factor_residual``
+* ``Factor.selinv``     Takahashi recurrence on the pattern of L (selected inverse)
+* ``inverse_on_pattern``, ``gradient``  (A^{-1} on the pattern of A; dl/dA, dl/db)
 
 It shares no code with the CUDA library.
 """

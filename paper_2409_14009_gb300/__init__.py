@@ -31,7 +31,7 @@ CHOL_PREC_BF16 = 3
 CHOL_UPDATE_RL = 0
 CHOL_UPDATE_RLB = 1
 
-EXPORTED = ["chol_default_options", "chol_analyze", "chol_factor", "chol_solve", "chol_solve_noalloc",
+EXPORTED = ["chol_default_options", "chol_analyze", "chol_factor", "chol_solve", "chol_solve_noalloc", "chol_check_waits",
             "chol_solve_refine", "chol_logdet", "chol_analyze_batch", "chol_logdet_batch", "chol_autotune",
             "chol_factor_batch", "chol_solve_batch",
             "chol_selected_inverse", "chol_adjoint",
@@ -48,7 +48,8 @@ class chol_options(C.Structure):
                 ("small_max_panel", C.c_int32), ("block_cols", C.c_int32),
                 ("device_mem_cap", C.c_int64), ("merge_growth", C.c_double),
                 ("small_max_rows", C.c_int32), ("persistent", C.c_int32), ("pivot_tau", C.c_double),
-                ("static_pivot", C.c_int32), ("use_graph", C.c_int32), ("update_mode", C.c_int32)]
+                ("static_pivot", C.c_int32), ("use_graph", C.c_int32), ("update_mode", C.c_int32),
+                ("wait_polls", C.c_int64), ("test_unreachable_flags", C.c_int32), ("reserved_opt", C.c_int32)]
 
 
 class chol_info(C.Structure):
@@ -95,6 +96,8 @@ def lib():
         L.chol_solve.restype = C.c_int
         L.chol_solve_noalloc.argtypes = [P, P, C.c_int32, P]
         L.chol_solve_noalloc.restype = C.c_int
+        L.chol_check_waits.argtypes = [P, P]
+        L.chol_check_waits.restype = C.c_int
         L.chol_solve_refine.argtypes = [P, P, P, C.c_int32, C.c_double, C.c_int32,
                                         C.POINTER(C.c_int32), P, P]
         L.chol_solve_refine.restype = C.c_int
@@ -223,6 +226,11 @@ def chol_solve(h, b, nrhs, stream=None) -> int:
 def chol_solve_noalloc(h, b, nrhs, stream=None) -> int:
     """chol_solve whose workspaces come from a fixed device array (no allocation)."""
     return lib().chol_solve_noalloc(h, _dev_ptr(b), int(nrhs), _stream(stream))
+
+
+def chol_check_waits(h, stream=None) -> int:
+    """Synchronize `stream`; CHOL_ETIMEOUT if a solve's bounded wait gave up since the last check."""
+    return lib().chol_check_waits(h, _stream(stream))
 
 
 def chol_solve_refine(h, b, x, nrhs, tol=1e-10, max_iter=30, stream=None):

@@ -655,7 +655,7 @@ extern "C" int chol_selected_inverse(chol_handle* h, double* zvals, void* stream
   NvtxRange nvtx_range("chol_selected_inverse");
   if (!h) return -1;
   if (!zvals && h->nnz_a > 0) return -2;
-  if (!h->factored) return CHOL_ESTATE;
+  if (int rc_state = chol_factored_here(h)) return rc_state;
   if (h->opt.precision != CHOL_PREC_FP64) return CHOL_ENOTSUP;
   cudaStream_t st = (cudaStream_t)stream;
   int rc = selinv(h, st);
@@ -674,7 +674,7 @@ extern "C" int chol_adjoint(chol_handle* h, const double* w, const double* x, in
   if (!x && nrhs > 0) return -3;
   if (nrhs < 0) return -4;
   if (!grad && h->nnz_a > 0) return -7;
-  if (!h->factored) return CHOL_ESTATE;
+  if (int rc_state = chol_factored_here(h)) return rc_state;
   if (h->opt.precision != CHOL_PREC_FP64) return CHOL_ENOTSUP;
   cudaStream_t st = (cudaStream_t)stream;
   int rc = ensure_adjoint(h);

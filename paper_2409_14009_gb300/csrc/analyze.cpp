@@ -33,6 +33,8 @@ extern "C" void chol_default_options(chol_options* opt) {
   opt->persistent = 0;
   opt->use_graph = 0;
   opt->update_mode = CHOL_UPDATE_RL;
+  opt->wait_polls = 0;
+  opt->test_unreachable_flags = 0;
 }
 
 namespace {

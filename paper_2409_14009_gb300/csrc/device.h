@@ -163,4 +163,18 @@ void chol_prof_resolve(chol_handle* h);   // sum the pending event pairs
 void chol_prof_free(chol_handle* h);
 
 int chol_device_ensure(chol_handle* h);   // allocate and upload on first use
+
+// CHOL_ESTATE unless the handle holds a factorization on the current device.
+// Calls after chol_factor launch on whichever device is current, while the
+// handle's buffers live on the device it was factored on; a mismatch would
+// make kernels read another device's memory, so it is refused up front.
+inline int chol_factored_here(const chol_handle* h) {
+  if (!h->factored || !h->dev) return CHOL_ESTATE;
+  int cur = -1;
+  if (cudaGetDevice(&cur) != cudaSuccess) {
+    cudaGetLastError();
+    return CHOL_ECUDA;
+  }
+  return cur == h->dev->device ? CHOL_OK : CHOL_ESTATE;
+}
 int chol_dalloc(chol_handle* h, void** p, size_t bytes);

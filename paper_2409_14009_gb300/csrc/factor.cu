@@ -1075,7 +1075,7 @@ extern "C" int chol_autotune(chol_handle* h, const double* values, void* stream)
 extern "C" int chol_logdet_batch(chol_handle* h, double* out, void* stream) {
   if (!h) return -1;
   if (!out) return -2;
-  if (!h->factored) return CHOL_ESTATE;
+  if (int rc_state = chol_factored_here(h)) return rc_state;
   DeviceState* D = h->dev;
   cudaStream_t st = (cudaStream_t)stream;
   const int count = (int)h->sys_ptr.size() - 1;
@@ -1101,7 +1101,7 @@ extern "C" int chol_logdet_batch(chol_handle* h, double* out, void* stream) {
 extern "C" int chol_logdet(chol_handle* h, double* out, void* stream) {
   if (!h) return -1;
   if (!out) return -2;
-  if (!h->factored) return CHOL_ESTATE;
+  if (int rc_state = chol_factored_here(h)) return rc_state;
   DeviceState* D = h->dev;
   cudaStream_t st = (cudaStream_t)stream;
   if (h->opt.precision != CHOL_PREC_FP64) return chol_logdet_mixed(h, out, st);
@@ -1121,7 +1121,7 @@ extern "C" int chol_logdet(chol_handle* h, double* out, void* stream) {
 
 extern "C" int chol_get_factor(chol_handle* h, int64_t* lp, int32_t* li, double* lx, void* stream) {
   if (!h) return -1;
-  if (!h->factored) return CHOL_ESTATE;
+  if (int rc_state = chol_factored_here(h)) return rc_state;
   DeviceState* D = h->dev;
   cudaStream_t st = (cudaStream_t)stream;
   const int32_t n = h->n;

@@ -187,7 +187,7 @@ extern "C" int chol_solve_refine(chol_handle* h, const double* b, double* x, int
   if (nrhs < 0 || nrhs > 1024) return -4;
   if (!(tol > 0.0)) return -5;
   if (max_iter < 1) return -6;
-  if (!h->factored) return CHOL_ESTATE;
+  if (int rc_state = chol_factored_here(h)) return rc_state;
   if (iters) *iters = 0;
   if (nrhs == 0 || h->n == 0) return CHOL_OK;
   cudaStream_t st = (cudaStream_t)stream;

@@ -128,7 +128,8 @@ size_t tri_smem(int nr) {
 template <class T, bool RM, bool TRANS>
 __global__ void __launch_bounds__(kT)
 k_sv_tri(const SnodeDev* __restrict__ sn, const TriItem* __restrict__ items, int nitems, const T* __restrict__ L,
-         T* __restrict__ Y, int n, int nrhs, int* __restrict__ flags, int* __restrict__ sync, int* __restrict__ err) {
+         T* __restrict__ Y, int n, int nrhs, int* __restrict__ flags, int* __restrict__ sync, int* __restrict__ err,
+         long long max_polls, int skew) {
   extern __shared__ __align__(16) unsigned char sv_smem[];
   T* ys = reinterpret_cast<T*>(sv_smem);   // a solved block j, 64 x nrhs
   T* yi = ys + kSub * nrhs;                 // this block's right-hand sides, 64 x nrhs
@@ -140,6 +141,7 @@ k_sv_tri(const SnodeDev* __restrict__ sn, const TriItem* __restrict__ items, int
   if (threadIdx.x == 0) target = ld_acquire(sync) + 1;
   __syncthreads();
   const int tgt = target;
+  const int wait_tgt = tgt + skew;          // skew != 0 only to test the failure path
   const int tid = threadIdx.x, r = tid & 63, g = tid >> 6;
   constexpr bool kfast = RM != TRANS;       // the stored-contiguous index of a product tile is k
   for (int it = blockIdx.x; it < nitems; it += gridDim.x) {
@@ -175,8 +177,8 @@ k_sv_tri(const SnodeDev* __restrict__ sn, const TriItem* __restrict__ items, int
       const int j0 = j * kSub, jb = min(kSub, d.s - j0);
       if (tid == 0) {
         long long polls = 0;
-        while (ld_acquire(flags + item.fbase + j) != tgt) {
-          if (++polls > kTriMaxPolls) { atomicExch(err, 1); break; }
+        while (ld_acquire(flags + item.fbase + j) != wait_tgt) {
+          if (++polls > max_polls) { atomicExch(err, 1); break; }
           if (polls > 4096) __nanosleep(100);   // spin first: the hand-off is on the critical path
         }
       }
@@ -743,8 +745,10 @@ int launch_tri(chol_handle* h, const LevelPlan& P, const T* L, T* Y, int nr, cud
   const int grid = std::min(P.tri_n, per_sm * D->sms);
   const TriItem* items = reinterpret_cast<const TriItem*>(D->tri) + P.tri_b;
   int nitems = P.tri_n, n = h->n;
+  long long max_polls = h->opt.wait_polls > 0 ? (long long)h->opt.wait_polls : kTriMaxPolls;
+  int skew = h->opt.test_unreachable_flags ? 1 : 0;
   void* args[] = {(void*)&D->sn, (void*)&items, (void*)&nitems, (void*)&L, (void*)&Y, (void*)&n, (void*)&nr,
-                  (void*)&D->tri_flags, (void*)&D->tri_sync, (void*)&D->sv_err};
+                  (void*)&D->tri_flags, (void*)&D->tri_sync, (void*)&D->sv_err, (void*)&max_polls, (void*)&skew};
   const cudaError_t e = cudaLaunchCooperativeKernel((const void*)k_sv_tri<T, RM, TRANS>, dim3(grid), dim3(kT), args,
                                                     tri_smem<T>(nr), st);
   if (e != cudaSuccess) {
@@ -939,12 +943,19 @@ int chol_solve_status(chol_handle* h) {
   return CHOL_OK;
 }
 
+extern "C" int chol_check_waits(chol_handle* h, void* stream) {
+  if (!h) return -1;
+  if (int rc_state = chol_factored_here(h)) return rc_state;
+  CHOL_CUDA_TRY(cudaStreamSynchronize((cudaStream_t)stream));
+  return chol_solve_status(h);
+}
+
 extern "C" int chol_solve(chol_handle* h, double* b, int32_t nrhs, void* stream) {
   NvtxRange nvtx_range("chol_solve");
   if (!h) return -1;
   if (!b && nrhs > 0 && h->n > 0) return -2;
   if (nrhs < 0) return -3;
-  if (!h->factored) return CHOL_ESTATE;
+  if (int rc_state = chol_factored_here(h)) return rc_state;
   if (nrhs == 0 || h->n == 0) return CHOL_OK;
   if (h->opt.precision != CHOL_PREC_FP64) return chol_solve_mixed(h, b, nrhs, (cudaStream_t)stream);
   int rc = set_solve_attrs();
@@ -973,8 +984,10 @@ extern "C" int chol_solve(chol_handle* h, double* b, int32_t nrhs, void* stream)
 // reading it, and each level writes its W rows before reading them).
 // Calls whose work overlaps on the GPU (different streams or threads) race on
 // the array. The first call on each device looks up the array's device address
-// with cudaGetSymbolAddress (with that device current); make that first call
-// before any stream capture.
+// with cudaGetSymbolAddress (with that device current), and looks it up again
+// when the device's context has changed (after a cudaDeviceReset); make that
+// first call before any stream capture. The handle's device must be current
+// (CHOL_ESTATE otherwise), because the array and the factor are per device.
 // ---------------------------------------------------------------------------
 constexpr int64_t kNoAllocScratchDoubles = int64_t(1) << 21;
 static __device__ __align__(256) double g_noalloc_scratch[kNoAllocScratchDoubles];
@@ -984,16 +997,46 @@ namespace {
 constexpr int kNoAllocMaxDevices = 64;
 std::mutex g_noalloc_mu;
 double* g_noalloc_addr[kNoAllocMaxDevices] = {};
+unsigned long long g_noalloc_ctx[kNoAllocMaxDevices] = {};   // context id the address belongs to
 
-// Device address of g_noalloc_scratch on the current device (looked up once).
+typedef CUresult (*CtxGetCurrentFn)(CUcontext*);
+typedef CUresult (*CtxGetIdFn)(CUcontext, unsigned long long*);
+
+// Process-unique id of the current context (0 if the driver cannot say). A
+// cudaDeviceReset destroys the primary context and the module with it; the next
+// context gets a new id, so the array's address is looked up again.
+unsigned long long current_ctx_id() {
+  static CtxGetCurrentFn get_cur = nullptr;
+  static CtxGetIdFn get_id = nullptr;
+  static bool resolved = false;
+  if (!resolved) {
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", (void**)&get_cur, 12000, cudaEnableDefault, &q) !=
+            cudaSuccess || q != cudaDriverEntryPointSuccess)
+      get_cur = nullptr;
+    if (cudaGetDriverEntryPointByVersion("cuCtxGetId", (void**)&get_id, 12000, cudaEnableDefault, &q) !=
+            cudaSuccess || q != cudaDriverEntryPointSuccess)
+      get_id = nullptr;
+    cudaGetLastError();
+    resolved = true;
+  }
+  CUcontext ctx = nullptr;
+  unsigned long long id = 0;
+  if (get_cur && get_id && get_cur(&ctx) == CUDA_SUCCESS && ctx && get_id(ctx, &id) == CUDA_SUCCESS) return id;
+  return 0;
+}
+
+// Device address of g_noalloc_scratch on the current device: looked up once
+// per device and context (cudaGetSymbolAddress with that device current).
 int noalloc_scratch(double** out) {
   int dev = -1;
   if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kNoAllocMaxDevices) {
     cudaGetLastError();
     return CHOL_ECUDA;
   }
+  const unsigned long long ctx = current_ctx_id();
   std::lock_guard<std::mutex> lock(g_noalloc_mu);
-  if (!g_noalloc_addr[dev]) {
+  if (!g_noalloc_addr[dev] || g_noalloc_ctx[dev] != ctx) {
     void* p = nullptr;
     const cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
     if (e != cudaSuccess || !p) {
@@ -1001,6 +1044,7 @@ int noalloc_scratch(double** out) {
       return CHOL_ECUDA;
     }
     g_noalloc_addr[dev] = static_cast<double*>(p);
+    g_noalloc_ctx[dev] = ctx;
   }
   *out = g_noalloc_addr[dev];
   return CHOL_OK;
@@ -1014,7 +1058,7 @@ extern "C" int chol_solve_noalloc(chol_handle* h, double* b, int32_t nrhs, void*
   if (nrhs < 0) return -3;
   const int64_t per_col = (int64_t)h->n + h->w_rows_max;
   if (per_col > kNoAllocScratchDoubles) return CHOL_ETOOBIG;
-  if (!h->factored || !h->dev) return CHOL_ESTATE;
+  if (int rc_state = chol_factored_here(h)) return rc_state;
   if (h->opt.precision != CHOL_PREC_FP64) return CHOL_ENOTSUP;
   if (nrhs == 0 || h->n == 0) return CHOL_OK;
   int rc = set_solve_attrs();

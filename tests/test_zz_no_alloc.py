@@ -13,6 +13,7 @@ import numpy as np
 import pytest
 
 import gridgen
+import oracle
 from gpu_util import colmajor, to_dev
 from lib_fixture import chol
 
@@ -52,5 +53,50 @@ def test_noalloc_solve_refuses_oversized_problem():
     try:
         dummy = to_dev(np.zeros(4))
         assert P.chol_solve_noalloc(h, dummy, 1) == P.CHOL_ETOOBIG
+    finally:
+        P.chol_destroy(h)
+
+
+def test_noalloc_first_solve_on_fresh_handle_single_rhs_vs_oracle():
+    """The first solve of a new handle (the handle's own solve workspaces were
+    never created) with one right-hand side, checked against the oracle's
+    solution and by its backward error; then chol_solve gives the same x."""
+    import torch
+    P = chol()
+    p = gridgen.laplacian_neumann_varcoef((14, 13, 12), 1e-2, 1e2, 1e-6, seed=7)
+    b = gridgen.rhs_uniform(p.n, 1, seed=8)
+    ref = oracle.reference(p, b)
+    rc, h = P.chol_analyze(p.n, p["colptr"], p["rowind"], p["perm"])
+    assert rc == 0
+    try:
+        assert P.chol_factor(h, to_dev(p["values"])) == 0
+        got = colmajor(b[:, 0])
+        assert P.chol_solve_noalloc(h, got, 1) == 0
+        assert P.chol_check_waits(h) == 0
+        x = got.cpu().numpy().reshape(-1, 1)
+        eta = oracle.backward_error(p.n, p["colptr"], p["rowind"], p["values"], b, x)
+        assert np.all(eta <= 1e-12), eta
+        xr = ref["x"].reshape(-1, 1)
+        assert np.max(np.abs(x - xr)) <= 1e-12 * np.max(np.abs(xr))
+        again = colmajor(b[:, 0])
+        assert P.chol_solve(h, again, 1) == 0
+        torch.cuda.synchronize()
+        assert np.array_equal(again.cpu().numpy().reshape(-1, 1), x)
+    finally:
+        P.chol_destroy(h)
+
+
+@pytest.mark.parametrize("prec", ["fp32", "bf16"])
+def test_noalloc_refuses_mixed_precision_handle(prec):
+    P = chol()
+    p = gridgen.laplacian_2d_dirichlet(24)
+    o = P.chol_default_options()
+    o.precision = P.CHOL_PREC_FP32 if prec == "fp32" else P.CHOL_PREC_BF16
+    rc, h = P.chol_analyze(p.n, p["colptr"], p["rowind"], p["perm"], o)
+    assert rc == 0
+    try:
+        assert P.chol_factor(h, to_dev(p["values"])) == 0
+        x = colmajor(gridgen.rhs_uniform(p.n, 1, seed=1)[:, 0])
+        assert P.chol_solve_noalloc(h, x, 1) == P.CHOL_ENOTSUP
     finally:
         P.chol_destroy(h)
