@@ -12,7 +12,8 @@ value = symbolic factor flops (sum_j c_j^2) / step time, summed over ranks
 (independent replicas: the single factorization does not shard).
 
 `--impl reference` times the CPU oracle (the plain FP64 left-looking column
-Cholesky) on a bounded sample of the same workload family on the host cores.
+Cholesky, numeric factor on every host core) on the same 3D 64^3 workload: one
+whole factorization split over the timed steps, then the 8-RHS solve.
 """
 import argparse
 import json
@@ -131,28 +132,80 @@ def oracle_sample(k=40, threads=1):
     return r["sym"].flops() / dt / 1e9, dt, p.n
 
 
+class OracleStepper:
+    """The oracle on the benchmark workload itself (3D 64^3, 8 RHS): one
+    multi-threaded numeric factorization split into `steps` pieces of
+    elimination-tree heights with equal flops (the heights run in order, so the
+    pieces together are exactly one factorization), the last piece followed by
+    the 8-RHS solve and log det. Permutation and symbolic analysis are done
+    before timing, as the GPU arm's analysis is."""
+
+    def __init__(self, steps, threads, k=64):
+        import gridgen
+        import oracle
+        self.oracle = oracle
+        # k = 64 is the benchmark workload (gridgen.workload("3d64")); smaller k
+        # only for quick checks of the harness
+        self.p = gridgen.laplacian_neumann_varcoef((k, k, k), 1e-2, 1e2, 1e-6, seed=2)
+        self.k = k
+        self.b = gridgen.rhs_uniform(self.p.n, NRHS, seed=2)
+        n = self.p.n
+        self.B = oracle.permute(n, self.p["colptr"], self.p["rowind"], self.p["values"], self.p["perm"])
+        self.sym = oracle.Symbolic(n, self.B[0], self.B[1])
+        self.flops = float(self.sym.flops())
+        self.threads = threads
+        self.steps = max(int(steps), 1)
+        self.S = None
+
+    def start(self):
+        bp, bi, bx = self.B
+        self.S = self.oracle.StagedFactor(self.p.n, bp, bi, bx, threads=self.threads, sym=self.sym)
+        w = np.cumsum(self.S.work())
+        targets = w[-1] * np.arange(1, self.steps) / self.steps
+        cuts = np.searchsorted(w, targets, side="left") + 1
+        self.cuts = [0] + [int(c) for c in cuts] + [self.S.max_height + 1]
+        self.piece = 0
+
+    def step(self):
+        """Run piece k; returns its wall seconds."""
+        t = time.perf_counter()
+        self.S.run(self.cuts[self.piece], self.cuts[self.piece + 1])
+        self.piece += 1
+        if self.piece == self.steps:
+            fac = self.S.finish()
+            self.x = fac.solve(self.p["perm"], self.b)
+            self.logdet = fac.logdet()
+            self.info = fac.info
+        return time.perf_counter() - t
+
+
 def run_reference(args, rank):
     if rank != 0:
         return
-    k = args.ref_grid
     cores = _cpu_cores()   # the oracle's multi-threaded numeric factor on every host core
     for _ in range(args.warmup):
-        oracle_sample(k, threads=cores)
-    vals, tot = [], 0.0
-    for _ in range(args.steps):
-        v, dt, n = oracle_sample(k, threads=cores)
-        vals.append(v); tot += dt
-    value = float(np.mean(vals))
-    sample = ("oracle factor+solve(8 RHS) of the same generator on a %d^3 grid (n=%d) per step, numeric factor "
-              "on %d threads" % (k, k ** 3, cores))
+        oracle_sample(16, threads=cores)
+    st = OracleStepper(args.steps, cores, args.ref_grid)
+    st.start()
+    secs = [st.step() for _ in range(args.steps)]
+    tot = float(np.sum(secs))
+    value = st.flops / tot / 1e9
+    eta = backward_error(st.p, st.b, st.x)
+    sample = ("the whole benchmark workload: one oracle factorization of the 3D %d^3 matrix (numeric factor on "
+              "%d threads) split over the %d timed steps by elimination-tree heights of equal flops, the last step "
+              "also solving the 8 right-hand sides and taking log det; warm-up steps factor a 16^3 grid"
+              % (args.ref_grid, cores, args.steps))
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "GFLOP/s",
             "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": 1e3 * tot / args.steps, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": WORKLOAD, "sample_grid": k, "l2": "inputs larger than L2"},
+            "config": {"workload": WORKLOAD if args.ref_grid == 64 else "3D 7-point var-coef Laplacian %d^3 "
+                       "(harness check, not the benchmark)" % args.ref_grid, "grid": args.ref_grid, "nrhs": NRHS,
+                       "precision": "fp64", "l2": "inputs larger than L2"},
             "cpu_baseline": {"value": value, "unit": "GFLOP/s", "cores": cores, "kind": "oracle, multi-threaded",
                              "sample": sample},
-            "e2e": {"value": value, "unit": "GFLOP/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+            "e2e": {"value": value, "unit": "GFLOP/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+            "backward_error": float(eta), "logdet": st.logdet, "factor_info": int(st.info)}
     print(json.dumps(line), flush=True)
 
 
@@ -313,6 +366,57 @@ def batch_run(args, P, gridgen, torch, dev):
     return out
 
 
+def config1_run(args, P, gridgen, torch, dev):
+    """The small 2D configuration: 5-point Dirichlet Laplacian on a 64^2 grid
+    (n = 4,096, diagonal 4 + 1e-3), FP64 factor + one right-hand side U(-1, 1)
+    + log det. About 2,000 supernodes, all at most 64 columns wide: the
+    latency end of the method. Timed with direct launches and with the
+    launch configuration the autotuner keeps (graph replay or the persistent
+    cooperative kernel)."""
+    p = gridgen.workload("2d64")
+    b = gridgen.rhs_uniform(p.n, 1, seed=1)
+    st = torch.cuda.current_stream()
+    vals = torch.as_tensor(p["values"], device=dev)
+    B = torch.as_tensor(b[:, 0].copy(), device=dev)
+    X = torch.empty_like(B)
+    out = {"workload": "2D 5-point Dirichlet Laplacian 64^2 (n=4096), FP64 factor + 1-RHS solve + log det"}
+    for name, tune in (("direct", False), ("autotuned", True)):
+        rc, h = P.chol_analyze(p.n, p["colptr"], p["rowind"], p["perm"])
+        assert rc == 0, rc
+        if tune:
+            assert P.chol_autotune(h, vals, st) == 0
+        info = P.chol_get_info(h)
+        ld = [0.0]
+
+        def step():
+            assert P.chol_factor(h, vals, st) == 0
+            X.copy_(B)
+            assert P.chol_solve(h, X, 1, st) == 0
+            ld[0] = P.chol_logdet(h, st)[1]
+        for _ in range(5):
+            step()
+        P.chol_get_stats(h, reset=True)
+        reps = 50
+        ms, _ = _timed(torch, st, step, reps)
+        stats = P.chol_get_stats(h, reset=True)
+        fms, _ = _timed(torch, st, lambda: P.chol_factor(h, vals, st), 20)
+        X.copy_(B)
+        sms, _ = _timed(torch, st, lambda: P.chol_solve(h, X, 1, st), 20)
+        X.copy_(B)
+        P.chol_solve(h, X, 1, st)
+        torch.cuda.synchronize()
+        eta = backward_error(p, b, X.cpu().numpy().reshape(-1, 1))
+        out[name] = {"ms_per_step": ms, "factor_ms": fms, "solve_ms": sms,
+                     "factor_gflops": info.flops / (fms * 1e-3) / 1e9,
+                     "launches_per_step": int(sum(v["launches"] for v in stats.values())) // reps,
+                     "backward_error": float(eta), "logdet": ld[0],
+                     "launch_mode": {"persistent": bool(info.launch_mode & 1), "graph": bool(info.launch_mode & 2)},
+                     "supernodes": info.nsuper_storage, "levels": info.nlevels}
+        P.chol_destroy(h)
+    out["flops"] = float(info.flops)
+    return out
+
+
 def rlb_run(args, P, torch, dev, p, b, vals, flops, rl_factor_ms, rl_u_doubles):
     """The right-looking blocked update (no update workspace) on the bench
     workload: FP64 factor + 8-RHS solve, timed like the RL factor."""
@@ -436,30 +540,30 @@ def run_ours(args, rank, world, local_rank):
     f0.record(st); S.solve_(X); f1.record(st); torch.cuda.synchronize()
     solve_ms = f0.elapsed_time(f1)
     eta = backward_error(p, b, X.cpu().numpy())
-    # end to end through the public API with host buffers
+    # end to end through the C ABI with host buffers: chol_factor_solve_host
+    # copies the values and right-hand sides in, factors, solves, takes log
+    # det and copies X out, every step
     hv = torch.as_tensor(p["values"]).pin_memory()
-    hb = torch.as_tensor(np.ascontiguousarray(b.T)).pin_memory()
+    hb = torch.as_tensor(np.ascontiguousarray(b.T)).pin_memory()   # column-major n x 8
     hx = torch.empty_like(hb).pin_memory()
-    dvals = torch.empty_like(vals)
-    dX = torch.empty((NRHS, p.n), dtype=torch.float64, device=dev)
 
     def e2e_step():
-        dvals.copy_(hv, non_blocking=True)
-        dX.copy_(hb, non_blocking=True)
-        S.factor(dvals)
-        S.solve_(dX.t())
-        hx.copy_(dX, non_blocking=True)
+        rc, ld_ = P.chol_factor_solve_host(S.h, hv, hb, hx, NRHS, True, st)
+        assert rc == 0, rc
+        return ld_
     e2e_step()
     torch.cuda.synchronize()
     f0.record(st)
     for _ in range(args.steps):
-        e2e_step()
+        ld_e2e = e2e_step()
     f1.record(st)
     torch.cuda.synchronize()
     e2e_ms = f0.elapsed_time(f1) / args.steps
+    eta_e2e = backward_error(p, b, hx.numpy().T)
     mixed = None if args.no_mixed else mixed_vs_fp64(args, P, gridgen, torch, dev, p, b, vals, flops,
                                                          factor_ms, solve_ms)
     batch = None if args.no_batch else batch_run(args, P, gridgen, torch, dev)
+    config1 = None if args.no_config1 else config1_run(args, P, gridgen, torch, dev)
     adjoint = None if args.no_adjoint else adjoint_run(args, P, gridgen, torch, dev)
     rlb = None if args.no_rlb else rlb_run(args, P, torch, dev, p, b, vals, flops, factor_ms,
                                            S.info.update_doubles)
@@ -479,11 +583,16 @@ def run_ours(args, rank, world, local_rank):
             cpu = {"value": v, "unit": "GFLOP/s", "cores": 1, "kind": "oracle",
                    "sample": "oracle FP64 factor+solve(8 RHS), same generator on a %d^3 grid (n=%d), %.1f s"
                              % (args.cpu_grid, n, dt)}
-            # the same loops on every host core (columns of one etree height in parallel)
+            # the same loops on every host core, on the benchmark workload itself
             cores = _cpu_cores()
-            vt, dtt, _ = oracle_sample(args.cpu_grid, threads=cores)
-            cpu_mt = {"value": vt, "unit": "GFLOP/s", "cores": cores, "kind": "oracle, multi-threaded",
-                      "sample": "same sample, numeric factor on %d threads, %.1f s" % (cores, dtt)}
+            ost = OracleStepper(1, cores)
+            ost.start()
+            dtt = ost.step()
+            cpu_mt = {"value": ost.flops / dtt / 1e9, "unit": "GFLOP/s", "cores": cores,
+                      "kind": "oracle, multi-threaded", "same_config": True,
+                      "sample": "the whole 3D 64^3 workload: numeric factor on %d threads + 8-RHS solve + log det, "
+                                "%.1f s (permutation and symbolic analysis not timed)" % (cores, dtt),
+                      "backward_error": float(backward_error(ost.p, ost.b, ost.x))}
         line = {"metric": METRIC, "value": replica_throughput(flops, world, ms), "unit": "GFLOP/s",
                 "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
                 "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
@@ -499,10 +608,13 @@ def run_ours(args, rank, world, local_rank):
                 "backward_error": float(eta), "logdet": ld[0],
                 "e2e": {"value": replica_throughput(flops, world, e2e_ms), "unit": "GFLOP/s",
                         "ms_per_step": e2e_ms, "h2d_bytes_per_step": int(hv.numel() * 8 + hb.numel() * 8),
-                        "d2h_bytes_per_step": int(hx.numel() * 8)},
+                        "d2h_bytes_per_step": int(hx.numel() * 8 + 8 + 4),
+                        "api": "chol_factor_solve_host (pinned host values and right-hand sides in, X and "
+                               "log det out; factor + 8-RHS solve + log det per step)",
+                        "backward_error": float(eta_e2e), "logdet": ld_e2e},
                 "gpu_launches": launches // max(args.steps, 1) * args.steps,
                 "roofline": roof, "cpu_baseline": cpu, "cpu_baseline_threads": cpu_mt, "clocks": clk.summary(),
-                "mixed_vs_fp64": mixed, "batch": batch, "adjoint": adjoint, "rlb": rlb}
+                "mixed_vs_fp64": mixed, "batch": batch, "adjoint": adjoint, "rlb": rlb, "config1_2d64": config1}
         print(json.dumps(line), flush=True)
     S.close()
     if dist:
@@ -516,7 +628,8 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--cpu-grid", type=int, default=40)
-    ap.add_argument("--ref-grid", type=int, default=32)
+    ap.add_argument("--ref-grid", type=int, default=64,
+                    help="grid side of the reference arm (64 = the benchmark workload itself)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-mixed", action="store_true", help="skip the mixed-precision comparison")
     ap.add_argument("--skip-elasticity", action="store_true")
@@ -524,6 +637,7 @@ def main():
     ap.add_argument("--batch-count", type=int, default=2000)
     ap.add_argument("--no-adjoint", action="store_true", help="skip the differentiable-solve workload")
     ap.add_argument("--no-rlb", action="store_true", help="skip the right-looking blocked (RLB) factor")
+    ap.add_argument("--no-config1", action="store_true", help="skip the 2D 64^2 configuration")
     ap.add_argument("--workload", default="3d64", choices=["3d64", "3d48"],
                     help="3d64 is the benchmark; 3d48 is the smaller case used for ncu captures")
     ap.add_argument("--merge", type=float, default=0.1,

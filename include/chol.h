@@ -231,6 +231,25 @@ int chol_check_waits(chol_handle* h, void* stream);
 int chol_solve_noalloc(chol_handle* h, double* b, int32_t nrhs, void* stream);
 
 /*
+ * Factor, solve and log det for a caller whose data lives in host memory
+ * (Sec. II-A factorization, then the triangular solves of Sec. I): copies the
+ * values and the right-hand sides to the device, runs chol_factor, chol_solve
+ * and (when logdet != NULL) chol_logdet on `stream`, copies X back and
+ * synchronizes. The staging buffers (nnz(A) values, n x nrhs right-hand
+ * sides) belong to the handle and are created by the first call (grown when
+ * nrhs grows). Page-locked host buffers make the copies asynchronous and
+ * faster; pageable ones also work.
+ *   values  host, colptr[n] doubles in the order of the analyzed rowind
+ *   b       host, n x nrhs column-major (ld n)
+ *   x       host, n x nrhs column-major output (may be b)
+ *   logdet  host, one double, or NULL
+ * Returns what chol_factor returns (+j, errors), then solve errors; a bounded
+ * wait of the solve that ran out gives CHOL_ETIMEOUT (x is then invalid).
+ */
+int chol_factor_solve_host(chol_handle* h, const double* values, const double* b, double* x, int32_t nrhs,
+                           double* logdet, void* stream);
+
+/*
  * log det A = 2 sum_j log L_jj, reduced in a fixed order (deterministic).
  *   out    host pointer to one double
  * Synchronizes `stream`.

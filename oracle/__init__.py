@@ -53,6 +53,18 @@ def lib():
         L.orc_factor_new.argtypes = [C.c_int32, P, P, P]
         L.orc_factor_new_mt.restype = C.c_void_p
         L.orc_factor_new_mt.argtypes = [C.c_int32, P, P, P, P, P, P, C.c_int32]
+        L.orc_mt_begin.restype = C.c_void_p
+        L.orc_mt_begin.argtypes = [C.c_int32, P, P, P, P, P, P, C.c_int32]
+        L.orc_mt_max_height.restype = C.c_int32
+        L.orc_mt_max_height.argtypes = [P]
+        L.orc_mt_schedule.restype = None
+        L.orc_mt_schedule.argtypes = [P, P, P]
+        L.orc_mt_run.restype = None
+        L.orc_mt_run.argtypes = [P, C.c_int32, C.c_int32]
+        L.orc_mt_finish.restype = C.c_void_p
+        L.orc_mt_finish.argtypes = [P]
+        L.orc_factor_residual_parts.restype = None
+        L.orc_factor_residual_parts.argtypes = [C.c_int32, P, P, P, P, P, P, C.c_int32, P, P]
         L.orc_factor_info.restype = C.c_int32
         L.orc_factor_info.argtypes = [P]
         L.orc_factor_nnz.restype = C.c_int64
@@ -153,11 +165,14 @@ class Factor:
     agrees with the serial one up to the order of the cmod sums.
     """
 
-    def __init__(self, n, bcolptr, browind, bvals, threads=1):
-        bcolptr = _c(bcolptr, np.int64); browind = _c(browind, np.int32); bvals = _c(bvals, np.float64)
-        if threads == 1:
+    def __init__(self, n, bcolptr, browind, bvals, threads=1, _handle=None):
+        if _handle is not None:
+            h = _handle
+        elif threads == 1:
+            bcolptr = _c(bcolptr, np.int64); browind = _c(browind, np.int32); bvals = _c(bvals, np.float64)
             h = lib().orc_factor_new(n, _p(bcolptr), _p(browind), _p(bvals))
         else:
+            bcolptr = _c(bcolptr, np.int64); browind = _c(browind, np.int32); bvals = _c(bvals, np.float64)
             sym = Symbolic(n, bcolptr, browind)
             li = sym.li if sym.li.size else np.zeros(1, np.int32)
             h = lib().orc_factor_new_mt(n, _p(bcolptr), _p(browind), _p(bvals), _p(sym.parent), _p(sym.lp),
@@ -196,6 +211,42 @@ class Factor:
         return self.lx[self.lp[:-1]]
 
 
+class StagedFactor:
+    """The multi-threaded factor (Factor with threads != 1) run in pieces:
+    run(h0, h1) factors the elimination-tree heights [h0, h1), in increasing
+    order, each height once; finish() returns the Factor. The loops and their
+    order are those of the one-piece run, so the result does not depend on
+    how the heights are split. work() gives sum c_j^2 per height, for
+    splitting by work."""
+
+    def __init__(self, n, bcolptr, browind, bvals, threads=0, sym=None):
+        self._keep = (_c(bcolptr, np.int64), _c(browind, np.int32), _c(bvals, np.float64))
+        bcolptr, browind, bvals = self._keep
+        self.n = n
+        sym = sym if sym is not None else Symbolic(n, bcolptr, browind)
+        self.sym = sym
+        li = sym.li if sym.li.size else np.zeros(1, np.int32)
+        self._li = li
+        self.h = lib().orc_mt_begin(n, _p(bcolptr), _p(browind), _p(bvals), _p(sym.parent), _p(sym.lp),
+                                    _p(li), int(threads))
+        self.max_height = lib().orc_mt_max_height(self.h)
+
+    def work(self):
+        mh = self.max_height
+        hp = np.zeros(mh + 2, np.int64)
+        byh = np.zeros(max(self.n, 1), np.int32)
+        lib().orc_mt_schedule(self.h, _p(hp), _p(byh))
+        c2 = np.diff(self.sym.lp).astype(np.float64) ** 2
+        return np.add.reduceat(c2[byh[: self.n]], hp[:-1]) if self.n else np.zeros(0)
+
+    def run(self, h0, h1):
+        lib().orc_mt_run(self.h, int(h0), int(h1))
+
+    def finish(self):
+        h, self.h = lib().orc_mt_finish(self.h), None
+        return Factor(self.n, None, None, None, _handle=h)
+
+
 def spmv(n, colptr, rowind, values, x):
     x = np.asfortranarray(x, dtype=np.float64)
     nrhs = 1 if x.ndim == 1 else x.shape[1]
@@ -223,6 +274,19 @@ def factor_residual(n, bcolptr, browind, bvals, lp, li, lx):
     if r < 0:
         raise ValueError("L L^T or B has an entry outside the pattern of L")
     return r
+
+
+def factor_residual_parts(n, bcolptr, browind, bvals, lp, li, lx, threads=0):
+    """(||B - L L^T||_F / ||B||_F, per-column residual ||r_j|| / ||B_j||) with
+    the columns computed in parallel (the global value is the quantity of
+    factor_residual; the column sums are added in column order)."""
+    num = np.zeros(max(n, 1)); den = np.zeros(max(n, 1))
+    lib().orc_factor_residual_parts(n, _p(_c(bcolptr, np.int64)), _p(_c(browind, np.int32)),
+                                    _p(_c(bvals, np.float64)), _p(_c(lp, np.int64)), _p(_c(li, np.int32)),
+                                    _p(_c(lx, np.float64)), int(threads), _p(num), _p(den))
+    num, den = num[:n], den[:n]
+    tot = float(np.sqrt(np.sum(num)) / np.sqrt(np.sum(den))) if n else 0.0
+    return tot, np.sqrt(num / den)
 
 
 def factor_residual_cols(n, bcolptr, browind, bvals, lp, li, lx, cols):

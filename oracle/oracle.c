@@ -340,9 +340,28 @@ void* orc_factor_new(int32_t n, const int64_t* bcolptr, const int32_t* browind, 
 #ifdef _OPENMP
 #include <omp.h>
 #endif
-void* orc_factor_new_mt(int32_t n, const int64_t* bcolptr, const int32_t* browind, const double* bvals,
-                        const int32_t* parent, const int64_t* lp, const int32_t* li, int32_t nthreads) {
+/* Staged form: orc_mt_begin builds the row lists and the height classes,     */
+/* orc_mt_run factors the heights [h0, h1) (heights must be run in increasing */
+/* order, each once), orc_mt_finish returns the factor. orc_factor_new_mt     */
+/* runs all heights in one go; splitting them changes nothing in the result.  */
+typedef struct {
+  orc_num* f;
+  const int64_t* bcolptr;
+  const int32_t* browind;
+  const double* bvals;
+  int64_t *rp, *rq, *hp;
+  int32_t *rk, *byh;
+  int32_t maxh, nt;
+  double* wall;
+  int32_t first_bad;   /* smallest j + 1 with a non-positive pivot */
+} orc_mt;
+
+void* orc_mt_begin(int32_t n, const int64_t* bcolptr, const int32_t* browind, const double* bvals,
+                   const int32_t* parent, const int64_t* lp, const int32_t* li, int32_t nthreads) {
+  orc_mt* m = (orc_mt*)calloc(1, sizeof(orc_mt));
   orc_num* f = (orc_num*)calloc(1, sizeof(orc_num));
+  m->f = f;
+  m->bcolptr = bcolptr; m->browind = browind; m->bvals = bvals;
   f->n = n;
   size_t nn = (size_t)(n > 0 ? n : 1);
   int64_t nnz = lp[n];
@@ -384,15 +403,47 @@ void* orc_factor_new_mt(int32_t n, const int64_t* bcolptr, const int32_t* browin
 #ifdef _OPENMP
   nt = nthreads > 0 ? nthreads : omp_get_max_threads();
 #endif
-  double* wall = (double*)calloc(nn * (size_t)nt, sizeof(double));
-  int32_t first_bad = INT32_MAX;   /* smallest j + 1 with a non-positive pivot */
-  for (int32_t h = 0; h <= maxh && n > 0; ++h) {
-    if (hp[h + 1] - hp[h] >= nt) {
+  (void)nthreads;
+  m->rp = rp; m->rk = rk; m->rq = rq; m->hp = hp; m->byh = byh;
+  m->maxh = n > 0 ? maxh : -1;
+  m->nt = nt;
+  m->wall = (double*)calloc(nn * (size_t)nt, sizeof(double));
+  m->first_bad = INT32_MAX;
+  free(fill); free(height);
+  return m;
+}
+
+int32_t orc_mt_max_height(void* h) { return ((orc_mt*)h)->maxh; }
+
+/* The column of each position in height order and the start of every height */
+/* (maxh + 2 offsets), for splitting the run by work.                          */
+void orc_mt_schedule(void* h, int64_t* hp, int32_t* byh) {
+  orc_mt* m = (orc_mt*)h;
+  if (hp) memcpy(hp, m->hp, sizeof(int64_t) * (size_t)(m->maxh + 2));
+  if (byh) memcpy(byh, m->byh, sizeof(int32_t) * (size_t)(m->hp[m->maxh + 1]));
+}
+
+void orc_mt_run(void* h, int32_t h0, int32_t h1) {
+  orc_mt* m = (orc_mt*)h;
+  orc_num* f = m->f;
+  const int32_t n = f->n;
+  const size_t nn = (size_t)(n > 0 ? n : 1);
+  const int64_t* lp = f->lp;
+  const int32_t* li = f->li;
+  const int64_t *bcolptr = m->bcolptr, *rp = m->rp, *rq = m->rq, *hp = m->hp;
+  const int32_t *browind = m->browind, *rk = m->rk, *byh = m->byh;
+  const double* bvals = m->bvals;
+  const int nt = m->nt;
+  double* wall = m->wall;
+  int32_t first_bad = m->first_bad;
+  if (h1 > m->maxh + 1) h1 = m->maxh + 1;
+  for (int32_t hh = h0 < 0 ? 0 : h0; hh < h1; ++hh) {
+    if (hp[hh + 1] - hp[hh] >= nt) {
       /* many columns at this height: one column per thread at a time */
 #ifdef _OPENMP
 #pragma omp parallel for schedule(dynamic, 16) num_threads(nt) reduction(min : first_bad)
 #endif
-      for (int64_t z = hp[h]; z < hp[h + 1]; ++z) {
+      for (int64_t z = hp[hh]; z < hp[hh + 1]; ++z) {
         int tid = 0;
 #ifdef _OPENMP
         tid = omp_get_thread_num();
@@ -421,7 +472,7 @@ void* orc_factor_new_mt(int32_t n, const int64_t* bcolptr, const int32_t* browin
       /* terms are split over the threads in fixed contiguous ranges, every */
       /* thread sums its range into its own accumulator, and the            */
       /* accumulators are added over the column's pattern in thread order   */
-      for (int64_t z = hp[h]; z < hp[h + 1]; ++z) {
+      for (int64_t z = hp[hh]; z < hp[hh + 1]; ++z) {
         int32_t j = byh[z];
         int64_t e0 = rp[j], e1 = rp[j + 1];
 #ifdef _OPENMP
@@ -463,9 +514,22 @@ void* orc_factor_new_mt(int32_t n, const int64_t* bcolptr, const int32_t* browin
       }
     }
   }
-  f->info = first_bad == INT32_MAX ? 0 : first_bad;
-  free(rp); free(rk); free(rq); free(fill); free(height); free(hp); free(byh); free(wall);
+  m->first_bad = first_bad;
+}
+
+void* orc_mt_finish(void* h) {
+  orc_mt* m = (orc_mt*)h;
+  orc_num* f = m->f;
+  f->info = m->first_bad == INT32_MAX ? 0 : m->first_bad;
+  free(m->rp); free(m->rk); free(m->rq); free(m->hp); free(m->byh); free(m->wall); free(m);
   return f;
+}
+
+void* orc_factor_new_mt(int32_t n, const int64_t* bcolptr, const int32_t* browind, const double* bvals,
+                        const int32_t* parent, const int64_t* lp, const int32_t* li, int32_t nthreads) {
+  void* m = orc_mt_begin(n, bcolptr, browind, bvals, parent, lp, li, nthreads);
+  orc_mt_run(m, 0, orc_mt_max_height(m) + 1);
+  return orc_mt_finish(m);
 }
 
 int32_t orc_factor_info(void* h) { return ((orc_num*)h)->info; }
@@ -660,6 +724,72 @@ void orc_factor_residual_cols(int32_t n, const int64_t* bcolptr, const int32_t* 
     out[q] = sqrt(rn) / sqrt(bn);
   }
   free(w); free(rcount); free(fill); free(rent); free(rcol);
+}
+
+/* Per-column parts of the factor residual ||B - L L^T||_F / ||B||_F (the same  */
+/* quantity as orc_factor_residual): for column j, with r_i = B_ij -             */
+/* sum_k L_ik L_jk over i >= j, num[j] = r_jj^2 + 2 sum_{i>j} r_i^2 and den[j] =  */
+/* B_jj^2 + 2 sum_{i>j} B_ij^2 (off-diagonal entries count twice). Columns are   */
+/* independent, so they run in parallel (one accumulator per thread); the      */
+/* caller adds num and den in column order.                                    */
+void orc_factor_residual_parts(int32_t n, const int64_t* bcolptr, const int32_t* browind, const double* bvals,
+                               const int64_t* lp, const int32_t* li, const double* lx, int32_t nthreads,
+                               double* num, double* den) {
+  int64_t nnz = lp[n];
+  size_t nn = (size_t)(n > 0 ? n : 1);
+  int64_t* rcount = (int64_t*)calloc(nn + 1, sizeof(int64_t));
+  for (int64_t t = 0; t < nnz; ++t) rcount[li[t] + 1]++;
+  for (int32_t i = 0; i < n; ++i) rcount[i + 1] += rcount[i];
+  int64_t* fill = (int64_t*)malloc(sizeof(int64_t) * nn);
+  for (int32_t i = 0; i < n; ++i) fill[i] = rcount[i];
+  int64_t* rent = (int64_t*)malloc(sizeof(int64_t) * (size_t)(nnz > 0 ? nnz : 1));
+  int32_t* rcol = (int32_t*)malloc(sizeof(int32_t) * (size_t)(nnz > 0 ? nnz : 1));
+  for (int32_t k = 0; k < n; ++k)
+    for (int64_t t = lp[k]; t < lp[k + 1]; ++t) { rent[fill[li[t]]] = t; rcol[fill[li[t]]] = k; fill[li[t]]++; }
+  int nt = 1;
+#ifdef _OPENMP
+  nt = nthreads > 0 ? nthreads : omp_get_max_threads();
+#endif
+  (void)nthreads;
+  double* wall = (double*)calloc(nn * (size_t)nt, sizeof(double));
+#ifdef _OPENMP
+#pragma omp parallel for schedule(dynamic, 64) num_threads(nt)
+#endif
+  for (int32_t j = 0; j < n; ++j) {
+    int tid = 0;
+#ifdef _OPENMP
+    tid = omp_get_thread_num();
+#endif
+    double* w = wall + (size_t)tid * nn;
+    double bn = 0.0;
+    for (int64_t t = bcolptr[j]; t < bcolptr[j + 1]; ++t) {
+      w[browind[t]] += bvals[t];
+      bn += (browind[t] == j ? 1.0 : 2.0) * bvals[t] * bvals[t];
+    }
+    for (int64_t e = rcount[j]; e < rcount[j + 1]; ++e) {
+      int64_t tj = rent[e];
+      int32_t k = rcol[e];
+      double ljk = lx[tj];
+      for (int64_t t = tj; t < lp[k + 1]; ++t) w[li[t]] -= lx[t] * ljk;
+    }
+    double rn = 0.0;
+    for (int64_t e = rcount[j]; e < rcount[j + 1]; ++e) {
+      int32_t k = rcol[e];
+      for (int64_t t = rent[e]; t < lp[k + 1]; ++t) {
+        int32_t i = li[t];
+        rn += (i == j ? 1.0 : 2.0) * w[i] * w[i];
+        w[i] = 0.0;
+      }
+    }
+    for (int64_t t = bcolptr[j]; t < bcolptr[j + 1]; ++t) {
+      int32_t i = browind[t];
+      rn += (i == j ? 1.0 : 2.0) * w[i] * w[i];
+      w[i] = 0.0;
+    }
+    num[j] = rn;
+    den[j] = bn;
+  }
+  free(wall); free(rcount); free(fill); free(rent); free(rcol);
 }
 
 /* ------------------------------------------------------------------------ */

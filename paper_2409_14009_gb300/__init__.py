@@ -31,7 +31,7 @@ CHOL_PREC_BF16 = 3
 CHOL_UPDATE_RL = 0
 CHOL_UPDATE_RLB = 1
 
-EXPORTED = ["chol_default_options", "chol_analyze", "chol_factor", "chol_solve", "chol_solve_noalloc", "chol_check_waits",
+EXPORTED = ["chol_default_options", "chol_analyze", "chol_factor", "chol_solve", "chol_solve_noalloc", "chol_check_waits", "chol_factor_solve_host",
             "chol_solve_refine", "chol_logdet", "chol_analyze_batch", "chol_logdet_batch", "chol_autotune",
             "chol_factor_batch", "chol_solve_batch",
             "chol_selected_inverse", "chol_adjoint",
@@ -98,6 +98,8 @@ def lib():
         L.chol_solve_noalloc.restype = C.c_int
         L.chol_check_waits.argtypes = [P, P]
         L.chol_check_waits.restype = C.c_int
+        L.chol_factor_solve_host.argtypes = [P, P, P, P, C.c_int32, C.POINTER(C.c_double), P]
+        L.chol_factor_solve_host.restype = C.c_int
         L.chol_solve_refine.argtypes = [P, P, P, C.c_int32, C.c_double, C.c_int32,
                                         C.POINTER(C.c_int32), P, P]
         L.chol_solve_refine.restype = C.c_int
@@ -226,6 +228,24 @@ def chol_solve(h, b, nrhs, stream=None) -> int:
 def chol_solve_noalloc(h, b, nrhs, stream=None) -> int:
     """chol_solve whose workspaces come from a fixed device array (no allocation)."""
     return lib().chol_solve_noalloc(h, _dev_ptr(b), int(nrhs), _stream(stream))
+
+
+def _host_ptr(a):
+    """Address of host data: a NumPy array or a CPU torch tensor (pinned or not)."""
+    if a is None:
+        return None
+    if isinstance(a, np.ndarray):
+        return a.ctypes.data_as(C.c_void_p)
+    return C.c_void_p(a.data_ptr())
+
+
+def chol_factor_solve_host(h, values, b, x, nrhs, want_logdet=True, stream=None):
+    """Factor + solve + log det from host buffers (values, b, x: host arrays).
+    Returns (rc, logdet or None)."""
+    ld = C.c_double(0.0)
+    rc = lib().chol_factor_solve_host(h, _host_ptr(values), _host_ptr(b), _host_ptr(x), int(nrhs),
+                                      C.byref(ld) if want_logdet else None, _stream(stream))
+    return rc, (ld.value if want_logdet else None)
 
 
 def chol_check_waits(h, stream=None) -> int:

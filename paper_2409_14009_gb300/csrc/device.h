@@ -94,6 +94,10 @@ struct DeviceState {
   // solve workspaces (grown on demand)
   double* Y = nullptr;          // permuted right-hand sides, n x chunk
   double* W = nullptr;          // per-level panel products, w_rows_max x chunk
+  // staging of chol_factor_solve_host (host-buffer entry point)
+  double* host_vals = nullptr;  // nnz(A) values
+  double* host_rhs = nullptr;   // n x nrhs right-hand sides / solutions
+  int64_t host_rhs_cap = 0;
 };
 
 // Right-hand sides are processed in chunks of at most this many columns.

@@ -648,7 +648,7 @@ void chol_device_free(chol_handle* h) {
                   D->ssmall, D->Zp, D->Tw, D->Ww, D->Uh, D->a_col, D->a_row, D->adj_xb, D->perm, D->status, D->part, D->scalar_dev, D->Y, D->W,
                   D->mx_diagpos, D->mx_aij, D->mx_d, D->mx_fallbacks, D->csr_ptr, D->csr_col, D->csr_src,
                   D->csr_val, D->Lbf, D->tmaps, D->tc_err, D->R, D->Z, D->Pv, D->Q, D->red, D->Y32, D->W32,
-                  D->rhs_scale};
+                  D->rhs_scale, D->host_vals, D->host_rhs};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   if (D->status_host) cudaFreeHost(D->status_host);
@@ -1117,6 +1117,45 @@ extern "C" int chol_logdet(chol_handle* h, double* out, void* stream) {
   CHOL_CUDA_TRY(cudaStreamSynchronize(st));
   *out = *D->scalar_host;
   return CHOL_OK;
+}
+
+extern "C" int chol_factor_solve_host(chol_handle* h, const double* values, const double* b, double* x,
+                                      int32_t nrhs, double* logdet, void* stream) {
+  NvtxRange nvtx_range("chol_factor_solve_host");
+  if (!h) return -1;
+  if (!values && h->nnz_a > 0) return -2;
+  if (!b && nrhs > 0 && h->n > 0) return -3;
+  if (!x && nrhs > 0 && h->n > 0) return -4;
+  if (nrhs < 0) return -5;
+  int rc = chol_device_ensure(h);
+  if (rc) return rc;
+  DeviceState* D = h->dev;
+  cudaStream_t st = (cudaStream_t)stream;
+  const size_t nb = (size_t)h->n * (size_t)nrhs;
+  if (h->nnz_a > 0 && !D->host_vals) {
+    if ((rc = chol_dalloc(h, (void**)&D->host_vals, sizeof(double) * (size_t)h->nnz_a))) return rc;
+  }
+  if (nb > (size_t)D->host_rhs_cap) {
+    if (D->host_rhs) {
+      cudaFree(D->host_rhs);
+      D->bytes -= sizeof(double) * (size_t)D->host_rhs_cap;
+      D->host_rhs = nullptr;
+      D->host_rhs_cap = 0;
+    }
+    if ((rc = chol_dalloc(h, (void**)&D->host_rhs, sizeof(double) * nb))) return rc;
+    D->host_rhs_cap = (int64_t)nb;
+  }
+  if (h->nnz_a > 0)
+    CHOL_CUDA_TRY(cudaMemcpyAsync(D->host_vals, values, sizeof(double) * (size_t)h->nnz_a, cudaMemcpyHostToDevice, st));
+  if ((rc = chol_factor(h, D->host_vals, stream))) return rc;
+  if (nb > 0) {
+    CHOL_CUDA_TRY(cudaMemcpyAsync(D->host_rhs, b, sizeof(double) * nb, cudaMemcpyHostToDevice, st));
+    if ((rc = chol_solve(h, D->host_rhs, nrhs, stream))) return rc;
+  }
+  if (logdet && (rc = chol_logdet(h, logdet, stream))) return rc;
+  if (nb > 0) CHOL_CUDA_TRY(cudaMemcpyAsync(x, D->host_rhs, sizeof(double) * nb, cudaMemcpyDeviceToHost, st));
+  CHOL_CUDA_TRY(cudaStreamSynchronize(st));
+  return chol_solve_status(h);
 }
 
 extern "C" int chol_get_factor(chol_handle* h, int64_t* lp, int32_t* li, double* lx, void* stream) {

@@ -134,3 +134,26 @@ def test_batch_entry_points_match_the_oracle_per_system():
             assert np.max(np.abs(x[s0:s1] - ref["x"])) <= 1e-12 * max(1.0, np.max(np.abs(ref["x"])))
     finally:
         P.chol_destroy(h)
+
+
+@pytest.mark.parametrize("persistent", [0, 1])
+def test_batch_large_sides_at_bench_thresholds(persistent):
+    """Systems with grid sides up to 96 (the top of the benchmark's range),
+    with the benchmark's kernel-class thresholds (160 columns, 24,576 panel
+    entries, 512 rows on the one-CTA kernel), graph replay: every system's x
+    and log det against the oracle."""
+    P = chol()
+    probs, bd = _batch(count=16, kmin=80, kmax=96, seed=21)
+    assert max(p["meta"]["k"] for p in probs) >= 90
+    b = gridgen.rhs_uniform(bd.n, 1, seed=22)
+    o = _opts(P, 0, persistent, 1)
+    o.small_max_cols, o.small_max_panel, o.small_max_rows = 160, 24576, 512
+    got = _run(P, bd, o, b)
+    assert got["info"].persistent_ok == 1
+    offs = bd["meta"]["offsets"]
+    for q, p in enumerate(probs):
+        bq = b[offs[q]:offs[q + 1]]
+        ref = oracle.reference(p, bq)
+        xq = got["x"][offs[q]:offs[q + 1]]
+        assert np.max(np.abs(xq - ref["x"])) <= 1e-11 * np.max(np.abs(ref["x"]))
+        assert abs(got["logdet"][q] - ref["fac"].logdet()) <= 1e-12 * abs(ref["fac"].logdet())

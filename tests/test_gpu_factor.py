@@ -10,7 +10,7 @@ import pytest
 
 import gridgen
 import oracle
-from gpu_util import check_parity, run
+from gpu_util import check_parity, colmajor, run
 from helpers import lower_csc_from_dense, random_spd
 from lib_fixture import chol
 
@@ -195,5 +195,41 @@ def test_solve_replays_from_a_cuda_graph():
             x = X.cpu().numpy()
             ref = oracle.reference(p, b)
             assert np.max(np.abs(x - ref["x"])) <= 1e-8 * np.max(np.abs(ref["x"]))
+    finally:
+        P.chol_destroy(h)
+
+
+def test_factor_solve_from_host_buffers_matches_device_path():
+    """chol_factor_solve_host (values and right-hand sides in host memory,
+    pinned or pageable) gives the device path's x and log det, and the oracle's."""
+    import torch
+    P = chol()
+    p = gridgen.laplacian_neumann_varcoef((13, 12, 11), 1e-2, 1e2, 1e-6, seed=9)
+    b = gridgen.rhs_uniform(p.n, 3, seed=10)
+    ref = oracle.reference(p, b)
+    rc, h = P.chol_analyze(p.n, p["colptr"], p["rowind"], p["perm"])
+    assert rc == 0
+    try:
+        for pinned in (False, True):
+            vals = torch.as_tensor(p["values"])
+            bh = torch.as_tensor(np.ascontiguousarray(b.T))          # column-major n x 3
+            xh = torch.zeros_like(bh)
+            if pinned:
+                vals, bh, xh = vals.pin_memory(), bh.pin_memory(), xh.pin_memory()
+            rc, ld = P.chol_factor_solve_host(h, vals, bh, xh, 3)
+            assert rc == 0
+            x = xh.numpy().T
+            eta = oracle.backward_error(p.n, p["colptr"], p["rowind"], p["values"], b, x)
+            assert np.all(eta <= 1e-12), eta
+            assert np.max(np.abs(x - ref["x"])) <= 1e-12 * np.max(np.abs(ref["x"]))
+            assert abs(ld - ref["fac"].logdet()) <= 1e-12 * abs(ref["fac"].logdet())
+        xd = colmajor(b)
+        assert P.chol_solve(h, xd, 3) == 0
+        torch.cuda.synchronize()
+        assert np.array_equal(xd.cpu().numpy(), x)
+        # x may alias b
+        bh2 = torch.as_tensor(np.ascontiguousarray(b.T)).pin_memory()
+        rc, _ = P.chol_factor_solve_host(h, torch.as_tensor(p["values"]), bh2, bh2, 3, want_logdet=False)
+        assert rc == 0 and np.array_equal(bh2.numpy().T, x)
     finally:
         P.chol_destroy(h)

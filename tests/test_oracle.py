@@ -439,3 +439,47 @@ def test_threaded_factor_reports_the_first_bad_pivot():
     assert b.info == 2
     cp, ri, vx = lower_csc_from_dense(np.zeros((0, 0)))
     assert oracle.Factor(0, np.zeros(1, np.int64), np.zeros(0, np.int32), np.zeros(0), threads=0).info == 0
+
+
+@pytest.mark.parametrize("threads", [0, 3])
+def test_staged_factor_equals_one_piece_run(threads):
+    """The timing form that runs the multi-threaded factor in pieces of
+    elimination-tree heights gives the one-piece result bit for bit, for any
+    split, and its per-height work adds up to the flop convention."""
+    g = gridgen.laplacian_neumann_varcoef((10, 9, 8), 1e-2, 1e2, 1e-6, seed=6)
+    bp, bi, bx = oracle.permute(g.n, g["colptr"], g["rowind"], g["values"], g["perm"])
+    one = oracle.Factor(g.n, bp, bi, bx, threads=threads)
+    rs = np.random.RandomState(threads)
+    for trial in range(3):
+        S = oracle.StagedFactor(g.n, bp, bi, bx, threads=threads)
+        w = S.work()
+        assert len(w) == S.max_height + 1
+        assert w.sum() == S.sym.flops()
+        cuts = np.unique(np.concatenate([[0, S.max_height + 1], rs.randint(0, S.max_height + 1, 4)]))
+        for a, b in zip(cuts[:-1], cuts[1:]):
+            S.run(a, b)
+        f = S.finish()
+        assert f.info == 0
+        assert np.array_equal(f.lp, one.lp) and np.array_equal(f.li, one.li) and np.array_equal(f.lx, one.lx)
+
+
+def test_residual_parts_match_dense_frobenius():
+    """The column-parallel factor residual against the dense formula
+    ||B - L L^T||_F / ||B||_F, on a perturbed factor (so that the residual is
+    far above rounding), and its per-column values against dense columns."""
+    A, cp, ri, vx, perm = random_spd(60, 0.1, 23)
+    bp, bi, bx = oracle.permute(60, cp, ri, vx, perm)
+    fac = oracle.Factor(60, bp, bi, bx)
+    lx = fac.lx * (1.0 + np.random.RandomState(5).uniform(-1e-7, 1e-7, fac.lx.shape))
+    Lp = csc_to_dense_lower(60, fac.lp, fac.li, lx)
+    P = np.eye(60)[perm]
+    B = P @ A @ P.T
+    R = B - Lp @ Lp.T
+    tot, cols = oracle.factor_residual_parts(60, bp, bi, bx, fac.lp, fac.li, lx, threads=3)
+    assert tot == pytest.approx(np.linalg.norm(R) / np.linalg.norm(B), rel=1e-8)
+    assert tot == pytest.approx(oracle.factor_residual(60, bp, bi, bx, fac.lp, fac.li, lx), rel=1e-8)
+    w = np.ones(60); w[1:] = 2.0
+    for j in (0, 11, 37, 59):
+        rj = R[j:, j]; bj = B[j:, j]
+        exp = np.sqrt(np.sum(w[: len(rj)] * rj ** 2) / np.sum(w[: len(bj)] * bj ** 2))
+        assert cols[j] == pytest.approx(exp, rel=1e-6)
