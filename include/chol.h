@@ -434,6 +434,7 @@ enum chol_kernel_class {
   CHOL_K_PERMUTE, CHOL_K_LOGDET, CHOL_K_SOLVE_GEMV,
   CHOL_K_SELINV_GATHER,  /* selected inverse: Z_RR gathered from the ancestors */
   CHOL_K_ADJOINT,        /* per-entry gradient */
+  CHOL_K_PANEL,          /* mixed modes: POTRF, TRSM and in-block updates of an outer column block */
   CHOL_K_NCLASSES
 };
 

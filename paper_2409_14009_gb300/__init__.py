@@ -40,7 +40,7 @@ EXPORTED = ["chol_default_options", "chol_analyze", "chol_factor", "chol_solve",
 
 KERNEL_CLASSES = ["scatter", "small", "potrf", "trsm", "gemm", "syrk", "assemble", "solve_diag",
                   "selinv_inv", "solve_fasm", "solve_bpanel", "selinv_gemm", "permute", "logdet",
-                  "solve_gemv", "selinv_gather", "adjoint"]
+                  "solve_gemv", "selinv_gather", "adjoint", "panel"]
 
 
 class chol_options(C.Structure):

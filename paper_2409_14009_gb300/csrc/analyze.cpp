@@ -425,6 +425,7 @@ void build(chol_handle* h, const int64_t* colptr, const int32_t* rowind) {
   // it at one 64-column block (a single SM's FP64 rate is the limit); binary32
   // takes 256 to cut the number of dependent launches.
   const bool tc_modes = h->opt.precision == CHOL_PREC_TF32 || h->opt.precision == CHOL_PREC_BF16;
+  const bool mixed = h->opt.precision != CHOL_PREC_FP64;
   const int tg = tc_modes ? kTileTC : kTile;
   std::vector<std::vector<int32_t>> by_level(h->nlevels);
   for (int32_t J = 0; J < ns; ++J) by_level[h->level[J]].push_back(J);
@@ -437,6 +438,7 @@ void build(chol_handle* h, const int64_t* colptr, const int32_t* rowind) {
   h->levels.assign(h->nlevels, LevelPlan{});
   h->level_snodes.clear(); h->small_list.clear(); h->potrf_list.clear();
   h->trsm_tasks.clear(); h->gemm_tasks.clear(); h->syrk_tasks.clear();
+  h->panel_items.clear(); h->panel_nflags = 0; h->panel_ntickets = 0;
   h->bpanel_tasks.clear(); h->tri_items.clear(); h->tri_nflags = 0;
   h->ssmall_list.clear();
   h->gemv_tasks.clear(); h->bpart_tasks.clear(); h->bred_tasks.clear();
@@ -486,7 +488,63 @@ void build(chol_handle* h, const int64_t* colptr, const int32_t* rowind) {
     for (int32_t J : large) maxs = std::max(maxs, h->snodes[J].s);
     // binary64 TRSM tasks are half as tall: each CTA's substitution is DFMA-bound
     const int32_t trsm_rows = h->opt.precision == CHOL_PREC_FP64 ? kTrsmRowsHost / 2 : kTrsmRowsHost;
-    for (int32_t k0 = 0; k0 < maxs; k0 += nb) {
+    // mixed modes: one panel launch per outer block of kTcOuter columns (its
+    // 64-column POTRF/TRSM/update steps inside, tile by tile), then the update
+    // of the columns right of it with K = the block
+    for (int32_t ob = 0; mixed && ob < maxs; ob += kTcOuter) {
+      StepRange st{};
+      st.potrf_b = (int32_t)h->potrf_list.size();
+      st.trsm_b = (int32_t)h->trsm_tasks.size();
+      st.gemm_b = (int32_t)h->gemm_tasks.size();
+      st.panel_b = (int32_t)h->panel_items.size();
+      st.panel_ticket = h->panel_ntickets++;
+      std::vector<int32_t> fb(large.size(), -1);
+      for (int32_t dsub = 0; dsub < kTcOuter / 64; ++dsub)
+        for (size_t q = 0; q < large.size(); ++q) {
+          const SnodeDev& d = h->snodes[large[q]];
+          if (d.s <= ob) continue;
+          if (fb[q] < 0) { fb[q] = h->panel_nflags; h->panel_nflags += kTcOuter / 64; }
+          const int32_t w = std::min(kTcOuter, d.s - ob);
+          if (dsub * 64 < w) h->panel_items.push_back({large[q], ob + dsub * 64, dsub, fb[q]});
+        }
+      for (size_t q = 0; q < large.size(); ++q) {
+        const SnodeDev& d = h->snodes[large[q]];
+        if (d.s <= ob) continue;
+        const int32_t w = std::min(kTcOuter, d.s - ob);
+        // diagonal tiles hold the rows [ob, ob + w); every row below is in a tile
+        for (int32_t r0 = ob + w; r0 < d.len; r0 += 64) h->panel_items.push_back({large[q], r0, -1, fb[q]});
+        // flop convention: the block's columns contribute sum c^2; the part of
+        // their outer products right of the block is the outer update's
+        for (int32_t j = ob; j < ob + w; ++j) st.panel_flops += (double)(d.len - j) * (d.len - j);
+      }
+      st.panel_n = (int32_t)h->panel_items.size() - st.panel_b;
+      st.ogemm_b = (int32_t)h->gemm_tasks.size();
+      st.ok0 = ob;
+      st.okb = kTcOuter;
+      const int32_t oend = ob + kTcOuter;
+      for (int32_t J : large) {
+        const SnodeDev& d = h->snodes[J];
+        if (d.s <= oend) continue;
+        const double w = (double)(d.s - oend), hgt = (double)(d.len - oend);
+        st.ogemm_flops += 2.0 * kTcOuter * (w * hgt - w * (w - 1.0) / 2.0);
+      }
+      st.panel_flops -= st.ogemm_flops;
+      // the next outer block's column tiles of every supernode first
+      for (int pass = 0; pass < 2; ++pass) {
+        for (int32_t J : large) {
+          const SnodeDev& d = h->snodes[J];
+          if (d.s <= oend) continue;
+          for (int32_t c0 = oend; c0 < d.s; c0 += tg) {
+            if ((pass == 0) != (c0 < oend + kTcOuter)) continue;
+            for (int32_t r0 = c0; r0 < d.len; r0 += tg) h->gemm_tasks.push_back({J, ob, r0, c0});
+          }
+        }
+        if (pass == 0) st.ogemm_next = (int32_t)h->gemm_tasks.size() - st.ogemm_b;
+      }
+      st.ogemm_n = (int32_t)h->gemm_tasks.size() - st.ogemm_b;
+      P.steps.push_back(st);
+    }
+    for (int32_t k0 = 0; !mixed && k0 < maxs; k0 += nb) {
       StepRange st{};
       st.potrf_b = (int32_t)h->potrf_list.size();
       st.potrf_flops = st.trsm_flops = st.gemm_flops = st.ogemm_flops = 0.0;

@@ -55,7 +55,10 @@ struct DeviceState {
   double* csr_val = nullptr;
   void* Lbf = nullptr;             // bf16 copy of the panels (CHOL_PREC_BF16)
   CUtensorMap* tmaps = nullptr;    // one TMA map per supernode
-  int32_t* tc_err = nullptr;       // tensor-core tile timeout flag
+  int32_t* tc_err = nullptr;       // tensor-core tile / panel wait timeout flag
+  PanelItem* panel = nullptr;      // panel-launch tiles (mixed modes)
+  int32_t* pflags = nullptr;       // panel work counters, then progress flags (zeroed per factorization)
+  int panel_ctas = 0;              // resident panel CTAs on the device
   // refinement workspaces
   double* R = nullptr;
   double* Z = nullptr;

@@ -63,10 +63,25 @@ struct AsmSeg {
 // of every supernode first (gemm_next of them: the next step's block column),
 // then the rest, so the rest can run beside the next POTRF and TRSM
 // (one-step lookahead).
+// Mixed modes: a step is one outer block [ok0, ok0 + kTcOuter) of columns; its
+// POTRF, TRSM and in-block updates run in one panel launch (panel_*: 64-row
+// tiles, see PanelItem; panel_ticket: the launch's work counter), then the
+// columns right of the block get one update with K = the block (ogemm_*, the
+// next block's column tiles first).
 struct StepRange {
   int32_t potrf_b, potrf_n, trsm_b, trsm_n, gemm_b, gemm_n, ogemm_b, ogemm_n, ok0, okb;
   int32_t gemm_next, ogemm_next;
-  double potrf_flops, trsm_flops, gemm_flops, ogemm_flops;
+  int32_t panel_b, panel_n, panel_ticket, pad;
+  double potrf_flops, trsm_flops, gemm_flops, ogemm_flops, panel_flops;
+};
+
+// One 64-row tile of a supernode's outer column block in a panel launch:
+// supernode J, first row r0 of the tile, d = index of the 64-column sub-block
+// whose diagonal block the rows hold (-1: the rows lie below the outer block),
+// fbase = first of J's four progress flags in the launch. Items are listed
+// with every diagonal tile (by d, then J) before the tiles below.
+struct PanelItem {
+  int32_t J, r0, d, fbase;
 };
 
 // Blocked triangular-solve step k0 of one level: diagonal blocks of every
@@ -153,6 +168,8 @@ struct chol_handle {
   std::vector<TileTask> gemv_tasks;             // solve: (J, r0) off-diagonal row tiles
   std::vector<TileTask> bpart_tasks, bred_tasks; // solve: row-major backward panel stages
   int64_t p_max = 0;                            // largest per-level partial-sum rows
+  std::vector<PanelItem> panel_items;           // mixed modes: panel-launch tiles, step by step
+  int32_t panel_nflags = 0, panel_ntickets = 0; // progress flags and work counters of all panel launches
   std::vector<AsmTask> asm_tasks;
   std::vector<AsmSeg> asm_segs;
   int32_t n_small = 0, n_large = 0;

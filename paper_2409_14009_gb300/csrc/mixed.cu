@@ -203,6 +203,263 @@ k_mx_trsm(const SnodeDev* __restrict__ sn, const TileTask* __restrict__ tasks, i
   }
 }
 
+// ---------------------------------------------------------------------------
+// Panel factorization of one outer column block [ob, ob + w), w <= kTcOuter,
+// of every large supernode of a level (Sec. II-A: the POTRF, TRSM and update
+// steps of the block's 64-column sub-blocks), binary32, in one launch.
+//
+// A CTA takes 64-row tiles of the block (PanelItem) from a work counter in
+// list order and keeps its tile (64 x w) in shared memory through every
+// sub-step. The tile holding the rows of sub-block d (a "diagonal tile"):
+// for each j < d, the TRSM of its sub-block j against L_jj and the update of
+// its sub-blocks j+1..d; then the POTRF of its diagonal block. A tile below
+// the block does the TRSM and update for every sub-block. Tiles hand results
+// to each other through global memory and one progress flag per diagonal
+// tile: prog(d) = j + 1 once its TRSM of sub-block j is stored (j < d), and
+// d + 1 once its L_dd is stored. A tile waits for prog(j) >= j + 1 (L_jj) and
+// for prog(j') >= j + 1 (rows of sub-block j', columns of j) before using
+// them. Every wait points to a diagonal tile with a smaller d, which comes
+// earlier in the list, and items are taken in list order by running CTAs, so
+// the smallest unfinished item can always proceed (no co-residency needed).
+// Waits are bounded: one that runs out sets *err and carries on (the factor
+// is then invalid and chol_factor reports CHOL_ETIMEOUT).
+//
+// Arithmetic per entry is that of the 64-column steps: the diagonal block in
+// 8-column panels (binary64 redo below tau), the TRSM by substitution with
+// the reciprocal pivots, the in-block updates as binary32 fused
+// multiply-subtracts in column order.
+// ---------------------------------------------------------------------------
+constexpr int kPnW = kTcOuter;          // outer block width
+static_assert(kPnW == 256, "the tile staging below indexes columns with 8 bits");
+constexpr int kPnLd = kPnW + 4;         // shared tile row stride (floats)
+constexpr size_t kPnSmem = sizeof(float) * ((size_t)64 * kPnLd + 2 * 64 * kPwLd + 64);
+constexpr long long kPanelMaxPolls = 1ll << 21;   // about a second with the back-off
+
+__device__ __forceinline__ int pn_ld_acquire(const int* p) {
+  int v;
+  asm volatile("ld.acquire.gpu.global.b32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+  return v;
+}
+
+__device__ __forceinline__ void pn_st_release(int* p, int v) {
+  asm volatile("st.release.gpu.global.b32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+
+// One thread waits (bounded) until *flag >= need; then the CTA proceeds. Once
+// any wait of the launch has run out (*err set), the others give up at once,
+// so a launch with a broken hand-off ends after one wait limit.
+__device__ __forceinline__ void pn_wait(const int* flag, int need, long long max_polls, int* err) {
+  if (threadIdx.x == 0) {
+    long long polls = 0;
+    while (pn_ld_acquire(flag) < need) {
+      if (++polls > max_polls) { atomicExch(err, 1); break; }
+      if ((polls & 255) == 0 && *(volatile int*)err != 0) break;
+      if (polls > 2048) __nanosleep(64);
+    }
+  }
+  __syncthreads();
+}
+
+// Publish after the CTA's global stores (release of everything the CTA wrote).
+__device__ __forceinline__ void pn_publish(int* flag, int v) {
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    __threadfence();
+    pn_st_release(flag, v);
+  }
+}
+
+__global__ void __launch_bounds__(256, 2)
+k_mx_panel(const SnodeDev* __restrict__ sn, const PanelItem* __restrict__ items, int nitems, int ob,
+           float* __restrict__ L, __nv_bfloat16* __restrict__ Lb, int* ticket, int* flags, int* err,
+           long long max_polls, float tau, int static_pivot, int* status, int* counters) {
+  extern __shared__ __align__(16) float pn_smem[];
+  float* Own = pn_smem;                 // the tile: 64 rows x w columns (row stride kPnLd)
+  float* Lk = Own + 64 * kPnLd;         // L_jj, column-major (ld kPwLd); POTRF staging (row-major)
+  float* Xo = Lk + 64 * kPwLd;          // rows of sub-block j', columns of j (row-major, ld kPwLd)
+  float* inv = Xo + 64 * kPwLd;         // reciprocal pivots of L_jj
+  __shared__ int s_item, s_ok;
+  __shared__ double colk_d[64];
+  __shared__ double sinv_d;
+  const int tid = threadIdx.x;
+  for (;;) {
+    __syncthreads();
+    if (tid == 0) s_item = atomicAdd(ticket, 1);
+    __syncthreads();
+    const int it = s_item;
+    if (it >= nitems) break;
+    const PanelItem item = items[it];
+    const SnodeDev d = sn[item.J];
+    const int w = min(kPnW, d.s - ob);
+    const int nsub = (w + 63) >> 6;
+    const int dd = item.d;                           // -1: below the block
+    // valid rows: a diagonal tile holds exactly the rows of its diagonal block
+    const int m = dd >= 0 ? min(64, w - dd * 64) : min(64, d.len - item.r0);
+    const int jend = dd >= 0 ? dd : nsub;            // TRSM sub-steps of this tile
+    int* fl = flags + item.fbase;
+    float* G = L + d.loff + (int64_t)item.r0 * d.ld + ob;   // row 0, column 0 of the tile
+    // stage the tile: 64 rows x 256 columns, 8 loads in flight per thread
+    for (int e0 = 0; e0 < 64 * kPnW; e0 += 8 * 256) {
+      float v[8];
+#pragma unroll
+      for (int u = 0; u < 8; ++u) {
+        const int e = e0 + u * 256 + tid, r = e >> 8, c = e & 255;
+        v[u] = (r < m && c < w) ? G[(int64_t)r * d.ld + c] : 0.f;
+      }
+#pragma unroll
+      for (int u = 0; u < 8; ++u) {
+        const int e = e0 + u * 256 + tid;
+        Own[(e >> 8) * kPnLd + (e & 255)] = v[u];
+      }
+    }
+    for (int j = 0; j < jend; ++j) {
+      const int c0 = j * 64, kb = min(64, w - c0);
+      // L_jj (stored by the diagonal tile j) and its reciprocal pivots
+      pn_wait(fl + j, j + 1, max_polls, err);
+      {
+        const float* Gd = L + d.loff + (int64_t)(ob + c0) * d.ld + ob + c0;
+        float v[16];
+#pragma unroll
+        for (int i = 0; i < 16; ++i) {
+          const int q = tid + 256 * i, r = q >> 6, c = q & 63;
+          v[i] = (r < kb && c <= r) ? __ldcg(Gd + (int64_t)r * d.ld + c) : 0.f;
+        }
+#pragma unroll
+        for (int i = 0; i < 16; ++i) {
+          const int q = tid + 256 * i;
+          Lk[(q >> 6) + (q & 63) * kPwLd] = v[i];
+        }
+      }
+      __syncthreads();
+      if (tid < kb) inv[tid] = 1.0f / Lk[tid + tid * kPwLd];
+      __syncthreads();
+      // TRSM of the tile's sub-block j: four lanes per row, lane q holds
+      // columns q + 4 mm; the solved entry is passed by shuffle
+      {
+        const int g = tid >> 2, q = tid & 3;
+        float* Xr = Own + g * kPnLd + c0;
+        float x[16];
+#pragma unroll
+        for (int mm = 0; mm < 16; ++mm) {
+          const int c = q + 4 * mm;
+          x[mm] = c < kb ? Xr[c] : 0.f;
+        }
+#pragma unroll
+        for (int jm = 0; jm < 16; ++jm) {
+#pragma unroll
+          for (int jq = 0; jq < 4; ++jq) {
+            const int jj = jm * 4 + jq;
+            if (jj < kb) {
+              const float xj = __shfl_sync(0xffffffffu, x[jm] * inv[jj], jq, 4);
+              if (q == jq) x[jm] = xj;
+#pragma unroll
+              for (int mm = jm; mm < 16; ++mm) {
+                const int c = q + 4 * mm;
+                if (c > jj && c < kb) x[mm] = fmaf(-xj, Lk[c + jj * kPwLd], x[mm]);
+              }
+            }
+          }
+        }
+        float* Gx = G + (int64_t)g * d.ld + c0;
+        __nv_bfloat16* Bx = Lb ? Lb + d.loff + (int64_t)(item.r0 + g) * d.ld + ob + c0 : nullptr;
+#pragma unroll
+        for (int mm = 0; mm < 16; ++mm) {
+          const int c = q + 4 * mm;
+          if (c < kb) {
+            Xr[c] = x[mm];
+            if (g < m) {
+              Gx[c] = x[mm];
+              if (Bx) Bx[c] = __float2bfloat16_rn(x[mm]);
+            }
+          }
+        }
+      }
+      if (dd >= 0) pn_publish(fl + dd, j + 1);   // this tile's rows of sub-block j are stored
+      __syncthreads();
+      // updates of the later sub-blocks j' this tile holds: below the block
+      // every j' < nsub; a diagonal tile up to its own diagonal block
+      const int jlast = dd >= 0 ? dd : nsub - 1;
+      for (int jp = j + 1; jp <= jlast; ++jp) {
+        const int cp = jp * 64, kbp = min(64, w - cp);
+        const float* Y;   // rows of sub-block j' (columns of j), row stride yld
+        int yld;
+        if (jp == dd) {
+          Y = Own + c0;
+          yld = kPnLd;
+        } else {
+          pn_wait(fl + jp, j + 1, max_polls, err);
+          const float* Gy = L + d.loff + (int64_t)(ob + cp) * d.ld + ob + c0;
+          float v[16];
+#pragma unroll
+          for (int i = 0; i < 16; ++i) {
+            const int q = tid + 256 * i, r = q >> 6, c = q & 63;
+            v[i] = (r < kbp && c < kb) ? __ldcg(Gy + (int64_t)r * d.ld + c) : 0.f;
+          }
+#pragma unroll
+          for (int i = 0; i < 16; ++i) {
+            const int q = tid + 256 * i;
+            Xo[(q >> 6) * kPwLd + (q & 63)] = v[i];
+          }
+          __syncthreads();
+          Y = Xo;
+          yld = kPwLd;
+        }
+        // Own[:, j'] -= Own[:, j] Y^T: thread (tx, ty) owns rows ty + 16 i,
+        // columns tx + 16 l; K in column order
+        const int tx = tid & 15, ty = tid >> 4;
+        float acc[4][4] = {};
+        for (int k = 0; k < kb; ++k) {
+          float a[4], bv[4];
+#pragma unroll
+          for (int i = 0; i < 4; ++i) a[i] = Own[(ty + 16 * i) * kPnLd + c0 + k];
+#pragma unroll
+          for (int l = 0; l < 4; ++l) bv[l] = Y[(tx + 16 * l) * yld + k];
+#pragma unroll
+          for (int i = 0; i < 4; ++i)
+#pragma unroll
+            for (int l = 0; l < 4; ++l) acc[i][l] = fmaf(a[i], bv[l], acc[i][l]);
+        }
+        __syncthreads();   // every read of Own[:, j] and Y is done
+#pragma unroll
+        for (int i = 0; i < 4; ++i)
+#pragma unroll
+          for (int l = 0; l < 4; ++l) {
+            const int c = tx + 16 * l;
+            if (c < kbp) Own[(ty + 16 * i) * kPnLd + cp + c] -= acc[i][l];
+          }
+        __syncthreads();
+      }
+    }
+    if (dd >= 0) {
+      // POTRF of the diagonal block dd (rows and columns [cd, cd + kbd) of the tile)
+      const int cd = dd * 64, kbd = min(64, w - cd);
+      for (int q = tid; q < 64 * 64; q += 256) {
+        const int r = q >> 6, c = q & 63;
+        Lk[r * kPwLd + c] = (r < kbd && c <= r) ? Own[r * kPnLd + cd + c] : 0.f;
+      }
+      const bool ok = potrf_panels_smem<float>(kbd, tau, Lk, &s_ok, status, false, d.f + ob + cd);
+      float* Gd = G + cd;   // the tile's rows are those of the diagonal block
+      if (ok) {
+        for (int q = tid; q < 64 * 64; q += 256) {
+          const int r = q >> 6, c = q & 63;
+          if (r < kbd && c <= r) Gd[(int64_t)r * d.ld + c] = Lk[r * kPwLd + c];
+        }
+      } else {
+        // binary64 redo from the updated (unfactored) block
+        if (tid == 0) atomicAdd(counters, 1);
+        for (int q = tid; q < 64 * 64; q += 256) {
+          const int r = q >> 6, c = q & 63;
+          if (r < kbd && c <= r) Gd[(int64_t)r * d.ld + c] = Own[r * kPnLd + cd + c];
+        }
+        __syncthreads();
+        potrf_block<double, true, float>(Gd, d.ld, kbd, static_pivot ? (double)tau : 0.0, counters + 1, nullptr,
+                                         status, true, d.f + ob + cd, colk_d, &sinv_d, -INFINITY);
+      }
+      pn_publish(fl + dd, dd + 1);
+    }
+  }
+}
+
 // 64 x 64 binary32 SIMT tile of C (op)= A B^T with row-major A, B (K
 // contiguous) and row-major C; entries with row + rdiag >= col only.
 template <bool SUB>
@@ -466,6 +723,21 @@ int chol_mixed_ensure(chol_handle* h) {
   if ((rc = chol_dalloc(h, (void**)&D->mx_d, sizeof(double) * (size_t)std::max(h->n, 1)))) return rc;
   if ((rc = chol_dalloc(h, (void**)&D->mx_fallbacks, 2 * sizeof(int32_t)))) return rc;
   if ((rc = chol_tc_prepare(h))) return rc;
+  if (!D->tc_err) {
+    if ((rc = chol_dalloc(h, (void**)&D->tc_err, sizeof(int32_t)))) return rc;
+    CHOL_CUDA_TRY(cudaMemset(D->tc_err, 0, sizeof(int32_t)));
+  }
+  if ((rc = upload_vec(h, &D->panel, h->panel_items))) return rc;
+  if ((rc = chol_dalloc(h, (void**)&D->pflags, sizeof(int32_t) * (size_t)std::max(h->panel_ntickets + h->panel_nflags, 1))))
+    return rc;
+  if (cudaFuncSetAttribute(k_mx_panel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kPnSmem) != cudaSuccess)
+    return CHOL_ECUDA;
+  {
+    int per_sm = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_mx_panel, 256, kPnSmem) != cudaSuccess || per_sm < 1)
+      return CHOL_ECUDA;
+    D->panel_ctas = per_sm * D->sms;
+  }
   if (cudaFuncSetAttribute(k_mx_assemble, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024) != cudaSuccess)
     return CHOL_ECUDA;
   if (cudaFuncSetAttribute(k_mx_small, cudaFuncAttributeMaxDynamicSharedMemorySize, 24576 * 4) != cudaSuccess)
@@ -513,10 +785,14 @@ int chol_enqueue_factor_mixed(chol_handle* h, const double* values, cudaStream_t
   auto gemm = [&](const TileTask* tasks, int n, bool outer, double flops, cudaStream_t s2) -> int {
     if (n <= 0) return CHOL_OK;
     KScope ks(h, CHOL_K_GEMM, s2, flops, 0.0);
-    if (tc) return chol_tc_gemm(h, tasks, n, outer ? kTcOuter : nb, outer ? 0 : 1, s2);
-    k_mx_gemm_simt<<<n, 256, 0, s2>>>(D->sn, tasks, nb, L);
+    const int kk = outer ? kTcOuter : nb;
+    if (tc) return chol_tc_gemm(h, tasks, n, kk, outer ? 0 : 1, s2);
+    k_mx_gemm_simt<<<n, 256, 0, s2>>>(D->sn, tasks, kk, L);
     return CHOL_OK;
   };
+  // progress flags and work counters of this factorization's panel launches
+  if (h->panel_ntickets > 0)
+    CHOL_CUDA_TRY(cudaMemsetAsync(D->pflags, 0, sizeof(int32_t) * (size_t)(h->panel_ntickets + h->panel_nflags), st));
   for (const LevelPlan& P : h->levels) {
     NvtxRange nvtx_level("level", (long long)(&P - h->levels.data()));
     if (P.small_n > 0) {
@@ -524,38 +800,34 @@ int chol_enqueue_factor_mixed(chol_handle* h, const double* values, cudaStream_t
       k_mx_small<<<P.small_n, 128, sizeof(float) * P.small_max_panel, st>>>(D->sn, D->small_list + P.small_b, L, U,
                                                                               D->status, spiv, D->mx_fallbacks);
     }
-    // one-step lookahead as in the binary64 factor: each step's in-block and
-    // outer trailing tiles past the next block column run on the side stream
+    // one launch per outer column block: the panel kernel (its POTRF, TRSM and
+    // in-block update steps), then the update of the columns right of the
+    // block; the next block's column tiles on the critical stream, the rest on
+    // the side stream beside the next panel (one-step lookahead)
     bool rest_pending = false;
     for (size_t k = 0; k < P.steps.size(); ++k) {
       const StepRange& s = P.steps[k];
-      const int k0 = (int)k * nb;
-      if (s.potrf_n > 0) {
-        KScope ks(h, CHOL_K_POTRF, st, s.potrf_flops, 8.0 * nb * nb * s.potrf_n);
-        k_mx_potrf<<<s.potrf_n, 256, 0, st>>>(D->sn, D->potrf_list + s.potrf_b, k0, nb, (float)h->opt.pivot_tau,
-                                              h->opt.static_pivot, L, D->status, D->mx_fallbacks);
+      if (s.panel_n > 0) {
+        KScope ks(h, CHOL_K_PANEL, st, s.panel_flops, 0.0);
+        const int grid = std::min(s.panel_n, D->panel_ctas);
+        k_mx_panel<<<grid, 256, kPnSmem, st>>>(
+            D->sn, D->panel + s.panel_b, s.panel_n, s.ok0, L,
+            (__nv_bfloat16*)(h->opt.precision == CHOL_PREC_BF16 ? D->Lbf : nullptr), D->pflags + s.panel_ticket,
+            D->pflags + h->panel_ntickets, D->tc_err, h->opt.wait_polls > 0 ? (long long)h->opt.wait_polls : kPanelMaxPolls,
+            (float)h->opt.pivot_tau, h->opt.static_pivot, D->status, D->mx_fallbacks);
       }
-      if (s.trsm_n > 0) {
-        KScope ks(h, CHOL_K_TRSM, st, s.trsm_flops, 8.0 * kTrsmRowsHost * nb * s.trsm_n);
-        k_mx_trsm<<<s.trsm_n, 256, 0, st>>>(D->sn, D->trsm + s.trsm_b, nb, L,
-                                            (__nv_bfloat16*)(h->opt.precision == CHOL_PREC_BF16 ? D->Lbf : nullptr));
-      }
-      const int irest = s.gemm_n - s.gemm_next, orest = s.ogemm_n - s.ogemm_next;
-      if (irest + orest > 0) {
-        CHOL_CUDA_TRY(cudaEventRecord(D->lev[0], st));   // step k's panel is final
+      const int orest = s.ogemm_n - s.ogemm_next;
+      if (orest > 0) {
+        CHOL_CUDA_TRY(cudaEventRecord(D->lev[0], st));   // the block's panel is final
         CHOL_CUDA_TRY(cudaStreamWaitEvent(D->lstream, D->lev[0], 0));
       }
       if (rest_pending) {
         CHOL_CUDA_TRY(cudaStreamWaitEvent(st, D->lev[1], 0));
         rest_pending = false;
       }
-      const double fi = s.gemm_n > 0 ? (double)s.gemm_next / s.gemm_n : 0.0;
       const double fo = s.ogemm_n > 0 ? (double)s.ogemm_next / s.ogemm_n : 0.0;
-      if ((rc = gemm(D->gemm + s.gemm_b, s.gemm_next, false, s.gemm_flops * fi, st))) return rc;
       if ((rc = gemm(D->gemm + s.ogemm_b, s.ogemm_next, true, s.ogemm_flops * fo, st))) return rc;
-      if (irest + orest > 0) {
-        if ((rc = gemm(D->gemm + s.gemm_b + s.gemm_next, irest, false, s.gemm_flops * (1.0 - fi), D->lstream)))
-          return rc;
+      if (orest > 0) {
         if ((rc = gemm(D->gemm + s.ogemm_b + s.ogemm_next, orest, true, s.ogemm_flops * (1.0 - fo), D->lstream)))
           return rc;
         CHOL_CUDA_TRY(cudaEventRecord(D->lev[1], D->lstream));

@@ -170,25 +170,13 @@ __device__ __forceinline__ T fmsub(T a, T b, T c) {   // c - a b, one rounding
   if constexpr (sizeof(T) == 8) return fma(-a, b, c);
   else return fmaf(-a, b, c);
 }
-template <class T, bool RM>
-__device__ __forceinline__ bool potrf_panels(T* __restrict__ G, int64_t ld, int kb, float accept, T* __restrict__ As,
-                                             int* sok, int* status, bool record, int fcol) {
+// The panel loop of potrf_panels on a block already staged in As (64 rows of
+// kPwLd entries, lower triangle of a kb x kb block); uniform return value as
+// below. Nothing is read from or written to global memory except *status.
+template <class T>
+__device__ __forceinline__ bool potrf_panels_smem(int kb, float accept, T* __restrict__ As, int* sok, int* status,
+                                                  bool record, int fcol) {
   const int tid = threadIdx.x;
-  {
-    T v[16];
-#pragma unroll
-    for (int i = 0; i < 16; ++i) {
-      const int q = tid + kPkThreads * i;
-      const int r = RM ? q >> 6 : q & 63, c = RM ? q & 63 : q >> 6;   // coalesced either way
-      v[i] = (r < kb && c <= r) ? (RM ? G[(int64_t)r * ld + c] : G[r + (int64_t)c * ld]) : T(0);
-    }
-#pragma unroll
-    for (int i = 0; i < 16; ++i) {
-      const int q = tid + kPkThreads * i;
-      const int r = RM ? q >> 6 : q & 63, c = RM ? q & 63 : q >> 6;
-      As[r * kPwLd + c] = v[i];
-    }
-  }
   if (tid == 0) *sok = 1;
   __syncthreads();
   const int lane = tid & 31;
@@ -249,7 +237,29 @@ __device__ __forceinline__ bool potrf_panels(T* __restrict__ G, int64_t ld, int 
     }
     __syncthreads();
   }
-  const bool ok = *sok != 0;
+  return *sok != 0;
+}
+
+template <class T, bool RM>
+__device__ __forceinline__ bool potrf_panels(T* __restrict__ G, int64_t ld, int kb, float accept, T* __restrict__ As,
+                                             int* sok, int* status, bool record, int fcol) {
+  const int tid = threadIdx.x;
+  {
+    T v[16];
+#pragma unroll
+    for (int i = 0; i < 16; ++i) {
+      const int q = tid + kPkThreads * i;
+      const int r = RM ? q >> 6 : q & 63, c = RM ? q & 63 : q >> 6;   // coalesced either way
+      v[i] = (r < kb && c <= r) ? (RM ? G[(int64_t)r * ld + c] : G[r + (int64_t)c * ld]) : T(0);
+    }
+#pragma unroll
+    for (int i = 0; i < 16; ++i) {
+      const int q = tid + kPkThreads * i;
+      const int r = RM ? q >> 6 : q & 63, c = RM ? q & 63 : q >> 6;
+      As[r * kPwLd + c] = v[i];
+    }
+  }
+  const bool ok = potrf_panels_smem<T>(kb, accept, As, sok, status, record, fcol);
   if (ok) {
 #pragma unroll
     for (int i = 0; i < 16; ++i) {

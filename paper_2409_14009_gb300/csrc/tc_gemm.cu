@@ -78,8 +78,10 @@ int chol_tc_prepare(chol_handle* h) {
   if (prec != CHOL_PREC_TF32 && prec != CHOL_PREC_BF16) return CHOL_OK;
   DeviceState* D = h->dev;
   int rc;
-  if ((rc = chol_dalloc(h, (void**)&D->tc_err, sizeof(int32_t)))) return rc;
-  CHOL_CUDA_TRY(cudaMemset(D->tc_err, 0, sizeof(int32_t)));
+  if (!D->tc_err) {
+    if ((rc = chol_dalloc(h, (void**)&D->tc_err, sizeof(int32_t)))) return rc;
+    CHOL_CUDA_TRY(cudaMemset(D->tc_err, 0, sizeof(int32_t)));
+  }
   void* base = D->L;
   size_t esz = 4;
   if (prec == CHOL_PREC_BF16) {

@@ -100,7 +100,7 @@ def test_3d_varcoef_mixed_refined(mode, merge):
     # definiteness there, so that mode runs with static pivoting
     got, ferr, rel, ref = _check(p, mode, nrhs=3, merge=merge, small_rows=32,
                                  static_pivot=1 if mode == "bf16" else 0)
-    assert got["stats"]["gemm"]["launches"] > 0 and got["stats"]["syrk"]["launches"] > 0
+    assert got["stats"]["panel"]["launches"] > 0 and got["stats"]["syrk"]["launches"] > 0
 
 
 @pytest.mark.parametrize("mode", ["fp32", "tf32", "bf16"])
@@ -109,21 +109,40 @@ def test_elasticity_mixed_refined(mode):
     _check(p, mode, nrhs=1, merge=0.05, small_rows=64)
 
 
-@pytest.mark.parametrize("n", [31, 32, 33, 64, 65, 100, 129])
-def test_fp32_blocked_diagonal_blocks_of_every_width(n):
-    # the small-supernode kernel is off, so every diagonal block, the full
-    # 64-wide ones and the ragged last one (1 to 64 columns), goes through the
-    # blocked binary32 POTRF
+def _dense_problem(n):
     from helpers import lower_csc_from_dense
     rs = np.random.RandomState(n)
     M = rs.normal(size=(n, n))
     A = M @ M.T + n * np.eye(n)
     cp, ri, vx = lower_csc_from_dense(A)
-    prob = dict(n=n, colptr=cp, rowind=ri, values=vx, perm=np.arange(n, dtype=np.int32))
-    got, ferr, rel, ref = _check(prob, "fp32", nrhs=2, extra=dict(small_max_cols=1, small_max_panel=1))
+    return dict(n=n, colptr=cp, rowind=ri, values=vx, perm=np.arange(n, dtype=np.int32))
+
+
+@pytest.mark.parametrize("n", [31, 32, 33, 64, 65, 100, 129, 255, 256, 257, 300, 520])
+def test_fp32_blocked_diagonal_blocks_of_every_width(n):
+    # the small-supernode kernel is off, so the whole matrix is one blocked
+    # supernode: one panel launch per 256-column outer block (full and ragged
+    # 64-column sub-blocks inside, 1 to 64 columns in the last one), and the
+    # update of the columns right of each block
+    got, ferr, rel, ref = _check(_dense_problem(n), "fp32", nrhs=2, extra=dict(small_max_cols=1, small_max_panel=1))
     assert got["info"].fp64_fallbacks == 0
-    assert got["stats"]["potrf"]["launches"] == (n + 63) // 64
+    assert got["stats"]["panel"]["launches"] == (n + 255) // 256
+    # per outer block b with columns right of it: the next block's tiles, and
+    # (when there are columns beyond that) the rest on the side stream
+    outer = sum((n > 256 * (b + 1)) + (n > 256 * (b + 2)) for b in range((n + 255) // 256))
+    assert got["stats"]["gemm"]["launches"] == outer
     assert ferr <= 1e-5, ferr
+
+
+@pytest.mark.parametrize("mode", ["tf32", "bf16"])
+@pytest.mark.parametrize("n", [300, 520, 777])
+def test_tensor_core_outer_updates_dense(mode, n):
+    # several outer blocks: the tcgen05 update of the columns right of each
+    # block (the next block's column tiles, then the rest on the side stream)
+    got, ferr, rel, ref = _check(_dense_problem(n), mode, nrhs=2, extra=dict(small_max_cols=1, small_max_panel=1))
+    assert got["stats"]["panel"]["launches"] == (n + 255) // 256
+    assert got["stats"]["gemm"]["launches"] >= (n - 1) // 256
+    assert ferr <= (1e-2 if mode == "tf32" else 5e-2), ferr
 
 
 def test_fp64_fallback_blocks_are_counted_and_exact():
