@@ -260,13 +260,12 @@ __device__ __forceinline__ void pn_wait(const int* flag, int need, long long max
   __syncthreads();
 }
 
-// Publish after the CTA's global stores (release of everything the CTA wrote).
+// Publish after the CTA's global stores: the barrier orders every thread's
+// stores before thread 0's release store, and the release (gpu scope,
+// cumulative) makes them visible to a consumer whose acquire load sees v.
 __device__ __forceinline__ void pn_publish(int* flag, int v) {
   __syncthreads();
-  if (threadIdx.x == 0) {
-    __threadfence();
-    pn_st_release(flag, v);
-  }
+  if (threadIdx.x == 0) pn_st_release(flag, v);
 }
 
 __global__ void __launch_bounds__(256, 2)
@@ -312,6 +311,7 @@ k_mx_panel(const SnodeDev* __restrict__ sn, const PanelItem* __restrict__ items,
         Own[(e >> 8) * kPnLd + (e & 255)] = v[u];
       }
     }
+    __syncthreads();   // the tile is staged (a d = 0 tile reads it right away)
     for (int j = 0; j < jend; ++j) {
       const int c0 = j * 64, kb = min(64, w - c0);
       // L_jj (stored by the diagonal tile j) and its reciprocal pivots
@@ -331,7 +331,9 @@ k_mx_panel(const SnodeDev* __restrict__ sn, const PanelItem* __restrict__ items,
         }
       }
       __syncthreads();
-      if (tid < kb) inv[tid] = 1.0f / Lk[tid + tid * kPwLd];
+      // reciprocal pivots; zero past kb, where the tile's columns and L_jj are
+      // zero too, so the substitution below needs no bounds on kb
+      if (tid < 64) inv[tid] = tid < kb ? 1.0f / Lk[tid + tid * kPwLd] : 0.f;
       __syncthreads();
       // TRSM of the tile's sub-block j: four lanes per row, lane q holds
       // columns q + 4 mm; the solved entry is passed by shuffle
@@ -340,23 +342,18 @@ k_mx_panel(const SnodeDev* __restrict__ sn, const PanelItem* __restrict__ items,
         float* Xr = Own + g * kPnLd + c0;
         float x[16];
 #pragma unroll
-        for (int mm = 0; mm < 16; ++mm) {
-          const int c = q + 4 * mm;
-          x[mm] = c < kb ? Xr[c] : 0.f;
-        }
+        for (int mm = 0; mm < 16; ++mm) x[mm] = Xr[q + 4 * mm];
 #pragma unroll
         for (int jm = 0; jm < 16; ++jm) {
 #pragma unroll
           for (int jq = 0; jq < 4; ++jq) {
             const int jj = jm * 4 + jq;
-            if (jj < kb) {
-              const float xj = __shfl_sync(0xffffffffu, x[jm] * inv[jj], jq, 4);
-              if (q == jq) x[jm] = xj;
+            const float xj = __shfl_sync(0xffffffffu, x[jm] * inv[jj], jq, 4);
+            if (q == jq) x[jm] = xj;
 #pragma unroll
-              for (int mm = jm; mm < 16; ++mm) {
-                const int c = q + 4 * mm;
-                if (c > jj && c < kb) x[mm] = fmaf(-xj, Lk[c + jj * kPwLd], x[mm]);
-              }
+            for (int mm = jm; mm < 16; ++mm) {
+              const int c = q + 4 * mm;
+              if (c > jj) x[mm] = fmaf(-xj, Lk[c + jj * kPwLd], x[mm]);
             }
           }
         }
@@ -365,12 +362,10 @@ k_mx_panel(const SnodeDev* __restrict__ sn, const PanelItem* __restrict__ items,
 #pragma unroll
         for (int mm = 0; mm < 16; ++mm) {
           const int c = q + 4 * mm;
-          if (c < kb) {
-            Xr[c] = x[mm];
-            if (g < m) {
-              Gx[c] = x[mm];
-              if (Bx) Bx[c] = __float2bfloat16_rn(x[mm]);
-            }
+          Xr[c] = x[mm];
+          if (g < m && c < kb) {
+            Gx[c] = x[mm];
+            if (Bx) Bx[c] = __float2bfloat16_rn(x[mm]);
           }
         }
       }

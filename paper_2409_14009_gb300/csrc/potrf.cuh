@@ -34,8 +34,10 @@ __device__ __forceinline__ void pk_coord(int e, int kb, int& r, int& c) {
   r = cc + (e - pk_off(cc, kb));
 }
 
-// Square root of a pivot and its reciprocal. binary32: the library functions.
-// binary64: on this GPU every FP64 instruction of the serial pivot chain holds
+// Square root of a pivot and its reciprocal. binary32 (the low-precision
+// factor of the mixed modes, refined in binary64 afterwards): the hardware
+// reciprocal square root rsqrtf (a few ulps) and sqrt(d) = d rsqrt(d), which
+// keeps the pivot chain short. binary64: on this GPU every FP64 instruction of the serial pivot chain holds
 // the narrow FP64 pipe for many cycles, and sqrt plus a division expand to
 // long dependent sequences; instead the reciprocal square root starts from the
 // binary32 estimate and takes two Newton-Raphson steps y <- y (3 - d y^2) / 2
@@ -43,8 +45,8 @@ __device__ __forceinline__ void pk_coord(int e, int kb, int& r, int& c) {
 // a few ulps), then sqrt(d) = d y. Pivots outside the binary32 normal range
 // take sqrt and a division.
 __device__ __forceinline__ void pivot_root(float d, bool bad, float& root, float& rroot) {
-  root = bad ? __int_as_float(0x7fc00000) : sqrtf(d);
-  rroot = 1.0f / root;
+  rroot = bad ? __int_as_float(0x7fc00000) : rsqrtf(d);
+  root = d * rroot;
 }
 __device__ __forceinline__ void pivot_root(double d, bool bad, double& root, double& rroot) {
   if (bad) {
@@ -273,3 +275,4 @@ __device__ __forceinline__ bool potrf_panels(T* __restrict__ G, int64_t ld, int 
   }
   return ok;
 }
+

@@ -45,6 +45,8 @@ def main():
     ap.add_argument("--factors", type=int, default=1, help="factorizations to run")
     ap.add_argument("--nrhs", type=int, default=0, help="solve with this many right-hand sides")
     ap.add_argument("--adjoint", action="store_true", help="run one adjoint (selected inverse + gradient)")
+    ap.add_argument("--time", type=int, default=0,
+                    help="time this many further factorizations (CUDA events), then one more with per-class events")
     a = ap.parse_args()
     p = make(a.grid)
     o = P.chol_default_options()
@@ -66,6 +68,23 @@ def main():
         rc = P.chol_adjoint(S.h, w, x, 1, 1.0, bbar, grad)
         if rc:
             raise P.CholError(rc, "chol_adjoint")
+    if a.time:
+        st = torch.cuda.current_stream()
+        ms = []
+        for _ in range(a.time):
+            e0 = torch.cuda.Event(enable_timing=True); e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(st); S.factor(vals); e1.record(st); torch.cuda.synchronize()
+            ms.append(e0.elapsed_time(e1))
+        med = float(np.median(ms))
+        print(f"factor: median {med:.3f} ms over {a.time} (min {min(ms):.3f}), {S.info.flops / med / 1e9:.1f} GFLOP/s")
+        P.chol_profile(S.h, (1 << len(P.KERNEL_CLASSES)) - 1)
+        P.chol_get_stats(S.h, reset=True)
+        S.factor(vals)
+        stats = P.chol_get_stats(S.h, reset=True)
+        P.chol_profile(S.h, 0)
+        for k, v in stats.items():
+            if v["launches"]:
+                print(f"  {k:14s} launches {v['launches']:6d}  event ms {v['ms']:9.3f}  flops {v['flops']:.3e}")
     torch.cuda.synchronize()
     print(f"ok n={p.n} flops={S.info.flops:.4g} panels={S.info.panel_doubles * (8 if a.precision == 'fp64' else 4) / 1e9:.3f} GB")
 
