@@ -333,6 +333,10 @@ typedef struct chol_info {
   int32_t persistent_threads; /* launch shape of the persistent kernel (0 = default) */
   int32_t persistent_ctas_per_sm;
   int32_t launch_mode;     /* bit 0: persistent kernel in use, bit 1: CUDA-graph replay */
+  int32_t tc_launches_shallow; /* tensor-core modes, last factorization: update launches on the */
+  int32_t tc_launches_deep;    /* 2-stage ring (3 CTAs per SM, grids of >= 2 tiles per SM) and */
+                               /* on the 6-stage ring (one CTA per SM)                        */
+  int32_t panel_launches;      /* mixed modes, last factorization: panel launches (outer blocks) */
 } chol_info;
 
 int chol_get_info(const chol_handle* h, chol_info* info);
@@ -449,6 +453,20 @@ typedef struct chol_kernel_stat {
 int chol_profile(chol_handle* h, uint32_t timing_mask);
 /* out[CHOL_K_NCLASSES]; reset != 0 clears the counters after reading. */
 int chol_get_stats(chol_handle* h, chol_kernel_stat* out, int32_t reset);
+
+/*
+ * Measured binary64 throughput of the current GPU (the paper has no
+ * counterpart; a measurement aid for the roofline of the binary64 factor,
+ * whose dense updates run on the FP64 FMA pipe). kind 0: DFMA, independent
+ * fused multiply-add chains on every SM; kind 1: DMMA, mma.sync m8n8k4 f64.
+ * Tries 8 and 16 independent chains per thread and 2, 4 and 6 CTAs of 256
+ * threads per SM, each shape with reps + 1 timed launches of a few
+ * milliseconds (the first a warm-up), and returns the best rate in *gflops
+ * (2 flops per multiply-add). Allocates and frees 8 bytes of device memory.
+ * Synchronizes `stream`.
+ * Errors: -1 bad kind, -2 reps < 1, -3 gflops NULL, CHOL_ECUDA.
+ */
+int chol_probe_fp64(int32_t kind, int32_t reps, double* gflops, void* stream);
 
 /* Release the handle and all its device memory. NULL is a no-op. */
 void chol_destroy(chol_handle* h);

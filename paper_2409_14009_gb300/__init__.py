@@ -31,7 +31,7 @@ CHOL_PREC_BF16 = 3
 CHOL_UPDATE_RL = 0
 CHOL_UPDATE_RLB = 1
 
-EXPORTED = ["chol_default_options", "chol_analyze", "chol_factor", "chol_solve", "chol_solve_noalloc", "chol_check_waits", "chol_factor_solve_host",
+EXPORTED = ["chol_default_options", "chol_analyze", "chol_factor", "chol_solve", "chol_solve_noalloc", "chol_check_waits", "chol_factor_solve_host", "chol_probe_fp64",
             "chol_solve_refine", "chol_logdet", "chol_analyze_batch", "chol_logdet_batch", "chol_autotune",
             "chol_factor_batch", "chol_solve_batch",
             "chol_selected_inverse", "chol_adjoint",
@@ -62,7 +62,8 @@ class chol_info(C.Structure):
                 ("flops_stored", C.c_double), ("precision", C.c_int32), ("fp64_fallbacks", C.c_int32),
                 ("perturbed_pivots", C.c_int32), ("nsys", C.c_int32), ("persistent_ok", C.c_int32),
                 ("persistent_threads", C.c_int32), ("persistent_ctas_per_sm", C.c_int32),
-                ("launch_mode", C.c_int32)]
+                ("launch_mode", C.c_int32), ("tc_launches_shallow", C.c_int32), ("tc_launches_deep", C.c_int32),
+                ("panel_launches", C.c_int32)]
 
 
 class chol_kernel_stat(C.Structure):
@@ -98,6 +99,8 @@ def lib():
         L.chol_solve_noalloc.restype = C.c_int
         L.chol_check_waits.argtypes = [P, P]
         L.chol_check_waits.restype = C.c_int
+        L.chol_probe_fp64.argtypes = [C.c_int32, C.c_int32, C.POINTER(C.c_double), P]
+        L.chol_probe_fp64.restype = C.c_int
         L.chol_factor_solve_host.argtypes = [P, P, P, P, C.c_int32, C.POINTER(C.c_double), P]
         L.chol_factor_solve_host.restype = C.c_int
         L.chol_solve_refine.argtypes = [P, P, P, C.c_int32, C.c_double, C.c_int32,
@@ -246,6 +249,13 @@ def chol_factor_solve_host(h, values, b, x, nrhs, want_logdet=True, stream=None)
     rc = lib().chol_factor_solve_host(h, _host_ptr(values), _host_ptr(b), _host_ptr(x), int(nrhs),
                                       C.byref(ld) if want_logdet else None, _stream(stream))
     return rc, (ld.value if want_logdet else None)
+
+
+def chol_probe_fp64(kind=0, reps=5, stream=None):
+    """Measured FP64 GFLOP/s of the current GPU: kind 0 = DFMA, 1 = DMMA. Returns (rc, gflops)."""
+    g = C.c_double(0.0)
+    rc = lib().chol_probe_fp64(int(kind), int(reps), C.byref(g), _stream(stream))
+    return rc, g.value
 
 
 def chol_check_waits(h, stream=None) -> int:

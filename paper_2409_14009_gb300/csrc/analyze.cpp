@@ -869,6 +869,9 @@ extern "C" int chol_get_info(const chol_handle* h, chol_info* info) {
   info->persistent_ctas_per_sm = h->persist_ctas;
   info->launch_mode = (h->opt.persistent ? 1 : 0) | (h->opt.use_graph ? 2 : 0);
   info->fp64_fallbacks = h->fp64_fallbacks;
+  info->tc_launches_shallow = h->tc_shallow;
+  info->tc_launches_deep = h->tc_deep;
+  info->panel_launches = h->panel_launches;
   info->perturbed_pivots = h->perturbed_pivots;
   info->nnz_stored = h->nnz_stored;
   info->flops_stored = h->flops_stored;

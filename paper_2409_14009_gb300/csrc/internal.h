@@ -145,6 +145,7 @@ struct chol_handle {
   std::vector<int32_t> csr_col;
   std::vector<int64_t> csr_src;     // CSR entry -> entry of the lower CSC input
   int32_t fp64_fallbacks = 0;
+  int32_t tc_shallow = 0, tc_deep = 0, panel_launches = 0;   // launch shapes of the last factorization
   std::vector<int64_t> a_colptr;    // the analyzed pattern of A (for gradients)
   std::vector<int32_t> a_rowind;
   bool selinv_valid = false;        // selected inverse of the current factor computed

@@ -749,6 +749,7 @@ int chol_enqueue_factor_mixed(chol_handle* h, const double* values, cudaStream_t
   const int nb = h->opt.block_cols;
   const bool tc = h->opt.precision == CHOL_PREC_TF32 || h->opt.precision == CHOL_PREC_BF16;
   chol_status_init(D->status, st);
+  h->tc_shallow = h->tc_deep = h->panel_launches = 0;
   CHOL_CUDA_TRY(cudaMemsetAsync(D->mx_fallbacks, 0, 2 * sizeof(int32_t), st));
   const float spiv = h->opt.static_pivot ? (float)h->opt.pivot_tau : 0.f;
   CHOL_CUDA_TRY(cudaMemsetAsync(L, 0, sizeof(float) * (size_t)h->panel_doubles, st));
@@ -804,6 +805,7 @@ int chol_enqueue_factor_mixed(chol_handle* h, const double* values, cudaStream_t
       const StepRange& s = P.steps[k];
       if (s.panel_n > 0) {
         KScope ks(h, CHOL_K_PANEL, st, s.panel_flops, 0.0);
+        ++h->panel_launches;
         const int grid = std::min(s.panel_n, D->panel_ctas);
         k_mx_panel<<<grid, 256, kPnSmem, st>>>(
             D->sn, D->panel + s.panel_b, s.panel_n, s.ok0, L,

@@ -126,6 +126,7 @@ int chol_tc_prepare(chol_handle* h) {
 int chol_tc_gemm(chol_handle* h, const TileTask* tasks, int n, int nb, int inner, cudaStream_t st) {
   DeviceState* D = h->dev;
   const int ns = tc::stages_for(n, D->sms);
+  ++(ns == tc::kFewStages ? h->tc_shallow : h->tc_deep);
   const int sm = tc::smem_bytes(ns);
   if (h->opt.precision == CHOL_PREC_TF32)
     k_tc_trailing<0><<<n, tc::kThreads, sm, st>>>(D->tmaps, tasks, D->sn, nb, inner, (float*)D->L, ns, D->tc_err);
@@ -137,6 +138,7 @@ int chol_tc_gemm(chol_handle* h, const TileTask* tasks, int n, int nb, int inner
 int chol_tc_syrk(chol_handle* h, const TileTask* tasks, int n, cudaStream_t st) {
   DeviceState* D = h->dev;
   const int ns = tc::stages_for(n, D->sms);
+  ++(ns == tc::kFewStages ? h->tc_shallow : h->tc_deep);
   const int sm = tc::smem_bytes(ns);
   if (h->opt.precision == CHOL_PREC_TF32)
     k_tc_syrk<0><<<n, tc::kThreads, sm, st>>>(D->tmaps, tasks, D->sn, (float*)D->U, ns, D->tc_err);

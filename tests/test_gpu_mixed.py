@@ -205,3 +205,53 @@ def test_static_pivoting_bf16_3d_refines():
         assert np.all(eta <= 1e-10)
     finally:
         P.chol_destroy(h)
+
+
+@pytest.mark.parametrize("mode", ["tf32", "bf16"])
+def test_elasticity_32_tensor_core_launch_shapes_and_unrefined_factor(mode):
+    """3D 32^3 x 3-dof elasticity with the benchmark's options: the factor
+    takes the tcgen05 update on both rings (2-stage, three CTAs per SM, for
+    grids of at least two tiles per SM; 6-stage otherwise) and the outer
+    K = 256 update right of every outer block. Before any refinement the
+    low-precision factor's backward error on sampled columns is within the
+    mode's bound, and refinement then reaches 1e-10 against the oracle's A."""
+    import torch
+    P = chol()
+    p = gridgen.elasticity_27pt(32, seed=3)
+    b = gridgen.rhs_uniform(p.n, 1, seed=4)
+    o = P.chol_default_options()
+    o.precision = MODES[mode]
+    o.merge_growth = 0.1
+    rc, h = P.chol_analyze(p.n, p["colptr"], p["rowind"], p["perm"], o)
+    assert rc == 0
+    try:
+        assert P.chol_factor(h, to_dev(p["values"])) == 0
+        info = P.chol_get_info(h)
+        stats = P.chol_get_stats(h)
+        print("%s: panel launches %d, tcgen05 launches shallow %d deep %d, outer updates %d, SYRK %d"
+              % (mode, info.panel_launches, info.tc_launches_shallow, info.tc_launches_deep,
+                 stats["gemm"]["launches"], stats["syrk"]["launches"]))
+        assert info.tc_launches_shallow > 0 and info.tc_launches_deep > 0
+        assert stats["gemm"]["launches"] > 0 and info.panel_launches == stats["panel"]["launches"] > 0
+        lp, li, lx = P.chol_get_factor(h)
+        bp, bi, bx = oracle.permute(p.n, p["colptr"], p["rowind"], p["values"], p["perm"])
+        # the factor approximates D B D (D = diag(B)^-1/2, B = P A P^T): compare
+        # D L against it, the residual the mode's bound is about
+        d = 1.0 / np.sqrt(bx[bp[:-1]])
+        bcol = np.repeat(np.arange(p.n), np.diff(bp))
+        bxs = bx * d[bi] * d[bcol]
+        lxs = lx * d[li]
+        rs = np.random.RandomState(1)
+        cols = np.unique(np.concatenate([rs.randint(0, p.n, 200), np.arange(p.n - 300, p.n)]))
+        res = oracle.factor_residual_cols(p.n, bp, bi, bxs, lp, li, lxs, cols)
+        print("%s: unrefined factor residual on %d columns: max %.3e" % (mode, len(cols), res.max()))
+        assert np.all(res <= RES_TOL[mode]), res.max()
+        B = colmajor(b)
+        X = torch.zeros_like(B)
+        rc, iters, berr = P.chol_solve_refine(h, B, X, 1, 1e-10, 100)
+        torch.cuda.synchronize()
+        assert rc == 0, (rc, iters, berr)
+        eta = oracle.backward_error(p.n, p["colptr"], p["rowind"], p["values"], b, X.cpu().numpy())
+        assert np.all(eta <= 1e-10), eta
+    finally:
+        P.chol_destroy(h)

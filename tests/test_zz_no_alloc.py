@@ -63,7 +63,8 @@ def test_noalloc_first_solve_on_fresh_handle_single_rhs_vs_oracle():
     solution and by its backward error; then chol_solve gives the same x."""
     import torch
     P = chol()
-    p = gridgen.laplacian_neumann_varcoef((14, 13, 12), 1e-2, 1e2, 1e-6, seed=7)
+    # Dirichlet-anchored (well conditioned), so x itself is compared tightly
+    p = gridgen.laplacian_dirichlet_weighted((14, 13, 12), gridgen.SplitMix64(7), 1e-2, 1e2)
     b = gridgen.rhs_uniform(p.n, 1, seed=8)
     ref = oracle.reference(p, b)
     rc, h = P.chol_analyze(p.n, p["colptr"], p["rowind"], p["perm"])
