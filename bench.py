@@ -33,6 +33,10 @@ WORKLOAD = "3D 7-point var-coef Laplacian 64^3 (n=262144), FP64 factor + 8-RHS s
 NRHS = 8
 # FP64 peak derived from unit counts: 152 SMs x 2 FP64 FMA/clk/SM x 2 flop x 2.07 GHz
 FP64_PEAK_GFLOPS = 152 * 2 * 2 * 2.07
+# DRAM bytes (read + write) per k_syrk launch on this workload, from the ncu
+# capture summarised in profiles/k_syrk_fp64_3d64_traffic.md (18 launches of one
+# factorization: 1.228 GB read + 2.780 GB written)
+K_SYRK_TRAFFIC_PER_LAUNCH = 4.0074e9 / 18
 
 
 def _env_int(k, d):
@@ -309,14 +313,19 @@ def mixed_vs_fp64(args, P, gridgen, torch, dev, p, b, vals, flops, factor_ms, so
     return out
 
 
-def batch_run(args, P, gridgen, torch, dev):
+def batch_run(args, P, gridgen, torch, dev, rank=0, world=1, dist=None):
     """2,000 independent 2D 5-point Laplacians (sides U{16..96}, log-uniform
     weights in [0.1, 10], Dirichlet ghosts), one RHS each: one block-diagonal
     analysis, autotuned launch configuration (persistent cooperative kernel in a
     CUDA graph when it wins); FP64 factor + solve, and binary32 factor +
-    refinement to eta <= 1e-10."""
+    refinement to eta <= 1e-10. With several ranks each takes its share of the
+    systems (balanced by the n^1.5 work model, paper_2409_14009_gb300.shard)
+    and the per-system log dets are all-gathered after the timed region."""
+    from paper_2409_14009_gb300.shard import gather_results, partition_systems
     t0 = time.perf_counter()
-    probs = gridgen.batch_2d(count=args.batch_count)
+    probs_all = gridgen.batch_2d(count=args.batch_count)
+    mine = partition_systems([p.n for p in probs_all], world)[rank]
+    probs = [probs_all[i] for i in mine]
     bd = gridgen.block_diagonal(probs)
     gen_s = time.perf_counter() - t0
     offs = bd["meta"]["offsets"].astype(np.int32)
@@ -324,7 +333,8 @@ def batch_run(args, P, gridgen, torch, dev):
     st = torch.cuda.current_stream()
     vals = torch.as_tensor(bd["values"], device=dev)
     out = {"workload": "batch of %d 2D 5-point Laplacians, sides U{16..96}, n_total=%d, 1 RHS each"
-                       % (len(probs), bd.n)}
+                       % (len(probs_all), sum(p.n for p in probs_all)),
+           "rank_share": {"systems": len(probs), "n": int(bd.n)}}
     for prec, name, mode in ((0, "fp64", 0), (0, "fp64_rlb", 1), (1, "fp32", 0)):
         opt = P.chol_default_options()
         opt.precision = prec
@@ -340,6 +350,8 @@ def batch_run(args, P, gridgen, torch, dev):
         info = P.chol_get_info(h)
         B = torch.as_tensor(np.ascontiguousarray(b.T), device=dev).t()
         X = torch.zeros_like(B)
+        if dist:
+            dist.barrier()
         fms, rcs = _timed(torch, st, lambda: P.chol_factor(h, vals, st), 5)
         assert rcs == 0, rcs
         if prec == 0:
@@ -351,17 +363,28 @@ def batch_run(args, P, gridgen, torch, dev):
         else:
             sms, res = _timed(torch, st, lambda: P.chol_solve_refine(h, B, X, 1, 1e-10, 50, st), 5)
             iters = res[1]
+        fms, sms = max_over_ranks(dist, [fms, sms], dev)
+        if dist:
+            tfl = torch.tensor([info.flops], dtype=torch.float64, device=dev)
+            dist.all_reduce(tfl)
+            flops_all = float(tfl.item())
+        else:
+            flops_all = info.flops
         eta = backward_error(bd, b, X.cpu().numpy())
+        # every rank learns every system's log det (the one exchange of the batch)
+        rcl, lds = P.chol_logdet_batch(h, len(probs), st)
+        ld_all, st_all = gather_results(dist, world, len(probs_all), mine, lds, [rcl] * len(probs), dev)
         out[name] = {"analyze_s": ana_s, "factor_ms": fms, "solve_ms": sms, "total_ms": fms + sms,
                      "refine_iterations": iters, "backward_error": float(eta),
-                     "factor_gflops": info.flops / (fms * 1e-3) / 1e9,
-                     "systems_per_s": len(probs) / ((fms + sms) * 1e-3),
+                     "factor_gflops": flops_all / (fms * 1e-3) / 1e9,
+                     "systems_per_s": len(probs_all) / ((fms + sms) * 1e-3),
+                     "logdets_gathered": int(np.isfinite(ld_all).sum()), "ranks": world,
                      "autotuned": {"persistent": bool(info.launch_mode & 1), "graph": bool(info.launch_mode & 2),
                                    "persistent_threads": info.persistent_threads,
                                    "persistent_ctas_per_sm": info.persistent_ctas_per_sm},
                      "supernodes": info.nsuper_storage, "levels": info.nlevels}
         P.chol_destroy(h)
-    out["flops"] = float(info.flops)
+    out["flops"] = float(flops_all)
     out["generate_s"] = gen_s
     return out
 
@@ -562,7 +585,7 @@ def run_ours(args, rank, world, local_rank):
     eta_e2e = backward_error(p, b, hx.numpy().T)
     mixed = None if args.no_mixed else mixed_vs_fp64(args, P, gridgen, torch, dev, p, b, vals, flops,
                                                          factor_ms, solve_ms)
-    batch = None if args.no_batch else batch_run(args, P, gridgen, torch, dev)
+    batch = None if args.no_batch else batch_run(args, P, gridgen, torch, dev, rank, world, dist)
     config1 = None if args.no_config1 else config1_run(args, P, gridgen, torch, dev)
     adjoint = None if args.no_adjoint else adjoint_run(args, P, gridgen, torch, dev)
     rlb = None if args.no_rlb else rlb_run(args, P, torch, dev, p, b, vals, flops, factor_ms,
@@ -572,10 +595,22 @@ def run_ours(args, rank, world, local_rank):
         dom = max(("gemm", "syrk"), key=lambda k: stats[k]["ms"])
         ds = stats[dom]
         achieved = ds["flops"] / (ds["ms"] * 1e-3) / 1e9 if ds["ms"] > 0 else None
+        stored_ratio = S.info.flops_stored / flops
+        rc_p, dfma = P.chol_probe_fp64(0, 3)
+        rc_q, dmma = P.chol_probe_fp64(1, 3)
         roof = {"bound": "alu", "kernel": "k_gemm_trailing" if dom == "gemm" else "k_syrk",
                 "achieved": achieved, "peak": FP64_PEAK_GFLOPS, "unit": "GFLOP/s",
-                "frac": (achieved / FP64_PEAK_GFLOPS) if achieved else None, "traffic": None,
-                "peak_source": "derived: 152 SMs x 2 FP64 FMA/clk x 2.07 GHz (FP64 DFMA pipe)",
+                "frac": (achieved / FP64_PEAK_GFLOPS) if achieved else None,
+                # the kernel's flops count the explicit zeros of relaxed merging;
+                # the method's own share scales by the symbolic / stored ratio
+                "frac_symbolic": (achieved / FP64_PEAK_GFLOPS / stored_ratio) if achieved else None,
+                "traffic": K_SYRK_TRAFFIC_PER_LAUNCH if dom == "syrk" else None,
+                "traffic_source": "profiles/k_syrk_fp64_3d64_traffic.md (ncu dram__bytes_read/write.sum of the "
+                                  "18 k_syrk launches of one 64^3 factorization, per launch)",
+                "peak_source": "derived: 152 SMs x 2 FP64 FMA/clk x 2.07 GHz (FP64 DFMA pipe); measured beside it "
+                               "by chol_probe_fp64 (profiles/fp64_peak_probe.md)",
+                "peak_measured": {"dfma": dfma if rc_p == 0 else None, "dmma": dmma if rc_q == 0 else None,
+                                  "frac_of_measured_dfma": (achieved / dfma) if (achieved and rc_p == 0) else None},
                 "launches": ds["launches"], "ms_total": ds["ms"]}
         cpu = cpu_mt = None
         if world == 1 and not args.no_cpu_baseline:
