@@ -335,11 +335,22 @@ def batch_run(args, P, gridgen, torch, dev, rank=0, world=1, dist=None):
     out = {"workload": "batch of %d 2D 5-point Laplacians, sides U{16..96}, n_total=%d, 1 RHS each"
                        % (len(probs_all), sum(p.n for p in probs_all)),
            "rank_share": {"systems": len(probs), "n": int(bd.n)}}
+    tuned = {}
     for prec, name, mode in ((0, "fp64", 0), (0, "fp64_rlb", 1), (1, "fp32", 0)):
-        opt = P.chol_default_options()
-        opt.precision = prec
-        opt.update_mode = mode   # fp64_rlb: updates straight into the ancestors, no assembly pass
-        opt.small_max_cols, opt.small_max_panel, opt.small_max_rows = 160, 24576, 512
+        base = P.chol_default_options()
+        base.precision = prec
+        base.update_mode = mode   # fp64_rlb: updates straight into the ancestors, no assembly pass
+        # analysis choices (one-CTA thresholds, relaxed merging) searched on every
+        # 10th system of this rank's share, then the whole share analyzed with them
+        t0 = time.perf_counter()
+        rc, opt, sample_ms, hit = P.chol_tune_batch(len(offs) - 1, offs, bd["colptr"], bd["rowind"], bd["perm"],
+                                                    vals, base, 10, None, st)
+        assert rc == 0, rc
+        tune_s = time.perf_counter() - t0
+        opt.persistent, opt.use_graph = 0, 0
+        tuned[name] = {"small_max_cols": opt.small_max_cols, "small_max_panel": opt.small_max_panel,
+                       "small_max_rows": opt.small_max_rows, "merge_growth": opt.merge_growth,
+                       "search_s": tune_s, "sample_factor_ms": sample_ms}
         t0 = time.perf_counter()
         rc, h = P.chol_analyze_batch(len(offs) - 1, offs, bd["colptr"], bd["rowind"], bd["perm"], opt)
         ana_s = time.perf_counter() - t0
@@ -379,9 +390,10 @@ def batch_run(args, P, gridgen, torch, dev, rank=0, world=1, dist=None):
                      "factor_gflops": flops_all / (fms * 1e-3) / 1e9,
                      "systems_per_s": len(probs_all) / ((fms + sms) * 1e-3),
                      "logdets_gathered": int(np.isfinite(ld_all).sum()), "ranks": world,
-                     "autotuned": {"persistent": bool(info.launch_mode & 1), "graph": bool(info.launch_mode & 2),
-                                   "persistent_threads": info.persistent_threads,
-                                   "persistent_ctas_per_sm": info.persistent_ctas_per_sm},
+                     "autotuned": dict(tuned[name], persistent=bool(info.launch_mode & 1),
+                                       graph=bool(info.launch_mode & 2),
+                                       persistent_threads=info.persistent_threads,
+                                       persistent_ctas_per_sm=info.persistent_ctas_per_sm),
                      "supernodes": info.nsuper_storage, "levels": info.nlevels}
         P.chol_destroy(h)
     out["flops"] = float(flops_all)

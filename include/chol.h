@@ -385,6 +385,33 @@ int chol_solve_batch(chol_handle* h, double* b, int32_t nrhs, void* stream);
 int chol_autotune(chol_handle* h, const double* values, void* stream);
 
 /*
+ * Analysis-level autotuner for batches (north star (2): tile shapes and
+ * schedules picked by an autotuner; the paper's own choice is a fixed size
+ * threshold between its CPU and GPU code paths, Sec. III-IV). Searches which
+ * supernodes take the one-CTA kernel and how much relaxed merging to allow:
+ * (small_max_cols, small_max_panel, small_max_rows) in {(64, 4096, 128),
+ * (128, 16384, 256), (160, 24576, 512)} x merge_growth in {0, 0.1, 0.25}; for
+ * each, analyzes a sample of the batch (every sample_every-th system), picks
+ * the launch configuration with chol_autotune and times three factorizations;
+ * keeps the fastest. Arguments as chol_analyze_batch, plus:
+ *   values        device, the whole batch's values (the sample is copied out)
+ *   base          options to start from (precision, update mode, ...) or NULL
+ *   sample_every  >= 1 (1 = the whole batch)
+ *   cache_path    a text file of earlier results, or NULL: a line whose key
+ *                 (hash of the pattern, precision, update mode and device)
+ *                 matches is used without searching; a new result is appended
+ *   best          receives the chosen options (persistent, use_graph included)
+ *   best_ms       the sample's factor time with them (may be NULL)
+ *   from_cache    1 if the cache answered (may be NULL)
+ * The caller then analyzes the whole batch with *best (and may call
+ * chol_autotune on it to fit the launch shape to the whole batch).
+ * Errors: -1..-10 for invalid arguments, errors of the calls it makes.
+ */
+int chol_tune_batch(int32_t count, const int32_t* sys_ptr, const int64_t* colptr, const int32_t* rowind,
+                    const int32_t* perm, const double* values, const chol_options* base, int32_t sample_every,
+                    const char* cache_path, chol_options* best, double* best_ms, int32_t* from_cache, void* stream);
+
+/*
  * Copy out the symbolic results (host arrays, sized from chol_info; any
  * pointer may be NULL to skip it):
  *   parent[n]            etree parent of each column of P A P^T (-1 = root)

@@ -31,7 +31,7 @@ CHOL_PREC_BF16 = 3
 CHOL_UPDATE_RL = 0
 CHOL_UPDATE_RLB = 1
 
-EXPORTED = ["chol_default_options", "chol_analyze", "chol_factor", "chol_solve", "chol_solve_noalloc", "chol_check_waits", "chol_factor_solve_host", "chol_probe_fp64",
+EXPORTED = ["chol_default_options", "chol_analyze", "chol_factor", "chol_solve", "chol_solve_noalloc", "chol_check_waits", "chol_factor_solve_host", "chol_probe_fp64", "chol_tune_batch",
             "chol_solve_refine", "chol_logdet", "chol_analyze_batch", "chol_logdet_batch", "chol_autotune",
             "chol_factor_batch", "chol_solve_batch",
             "chol_selected_inverse", "chol_adjoint",
@@ -99,6 +99,9 @@ def lib():
         L.chol_solve_noalloc.restype = C.c_int
         L.chol_check_waits.argtypes = [P, P]
         L.chol_check_waits.restype = C.c_int
+        L.chol_tune_batch.argtypes = [C.c_int32, P, P, P, P, P, C.POINTER(chol_options), C.c_int32, C.c_char_p,
+                                      C.POINTER(chol_options), C.POINTER(C.c_double), C.POINTER(C.c_int32), P]
+        L.chol_tune_batch.restype = C.c_int
         L.chol_probe_fp64.argtypes = [C.c_int32, C.c_int32, C.POINTER(C.c_double), P]
         L.chol_probe_fp64.restype = C.c_int
         L.chol_factor_solve_host.argtypes = [P, P, P, P, C.c_int32, C.POINTER(C.c_double), P]
@@ -249,6 +252,21 @@ def chol_factor_solve_host(h, values, b, x, nrhs, want_logdet=True, stream=None)
     rc = lib().chol_factor_solve_host(h, _host_ptr(values), _host_ptr(b), _host_ptr(x), int(nrhs),
                                       C.byref(ld) if want_logdet else None, _stream(stream))
     return rc, (ld.value if want_logdet else None)
+
+
+def chol_tune_batch(count, sys_ptr, colptr, rowind, perm, values, base=None, sample_every=10, cache_path=None,
+                    stream=None):
+    """Returns (rc, best chol_options, sample factor ms, from_cache)."""
+    sys_ptr = _np(sys_ptr, np.int32); colptr = _np(colptr, np.int64)
+    rowind = _np(rowind, np.int32); perm = _np(perm, np.int32)
+    best = chol_options()
+    ms = C.c_double(0.0)
+    fc = C.c_int32(0)
+    rc = lib().chol_tune_batch(int(count), _ptr(sys_ptr), _ptr(colptr), _ptr(rowind), _ptr(perm), _dev_ptr(values),
+                               C.byref(base) if base is not None else None, int(sample_every),
+                               cache_path.encode() if cache_path else None, C.byref(best), C.byref(ms),
+                               C.byref(fc), _stream(stream))
+    return rc, best, ms.value, bool(fc.value)
 
 
 def chol_probe_fp64(kind=0, reps=5, stream=None):

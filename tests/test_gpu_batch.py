@@ -157,3 +157,34 @@ def test_batch_large_sides_at_bench_thresholds(persistent):
         xq = got["x"][offs[q]:offs[q + 1]]
         assert np.max(np.abs(xq - ref["x"])) <= 1e-11 * np.max(np.abs(ref["x"]))
         assert abs(got["logdet"][q] - ref["fac"].logdet()) <= 1e-12 * abs(ref["fac"].logdet())
+
+
+def test_tune_batch_searches_caches_and_keeps_parity(tmp_path):
+    """chol_tune_batch: a search on a sample of the systems picks thresholds,
+    merging and the launch configuration; the same pattern then comes from the
+    cache file; the whole batch analyzed with the choice matches the oracle."""
+    import torch
+    P = chol()
+    probs, bd = _batch(count=60, kmin=4, kmax=28, seed=31)
+    offs = bd["meta"]["offsets"].astype(np.int32)
+    vals = to_dev(bd["values"])
+    cache = str(tmp_path / "tune.txt")
+    rc, best, ms, hit = P.chol_tune_batch(len(offs) - 1, offs, bd["colptr"], bd["rowind"], bd["perm"], vals,
+                                          sample_every=3, cache_path=cache)
+    assert rc == 0 and not hit and ms > 0
+    assert (best.small_max_cols, best.small_max_panel, best.small_max_rows) in (
+        (64, 4096, 128), (128, 16384, 256), (160, 24576, 512))
+    assert best.merge_growth in (0.0, 0.1, 0.25)
+    rc2, best2, ms2, hit2 = P.chol_tune_batch(len(offs) - 1, offs, bd["colptr"], bd["rowind"], bd["perm"], vals,
+                                              sample_every=3, cache_path=cache)
+    assert rc2 == 0 and hit2
+    assert (best2.small_max_cols, best2.merge_growth, best2.persistent, best2.use_graph) == \
+        (best.small_max_cols, best.merge_growth, best.persistent, best.use_graph)
+    b = gridgen.rhs_uniform(bd.n, 1, seed=32)
+    got = _run(P, bd, best, b)
+    for q, p in enumerate(probs):
+        bq = b[offs[q]:offs[q + 1]]
+        ref = oracle.reference(p, bq)
+        xq = got["x"][offs[q]:offs[q + 1]]
+        assert np.max(np.abs(xq - ref["x"])) <= 1e-11 * np.max(np.abs(ref["x"]))
+        assert abs(got["logdet"][q] - ref["fac"].logdet()) <= 1e-12 * abs(ref["fac"].logdet())
