@@ -608,8 +608,8 @@ def run_ours(args, rank, world, local_rank):
         ds = stats[dom]
         achieved = ds["flops"] / (ds["ms"] * 1e-3) / 1e9 if ds["ms"] > 0 else None
         stored_ratio = S.info.flops_stored / flops
-        rc_p, dfma = P.chol_probe_fp64(0, 3)
-        rc_q, dmma = P.chol_probe_fp64(1, 3)
+        rc_p, dfma, dfma_ghz = P.chol_probe_fp64(0, 3)
+        rc_q, dmma, dmma_ghz = P.chol_probe_fp64(1, 3)
         roof = {"bound": "alu", "kernel": "k_gemm_trailing" if dom == "gemm" else "k_syrk",
                 "achieved": achieved, "peak": FP64_PEAK_GFLOPS, "unit": "GFLOP/s",
                 "frac": (achieved / FP64_PEAK_GFLOPS) if achieved else None,
@@ -621,8 +621,10 @@ def run_ours(args, rank, world, local_rank):
                                   "18 k_syrk launches of one 64^3 factorization, per launch)",
                 "peak_source": "derived: 152 SMs x 2 FP64 FMA/clk x 2.07 GHz (FP64 DFMA pipe); measured beside it "
                                "by chol_probe_fp64 (profiles/fp64_peak_probe.md)",
-                "peak_measured": {"dfma": dfma if rc_p == 0 else None, "dmma": dmma if rc_q == 0 else None,
-                                  "frac_of_measured_dfma": (achieved / dfma) if (achieved and rc_p == 0) else None},
+                "peak_measured": {"dfma": dfma if rc_p == 0 else None, "dfma_sm_ghz": dfma_ghz,
+                                  "dmma": dmma if rc_q == 0 else None, "dmma_sm_ghz": dmma_ghz,
+                                  "dfma_at_2070mhz": (dfma * 2.07 / dfma_ghz) if (rc_p == 0 and dfma_ghz > 0)
+                                  else None},
                 "launches": ds["launches"], "ms_total": ds["ms"]}
         cpu = cpu_mt = None
         if world == 1 and not args.no_cpu_baseline:

@@ -489,11 +489,13 @@ int chol_get_stats(chol_handle* h, chol_kernel_stat* out, int32_t reset);
  * Tries 8 and 16 independent chains per thread and 2, 4 and 6 CTAs of 256
  * threads per SM, each shape with reps + 1 timed launches of a few
  * milliseconds (the first a warm-up), and returns the best rate in *gflops
- * (2 flops per multiply-add). Allocates and frees 8 bytes of device memory.
- * Synchronizes `stream`.
+ * (2 flops per multiply-add) and, in *sm_ghz (may be NULL), the SM clock that
+ * run actually had (SM cycles over wall time of one CTA; a long FP64 burst on
+ * every SM can run below the maximum clock under the power limit). Allocates
+ * and frees 24 bytes of device memory. Synchronizes `stream`.
  * Errors: -1 bad kind, -2 reps < 1, -3 gflops NULL, CHOL_ECUDA.
  */
-int chol_probe_fp64(int32_t kind, int32_t reps, double* gflops, void* stream);
+int chol_probe_fp64(int32_t kind, int32_t reps, double* gflops, double* sm_ghz, void* stream);
 
 /* Release the handle and all its device memory. NULL is a no-op. */
 void chol_destroy(chol_handle* h);

@@ -102,7 +102,7 @@ def lib():
         L.chol_tune_batch.argtypes = [C.c_int32, P, P, P, P, P, C.POINTER(chol_options), C.c_int32, C.c_char_p,
                                       C.POINTER(chol_options), C.POINTER(C.c_double), C.POINTER(C.c_int32), P]
         L.chol_tune_batch.restype = C.c_int
-        L.chol_probe_fp64.argtypes = [C.c_int32, C.c_int32, C.POINTER(C.c_double), P]
+        L.chol_probe_fp64.argtypes = [C.c_int32, C.c_int32, C.POINTER(C.c_double), C.POINTER(C.c_double), P]
         L.chol_probe_fp64.restype = C.c_int
         L.chol_factor_solve_host.argtypes = [P, P, P, P, C.c_int32, C.POINTER(C.c_double), P]
         L.chol_factor_solve_host.restype = C.c_int
@@ -270,10 +270,12 @@ def chol_tune_batch(count, sys_ptr, colptr, rowind, perm, values, base=None, sam
 
 
 def chol_probe_fp64(kind=0, reps=5, stream=None):
-    """Measured FP64 GFLOP/s of the current GPU: kind 0 = DFMA, 1 = DMMA. Returns (rc, gflops)."""
+    """Measured FP64 GFLOP/s of the current GPU: kind 0 = DFMA, 1 = DMMA.
+    Returns (rc, gflops, SM GHz during the best run)."""
     g = C.c_double(0.0)
-    rc = lib().chol_probe_fp64(int(kind), int(reps), C.byref(g), _stream(stream))
-    return rc, g.value
+    ghz = C.c_double(0.0)
+    rc = lib().chol_probe_fp64(int(kind), int(reps), C.byref(g), C.byref(ghz), _stream(stream))
+    return rc, g.value, ghz.value
 
 
 def chol_check_waits(h, stream=None) -> int:

@@ -1,8 +1,8 @@
 // probe.cu -- measured FP64 throughput of this GPU, the denominator the
 // binary64 factorization is compared with (its dense updates are DFMA-bound).
 //
-// DFMA: every thread runs ACC independent chains of fused multiply-adds (one
-// dependent FMA per chain per iteration). DMMA: every warp issues mma.sync
+// DFMA: every thread runs 8 independent chains of fused multiply-adds, or a
+// 4 x 4 register-tile outer product (16 accumulators). DMMA: every warp issues mma.sync
 // m8n8k4 f64 (512 flops each) on ACC independent accumulator tiles. Both are
 // tried with 8 and 16 chains and 2, 4 and 6 CTAs of 256 threads per SM; the
 // best shape is the measured peak. Flops = 2 per FMA (the convention of the
@@ -13,26 +13,70 @@
 
 namespace {
 
-constexpr int kIters = 4096;
+constexpr int kIters = 1024;
+
+// kAcc = 8: eight independent chains a <- a m + c; kAcc = 16: a 4 x 4
+// register-tile outer product acc[i][j] <- x[i] y[j] + acc[i][j] (the inner
+// loop of a register-tiled update, sixteen independent accumulators).
+__device__ __forceinline__ unsigned long long probe_ns() {
+  unsigned long long t;
+  asm volatile("mov.u64 %0, %globaltimer;" : "=l"(t));
+  return t;
+}
+
+// Block 0, thread 0 records SM cycles and nanoseconds across its own run (the
+// clock the SMs actually ran at during the burst).
+__device__ __forceinline__ void probe_stamp(double* out, long long c0, unsigned long long t0) {
+  if (blockIdx.x == 0 && threadIdx.x == 0) {
+    out[1] = (double)(clock64() - c0);
+    out[2] = (double)(probe_ns() - t0);
+  }
+}
 
 template <int kAcc>
 __global__ void __launch_bounds__(256) k_probe_dfma(double* out, double seed) {
-  double a[kAcc];
-#pragma unroll
-  for (int i = 0; i < kAcc; ++i) a[i] = seed + i + threadIdx.x;
-  const double m = 1.0 - 1e-12, c = 1e-9;
-  for (int it = 0; it < kIters; ++it) {
-#pragma unroll
-    for (int i = 0; i < kAcc; ++i) a[i] = fma(a[i], m, c);
-  }
+  const long long c0 = clock64();
+  const unsigned long long t0 = probe_ns();
   double s = 0.0;
+  if (kAcc == 16) {
+    double x[4], y[4], acc[4][4];
 #pragma unroll
-  for (int i = 0; i < kAcc; ++i) s += a[i];
+    for (int i = 0; i < 4; ++i) {
+      x[i] = seed + 1e-3 * (threadIdx.x + i);
+      y[i] = 1.0 - 1e-7 * (i + 1);
+#pragma unroll
+      for (int j = 0; j < 4; ++j) acc[i][j] = 0.0;
+    }
+    for (int it = 0; it < kIters; ++it) {
+#pragma unroll
+      for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j) acc[i][j] = fma(x[i], y[j], acc[i][j]);
+    }
+#pragma unroll
+    for (int i = 0; i < 4; ++i)
+#pragma unroll
+      for (int j = 0; j < 4; ++j) s += acc[i][j];
+  } else {
+    double a[kAcc];
+#pragma unroll
+    for (int i = 0; i < kAcc; ++i) a[i] = seed + i + threadIdx.x;
+    const double m = 1.0 - 1e-12, c = 1e-9;
+    for (int it = 0; it < kIters; ++it) {
+#pragma unroll
+      for (int i = 0; i < kAcc; ++i) a[i] = fma(a[i], m, c);
+    }
+#pragma unroll
+    for (int i = 0; i < kAcc; ++i) s += a[i];
+  }
   if (s == 12345.678) out[0] = s;   // keeps the chains alive; never true for these inputs
+  probe_stamp(out, c0, t0);
 }
 
 template <int kAcc>
 __global__ void __launch_bounds__(256) k_probe_dmma(double* out, double seed) {
+  const long long c0 = clock64();
+  const unsigned long long t0 = probe_ns();
   double acc[kAcc][2];
 #pragma unroll
   for (int i = 0; i < kAcc; ++i) acc[i][0] = acc[i][1] = 0.0;
@@ -48,11 +92,12 @@ __global__ void __launch_bounds__(256) k_probe_dmma(double* out, double seed) {
 #pragma unroll
   for (int i = 0; i < kAcc; ++i) s += acc[i][0] + acc[i][1];
   if (s == 12345.678) out[0] = s;
+  probe_stamp(out, c0, t0);
 }
 
 }  // namespace
 
-extern "C" int chol_probe_fp64(int32_t kind, int32_t reps, double* gflops, void* stream) {
+extern "C" int chol_probe_fp64(int32_t kind, int32_t reps, double* gflops, double* sm_ghz, void* stream) {
   if (kind != 0 && kind != 1) return -1;
   if (reps < 1) return -2;
   if (!gflops) return -3;
@@ -61,16 +106,17 @@ extern "C" int chol_probe_fp64(int32_t kind, int32_t reps, double* gflops, void*
   CHOL_CUDA_TRY(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
   cudaStream_t st = (cudaStream_t)stream;
   double* out = nullptr;
-  CHOL_CUDA_TRY(cudaMalloc(&out, sizeof(double)));
+  CHOL_CUDA_TRY(cudaMalloc(&out, 3 * sizeof(double)));
   cudaEvent_t e0, e1;
   CHOL_CUDA_TRY(cudaEventCreate(&e0));
   CHOL_CUDA_TRY(cudaEventCreate(&e1));
-  double best_rate = 0.0;
+  double best_rate = 0.0, best_ghz = 0.0;
   int rc = CHOL_OK;
   for (int acc : {8, 16}) {
     for (int per_sm : {2, 4, 6}) {
       const int grid = per_sm * sms;
       float best = 1e30f;
+      double ghz_at_best = 0.0;
       for (int r = 0; r < reps + 1 && rc == CHOL_OK; ++r) {   // the first run is a warm-up
         cudaEventRecord(e0, st);
         if (kind == 0 && acc == 8) k_probe_dfma<8><<<grid, 256, 0, st>>>(out, 1.0 + r);
@@ -81,7 +127,12 @@ extern "C" int chol_probe_fp64(int32_t kind, int32_t reps, double* gflops, void*
         if (cudaEventSynchronize(e1) != cudaSuccess) { rc = CHOL_ECUDA; break; }
         float ms = 0.f;
         cudaEventElapsedTime(&ms, e0, e1);
-        if (r > 0) best = ms < best ? ms : best;
+        double st3[3] = {0, 0, 0};
+        if (cudaMemcpy(st3, out, sizeof(st3), cudaMemcpyDeviceToHost) != cudaSuccess) { rc = CHOL_ECUDA; break; }
+        if (r > 0 && ms < best) {
+          best = ms;
+          ghz_at_best = st3[2] > 0 ? st3[1] / st3[2] : 0.0;
+        }
       }
       if (rc != CHOL_OK) break;
       if (cudaGetLastError() != cudaSuccess) { rc = CHOL_ECUDA; break; }
@@ -89,10 +140,14 @@ extern "C" int chol_probe_fp64(int32_t kind, int32_t reps, double* gflops, void*
       const double flops = kind == 0 ? threads * kIters * acc * 2.0
                                      : (threads / 32.0) * (kIters / 4) * acc * 512.0;
       const double rate = flops / (best * 1e-3) / 1e9;
-      best_rate = rate > best_rate ? rate : best_rate;
+      if (rate > best_rate) {
+        best_rate = rate;
+        best_ghz = ghz_at_best;
+      }
     }
   }
   *gflops = rc == CHOL_OK ? best_rate : 0.0;
+  if (sm_ghz) *sm_ghz = rc == CHOL_OK ? best_ghz : 0.0;
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
   cudaFree(out);

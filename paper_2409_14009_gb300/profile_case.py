@@ -3,6 +3,7 @@ synthetic workload, for running under a profiler.
 
     python -m paper_2409_14009_gb300.profile_case --grid elast:32 --precision bf16
     python -m paper_2409_14009_gb300.profile_case --grid neumann:48 --adjoint
+    python -m paper_2409_14009_gb300.profile_case --batch 2000
 
 Grids: ``neumann:k`` (7-point variable-coefficient k^3 Laplacian, Neumann,
 shift 1e-6), ``dirichlet:k`` (7-point weighted k^3 Laplacian with Dirichlet
@@ -45,15 +46,41 @@ def main():
     ap.add_argument("--factors", type=int, default=1, help="factorizations to run")
     ap.add_argument("--nrhs", type=int, default=0, help="solve with this many right-hand sides")
     ap.add_argument("--adjoint", action="store_true", help="run one adjoint (selected inverse + gradient)")
+    ap.add_argument("--batch", type=int, default=0,
+                    help="instead of --grid: this many independent 2D systems (sides U{16..96}), analysis options "
+                         "from chol_tune_batch on every 10th system")
+    ap.add_argument("--tuned", default="",
+                    help="with --batch: skip the search and use 'cols,panel,rows,merge' (e.g. 128,16384,256,0.25)")
     ap.add_argument("--time", type=int, default=0,
                     help="time this many further factorizations (CUDA events), then one more with per-class events")
     a = ap.parse_args()
-    p = make(a.grid)
     o = P.chol_default_options()
     o.precision = PRECISIONS[a.precision]
     o.merge_growth = a.merge
-    S = P.SparseCholesky(p.n, p["colptr"], p["rowind"], p["perm"], o)
-    vals = torch.as_tensor(p["values"], device="cuda")
+    if a.batch:
+        probs = gridgen.batch_2d(count=a.batch)
+        p = gridgen.block_diagonal(probs)
+        offs = p["meta"]["offsets"].astype(np.int32)
+        vals = torch.as_tensor(p["values"], device="cuda")
+        if a.tuned:
+            c, pn, r, m = a.tuned.split(",")
+            o.small_max_cols, o.small_max_panel, o.small_max_rows, o.merge_growth = int(c), int(pn), int(r), float(m)
+            o.use_graph = 1
+        else:
+            rc, o, ms, _ = P.chol_tune_batch(len(offs) - 1, offs, p["colptr"], p["rowind"], p["perm"], vals, o, 10)
+            if rc:
+                raise P.CholError(rc, "chol_tune_batch")
+        print(f"tuned: cols {o.small_max_cols} panel {o.small_max_panel} rows {o.small_max_rows} "
+              f"merge {o.merge_growth} persistent {o.persistent} graph {o.use_graph}")
+        rc, h = P.chol_analyze_batch(len(offs) - 1, offs, p["colptr"], p["rowind"], p["perm"], o)
+        if rc:
+            raise P.CholError(rc, "chol_analyze_batch")
+        S = P.SparseCholesky.__new__(P.SparseCholesky)
+        S.h, S.n, S.info = h, p.n, P.chol_get_info(h)
+    else:
+        p = make(a.grid)
+        S = P.SparseCholesky(p.n, p["colptr"], p["rowind"], p["perm"], o)
+        vals = torch.as_tensor(p["values"], device="cuda")
     for _ in range(a.factors):
         S.factor(vals)
     if a.nrhs:
