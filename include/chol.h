@@ -491,7 +491,8 @@ int chol_get_stats(chol_handle* h, chol_kernel_stat* out, int32_t reset);
  * milliseconds (the first a warm-up), and returns the best rate in *gflops
  * (2 flops per multiply-add) and, in *sm_ghz (may be NULL), the SM clock that
  * run actually had (SM cycles over wall time of one CTA; a long FP64 burst on
- * every SM can run below the maximum clock under the power limit). Allocates
+ * every SM can run below the maximum clock under the power limit; 0 for DMMA,
+ * which does not record it). Allocates
  * and frees 24 bytes of device memory. Synchronizes `stream`.
  * Errors: -1 bad kind, -2 reps < 1, -3 gflops NULL, CHOL_ECUDA.
  */

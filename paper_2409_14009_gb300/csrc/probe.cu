@@ -13,7 +13,8 @@
 
 namespace {
 
-constexpr int kIters = 1024;
+constexpr int kIters = 1024;      // DFMA iterations (about a millisecond)
+constexpr int kItersMma = 4096;   // DMMA iterations
 
 // kAcc = 8: eight independent chains a <- a m + c; kAcc = 16: a 4 x 4
 // register-tile outer product acc[i][j] <- x[i] y[j] + acc[i][j] (the inner
@@ -75,13 +76,11 @@ __global__ void __launch_bounds__(256) k_probe_dfma(double* out, double seed) {
 
 template <int kAcc>
 __global__ void __launch_bounds__(256) k_probe_dmma(double* out, double seed) {
-  const long long c0 = clock64();
-  const unsigned long long t0 = probe_ns();
   double acc[kAcc][2];
 #pragma unroll
   for (int i = 0; i < kAcc; ++i) acc[i][0] = acc[i][1] = 0.0;
   const double a = seed + threadIdx.x * 1e-3, b = 1.0 - 1e-12;
-  for (int it = 0; it < kIters / 4; ++it) {
+  for (int it = 0; it < kItersMma / 4; ++it) {
 #pragma unroll
     for (int i = 0; i < kAcc; ++i)
       asm volatile("mma.sync.aligned.m8n8k4.row.col.f64.f64.f64.f64 {%0, %1}, {%2}, {%3}, {%0, %1};"
@@ -92,7 +91,6 @@ __global__ void __launch_bounds__(256) k_probe_dmma(double* out, double seed) {
 #pragma unroll
   for (int i = 0; i < kAcc; ++i) s += acc[i][0] + acc[i][1];
   if (s == 12345.678) out[0] = s;
-  probe_stamp(out, c0, t0);
 }
 
 }  // namespace
@@ -107,6 +105,7 @@ extern "C" int chol_probe_fp64(int32_t kind, int32_t reps, double* gflops, doubl
   cudaStream_t st = (cudaStream_t)stream;
   double* out = nullptr;
   CHOL_CUDA_TRY(cudaMalloc(&out, 3 * sizeof(double)));
+  CHOL_CUDA_TRY(cudaMemset(out, 0, 3 * sizeof(double)));   // the DMMA kernels record no clock (0)
   cudaEvent_t e0, e1;
   CHOL_CUDA_TRY(cudaEventCreate(&e0));
   CHOL_CUDA_TRY(cudaEventCreate(&e1));
@@ -138,7 +137,7 @@ extern "C" int chol_probe_fp64(int32_t kind, int32_t reps, double* gflops, doubl
       if (cudaGetLastError() != cudaSuccess) { rc = CHOL_ECUDA; break; }
       const double threads = (double)grid * 256.0;
       const double flops = kind == 0 ? threads * kIters * acc * 2.0
-                                     : (threads / 32.0) * (kIters / 4) * acc * 512.0;
+                                     : (threads / 32.0) * (kItersMma / 4) * acc * 512.0;
       const double rate = flops / (best * 1e-3) / 1e9;
       if (rate > best_rate) {
         best_rate = rate;
