@@ -550,8 +550,6 @@ void build(chol_handle* h, const int64_t* colptr, const int32_t* rowind) {
       st.potrf_flops = st.trsm_flops = st.gemm_flops = st.ogemm_flops = 0.0;
       st.trsm_b = (int32_t)h->trsm_tasks.size();
       st.gemm_b = (int32_t)h->gemm_tasks.size();
-      // tensor-core modes: the outer block holding this step, [ob, ob + kTcOuter)
-      const int32_t ob = (k0 / kTcOuter) * kTcOuter;
       for (int32_t J : large) {
         const SnodeDev& d = h->snodes[J];
         if (d.s <= k0) continue;
@@ -562,8 +560,8 @@ void build(chol_handle* h, const int64_t* colptr, const int32_t* rowind) {
         const double below = (double)(d.len - k0 - kb);
         st.trsm_flops += below * (double)kb * (double)kb;   // kb divisions + 2*kb(kb-1)/2 per row
         for (int32_t r0 = k0 + kb; r0 < d.len; r0 += trsm_rows) h->trsm_tasks.push_back({J, k0, r0, 0});
-        // trailing update: 2 kb flops per entry (r, c) with c in [k0+kb, cend), r in [c, len)
-        const int32_t cend = tc_modes ? std::min(d.s, ob + kTcOuter) : d.s;
+        // trailing update: 2 kb flops per entry (r, c) with c in [k0+kb, s), r in [c, len)
+        const int32_t cend = d.s;
         {
           const double w = (double)(cend - k0 - kb), hgt = (double)(d.len - k0 - kb);
           st.gemm_flops += 2.0 * kb * (w * hgt - w * (w - 1.0) / 2.0);
@@ -576,8 +574,7 @@ void build(chol_handle* h, const int64_t* colptr, const int32_t* rowind) {
           const SnodeDev& d = h->snodes[J];
           if (d.s <= k0) continue;
           const int32_t kb = std::min(nb, d.s - k0);
-          const int32_t cend = tc_modes ? std::min(d.s, ob + kTcOuter) : d.s;
-          for (int32_t c0 = k0 + kb; c0 < cend; c0 += tg) {
+          for (int32_t c0 = k0 + kb; c0 < d.s; c0 += tg) {
             if ((pass == 0) != (c0 == k0 + kb)) continue;
             for (int32_t r0 = c0; r0 < d.len; r0 += tg) h->gemm_tasks.push_back({J, k0, r0, c0});
           }
@@ -587,32 +584,10 @@ void build(chol_handle* h, const int64_t* colptr, const int32_t* rowind) {
       st.potrf_n = (int32_t)h->potrf_list.size() - st.potrf_b;
       st.trsm_n = (int32_t)h->trsm_tasks.size() - st.trsm_b;
       st.gemm_n = (int32_t)h->gemm_tasks.size() - st.gemm_b;
-      // after the last step of an outer block: the columns right of it, K = the block
       st.ogemm_b = (int32_t)h->gemm_tasks.size();
-      st.ok0 = ob;
-      st.okb = kTcOuter;
+      st.ok0 = k0;
+      st.okb = 0;
       st.ogemm_next = 0;
-      if (tc_modes && (k0 + nb) % kTcOuter == 0) {
-        const int32_t oend = ob + kTcOuter;
-        for (int32_t J : large) {
-          const SnodeDev& d = h->snodes[J];
-          if (d.s <= oend) continue;
-          const double w = (double)(d.s - oend), hgt = (double)(d.len - oend);
-          st.ogemm_flops += 2.0 * kTcOuter * (w * hgt - w * (w - 1.0) / 2.0);
-        }
-        // first column tiles (the next step's block column) of every supernode first
-        for (int pass = 0; pass < 2; ++pass) {
-          for (int32_t J : large) {
-            const SnodeDev& d = h->snodes[J];
-            if (d.s <= oend) continue;
-            for (int32_t c0 = oend; c0 < d.s; c0 += tg) {
-              if ((pass == 0) != (c0 == oend)) continue;
-              for (int32_t r0 = c0; r0 < d.len; r0 += tg) h->gemm_tasks.push_back({J, ob, r0, c0});
-            }
-          }
-          if (pass == 0) st.ogemm_next = (int32_t)h->gemm_tasks.size() - st.ogemm_b;
-        }
-      }
       st.ogemm_n = (int32_t)h->gemm_tasks.size() - st.ogemm_b;
       P.steps.push_back(st);
     }

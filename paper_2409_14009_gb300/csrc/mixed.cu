@@ -4,12 +4,14 @@
 // The matrix is scaled to D A D (D = diag(A)^{-1/2}, unit diagonal) while its
 // values are scattered into binary32 panels. The panels are row-major, so both
 // operands of every update GEMM are K-major, which the tensor cores want. The
-// per-supernode steps are the same as in binary64:
-// - POTRF of 64-column diagonal blocks in binary32. A block whose binary32
-//   pivots fall below pivot_tau is redone in binary64.
-// - TRSM of the rows below.
-// - The trailing update and the SYRK update matrix.
-// - The pull-ordered relind scatter-add.
+// per-supernode steps are those of binary64 (Sec. II-A), grouped differently:
+// - one panel launch per 256-column outer block does the POTRF of its 64-column
+//   diagonal blocks (binary32; a block whose pivots fall below pivot_tau is
+//   redone in binary64), the TRSM of the rows below and the updates inside the
+//   block (k_mx_panel);
+// - the columns right of the block get one update with K = 256, and the SYRK
+//   forms the update matrix;
+// - the pull-ordered relind scatter-add.
 // In CHOL_PREC_FP32 the updates run on binary32 SIMT tiles; in TF32/BF16 they
 // run on tcgen05 tensor-core tiles (tc_gemm.cuh). Accuracy is won back by
 // iterative refinement with binary64 residuals (refine.cu).
@@ -110,97 +112,6 @@ k_mx_small(const SnodeDev* __restrict__ sn, const int32_t* __restrict__ list, fl
            float* __restrict__ U, int* status, float spiv, int* counters) {
   extern __shared__ float Pf[];
   mx_small_body(sn[list[blockIdx.x]], L, U, status, spiv, counters, Pf);
-}
-
-// Blocked path, step k0: diagonal block in binary32 (8-column panels on a
-// shared-memory copy, potrf.cuh); redone in binary64 (packed right-looking
-// Cholesky) from the unmodified block when a binary32 pivot (before its square
-// root) falls below tau.
-__global__ void __launch_bounds__(kPkThreads)
-k_mx_potrf(const SnodeDev* __restrict__ sn, const int32_t* __restrict__ list, int k0, int nb, float tau,
-           int static_pivot, float* __restrict__ L, int* status, int* counters) {
-  __shared__ double colk_d[64];
-  __shared__ float As[64 * kPwLd];
-  __shared__ double sinv_d;
-  __shared__ int accepted;
-  const SnodeDev d = sn[list[blockIdx.x]];
-  const int kb = min(nb, d.s - k0);
-  float* G = L + d.loff + (int64_t)k0 * d.ld + k0;
-  if (!potrf_panels<float, true>(G, d.ld, kb, tau, As, &accepted, status, false, d.f + k0)) {
-    if (threadIdx.x == 0) atomicAdd(counters, 1);
-    potrf_block<double, true, float>(G, d.ld, kb, static_pivot ? (double)tau : 0.0, counters + 1, nullptr, status,
-                                     true, d.f + k0, colk_d, &sinv_d, -INFINITY);
-  }
-}
-
-// Blocked path, step k0: rows [r0, r0+32) of the column block become
-// X = B L_kk^{-T}; eight lanes per row, shuffle broadcast (as in binary64).
-__global__ void __launch_bounds__(256)
-k_mx_trsm(const SnodeDev* __restrict__ sn, const TileTask* __restrict__ tasks, int nb,
-          float* __restrict__ L, __nv_bfloat16* __restrict__ Lb) {
-  __shared__ float Lk[64 * 65];
-  __shared__ float inv[64];
-  const TileTask t = tasks[blockIdx.x];
-  const SnodeDev d = sn[t.J];
-  const int kb = min(nb, d.s - t.k0);
-  const float* Gd = L + d.loff + (int64_t)t.k0 * d.ld + t.k0;
-  {
-    // stage the diagonal block: all 16 loads of a thread issued before the
-    // stores (row-major source: consecutive threads read consecutive columns)
-    float v[16];
-#pragma unroll
-    for (int i = 0; i < 16; ++i) {
-      const int q = threadIdx.x + 256 * i, r = q >> 6, c = q & 63;
-      v[i] = (r < kb && c < kb) ? Gd[(int64_t)r * d.ld + c] : 0.f;
-    }
-#pragma unroll
-    for (int i = 0; i < 16; ++i) {
-      const int q = threadIdx.x + 256 * i;
-      Lk[(q >> 6) + (q & 63) * 65] = v[i];
-    }
-  }
-  __syncthreads();
-  for (int c = threadIdx.x; c < kb; c += blockDim.x) inv[c] = 1.0f / Lk[c + c * 65];
-  __syncthreads();
-  const int g = threadIdx.x >> 3, q = threadIdx.x & 7;
-  const int row = t.r0 + g;
-  const bool live = row < d.len;
-  float* Gx = L + d.loff + (int64_t)row * d.ld + t.k0;
-  float x[8];
-#pragma unroll
-  for (int m = 0; m < 8; ++m) {
-    const int c = q + 8 * m;
-    x[m] = (live && c < kb) ? Gx[c] : 0.f;
-  }
-#pragma unroll
-  for (int jm = 0; jm < 8; ++jm) {
-#pragma unroll
-    for (int jq = 0; jq < 8; ++jq) {
-      const int j = jm * 8 + jq;
-      if (j < kb) {
-        const float xj = __shfl_sync(0xffffffffu, x[jm] * inv[j], jq, 8);
-        if (q == jq) x[jm] = xj;
-#pragma unroll
-        for (int m = jm; m < 8; ++m) {
-          const int c = q + 8 * m;
-          if (c > j && c < kb) x[m] = fmaf(-xj, Lk[c + j * 65], x[m]);
-        }
-      }
-    }
-  }
-  if (live) {
-    // the bf16 copy (CHOL_PREC_BF16) feeds the tensor-core tiles; these rows
-    // are final once solved
-    __nv_bfloat16* Bx = Lb ? Lb + d.loff + (int64_t)row * d.ld + t.k0 : nullptr;
-#pragma unroll
-    for (int m = 0; m < 8; ++m) {
-      const int c = q + 8 * m;
-      if (c < kb) {
-        Gx[c] = x[m];
-        if (Bx) Bx[c] = __float2bfloat16_rn(x[m]);
-      }
-    }
-  }
 }
 
 // ---------------------------------------------------------------------------
