@@ -51,6 +51,8 @@ def main():
                          "from chol_tune_batch on every 10th system")
     ap.add_argument("--tuned", default="",
                     help="with --batch: skip the search and use 'cols,panel,rows,merge' (e.g. 128,16384,256,0.25)")
+    ap.add_argument("--persistent", action="store_true",
+                    help="with --batch --tuned: the persistent cooperative kernel instead of graph replay")
     ap.add_argument("--time", type=int, default=0,
                     help="time this many further factorizations (CUDA events), then one more with per-class events")
     a = ap.parse_args()
@@ -65,7 +67,7 @@ def main():
         if a.tuned:
             c, pn, r, m = a.tuned.split(",")
             o.small_max_cols, o.small_max_panel, o.small_max_rows, o.merge_growth = int(c), int(pn), int(r), float(m)
-            o.use_graph = 1
+            o.use_graph, o.persistent = (0, 1) if a.persistent else (1, 0)
         else:
             rc, o, ms, _ = P.chol_tune_batch(len(offs) - 1, offs, p["colptr"], p["rowind"], p["perm"], vals, o, 10)
             if rc:
@@ -103,7 +105,7 @@ def main():
             e0.record(st); S.factor(vals); e1.record(st); torch.cuda.synchronize()
             ms.append(e0.elapsed_time(e1))
         med = float(np.median(ms))
-        print(f"factor: median {med:.3f} ms over {a.time} (min {min(ms):.3f}), {S.info.flops / med / 1e9:.1f} GFLOP/s")
+        print(f"factor: median {med:.3f} ms over {a.time} (min {min(ms):.3f}), {S.info.flops / med / 1e6:.1f} GFLOP/s")
         P.chol_profile(S.h, (1 << len(P.KERNEL_CLASSES)) - 1)
         P.chol_get_stats(S.h, reset=True)
         S.factor(vals)
