@@ -46,7 +46,8 @@ enum {
   CHOL_ENOCONV = -1004,   /* iterative refinement did not reach the tolerance */
   CHOL_ESTATE = -1005,    /* call made in the wrong state (e.g. solve before factor) */
   CHOL_ENOTSUP = -1006,   /* option combination not supported */
-  CHOL_ETOOBIG = -1007    /* problem exceeds a fixed-size workspace */
+  CHOL_ETOOBIG = -1007,   /* problem exceeds a fixed-size workspace */
+  CHOL_EBOUNDS = -1008    /* CHOL_BOUNDS_CHECK build: a range check failed (access skipped) */
 };
 
 /*
@@ -337,6 +338,10 @@ typedef struct chol_info {
   int32_t tc_launches_deep;    /* 2-stage ring (3 CTAs per SM, grids of >= 2 tiles per SM) and */
                                /* on the 6-stage ring (one CTA per SM)                        */
   int32_t panel_launches;      /* mixed modes, last factorization: panel launches (outer blocks) */
+  int32_t bounds_code;         /* CHOL_BOUNDS_CHECK build: first failed check of the last */
+                               /* factorization (1 task target, 2 task positions, 3 segment */
+                               /* source, 4 segment range, 5 target row, 6 target column,  */
+                               /* 7 value scatter); 0 otherwise                            */
 } chol_info;
 
 int chol_get_info(const chol_handle* h, chol_info* info);
@@ -372,6 +377,28 @@ int chol_logdet_batch(chol_handle* h, double* out, void* stream);
  * sequence (or one graph replay / persistent launch, as analysed). */
 int chol_factor_batch(chol_handle* h, const double* values, void* stream);
 int chol_solve_batch(chol_handle* h, double* b, int32_t nrhs, void* stream);
+
+/*
+ * The bounds-checked build (compiled with -DCHOL_BOUNDS_CHECK; the package's
+ * build(checked=True) makes it beside the normal library). Its kernels
+ * range-check what comes from the plan before using it: every relind assembly
+ * task (target supernode, row positions, segment range) and segment (source
+ * supernode, rows and columns of U_J), every target row found by the binary
+ * search (it must be present in the target's structure) and every target
+ * column, and every position of the value scatter into the panels. A failed
+ * check records its code (chol_info.bounds_code) and skips the access, and
+ * chol_factor returns CHOL_EBOUNDS. (The paper's assembly is CPU code; this is
+ * a debugging aid of the GPU form.)
+ *
+ * chol_test_corrupt_plan damages the host copy of a handle's plan before its
+ * first chol_factor uploads it, for testing the checks without a fault:
+ * kind 1: a segment's source supernode out of range; 2: a segment's rows past
+ * U_J; 3: a task's row positions past the target; 4: a value's panel position
+ * past the panels; 5: a warp-sized task's segment with a negative source.
+ * CHOL_ESTATE after the first factorization; CHOL_ENOTSUP in the normal build
+ * or when the plan has no task of that kind; -2 for an unknown kind.
+ */
+int chol_test_corrupt_plan(chol_handle* h, int32_t kind);
 
 /*
  * Autotuner of the launch configuration: factors `values` (device, as for

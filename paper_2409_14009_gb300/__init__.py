@@ -24,6 +24,7 @@ CHOL_ENOCONV = -1004
 CHOL_ESTATE = -1005
 CHOL_ENOTSUP = -1006
 CHOL_ETOOBIG = -1007
+CHOL_EBOUNDS = -1008
 CHOL_PREC_FP64 = 0
 CHOL_PREC_FP32 = 1
 CHOL_PREC_TF32 = 2
@@ -31,7 +32,7 @@ CHOL_PREC_BF16 = 3
 CHOL_UPDATE_RL = 0
 CHOL_UPDATE_RLB = 1
 
-EXPORTED = ["chol_default_options", "chol_analyze", "chol_factor", "chol_solve", "chol_solve_noalloc", "chol_check_waits", "chol_factor_solve_host", "chol_probe_fp64", "chol_tune_batch",
+EXPORTED = ["chol_default_options", "chol_analyze", "chol_factor", "chol_solve", "chol_solve_noalloc", "chol_check_waits", "chol_factor_solve_host", "chol_probe_fp64", "chol_tune_batch", "chol_test_corrupt_plan",
             "chol_solve_refine", "chol_logdet", "chol_analyze_batch", "chol_logdet_batch", "chol_autotune",
             "chol_factor_batch", "chol_solve_batch",
             "chol_selected_inverse", "chol_adjoint",
@@ -63,7 +64,7 @@ class chol_info(C.Structure):
                 ("perturbed_pivots", C.c_int32), ("nsys", C.c_int32), ("persistent_ok", C.c_int32),
                 ("persistent_threads", C.c_int32), ("persistent_ctas_per_sm", C.c_int32),
                 ("launch_mode", C.c_int32), ("tc_launches_shallow", C.c_int32), ("tc_launches_deep", C.c_int32),
-                ("panel_launches", C.c_int32)]
+                ("panel_launches", C.c_int32), ("bounds_code", C.c_int32)]
 
 
 class chol_kernel_stat(C.Structure):
@@ -78,6 +79,8 @@ class CholError(RuntimeError):
 
 
 _lib = None
+_lib_checked = None
+LIB_CHECKED_PATH = os.path.join(_HERE, "_build_checked", "libchol.so")
 
 
 def lib():
@@ -86,7 +89,24 @@ def lib():
     if _lib is None:
         if not os.path.exists(LIB_PATH):
             raise ImportError("libchol.so is not built: run __graft_entry__.build()")
-        L = C.CDLL(LIB_PATH)
+        _lib = _declare(C.CDLL(LIB_PATH))
+    return _lib
+
+
+def lib_checked():
+    """The bounds-checked build (``build.build(checked=True)``), same C ABI; its
+    handles are used with its own functions only."""
+    global _lib_checked
+    if _lib_checked is None:
+        if not os.path.exists(LIB_CHECKED_PATH):
+            raise ImportError("the bounds-checked library is not built: build.build(checked=True)")
+        _lib_checked = _declare(C.CDLL(LIB_CHECKED_PATH))
+    return _lib_checked
+
+
+def _declare(L):
+    """Argument and result types of every exported function."""
+    if True:
         P = C.c_void_p
         L.chol_default_options.argtypes = [C.POINTER(chol_options)]
         L.chol_analyze.argtypes = [C.c_int32, P, P, P, C.POINTER(chol_options), C.POINTER(C.c_void_p)]
@@ -141,8 +161,9 @@ def lib():
         L.chol_destroy.restype = None
         L.chol_strerror.argtypes = [C.c_int]
         L.chol_strerror.restype = C.c_char_p
-        _lib = L
-    return _lib
+        L.chol_test_corrupt_plan.argtypes = [P, C.c_int32]
+        L.chol_test_corrupt_plan.restype = C.c_int
+    return L
 
 
 def _np(a, dt):
@@ -276,6 +297,11 @@ def chol_probe_fp64(kind=0, reps=5, stream=None):
     ghz = C.c_double(0.0)
     rc = lib().chol_probe_fp64(int(kind), int(reps), C.byref(g), C.byref(ghz), _stream(stream))
     return rc, g.value, ghz.value
+
+
+def chol_test_corrupt_plan(h, kind) -> int:
+    """Damage the host plan of a fresh handle (bounds-checked build only, for tests)."""
+    return lib().chol_test_corrupt_plan(h, int(kind))
 
 
 def chol_check_waits(h, stream=None) -> int:

@@ -847,6 +847,7 @@ extern "C" int chol_get_info(const chol_handle* h, chol_info* info) {
   info->tc_launches_shallow = h->tc_shallow;
   info->tc_launches_deep = h->tc_deep;
   info->panel_launches = h->panel_launches;
+  info->bounds_code = h->bounds_code;
   info->perturbed_pivots = h->perturbed_pivots;
   info->nnz_stored = h->nnz_stored;
   info->flops_stored = h->flops_stored;
@@ -974,6 +975,7 @@ extern "C" const char* chol_strerror(int code) {
     case CHOL_ESTATE: return "call made in the wrong state";
     case CHOL_ENOTSUP: return "option combination not supported";
     case CHOL_ETOOBIG: return "problem exceeds the fixed-size workspace of this call";
+    case CHOL_EBOUNDS: return "a range check of the bounds-checked build failed (the access was skipped)";
     default: break;
   }
   if (code > 0) return "matrix is not positive definite (return value = failing column, 1-based)";

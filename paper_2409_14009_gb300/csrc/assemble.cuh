@@ -13,6 +13,7 @@
 #include <cstdint>
 
 #include "internal.h"
+#include "bounds.cuh"
 
 constexpr int kAsmWarpUnroll = 4;
 
@@ -26,17 +27,35 @@ __device__ __forceinline__ void assemble_warp_task(const AsmTask& t, const AsmSe
                                                    const int32_t* __restrict__ rows, const T* __restrict__ U,
                                                    T* __restrict__ L, int32_t* sK, int32_t* pos) {
   const int lane = threadIdx.x & 31;
+#ifdef CHOL_BOUNDS_CHECK
+  if (!CHOL_BC(t.K >= 0 && t.K < bc_lim.ns, kBcTaskTarget)) return;
+#endif
   const SnodeDev dk = sn[t.K];
   const int np = t.p1 - t.p0;
+#ifdef CHOL_BOUNDS_CHECK
+  if (!CHOL_BC(t.p0 >= 0 && np >= 0 && t.p1 <= dk.len && np <= kAsmWarpPos && t.seg_begin >= 0 &&
+                   t.seg_begin <= t.seg_end && t.seg_end <= bc_lim.nsegs,
+               kBcTaskPositions))
+    return;
+#endif
   const int32_t* rk = rows + dk.roff + t.p0;
   for (int i = lane; i < np; i += 32) sK[i] = rk[i];
   T* Lk = L + dk.loff;
   for (int g = t.seg_begin; g < t.seg_end; ++g) {
     const AsmSeg sg = segs[g];
+#ifdef CHOL_BOUNDS_CHECK
+    if (!CHOL_BC(sg.J >= 0 && sg.J < bc_lim.ns, kBcSegSource)) continue;
+#endif
     const SnodeDev dj = sn[sg.J];
     const int b = dj.len - dj.s;
     const int32_t* rj = rows + dj.roff + dj.s;
     const int nu = sg.ub - sg.ua, w = sg.cb - sg.ca;
+#ifdef CHOL_BOUNDS_CHECK
+    if (!CHOL_BC(sg.ua >= 0 && sg.ua <= sg.ub && sg.ub <= b && sg.ca >= 0 && sg.ca <= sg.cb && sg.cb <= b &&
+                     nu <= kAsmWarpPos,
+                 kBcSegRange))
+      continue;
+#endif
     __syncwarp();   // sK staged / previous segment done with pos[]
     for (int i = lane; i < nu; i += 32) {
       const int32_t key = rj[sg.ua + i];
@@ -46,6 +65,9 @@ __device__ __forceinline__ void assemble_warp_task(const AsmTask& t, const AsmSe
         if (sK[mid] < key) lo = mid + 1; else hi = mid;
       }
       pos[i] = t.p0 + lo;
+#ifdef CHOL_BOUNDS_CHECK
+      if (!CHOL_BC(lo < np && sK[lo] == key, kBcTargetRow)) pos[i] = -1;
+#endif
     }
     __syncwarp();
     const T* Uj = U + dj.uoff;
@@ -65,6 +87,9 @@ __device__ __forceinline__ void assemble_warp_task(const AsmTask& t, const AsmSe
           const int u = sg.ua + ui, c = sg.ca + ci;
           if (c <= u) {
             const int64_t col = rj[c] - dk.f;
+#ifdef CHOL_BOUNDS_CHECK
+            if (!CHOL_BC(col >= 0 && col < dk.s, kBcTargetCol) || pos[ui] < 0) continue;
+#endif
             off[q] = ROWMAJOR ? (int64_t)pos[ui] * dk.ld + col : col * dk.ld + pos[ui];
             v[q] = ROWMAJOR ? Uj[(int64_t)u * ldu + c] : Uj[(int64_t)c * ldu + u];
           }

@@ -88,8 +88,12 @@ __global__ void k_status_init(int* status) { *status = INT_MAX; }
 __global__ void k_scatter(const double* __restrict__ vals, const int64_t* __restrict__ amap,
                           int64_t nnz, double* __restrict__ L) {
   for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < nnz;
-       t += (int64_t)gridDim.x * blockDim.x)
+       t += (int64_t)gridDim.x * blockDim.x) {
+#ifdef CHOL_BOUNDS_CHECK
+    if (!CHOL_BC(amap[t] >= 0 && amap[t] < bc_lim.panel, kBcScatter)) continue;
+#endif
     L[amap[t]] = vals[t];
+  }
 }
 
 // One CTA per small supernode: the whole len x s panel lives in shared memory.
@@ -402,8 +406,17 @@ __device__ __forceinline__ void assemble_body(const AsmTask& t, const AsmSeg* __
                                               const SnodeDev* __restrict__ sn, const int32_t* __restrict__ rows,
                                               const double* __restrict__ U, double* __restrict__ L, int32_t* ssm) {
   __shared__ int32_t tcol[kAsmCols];
+#ifdef CHOL_BOUNDS_CHECK
+  if (!CHOL_BC(t.K >= 0 && t.K < bc_lim.ns, kBcTaskTarget)) return;
+#endif
   const SnodeDev dk = sn[t.K];
   const int np = t.p1 - t.p0;
+#ifdef CHOL_BOUNDS_CHECK
+  if (!CHOL_BC(t.p0 >= 0 && np >= 0 && t.p1 <= dk.len && np <= kAsmPos && t.seg_begin >= 0 &&
+                   t.seg_begin <= t.seg_end && t.seg_end <= bc_lim.nsegs,
+               kBcTaskPositions))
+    return;
+#endif
   int32_t* sK = ssm;              // struct(K) at positions p0 .. p1-1
   int32_t* pos = ssm + kAsmPos;   // positions of rows ua .. ub-1 of the current segment
   const int32_t* rk = rows + dk.roff + t.p0;
@@ -412,10 +425,19 @@ __device__ __forceinline__ void assemble_body(const AsmTask& t, const AsmSeg* __
   const int nwarps = blockDim.x >> 5;
   for (int g = t.seg_begin; g < t.seg_end; ++g) {
     const AsmSeg sg = segs[g];
+#ifdef CHOL_BOUNDS_CHECK
+    if (!CHOL_BC(sg.J >= 0 && sg.J < bc_lim.ns, kBcSegSource)) continue;
+#endif
     const SnodeDev dj = sn[sg.J];
     const int b = dj.len - dj.s;
     const int32_t* rj = rows + dj.roff + dj.s;
     const int nu = sg.ub - sg.ua, w = sg.cb - sg.ca;
+#ifdef CHOL_BOUNDS_CHECK
+    if (!CHOL_BC(sg.ua >= 0 && sg.ua <= sg.ub && sg.ub <= b && sg.ca >= 0 && sg.ca <= sg.cb && sg.cb <= b &&
+                     nu <= kAsmPos && w <= kAsmCols,
+                 kBcSegRange))
+      continue;
+#endif
     __syncthreads();   // sK loaded / previous segment finished with pos[] and tcol[]
     for (int i = threadIdx.x; i < nu; i += blockDim.x) {
       const int32_t key = rj[sg.ua + i];
@@ -425,8 +447,16 @@ __device__ __forceinline__ void assemble_body(const AsmTask& t, const AsmSeg* __
         if (sK[mid] < key) lo = mid + 1; else hi = mid;
       }
       pos[i] = t.p0 + lo;
+#ifdef CHOL_BOUNDS_CHECK
+      if (!CHOL_BC(lo < np && sK[lo] == key, kBcTargetRow)) pos[i] = -1;
+#endif
     }
-    for (int c = threadIdx.x; c < w; c += blockDim.x) tcol[c] = rj[sg.ca + c] - dk.f;
+    for (int c = threadIdx.x; c < w; c += blockDim.x) {
+      tcol[c] = rj[sg.ca + c] - dk.f;
+#ifdef CHOL_BOUNDS_CHECK
+      if (!CHOL_BC(tcol[c] >= 0 && tcol[c] < dk.s, kBcTargetCol)) tcol[c] = -1;
+#endif
+    }
     __syncthreads();
     const double* Uj = U + dj.uoff;
     double* Lk = L + dk.loff;
@@ -444,6 +474,9 @@ __device__ __forceinline__ void assemble_body(const AsmTask& t, const AsmSeg* __
           const int c = sg.ca + cc;
           const int u = sg.ua + (i - cc * nch) * 32 + lane;
           if (u < sg.ub && u >= c) {
+#ifdef CHOL_BOUNDS_CHECK
+            if (tcol[cc] < 0 || pos[u - sg.ua] < 0) continue;
+#endif
             off[q] = (int64_t)tcol[cc] * dk.ld + pos[u - sg.ua];
             v[q] = Uj[(int64_t)c * b + u];
           }
@@ -940,6 +973,10 @@ extern "C" int chol_factor(chol_handle* h, const double* values, void* stream) {
   h->factored = false;
   h->selinv_valid = false;
   if (h->opt.precision != CHOL_PREC_FP64 && (rc = chol_mixed_ensure(h))) return rc;
+  h->bounds_code = 0;
+#ifdef CHOL_BOUNDS_CHECK
+  if (bc_begin(h) || chol_bc_begin_mixed(h)) return CHOL_ECUDA;
+#endif
   if (h->opt.use_graph) {
     // replay a graph of the whole launch sequence; the values go through a copy
     // owned by the handle so that the captured pointers stay valid. Capture and
@@ -1011,6 +1048,16 @@ int chol_finish_factor(chol_handle* h, cudaStream_t st) {
     h->fp64_fallbacks = D->status_host[1];
     h->perturbed_pivots = D->status_host[2];
   }
+#ifdef CHOL_BOUNDS_CHECK
+  {
+    const int e1 = bc_read(), e2 = chol_bc_read_mixed();
+    if (e1 < 0 || e2 < 0) return CHOL_ECUDA;
+    if (e1 || e2) {
+      h->bounds_code = e1 ? e1 : e2;
+      return CHOL_EBOUNDS;
+    }
+  }
+#endif
   const int32_t s = D->status_host[0];
   if (s != INT_MAX) return s;
   if (h->opt.precision != CHOL_PREC_FP64) {
@@ -1023,6 +1070,52 @@ int chol_finish_factor(chol_handle* h, cudaStream_t st) {
   }
   h->factored = true;
   return CHOL_OK;
+}
+
+extern "C" int chol_test_corrupt_plan(chol_handle* h, int32_t kind) {
+#ifdef CHOL_BOUNDS_CHECK
+  if (!h) return -1;
+  if (h->dev) return CHOL_ESTATE;   // the plan is uploaded by the first factorization
+  // first level with a CTA-sized (kind 1-3) or a warp-sized (kind 5) assembly task
+  const LevelPlan* cta = nullptr;
+  const LevelPlan* warp = nullptr;
+  for (const LevelPlan& P : h->levels) {
+    if (!cta && P.asm_n > 0) cta = &P;
+    if (!warp && P.asmw_n > 0) warp = &P;
+  }
+  switch (kind) {
+    case 1:   // a segment's source supernode out of range
+      if (!cta) return CHOL_ENOTSUP;
+      h->asm_segs[h->asm_tasks[cta->asm_b].seg_begin].J = h->ns + 5;
+      return CHOL_OK;
+    case 2: {  // a segment's rows past U_J
+      if (!cta) return CHOL_ENOTSUP;
+      AsmSeg& g = h->asm_segs[h->asm_tasks[cta->asm_b].seg_begin];
+      g.ub = h->snodes[g.J].len - h->snodes[g.J].s + 100;
+      return CHOL_OK;
+    }
+    case 3: {  // a task's row positions past the target
+      if (!cta) return CHOL_ENOTSUP;
+      AsmTask& t = h->asm_tasks[cta->asm_b];
+      t.p1 = h->snodes[t.K].len + 50;
+      return CHOL_OK;
+    }
+    case 4:   // a value's panel position past the panels
+      if (h->amap.empty()) return CHOL_ENOTSUP;
+      h->amap[0] = h->panel_doubles + 1000;
+      return CHOL_OK;
+    case 5:   // a warp task's segment source out of range (negative)
+      if (!warp) return CHOL_ENOTSUP;
+      h->asm_segs[h->asm_tasks[warp->asm_b + warp->asm_n].seg_begin].J = -3;
+      return CHOL_OK;
+    default:
+      return -2;
+  }
+#else
+  (void)h;
+  (void)kind;
+  return CHOL_ENOTSUP;
+#endif
 }
 
 extern "C" int chol_autotune(chol_handle* h, const double* values, void* stream) {

@@ -146,6 +146,7 @@ struct chol_handle {
   std::vector<int64_t> csr_src;     // CSR entry -> entry of the lower CSC input
   int32_t fp64_fallbacks = 0;
   int32_t tc_shallow = 0, tc_deep = 0, panel_launches = 0;   // launch shapes of the last factorization
+  int32_t bounds_code = 0;          // CHOL_BOUNDS_CHECK build: first failed check of the last factorization
   std::vector<int64_t> a_colptr;    // the analyzed pattern of A (for gradients)
   std::vector<int32_t> a_rowind;
   bool selinv_valid = false;        // selected inverse of the current factor computed

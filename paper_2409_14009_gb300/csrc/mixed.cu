@@ -46,8 +46,12 @@ __global__ void k_mx_scale(const double* __restrict__ vals, const int64_t* __res
 __global__ void k_mx_scatter(const double* __restrict__ vals, const int64_t* __restrict__ amap,
                              const int32_t* __restrict__ aij, const double* __restrict__ d, int64_t nnz,
                              float* __restrict__ L) {
-  for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < nnz; t += (int64_t)gridDim.x * blockDim.x)
+  for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < nnz; t += (int64_t)gridDim.x * blockDim.x) {
+#ifdef CHOL_BOUNDS_CHECK
+    if (!CHOL_BC(amap[t] >= 0 && amap[t] < bc_lim.panel, kBcScatter)) continue;
+#endif
     L[amap[t]] = (float)(vals[t] * d[aij[2 * t]] * d[aij[2 * t + 1]]);
+  }
 }
 
 // Dense right-looking Cholesky of the first s columns of a len x s row-major
@@ -451,8 +455,17 @@ __device__ __forceinline__ void mx_assemble_body(const AsmTask& t, const AsmSeg*
                                                  const SnodeDev* __restrict__ sn, const int32_t* __restrict__ rows,
                                                  const float* __restrict__ U, float* __restrict__ L, int32_t* ssm) {
   __shared__ int32_t tcol[kAsmCols];
+#ifdef CHOL_BOUNDS_CHECK
+  if (!CHOL_BC(t.K >= 0 && t.K < bc_lim.ns, kBcTaskTarget)) return;
+#endif
   const SnodeDev dk = sn[t.K];
   const int np = t.p1 - t.p0;
+#ifdef CHOL_BOUNDS_CHECK
+  if (!CHOL_BC(t.p0 >= 0 && np >= 0 && t.p1 <= dk.len && np <= kAsmPos && t.seg_begin >= 0 &&
+                   t.seg_begin <= t.seg_end && t.seg_end <= bc_lim.nsegs,
+               kBcTaskPositions))
+    return;
+#endif
   int32_t* sK = ssm;
   int32_t* pos = ssm + kAsmPos;
   const int32_t* rk = rows + dk.roff + t.p0;
@@ -461,11 +474,20 @@ __device__ __forceinline__ void mx_assemble_body(const AsmTask& t, const AsmSeg*
   const int nwarps = blockDim.x >> 5;
   for (int g = t.seg_begin; g < t.seg_end; ++g) {
     const AsmSeg sg = segs[g];
+#ifdef CHOL_BOUNDS_CHECK
+    if (!CHOL_BC(sg.J >= 0 && sg.J < bc_lim.ns, kBcSegSource)) continue;
+#endif
     const SnodeDev dj = sn[sg.J];
     const int b = dj.len - dj.s;
     const int ldu = (b + 7) & ~7;
     const int32_t* rj = rows + dj.roff + dj.s;
     const int nu = sg.ub - sg.ua, w = sg.cb - sg.ca;
+#ifdef CHOL_BOUNDS_CHECK
+    if (!CHOL_BC(sg.ua >= 0 && sg.ua <= sg.ub && sg.ub <= b && sg.ca >= 0 && sg.ca <= sg.cb && sg.cb <= b &&
+                     nu <= kAsmPos && w <= kAsmCols,
+                 kBcSegRange))
+      continue;
+#endif
     __syncthreads();
     for (int i = threadIdx.x; i < nu; i += blockDim.x) {
       const int32_t key = rj[sg.ua + i];
@@ -475,8 +497,16 @@ __device__ __forceinline__ void mx_assemble_body(const AsmTask& t, const AsmSeg*
         if (sK[mid] < key) lo = mid + 1; else hi = mid;
       }
       pos[i] = t.p0 + lo;
+#ifdef CHOL_BOUNDS_CHECK
+      if (!CHOL_BC(lo < np && sK[lo] == key, kBcTargetRow)) pos[i] = -1;
+#endif
     }
-    for (int c = threadIdx.x; c < w; c += blockDim.x) tcol[c] = rj[sg.ca + c] - dk.f;
+    for (int c = threadIdx.x; c < w; c += blockDim.x) {
+      tcol[c] = rj[sg.ca + c] - dk.f;
+#ifdef CHOL_BOUNDS_CHECK
+      if (!CHOL_BC(tcol[c] >= 0 && tcol[c] < dk.s, kBcTargetCol)) tcol[c] = -1;
+#endif
+    }
     __syncthreads();
     const float* Uj = U + dj.uoff;
     float* Lk = L + dk.loff;
@@ -498,6 +528,9 @@ __device__ __forceinline__ void mx_assemble_body(const AsmTask& t, const AsmSeg*
           const int cc = (nc == 2 ? (i & 1) * 32 : 0) + cl;
           const int u = sg.ua + ui, c = sg.ca + cc;
           if (cc < w && c <= u) {
+#ifdef CHOL_BOUNDS_CHECK
+            if (tcol[cc] < 0 || pos[ui] < 0) continue;
+#endif
             off[q] = (int64_t)pos[ui] * dk.ld + tcol[cc];
             v[q] = Uj[(int64_t)u * ldu + c];
           }
@@ -803,4 +836,23 @@ int chol_gather_mixed(chol_handle* h, const int64_t* dmap, const int32_t* dlrow,
   k_mx_gather<<<grid1d(h->nnz_l, 256), 256, 0, st>>>((const float*)D->L, dmap, dlrow, D->mx_d, h->nnz_l, dlx);
   CHOL_CUDA_TRY(cudaGetLastError());
   return CHOL_OK;
+}
+
+// CHOL_BOUNDS_CHECK build: the limits and the error word of this translation
+// unit's checked kernels (no-ops in the normal build).
+int chol_bc_begin_mixed(const chol_handle* h) {
+#ifdef CHOL_BOUNDS_CHECK
+  return bc_begin(h);
+#else
+  (void)h;
+  return 0;
+#endif
+}
+
+int chol_bc_read_mixed() {
+#ifdef CHOL_BOUNDS_CHECK
+  return bc_read();
+#else
+  return 0;
+#endif
 }
