@@ -172,70 +172,103 @@ __device__ __forceinline__ T fmsub(T a, T b, T c) {   // c - a b, one rounding
   if constexpr (sizeof(T) == 8) return fma(-a, b, c);
   else return fmaf(-a, b, c);
 }
+// Warp 0 factors the 8-column panel [c0, c0 + w) of As in registers (lane l
+// holds rows c0 + l and c0 + l + 32): right-looking, one column at a time, the
+// pivot and the column entries L(c0 + jj, k) passed by shuffles. Clears *sok
+// if a pivot (before its square root) is below `accept` (when accept >
+// -INFINITY), zero, negative or NaN.
+template <class T>
+__device__ __forceinline__ void potrf_panel_warp(T* __restrict__ As, int c0, int w, float accept, int* sok,
+                                                 int* status, bool record, int fcol) {
+  const int lane = threadIdx.x & 31;
+  const int ra = c0 + lane, rb = ra + 32;
+  T xa[8], xb[8];
+#pragma unroll
+  for (int t = 0; t < 8; ++t) {
+    xa[t] = ra < 64 ? As[ra * kPwLd + c0 + t] : T(0);
+    xb[t] = rb < 64 ? As[rb * kPwLd + c0 + t] : T(0);
+  }
+  bool ok = true;
+  const bool check = accept > -INFINITY;
+#pragma unroll
+  for (int kk = 0; kk < 8; ++kk) {
+    if (kk < w) {
+      const T dk = __shfl_sync(0xffffffffu, xa[kk], kk);
+      const bool bad = !(dk > T(0));
+      ok = ok && (!check || (!bad && (float)dk >= accept));
+      if (bad && record && lane == 0) atomicMin(status, fcol + c0 + kk + 1);
+      T root, rroot;
+      pivot_root(dk, bad, root, rroot);
+      const int rk = c0 + kk;
+      xa[kk] = ra == rk ? root : (ra > rk ? xa[kk] * rroot : xa[kk]);
+      xb[kk] = xb[kk] * rroot;   // rb >= c0 + 32 > rk
+#pragma unroll
+      for (int jj = kk + 1; jj < 8; ++jj) {
+        const T cj = __shfl_sync(0xffffffffu, xa[kk], jj);   // L(c0 + jj, rk)
+        xa[jj] = fmsub(xa[kk], cj, xa[jj]);
+        xb[jj] = fmsub(xb[kk], cj, xb[jj]);
+      }
+    }
+  }
+#pragma unroll
+  for (int t = 0; t < 8; ++t) {
+    if (ra < 64) As[ra * kPwLd + c0 + t] = xa[t];
+    if (rb < 64) As[rb * kPwLd + c0 + t] = xb[t];
+  }
+  if (lane == 0 && !ok) *sok = 0;
+}
+
+// Entry (r, j) -= sum_t L(r, c0 + t) L(j, c0 + t), t < w, in t order.
+template <class T>
+__device__ __forceinline__ void potrf_rank8(T* __restrict__ As, int r, int j, int c0, int w) {
+  const T* Ar = As + r * kPwLd + c0;
+  const T* Aj = As + j * kPwLd + c0;
+  T acc = As[r * kPwLd + j];
+#pragma unroll
+  for (int t = 0; t < 8; ++t)
+    if (t < w) acc = fmsub(Ar[t], Aj[t], acc);
+  As[r * kPwLd + j] = acc;
+}
+
 // The panel loop of potrf_panels on a block already staged in As (64 rows of
-// kPwLd entries, lower triangle of a kb x kb block); uniform return value as
-// below. Nothing is read from or written to global memory except *status.
+// kPwLd entries, lower triangle of a kb x kb block), with a one-panel
+// lookahead. For each panel p: first every thread subtracts panel p's rank-8
+// product from panel p + 1's columns (a short step), then warp 0 factors panel
+// p + 1 while warps 1-7 subtract panel p's product from the columns right of
+// it. Every entry still receives its panel products in panel order, each as w
+// fused multiply-subtracts in column order, so the factor is bitwise that of
+// the plain panel loop; the trailing update is off the critical path. Uniform
+// return value as below. Nothing is read from or written to global memory
+// except *status.
 template <class T>
 __device__ __forceinline__ bool potrf_panels_smem(int kb, float accept, T* __restrict__ As, int* sok, int* status,
                                                   bool record, int fcol) {
   const int tid = threadIdx.x;
   if (tid == 0) *sok = 1;
   __syncthreads();
-  const int lane = tid & 31;
+  if (tid < 32 && kb > 0) potrf_panel_warp<T>(As, 0, min(8, kb), accept, sok, status, record, fcol);
+  __syncthreads();
   for (int c0 = 0; c0 < kb; c0 += 8) {
-    const int w = min(8, kb - c0), c1 = c0 + w;
-    if (tid < 32) {
-      const int ra = c0 + lane, rb = ra + 32;
-      T xa[8], xb[8];
-#pragma unroll
-      for (int t = 0; t < 8; ++t) {
-        xa[t] = ra < 64 ? As[ra * kPwLd + c0 + t] : T(0);
-        xb[t] = rb < 64 ? As[rb * kPwLd + c0 + t] : T(0);
-      }
-      bool ok = true;
-      const bool check = accept > -INFINITY;
-#pragma unroll
-      for (int kk = 0; kk < 8; ++kk) {
-        if (kk < w) {
-          const T dk = __shfl_sync(0xffffffffu, xa[kk], kk);
-          const bool bad = !(dk > T(0));
-          ok = ok && (!check || (!bad && (float)dk >= accept));
-          if (bad && record && lane == 0) atomicMin(status, fcol + c0 + kk + 1);
-          T root, rroot;
-          pivot_root(dk, bad, root, rroot);
-          const int rk = c0 + kk;
-          xa[kk] = ra == rk ? root : (ra > rk ? xa[kk] * rroot : xa[kk]);
-          xb[kk] = xb[kk] * rroot;   // rb >= c0 + 32 > rk
-#pragma unroll
-          for (int jj = kk + 1; jj < 8; ++jj) {
-            const T cj = __shfl_sync(0xffffffffu, xa[kk], jj);   // L(c0 + jj, rk)
-            xa[jj] = fmsub(xa[kk], cj, xa[jj]);
-            xb[jj] = fmsub(xb[kk], cj, xb[jj]);
-          }
-        }
-      }
-#pragma unroll
-      for (int t = 0; t < 8; ++t) {
-        if (ra < 64) As[ra * kPwLd + c0 + t] = xa[t];
-        if (rb < 64) As[rb * kPwLd + c0 + t] = xb[t];
-      }
-      if (lane == 0 && !ok) *sok = 0;
+    const int w = min(8, kb - c0), n0 = c0 + w;        // panel p = [c0, n0), next panel [n0, n1)
+    const int nw = min(8, kb - n0), n1 = n0 + nw;
+    if (n0 >= kb) break;                                // uniform: p was the last panel
+    // panel p+1's columns: entry (r, j), n0 <= j < n1, j <= r; thread owns row
+    // n0 + tid / 4 and columns n0 + (tid & 3), n0 + (tid & 3) + 4
+    {
+      const int r = n0 + (tid >> 2);
+      if (r < kb)
+        for (int j = n0 + (tid & 3); j < n1 && j <= r; j += 4) potrf_rank8<T>(As, r, j, c0, w);
     }
     __syncthreads();
-    const int r = c1 + (tid >> 2);
-    if (r < kb) {
-      T lr[8];
-#pragma unroll
-      for (int t = 0; t < 8; ++t) lr[t] = t < w ? As[r * kPwLd + c0 + t] : T(0);
-      T* Ar = As + r * kPwLd;
-      for (int j = c1 + (tid & 3); j <= r; j += 4) {
-        const T* Aj = As + j * kPwLd + c0;
-        T acc = Ar[j];
-#pragma unroll
-        for (int t = 0; t < 8; ++t)
-          if (t < w) acc = fmsub(lr[t], Aj[t], acc);
-        Ar[j] = acc;
-      }
+    if (tid < 32) {
+      potrf_panel_warp<T>(As, n0, nw, accept, sok, status, record, fcol);
+    } else {
+      // the columns right of panel p+1: entry (r, j), n1 <= j <= r; a thread
+      // owns row r = n1 + (tid - 32) / 4 and every fourth column of it
+      const int t2 = tid - 32;
+      const int r = n1 + (t2 >> 2);
+      if (r < kb)
+        for (int j = n1 + (t2 & 3); j <= r; j += 4) potrf_rank8<T>(As, r, j, c0, w);
     }
     __syncthreads();
   }

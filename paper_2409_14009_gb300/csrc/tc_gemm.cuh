@@ -14,7 +14,8 @@
 // - Four warps read the accumulator back with tcgen05.ld (32 columns per load)
 //   and apply the masked epilogue (overwrite for U, subtract for the panel),
 //   with 16-byte loads and stores where a 32-column run is entirely in the
-//   mask; the C values of a run are loaded before the accumulator read.
+//   mask; the subtracting epilogue reads the first run of C while the MMAs
+//   run and each later run while the previous one is processed.
 // Every wait is bounded: on a timeout the CTA records an error code, stops
 // issuing, waits (bounded) for its own copies in flight, frees its tensor memory
 // and returns.
@@ -240,6 +241,21 @@ __device__ __forceinline__ void tile_body(const TileJob& job, uint8_t* smem_raw,
     mma_commit(smem_u32(&accum_bar));
   }
   __syncwarp();
+  const int row = warp * 32 + lane;
+  float* crow = job.C + (int64_t)row * job.ldc;
+  // a 32-column run of this thread's row lies inside the tile and the mask and
+  // is 16-byte aligned
+  auto full_run = [&](int c0) {
+    return row < job.m && c0 + 32 <= job.n && row + job.rdiag >= c0 + 31 &&
+           (reinterpret_cast<uintptr_t>(crow + c0) & 15u) == 0;
+  };
+  // subtracting epilogue: the first run of C is read while the MMAs still run,
+  // each later run while the one before it is processed
+  float4 cbuf[2][8];
+  if (job.sub && full_run(0)) {
+#pragma unroll
+    for (int q = 0; q < 8; ++q) cbuf[0][q] = reinterpret_cast<const float4*>(crow)[q];
+  }
   // one thread waits for the accumulator, then the whole CTA reads it
   __shared__ int acc_ready;
   if (threadIdx.x == 0) {
@@ -250,19 +266,15 @@ __device__ __forceinline__ void tile_body(const TileJob& job, uint8_t* smem_raw,
   __syncthreads();
   fence_after();
   if (acc_ready) {
-    const int row = warp * 32 + lane;
     const uint32_t trow = tmem + ((uint32_t)(warp * 32) << 16);
-    float* crow = job.C + (int64_t)row * job.ldc;
+#pragma unroll
     for (int cb = 0; cb < kTileN / 32; ++cb) {
       const int c0 = cb * 32;
       if (c0 >= job.n) break;                            // uniform across the CTA
-      // the whole run is inside the tile and the mask, and 16-byte aligned
-      const bool full = row < job.m && c0 + 32 <= job.n && row + job.rdiag >= c0 + 31 &&
-                        (reinterpret_cast<uintptr_t>(crow + c0) & 15u) == 0;
-      float4 c[8];
-      if (job.sub && full) {
+      const bool full = full_run(c0);
+      if (cb + 1 < kTileN / 32 && job.sub && full_run(c0 + 32)) {
 #pragma unroll
-        for (int q = 0; q < 8; ++q) c[q] = reinterpret_cast<const float4*>(crow + c0)[q];
+        for (int q = 0; q < 8; ++q) cbuf[(cb + 1) & 1][q] = reinterpret_cast<const float4*>(crow + c0 + 32)[q];
       }
       float v[32];
       tmem_ld32(trow + (uint32_t)c0, v);
@@ -270,7 +282,10 @@ __device__ __forceinline__ void tile_body(const TileJob& job, uint8_t* smem_raw,
 #pragma unroll
         for (int q = 0; q < 8; ++q) {
           float4 o = make_float4(v[4 * q], v[4 * q + 1], v[4 * q + 2], v[4 * q + 3]);
-          if (job.sub) o = make_float4(c[q].x - o.x, c[q].y - o.y, c[q].z - o.z, c[q].w - o.w);
+          if (job.sub) {
+            const float4 c = cbuf[cb & 1][q];
+            o = make_float4(c.x - o.x, c.y - o.y, c.z - o.z, c.w - o.w);
+          }
           reinterpret_cast<float4*>(crow + c0)[q] = o;
         }
       } else if (row < job.m) {
