@@ -43,6 +43,7 @@ def main():
     ap.add_argument("--grid", default="neumann:48")
     ap.add_argument("--precision", default="fp64", choices=sorted(PRECISIONS))
     ap.add_argument("--merge", type=float, default=0.1)
+    ap.add_argument("--block-cols", type=int, default=0, help="column block of the blocked path (0 = default)")
     ap.add_argument("--factors", type=int, default=1, help="factorizations to run")
     ap.add_argument("--nrhs", type=int, default=0, help="solve with this many right-hand sides")
     ap.add_argument("--adjoint", action="store_true", help="run one adjoint (selected inverse + gradient)")
@@ -59,6 +60,8 @@ def main():
     o = P.chol_default_options()
     o.precision = PRECISIONS[a.precision]
     o.merge_growth = a.merge
+    if a.block_cols:
+        o.block_cols = a.block_cols
     if a.batch:
         probs = gridgen.batch_2d(count=a.batch)
         p = gridgen.block_diagonal(probs)
