@@ -681,7 +681,7 @@ void chol_device_free(chol_handle* h) {
                   D->ssmall, D->Zp, D->Tw, D->Ww, D->Uh, D->a_col, D->a_row, D->adj_xb, D->perm, D->status, D->part, D->scalar_dev, D->Y, D->W,
                   D->mx_diagpos, D->mx_aij, D->mx_d, D->mx_fallbacks, D->csr_ptr, D->csr_col, D->csr_src,
                   D->csr_val, D->Lbf, D->tmaps, D->tc_err, D->R, D->Z, D->Pv, D->Q, D->red, D->Y32, D->W32,
-                  D->rhs_scale, D->host_vals, D->host_rhs, D->panel, D->pflags};
+                  D->rhs_scale, D->host_vals, D->host_rhs, D->panel, D->pflags, D->dinv};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   if (D->status_host) cudaFreeHost(D->status_host);
@@ -906,8 +906,11 @@ int enqueue_factor_fp64(chol_handle* h, const double* values, cudaStream_t st) {
 }
 
 int enqueue_factor(chol_handle* h, const double* values, cudaStream_t st) {
-  return h->opt.precision == CHOL_PREC_FP64 ? enqueue_factor_fp64(h, values, st)
-                                            : chol_enqueue_factor_mixed(h, values, st);
+  if (h->opt.precision == CHOL_PREC_FP64) return enqueue_factor_fp64(h, values, st);
+  const int rc = chol_enqueue_factor_mixed(h, values, st);
+  if (rc) return rc;
+  // the binary32 triangle solve multiplies by the diagonal blocks' inverses
+  return chol_diag_inv(h, st);
 }
 
 void drop_graph(chol_handle* h) {

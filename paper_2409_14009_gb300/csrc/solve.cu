@@ -128,8 +128,8 @@ size_t tri_smem(int nr) {
 template <class T, bool RM, bool TRANS>
 __global__ void __launch_bounds__(kT)
 k_sv_tri(const SnodeDev* __restrict__ sn, const TriItem* __restrict__ items, int nitems, const T* __restrict__ L,
-         T* __restrict__ Y, int n, int nrhs, int* __restrict__ flags, int* __restrict__ sync, int* __restrict__ err,
-         long long max_polls, int skew) {
+         const T* __restrict__ Dinv, T* __restrict__ Y, int n, int nrhs, int* __restrict__ flags,
+         int* __restrict__ sync, int* __restrict__ err, long long max_polls, int skew) {
   extern __shared__ __align__(16) unsigned char sv_smem[];
   T* ys = reinterpret_cast<T*>(sv_smem);   // a solved block j, 64 x nrhs
   T* yi = ys + kSub * nrhs;                 // this block's right-hand sides, 64 x nrhs
@@ -144,18 +144,29 @@ k_sv_tri(const SnodeDev* __restrict__ sn, const TriItem* __restrict__ items, int
   const int wait_tgt = tgt + skew;          // skew != 0 only to test the failure path
   const int tid = threadIdx.x, r = tid & 63, g = tid >> 6;
   constexpr bool kfast = RM != TRANS;       // the stored-contiguous index of a product tile is k
+  // binary32: multiply by the diagonal block's inverse (from the factor) instead
+  // of substituting: the substitution is a 64-step dependent chain, more than
+  // half of each link of the triangle chain; binary64 keeps it (a product of
+  // the same size is bound by the FP64 pipe of one SM)
+  constexpr bool kInvDiag = sizeof(T) == 4;
   for (int it = blockIdx.x; it < nitems; it += gridDim.x) {
     const TriItem item = items[it];
     const SnodeDev d = sn[item.J];
     const T* P = L + d.loff;
     const int blk = TRANS ? item.nb - 1 - item.i : item.i;
     const int i0 = blk * kSub, kb = min(kSub, d.s - i0);
-    // stage the diagonal tile and the last dependency's tile before waiting
-    for (int e = tid; e < kb * kb; e += kT) {
-      const int rr = RM ? e / kb : e % kb, cc = RM ? e % kb : e / kb;
-      Ls[rr + cc * 65] = lval<T, RM>(P, d, i0 + rr, i0 + cc);
+    // stage the diagonal tile (binary64: for the substitution) or its inverse
+    // (binary32: for a product), and the last dependency's tile, before waiting
+    if constexpr (kInvDiag) {
+      const T* Di = Dinv + (int64_t)(item.fbase + blk) * (kSub * kSub);
+      for (int e = tid; e < kSub * kSub; e += kT) Ls[(e >> 6) + (e & 63) * 65] = Di[e];
+    } else {
+      for (int e = tid; e < kb * kb; e += kT) {
+        const int rr = RM ? e / kb : e % kb, cc = RM ? e % kb : e / kb;
+        Ls[rr + cc * 65] = lval<T, RM>(P, d, i0 + rr, i0 + cc);
+      }
+      for (int c = tid; c < kb; c += kT) inv[c] = T(1) / lval<T, RM>(P, d, i0 + c, i0 + c);
     }
-    for (int c = tid; c < kb; c += kT) inv[c] = T(1) / lval<T, RM>(P, d, i0 + c, i0 + c);
     // this block's right-hand sides (written by earlier launches only)
     for (int e = tid; e < kb * nrhs; e += kT) {
       const int rr = e % kb, m = e / kb;
@@ -230,56 +241,87 @@ k_sv_tri(const SnodeDev* __restrict__ sn, const TriItem* __restrict__ items, int
       yi[rr + m * kSub] -= sum;
     }
     __syncthreads();
-    // substitution: 16 lanes per right-hand side, lane q holds rows q + 16a;
-    // warps without a live right-hand side skip it, the others take part in the
-    // shuffles with all lanes and only live ones write
-    const int rr = tid >> 4, q = tid & 15;
-    const bool live = rr < nrhs;
-    if ((tid >> 5) * 2 < nrhs) {
-      T y[4];
+    if constexpr (kInvDiag) {
+      // y = L_ii^{-1} yi (forward) or L_ii^{-T} yi (transposed): thread (r, g)
+      // sums k in [16 g, 16 g + 16) for row r, the four partial sums are added
+      // in group order
+      T acc2[kSolveChunk];
 #pragma unroll
-      for (int a = 0; a < 4; ++a) {
-        const int i = q + 16 * a;
-        y[a] = (live && i < kb) ? yi[i + rr * kSub] : T(0);
-      }
-      if (!TRANS) {
+      for (int m = 0; m < kSolveChunk; ++m) acc2[m] = T(0);
+      if (r < kb) {
+#pragma unroll 4
+        for (int kk = 0; kk < 16; ++kk) {
+          const int k = 16 * g + kk;
+          // rows of yi past kb are not staged: skip them (never multiply by 0)
+          if (TRANS ? (k >= r && k < kb) : (k <= r)) {
+            const T a = TRANS ? Ls[k + r * 65] : Ls[r + k * 65];
 #pragma unroll
-        for (int ka = 0; ka < 4; ++ka)
-#pragma unroll
-          for (int kq = 0; kq < 16; ++kq) {
-            const int k = ka * 16 + kq;
-            if (k < kb) {
-              const T yk = __shfl_sync(0xffffffffu, y[ka] * inv[k], kq, 16);
-              if (q == kq) y[ka] = yk;
-#pragma unroll
-              for (int a = ka; a < 4; ++a) {   // rows of earlier slots are solved
-                const int i = q + 16 * a;
-                if (i > k && i < kb) y[a] -= Ls[i + k * 65] * yk;
-              }
-            }
+            for (int m = 0; m < kSolveChunk; ++m)
+              if (m < nrhs) acc2[m] += a * yi[k + m * kSub];
           }
-      } else {
-#pragma unroll
-        for (int ka = 3; ka >= 0; --ka)
-#pragma unroll
-          for (int kq = 15; kq >= 0; --kq) {
-            const int k = ka * 16 + kq;
-            if (k < kb) {
-              const T yk = __shfl_sync(0xffffffffu, y[ka] * inv[k], kq, 16);
-              if (q == kq) y[ka] = yk;
-#pragma unroll
-              for (int a = 0; a <= ka; ++a) {  // rows of later slots are solved
-                const int i = q + 16 * a;
-                if (i < k) y[a] -= Ls[k + i * 65] * yk;
-              }
-            }
-          }
+        }
       }
-      if (live) {
 #pragma unroll
+      for (int m = 0; m < kSolveChunk; ++m)
+        if (m < nrhs) red[(g * kSub + r) + m * 4 * kSub] = acc2[m];
+      __syncthreads();
+      for (int e = tid; e < kb * nrhs; e += kT) {
+        const int rr = e % kb, m = e / kb;
+        const T* pr = red + m * 4 * kSub + rr;
+        Y[d.f + i0 + rr + (int64_t)m * n] = ((pr[0] + pr[kSub]) + pr[2 * kSub]) + pr[3 * kSub];
+      }
+    } else {
+      // substitution: 16 lanes per right-hand side, lane q holds rows q + 16a;
+      // warps without a live right-hand side skip it, the others take part in the
+      // shuffles with all lanes and only live ones write
+      const int rr = tid >> 4, q = tid & 15;
+      const bool live = rr < nrhs;
+      if ((tid >> 5) * 2 < nrhs) {
+        T y[4];
+  #pragma unroll
         for (int a = 0; a < 4; ++a) {
           const int i = q + 16 * a;
-          if (i < kb) Y[d.f + i0 + i + (int64_t)rr * n] = y[a];
+          y[a] = (live && i < kb) ? yi[i + rr * kSub] : T(0);
+        }
+        if (!TRANS) {
+  #pragma unroll
+          for (int ka = 0; ka < 4; ++ka)
+  #pragma unroll
+            for (int kq = 0; kq < 16; ++kq) {
+              const int k = ka * 16 + kq;
+              if (k < kb) {
+                const T yk = __shfl_sync(0xffffffffu, y[ka] * inv[k], kq, 16);
+                if (q == kq) y[ka] = yk;
+  #pragma unroll
+                for (int a = ka; a < 4; ++a) {   // rows of earlier slots are solved
+                  const int i = q + 16 * a;
+                  if (i > k && i < kb) y[a] -= Ls[i + k * 65] * yk;
+                }
+              }
+            }
+        } else {
+  #pragma unroll
+          for (int ka = 3; ka >= 0; --ka)
+  #pragma unroll
+            for (int kq = 15; kq >= 0; --kq) {
+              const int k = ka * 16 + kq;
+              if (k < kb) {
+                const T yk = __shfl_sync(0xffffffffu, y[ka] * inv[k], kq, 16);
+                if (q == kq) y[ka] = yk;
+  #pragma unroll
+                for (int a = 0; a <= ka; ++a) {  // rows of later slots are solved
+                  const int i = q + 16 * a;
+                  if (i < k) y[a] -= Ls[k + i * 65] * yk;
+                }
+              }
+            }
+        }
+        if (live) {
+  #pragma unroll
+          for (int a = 0; a < 4; ++a) {
+            const int i = q + 16 * a;
+            if (i < kb) Y[d.f + i0 + i + (int64_t)rr * n] = y[a];
+          }
         }
       }
     }
@@ -731,6 +773,56 @@ k_sv_small_bwd(const SnodeDev* __restrict__ sn, const int32_t* __restrict__ list
   }
 }
 
+// Inverse of the 64 x 64 diagonal block blk = item.i of every supernode whose
+// triangle the solve handles (one CTA per tri item of the forward order, which
+// lists each block once), for the binary32 solve: thread group g (four lanes)
+// solves L_ii x = e_g by substitution, giving column g of L_ii^{-1}, stored
+// row-major: Dinv[(fbase + blk) * 4096 + r * 64 + c] = (L_ii^{-1})_rc, zero
+// above the diagonal and past the block's width.
+template <class T, bool RM>
+__global__ void __launch_bounds__(kT)
+k_diag_inv(const SnodeDev* __restrict__ sn, const TriItem* __restrict__ items, const T* __restrict__ L,
+           T* __restrict__ Dinv) {
+  __shared__ T Lk[kSub * 65];
+  __shared__ T rinv[kSub];
+  const TriItem item = items[blockIdx.x];
+  const SnodeDev d = sn[item.J];
+  const T* P = L + d.loff;
+  const int blk = item.i, i0 = blk * kSub, kb = min(kSub, d.s - i0);
+  const int tid = threadIdx.x;
+  for (int e = tid; e < kSub * kSub; e += kT) {
+    const int rr = e & 63, cc = e >> 6;
+    Lk[rr + cc * 65] = (rr < kb && cc <= rr) ? lval<T, RM>(P, d, i0 + rr, i0 + cc) : T(0);
+  }
+  __syncthreads();
+  if (tid < kSub) rinv[tid] = tid < kb ? T(1) / Lk[tid + tid * 65] : T(0);
+  __syncthreads();
+  const int g = tid >> 2, q = tid & 3;
+  T x[16];
+#pragma unroll
+  for (int mm = 0; mm < 16; ++mm) x[mm] = (q + 4 * mm == g) ? T(1) : T(0);
+#pragma unroll
+  for (int jm = 0; jm < 16; ++jm) {
+#pragma unroll
+    for (int jq = 0; jq < 4; ++jq) {
+      const int jj = jm * 4 + jq;
+      const T xj = __shfl_sync(0xffffffffu, x[jm] * rinv[jj], jq, 4);
+      if (q == jq) x[jm] = xj;
+#pragma unroll
+      for (int mm = jm; mm < 16; ++mm) {
+        const int c = q + 4 * mm;
+        if (c > jj) x[mm] -= xj * Lk[c + jj * 65];
+      }
+    }
+  }
+  T* Di = Dinv + (int64_t)(item.fbase + blk) * (kSub * kSub);
+#pragma unroll
+  for (int mm = 0; mm < 16; ++mm) {
+    const int c = q + 4 * mm;
+    Di[c * kSub + g] = (c < kb && g < kb) ? x[mm] : T(0);
+  }
+}
+
 // The level schedule of one solve on a chunk of nr <= 16 right-hand sides
 // already permuted into Y (W: per-level panel products). `prof` enables the
 // per-class launch accounting (off for the no-allocation entry point).
@@ -745,10 +837,12 @@ int launch_tri(chol_handle* h, const LevelPlan& P, const T* L, T* Y, int nr, cud
   const int grid = std::min(P.tri_n, per_sm * D->sms);
   const TriItem* items = reinterpret_cast<const TriItem*>(D->tri) + P.tri_b;
   int nitems = P.tri_n, n = h->n;
+  const T* Dinv = reinterpret_cast<const T*>(D->dinv);
   long long max_polls = h->opt.wait_polls > 0 ? (long long)h->opt.wait_polls : kTriMaxPolls;
   int skew = h->opt.test_unreachable_flags ? 1 : 0;
-  void* args[] = {(void*)&D->sn, (void*)&items, (void*)&nitems, (void*)&L, (void*)&Y, (void*)&n, (void*)&nr,
-                  (void*)&D->tri_flags, (void*)&D->tri_sync, (void*)&D->sv_err, (void*)&max_polls, (void*)&skew};
+  void* args[] = {(void*)&D->sn, (void*)&items, (void*)&nitems, (void*)&L, (void*)&Dinv, (void*)&Y, (void*)&n,
+                  (void*)&nr, (void*)&D->tri_flags, (void*)&D->tri_sync, (void*)&D->sv_err, (void*)&max_polls,
+                  (void*)&skew};
   const cudaError_t e = cudaLaunchCooperativeKernel((const void*)k_sv_tri<T, RM, TRANS>, dim3(grid), dim3(kT), args,
                                                     tri_smem<T>(nr), st);
   if (e != cudaSuccess) {
@@ -925,6 +1019,19 @@ int chol_solve_mixed(chol_handle* h, double* b, int32_t nrhs, cudaStream_t st) {
       k_sv_permute_out<float><<<grid1d((int64_t)n * nr, 256), 256, 0, st>>>(D->Y32, D->perm, D->mx_d, sc, n, nr, B);
     }
   }
+  CHOL_CUDA_TRY(cudaGetLastError());
+  return CHOL_OK;
+}
+
+// Inverses of the diagonal blocks the binary32 triangle solve multiplies by,
+// for the mixed-precision factor just enqueued on st (row-major panels).
+int chol_diag_inv(chol_handle* h, cudaStream_t st) {
+  DeviceState* D = h->dev;
+  const int nitems = (int)h->tri_items.size();
+  if (nitems == 0 || h->opt.precision == CHOL_PREC_FP64) return CHOL_OK;
+  const TriItem* items = reinterpret_cast<const TriItem*>(D->tri);
+  KScope ks(h, CHOL_K_SOLVE_DIAG, st, (double)nitems * 64.0 * 64.0 * 64.0 / 3.0, (double)nitems * 64.0 * 64.0 * 8.0);
+  k_diag_inv<float, true><<<nitems, kT, 0, st>>>(D->sn, items, (const float*)D->L, (float*)D->dinv);
   CHOL_CUDA_TRY(cudaGetLastError());
   return CHOL_OK;
 }
