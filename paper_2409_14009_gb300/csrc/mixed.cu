@@ -147,7 +147,9 @@ k_mx_small(const SnodeDev* __restrict__ sn, const int32_t* __restrict__ list, fl
 constexpr int kPnW = kTcOuter;          // outer block width
 static_assert(kPnW == 256, "the tile staging below indexes columns with 8 bits");
 constexpr int kPnLd = kPnW + 4;         // shared tile row stride (floats)
-constexpr size_t kPnSmem = sizeof(float) * ((size_t)64 * kPnLd + 2 * 64 * kPwLd + 64);
+constexpr int kPvLd = 68;              // row stride of the staged L_jj and Xo tiles: rows start on 16 bytes
+static_assert(kPvLd >= kPwLd && kPvLd % 4 == 0 && kPnLd % 4 == 0, "16-byte row starts");
+constexpr size_t kPnSmem = sizeof(float) * ((size_t)64 * kPnLd + 2 * 64 * kPvLd + 64);
 constexpr long long kPanelMaxPolls = 1ll << 21;   // about a second with the back-off
 
 __device__ __forceinline__ int pn_ld_acquire(const int* p) {
@@ -189,9 +191,9 @@ k_mx_panel(const SnodeDev* __restrict__ sn, const PanelItem* __restrict__ items,
            long long max_polls, float tau, int static_pivot, int* status, int* counters) {
   extern __shared__ __align__(16) float pn_smem[];
   float* Own = pn_smem;                 // the tile: 64 rows x w columns (row stride kPnLd)
-  float* Lk = Own + 64 * kPnLd;         // L_jj, column-major (ld kPwLd); POTRF staging (row-major)
-  float* Xo = Lk + 64 * kPwLd;          // rows of sub-block j', columns of j (row-major, ld kPwLd)
-  float* inv = Xo + 64 * kPwLd;         // reciprocal pivots of L_jj
+  float* Lk = Own + 64 * kPnLd;         // L_jj, column-major (ld kPvLd); POTRF staging (row-major, ld kPwLd)
+  float* Xo = Lk + 64 * kPvLd;          // rows of sub-block j', columns of j (row-major, ld kPvLd)
+  float* inv = Xo + 64 * kPvLd;         // reciprocal pivots of L_jj
   __shared__ int s_item, s_ok;
   __shared__ double colk_d[64];
   __shared__ double sinv_d;
@@ -242,45 +244,102 @@ k_mx_panel(const SnodeDev* __restrict__ sn, const PanelItem* __restrict__ items,
 #pragma unroll
         for (int i = 0; i < 16; ++i) {
           const int q = tid + 256 * i;
-          Lk[(q >> 6) + (q & 63) * kPwLd] = v[i];
+          Lk[(q >> 6) + (q & 63) * kPvLd] = v[i];
         }
       }
       __syncthreads();
       // reciprocal pivots; zero past kb, where the tile's columns and L_jj are
       // zero too, so the substitution below needs no bounds on kb
-      if (tid < 64) inv[tid] = tid < kb ? 1.0f / Lk[tid + tid * kPwLd] : 0.f;
+      if (tid < 64) inv[tid] = tid < kb ? 1.0f / Lk[tid + tid * kPvLd] : 0.f;
       __syncthreads();
-      // TRSM of the tile's sub-block j: four lanes per row, lane q holds
-      // columns q + 4 mm; the solved entry is passed by shuffle
-      {
-        const int g = tid >> 2, q = tid & 3;
-        float* Xr = Own + g * kPnLd + c0;
-        float x[16];
+      // TRSM of the tile's sub-block j: two threads per row (threads 0-127),
+      // thread h of row r holding columns [32 h, 32 h + 32) in registers. The
+      // low half substitutes its columns and passes them through shared memory
+      // (Xo is free until the updates); the high half then subtracts their
+      // products, in column order, and substitutes its own. Per entry the same
+      // fused multiply-subtracts in the same order as a column-by-column
+      // substitution with the reciprocal pivots.
+      if (tid < 128) {
+        const int r = tid & 63, h = tid >> 6;
+        float* Xr = Own + r * kPnLd + c0 + 32 * h;
+        float* xs = Xo + r * 33;
+        float x[32];
 #pragma unroll
-        for (int mm = 0; mm < 16; ++mm) x[mm] = Xr[q + 4 * mm];
+        for (int k4 = 0; k4 < 8; ++k4) {
+          const float4 a = *reinterpret_cast<const float4*>(Xr + 4 * k4);
+          x[4 * k4] = a.x; x[4 * k4 + 1] = a.y; x[4 * k4 + 2] = a.z; x[4 * k4 + 3] = a.w;
+        }
+        // substitution of columns [32 h, 32 h + 32) of this row
+        auto substitute = [&](int cb) {
 #pragma unroll
-        for (int jm = 0; jm < 16; ++jm) {
+          for (int jl = 0; jl < 32; ++jl) {
+            const int jj = cb + jl;
+            x[jl] = x[jl] * inv[jj];
+            const float xj = x[jl];
 #pragma unroll
-          for (int jq = 0; jq < 4; ++jq) {
-            const int jj = jm * 4 + jq;
-            const float xj = __shfl_sync(0xffffffffu, x[jm] * inv[jj], jq, 4);
-            if (q == jq) x[jm] = xj;
+            for (int k4 = (jl + 1) >> 2; k4 < 8; ++k4) {
+              const float4 l4 = *reinterpret_cast<const float4*>(Lk + jj * kPvLd + cb + 4 * k4);
+              const float lv[4] = {l4.x, l4.y, l4.z, l4.w};
 #pragma unroll
-            for (int mm = jm; mm < 16; ++mm) {
-              const int c = q + 4 * mm;
-              if (c > jj) x[mm] = fmaf(-xj, Lk[c + jj * kPwLd], x[mm]);
+              for (int u = 0; u < 4; ++u)
+                if (4 * k4 + u > jl) x[4 * k4 + u] = fmaf(-xj, lv[u], x[4 * k4 + u]);
             }
           }
-        }
-        float* Gx = G + (int64_t)g * d.ld + c0;
-        __nv_bfloat16* Bx = Lb ? Lb + d.loff + (int64_t)(item.r0 + g) * d.ld + ob + c0 : nullptr;
+        };
+        if (h == 0) {
+          substitute(0);
 #pragma unroll
-        for (int mm = 0; mm < 16; ++mm) {
-          const int c = q + 4 * mm;
-          Xr[c] = x[mm];
-          if (g < m && c < kb) {
-            Gx[c] = x[mm];
-            if (Bx) Bx[c] = __float2bfloat16_rn(x[mm]);
+          for (int jl = 0; jl < 32; ++jl) xs[jl] = x[jl];
+        }
+        asm volatile("bar.sync 1, 128;" ::: "memory");
+        if (h == 1) {
+#pragma unroll 4
+          for (int jj = 0; jj < 32; ++jj) {
+            const float xj = xs[jj];
+#pragma unroll
+            for (int k4 = 0; k4 < 8; ++k4) {
+              const float4 l4 = *reinterpret_cast<const float4*>(Lk + jj * kPvLd + 32 + 4 * k4);
+              x[4 * k4] = fmaf(-xj, l4.x, x[4 * k4]);
+              x[4 * k4 + 1] = fmaf(-xj, l4.y, x[4 * k4 + 1]);
+              x[4 * k4 + 2] = fmaf(-xj, l4.z, x[4 * k4 + 2]);
+              x[4 * k4 + 3] = fmaf(-xj, l4.w, x[4 * k4 + 3]);
+            }
+          }
+          substitute(32);
+        }
+#pragma unroll
+        for (int k4 = 0; k4 < 8; ++k4)
+          *reinterpret_cast<float4*>(Xr + 4 * k4) =
+              make_float4(x[4 * k4], x[4 * k4 + 1], x[4 * k4 + 2], x[4 * k4 + 3]);
+      }
+      __syncthreads();
+      // the solved sub-block to the panel (and its bf16 copy): 16-byte stores,
+      // a warp writing two rows of 256 contiguous bytes
+      {
+        __nv_bfloat16* Bt = Lb ? Lb + d.loff + (int64_t)item.r0 * d.ld + ob + c0 : nullptr;
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+          const int e = tid + 256 * i, r = e >> 4, c = (e & 15) * 4;
+          if (r < m && c < kb) {
+            const float4 v = *reinterpret_cast<const float4*>(Own + r * kPnLd + c0 + c);
+            float* Gx = G + (int64_t)r * d.ld + c0 + c;
+            __nv_bfloat16* Bx = Bt ? Bt + (int64_t)r * d.ld + c : nullptr;
+            if (c + 4 <= kb) {
+              *reinterpret_cast<float4*>(Gx) = v;
+              if (Bx) {
+                const __nv_bfloat162 lo = __floats2bfloat162_rn(v.x, v.y), hi = __floats2bfloat162_rn(v.z, v.w);
+                uint2 u;
+                u.x = *reinterpret_cast<const uint32_t*>(&lo);
+                u.y = *reinterpret_cast<const uint32_t*>(&hi);
+                *reinterpret_cast<uint2*>(Bx) = u;
+              }
+            } else {
+              const float vv[4] = {v.x, v.y, v.z, v.w};
+              for (int u = 0; u < 4 && c + u < kb; ++u) {
+                Gx[u] = vv[u];
+                if (Bx) Bx[u] = __float2bfloat16_rn(vv[u]);
+              }
+            }
           }
         }
       }
@@ -308,17 +367,34 @@ k_mx_panel(const SnodeDev* __restrict__ sn, const PanelItem* __restrict__ items,
 #pragma unroll
           for (int i = 0; i < 16; ++i) {
             const int q = tid + 256 * i;
-            Xo[(q >> 6) * kPwLd + (q & 63)] = v[i];
+            Xo[(q >> 6) * kPvLd + (q & 63)] = v[i];
           }
           __syncthreads();
           Y = Xo;
-          yld = kPwLd;
+          yld = kPvLd;
         }
         // Own[:, j'] -= Own[:, j] Y^T: thread (tx, ty) owns rows ty + 16 i,
         // columns tx + 16 l; K in column order
         const int tx = tid & 15, ty = tid >> 4;
         float acc[4][4] = {};
-        for (int k = 0; k < kb; ++k) {
+        const int k4 = kb & ~3;
+        for (int k = 0; k < k4; k += 4) {   // four k at a time from 16-byte loads, k in order
+          float4 a[4];
+#pragma unroll
+          for (int i = 0; i < 4; ++i) a[i] = *reinterpret_cast<const float4*>(Own + (ty + 16 * i) * kPnLd + c0 + k);
+#pragma unroll
+          for (int l = 0; l < 4; ++l) {
+            const float4 bv = *reinterpret_cast<const float4*>(Y + (tx + 16 * l) * yld + k);
+#pragma unroll
+            for (int i = 0; i < 4; ++i) {
+              acc[i][l] = fmaf(a[i].x, bv.x, acc[i][l]);
+              acc[i][l] = fmaf(a[i].y, bv.y, acc[i][l]);
+              acc[i][l] = fmaf(a[i].z, bv.z, acc[i][l]);
+              acc[i][l] = fmaf(a[i].w, bv.w, acc[i][l]);
+            }
+          }
+        }
+        for (int k = k4; k < kb; ++k) {
           float a[4], bv[4];
 #pragma unroll
           for (int i = 0; i < 4; ++i) a[i] = Own[(ty + 16 * i) * kPnLd + c0 + k];
