@@ -214,18 +214,33 @@ k_mx_panel(const SnodeDev* __restrict__ sn, const PanelItem* __restrict__ items,
     const int jend = dd >= 0 ? dd : nsub;            // TRSM sub-steps of this tile
     int* fl = flags + item.fbase;
     float* G = L + d.loff + (int64_t)item.r0 * d.ld + ob;   // row 0, column 0 of the tile
-    // stage the tile: 64 rows x 256 columns, 8 loads in flight per thread
-    for (int e0 = 0; e0 < 64 * kPnW; e0 += 8 * 256) {
-      float v[8];
+    // stage the tile's nsub 64-column sub-blocks (the only columns any step
+    // reads; zero past w and below the valid rows): 16-byte loads, all of a
+    // thread's loads issued before its stores
 #pragma unroll
-      for (int u = 0; u < 8; ++u) {
-        const int e = e0 + u * 256 + tid, r = e >> 8, c = e & 255;
-        v[u] = (r < m && c < w) ? G[(int64_t)r * d.ld + c] : 0.f;
+    for (int s0 = 0; s0 < 4; s0 += 2) {   // two sub-blocks at a time: 8 loads in flight
+      if (s0 >= nsub) break;
+      float4 v[8];
+#pragma unroll
+      for (int q = 0; q < 8; ++q) {
+        const int sb = s0 + (q >> 2), e = tid + 256 * (q & 3), r = e >> 4, c = sb * 64 + (e & 15) * 4;
+        float4 x = make_float4(0.f, 0.f, 0.f, 0.f);
+        if (sb < nsub && r < m) {
+          const float* g = G + (int64_t)r * d.ld + c;
+          if (c + 4 <= w) {
+            x = *reinterpret_cast<const float4*>(g);
+          } else if (c < w) {
+            x.x = g[0];
+            if (c + 1 < w) x.y = g[1];
+            if (c + 2 < w) x.z = g[2];
+          }
+        }
+        v[q] = x;
       }
 #pragma unroll
-      for (int u = 0; u < 8; ++u) {
-        const int e = e0 + u * 256 + tid;
-        Own[(e >> 8) * kPnLd + (e & 255)] = v[u];
+      for (int q = 0; q < 8; ++q) {
+        const int sb = s0 + (q >> 2), e = tid + 256 * (q & 3), r = e >> 4, c = sb * 64 + (e & 15) * 4;
+        if (sb < nsub) *reinterpret_cast<float4*>(Own + r * kPnLd + c) = v[q];
       }
     }
     __syncthreads();   // the tile is staged (a d = 0 tile reads it right away)
