@@ -192,8 +192,8 @@ struct chol_handle {
 constexpr int kTile = 64;        // SIMT GEMM/SYRK tile edge
 constexpr int kTileTC = 128;     // tensor-core (tcgen05) GEMM/SYRK tile edge
 constexpr int kTcOuter = 256;    // outer column block of the tensor-core trailing update
-constexpr int kAsmCols = 64;     // assembly task width (target columns)
-constexpr int kAsmPos = 256;     // assembly task height (row positions of the target)
+constexpr int kAsmCols = 32;     // assembly task width (target columns)
+constexpr int kAsmPos = 64;      // assembly task height (row positions of the target)
 constexpr int kAsmWarpPos = 256;       // warp-sized assembly tasks: at most this many positions
 constexpr int kAsmWarpEntries = 4096;  // ... and this many entries over all segments
 constexpr int kTrsmRowsHost = 32; // TRSM task height (rows; binary64 tasks take half)

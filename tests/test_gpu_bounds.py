@@ -80,7 +80,9 @@ def test_checked_build_gives_the_normal_factor(precision):
 @pytest.mark.parametrize("precision", [0, 1])
 def test_damaged_plan_is_caught_without_a_fault(kind, precision):
     P, Lc = _libs()
-    p = gridgen.laplacian_neumann_varcoef((24, 24, 24), 1e-2, 1e2, 1e-6, seed=3)
+    # 3-dof elasticity: its levels have both CTA-sized and warp-sized assembly
+    # tasks (on the 7-point grids every task is warp-sized)
+    p = gridgen.elasticity_27pt(12, seed=3)
     vals = to_dev(p["values"])
     h = _analyze(P, Lc, p, precision)
     try:
