@@ -758,7 +758,8 @@ int chol_mixed_ensure(chol_handle* h) {
     CHOL_CUDA_TRY(cudaMemset(D->tc_err, 0, sizeof(int32_t)));
   }
   if ((rc = upload_vec(h, &D->panel, h->panel_items))) return rc;
-  if ((rc = chol_dalloc(h, &D->dinv, sizeof(float) * 64 * 64 * (size_t)std::max(h->tri_nflags, 1)))) return rc;
+  // per diagonal block of the solve: its inverse and the two last-dependency products
+  if ((rc = chol_dalloc(h, &D->dinv, sizeof(float) * 3 * 64 * 64 * (size_t)std::max(h->tri_nflags, 1)))) return rc;
   if ((rc = chol_dalloc(h, (void**)&D->pflags, sizeof(int32_t) * (size_t)std::max(h->panel_ntickets + h->panel_nflags, 1))))
     return rc;
   if (cudaFuncSetAttribute(k_mx_panel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kPnSmem) != cudaSuccess)

@@ -128,8 +128,8 @@ size_t tri_smem(int nr) {
 template <class T, bool RM, bool TRANS>
 __global__ void __launch_bounds__(kT)
 k_sv_tri(const SnodeDev* __restrict__ sn, const TriItem* __restrict__ items, int nitems, const T* __restrict__ L,
-         const T* __restrict__ Dinv, T* __restrict__ Y, int n, int nrhs, int* __restrict__ flags,
-         int* __restrict__ sync, int* __restrict__ err, long long max_polls, int skew) {
+         T* __restrict__ Y, int n, int nrhs, int* __restrict__ flags, int* __restrict__ sync, int* __restrict__ err,
+         long long max_polls, int skew) {
   extern __shared__ __align__(16) unsigned char sv_smem[];
   T* ys = reinterpret_cast<T*>(sv_smem);   // a solved block j, 64 x nrhs
   T* yi = ys + kSub * nrhs;                 // this block's right-hand sides, 64 x nrhs
@@ -144,29 +144,19 @@ k_sv_tri(const SnodeDev* __restrict__ sn, const TriItem* __restrict__ items, int
   const int wait_tgt = tgt + skew;          // skew != 0 only to test the failure path
   const int tid = threadIdx.x, r = tid & 63, g = tid >> 6;
   constexpr bool kfast = RM != TRANS;       // the stored-contiguous index of a product tile is k
-  // binary32: multiply by the diagonal block's inverse (from the factor) instead
-  // of substituting: the substitution is a 64-step dependent chain, more than
-  // half of each link of the triangle chain; binary64 keeps it (a product of
-  // the same size is bound by the FP64 pipe of one SM)
-  constexpr bool kInvDiag = sizeof(T) == 4;
+  static_assert(sizeof(T) == 8, "binary64 only: binary32 solves take k_sv_tri32");
   for (int it = blockIdx.x; it < nitems; it += gridDim.x) {
     const TriItem item = items[it];
     const SnodeDev d = sn[item.J];
     const T* P = L + d.loff;
     const int blk = TRANS ? item.nb - 1 - item.i : item.i;
     const int i0 = blk * kSub, kb = min(kSub, d.s - i0);
-    // stage the diagonal tile (binary64: for the substitution) or its inverse
-    // (binary32: for a product), and the last dependency's tile, before waiting
-    if constexpr (kInvDiag) {
-      const T* Di = Dinv + (int64_t)(item.fbase + blk) * (kSub * kSub);
-      for (int e = tid; e < kSub * kSub; e += kT) Ls[(e >> 6) + (e & 63) * 65] = Di[e];
-    } else {
-      for (int e = tid; e < kb * kb; e += kT) {
-        const int rr = RM ? e / kb : e % kb, cc = RM ? e % kb : e / kb;
-        Ls[rr + cc * 65] = lval<T, RM>(P, d, i0 + rr, i0 + cc);
-      }
-      for (int c = tid; c < kb; c += kT) inv[c] = T(1) / lval<T, RM>(P, d, i0 + c, i0 + c);
+    // stage the diagonal tile and the last dependency's tile before waiting
+    for (int e = tid; e < kb * kb; e += kT) {
+      const int rr = RM ? e / kb : e % kb, cc = RM ? e % kb : e / kb;
+      Ls[rr + cc * 65] = lval<T, RM>(P, d, i0 + rr, i0 + cc);
     }
+    for (int c = tid; c < kb; c += kT) inv[c] = T(1) / lval<T, RM>(P, d, i0 + c, i0 + c);
     // this block's right-hand sides (written by earlier launches only)
     for (int e = tid; e < kb * nrhs; e += kT) {
       const int rr = e % kb, m = e / kb;
@@ -241,87 +231,56 @@ k_sv_tri(const SnodeDev* __restrict__ sn, const TriItem* __restrict__ items, int
       yi[rr + m * kSub] -= sum;
     }
     __syncthreads();
-    if constexpr (kInvDiag) {
-      // y = L_ii^{-1} yi (forward) or L_ii^{-T} yi (transposed): thread (r, g)
-      // sums k in [16 g, 16 g + 16) for row r, the four partial sums are added
-      // in group order
-      T acc2[kSolveChunk];
+    // substitution: 16 lanes per right-hand side, lane q holds rows q + 16a;
+    // warps without a live right-hand side skip it, the others take part in the
+    // shuffles with all lanes and only live ones write
+    const int rr = tid >> 4, q = tid & 15;
+    const bool live = rr < nrhs;
+    if ((tid >> 5) * 2 < nrhs) {
+      T y[4];
 #pragma unroll
-      for (int m = 0; m < kSolveChunk; ++m) acc2[m] = T(0);
-      if (r < kb) {
-#pragma unroll 4
-        for (int kk = 0; kk < 16; ++kk) {
-          const int k = 16 * g + kk;
-          // rows of yi past kb are not staged: skip them (never multiply by 0)
-          if (TRANS ? (k >= r && k < kb) : (k <= r)) {
-            const T a = TRANS ? Ls[k + r * 65] : Ls[r + k * 65];
+      for (int a = 0; a < 4; ++a) {
+        const int i = q + 16 * a;
+        y[a] = (live && i < kb) ? yi[i + rr * kSub] : T(0);
+      }
+      if (!TRANS) {
 #pragma unroll
-            for (int m = 0; m < kSolveChunk; ++m)
-              if (m < nrhs) acc2[m] += a * yi[k + m * kSub];
+        for (int ka = 0; ka < 4; ++ka)
+#pragma unroll
+          for (int kq = 0; kq < 16; ++kq) {
+            const int k = ka * 16 + kq;
+            if (k < kb) {
+              const T yk = __shfl_sync(0xffffffffu, y[ka] * inv[k], kq, 16);
+              if (q == kq) y[ka] = yk;
+#pragma unroll
+              for (int a = ka; a < 4; ++a) {   // rows of earlier slots are solved
+                const int i = q + 16 * a;
+                if (i > k && i < kb) y[a] -= Ls[i + k * 65] * yk;
+              }
+            }
           }
-        }
-      }
+      } else {
 #pragma unroll
-      for (int m = 0; m < kSolveChunk; ++m)
-        if (m < nrhs) red[(g * kSub + r) + m * 4 * kSub] = acc2[m];
-      __syncthreads();
-      for (int e = tid; e < kb * nrhs; e += kT) {
-        const int rr = e % kb, m = e / kb;
-        const T* pr = red + m * 4 * kSub + rr;
-        Y[d.f + i0 + rr + (int64_t)m * n] = ((pr[0] + pr[kSub]) + pr[2 * kSub]) + pr[3 * kSub];
+        for (int ka = 3; ka >= 0; --ka)
+#pragma unroll
+          for (int kq = 15; kq >= 0; --kq) {
+            const int k = ka * 16 + kq;
+            if (k < kb) {
+              const T yk = __shfl_sync(0xffffffffu, y[ka] * inv[k], kq, 16);
+              if (q == kq) y[ka] = yk;
+#pragma unroll
+              for (int a = 0; a <= ka; ++a) {  // rows of later slots are solved
+                const int i = q + 16 * a;
+                if (i < k) y[a] -= Ls[k + i * 65] * yk;
+              }
+            }
+          }
       }
-    } else {
-      // substitution: 16 lanes per right-hand side, lane q holds rows q + 16a;
-      // warps without a live right-hand side skip it, the others take part in the
-      // shuffles with all lanes and only live ones write
-      const int rr = tid >> 4, q = tid & 15;
-      const bool live = rr < nrhs;
-      if ((tid >> 5) * 2 < nrhs) {
-        T y[4];
-  #pragma unroll
+      if (live) {
+#pragma unroll
         for (int a = 0; a < 4; ++a) {
           const int i = q + 16 * a;
-          y[a] = (live && i < kb) ? yi[i + rr * kSub] : T(0);
-        }
-        if (!TRANS) {
-  #pragma unroll
-          for (int ka = 0; ka < 4; ++ka)
-  #pragma unroll
-            for (int kq = 0; kq < 16; ++kq) {
-              const int k = ka * 16 + kq;
-              if (k < kb) {
-                const T yk = __shfl_sync(0xffffffffu, y[ka] * inv[k], kq, 16);
-                if (q == kq) y[ka] = yk;
-  #pragma unroll
-                for (int a = ka; a < 4; ++a) {   // rows of earlier slots are solved
-                  const int i = q + 16 * a;
-                  if (i > k && i < kb) y[a] -= Ls[i + k * 65] * yk;
-                }
-              }
-            }
-        } else {
-  #pragma unroll
-          for (int ka = 3; ka >= 0; --ka)
-  #pragma unroll
-            for (int kq = 15; kq >= 0; --kq) {
-              const int k = ka * 16 + kq;
-              if (k < kb) {
-                const T yk = __shfl_sync(0xffffffffu, y[ka] * inv[k], kq, 16);
-                if (q == kq) y[ka] = yk;
-  #pragma unroll
-                for (int a = 0; a <= ka; ++a) {  // rows of later slots are solved
-                  const int i = q + 16 * a;
-                  if (i < k) y[a] -= Ls[k + i * 65] * yk;
-                }
-              }
-            }
-        }
-        if (live) {
-  #pragma unroll
-          for (int a = 0; a < 4; ++a) {
-            const int i = q + 16 * a;
-            if (i < kb) Y[d.f + i0 + i + (int64_t)rr * n] = y[a];
-          }
+          if (i < kb) Y[d.f + i0 + i + (int64_t)rr * n] = y[a];
         }
       }
     }
@@ -773,53 +732,306 @@ k_sv_small_bwd(const SnodeDev* __restrict__ sn, const int32_t* __restrict__ list
   }
 }
 
-// Inverse of the 64 x 64 diagonal block blk = item.i of every supernode whose
-// triangle the solve handles (one CTA per tri item of the forward order, which
-// lists each block once), for the binary32 solve: thread group g (four lanes)
-// solves L_ii x = e_g by substitution, giving column g of L_ii^{-1}, stored
-// row-major: Dinv[(fbase + blk) * 4096 + r * 64 + c] = (L_ii^{-1})_rc, zero
-// above the diagonal and past the block's width.
-template <class T, bool RM>
+// ---------------------------------------------------------------------------
+// Binary32 diagonal triangles: each 64-row block is solved by a product with
+// its inverse, and the product with its last dependency's solved block goes
+// through a matrix formed with that inverse in advance, so that after the last
+// wait a block does one tile product. Per block three 64 x 64 row-major
+// matrices, at Dinv + (fbase + blk) * kInvStride:
+//   Li   = L_ii^{-1};
+//   Mf   = L_ii^{-1} L(i, i-1)        (forward, i >= 1);
+//   Mb   = L_ii^{-T} L(i+1, i)^T      (transposed, i + 1 < nb).
+constexpr int kInvStride = 3 * kSub * kSub;
+
+// One CTA per block of the forward item order (which lists each block once):
+// thread group g (four lanes) solves L_ii x = e_g by substitution, giving
+// column g of L_ii^{-1}; then the two 64 x 64 x 64 products, k in order.
 __global__ void __launch_bounds__(kT)
-k_diag_inv(const SnodeDev* __restrict__ sn, const TriItem* __restrict__ items, const T* __restrict__ L,
-           T* __restrict__ Dinv) {
-  __shared__ T Lk[kSub * 65];
-  __shared__ T rinv[kSub];
+k_diag_inv(const SnodeDev* __restrict__ sn, const TriItem* __restrict__ items, const float* __restrict__ L,
+           float* __restrict__ Dinv) {
+  __shared__ float Lk[kSub * 65];              // L_ii (column-major), then the tile of a product
+  __shared__ __align__(16) float Li[kSub * kSub];   // L_ii^{-1}, row-major
+  __shared__ float rinv[kSub];
   const TriItem item = items[blockIdx.x];
   const SnodeDev d = sn[item.J];
-  const T* P = L + d.loff;
+  const float* P = L + d.loff;
   const int blk = item.i, i0 = blk * kSub, kb = min(kSub, d.s - i0);
   const int tid = threadIdx.x;
   for (int e = tid; e < kSub * kSub; e += kT) {
-    const int rr = e & 63, cc = e >> 6;
-    Lk[rr + cc * 65] = (rr < kb && cc <= rr) ? lval<T, RM>(P, d, i0 + rr, i0 + cc) : T(0);
+    const int rr = e >> 6, cc = e & 63;   // consecutive threads read consecutive columns of a row
+    Lk[rr + cc * 65] = (rr < kb && cc <= rr) ? P[(int64_t)(i0 + rr) * d.ld + i0 + cc] : 0.f;
   }
   __syncthreads();
-  if (tid < kSub) rinv[tid] = tid < kb ? T(1) / Lk[tid + tid * 65] : T(0);
+  if (tid < kSub) rinv[tid] = tid < kb ? 1.f / Lk[tid + tid * 65] : 0.f;
   __syncthreads();
-  const int g = tid >> 2, q = tid & 3;
-  T x[16];
+  {
+    const int g = tid >> 2, q = tid & 3;
+    float x[16];
 #pragma unroll
-  for (int mm = 0; mm < 16; ++mm) x[mm] = (q + 4 * mm == g) ? T(1) : T(0);
+    for (int mm = 0; mm < 16; ++mm) x[mm] = (q + 4 * mm == g) ? 1.f : 0.f;
 #pragma unroll
-  for (int jm = 0; jm < 16; ++jm) {
+    for (int jm = 0; jm < 16; ++jm) {
 #pragma unroll
-    for (int jq = 0; jq < 4; ++jq) {
-      const int jj = jm * 4 + jq;
-      const T xj = __shfl_sync(0xffffffffu, x[jm] * rinv[jj], jq, 4);
-      if (q == jq) x[jm] = xj;
+      for (int jq = 0; jq < 4; ++jq) {
+        const int jj = jm * 4 + jq;
+        const float xj = __shfl_sync(0xffffffffu, x[jm] * rinv[jj], jq, 4);
+        if (q == jq) x[jm] = xj;
 #pragma unroll
-      for (int mm = jm; mm < 16; ++mm) {
-        const int c = q + 4 * mm;
-        if (c > jj) x[mm] -= xj * Lk[c + jj * 65];
+        for (int mm = jm; mm < 16; ++mm) {
+          const int c = q + 4 * mm;
+          if (c > jj) x[mm] -= xj * Lk[c + jj * 65];
+        }
       }
     }
-  }
-  T* Di = Dinv + (int64_t)(item.fbase + blk) * (kSub * kSub);
+    float* Di = Dinv + (int64_t)(item.fbase + blk) * kInvStride;
 #pragma unroll
-  for (int mm = 0; mm < 16; ++mm) {
-    const int c = q + 4 * mm;
-    Di[c * kSub + g] = (c < kb && g < kb) ? x[mm] : T(0);
+    for (int mm = 0; mm < 16; ++mm) {
+      const int c = q + 4 * mm;
+      const float v = (c < kb && g < kb) ? x[mm] : 0.f;
+      Di[c * kSub + g] = v;
+      Li[c * kSub + g] = v;
+    }
+  }
+  const int tx = tid & 15, ty = tid >> 4;
+  float* Mf = Dinv + (int64_t)(item.fbase + blk) * kInvStride + kSub * kSub;
+  float* Mb = Mf + kSub * kSub;
+  if (blk >= 1) {
+    // Mf = L_ii^{-1} L(i, i-1): the tile rows i0.., columns (blk - 1) * 64.. (full)
+    __syncthreads();   // Li is complete, Lk is free
+    const int c0 = (blk - 1) * kSub;
+    for (int e = tid; e < kSub * kSub; e += kT) {
+      const int t = e >> 6, k = e & 63;
+      Lk[t * 65 + k] = t < kb ? P[(int64_t)(i0 + t) * d.ld + c0 + k] : 0.f;
+    }
+    __syncthreads();
+    float acc[4][4] = {};
+    for (int t = 0; t < kSub; ++t) {
+      float a[4], b[4];
+#pragma unroll
+      for (int i = 0; i < 4; ++i) a[i] = Li[(ty + 16 * i) * kSub + t];
+#pragma unroll
+      for (int l = 0; l < 4; ++l) b[l] = Lk[t * 65 + tx + 16 * l];
+#pragma unroll
+      for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int l = 0; l < 4; ++l) acc[i][l] = fmaf(a[i], b[l], acc[i][l]);
+    }
+#pragma unroll
+    for (int i = 0; i < 4; ++i)
+#pragma unroll
+      for (int l = 0; l < 4; ++l) Mf[(ty + 16 * i) * kSub + tx + 16 * l] = acc[i][l];
+  }
+  if (blk + 1 < item.nb) {
+    // Mb = L_ii^{-T} L(i+1, i)^T: the tile rows (blk + 1) * 64.., columns i0..,
+    // staged transposed: Lk[t * 65 + k] = L((blk + 1) * 64 + k, i0 + t)
+    __syncthreads();   // Li is complete, the previous product is done with Lk
+    const int r1 = (blk + 1) * kSub, rb = min(kSub, d.s - r1);
+    for (int e = tid; e < kSub * kSub; e += kT) {
+      const int k = e >> 6, t = e & 63;   // consecutive threads read consecutive columns of a row
+      Lk[t * 65 + k] = (k < rb && t < kb) ? P[(int64_t)(r1 + k) * d.ld + i0 + t] : 0.f;
+    }
+    __syncthreads();
+    float acc[4][4] = {};
+    for (int t = 0; t < kSub; ++t) {
+      float a[4], b[4];
+#pragma unroll
+      for (int i = 0; i < 4; ++i) a[i] = Li[t * kSub + ty + 16 * i];
+#pragma unroll
+      for (int l = 0; l < 4; ++l) b[l] = Lk[t * 65 + tx + 16 * l];
+#pragma unroll
+      for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int l = 0; l < 4; ++l) acc[i][l] = fmaf(a[i], b[l], acc[i][l]);
+    }
+#pragma unroll
+    for (int i = 0; i < 4; ++i)
+#pragma unroll
+      for (int l = 0; l < 4; ++l) Mb[(ty + 16 * i) * kSub + tx + 16 * l] = acc[i][l];
+  }
+}
+
+size_t tri32_smem(int nr) {
+  // ys, yi (64 x nr each), L_ii^{-1} and M (64 x 65 each), the k-group
+  // partial sums (4 x 64 x nr)
+  return sizeof(float) * ((size_t)6 * kSub * nr + 2 * kSub * 65);
+}
+
+// Binary32 diagonal triangles of a level (row-major panels). Same items,
+// flags, epochs and bounded waits as k_sv_tri. For block i with last
+// dependency l (forward l = i - 1; transposed l = i + 1):
+//   pre = L_ii^{-1} (b_i - sum over the other dependencies j of L(i, j) y_j)
+// is formed before the last wait (forward; the transposed solve uses
+// L_ii^{-T} and L(j, i)^T), then y_i = pre - M y_l with M = Mf or Mb. Thread
+// (r, g) owns row r and the k range [16 g, 16 g + 16) of every product; the
+// four partial sums are added in group order, so the solve is deterministic.
+template <bool TRANS>
+__global__ void __launch_bounds__(kT)
+k_sv_tri32(const SnodeDev* __restrict__ sn, const TriItem* __restrict__ items, int nitems, const float* __restrict__ L,
+           const float* __restrict__ Dinv, float* __restrict__ Y, int n, int nrhs, int* __restrict__ flags,
+           int* __restrict__ sync, int* __restrict__ err, long long max_polls, int skew) {
+  extern __shared__ __align__(16) unsigned char sv_smem[];
+  float* ys = reinterpret_cast<float*>(sv_smem);   // a solved block j, 64 x nrhs
+  float* yi = ys + kSub * nrhs;                     // this block's right-hand sides, then pre
+  float* red = yi + kSub * nrhs;                    // k-group partial sums, 4 x 64 x nrhs
+  float* Ls = red + 4 * kSub * nrhs;                // L_ii^{-1}, column-major (ld 65)
+  float* Ms = Ls + kSub * 65;                       // M, column-major (ld 65)
+  __shared__ int target;
+  if (threadIdx.x == 0) target = ld_acquire(sync) + 1;
+  __syncthreads();
+  const int tgt = target;
+  const int wait_tgt = tgt + skew;          // skew != 0 only to test the failure path
+  const int tid = threadIdx.x, r = tid & 63, g = tid >> 6, ka = 16 * g;
+  auto wait_flag = [&](int j) {
+    if (tid == 0) {
+      long long polls = 0;
+      while (ld_acquire(flags + j) != wait_tgt) {
+        if (++polls > max_polls) { atomicExch(err, 1); break; }
+        if (polls > 4096) __nanosleep(100);   // spin first: the hand-off is on the critical path
+      }
+    }
+  };
+  // partial sums of acc into red, then out[rr] = base[rr] - (sum in group order)
+  auto reduce = [&](const float (&acc)[kSolveChunk], int kb) {
+#pragma unroll
+    for (int m = 0; m < kSolveChunk; ++m)
+      if (m < nrhs) red[(g * kSub + r) + m * 4 * kSub] = acc[m];
+    __syncthreads();
+    (void)kb;
+  };
+  for (int it = blockIdx.x; it < nitems; it += gridDim.x) {
+    const TriItem item = items[it];
+    const SnodeDev d = sn[item.J];
+    const float* P = L + d.loff;
+    const int blk = TRANS ? item.nb - 1 - item.i : item.i;
+    const int i0 = blk * kSub, kb = min(kSub, d.s - i0);
+    const float* Di = Dinv + (int64_t)(item.fbase + blk) * kInvStride;
+    // the inverse, M and the right-hand sides, before any wait
+    for (int e = tid; e < kSub * kSub; e += kT) Ls[(e >> 6) + (e & 63) * 65] = Di[e];
+    if (item.i > 0) {
+      const float* Mx = Di + (TRANS ? 2 : 1) * kSub * kSub;
+      for (int e = tid; e < kSub * kSub; e += kT) Ms[(e >> 6) + (e & 63) * 65] = Mx[e];
+    }
+    for (int e = tid; e < kb * nrhs; e += kT) {
+      const int rr = e % kb, m = e / kb;
+      yi[rr + m * kSub] = Y[d.f + i0 + rr + (int64_t)m * n];
+    }
+    float acc[kSolveChunk];
+#pragma unroll
+    for (int m = 0; m < kSolveChunk; ++m) acc[m] = 0.f;
+    // the dependencies other than the last, from the panel
+    for (int q = 0; q + 1 < item.i; ++q) {
+      const int j = TRANS ? item.nb - 1 - q : q;
+      const int j0 = j * kSub, jb = min(kSub, d.s - j0);
+      wait_flag(item.fbase + j);
+      __syncthreads();   // also: the previous block is done with ys
+      for (int e = tid; e < jb * nrhs; e += kT) {
+        const int k = e % jb, m = e / jb;
+        ys[k + m * kSub] = __ldcg(Y + d.f + j0 + k + (int64_t)m * n);
+      }
+      __syncthreads();
+      if (r < kb) {
+        const int kz = min(jb, ka + 16), row = i0 + r;
+        float lv[16];
+#pragma unroll
+        for (int kk = 0; kk < 16; ++kk) {
+          const int k = ka + kk;
+          lv[kk] = k < kz ? (TRANS ? P[(int64_t)(j0 + k) * d.ld + row] : P[(int64_t)row * d.ld + j0 + k]) : 0.f;
+        }
+#pragma unroll
+        for (int kk = 0; kk < 16; ++kk) {
+          if (ka + kk >= kz) break;
+#pragma unroll
+          for (int m = 0; m < kSolveChunk; ++m)
+            if (m < nrhs) acc[m] += lv[kk] * ys[ka + kk + m * kSub];
+        }
+      }
+    }
+    __syncthreads();   // every thread is done with ys and red
+    reduce(acc, kb);
+    for (int e = tid; e < kb * nrhs; e += kT) {
+      const int rr = e % kb, m = e / kb;
+      const float* pr = red + m * 4 * kSub + rr;
+      yi[rr + m * kSub] -= ((pr[0] + pr[kSub]) + pr[2 * kSub]) + pr[3 * kSub];
+    }
+    __syncthreads();
+    // pre = L_ii^{-1} yi (forward) or L_ii^{-T} yi (transposed)
+    float acc2[kSolveChunk];
+#pragma unroll
+    for (int m = 0; m < kSolveChunk; ++m) acc2[m] = 0.f;
+    if (r < kb) {
+#pragma unroll 4
+      for (int kk = 0; kk < 16; ++kk) {
+        const int k = ka + kk;
+        // rows of yi past kb are not staged: skip them (never multiply by 0)
+        if (TRANS ? (k >= r && k < kb) : (k <= r)) {
+          const float a = TRANS ? Ls[k + r * 65] : Ls[r + k * 65];
+#pragma unroll
+          for (int m = 0; m < kSolveChunk; ++m)
+            if (m < nrhs) acc2[m] += a * yi[k + m * kSub];
+        }
+      }
+    }
+    __syncthreads();   // every read of yi is done
+    reduce(acc2, kb);
+    for (int e = tid; e < kb * nrhs; e += kT) {
+      const int rr = e % kb, m = e / kb;
+      const float* pr = red + m * 4 * kSub + rr;
+      yi[rr + m * kSub] = ((pr[0] + pr[kSub]) + pr[2 * kSub]) + pr[3 * kSub];
+    }
+    if (item.i > 0) {
+      // the last dependency: y_i = pre - M y_l
+      const int q = item.i - 1;
+      const int j = TRANS ? item.nb - 1 - q : q;
+      const int j0 = j * kSub, jb = min(kSub, d.s - j0);
+      wait_flag(item.fbase + j);
+      __syncthreads();   // also: pre is in yi, red is free
+      for (int e = tid; e < jb * nrhs; e += kT) {
+        const int k = e % jb, m = e / jb;
+        ys[k + m * kSub] = __ldcg(Y + d.f + j0 + k + (int64_t)m * n);
+      }
+      __syncthreads();
+      float acc3[kSolveChunk];
+#pragma unroll
+      for (int m = 0; m < kSolveChunk; ++m) acc3[m] = 0.f;
+      if (r < kb) {
+        const int kz = min(jb, ka + 16);
+#pragma unroll
+        for (int kk = 0; kk < 16; ++kk) {
+          if (ka + kk >= kz) break;
+          const float a = Ms[r + (ka + kk) * 65];
+#pragma unroll
+          for (int m = 0; m < kSolveChunk; ++m)
+            if (m < nrhs) acc3[m] += a * ys[ka + kk + m * kSub];
+        }
+      }
+      reduce(acc3, kb);
+      for (int e = tid; e < kb * nrhs; e += kT) {
+        const int rr = e % kb, m = e / kb;
+        const float* pr = red + m * 4 * kSub + rr;
+        Y[d.f + i0 + rr + (int64_t)m * n] = yi[rr + m * kSub] - (((pr[0] + pr[kSub]) + pr[2 * kSub]) + pr[3 * kSub]);
+      }
+    } else {
+      __syncthreads();
+      for (int e = tid; e < kb * nrhs; e += kT) {
+        const int rr = e % kb, m = e / kb;
+        Y[d.f + i0 + rr + (int64_t)m * n] = yi[rr + m * kSub];
+      }
+    }
+    __syncthreads();   // every thread's rows of Y are written (CTA order) ...
+    if (tid == 0) {
+      __threadfence();  // ... and made visible at GPU scope before the flag
+      st_release(flags + item.fbase + blk, tgt);
+    }
+  }
+  // the last CTA to finish advances the epoch for the next launch
+  __syncthreads();
+  if (tid == 0) {
+    __threadfence();
+    if (atomicAdd(sync + 1, 1) == (int)gridDim.x - 1) {
+      atomicExch(sync + 1, 0);
+      __threadfence();
+      atomicAdd(sync, 1);
+    }
   }
 }
 
@@ -829,22 +1041,33 @@ k_diag_inv(const SnodeDev* __restrict__ sn, const TriItem* __restrict__ items, c
 // Resident CTAs per SM of each triangle kernel per chunk width (set once).
 int g_tri_per_sm[2][2][kSolveChunk + 1] = {};   // [binary32][transposed][nr]
 
+// One cooperative launch of the level's diagonal triangles: k_sv_tri
+// (binary64, substitution) or k_sv_tri32 (binary32, products with the blocks'
+// inverses).
 template <class T, bool RM, bool TRANS>
 int launch_tri(chol_handle* h, const LevelPlan& P, const T* L, T* Y, int nr, cudaStream_t st) {
   DeviceState* D = h->dev;
-  const int per_sm = g_tri_per_sm[sizeof(T) == 4][TRANS][nr];
+  constexpr bool f32 = sizeof(T) == 4;
+  const int per_sm = g_tri_per_sm[f32][TRANS][nr];
   if (per_sm < 1) return CHOL_ENOTSUP;
   const int grid = std::min(P.tri_n, per_sm * D->sms);
   const TriItem* items = reinterpret_cast<const TriItem*>(D->tri) + P.tri_b;
   int nitems = P.tri_n, n = h->n;
-  const T* Dinv = reinterpret_cast<const T*>(D->dinv);
+  const float* Dinv = reinterpret_cast<const float*>(D->dinv);
   long long max_polls = h->opt.wait_polls > 0 ? (long long)h->opt.wait_polls : kTriMaxPolls;
   int skew = h->opt.test_unreachable_flags ? 1 : 0;
-  void* args[] = {(void*)&D->sn, (void*)&items, (void*)&nitems, (void*)&L, (void*)&Dinv, (void*)&Y, (void*)&n,
-                  (void*)&nr, (void*)&D->tri_flags, (void*)&D->tri_sync, (void*)&D->sv_err, (void*)&max_polls,
-                  (void*)&skew};
-  const cudaError_t e = cudaLaunchCooperativeKernel((const void*)k_sv_tri<T, RM, TRANS>, dim3(grid), dim3(kT), args,
-                                                    tri_smem<T>(nr), st);
+  cudaError_t e;
+  if constexpr (f32) {
+    void* args[] = {(void*)&D->sn, (void*)&items, (void*)&nitems, (void*)&L, (void*)&Dinv, (void*)&Y, (void*)&n,
+                    (void*)&nr, (void*)&D->tri_flags, (void*)&D->tri_sync, (void*)&D->sv_err, (void*)&max_polls,
+                    (void*)&skew};
+    e = cudaLaunchCooperativeKernel((const void*)k_sv_tri32<TRANS>, dim3(grid), dim3(kT), args, tri32_smem(nr), st);
+  } else {
+    void* args[] = {(void*)&D->sn, (void*)&items, (void*)&nitems, (void*)&L, (void*)&Y, (void*)&n, (void*)&nr,
+                    (void*)&D->tri_flags, (void*)&D->tri_sync, (void*)&D->sv_err, (void*)&max_polls, (void*)&skew};
+    e = cudaLaunchCooperativeKernel((const void*)k_sv_tri<T, RM, TRANS>, dim3(grid), dim3(kT), args, tri_smem<T>(nr),
+                                    st);
+  }
   if (e != cudaSuccess) {
     cudaGetLastError();
     return CHOL_ECUDA;
@@ -932,16 +1155,16 @@ int set_solve_attrs() {
   static std::once_flag once;
   static int rc = CHOL_OK;
   std::call_once(once, [] {
-    const size_t dd = tri_smem<double>(kSolveChunk), df = tri_smem<float>(kSolveChunk);
+    const size_t dd = tri_smem<double>(kSolveChunk), df = tri32_smem(kSolveChunk);
     const void* kd[2] = {(const void*)k_sv_tri<double, false, false>, (const void*)k_sv_tri<double, false, true>};
-    const void* kf[2] = {(const void*)k_sv_tri<float, true, false>, (const void*)k_sv_tri<float, true, true>};
+    const void* kf[2] = {(const void*)k_sv_tri32<false>, (const void*)k_sv_tri32<true>};
     cudaError_t e = cudaSuccess;
     for (int t = 0; t < 2; ++t) {
       e = e ? e : cudaFuncSetAttribute(kd[t], cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dd);
       e = e ? e : cudaFuncSetAttribute(kf[t], cudaFuncAttributeMaxDynamicSharedMemorySize, (int)df);
       for (int nr = 1; nr <= kSolveChunk; ++nr) {
         e = e ? e : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&g_tri_per_sm[0][t][nr], kd[t], kT, tri_smem<double>(nr));
-        e = e ? e : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&g_tri_per_sm[1][t][nr], kf[t], kT, tri_smem<float>(nr));
+        e = e ? e : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&g_tri_per_sm[1][t][nr], kf[t], kT, tri32_smem(nr));
       }
     }
     if (e != cudaSuccess) {
@@ -1030,8 +1253,10 @@ int chol_diag_inv(chol_handle* h, cudaStream_t st) {
   const int nitems = (int)h->tri_items.size();
   if (nitems == 0 || h->opt.precision == CHOL_PREC_FP64) return CHOL_OK;
   const TriItem* items = reinterpret_cast<const TriItem*>(D->tri);
-  KScope ks(h, CHOL_K_SOLVE_DIAG, st, (double)nitems * 64.0 * 64.0 * 64.0 / 3.0, (double)nitems * 64.0 * 64.0 * 8.0);
-  k_diag_inv<float, true><<<nitems, kT, 0, st>>>(D->sn, items, (const float*)D->L, (float*)D->dinv);
+  // per block: the inverse by substitution and up to two 64^3 products
+  KScope ks(h, CHOL_K_SOLVE_DIAG, st, (double)nitems * 5.0 * 64.0 * 64.0 * 64.0,
+            (double)nitems * 64.0 * 64.0 * 4.0 * 6.0);
+  k_diag_inv<<<nitems, kT, 0, st>>>(D->sn, items, (const float*)D->L, (float*)D->dinv);
   CHOL_CUDA_TRY(cudaGetLastError());
   return CHOL_OK;
 }
