@@ -29,8 +29,8 @@ struct DeviceState {
   int4* rlb_pairs = nullptr;    // RLB: (K, c0, c1, -) of every (J, K) pair, J-major
   int32_t* rlb_pbeg = nullptr;  // RLB: first pair of every supernode
   double* zrr_ws = nullptr;     // adjoint: Z_RR workspace when there is no update workspace (RLB)
-  int32_t* tri_flags = nullptr; // solve: one flag per diagonal block (zeroed once)
-  void* dinv = nullptr;         // mixed modes: per 64-row diagonal block of the solve, L_ii^{-1} and two products (binary32)
+  int32_t* tri_flags = nullptr; // solve: one flag per diagonal block and chunk column (zeroed once)
+  void* dinv = nullptr;         // per 64-row diagonal block of the solve: binary64 L_ii^{-1}; mixed modes: L_ii^{-1} and two products (binary32)
   int32_t* tri_sync = nullptr;  // solve: {epoch, CTAs done} of the triangle launches
   int32_t* sv_err = nullptr;    // solve: set when a bounded wait gave up
   int32_t* ssmall = nullptr;

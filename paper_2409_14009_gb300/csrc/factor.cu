@@ -760,10 +760,15 @@ int chol_device_ensure(chol_handle* h) {
     if ((rc = upload(h, &D->rlb_pairs, pr))) return fail(rc);
     if ((rc = upload(h, &D->rlb_pbeg, h->pair_beg))) return fail(rc);
   }
-  if ((rc = chol_dalloc(h, (void**)&D->tri_flags, sizeof(int32_t) * (size_t)std::max(h->tri_nflags, 1)))) return fail(rc);
+  // one flag per diagonal block and right-hand-side column of a chunk
+  const size_t nflags = (size_t)std::max(h->tri_nflags, 1) * kSolveChunk;
+  if ((rc = chol_dalloc(h, (void**)&D->tri_flags, sizeof(int32_t) * nflags))) return fail(rc);
+  if (h->opt.precision == CHOL_PREC_FP64 &&
+      (rc = chol_dalloc(h, &D->dinv, sizeof(double) * 64 * 64 * (size_t)std::max(h->tri_nflags, 1))))
+    return fail(rc);
   if ((rc = chol_dalloc(h, (void**)&D->tri_sync, sizeof(int32_t) * 2))) return fail(rc);
   if ((rc = chol_dalloc(h, (void**)&D->sv_err, sizeof(int32_t)))) return fail(rc);
-  if (cudaMemset(D->tri_flags, 0, sizeof(int32_t) * (size_t)std::max(h->tri_nflags, 1)) != cudaSuccess ||
+  if (cudaMemset(D->tri_flags, 0, sizeof(int32_t) * nflags) != cudaSuccess ||
       cudaMemset(D->tri_sync, 0, sizeof(int32_t) * 2) != cudaSuccess ||
       cudaMemset(D->sv_err, 0, sizeof(int32_t)) != cudaSuccess)
     return fail(CHOL_ECUDA);
@@ -906,10 +911,10 @@ int enqueue_factor_fp64(chol_handle* h, const double* values, cudaStream_t st) {
 }
 
 int enqueue_factor(chol_handle* h, const double* values, cudaStream_t st) {
-  if (h->opt.precision == CHOL_PREC_FP64) return enqueue_factor_fp64(h, values, st);
-  const int rc = chol_enqueue_factor_mixed(h, values, st);
+  const int rc = h->opt.precision == CHOL_PREC_FP64 ? enqueue_factor_fp64(h, values, st)
+                                                    : chol_enqueue_factor_mixed(h, values, st);
   if (rc) return rc;
-  // the binary32 triangle solve multiplies by the diagonal blocks' inverses
+  // the triangle solves multiply by the diagonal blocks' inverses
   return chol_diag_inv(h, st);
 }
 

@@ -89,19 +89,21 @@ __global__ void k_sv_maxabs(const double* __restrict__ b, int n, int nr, unsigne
 // Diagonal triangles of every (non-warp) supernode of a level in one
 // cooperative launch. Item (J, i) owns the 64-row block blk of L_JJ (blk = i
 // forward, nb-1-i transposed); the items of J are listed in dependency order.
-// A CTA takes items blockIdx.x, blockIdx.x + gridDim.x, ...; for each it
-// accumulates the products with the blocks already solved (forward: blocks
-// j < blk, L(blk, j) y_j; transposed: blocks j > blk, L(j, blk)^T x_j) as
-// their flags are published, then solves its own 64 x 64 triangle by
-// substitution (16 lanes per right-hand side, the solved entry broadcast by
-// shuffle), writes its rows of Y and publishes its flag. Waits point only to
-// items with smaller indices and every CTA is resident (cooperative launch),
-// so the smallest unfinished item can always proceed. Each wait is bounded;
-// one that gives up sets *err and carries on (the result is then invalid).
-// Flags hold the value epoch + 1 of the launch that published them; the last
-// CTA to finish advances the device-side epoch, so no reset is needed between
-// launches (also when they are replayed from a CUDA graph). Every entry of Y is
-// computed by one thread in a fixed order: the solve is deterministic.
+// The binary64 kernel (k_sv_tri64) runs one right-hand-side column per item:
+// virtual item v = item * nrhs + m. The binary32 kernel (k_sv_tri32) takes all
+// columns of a chunk in one item. A CTA takes virtual items blockIdx.x,
+// blockIdx.x + gridDim.x, ...; for each it accumulates the products with the
+// blocks already solved (forward: blocks j < blk, L(blk, j) y_j; transposed:
+// blocks j > blk, L(j, blk)^T x_j) as their flags are published, then
+// multiplies by the block's inverse, writes its rows of Y and publishes its
+// flag. Waits point only to items with smaller indices and every CTA is
+// resident (cooperative launch), so the smallest unfinished item can always
+// proceed. Each wait is bounded; one that gives up sets *err and carries on
+// (the result is then invalid). Flags hold the value epoch + 1 of the launch
+// that published them; the last CTA to finish advances the device-side epoch,
+// so no reset is needed between launches (also when they are replayed from a
+// CUDA graph). Every entry of Y is computed by one thread in a fixed order: the
+// solve is deterministic.
 struct TriItem {
   int32_t J, i, nb, fbase;
 };
@@ -118,176 +120,175 @@ __device__ __forceinline__ void st_release(int* p, int v) {
 
 constexpr long long kTriMaxPolls = 1ll << 24;   // seconds, with the back-off below
 
-template <class T>
-size_t tri_smem(int nr) {
-  // ys (64 x nr), yi (64 x nr), Ls (64 x 65), Lt (64 x 65; later the k-group
-  // partial sums, 4 x 64 x nr), inv (64)
-  return sizeof(T) * ((size_t)2 * kSub * nr + 2 * kSub * 65 + kSub);
+// ---------------------------------------------------------------------------
+// Binary64 diagonal triangles through inverted 64 x 64 diagonal blocks.
+// On this part a dependent binary64 FMA takes about 65 cycles and one SM
+// retires two binary64 FMAs per cycle, so a 64-step substitution is a long
+// latency chain and a 64 x 64 tile product with 8 right-hand sides keeps one
+// SM's FP64 pipe busy for 8 us. Here each right-hand-side column of a block is
+// its own item (8 columns run on 8 SMs), and after its last wait a block does
+// two 64 x 64 matrix-vector products (the last dependency's tile, then the
+// inverse) instead of the substitution. The inverses are formed once after the
+// factor (k_diag_inv64), column-major: Dinv[(fbase + blk) * 4096 + r + 64 c] =
+// (L_ii^{-1})(r, c), zero above the diagonal and past the block's width.
+constexpr int kInv64Stride = kSub * kSub;
+
+// One CTA per block: thread group g (four lanes) solves L_ii x = e_g by
+// substitution, lane q holding rows q + 4 mm, giving column g of L_ii^{-1}.
+__global__ void __launch_bounds__(kT)
+k_diag_inv64(const SnodeDev* __restrict__ sn, const TriItem* __restrict__ items, const double* __restrict__ L,
+             double* __restrict__ Dinv) {
+  __shared__ double Lk[kSub * 65];   // L_ii, column-major (ld 65), zero above the diagonal and past kb
+  __shared__ double rinv[kSub];
+  const TriItem item = items[blockIdx.x];
+  const SnodeDev d = sn[item.J];
+  const double* P = L + d.loff;
+  const int blk = item.i, i0 = blk * kSub, kb = min(kSub, d.s - i0);
+  const int tid = threadIdx.x;
+  for (int e = tid; e < kSub * kSub; e += kT) {
+    const int rr = e & 63, cc = e >> 6;   // consecutive threads read consecutive rows of a column
+    Lk[rr + cc * 65] = (rr < kb && cc <= rr) ? P[(i0 + rr) + (int64_t)(i0 + cc) * d.ld] : 0.0;
+  }
+  __syncthreads();
+  if (tid < kSub) rinv[tid] = tid < kb ? 1.0 / Lk[tid * 66] : 0.0;
+  __syncthreads();
+  const int g = tid >> 2, q = tid & 3;
+  double x[16];
+#pragma unroll
+  for (int mm = 0; mm < 16; ++mm) x[mm] = (q + 4 * mm == g) ? 1.0 : 0.0;
+#pragma unroll
+  for (int jm = 0; jm < 16; ++jm) {
+#pragma unroll
+    for (int jq = 0; jq < 4; ++jq) {
+      const int jj = jm * 4 + jq;
+      const double xj = __shfl_sync(0xffffffffu, x[jm] * rinv[jj], jq, 4);
+      if (q == jq) x[jm] = xj;
+#pragma unroll
+      for (int mm = jm; mm < 16; ++mm) {
+        const int c = q + 4 * mm;
+        if (c > jj) x[mm] = fma(-xj, Lk[c + jj * 65], x[mm]);
+      }
+    }
+  }
+  double* Di = Dinv + (int64_t)(item.fbase + blk) * kInv64Stride;
+#pragma unroll
+  for (int mm = 0; mm < 16; ++mm) {
+    const int c = q + 4 * mm;
+    Di[c + g * kSub] = (c < kb && g < kb) ? x[mm] : 0.0;
+  }
 }
 
-template <class T, bool RM, bool TRANS>
-__global__ void __launch_bounds__(kT)
-k_sv_tri(const SnodeDev* __restrict__ sn, const TriItem* __restrict__ items, int nitems, const T* __restrict__ L,
-         T* __restrict__ Y, int n, int nrhs, int* __restrict__ flags, int* __restrict__ sync, int* __restrict__ err,
-         long long max_polls, int skew) {
-  extern __shared__ __align__(16) unsigned char sv_smem[];
-  T* ys = reinterpret_cast<T*>(sv_smem);   // a solved block j, 64 x nrhs
-  T* yi = ys + kSub * nrhs;                 // this block's right-hand sides, 64 x nrhs
-  T* Ls = yi + kSub * nrhs;                 // diagonal tile, 64 x 65
-  T* Lt = Ls + kSub * 65;                   // tile of the last dependency, 64 x 65
-  T* red = Lt;                              // then: k-group partial sums, 4 x 64 x nrhs
-  T* inv = Lt + kSub * 65;                  // 64
+// The binary64 triangle items of a level, one right-hand-side column each
+// (column-major panels). Thread (r, g) owns row r of the block and the k range
+// [16 g, 16 g + 16) of every product; it keeps four partial sums (k mod 4),
+// added pairwise, and the four k-groups are added in group order, so each
+// entry of Y is computed in a fixed order. The block's inverse entries and the
+// last dependency's tile are loaded into registers before any wait, and each
+// earlier tile's entries before its flag is read.
+template <bool TRANS>
+__global__ void __launch_bounds__(kT, 2)
+k_sv_tri64(const SnodeDev* __restrict__ sn, const TriItem* __restrict__ items, int nitems, const double* __restrict__ L,
+           const double* __restrict__ Dinv, double* __restrict__ Y, int n, int nrhs, int* __restrict__ flags,
+           int* __restrict__ sync, int* __restrict__ err, long long max_polls, int skew) {
+  __shared__ double ys[kSub];         // a solved block's column
+  __shared__ double zs[kSub];         // this block's right-hand side, then z
+  __shared__ double red[4 * kSub];    // k-group partial sums
   __shared__ int target;
-  if (threadIdx.x == 0) target = ld_acquire(sync) + 1;
+  const int tid = threadIdx.x, r = tid & 63, g = tid >> 6, ka = 16 * g;
+  if (tid == 0) target = ld_acquire(sync) + 1;
   __syncthreads();
   const int tgt = target;
-  const int wait_tgt = tgt + skew;          // skew != 0 only to test the failure path
-  const int tid = threadIdx.x, r = tid & 63, g = tid >> 6;
-  constexpr bool kfast = RM != TRANS;       // the stored-contiguous index of a product tile is k
-  static_assert(sizeof(T) == 8, "binary64 only: binary32 solves take k_sv_tri32");
-  for (int it = blockIdx.x; it < nitems; it += gridDim.x) {
+  const int wait_tgt = tgt + skew;   // skew != 0 only to test the failure path
+  auto wait_flag = [&](const int* f) {
+    if (tid == 0) {
+      long long polls = 0;
+      while (ld_acquire(f) != wait_tgt) {
+        if (++polls > max_polls) { atomicExch(err, 1); break; }
+        if (polls > 4096) __nanosleep(100);   // spin first: the hand-off is on the critical path
+      }
+    }
+  };
+  // zs[r] -= (sum of the four k-groups' partial sums), group order
+  auto subtract_sums = [&](double part) {
+    red[g * kSub + r] = part;
+    __syncthreads();
+    if (tid < kSub) zs[tid] -= ((red[tid] + red[kSub + tid]) + red[2 * kSub + tid]) + red[3 * kSub + tid];
+    __syncthreads();
+  };
+  const int64_t nv = (int64_t)nitems * nrhs;
+  for (int64_t v = blockIdx.x; v < nv; v += gridDim.x) {
+    const int it = (int)(v / nrhs), m = (int)(v - (int64_t)it * nrhs);
     const TriItem item = items[it];
     const SnodeDev d = sn[item.J];
-    const T* P = L + d.loff;
+    const double* P = L + d.loff;
     const int blk = TRANS ? item.nb - 1 - item.i : item.i;
     const int i0 = blk * kSub, kb = min(kSub, d.s - i0);
-    // stage the diagonal tile and the last dependency's tile before waiting
-    for (int e = tid; e < kb * kb; e += kT) {
-      const int rr = RM ? e / kb : e % kb, cc = RM ? e % kb : e / kb;
-      Ls[rr + cc * 65] = lval<T, RM>(P, d, i0 + rr, i0 + cc);
-    }
-    for (int c = tid; c < kb; c += kT) inv[c] = T(1) / lval<T, RM>(P, d, i0 + c, i0 + c);
-    // this block's right-hand sides (written by earlier launches only)
-    for (int e = tid; e < kb * nrhs; e += kT) {
-      const int rr = e % kb, m = e / kb;
-      yi[rr + m * kSub] = Y[d.f + i0 + rr + (int64_t)m * n];
-    }
+    double* Ym = Y + d.f + (int64_t)m * n;
+    int* fl = flags + m;   // flag of block j: fl[(fbase + j) * kSolveChunk]
+    // L(row, col) of the block row r and a dependency's column k (forward), or
+    // the transposed pair (L(j, blk)^T), both column-major in the panel
+    auto lrow = [&](int j0, int k) -> double {
+      return TRANS ? P[(j0 + k) + (int64_t)(i0 + r) * d.ld] : P[(i0 + r) + (int64_t)(j0 + k) * d.ld];
+    };
+    // the inverse's entries of row r (forward: L_ii^{-1}(r, k); transposed:
+    // L_ii^{-T}(r, k) = L_ii^{-1}(k, r)), zero where the product has none
+    const double* Di = Dinv + (int64_t)(item.fbase + blk) * kInv64Stride;
+    const bool inv_live = TRANS ? (ka + 15 >= r) : (ka <= r);
+    double li[16];
+#pragma unroll
+    for (int kk = 0; kk < 16; ++kk)
+      li[kk] = inv_live ? (TRANS ? Di[(ka + kk) + r * kSub] : Di[r + (ka + kk) * kSub]) : 0.0;
+    if (tid < kSub) zs[tid] = tid < kb ? Ym[i0 + tid] : 0.0;
+    // the last dependency's tile
+    double lt[16];
+    int jl0 = 0, jlb = 0;
     if (item.i > 0) {
-      const int jl = TRANS ? blk + 1 : blk - 1, jl0 = jl * kSub, jlb = min(kSub, d.s - jl0);
-      for (int e = tid; e < kb * jlb; e += kT) {
-        const int rr = kfast ? e / jlb : e % kb, k = kfast ? e % jlb : e / kb;
-        Lt[rr + k * 65] = TRANS ? lval<T, RM>(P, d, jl0 + k, i0 + rr) : lval<T, RM>(P, d, i0 + rr, jl0 + k);
-      }
-    }
-    T acc[kSolveChunk];
+      const int jl = TRANS ? blk + 1 : blk - 1;
+      jl0 = jl * kSub;
+      jlb = min(kSub, d.s - jl0);
 #pragma unroll
-    for (int m = 0; m < kSolveChunk; ++m) acc[m] = T(0);
-    const int ka = g * 16;                  // this thread's k range within a tile
-    for (int q = 0; q < item.i; ++q) {
-      const int j = TRANS ? item.nb - 1 - q : q;       // an already solved block
+      for (int kk = 0; kk < 16; ++kk) lt[kk] = (r < kb && ka + kk < jlb) ? lrow(jl0, ka + kk) : 0.0;
+    }
+    // the dependencies other than the last, straight from the panel
+    double a[4] = {0.0, 0.0, 0.0, 0.0};
+    for (int q = 0; q + 1 < item.i; ++q) {
+      const int j = TRANS ? item.nb - 1 - q : q;
       const int j0 = j * kSub, jb = min(kSub, d.s - j0);
-      if (tid == 0) {
-        long long polls = 0;
-        while (ld_acquire(flags + item.fbase + j) != wait_tgt) {
-          if (++polls > max_polls) { atomicExch(err, 1); break; }
-          if (polls > 4096) __nanosleep(100);   // spin first: the hand-off is on the critical path
-        }
-      }
+      double lv[16];
+#pragma unroll
+      for (int kk = 0; kk < 16; ++kk) lv[kk] = (r < kb && ka + kk < jb) ? lrow(j0, ka + kk) : 0.0;
+      wait_flag(fl + (int64_t)(item.fbase + j) * kSolveChunk);
       __syncthreads();   // also: the previous tile is done with ys
-      for (int e = tid; e < jb * nrhs; e += kT) {
-        const int k = e % jb, rr = e / jb;
-        ys[k + rr * kSub] = __ldcg(Y + d.f + j0 + k + (int64_t)rr * n);
-      }
+      if (tid < kSub) ys[tid] = tid < jb ? __ldcg(Ym + j0 + tid) : 0.0;
       __syncthreads();
-      if (r < kb) {
-        const int kz = min(jb, ka + 16);
-        if (q + 1 < item.i) {
-          // an earlier tile, straight from the panel: all 16 loads issued
-          // before the products
-          const int row = i0 + r;
-          T lv[16];
 #pragma unroll
-          for (int kk = 0; kk < 16; ++kk) {
-            const int k = ka + kk;
-            lv[kk] = k < kz ? (TRANS ? lval<T, RM>(P, d, j0 + k, row) : lval<T, RM>(P, d, row, j0 + k)) : T(0);
-          }
-#pragma unroll
-          for (int kk = 0; kk < 16; ++kk) {
-            if (ka + kk >= kz) break;
-#pragma unroll
-            for (int m = 0; m < kSolveChunk; ++m)
-              if (m < nrhs) acc[m] += lv[kk] * ys[ka + kk + m * kSub];
-          }
-        } else {
-          for (int k = ka; k < kz; ++k) {
-            const T l = Lt[r + k * 65];
-#pragma unroll
-            for (int m = 0; m < kSolveChunk; ++m)
-              if (m < nrhs) acc[m] += l * ys[k + m * kSub];
-          }
-        }
-      }
+      for (int kk = 0; kk < 16; ++kk) a[kk & 3] = fma(lv[kk], ys[ka + kk], a[kk & 3]);
     }
-    __syncthreads();   // Lt is free: it now holds the partial sums
+    subtract_sums((a[0] + a[1]) + (a[2] + a[3]));
+    if (item.i > 0) {
+      // the last dependency: z = pre - L(i, l) y_l
+      wait_flag(fl + (int64_t)(item.fbase + (TRANS ? blk + 1 : blk - 1)) * kSolveChunk);
+      __syncthreads();
+      if (tid < kSub) ys[tid] = tid < jlb ? __ldcg(Ym + jl0 + tid) : 0.0;
+      __syncthreads();
+      double b[4] = {0.0, 0.0, 0.0, 0.0};
 #pragma unroll
-    for (int m = 0; m < kSolveChunk; ++m)
-      if (m < nrhs) red[(g * kSub + r) + m * 4 * kSub] = acc[m];
+      for (int kk = 0; kk < 16; ++kk) b[kk & 3] = fma(lt[kk], ys[ka + kk], b[kk & 3]);
+      subtract_sums((b[0] + b[1]) + (b[2] + b[3]));
+    }
+    // y_i = L_ii^{-1} z (forward) or L_ii^{-T} z (transposed)
+    double c[4] = {0.0, 0.0, 0.0, 0.0};
+    if (inv_live) {
+#pragma unroll
+      for (int kk = 0; kk < 16; ++kk) c[kk & 3] = fma(li[kk], zs[ka + kk], c[kk & 3]);
+    }
+    red[g * kSub + r] = (c[0] + c[1]) + (c[2] + c[3]);
     __syncthreads();
-    // right-hand sides of this block minus the accumulated products (fixed order)
-    for (int e = tid; e < kb * nrhs; e += kT) {
-      const int rr = e % kb, m = e / kb;
-      const T* pr = red + m * 4 * kSub + rr;
-      const T sum = ((pr[0] + pr[kSub]) + pr[2 * kSub]) + pr[3 * kSub];
-      yi[rr + m * kSub] -= sum;
-    }
-    __syncthreads();
-    // substitution: 16 lanes per right-hand side, lane q holds rows q + 16a;
-    // warps without a live right-hand side skip it, the others take part in the
-    // shuffles with all lanes and only live ones write
-    const int rr = tid >> 4, q = tid & 15;
-    const bool live = rr < nrhs;
-    if ((tid >> 5) * 2 < nrhs) {
-      T y[4];
-#pragma unroll
-      for (int a = 0; a < 4; ++a) {
-        const int i = q + 16 * a;
-        y[a] = (live && i < kb) ? yi[i + rr * kSub] : T(0);
-      }
-      if (!TRANS) {
-#pragma unroll
-        for (int ka = 0; ka < 4; ++ka)
-#pragma unroll
-          for (int kq = 0; kq < 16; ++kq) {
-            const int k = ka * 16 + kq;
-            if (k < kb) {
-              const T yk = __shfl_sync(0xffffffffu, y[ka] * inv[k], kq, 16);
-              if (q == kq) y[ka] = yk;
-#pragma unroll
-              for (int a = ka; a < 4; ++a) {   // rows of earlier slots are solved
-                const int i = q + 16 * a;
-                if (i > k && i < kb) y[a] -= Ls[i + k * 65] * yk;
-              }
-            }
-          }
-      } else {
-#pragma unroll
-        for (int ka = 3; ka >= 0; --ka)
-#pragma unroll
-          for (int kq = 15; kq >= 0; --kq) {
-            const int k = ka * 16 + kq;
-            if (k < kb) {
-              const T yk = __shfl_sync(0xffffffffu, y[ka] * inv[k], kq, 16);
-              if (q == kq) y[ka] = yk;
-#pragma unroll
-              for (int a = 0; a <= ka; ++a) {  // rows of later slots are solved
-                const int i = q + 16 * a;
-                if (i < k) y[a] -= Ls[k + i * 65] * yk;
-              }
-            }
-          }
-      }
-      if (live) {
-#pragma unroll
-        for (int a = 0; a < 4; ++a) {
-          const int i = q + 16 * a;
-          if (i < kb) Y[d.f + i0 + i + (int64_t)rr * n] = y[a];
-        }
-      }
-    }
+    if (tid < kb) Ym[i0 + tid] = ((red[tid] + red[kSub + tid]) + red[2 * kSub + tid]) + red[3 * kSub + tid];
     __syncthreads();   // every thread's rows of Y are written (CTA order) ...
     if (tid == 0) {
       __threadfence();  // ... and made visible at GPU scope before the flag
-      st_release(flags + item.fbase + blk, tgt);
+      st_release(fl + (int64_t)(item.fbase + blk) * kSolveChunk, tgt);
     }
   }
   // the last CTA to finish advances the epoch for the next launch
@@ -1041,32 +1042,35 @@ k_sv_tri32(const SnodeDev* __restrict__ sn, const TriItem* __restrict__ items, i
 // Resident CTAs per SM of each triangle kernel per chunk width (set once).
 int g_tri_per_sm[2][2][kSolveChunk + 1] = {};   // [binary32][transposed][nr]
 
-// One cooperative launch of the level's diagonal triangles: k_sv_tri
-// (binary64, substitution) or k_sv_tri32 (binary32, products with the blocks'
-// inverses).
+// One cooperative launch of the level's diagonal triangles: k_sv_tri64
+// (binary64, one right-hand-side column per item) or k_sv_tri32 (binary32, all
+// columns of the chunk per item); both multiply by the blocks' inverses.
 template <class T, bool RM, bool TRANS>
 int launch_tri(chol_handle* h, const LevelPlan& P, const T* L, T* Y, int nr, cudaStream_t st) {
   DeviceState* D = h->dev;
   constexpr bool f32 = sizeof(T) == 4;
   const int per_sm = g_tri_per_sm[f32][TRANS][nr];
   if (per_sm < 1) return CHOL_ENOTSUP;
-  const int grid = std::min(P.tri_n, per_sm * D->sms);
+  const int64_t work = f32 ? (int64_t)P.tri_n : (int64_t)P.tri_n * nr;
+  const int grid = (int)std::min<int64_t>(work, (int64_t)per_sm * D->sms);
   const TriItem* items = reinterpret_cast<const TriItem*>(D->tri) + P.tri_b;
   int nitems = P.tri_n, n = h->n;
-  const float* Dinv = reinterpret_cast<const float*>(D->dinv);
   long long max_polls = h->opt.wait_polls > 0 ? (long long)h->opt.wait_polls : kTriMaxPolls;
   int skew = h->opt.test_unreachable_flags ? 1 : 0;
   cudaError_t e;
   if constexpr (f32) {
+    const float* Dinv = reinterpret_cast<const float*>(D->dinv);
     void* args[] = {(void*)&D->sn, (void*)&items, (void*)&nitems, (void*)&L, (void*)&Dinv, (void*)&Y, (void*)&n,
                     (void*)&nr, (void*)&D->tri_flags, (void*)&D->tri_sync, (void*)&D->sv_err, (void*)&max_polls,
                     (void*)&skew};
     e = cudaLaunchCooperativeKernel((const void*)k_sv_tri32<TRANS>, dim3(grid), dim3(kT), args, tri32_smem(nr), st);
   } else {
-    void* args[] = {(void*)&D->sn, (void*)&items, (void*)&nitems, (void*)&L, (void*)&Y, (void*)&n, (void*)&nr,
-                    (void*)&D->tri_flags, (void*)&D->tri_sync, (void*)&D->sv_err, (void*)&max_polls, (void*)&skew};
-    e = cudaLaunchCooperativeKernel((const void*)k_sv_tri<T, RM, TRANS>, dim3(grid), dim3(kT), args, tri_smem<T>(nr),
-                                    st);
+    static_assert(f32 || !RM, "binary64 panels are column-major");
+    const double* Dinv = reinterpret_cast<const double*>(D->dinv);
+    void* args[] = {(void*)&D->sn, (void*)&items, (void*)&nitems, (void*)&L, (void*)&Dinv, (void*)&Y, (void*)&n,
+                    (void*)&nr, (void*)&D->tri_flags, (void*)&D->tri_sync, (void*)&D->sv_err, (void*)&max_polls,
+                    (void*)&skew};
+    e = cudaLaunchCooperativeKernel((const void*)k_sv_tri64<TRANS>, dim3(grid), dim3(kT), args, 0, st);
   }
   if (e != cudaSuccess) {
     cudaGetLastError();
@@ -1155,15 +1159,14 @@ int set_solve_attrs() {
   static std::once_flag once;
   static int rc = CHOL_OK;
   std::call_once(once, [] {
-    const size_t dd = tri_smem<double>(kSolveChunk), df = tri32_smem(kSolveChunk);
-    const void* kd[2] = {(const void*)k_sv_tri<double, false, false>, (const void*)k_sv_tri<double, false, true>};
+    const size_t df = tri32_smem(kSolveChunk);
+    const void* kd[2] = {(const void*)k_sv_tri64<false>, (const void*)k_sv_tri64<true>};
     const void* kf[2] = {(const void*)k_sv_tri32<false>, (const void*)k_sv_tri32<true>};
     cudaError_t e = cudaSuccess;
     for (int t = 0; t < 2; ++t) {
-      e = e ? e : cudaFuncSetAttribute(kd[t], cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dd);
       e = e ? e : cudaFuncSetAttribute(kf[t], cudaFuncAttributeMaxDynamicSharedMemorySize, (int)df);
       for (int nr = 1; nr <= kSolveChunk; ++nr) {
-        e = e ? e : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&g_tri_per_sm[0][t][nr], kd[t], kT, tri_smem<double>(nr));
+        e = e ? e : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&g_tri_per_sm[0][t][nr], kd[t], kT, 0);
         e = e ? e : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&g_tri_per_sm[1][t][nr], kf[t], kT, tri32_smem(nr));
       }
     }
@@ -1246,17 +1249,25 @@ int chol_solve_mixed(chol_handle* h, double* b, int32_t nrhs, cudaStream_t st) {
   return CHOL_OK;
 }
 
-// Inverses of the diagonal blocks the binary32 triangle solve multiplies by,
-// for the mixed-precision factor just enqueued on st (row-major panels).
+// Inverses of the diagonal blocks the triangle solves multiply by, for the
+// factor just enqueued on st: binary64 (column-major panels) the inverse alone,
+// binary32 (row-major panels) the inverse and the two last-dependency products.
 int chol_diag_inv(chol_handle* h, cudaStream_t st) {
   DeviceState* D = h->dev;
   const int nitems = (int)h->tri_items.size();
-  if (nitems == 0 || h->opt.precision == CHOL_PREC_FP64) return CHOL_OK;
+  if (nitems == 0) return CHOL_OK;
   const TriItem* items = reinterpret_cast<const TriItem*>(D->tri);
-  // per block: the inverse by substitution and up to two 64^3 products
-  KScope ks(h, CHOL_K_SOLVE_DIAG, st, (double)nitems * 5.0 * 64.0 * 64.0 * 64.0,
-            (double)nitems * 64.0 * 64.0 * 4.0 * 6.0);
-  k_diag_inv<<<nitems, kT, 0, st>>>(D->sn, items, (const float*)D->L, (float*)D->dinv);
+  if (h->opt.precision == CHOL_PREC_FP64) {
+    // per block: the inverse by substitution, about 64^3 / 3 flops
+    KScope ks(h, CHOL_K_SOLVE_DIAG, st, (double)nitems * 64.0 * 64.0 * 64.0 / 3.0,
+              (double)nitems * 64.0 * 64.0 * 8.0 * 1.5);
+    k_diag_inv64<<<nitems, kT, 0, st>>>(D->sn, items, (const double*)D->L, (double*)D->dinv);
+  } else {
+    // per block: the inverse by substitution and up to two 64^3 products
+    KScope ks(h, CHOL_K_SOLVE_DIAG, st, (double)nitems * 5.0 * 64.0 * 64.0 * 64.0,
+              (double)nitems * 64.0 * 64.0 * 4.0 * 6.0);
+    k_diag_inv<<<nitems, kT, 0, st>>>(D->sn, items, (const float*)D->L, (float*)D->dinv);
+  }
   CHOL_CUDA_TRY(cudaGetLastError());
   return CHOL_OK;
 }
