@@ -443,6 +443,7 @@ void build(chol_handle* h, const int64_t* colptr, const int32_t* rowind) {
   h->ssmall_list.clear();
   h->gemv_tasks.clear(); h->bpart_tasks.clear(); h->bred_tasks.clear();
   h->p_max = 0;
+  h->split_slots_max = 0;
   h->asm_tasks.clear(); h->asm_segs.clear();
   h->n_small = h->n_large = 0;
   h->update_doubles = 0;
@@ -627,13 +628,44 @@ void build(chol_handle* h, const int64_t* colptr, const int32_t* rowind) {
     const int32_t bpanel_cols = h->opt.precision == CHOL_PREC_FP64 ? 16 : 64;
     P.gemv_b = (int32_t)h->gemv_tasks.size();
     P.bpanel_b = (int32_t)h->bpanel_tasks.size();
+    // Binary64: a level with fewer tasks than kSplitTasks (the top of the tree:
+    // few supernodes with long panels) splits each task's sum (gemv: over the
+    // columns, bpanel: over the rows) into up to kMaxSplit parts of at least
+    // kSplitMin, so that its products spread over the GPU. Parts write partial
+    // sums to slots [slot, slot + parts) and the last part to finish adds them
+    // in part order. Task fields: k0 = part | parts << 16; gemv: c0 = slot;
+    // bpanel: r0 = slot.
+    int32_t gemv_groups = 0, bpanel_groups = 0;
     for (int32_t J : Js) {
       const SnodeDev& d = h->snodes[J];
       const int32_t b = d.len - d.s;
       if (b <= 0 || warp_solved(J)) continue;
-      for (int32_t r0 = 0; r0 < b; r0 += gemv_rows) h->gemv_tasks.push_back({J, 0, r0, 0});
-      for (int32_t c0 = 0; c0 < d.s; c0 += bpanel_cols) h->bpanel_tasks.push_back({J, 0, 0, c0});
+      gemv_groups += (b + gemv_rows - 1) / gemv_rows;
+      bpanel_groups += (d.s + bpanel_cols - 1) / bpanel_cols;
     }
+    const bool fp64 = h->opt.precision == CHOL_PREC_FP64;
+    auto level_split = [&](int32_t groups) {
+      if (!fp64 || groups <= 0 || groups >= kSplitTasks) return 1;
+      return std::min(kMaxSplit, (kSplitTasks + groups - 1) / groups);
+    };
+    const int32_t gemv_split = level_split(gemv_groups), bpanel_split = level_split(bpanel_groups);
+    int32_t gemv_slots = 0, bpanel_slots = 0;
+    for (int32_t J : Js) {
+      const SnodeDev& d = h->snodes[J];
+      const int32_t b = d.len - d.s;
+      if (b <= 0 || warp_solved(J)) continue;
+      const int32_t gs = std::max(1, std::min(gemv_split, d.s / kSplitMin));
+      for (int32_t r0 = 0; r0 < b; r0 += gemv_rows) {
+        for (int32_t q = 0; q < gs; ++q) h->gemv_tasks.push_back({J, q | (gs << 16), r0, gs > 1 ? gemv_slots : 0});
+        if (gs > 1) gemv_slots += gs;
+      }
+      const int32_t bs = std::max(1, std::min(bpanel_split, b / kSplitMin));
+      for (int32_t c0 = 0; c0 < d.s; c0 += bpanel_cols) {
+        for (int32_t q = 0; q < bs; ++q) h->bpanel_tasks.push_back({J, q | (bs << 16), bs > 1 ? bpanel_slots : 0, c0});
+        if (bs > 1) bpanel_slots += bs;
+      }
+    }
+    h->split_slots_max = std::max<int64_t>(h->split_slots_max, std::max(gemv_slots, bpanel_slots));
     P.gemv_n = (int32_t)h->gemv_tasks.size() - P.gemv_b;
     // row-major backward panel: 64-row chunks x 256-column tiles, then a reduction
     P.bpart_b = (int32_t)h->bpart_tasks.size();

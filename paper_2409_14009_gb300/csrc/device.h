@@ -42,6 +42,8 @@ struct DeviceState {
   int32_t* status = nullptr;    // device status word (first failing column + 1)
   int32_t* status_host = nullptr;  // pinned
   double* part = nullptr;       // logdet partial sums (one per supernode)
+  double* split_part = nullptr; // binary64 solve: partial sums of split panel products (split_slots_max x 64 x chunk)
+  int32_t* split_cnt = nullptr; // ... and one arrival counter per slot (zero between uses)
   double* scalar_host = nullptr;   // pinned
   double* scalar_dev = nullptr;
   // mixed modes

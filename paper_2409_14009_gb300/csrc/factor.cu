@@ -681,7 +681,7 @@ void chol_device_free(chol_handle* h) {
                   D->ssmall, D->Zp, D->Tw, D->Ww, D->Uh, D->a_col, D->a_row, D->adj_xb, D->perm, D->status, D->part, D->scalar_dev, D->Y, D->W,
                   D->mx_diagpos, D->mx_aij, D->mx_d, D->mx_fallbacks, D->csr_ptr, D->csr_col, D->csr_src,
                   D->csr_val, D->Lbf, D->tmaps, D->tc_err, D->R, D->Z, D->Pv, D->Q, D->red, D->Y32, D->W32,
-                  D->rhs_scale, D->host_vals, D->host_rhs, D->panel, D->pflags, D->dinv};
+                  D->rhs_scale, D->host_vals, D->host_rhs, D->panel, D->pflags, D->dinv, D->split_part, D->split_cnt};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   if (D->status_host) cudaFreeHost(D->status_host);
@@ -763,9 +763,14 @@ int chol_device_ensure(chol_handle* h) {
   // one flag per diagonal block and right-hand-side column of a chunk
   const size_t nflags = (size_t)std::max(h->tri_nflags, 1) * kSolveChunk;
   if ((rc = chol_dalloc(h, (void**)&D->tri_flags, sizeof(int32_t) * nflags))) return fail(rc);
-  if (h->opt.precision == CHOL_PREC_FP64 &&
-      (rc = chol_dalloc(h, &D->dinv, sizeof(double) * 64 * 64 * (size_t)std::max(h->tri_nflags, 1))))
-    return fail(rc);
+  if (h->opt.precision == CHOL_PREC_FP64) {
+    if ((rc = chol_dalloc(h, &D->dinv, sizeof(double) * 64 * 64 * (size_t)std::max(h->tri_nflags, 1))))
+      return fail(rc);
+    const size_t slots = (size_t)std::max<int64_t>(h->split_slots_max, 1);
+    if ((rc = chol_dalloc(h, (void**)&D->split_part, sizeof(double) * 64 * kSolveChunk * slots))) return fail(rc);
+    if ((rc = chol_dalloc(h, (void**)&D->split_cnt, sizeof(int32_t) * slots))) return fail(rc);
+    if (cudaMemset(D->split_cnt, 0, sizeof(int32_t) * slots) != cudaSuccess) return fail(CHOL_ECUDA);
+  }
   if ((rc = chol_dalloc(h, (void**)&D->tri_sync, sizeof(int32_t) * 2))) return fail(rc);
   if ((rc = chol_dalloc(h, (void**)&D->sv_err, sizeof(int32_t)))) return fail(rc);
   if (cudaMemset(D->tri_flags, 0, sizeof(int32_t) * nflags) != cudaSuccess ||

@@ -170,6 +170,7 @@ struct chol_handle {
   std::vector<TileTask> gemv_tasks;             // solve: (J, r0) off-diagonal row tiles
   std::vector<TileTask> bpart_tasks, bred_tasks; // solve: row-major backward panel stages
   int64_t p_max = 0;                            // largest per-level partial-sum rows
+  int64_t split_slots_max = 0;                  // binary64 solve: largest per-level count of split-sum slots
   std::vector<PanelItem> panel_items;           // mixed modes: panel-launch tiles, step by step
   int32_t panel_nflags = 0, panel_ntickets = 0; // progress flags and work counters of all panel launches
   std::vector<AsmTask> asm_tasks;
@@ -199,6 +200,9 @@ constexpr int kAsmWarpEntries = 4096;  // ... and this many entries over all seg
 constexpr int kTrsmRowsHost = 32; // TRSM task height (rows; binary64 tasks take half)
 constexpr int kSolveSmallCols = 32;   // supernodes solved by one warp: s <= 32 and
 constexpr int kSolveSmallRows = 256;  // len <= 256
+constexpr int kSplitTasks = 608;      // binary64 solve panel products: split levels with fewer tasks (4 x 152 SMs)
+constexpr int kMaxSplit = 16;         // ... into at most this many parts
+constexpr int kSplitMin = 128;        // ... of at least this many columns (gemv) or rows (bpanel)
 constexpr int kRlbSmallRows = 1024;   // RLB: rows of a supernode on the one-CTA kernel (small_max_rows cap)
 
 void chol_device_free(chol_handle* h);  // CUDA side

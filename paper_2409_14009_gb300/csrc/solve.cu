@@ -315,7 +315,8 @@ k_sv_tri64(const SnodeDev* __restrict__ sn, const TriItem* __restrict__ items, i
 template <class T, bool RM>
 __global__ void __launch_bounds__(kT)
 k_sv_gemv(const SnodeDev* __restrict__ sn, const TileTask* __restrict__ tasks, const T* __restrict__ L,
-          const T* __restrict__ Y, int n, T* __restrict__ W, int nrhs) {
+          const T* __restrict__ Y, int n, T* __restrict__ W, int nrhs, T* __restrict__ spart,
+          int* __restrict__ scnt) {
   constexpr int KC = 256;
   __shared__ __align__(16) T yk[KC * kSolveChunk];
   const TileTask t = tasks[blockIdx.x];
@@ -334,8 +335,16 @@ k_sv_gemv(const SnodeDev* __restrict__ sn, const TileTask* __restrict__ tasks, c
     for (int h = 0; h < 2; ++h)
 #pragma unroll
       for (int r = 0; r < kSolveChunk; ++r) acc[h][r] = T(0);
-    for (int kc = 0; kc < d.s; kc += KC) {
-      const int kn = min(KC, d.s - kc);
+    // part `split` of `nsplit` sums over the columns [kbeg, kend) only
+    const int split = t.k0 & 0xffff, nsplit = t.k0 >> 16;
+    int kbeg = 0, kend = d.s;
+    if (nsplit > 1) {
+      const int ch = (d.s + nsplit - 1) / nsplit;
+      kbeg = min(d.s, split * ch);
+      kend = min(d.s, kbeg + ch);
+    }
+    for (int kc = kbeg; kc < kend; kc += KC) {
+      const int kn = min(KC, kend - kc);
       __syncthreads();
       for (int q = threadIdx.x; q < kn * nrhs; q += blockDim.x) {
         const int i = q % kn, r = q / kn;
@@ -388,7 +397,33 @@ k_sv_gemv(const SnodeDev* __restrict__ sn, const TileTask* __restrict__ tasks, c
         T v = T(0);
 #pragma unroll
         for (int w = 0; w < NW; ++w) v += red[(w * 64 + row) * 4 + q];
-        Wj[u + (int64_t)(r0 + q) * b] = v;
+        if (nsplit > 1) spart[((int64_t)(t.c0 + split) * kSolveChunk + r0 + q) * 64 + row] = v;
+        else Wj[u + (int64_t)(r0 + q) * b] = v;
+      }
+    }
+    if (nsplit > 1) {
+      // the last part of the group to finish adds the parts' sums in part order
+      __shared__ int last;
+      __syncthreads();
+      if (threadIdx.x == 0) {
+        __threadfence();
+        last = atomicAdd(scnt + t.c0, 1) == nsplit - 1;
+        if (last) {
+          __threadfence();
+          scnt[t.c0] = 0;   // reset for the next level or solve
+        }
+      }
+      __syncthreads();
+      if (last) {
+        for (int e = threadIdx.x; e < 64 * nrhs; e += blockDim.x) {
+          const int row = e & 63, r = e >> 6;
+          const int u = t.r0 + row;
+          if (u >= b) continue;
+          const T* src = spart + ((int64_t)t.c0 * kSolveChunk + r) * 64 + row;
+          T v = __ldcg(src);
+          for (int q = 1; q < nsplit; ++q) v += __ldcg(src + (int64_t)q * kSolveChunk * 64);
+          Wj[u + (int64_t)r * b] = v;
+        }
       }
     }
   } else {
@@ -494,7 +529,8 @@ k_sv_fasm(const AsmTask* __restrict__ tasks, int ntasks, const AsmSeg* __restric
 template <class T, bool RM>
 __global__ void __launch_bounds__(kT)
 k_sv_bpanel(const SnodeDev* __restrict__ sn, const TileTask* __restrict__ tasks, const int32_t* __restrict__ rows,
-            const T* __restrict__ L, T* __restrict__ Y, int n, int nrhs) {
+            const T* __restrict__ L, T* __restrict__ Y, int n, int nrhs, T* __restrict__ spart,
+            int* __restrict__ scnt) {
   const TileTask t = tasks[blockIdx.x];
   const SnodeDev d = sn[t.J];
   const int b = d.len - d.s;
@@ -513,8 +549,16 @@ k_sv_bpanel(const SnodeDev* __restrict__ sn, const TileTask* __restrict__ tasks,
     for (int h = 0; h < 2; ++h)
 #pragma unroll
       for (int r = 0; r < kSolveChunk; ++r) acc[h][r] = T(0);
-    for (int ub = 0; ub < b; ub += CH) {
-      const int un = min(CH, b - ub);
+    // part `split` of `nsplit` sums over the rows [ubeg, uend) only
+    const int split = t.k0 & 0xffff, nsplit = t.k0 >> 16;
+    int ubeg = 0, uend = b;
+    if (nsplit > 1) {
+      const int ch = (b + nsplit - 1) / nsplit;
+      ubeg = min(b, split * ch);
+      uend = min(b, ubeg + ch);
+    }
+    for (int ub = ubeg; ub < uend; ub += CH) {
+      const int un = min(CH, uend - ub);
       __syncthreads();
       for (int q = threadIdx.x; q < un * nrhs; q += blockDim.x) {
         const int i = q % un, r = q / un;
@@ -551,8 +595,42 @@ k_sv_bpanel(const SnodeDev* __restrict__ sn, const TileTask* __restrict__ tasks,
         v0 += __shfl_xor_sync(0xffffffffu, v0, o);
         v1 += __shfl_xor_sync(0xffffffffu, v1, o);
       }
-      if (lane == 0 && in0) Y[d.f + c0 + (int64_t)r * n] -= v0;
-      if (lane == 0 && in1) Y[d.f + c0 + 1 + (int64_t)r * n] -= v1;
+      if (nsplit > 1) {
+        // slot: 16 columns x kSolveChunk right-hand sides
+        if (lane == 0) {
+          T* dst = spart + ((int64_t)(t.r0 + split) * kSolveChunk + r) * 16 + 2 * warp;
+          dst[0] = v0;
+          dst[1] = v1;
+        }
+      } else {
+        if (lane == 0 && in0) Y[d.f + c0 + (int64_t)r * n] -= v0;
+        if (lane == 0 && in1) Y[d.f + c0 + 1 + (int64_t)r * n] -= v1;
+      }
+    }
+    if (nsplit > 1) {
+      // the last part of the group to finish subtracts the parts' sums, added in part order
+      __shared__ int last;
+      __syncthreads();
+      if (threadIdx.x == 0) {
+        __threadfence();
+        last = atomicAdd(scnt + t.r0, 1) == nsplit - 1;
+        if (last) {
+          __threadfence();
+          scnt[t.r0] = 0;   // reset for the next level or solve
+        }
+      }
+      __syncthreads();
+      if (last) {
+        for (int e = threadIdx.x; e < 16 * nrhs; e += blockDim.x) {
+          const int col = e & 15, r = e >> 4;
+          const int c = t.c0 + col;
+          if (c >= d.s) continue;
+          const T* src = spart + ((int64_t)t.r0 * kSolveChunk + r) * 16 + col;
+          T v = __ldcg(src);
+          for (int q = 1; q < nsplit; ++q) v += __ldcg(src + (int64_t)q * kSolveChunk * 16);
+          Y[d.f + c + (int64_t)r * n] -= v;
+        }
+      }
     }
   } else {
     __shared__ T part[4][64][kSolveChunk + 1];
@@ -1106,7 +1184,8 @@ int solve_levels(chol_handle* h, const T* L, T* Y, T* W, T* part, int nr, cudaSt
     }
     if (P.gemv_n > 0) {
       KScope* ks = scope(CHOL_K_SOLVE_GEMV);
-      k_sv_gemv<T, RM><<<P.gemv_n, kT, 0, st>>>(D->sn, D->gemv + P.gemv_b, L, Y, n, W, nr);
+      k_sv_gemv<T, RM><<<P.gemv_n, kT, 0, st>>>(D->sn, D->gemv + P.gemv_b, L, Y, n, W, nr, (T*)D->split_part,
+                                                D->split_cnt);
       delete ks;
     }
     if (P.asm_n + P.asmw_n > 0) {
@@ -1131,7 +1210,8 @@ int solve_levels(chol_handle* h, const T* L, T* Y, T* W, T* part, int nr, cudaSt
       }
     } else if (P.bpanel_n > 0) {
       KScope* ks = scope(CHOL_K_SOLVE_BPANEL);
-      k_sv_bpanel<T, RM><<<P.bpanel_n, kT, 0, st>>>(D->sn, D->bpanel + P.bpanel_b, D->rows, L, Y, n, nr);
+      k_sv_bpanel<T, RM><<<P.bpanel_n, kT, 0, st>>>(D->sn, D->bpanel + P.bpanel_b, D->rows, L, Y, n, nr,
+                                                    (T*)D->split_part, D->split_cnt);
       delete ks;
     }
     if (P.ssmall_n > 0) {
