@@ -73,6 +73,7 @@ struct DeviceState {
   float* Y32 = nullptr;            // binary32 solve workspaces
   float* W32 = nullptr;
   float* P32 = nullptr;             // row-major backward-panel partials
+  unsigned long long* hand32 = nullptr;   // binary32 triangle solve: tagged hand-off words, n x chunk
   double* rhs_scale = nullptr;
   // batches, persistent launches and graphs
   PersistLevel* plevels = nullptr;

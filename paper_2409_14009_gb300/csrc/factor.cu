@@ -681,7 +681,7 @@ void chol_device_free(chol_handle* h) {
                   D->ssmall, D->Zp, D->Tw, D->Ww, D->Uh, D->a_col, D->a_row, D->adj_xb, D->perm, D->status, D->part, D->scalar_dev, D->Y, D->W,
                   D->mx_diagpos, D->mx_aij, D->mx_d, D->mx_fallbacks, D->csr_ptr, D->csr_col, D->csr_src,
                   D->csr_val, D->Lbf, D->tmaps, D->tc_err, D->R, D->Z, D->Pv, D->Q, D->red, D->Y32, D->W32,
-                  D->rhs_scale, D->host_vals, D->host_rhs, D->panel, D->pflags, D->dinv, D->split_part, D->split_cnt};
+                  D->rhs_scale, D->host_vals, D->host_rhs, D->panel, D->pflags, D->dinv, D->split_part, D->split_cnt, D->hand32};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   if (D->status_host) cudaFreeHost(D->status_host);

@@ -21,6 +21,7 @@
 // Every output entry is written by exactly one thread per launch and every
 // reduction runs in a fixed order, so the solve is deterministic.
 #include <mutex>
+#include <type_traits>
 
 #include "device.h"
 #include "mixed.h"
@@ -193,9 +194,12 @@ k_sv_tri64(const SnodeDev* __restrict__ sn, const TriItem* __restrict__ items, i
   __shared__ double ys[kSub];         // a solved block's column
   __shared__ double zs[kSub];         // this block's right-hand side, then z
   __shared__ double red[4 * kSub];    // k-group partial sums
-  __shared__ int target;
+  __shared__ int target, savail;
   const int tid = threadIdx.x, r = tid & 63, g = tid >> 6, ka = 16 * g;
-  if (tid == 0) target = ld_acquire(sync) + 1;
+  if (tid == 0) {
+    target = ld_acquire(sync) + 1;
+    savail = -1;
+  }
   __syncthreads();
   const int tgt = target;
   const int wait_tgt = tgt + skew;   // skew != 0 only to test the failure path
@@ -250,15 +254,26 @@ k_sv_tri64(const SnodeDev* __restrict__ sn, const TriItem* __restrict__ items, i
       for (int kk = 0; kk < 16; ++kk) lt[kk] = (r < kb && ka + kk < jlb) ? lrow(jl0, ka + kk) : 0.0;
     }
     // the dependencies other than the last, straight from the panel
+    // (blocks are published in dependency order, so once the flag of the last
+    // of them is seen no further flag is read)
     double a[4] = {0.0, 0.0, 0.0, 0.0};
-    for (int q = 0; q + 1 < item.i; ++q) {
+    const int ndep = item.i - 1;
+    int avail = -1;   // dependencies 0 .. avail are known to be published
+    for (int q = 0; q < ndep; ++q) {
       const int j = TRANS ? item.nb - 1 - q : q;
       const int j0 = j * kSub, jb = min(kSub, d.s - j0);
       double lv[16];
 #pragma unroll
       for (int kk = 0; kk < 16; ++kk) lv[kk] = (r < kb && ka + kk < jb) ? lrow(j0, ka + kk) : 0.0;
-      wait_flag(fl + (int64_t)(item.fbase + j) * kSolveChunk);
-      __syncthreads();   // also: the previous tile is done with ys
+      if (q > avail) {
+        wait_flag(fl + (int64_t)(item.fbase + j) * kSolveChunk);
+        if (tid == 0) {
+          const int jl = TRANS ? item.nb - ndep : ndep - 1;   // the last of them
+          savail = ld_acquire(fl + (int64_t)(item.fbase + jl) * kSolveChunk) == wait_tgt ? ndep - 1 : q;
+        }
+      }
+      __syncthreads();   // the flag (and savail) seen; the previous tile is done with ys
+      avail = savail;
       if (tid < kSub) ys[tid] = tid < jb ? __ldcg(Ym + j0 + tid) : 0.0;
       __syncthreads();
 #pragma unroll
@@ -285,11 +300,11 @@ k_sv_tri64(const SnodeDev* __restrict__ sn, const TriItem* __restrict__ items, i
     red[g * kSub + r] = (c[0] + c[1]) + (c[2] + c[3]);
     __syncthreads();
     if (tid < kb) Ym[i0 + tid] = ((red[tid] + red[kSub + tid]) + red[2 * kSub + tid]) + red[3 * kSub + tid];
-    __syncthreads();   // every thread's rows of Y are written (CTA order) ...
-    if (tid == 0) {
-      __threadfence();  // ... and made visible at GPU scope before the flag
-      st_release(fl + (int64_t)(item.fbase + blk) * kSolveChunk, tgt);
-    }
+    // the barrier orders every thread's stores of Y before thread 0's release
+    // store (gpu scope, cumulative), so a consumer whose acquire load sees the
+    // flag sees the rows
+    __syncthreads();
+    if (tid == 0) st_release(fl + (int64_t)(item.fbase + blk) * kSolveChunk, tgt);
   }
   // the last CTA to finish advances the epoch for the next launch
   __syncthreads();
@@ -312,13 +327,14 @@ k_sv_tri64(const SnodeDev* __restrict__ sn, const TriItem* __restrict__ items, i
 // sums are then combined in warp order through shared memory.
 // Row-major (binary32): 32 rows, a warp per 4 rows, lanes along K,
 // fixed-order shuffle reduction.
-template <class T, bool RM>
+template <class T, bool RM, int NR>
 __global__ void __launch_bounds__(kT)
 k_sv_gemv(const SnodeDev* __restrict__ sn, const TileTask* __restrict__ tasks, const T* __restrict__ L,
           const T* __restrict__ Y, int n, T* __restrict__ W, int nrhs, T* __restrict__ spart,
           int* __restrict__ scnt) {
   constexpr int KC = 256;
-  __shared__ __align__(16) T yk[KC * kSolveChunk];
+  constexpr int kYk = KC * NR > 2048 ? KC * NR : 2048;   // also the binary64 warp partials (8 x 64 x 4)
+  __shared__ __align__(16) T yk[kYk];
   const TileTask t = tasks[blockIdx.x];
   const SnodeDev d = sn[t.J];
   const int b = d.len - d.s;
@@ -330,11 +346,11 @@ k_sv_gemv(const SnodeDev* __restrict__ sn, const TileTask* __restrict__ tasks, c
     const int u0 = t.r0 + lane, u1 = u0 + 32;
     const bool in0 = u0 < b, in1 = u1 < b;
     const T* col0 = P + d.s + u0;   // L(s + u0, k) = col0[k * ld]
-    T acc[2][kSolveChunk];
+    T acc[2][NR];
 #pragma unroll
     for (int h = 0; h < 2; ++h)
 #pragma unroll
-      for (int r = 0; r < kSolveChunk; ++r) acc[h][r] = T(0);
+      for (int r = 0; r < NR; ++r) acc[h][r] = T(0);
     // part `split` of `nsplit` sums over the columns [kbeg, kend) only
     const int split = t.k0 & 0xffff, nsplit = t.k0 >> 16;
     int kbeg = 0, kend = d.s;
@@ -366,7 +382,7 @@ k_sv_gemv(const SnodeDev* __restrict__ sn, const TileTask* __restrict__ tasks, c
         for (int j = 0; j < 4; ++j) {
           const int k = min(k4 + j * NW, KC - 1);   // l = 0 past kn
 #pragma unroll
-          for (int r = 0; r < kSolveChunk; ++r) {
+          for (int r = 0; r < NR; ++r) {
             if (r >= nrhs) break;
             const T y = yk[k + r * KC];
             acc[0][r] += l[j][0] * y;
@@ -384,7 +400,7 @@ k_sv_gemv(const SnodeDev* __restrict__ sn, const TileTask* __restrict__ tasks, c
         if (r0 + q >= nrhs) break;
         T v0 = T(0), v1 = T(0);
 #pragma unroll
-        for (int r = 0; r < kSolveChunk; ++r)
+        for (int r = 0; r < NR; ++r)
           if (r == r0 + q) { v0 = acc[0][r]; v1 = acc[1][r]; }
         red[(warp * 64 + lane) * 4 + q] = v0;
         red[(warp * 64 + lane + 32) * 4 + q] = v1;
@@ -432,11 +448,11 @@ k_sv_gemv(const SnodeDev* __restrict__ sn, const TileTask* __restrict__ tasks, c
     // passes per staged chunk: 8 loads of 16 bytes in flight per lane
     static_assert(sizeof(T) == 4, "row-major panels are binary32");
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    T acc[4][kSolveChunk];   // 4 rows per warp, 32 rows per task
+    T acc[4][NR];   // 4 rows per warp, 32 rows per task
 #pragma unroll
     for (int m = 0; m < 4; ++m)
 #pragma unroll
-      for (int r = 0; r < kSolveChunk; ++r) acc[m][r] = T(0);
+      for (int r = 0; r < NR; ++r) acc[m][r] = T(0);
     for (int kc = 0; kc < d.s; kc += KC) {
       const int kn = min(KC, d.s - kc);
       __syncthreads();
@@ -469,7 +485,7 @@ k_sv_gemv(const SnodeDev* __restrict__ sn, const TileTask* __restrict__ tasks, c
       for (int h = 0; h < 2; ++h) {
         const int k = 4 * lane + 128 * h;
 #pragma unroll
-        for (int r = 0; r < kSolveChunk; ++r) {
+        for (int r = 0; r < NR; ++r) {
           if (r >= nrhs) break;
           const float4 y4 = *reinterpret_cast<const float4*>(reinterpret_cast<const float*>(yk) + k + r * KC);
 #pragma unroll
@@ -482,7 +498,7 @@ k_sv_gemv(const SnodeDev* __restrict__ sn, const TileTask* __restrict__ tasks, c
     for (int m = 0; m < 4; ++m) {
       const int u = t.r0 + warp * 4 + m;
 #pragma unroll
-      for (int r = 0; r < kSolveChunk; ++r) {
+      for (int r = 0; r < NR; ++r) {
         T v = acc[m][r];
         for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
         if (lane == 0 && u < b && r < nrhs) Wj[u + (int64_t)r * b] = v;
@@ -526,7 +542,7 @@ k_sv_fasm(const AsmTask* __restrict__ tasks, int ntasks, const AsmSeg* __restric
 // at a time (8 independent loads in flight, each warp load a contiguous 256
 // bytes), then a fixed shuffle tree sums the lanes. Row-major: 64 columns per
 // task, a thread per (column, row group of 4), fixed-order combination.
-template <class T, bool RM>
+template <class T, bool RM, int NR>
 __global__ void __launch_bounds__(kT)
 k_sv_bpanel(const SnodeDev* __restrict__ sn, const TileTask* __restrict__ tasks, const int32_t* __restrict__ rows,
             const T* __restrict__ L, T* __restrict__ Y, int n, int nrhs, T* __restrict__ spart,
@@ -538,17 +554,17 @@ k_sv_bpanel(const SnodeDev* __restrict__ sn, const TileTask* __restrict__ tasks,
   const T* P = L + d.loff;
   if constexpr (!RM) {
     constexpr int CH = 256;
-    __shared__ T xs[CH * kSolveChunk];
+    __shared__ T xs[CH * NR];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int c0 = t.c0 + 2 * warp;
     const bool in0 = c0 < d.s, in1 = c0 + 1 < d.s;
     const T* colA = P + d.s + (int64_t)c0 * d.ld;   // L(s + u, c0) = colA[u]
     const T* colB = colA + d.ld;
-    T acc[2][kSolveChunk];
+    T acc[2][NR];
 #pragma unroll
     for (int h = 0; h < 2; ++h)
 #pragma unroll
-      for (int r = 0; r < kSolveChunk; ++r) acc[h][r] = T(0);
+      for (int r = 0; r < NR; ++r) acc[h][r] = T(0);
     // part `split` of `nsplit` sums over the rows [ubeg, uend) only
     const int split = t.k0 & 0xffff, nsplit = t.k0 >> 16;
     int ubeg = 0, uend = b;
@@ -578,7 +594,7 @@ k_sv_bpanel(const SnodeDev* __restrict__ sn, const TileTask* __restrict__ tasks,
           const int i = i4 + 32 * j;
           if (i >= un) break;
 #pragma unroll
-          for (int r = 0; r < kSolveChunk; ++r) {
+          for (int r = 0; r < NR; ++r) {
             if (r >= nrhs) break;
             const T x = xs[i + r * CH];
             acc[0][r] += l[j][0] * x;
@@ -588,7 +604,7 @@ k_sv_bpanel(const SnodeDev* __restrict__ sn, const TileTask* __restrict__ tasks,
       }
     }
 #pragma unroll
-    for (int r = 0; r < kSolveChunk; ++r) {
+    for (int r = 0; r < NR; ++r) {
       if (r >= nrhs) break;
       T v0 = acc[0][r], v1 = acc[1][r];
       for (int o = 16; o > 0; o >>= 1) {
@@ -633,23 +649,23 @@ k_sv_bpanel(const SnodeDev* __restrict__ sn, const TileTask* __restrict__ tasks,
       }
     }
   } else {
-    __shared__ T part[4][64][kSolveChunk + 1];
+    __shared__ T part[4][64][NR + 1];
     const int col = threadIdx.x & 63, rg = threadIdx.x >> 6;
     const int c = t.c0 + col;
-    T acc[kSolveChunk];
+    T acc[NR];
 #pragma unroll
-    for (int r = 0; r < kSolveChunk; ++r) acc[r] = T(0);
+    for (int r = 0; r < NR; ++r) acc[r] = T(0);
     if (c < d.s) {
       for (int u = rg; u < b; u += 4) {
         const T l = lval<T, RM>(P, d, d.s + u, c);
         const int32_t g = rj[u];
 #pragma unroll
-        for (int r = 0; r < kSolveChunk; ++r)
+        for (int r = 0; r < NR; ++r)
           if (r < nrhs) acc[r] += l * Y[g + (int64_t)r * n];
       }
     }
 #pragma unroll
-    for (int r = 0; r < kSolveChunk; ++r) part[rg][col][r] = acc[r];
+    for (int r = 0; r < NR; ++r) part[rg][col][r] = acc[r];
     __syncthreads();
     if (rg == 0 && c < d.s) {
       for (int r = 0; r < nrhs; ++r) {
@@ -664,12 +680,12 @@ k_sv_bpanel(const SnodeDev* __restrict__ sn, const TileTask* __restrict__ tasks,
 // chunk u0, 256-column tile c0) writes part[chunk][c] = sum over its rows of
 // L(s+u, c) x[rows[s+u]] (rows walked contiguously, coalesced). Stage 2: for
 // each column, the chunk partials are summed in chunk order and subtracted.
-template <class T>
+template <class T, int NR>
 __global__ void __launch_bounds__(kT)
 k_sv_bpart(const SnodeDev* __restrict__ sn, const TileTask* __restrict__ tasks, const int32_t* __restrict__ rows,
            const T* __restrict__ L, const T* __restrict__ Y, int n, T* __restrict__ part, int64_t pstride,
            int nrhs) {
-  __shared__ T xs[kSub * kSolveChunk];
+  __shared__ T xs[kSub * NR];
   const TileTask t = tasks[blockIdx.x];
   const SnodeDev d = sn[t.J];
   const int b = d.len - d.s;
@@ -684,18 +700,19 @@ k_sv_bpart(const SnodeDev* __restrict__ sn, const TileTask* __restrict__ tasks, 
   const int c = t.c0 + threadIdx.x;
   if (c >= d.s) return;
   const T* P = L + d.loff + (int64_t)(d.s + u0) * d.ld + c;
-  T acc[kSolveChunk];
+  T acc[NR];
 #pragma unroll
-  for (int r = 0; r < kSolveChunk; ++r) acc[r] = T(0);
+  for (int r = 0; r < NR; ++r) acc[r] = T(0);
+#pragma unroll 8
   for (int u = 0; u < nr64; ++u) {
     const T l = P[(int64_t)u * d.ld];
 #pragma unroll
-    for (int r = 0; r < kSolveChunk; ++r)
+    for (int r = 0; r < NR; ++r)
       if (r < nrhs) acc[r] += l * xs[u + r * kSub];
   }
   T* out = part + d.ppre + (int64_t)chunk * d.s + c;
 #pragma unroll
-  for (int r = 0; r < kSolveChunk; ++r)
+  for (int r = 0; r < NR; ++r)
     if (r < nrhs) out[r * pstride] = acc[r];
 }
 
@@ -935,19 +952,35 @@ size_t tri32_smem(int nr) {
   return sizeof(float) * ((size_t)6 * kSub * nr + 2 * kSub * 65);
 }
 
-// Binary32 diagonal triangles of a level (row-major panels). Same items,
-// flags, epochs and bounded waits as k_sv_tri. For block i with last
-// dependency l (forward l = i - 1; transposed l = i + 1):
+// Binary32 diagonal triangles of a level (row-major panels). Same items, epochs
+// and bounded waits as k_sv_tri64, but a solved block is handed over through
+// tagged words instead of flags: besides its rows of Y, a block stores each
+// entry as one 64-bit word {binary32 bits, launch tag} (hand, indexed like Y),
+// and a consumer spins on the words it needs until they carry this launch's
+// tag. A 64-bit aligned access is single-copy atomic, so a word with the right
+// tag holds the right value: no flag, fence or barrier sits between a block's
+// result and its consumers, and the hand-off costs one memory round trip.
+// For block i with last dependency l (forward l = i - 1; transposed l = i + 1):
 //   pre = L_ii^{-1} (b_i - sum over the other dependencies j of L(i, j) y_j)
 // is formed before the last wait (forward; the transposed solve uses
 // L_ii^{-T} and L(j, i)^T), then y_i = pre - M y_l with M = Mf or Mb. Thread
 // (r, g) owns row r and the k range [16 g, 16 g + 16) of every product; the
 // four partial sums are added in group order, so the solve is deterministic.
+__device__ __forceinline__ unsigned long long ld_relaxed_u64(const unsigned long long* p) {
+  unsigned long long v;
+  asm volatile("ld.relaxed.gpu.global.b64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
+  return v;
+}
+
+__device__ __forceinline__ void st_relaxed_u64(unsigned long long* p, unsigned long long v) {
+  asm volatile("st.relaxed.gpu.global.b64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
+}
+
 template <bool TRANS>
 __global__ void __launch_bounds__(kT)
 k_sv_tri32(const SnodeDev* __restrict__ sn, const TriItem* __restrict__ items, int nitems, const float* __restrict__ L,
-           const float* __restrict__ Dinv, float* __restrict__ Y, int n, int nrhs, int* __restrict__ flags,
-           int* __restrict__ sync, int* __restrict__ err, long long max_polls, int skew) {
+           const float* __restrict__ Dinv, float* __restrict__ Y, unsigned long long* __restrict__ hand, int n,
+           int nrhs, int* __restrict__ sync, int* __restrict__ err, long long max_polls, int skew) {
   extern __shared__ __align__(16) unsigned char sv_smem[];
   float* ys = reinterpret_cast<float*>(sv_smem);   // a solved block j, 64 x nrhs
   float* yi = ys + kSub * nrhs;                     // this block's right-hand sides, then pre
@@ -958,24 +991,37 @@ k_sv_tri32(const SnodeDev* __restrict__ sn, const TriItem* __restrict__ items, i
   if (threadIdx.x == 0) target = ld_acquire(sync) + 1;
   __syncthreads();
   const int tgt = target;
-  const int wait_tgt = tgt + skew;          // skew != 0 only to test the failure path
+  const unsigned wait_tag = (unsigned)(tgt + skew);   // skew != 0 only to test the failure path
+  const unsigned long long tag_hi = (unsigned long long)(unsigned)tgt << 32;
   const int tid = threadIdx.x, r = tid & 63, g = tid >> 6, ka = 16 * g;
-  auto wait_flag = [&](int j) {
-    if (tid == 0) {
-      long long polls = 0;
-      while (ld_acquire(flags + j) != wait_tgt) {
-        if (++polls > max_polls) { atomicExch(err, 1); break; }
-        if (polls > 4096) __nanosleep(100);   // spin first: the hand-off is on the critical path
+  // ys = the solved rows [j0, j0 + jb) of the supernode starting at column f
+  // (zero past jb), each read from its tagged word once the tag is this
+  // launch's (bounded: a wait that gives up sets *err and takes the value)
+  auto stage_solved = [&](int64_t f, int j0, int jb) {
+    for (int e = tid; e < kSub * nrhs; e += kT) {
+      const int k = e & (kSub - 1), m = e / kSub;
+      float v = 0.f;
+      if (k < jb) {
+        const unsigned long long* p = hand + f + j0 + k + (int64_t)m * n;
+        unsigned long long w = ld_relaxed_u64(p);
+        long long polls = 0;
+        while ((unsigned)(w >> 32) != wait_tag) {
+          if (++polls > max_polls) { atomicExch(err, 1); break; }
+          if ((polls & 255) == 0 && *(volatile int*)err != 0) break;   // another wait gave up: stop
+          if (polls > 4096) __nanosleep(100);   // spin first: the hand-off is on the critical path
+          w = ld_relaxed_u64(p);
+        }
+        v = __uint_as_float((unsigned)w);
       }
+      ys[k + m * kSub] = v;
     }
   };
-  // partial sums of acc into red, then out[rr] = base[rr] - (sum in group order)
-  auto reduce = [&](const float (&acc)[kSolveChunk], int kb) {
+  // partial sums of acc into red (the caller then combines them)
+  auto reduce = [&](const float (&acc)[kSolveChunk]) {
 #pragma unroll
     for (int m = 0; m < kSolveChunk; ++m)
       if (m < nrhs) red[(g * kSub + r) + m * 4 * kSub] = acc[m];
     __syncthreads();
-    (void)kb;
   };
   for (int it = blockIdx.x; it < nitems; it += gridDim.x) {
     const TriItem item = items[it];
@@ -997,36 +1043,42 @@ k_sv_tri32(const SnodeDev* __restrict__ sn, const TriItem* __restrict__ items, i
     float acc[kSolveChunk];
 #pragma unroll
     for (int m = 0; m < kSolveChunk; ++m) acc[m] = 0.f;
-    // the dependencies other than the last, from the panel
-    for (int q = 0; q + 1 < item.i; ++q) {
+    // the dependencies other than the last, from the panel; the next tile's
+    // entries are loaded while the current one is multiplied
+    const int ndep = item.i - 1;
+    auto load_tile = [&](int q, float (&dst)[16]) {
       const int j = TRANS ? item.nb - 1 - q : q;
       const int j0 = j * kSub, jb = min(kSub, d.s - j0);
-      wait_flag(item.fbase + j);
-      __syncthreads();   // also: the previous block is done with ys
-      for (int e = tid; e < jb * nrhs; e += kT) {
-        const int k = e % jb, m = e / jb;
-        ys[k + m * kSub] = __ldcg(Y + d.f + j0 + k + (int64_t)m * n);
+      const int row = i0 + r;
+#pragma unroll
+      for (int kk = 0; kk < 16; ++kk) {
+        const int k = ka + kk;
+        dst[kk] = (r < kb && k < jb) ? (TRANS ? P[(int64_t)(j0 + k) * d.ld + row] : P[(int64_t)row * d.ld + j0 + k])
+                                     : 0.f;
       }
+    };
+    float lv[16];
+    if (ndep > 0) load_tile(0, lv);
+    for (int q = 0; q < ndep; ++q) {
+      const int j = TRANS ? item.nb - 1 - q : q;
+      const int j0 = j * kSub, jb = min(kSub, d.s - j0);
+      __syncthreads();   // the previous tile is done with ys
+      stage_solved(d.f, j0, jb);
       __syncthreads();
-      if (r < kb) {
-        const int kz = min(jb, ka + 16), row = i0 + r;
-        float lv[16];
+      float nx[16];
+      if (q + 1 < ndep) load_tile(q + 1, nx);
 #pragma unroll
-        for (int kk = 0; kk < 16; ++kk) {
-          const int k = ka + kk;
-          lv[kk] = k < kz ? (TRANS ? P[(int64_t)(j0 + k) * d.ld + row] : P[(int64_t)row * d.ld + j0 + k]) : 0.f;
-        }
+      for (int kk = 0; kk < 16; ++kk)
 #pragma unroll
-        for (int kk = 0; kk < 16; ++kk) {
-          if (ka + kk >= kz) break;
+        for (int m = 0; m < kSolveChunk; ++m)
+          if (m < nrhs) acc[m] += lv[kk] * ys[ka + kk + m * kSub];
+      if (q + 1 < ndep) {
 #pragma unroll
-          for (int m = 0; m < kSolveChunk; ++m)
-            if (m < nrhs) acc[m] += lv[kk] * ys[ka + kk + m * kSub];
-        }
+        for (int kk = 0; kk < 16; ++kk) lv[kk] = nx[kk];
       }
     }
     __syncthreads();   // every thread is done with ys and red
-    reduce(acc, kb);
+    reduce(acc);
     for (int e = tid; e < kb * nrhs; e += kT) {
       const int rr = e % kb, m = e / kb;
       const float* pr = red + m * 4 * kSub + rr;
@@ -1051,23 +1103,25 @@ k_sv_tri32(const SnodeDev* __restrict__ sn, const TriItem* __restrict__ items, i
       }
     }
     __syncthreads();   // every read of yi is done
-    reduce(acc2, kb);
+    reduce(acc2);
     for (int e = tid; e < kb * nrhs; e += kT) {
       const int rr = e % kb, m = e / kb;
       const float* pr = red + m * 4 * kSub + rr;
       yi[rr + m * kSub] = ((pr[0] + pr[kSub]) + pr[2 * kSub]) + pr[3 * kSub];
     }
+    // y_i (pre, minus M y_l for i > 0): rows of Y and their tagged words
+    auto publish = [&](int rr, int m, float y) {
+      const int64_t q = d.f + i0 + rr + (int64_t)m * n;
+      Y[q] = y;
+      st_relaxed_u64(hand + q, tag_hi | __float_as_uint(y));
+    };
     if (item.i > 0) {
       // the last dependency: y_i = pre - M y_l
       const int q = item.i - 1;
       const int j = TRANS ? item.nb - 1 - q : q;
       const int j0 = j * kSub, jb = min(kSub, d.s - j0);
-      wait_flag(item.fbase + j);
-      __syncthreads();   // also: pre is in yi, red is free
-      for (int e = tid; e < jb * nrhs; e += kT) {
-        const int k = e % jb, m = e / jb;
-        ys[k + m * kSub] = __ldcg(Y + d.f + j0 + k + (int64_t)m * n);
-      }
+      __syncthreads();   // pre is in yi, red is free
+      stage_solved(d.f, j0, jb);
       __syncthreads();
       float acc3[kSolveChunk];
 #pragma unroll
@@ -1083,28 +1137,24 @@ k_sv_tri32(const SnodeDev* __restrict__ sn, const TriItem* __restrict__ items, i
             if (m < nrhs) acc3[m] += a * ys[ka + kk + m * kSub];
         }
       }
-      reduce(acc3, kb);
+      reduce(acc3);
       for (int e = tid; e < kb * nrhs; e += kT) {
         const int rr = e % kb, m = e / kb;
         const float* pr = red + m * 4 * kSub + rr;
-        Y[d.f + i0 + rr + (int64_t)m * n] = yi[rr + m * kSub] - (((pr[0] + pr[kSub]) + pr[2 * kSub]) + pr[3 * kSub]);
+        publish(rr, m, yi[rr + m * kSub] - (((pr[0] + pr[kSub]) + pr[2 * kSub]) + pr[3 * kSub]));
       }
     } else {
       __syncthreads();
       for (int e = tid; e < kb * nrhs; e += kT) {
         const int rr = e % kb, m = e / kb;
-        Y[d.f + i0 + rr + (int64_t)m * n] = yi[rr + m * kSub];
+        publish(rr, m, yi[rr + m * kSub]);
       }
     }
-    __syncthreads();   // every thread's rows of Y are written (CTA order) ...
-    if (tid == 0) {
-      __threadfence();  // ... and made visible at GPU scope before the flag
-      st_release(flags + item.fbase + blk, tgt);
-    }
+    __syncthreads();   // the next item reuses the shared buffers
   }
   // the last CTA to finish advances the epoch for the next launch
   __syncthreads();
-  if (tid == 0) {
+  if (threadIdx.x == 0) {
     __threadfence();
     if (atomicAdd(sync + 1, 1) == (int)gridDim.x - 1) {
       atomicExch(sync + 1, 0);
@@ -1138,9 +1188,8 @@ int launch_tri(chol_handle* h, const LevelPlan& P, const T* L, T* Y, int nr, cud
   cudaError_t e;
   if constexpr (f32) {
     const float* Dinv = reinterpret_cast<const float*>(D->dinv);
-    void* args[] = {(void*)&D->sn, (void*)&items, (void*)&nitems, (void*)&L, (void*)&Dinv, (void*)&Y, (void*)&n,
-                    (void*)&nr, (void*)&D->tri_flags, (void*)&D->tri_sync, (void*)&D->sv_err, (void*)&max_polls,
-                    (void*)&skew};
+    void* args[] = {(void*)&D->sn, (void*)&items, (void*)&nitems, (void*)&L, (void*)&Dinv, (void*)&Y, (void*)&D->hand32,
+                    (void*)&n, (void*)&nr, (void*)&D->tri_sync, (void*)&D->sv_err, (void*)&max_polls, (void*)&skew};
     e = cudaLaunchCooperativeKernel((const void*)k_sv_tri32<TRANS>, dim3(grid), dim3(kT), args, tri32_smem(nr), st);
   } else {
     static_assert(f32 || !RM, "binary64 panels are column-major");
@@ -1155,6 +1204,15 @@ int launch_tri(chol_handle* h, const LevelPlan& P, const T* L, T* Y, int nr, cud
     return CHOL_ECUDA;
   }
   return CHOL_OK;
+}
+
+// The panel-product kernels keep per-thread sums for at most NR right-hand
+// sides: 1, 4 or the chunk (fewer registers, more resident CTAs for few).
+template <class F>
+void with_nr(int nr, F&& f) {
+  if (nr <= 1) f(std::integral_constant<int, 1>{});
+  else if (nr <= 4) f(std::integral_constant<int, 4>{});
+  else f(std::integral_constant<int, kSolveChunk>{});
 }
 
 template <class T, bool RM>
@@ -1184,8 +1242,10 @@ int solve_levels(chol_handle* h, const T* L, T* Y, T* W, T* part, int nr, cudaSt
     }
     if (P.gemv_n > 0) {
       KScope* ks = scope(CHOL_K_SOLVE_GEMV);
-      k_sv_gemv<T, RM><<<P.gemv_n, kT, 0, st>>>(D->sn, D->gemv + P.gemv_b, L, Y, n, W, nr, (T*)D->split_part,
-                                                D->split_cnt);
+      with_nr(nr, [&](auto c) {
+        k_sv_gemv<T, RM, decltype(c)::value><<<P.gemv_n, kT, 0, st>>>(D->sn, D->gemv + P.gemv_b, L, Y, n, W, nr,
+                                                                      (T*)D->split_part, D->split_cnt);
+      });
       delete ks;
     }
     if (P.asm_n + P.asmw_n > 0) {
@@ -1204,14 +1264,19 @@ int solve_levels(chol_handle* h, const T* L, T* Y, T* W, T* part, int nr, cudaSt
     if constexpr (RM) {
       if (P.bpart_n > 0) {
         KScope* ks = scope(CHOL_K_SOLVE_BPANEL);
-        k_sv_bpart<T><<<P.bpart_n, kT, 0, st>>>(D->sn, D->bpart + P.bpart_b, D->rows, L, Y, n, part, h->p_max, nr);
+        with_nr(nr, [&](auto c) {
+          k_sv_bpart<T, decltype(c)::value><<<P.bpart_n, kT, 0, st>>>(D->sn, D->bpart + P.bpart_b, D->rows, L, Y, n,
+                                                                      part, h->p_max, nr);
+        });
         k_sv_bred<T><<<P.bred_n, kT, 0, st>>>(D->sn, D->bred + P.bred_b, part, h->p_max, Y, n, nr);
         delete ks;
       }
     } else if (P.bpanel_n > 0) {
       KScope* ks = scope(CHOL_K_SOLVE_BPANEL);
-      k_sv_bpanel<T, RM><<<P.bpanel_n, kT, 0, st>>>(D->sn, D->bpanel + P.bpanel_b, D->rows, L, Y, n, nr,
-                                                    (T*)D->split_part, D->split_cnt);
+      with_nr(nr, [&](auto c) {
+        k_sv_bpanel<T, RM, decltype(c)::value><<<P.bpanel_n, kT, 0, st>>>(D->sn, D->bpanel + P.bpanel_b, D->rows, L,
+                                                                          Y, n, nr, (T*)D->split_part, D->split_cnt);
+      });
       delete ks;
     }
     if (P.ssmall_n > 0) {
@@ -1303,6 +1368,10 @@ int chol_solve_mixed(chol_handle* h, double* b, int32_t nrhs, cudaStream_t st) {
   const int n = h->n;
   if (!D->Y32) {
     if ((rc = chol_dalloc(h, (void**)&D->Y32, sizeof(float) * (size_t)std::max(n, 1) * kSolveChunk))) return rc;
+    // tagged hand-off words of the triangle launches: zero (no launch tag) once
+    if ((rc = chol_dalloc(h, (void**)&D->hand32, sizeof(unsigned long long) * (size_t)std::max(n, 1) * kSolveChunk)))
+      return rc;
+    CHOL_CUDA_TRY(cudaMemset(D->hand32, 0, sizeof(unsigned long long) * (size_t)std::max(n, 1) * kSolveChunk));
     if ((rc = chol_dalloc(h, (void**)&D->W32, sizeof(float) * (size_t)std::max<int64_t>(h->w_rows_max, 1) * kSolveChunk)))
       return rc;
     if ((rc = chol_dalloc(h, (void**)&D->rhs_scale, sizeof(double) * kSolveChunk))) return rc;
