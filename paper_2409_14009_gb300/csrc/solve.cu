@@ -157,17 +157,22 @@ k_diag_inv64(const SnodeDev* __restrict__ sn, const TriItem* __restrict__ items,
   double x[16];
 #pragma unroll
   for (int mm = 0; mm < 16; ++mm) x[mm] = (q + 4 * mm == g) ? 1.0 : 0.0;
+  // only the first kb steps and the warps holding columns g < kb do work (a
+  // ragged block of a small supernode is often much narrower than 64)
+  if ((tid >> 5) * 8 < kb) {
 #pragma unroll
-  for (int jm = 0; jm < 16; ++jm) {
+    for (int jm = 0; jm < 16; ++jm) {
+      if (jm * 4 >= kb) break;   // uniform across the CTA
 #pragma unroll
-    for (int jq = 0; jq < 4; ++jq) {
-      const int jj = jm * 4 + jq;
-      const double xj = __shfl_sync(0xffffffffu, x[jm] * rinv[jj], jq, 4);
-      if (q == jq) x[jm] = xj;
+      for (int jq = 0; jq < 4; ++jq) {
+        const int jj = jm * 4 + jq;
+        const double xj = __shfl_sync(0xffffffffu, x[jm] * rinv[jj], jq, 4);
+        if (q == jq) x[jm] = xj;
 #pragma unroll
-      for (int mm = jm; mm < 16; ++mm) {
-        const int c = q + 4 * mm;
-        if (c > jj) x[mm] = fma(-xj, Lk[c + jj * 65], x[mm]);
+        for (int mm = jm; mm < 16; ++mm) {
+          const int c = q + 4 * mm;
+          if (c > jj && 4 * mm < kb) x[mm] = fma(-xj, Lk[c + jj * 65], x[mm]);
+        }
       }
     }
   }
@@ -1207,11 +1212,12 @@ int launch_tri(chol_handle* h, const LevelPlan& P, const T* L, T* Y, int nr, cud
 }
 
 // The panel-product kernels keep per-thread sums for at most NR right-hand
-// sides: 1, 4 or the chunk (fewer registers, more resident CTAs for few).
+// sides: 1, 4, 8 or the chunk (fewer registers, more resident CTAs for few).
 template <class F>
 void with_nr(int nr, F&& f) {
   if (nr <= 1) f(std::integral_constant<int, 1>{});
   else if (nr <= 4) f(std::integral_constant<int, 4>{});
+  else if (nr <= 8) f(std::integral_constant<int, 8>{});
   else f(std::integral_constant<int, kSolveChunk>{});
 }
 
