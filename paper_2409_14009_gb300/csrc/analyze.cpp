@@ -521,23 +521,53 @@ void build(chol_handle* h, const int64_t* colptr, const int32_t* rowind) {
       st.panel_n = (int32_t)h->panel_items.size() - st.panel_b;
       st.ogemm_b = (int32_t)h->gemm_tasks.size();
       st.ok0 = ob;
-      st.okb = kTcOuter;
       const int32_t oend = ob + kTcOuter;
+      // the block's outer products right of it belong to the outer updates
+      // (flop convention), whichever launch applies them
       for (int32_t J : large) {
         const SnodeDev& d = h->snodes[J];
         if (d.s <= oend) continue;
         const double w = (double)(d.s - oend), hgt = (double)(d.len - oend);
-        st.ogemm_flops += 2.0 * kTcOuter * (w * hgt - w * (w - 1.0) / 2.0);
+        st.panel_flops -= 2.0 * kTcOuter * (w * hgt - w * (w - 1.0) / 2.0);
       }
-      st.panel_flops -= st.ogemm_flops;
-      // the next outer block's column tiles of every supernode first
+      // With the tensor-core updates, outer blocks go in pairs, so that most
+      // of the trailing matrix is read and written once per 512 columns
+      // instead of once per 256:
+      // - the first block of a pair updates only the next block's columns
+      //   (K = the block), which the next panel needs;
+      // - the second updates every column right of it with K = both blocks
+      //   (the next pair's two blocks' columns first, on the critical stream;
+      //   the rest beside the next panels).
+      // Otherwise (binary32 SIMT tiles) every block updates every column right
+      // of it with K = the block, the next block's columns first. Every entry
+      // receives the blocks' updates in block order either way.
+      const bool pairs = h->opt.precision == CHOL_PREC_TF32 || h->opt.precision == CHOL_PREC_BF16;
+      const bool second = pairs && ((ob / kTcOuter) & 1);
+      const bool first = pairs && !second;
+      const int32_t kbeg = second ? ob - kTcOuter : ob;
+      st.okb = second ? 2 * kTcOuter : kTcOuter;
+      // the critical stream waits for the previous side-stream update before
+      // this step's outer update (with pairs: only where that update's columns
+      // reach the side stream's)
+      st.join_rest = pairs ? (second ? 1 : 0) : 1;
+      const int32_t next_end = oend + (second ? 2 * kTcOuter : kTcOuter);
+      for (int32_t J : large) {
+        const SnodeDev& d = h->snodes[J];
+        if (d.s <= oend) continue;
+        const int32_t cend = first ? std::min(d.s, next_end) : d.s;
+        const double kk = (double)std::min(st.okb, d.s - kbeg);
+        const double w = (double)(cend - oend), hgt = (double)(d.len - oend);
+        st.ogemm_flops += 2.0 * kk * (w * hgt - w * (w - 1.0) / 2.0);
+      }
+      // the columns the next panels need first
       for (int pass = 0; pass < 2; ++pass) {
         for (int32_t J : large) {
           const SnodeDev& d = h->snodes[J];
           if (d.s <= oend) continue;
-          for (int32_t c0 = oend; c0 < d.s; c0 += tg) {
-            if ((pass == 0) != (c0 < oend + kTcOuter)) continue;
-            for (int32_t r0 = c0; r0 < d.len; r0 += tg) h->gemm_tasks.push_back({J, ob, r0, c0});
+          const int32_t cend = first ? std::min(d.s, next_end) : d.s;
+          for (int32_t c0 = oend; c0 < cend; c0 += tg) {
+            if ((pass == 0) != (c0 < next_end)) continue;
+            for (int32_t r0 = c0; r0 < d.len; r0 += tg) h->gemm_tasks.push_back({J, kbeg, r0, c0});
           }
         }
         if (pass == 0) st.ogemm_next = (int32_t)h->gemm_tasks.size() - st.ogemm_b;

@@ -65,13 +65,16 @@ struct AsmSeg {
 // (one-step lookahead).
 // Mixed modes: a step is one outer block [ok0, ok0 + kTcOuter) of columns; its
 // POTRF, TRSM and in-block updates run in one panel launch (panel_*: 64-row
-// tiles, see PanelItem; panel_ticket: the launch's work counter), then the
-// columns right of the block get one update with K = the block (ogemm_*, the
-// next block's column tiles first).
+// tiles, see PanelItem; panel_ticket: the launch's work counter), then an
+// outer update with K = okb from each task's k0 (ogemm_*, the columns the next
+// panels need first). With tensor-core updates blocks go in pairs: the first
+// block updates the next block's columns (okb = kTcOuter), the second every
+// column right of the pair (okb = 2 kTcOuter); join_rest: wait for the previous
+// side-stream update first.
 struct StepRange {
   int32_t potrf_b, potrf_n, trsm_b, trsm_n, gemm_b, gemm_n, ogemm_b, ogemm_n, ok0, okb;
   int32_t gemm_next, ogemm_next;
-  int32_t panel_b, panel_n, panel_ticket, pad;
+  int32_t panel_b, panel_n, panel_ticket, join_rest;
   double potrf_flops, trsm_flops, gemm_flops, ogemm_flops, panel_flops;
 };
 

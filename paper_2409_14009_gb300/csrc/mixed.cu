@@ -814,12 +814,11 @@ int chol_enqueue_factor_mixed(chol_handle* h, const double* values, cudaStream_t
     CHOL_CUDA_TRY(cudaStreamWaitEvent(D->hstream, D->lev[2], 0));
     st = D->hstream;
   }
-  // trailing tiles of a step, in-block (K = nb) or outer (K = kTcOuter)
-  auto gemm = [&](const TileTask* tasks, int n, bool outer, double flops, cudaStream_t s2) -> int {
+  // outer-update tiles of a step (K = kk: one or two outer blocks, from each task's k0)
+  auto gemm = [&](const TileTask* tasks, int n, int kk, double flops, cudaStream_t s2) -> int {
     if (n <= 0) return CHOL_OK;
     KScope ks(h, CHOL_K_GEMM, s2, flops, 0.0);
-    const int kk = outer ? kTcOuter : nb;
-    if (tc) return chol_tc_gemm(h, tasks, n, kk, outer ? 0 : 1, s2);
+    if (tc) return chol_tc_gemm(h, tasks, n, kk, 0, s2);
     k_mx_gemm_simt<<<n, 256, 0, s2>>>(D->sn, tasks, kk, L);
     return CHOL_OK;
   };
@@ -834,9 +833,10 @@ int chol_enqueue_factor_mixed(chol_handle* h, const double* values, cudaStream_t
                                                                               D->status, spiv, D->mx_fallbacks);
     }
     // one launch per outer column block: the panel kernel (its POTRF, TRSM and
-    // in-block update steps), then the update of the columns right of the
-    // block; the next block's column tiles on the critical stream, the rest on
-    // the side stream beside the next panel (one-step lookahead)
+    // in-block update steps), then the outer update of a pair of blocks (the
+    // next block's columns after the first block, everything right of the pair
+    // after the second); the columns the next panels need on the critical
+    // stream, the rest on the side stream beside the next panels (lookahead)
     bool rest_pending = false;
     for (size_t k = 0; k < P.steps.size(); ++k) {
       const StepRange& s = P.steps[k];
@@ -855,14 +855,16 @@ int chol_enqueue_factor_mixed(chol_handle* h, const double* values, cudaStream_t
         CHOL_CUDA_TRY(cudaEventRecord(D->lev[0], st));   // the block's panel is final
         CHOL_CUDA_TRY(cudaStreamWaitEvent(D->lstream, D->lev[0], 0));
       }
-      if (rest_pending) {
+      // the side stream's update of a pair reaches the columns of the next
+      // pair's second block onwards: wait for it before updating those
+      if (rest_pending && s.join_rest) {
         CHOL_CUDA_TRY(cudaStreamWaitEvent(st, D->lev[1], 0));
         rest_pending = false;
       }
       const double fo = s.ogemm_n > 0 ? (double)s.ogemm_next / s.ogemm_n : 0.0;
-      if ((rc = gemm(D->gemm + s.ogemm_b, s.ogemm_next, true, s.ogemm_flops * fo, st))) return rc;
+      if ((rc = gemm(D->gemm + s.ogemm_b, s.ogemm_next, s.okb, s.ogemm_flops * fo, st))) return rc;
       if (orest > 0) {
-        if ((rc = gemm(D->gemm + s.ogemm_b + s.ogemm_next, orest, true, s.ogemm_flops * (1.0 - fo), D->lstream)))
+        if ((rc = gemm(D->gemm + s.ogemm_b + s.ogemm_next, orest, s.okb, s.ogemm_flops * (1.0 - fo), D->lstream)))
           return rc;
         CHOL_CUDA_TRY(cudaEventRecord(D->lev[1], D->lstream));
         rest_pending = true;

@@ -118,7 +118,19 @@ def _dense_problem(n):
     return dict(n=n, colptr=cp, rowind=ri, values=vx, perm=np.arange(n, dtype=np.int32))
 
 
-@pytest.mark.parametrize("n", [31, 32, 33, 64, 65, 100, 129, 255, 256, 257, 300, 520])
+def _outer_launches(n, pairs):
+    """Outer-update launches of one dense blocked supernode of n columns.
+    Tensor-core modes (pairs): block b = 2p updates the next block's columns
+    (K = 256) when there are any; block b = 2p + 1 updates the next pair's
+    columns (K = 512, the pair) on the critical stream and, when there are
+    columns beyond those, the rest on the side stream. binary32 SIMT tiles:
+    every block updates the next block's columns, then the rest."""
+    if pairs:
+        return sum((n > 256 * (b + 1)) + (b % 2 == 1 and n > 256 * (b + 3)) for b in range((n + 255) // 256))
+    return sum((n > 256 * (b + 1)) + (n > 256 * (b + 2)) for b in range((n + 255) // 256))
+
+
+@pytest.mark.parametrize("n", [31, 32, 33, 64, 65, 100, 129, 255, 256, 257, 300, 520, 1100])
 def test_fp32_blocked_diagonal_blocks_of_every_width(n):
     # the small-supernode kernel is off, so the whole matrix is one blocked
     # supernode: one panel launch per 256-column outer block (full and ragged
@@ -127,21 +139,19 @@ def test_fp32_blocked_diagonal_blocks_of_every_width(n):
     got, ferr, rel, ref = _check(_dense_problem(n), "fp32", nrhs=2, extra=dict(small_max_cols=1, small_max_panel=1))
     assert got["info"].fp64_fallbacks == 0
     assert got["stats"]["panel"]["launches"] == (n + 255) // 256
-    # per outer block b with columns right of it: the next block's tiles, and
-    # (when there are columns beyond that) the rest on the side stream
-    outer = sum((n > 256 * (b + 1)) + (n > 256 * (b + 2)) for b in range((n + 255) // 256))
-    assert got["stats"]["gemm"]["launches"] == outer
+    assert got["stats"]["gemm"]["launches"] == _outer_launches(n, pairs=False)
     assert ferr <= 1e-5, ferr
 
 
 @pytest.mark.parametrize("mode", ["tf32", "bf16"])
-@pytest.mark.parametrize("n", [300, 520, 777])
+@pytest.mark.parametrize("n", [300, 520, 777, 1100])
 def test_tensor_core_outer_updates_dense(mode, n):
-    # several outer blocks: the tcgen05 update of the columns right of each
-    # block (the next block's column tiles, then the rest on the side stream)
+    # several outer blocks: the tcgen05 updates of the columns right of each
+    # pair of blocks (K = 256 after the first block, K = 512 after the second,
+    # the columns the next panels need first, the rest on the side stream)
     got, ferr, rel, ref = _check(_dense_problem(n), mode, nrhs=2, extra=dict(small_max_cols=1, small_max_panel=1))
     assert got["stats"]["panel"]["launches"] == (n + 255) // 256
-    assert got["stats"]["gemm"]["launches"] >= (n - 1) // 256
+    assert got["stats"]["gemm"]["launches"] == _outer_launches(n, pairs=True)
     assert ferr <= (1e-2 if mode == "tf32" else 5e-2), ferr
 
 
@@ -212,7 +222,7 @@ def test_elasticity_32_tensor_core_launch_shapes_and_unrefined_factor(mode):
     """3D 32^3 x 3-dof elasticity with the benchmark's options: the factor
     takes the tcgen05 update on both rings (2-stage, three CTAs per SM, for
     grids of at least two tiles per SM; 6-stage otherwise) and the outer
-    K = 256 update right of every outer block. Before any refinement the
+    updates right of every pair of outer blocks (K = 256 and 512). Before any refinement the
     low-precision factor's backward error on sampled columns is within the
     mode's bound, and refinement then reaches 1e-10 against the oracle's A."""
     import torch
