@@ -951,10 +951,13 @@ k_diag_inv(const SnodeDev* __restrict__ sn, const TriItem* __restrict__ items, c
   }
 }
 
+// catch-up tiles of the binary32 triangle kernel per staging round
+constexpr int kCatch = 4;
+
 size_t tri32_smem(int nr) {
-  // ys, yi (64 x nr each), L_ii^{-1} and M (64 x 65 each), the k-group
-  // partial sums (4 x 64 x nr)
-  return sizeof(float) * ((size_t)6 * kSub * nr + 2 * kSub * 65);
+  // ys (kCatch solved blocks, kCatch x 64 x nr), yi (64 x nr), L_ii^{-1} and M
+  // (64 x 65 each), the k-group partial sums (4 x 64 x nr)
+  return sizeof(float) * ((size_t)(kCatch + 5) * kSub * nr + 2 * kSub * 65);
 }
 
 // Binary32 diagonal triangles of a level (row-major panels). Same items, epochs
@@ -981,14 +984,14 @@ __device__ __forceinline__ void st_relaxed_u64(unsigned long long* p, unsigned l
   asm volatile("st.relaxed.gpu.global.b64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
 }
 
-template <bool TRANS>
+template <bool TRANS, int NR>
 __global__ void __launch_bounds__(kT)
 k_sv_tri32(const SnodeDev* __restrict__ sn, const TriItem* __restrict__ items, int nitems, const float* __restrict__ L,
            const float* __restrict__ Dinv, float* __restrict__ Y, unsigned long long* __restrict__ hand, int n,
            int nrhs, int* __restrict__ sync, int* __restrict__ err, long long max_polls, int skew) {
   extern __shared__ __align__(16) unsigned char sv_smem[];
-  float* ys = reinterpret_cast<float*>(sv_smem);   // a solved block j, 64 x nrhs
-  float* yi = ys + kSub * nrhs;                     // this block's right-hand sides, then pre
+  float* ys = reinterpret_cast<float*>(sv_smem);   // kCatch solved blocks, kCatch x 64 x nrhs
+  float* yi = ys + kCatch * kSub * nrhs;            // this block's right-hand sides, then pre
   float* red = yi + kSub * nrhs;                    // k-group partial sums, 4 x 64 x nrhs
   float* Ls = red + 4 * kSub * nrhs;                // L_ii^{-1}, column-major (ld 65)
   float* Ms = Ls + kSub * 65;                       // M, column-major (ld 65)
@@ -1002,7 +1005,7 @@ k_sv_tri32(const SnodeDev* __restrict__ sn, const TriItem* __restrict__ items, i
   // ys = the solved rows [j0, j0 + jb) of the supernode starting at column f
   // (zero past jb), each read from its tagged word once the tag is this
   // launch's (bounded: a wait that gives up sets *err and takes the value)
-  auto stage_solved = [&](int64_t f, int j0, int jb) {
+  auto stage_solved = [&](float* dst, int64_t f, int j0, int jb) {
     for (int e = tid; e < kSub * nrhs; e += kT) {
       const int k = e & (kSub - 1), m = e / kSub;
       float v = 0.f;
@@ -1018,13 +1021,13 @@ k_sv_tri32(const SnodeDev* __restrict__ sn, const TriItem* __restrict__ items, i
         }
         v = __uint_as_float((unsigned)w);
       }
-      ys[k + m * kSub] = v;
+      dst[k + m * kSub] = v;
     }
   };
   // partial sums of acc into red (the caller then combines them)
-  auto reduce = [&](const float (&acc)[kSolveChunk]) {
+  auto reduce = [&](const float (&acc)[NR]) {
 #pragma unroll
-    for (int m = 0; m < kSolveChunk; ++m)
+    for (int m = 0; m < NR; ++m)
       if (m < nrhs) red[(g * kSub + r) + m * 4 * kSub] = acc[m];
     __syncthreads();
   };
@@ -1045,41 +1048,76 @@ k_sv_tri32(const SnodeDev* __restrict__ sn, const TriItem* __restrict__ items, i
       const int rr = e % kb, m = e / kb;
       yi[rr + m * kSub] = Y[d.f + i0 + rr + (int64_t)m * n];
     }
-    float acc[kSolveChunk];
+    float acc[NR];
 #pragma unroll
-    for (int m = 0; m < kSolveChunk; ++m) acc[m] = 0.f;
-    // the dependencies other than the last, from the panel; the next tile's
-    // entries are loaded while the current one is multiplied
+    for (int m = 0; m < NR; ++m) acc[m] = 0.f;
+    // the dependencies other than the last, from the panel, kCatch tiles a
+    // round: their entries are loaded first, then their solved blocks are
+    // staged together (one hand-off round trip per round, overlapping the
+    // loads), then the products in dependency order
     const int ndep = item.i - 1;
-    auto load_tile = [&](int q, float (&dst)[16]) {
-      const int j = TRANS ? item.nb - 1 - q : q;
-      const int j0 = j * kSub, jb = min(kSub, d.s - j0);
-      const int row = i0 + r;
+    for (int q0 = 0; q0 < ndep; q0 += kCatch) {
+      float lv[kCatch][16];
 #pragma unroll
-      for (int kk = 0; kk < 16; ++kk) {
-        const int k = ka + kk;
-        dst[kk] = (r < kb && k < jb) ? (TRANS ? P[(int64_t)(j0 + k) * d.ld + row] : P[(int64_t)row * d.ld + j0 + k])
-                                     : 0.f;
+      for (int t = 0; t < kCatch; ++t) {
+        const int q = q0 + t;
+        const int j = TRANS ? item.nb - 1 - q : q;
+        const int j0 = j * kSub, jb = min(kSub, d.s - j0);
+        const int row = i0 + r;
+#pragma unroll
+        for (int kk = 0; kk < 16; ++kk) {
+          const int k = ka + kk;
+          lv[t][kk] = (q < ndep && r < kb && k < jb)
+                          ? (TRANS ? P[(int64_t)(j0 + k) * d.ld + row] : P[(int64_t)row * d.ld + j0 + k])
+                          : 0.f;
+        }
       }
-    };
-    float lv[16];
-    if (ndep > 0) load_tile(0, lv);
-    for (int q = 0; q < ndep; ++q) {
-      const int j = TRANS ? item.nb - 1 - q : q;
-      const int j0 = j * kSub, jb = min(kSub, d.s - j0);
-      __syncthreads();   // the previous tile is done with ys
-      stage_solved(d.f, j0, jb);
+      __syncthreads();   // the previous round is done with ys
+      {
+        // the round's solved blocks: up to four tagged words of a thread in
+        // flight at once, then each checked (and waited for, bounded)
+        const int per = kSub * nrhs, tot = min(kCatch, ndep - q0) * per;
+        for (int e0 = tid; e0 < tot; e0 += 4 * kT) {
+          unsigned long long w[4];
+          const unsigned long long* src[4];
+          int dsti[4];
+#pragma unroll
+          for (int u = 0; u < 4; ++u) {
+            const int e = e0 + u * kT;
+            const int t = e / per, em = e - t * per, k = em & (kSub - 1), m = em / kSub;
+            const int j = TRANS ? item.nb - 1 - (q0 + t) : q0 + t;
+            const int j0 = j * kSub, jb = min(kSub, d.s - j0);
+            src[u] = (e < tot && k < jb) ? hand + d.f + j0 + k + (int64_t)m * n : nullptr;
+            dsti[u] = e < tot ? e : -1;
+            w[u] = src[u] ? ld_relaxed_u64(src[u]) : 0ull;
+          }
+#pragma unroll
+          for (int u = 0; u < 4; ++u) {
+            if (dsti[u] < 0) continue;
+            float v = 0.f;   // zero past a ragged block
+            if (src[u]) {
+              long long polls = 0;
+              while ((unsigned)(w[u] >> 32) != wait_tag) {
+                if (++polls > max_polls) { atomicExch(err, 1); break; }
+                if ((polls & 255) == 0 && *(volatile int*)err != 0) break;
+                if (polls > 4096) __nanosleep(100);
+                w[u] = ld_relaxed_u64(src[u]);
+              }
+              v = __uint_as_float((unsigned)w[u]);
+            }
+            ys[dsti[u]] = v;
+          }
+        }
+      }
       __syncthreads();
-      float nx[16];
-      if (q + 1 < ndep) load_tile(q + 1, nx);
 #pragma unroll
-      for (int kk = 0; kk < 16; ++kk)
+      for (int t = 0; t < kCatch; ++t) {
+        if (q0 + t >= ndep) break;
 #pragma unroll
-        for (int m = 0; m < kSolveChunk; ++m)
-          if (m < nrhs) acc[m] += lv[kk] * ys[ka + kk + m * kSub];
-      if (q + 1 < ndep) {
+        for (int kk = 0; kk < 16; ++kk)
 #pragma unroll
-        for (int kk = 0; kk < 16; ++kk) lv[kk] = nx[kk];
+          for (int m = 0; m < NR; ++m)
+            if (m < nrhs) acc[m] += lv[t][kk] * ys[t * kSub * nrhs + ka + kk + m * kSub];
       }
     }
     __syncthreads();   // every thread is done with ys and red
@@ -1091,9 +1129,9 @@ k_sv_tri32(const SnodeDev* __restrict__ sn, const TriItem* __restrict__ items, i
     }
     __syncthreads();
     // pre = L_ii^{-1} yi (forward) or L_ii^{-T} yi (transposed)
-    float acc2[kSolveChunk];
+    float acc2[NR];
 #pragma unroll
-    for (int m = 0; m < kSolveChunk; ++m) acc2[m] = 0.f;
+    for (int m = 0; m < NR; ++m) acc2[m] = 0.f;
     if (r < kb) {
 #pragma unroll 4
       for (int kk = 0; kk < 16; ++kk) {
@@ -1102,7 +1140,7 @@ k_sv_tri32(const SnodeDev* __restrict__ sn, const TriItem* __restrict__ items, i
         if (TRANS ? (k >= r && k < kb) : (k <= r)) {
           const float a = TRANS ? Ls[k + r * 65] : Ls[r + k * 65];
 #pragma unroll
-          for (int m = 0; m < kSolveChunk; ++m)
+          for (int m = 0; m < NR; ++m)
             if (m < nrhs) acc2[m] += a * yi[k + m * kSub];
         }
       }
@@ -1126,11 +1164,11 @@ k_sv_tri32(const SnodeDev* __restrict__ sn, const TriItem* __restrict__ items, i
       const int j = TRANS ? item.nb - 1 - q : q;
       const int j0 = j * kSub, jb = min(kSub, d.s - j0);
       __syncthreads();   // pre is in yi, red is free
-      stage_solved(d.f, j0, jb);
+      stage_solved(ys, d.f, j0, jb);
       __syncthreads();
-      float acc3[kSolveChunk];
+      float acc3[NR];
 #pragma unroll
-      for (int m = 0; m < kSolveChunk; ++m) acc3[m] = 0.f;
+      for (int m = 0; m < NR; ++m) acc3[m] = 0.f;
       if (r < kb) {
         const int kz = min(jb, ka + 16);
 #pragma unroll
@@ -1138,7 +1176,7 @@ k_sv_tri32(const SnodeDev* __restrict__ sn, const TriItem* __restrict__ items, i
           if (ka + kk >= kz) break;
           const float a = Ms[r + (ka + kk) * 65];
 #pragma unroll
-          for (int m = 0; m < kSolveChunk; ++m)
+          for (int m = 0; m < NR; ++m)
             if (m < nrhs) acc3[m] += a * ys[ka + kk + m * kSub];
         }
       }
@@ -1175,6 +1213,17 @@ k_sv_tri32(const SnodeDev* __restrict__ sn, const TriItem* __restrict__ items, i
 // Resident CTAs per SM of each triangle kernel per chunk width (set once).
 int g_tri_per_sm[2][2][kSolveChunk + 1] = {};   // [binary32][transposed][nr]
 
+// The panel-product and binary32 triangle kernels keep per-thread sums for at
+// most NR right-hand sides: 1, 4, 8 or the chunk (fewer registers, more
+// resident CTAs for few).
+template <class F>
+void with_nr(int nr, F&& f) {
+  if (nr <= 1) f(std::integral_constant<int, 1>{});
+  else if (nr <= 4) f(std::integral_constant<int, 4>{});
+  else if (nr <= 8) f(std::integral_constant<int, 8>{});
+  else f(std::integral_constant<int, kSolveChunk>{});
+}
+
 // One cooperative launch of the level's diagonal triangles: k_sv_tri64
 // (binary64, one right-hand-side column per item) or k_sv_tri32 (binary32, all
 // columns of the chunk per item); both multiply by the blocks' inverses.
@@ -1195,7 +1244,10 @@ int launch_tri(chol_handle* h, const LevelPlan& P, const T* L, T* Y, int nr, cud
     const float* Dinv = reinterpret_cast<const float*>(D->dinv);
     void* args[] = {(void*)&D->sn, (void*)&items, (void*)&nitems, (void*)&L, (void*)&Dinv, (void*)&Y, (void*)&D->hand32,
                     (void*)&n, (void*)&nr, (void*)&D->tri_sync, (void*)&D->sv_err, (void*)&max_polls, (void*)&skew};
-    e = cudaLaunchCooperativeKernel((const void*)k_sv_tri32<TRANS>, dim3(grid), dim3(kT), args, tri32_smem(nr), st);
+    with_nr(nr, [&](auto c) {
+      e = cudaLaunchCooperativeKernel((const void*)k_sv_tri32<TRANS, decltype(c)::value>, dim3(grid), dim3(kT), args,
+                                      tri32_smem(nr), st);
+    });
   } else {
     static_assert(f32 || !RM, "binary64 panels are column-major");
     const double* Dinv = reinterpret_cast<const double*>(D->dinv);
@@ -1209,16 +1261,6 @@ int launch_tri(chol_handle* h, const LevelPlan& P, const T* L, T* Y, int nr, cud
     return CHOL_ECUDA;
   }
   return CHOL_OK;
-}
-
-// The panel-product kernels keep per-thread sums for at most NR right-hand
-// sides: 1, 4, 8 or the chunk (fewer registers, more resident CTAs for few).
-template <class F>
-void with_nr(int nr, F&& f) {
-  if (nr <= 1) f(std::integral_constant<int, 1>{});
-  else if (nr <= 4) f(std::integral_constant<int, 4>{});
-  else if (nr <= 8) f(std::integral_constant<int, 8>{});
-  else f(std::integral_constant<int, kSolveChunk>{});
 }
 
 template <class T, bool RM>
@@ -1310,15 +1352,19 @@ int set_solve_attrs() {
   static std::once_flag once;
   static int rc = CHOL_OK;
   std::call_once(once, [] {
-    const size_t df = tri32_smem(kSolveChunk);
     const void* kd[2] = {(const void*)k_sv_tri64<false>, (const void*)k_sv_tri64<true>};
-    const void* kf[2] = {(const void*)k_sv_tri32<false>, (const void*)k_sv_tri32<true>};
     cudaError_t e = cudaSuccess;
     for (int t = 0; t < 2; ++t) {
-      e = e ? e : cudaFuncSetAttribute(kf[t], cudaFuncAttributeMaxDynamicSharedMemorySize, (int)df);
       for (int nr = 1; nr <= kSolveChunk; ++nr) {
         e = e ? e : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&g_tri_per_sm[0][t][nr], kd[t], kT, 0);
-        e = e ? e : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&g_tri_per_sm[1][t][nr], kf[t], kT, tri32_smem(nr));
+        // the binary32 kernel of this chunk width's NR class
+        with_nr(nr, [&](auto c) {
+          const void* kf = t ? (const void*)k_sv_tri32<true, decltype(c)::value>
+                             : (const void*)k_sv_tri32<false, decltype(c)::value>;
+          e = e ? e : cudaFuncSetAttribute(kf, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                           (int)tri32_smem(decltype(c)::value));
+          e = e ? e : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&g_tri_per_sm[1][t][nr], kf, kT, tri32_smem(nr));
+        });
       }
     }
     if (e != cudaSuccess) {
