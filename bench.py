@@ -546,8 +546,10 @@ def run_ours(args, rank, world, local_rank):
     for _ in range(max(args.warmup, 0)):
         step()
     torch.cuda.synchronize()
-    # time the two dense FP64 update kernels inside the timed region
-    P.chol_profile(S.h, (1 << 4) | (1 << 5))
+    # time the dominant kernel (the SYRK class: 62% of the serialised factor
+    # time in the ncu launch list, the trailing GEMM class 30%) inside the timed
+    # region; per-launch events on one class only keep the step's overhead small
+    P.chol_profile(S.h, 1 << P.KERNEL_CLASSES.index("syrk"))
     P.chol_get_stats(S.h, reset=True)
     e0 = torch.cuda.Event(enable_timing=True)
     e1 = torch.cuda.Event(enable_timing=True)
@@ -604,7 +606,7 @@ def run_ours(args, rank, world, local_rank):
                                            S.info.update_doubles)
     ms, e2e_ms = max_over_ranks(dist, [ms, e2e_ms], dev)
     if rank == 0:
-        dom = max(("gemm", "syrk"), key=lambda k: stats[k]["ms"])
+        dom = "syrk"
         ds = stats[dom]
         achieved = ds["flops"] / (ds["ms"] * 1e-3) / 1e9 if ds["ms"] > 0 else None
         stored_ratio = S.info.flops_stored / flops
