@@ -748,43 +748,57 @@ template <class T, bool RM, int S>
 __global__ void __launch_bounds__(kT)
 k_sv_small_fwd(const SnodeDev* __restrict__ sn, const int32_t* __restrict__ list, int count,
                const T* __restrict__ L, T* __restrict__ Y, int n, T* __restrict__ W, int nrhs) {
+  __shared__ T ysh[kT / 32][S];
   const int wid = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
   if (wid >= count) return;
   const SnodeDev d = sn[list[wid]];
   const T* P = L + d.loff;
   const int b = d.len - d.s;
   T* Wj = W + d.wpre * nrhs;
-  T lrow[S];   // L(lane, k), k < lane (s <= S)
-#pragma unroll
-  for (int k = 0; k < S; ++k) lrow[k] = (k < lane && lane < d.s) ? lval<T, RM>(P, d, lane, k) : T(0);
+  // lane i holds row i of the block scaled by 1 / L(i, i): y_i = b_i / L(i, i)
+  // - sum_k (L(i, k) / L(i, i)) y_k, so a step of the substitution chain is a
+  // shuffle and one FMA (a binary64 multiply on the chain costs ~65 cycles)
   const T rdiag = lane < d.s ? T(1) / lval<T, RM>(P, d, lane, lane) : T(0);
+  T lrow[S];   // L(lane, k) / L(lane, lane), k < lane (s <= S)
+#pragma unroll
+  for (int k = 0; k < S; ++k) lrow[k] = (k < lane && lane < d.s) ? lval<T, RM>(P, d, lane, k) * rdiag : T(0);
   for (int r = 0; r < nrhs; ++r) {
-    T y = lane < d.s ? Y[d.f + lane + (int64_t)r * n] : T(0);
+    T y = lane < d.s ? Y[d.f + lane + (int64_t)r * n] * rdiag : T(0);
 #pragma unroll
     for (int k = 0; k < S; ++k) {
       if (k < d.s) {   // uniform across the warp
-        const T yk = __shfl_sync(0xffffffffu, y * rdiag, k);
-        if (lane == k) y = yk;
+        const T yk = __shfl_sync(0xffffffffu, y, k);
         if (lane > k) y -= lrow[k] * yk;
       }
     }
     if (lane < d.s) Y[d.f + lane + (int64_t)r * n] = y;
-    T acc[kSolveSmallRows / 32];
-#pragma unroll
-    for (int c = 0; c < kSolveSmallRows / 32; ++c) acc[c] = T(0);
-    for (int k = 0; k < d.s; ++k) {
-      const T yk = __shfl_sync(0xffffffffu, y, k);
-#pragma unroll
-      for (int c = 0; c < kSolveSmallRows / 32; ++c) {
-        const int u = lane + 32 * c;
-        if (u < b) acc[c] += lval<T, RM>(P, d, d.s + u, k) * yk;
-      }
-    }
-#pragma unroll
+    // w_J = L_RJ y_J, lane u holding rows u, u + 32, ...: per 32-row group all
+    // s entries of the lane's row are loaded at once (one memory round trip per
+    // group), then multiplied with y_J broadcast by shuffle; four partial sums
+    // (k mod 4), added pairwise
+    T* yk = ysh[threadIdx.x >> 5];   // y_J of this warp's supernode (broadcast reads)
+    if (lane < S) yk[lane] = y;
+    __syncwarp();
     for (int c = 0; c < kSolveSmallRows / 32; ++c) {
+      if (32 * c >= b) break;   // uniform across the warp
       const int u = lane + 32 * c;
-      if (u < b) Wj[u + (int64_t)r * b] = acc[c];
+      // binary64 with S = 32: two halves of 16 loads (the row copy of the
+      // block stays in registers for every right-hand side)
+      constexpr int KH = (sizeof(T) == 8 && S > 16) ? 16 : S;
+      T a4[4] = {T(0), T(0), T(0), T(0)};
+#pragma unroll 1
+      for (int k0 = 0; k0 < S; k0 += KH) {
+        if (k0 >= d.s) break;   // uniform across the warp
+        T lv[KH];
+#pragma unroll
+        for (int kk = 0; kk < KH; ++kk)
+          lv[kk] = (k0 + kk < d.s && u < b) ? lval<T, RM>(P, d, d.s + u, k0 + kk) : T(0);
+#pragma unroll
+        for (int kk = 0; kk < KH; ++kk) a4[kk & 3] += lv[kk] * yk[k0 + kk];
+      }
+      if (u < b) Wj[u + (int64_t)r * b] = (a4[0] + a4[1]) + (a4[2] + a4[3]);
     }
+    __syncwarp();   // the next right-hand side rewrites yk
   }
 }
 
@@ -801,31 +815,35 @@ k_sv_small_bwd(const SnodeDev* __restrict__ sn, const int32_t* __restrict__ list
   const T* P = L + d.loff;
   const int b = d.len - d.s;
   const int32_t* rj = rows + d.roff + d.s;
-  T lcol[S];   // L(k, lane), k > lane (s <= S)
-#pragma unroll
-  for (int k = 0; k < S; ++k) lcol[k] = (k > lane && k < d.s) ? lval<T, RM>(P, d, k, lane) : T(0);
+  // lane i holds column i of the block scaled by 1 / L(i, i) (as in the forward
+  // kernel: a step of the chain is a shuffle and one FMA)
   const T rdiag = lane < d.s ? T(1) / lval<T, RM>(P, d, lane, lane) : T(0);
-  for (int r = 0; r < nrhs; ++r) {
-    T t = T(0);
-    if (lane < d.s) {
-      for (int u0 = 0; u0 < b; u0 += 4) {
-        T lv[4], xv[4];
+  T lcol[S];   // L(k, lane) / L(lane, lane), k > lane (s <= S)
 #pragma unroll
-        for (int uu = 0; uu < 4; ++uu) {
+  for (int k = 0; k < S; ++k) lcol[k] = (k > lane && k < d.s) ? lval<T, RM>(P, d, k, lane) * rdiag : T(0);
+  for (int r = 0; r < nrhs; ++r) {
+    // four partial sums (u mod 4), added pairwise: a chain of b/4 dependent FMAs
+    // (16 rows' loads in flight per round)
+    T t4[4] = {T(0), T(0), T(0), T(0)};
+    if (lane < d.s) {
+      for (int u0 = 0; u0 < b; u0 += 16) {
+        T lv[16], xv[16];
+#pragma unroll
+        for (int uu = 0; uu < 16; ++uu) {
           const int u = u0 + uu;
           lv[uu] = u < b ? lval<T, RM>(P, d, d.s + u, lane) : T(0);
           xv[uu] = u < b ? Y[rj[u] + (int64_t)r * n] : T(0);
         }
 #pragma unroll
-        for (int uu = 0; uu < 4; ++uu) t += lv[uu] * xv[uu];
+        for (int uu = 0; uu < 16; ++uu) t4[uu & 3] += lv[uu] * xv[uu];
       }
     }
-    T y = lane < d.s ? Y[d.f + lane + (int64_t)r * n] - t : T(0);
+    const T t = (t4[0] + t4[1]) + (t4[2] + t4[3]);
+    T y = lane < d.s ? (Y[d.f + lane + (int64_t)r * n] - t) * rdiag : T(0);
 #pragma unroll
     for (int k = S - 1; k >= 0; --k) {
       if (k < d.s) {   // uniform across the warp
-        const T xk = __shfl_sync(0xffffffffu, y * rdiag, k);
-        if (lane == k) y = xk;
+        const T xk = __shfl_sync(0xffffffffu, y, k);
         if (lane < k) y -= lcol[k] * xk;
       }
     }
