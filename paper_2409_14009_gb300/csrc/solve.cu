@@ -755,27 +755,38 @@ k_sv_small_fwd(const SnodeDev* __restrict__ sn, const int32_t* __restrict__ list
   const T* P = L + d.loff;
   const int b = d.len - d.s;
   T* Wj = W + d.wpre * nrhs;
-  // lane i holds row i of the block scaled by 1 / L(i, i): y_i = b_i / L(i, i)
-  // - sum_k (L(i, k) / L(i, i)) y_k, so a step of the substitution chain is a
-  // shuffle and one FMA (a binary64 multiply on the chain costs ~65 cycles)
+  // binary64: lane i holds row i of the block scaled by 1 / L(i, i), y_i =
+  // b_i / L(i, i) - sum_k (L(i, k) / L(i, i)) y_k, so a step of the substitution
+  // chain is a shuffle and one FMA (a binary64 multiply on the chain costs ~65
+  // cycles). binary32 (4-cycle multiplies) keeps the unscaled rows and divides
+  // on the chain, which rounds once less per entry.
+  constexpr bool kScaled = sizeof(T) == 8;
   const T rdiag = lane < d.s ? T(1) / lval<T, RM>(P, d, lane, lane) : T(0);
-  T lrow[S];   // L(lane, k) / L(lane, lane), k < lane (s <= S)
+  T lrow[S];   // L(lane, k) (binary64: / L(lane, lane)), k < lane (s <= S)
 #pragma unroll
-  for (int k = 0; k < S; ++k) lrow[k] = (k < lane && lane < d.s) ? lval<T, RM>(P, d, lane, k) * rdiag : T(0);
+  for (int k = 0; k < S; ++k)
+    lrow[k] = (k < lane && lane < d.s) ? lval<T, RM>(P, d, lane, k) * (kScaled ? rdiag : T(1)) : T(0);
   for (int r = 0; r < nrhs; ++r) {
-    T y = lane < d.s ? Y[d.f + lane + (int64_t)r * n] * rdiag : T(0);
+    T y = lane < d.s ? Y[d.f + lane + (int64_t)r * n] * (kScaled ? rdiag : T(1)) : T(0);
 #pragma unroll
     for (int k = 0; k < S; ++k) {
       if (k < d.s) {   // uniform across the warp
-        const T yk = __shfl_sync(0xffffffffu, y, k);
-        if (lane > k) y -= lrow[k] * yk;
+        if constexpr (kScaled) {
+          const T yk = __shfl_sync(0xffffffffu, y, k);
+          if (lane > k) y -= lrow[k] * yk;
+        } else {
+          const T yk = __shfl_sync(0xffffffffu, y * rdiag, k);
+          if (lane == k) y = yk;
+          if (lane > k) y -= lrow[k] * yk;
+        }
       }
     }
     if (lane < d.s) Y[d.f + lane + (int64_t)r * n] = y;
     // w_J = L_RJ y_J, lane u holding rows u, u + 32, ...: per 32-row group all
     // s entries of the lane's row are loaded at once (one memory round trip per
-    // group), then multiplied with y_J broadcast by shuffle; four partial sums
-    // (k mod 4), added pairwise
+    // group), then multiplied with y_J from shared memory; binary64 keeps four
+    // partial sums (k mod 4, added pairwise) to shorten its FMA chain, binary32
+    // one, in k order
     T* yk = ysh[threadIdx.x >> 5];   // y_J of this warp's supernode (broadcast reads)
     if (lane < S) yk[lane] = y;
     __syncwarp();
@@ -794,7 +805,7 @@ k_sv_small_fwd(const SnodeDev* __restrict__ sn, const int32_t* __restrict__ list
         for (int kk = 0; kk < KH; ++kk)
           lv[kk] = (k0 + kk < d.s && u < b) ? lval<T, RM>(P, d, d.s + u, k0 + kk) : T(0);
 #pragma unroll
-        for (int kk = 0; kk < KH; ++kk) a4[kk & 3] += lv[kk] * yk[k0 + kk];
+        for (int kk = 0; kk < KH; ++kk) a4[kScaled ? (kk & 3) : 0] += lv[kk] * yk[k0 + kk];
       }
       if (u < b) Wj[u + (int64_t)r * b] = (a4[0] + a4[1]) + (a4[2] + a4[3]);
     }
@@ -815,15 +826,18 @@ k_sv_small_bwd(const SnodeDev* __restrict__ sn, const int32_t* __restrict__ list
   const T* P = L + d.loff;
   const int b = d.len - d.s;
   const int32_t* rj = rows + d.roff + d.s;
-  // lane i holds column i of the block scaled by 1 / L(i, i) (as in the forward
-  // kernel: a step of the chain is a shuffle and one FMA)
+  // lane i holds column i of the block (binary64: scaled by 1 / L(i, i), as in
+  // the forward kernel)
+  constexpr bool kScaled = sizeof(T) == 8;
   const T rdiag = lane < d.s ? T(1) / lval<T, RM>(P, d, lane, lane) : T(0);
-  T lcol[S];   // L(k, lane) / L(lane, lane), k > lane (s <= S)
+  T lcol[S];   // L(k, lane) (binary64: / L(lane, lane)), k > lane (s <= S)
 #pragma unroll
-  for (int k = 0; k < S; ++k) lcol[k] = (k > lane && k < d.s) ? lval<T, RM>(P, d, k, lane) * rdiag : T(0);
+  for (int k = 0; k < S; ++k)
+    lcol[k] = (k > lane && k < d.s) ? lval<T, RM>(P, d, k, lane) * (kScaled ? rdiag : T(1)) : T(0);
   for (int r = 0; r < nrhs; ++r) {
-    // four partial sums (u mod 4), added pairwise: a chain of b/4 dependent FMAs
-    // (16 rows' loads in flight per round)
+    // binary64: four partial sums (u mod 4), added pairwise, a chain of b/4
+    // dependent FMAs; binary32: one, in u order (16 rows' loads in flight per
+    // round)
     T t4[4] = {T(0), T(0), T(0), T(0)};
     if (lane < d.s) {
       for (int u0 = 0; u0 < b; u0 += 16) {
@@ -835,16 +849,22 @@ k_sv_small_bwd(const SnodeDev* __restrict__ sn, const int32_t* __restrict__ list
           xv[uu] = u < b ? Y[rj[u] + (int64_t)r * n] : T(0);
         }
 #pragma unroll
-        for (int uu = 0; uu < 16; ++uu) t4[uu & 3] += lv[uu] * xv[uu];
+        for (int uu = 0; uu < 16; ++uu) t4[kScaled ? (uu & 3) : 0] += lv[uu] * xv[uu];
       }
     }
     const T t = (t4[0] + t4[1]) + (t4[2] + t4[3]);
-    T y = lane < d.s ? (Y[d.f + lane + (int64_t)r * n] - t) * rdiag : T(0);
+    T y = lane < d.s ? (Y[d.f + lane + (int64_t)r * n] - t) * (kScaled ? rdiag : T(1)) : T(0);
 #pragma unroll
     for (int k = S - 1; k >= 0; --k) {
       if (k < d.s) {   // uniform across the warp
-        const T xk = __shfl_sync(0xffffffffu, y, k);
-        if (lane < k) y -= lcol[k] * xk;
+        if constexpr (kScaled) {
+          const T xk = __shfl_sync(0xffffffffu, y, k);
+          if (lane < k) y -= lcol[k] * xk;
+        } else {
+          const T xk = __shfl_sync(0xffffffffu, y * rdiag, k);
+          if (lane == k) y = xk;
+          if (lane < k) y -= lcol[k] * xk;
+        }
       }
     }
     if (lane < d.s) Y[d.f + lane + (int64_t)r * n] = y;
