@@ -111,7 +111,8 @@ typedef struct chol_options {
                            /* rounding but not bit for bit between runs.         */
                            /* CHOL_PREC_FP64 and persistent = 0 only.            */
   int64_t wait_polls;      /* bounded device waits of the triangle solve give up */
-                           /* after this many polls of a flag (the solve is then */
+                           /* after this many polls of a flag or hand-off word   */
+                           /* (the solve is then                                 */
                            /* invalid and chol_check_waits reports              */
                            /* CHOL_ETIMEOUT); 0 = default 2^24 (seconds)        */
   int32_t test_unreachable_flags; /* testing the failure path only: 1 = the   */
@@ -173,7 +174,9 @@ int chol_analyze(int32_t n, const int64_t* colptr, const int32_t* rowind,
  * the supernodal panels, then, level by level of the supernodal elimination
  * tree (leaves first), POTRF of each diagonal block, TRSM of each panel,
  * SYRK of each update matrix U_J = L_RJ L_RJ^T and the relind scatter-add of
- * U_J into the ancestors (pull-ordered, atomic-free, deterministic).
+ * U_J into the ancestors (pull-ordered, atomic-free, deterministic). It ends
+ * by inverting the 64x64 diagonal blocks the triangle solves multiply by
+ * (binary64: the inverse; mixed modes: also the last-dependency products).
  *   values  device, colptr[n] doubles in the order of the analyzed rowind
  *   stream  cudaStream_t as void*
  * Returns CHOL_OK, +j (not positive definite at column j of P A P^T), or an
@@ -184,7 +187,8 @@ int chol_factor(chol_handle* h, const double* values, void* stream);
 /*
  * Solve A X = B with the computed factor: X = P^T L^{-T} L^{-1} P B
  * (forward substitution over the levels leaves->root, backward substitution
- * root->leaves; the diagonal triangles of a level in one cooperative launch).
+ * root->leaves; the diagonal triangles of a level in one cooperative launch,
+ * 64-row blocks handed from block to block and multiplied by their inverses).
  *   b      device, n x nrhs column-major (leading dimension n); overwritten by X
  *   nrhs   >= 0
  * Returns CHOL_ESTATE without a successful chol_factor. Asynchronous. The
