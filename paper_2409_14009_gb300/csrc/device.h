@@ -86,6 +86,8 @@ struct DeviceState {
   cudaStream_t lstream = nullptr;  // side stream of the lookahead trailing updates (lowest priority)
   cudaStream_t hstream = nullptr;  // critical path of the blocked levels (highest priority)
   cudaEvent_t lev[3] = {nullptr, nullptr, nullptr};   // panel final / rest done / fork-join
+  cudaStream_t istream = nullptr;  // binary64: diagonal-block inverses of finished levels (lowest priority)
+  cudaEvent_t iev[2] = {nullptr, nullptr};            // level factored / inverses done
   chol_kernel_stat graph_delta[CHOL_K_NCLASSES] = {};
   float mx_spiv = 0.f;             // static-pivot threshold passed to the persistent kernel
   // selected inverse and adjoint

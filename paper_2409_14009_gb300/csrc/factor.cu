@@ -691,7 +691,10 @@ void chol_device_free(chol_handle* h) {
   if (D->gstream) cudaStreamDestroy(D->gstream);
   if (D->lstream) cudaStreamDestroy(D->lstream);
   if (D->hstream) cudaStreamDestroy(D->hstream);
+  if (D->istream) cudaStreamDestroy(D->istream);
   for (cudaEvent_t e : D->lev)
+    if (e) cudaEventDestroy(e);
+  for (cudaEvent_t e : D->iev)
     if (e) cudaEventDestroy(e);
   for (cudaEvent_t e : D->gev)
     if (e) cudaEventDestroy(e);
@@ -722,6 +725,9 @@ int chol_device_ensure(chol_handle* h) {
     if (cudaDeviceGetStreamPriorityRange(&lo, &hi) != cudaSuccess ||
         cudaStreamCreateWithPriority(&D->hstream, cudaStreamNonBlocking, hi) != cudaSuccess ||
         cudaStreamCreateWithPriority(&D->lstream, cudaStreamNonBlocking, lo) != cudaSuccess ||
+        cudaStreamCreateWithPriority(&D->istream, cudaStreamNonBlocking, lo) != cudaSuccess ||
+        cudaEventCreateWithFlags(&D->iev[0], cudaEventDisableTiming) != cudaSuccess ||
+        cudaEventCreateWithFlags(&D->iev[1], cudaEventDisableTiming) != cudaSuccess ||
         cudaEventCreateWithFlags(&D->lev[0], cudaEventDisableTiming) != cudaSuccess ||
         cudaEventCreateWithFlags(&D->lev[1], cudaEventDisableTiming) != cudaSuccess ||
         cudaEventCreateWithFlags(&D->lev[2], cudaEventDisableTiming) != cudaSuccess)
@@ -821,8 +827,12 @@ int enqueue_factor_fp64(chol_handle* h, const double* values, cudaStream_t st) {
     if (h->n_large > 0 || h->opt.update_mode != CHOL_UPDATE_RL) return CHOL_ENOTSUP;
     double fl = 0.0, by = 0.0;
     for (const LevelPlan& P : h->levels) { fl += P.small_flops; by += P.small_bytes; }
-    KScope ks(h, CHOL_K_SMALL, st, fl, by);
-    return chol_launch_persistent(h, (void*)D->L, (void*)D->U, st);
+    {
+      KScope ks(h, CHOL_K_SMALL, st, fl, by);
+      const int rc = chol_launch_persistent(h, (void*)D->L, (void*)D->U, st);
+      if (rc) return rc;
+    }
+    return chol_diag_inv(h, 0, (int)h->tri_items.size(), st);
   }
   // levels with blocked supernodes run on the high-priority stream (forked from
   // and joined back to the caller's stream)
@@ -832,6 +842,7 @@ int enqueue_factor_fp64(chol_handle* h, const double* values, cudaStream_t st) {
     CHOL_CUDA_TRY(cudaStreamWaitEvent(D->hstream, D->lev[2], 0));
     st = D->hstream;
   }
+  bool inv_pending = false;
   for (const LevelPlan& P : h->levels) {
     NvtxRange nvtx_level("level", (long long)(&P - h->levels.data()));
     const bool rlb = h->opt.update_mode == CHOL_UPDATE_RLB;
@@ -888,6 +899,14 @@ int enqueue_factor_fp64(chol_handle* h, const double* values, cudaStream_t st) {
       }
     }
     if (rest_pending) CHOL_CUDA_TRY(cudaStreamWaitEvent(st, D->lev[1], 0));   // join before SYRK
+    // the level's diagonal blocks are final: their inverses (for the triangle
+    // solves) on a side stream, beside the SYRK, the assembly and later levels
+    if (P.tri_n > 0) {
+      CHOL_CUDA_TRY(cudaEventRecord(D->iev[0], st));
+      CHOL_CUDA_TRY(cudaStreamWaitEvent(D->istream, D->iev[0], 0));
+      if (int rc = chol_diag_inv(h, P.tri_b, P.tri_n, D->istream)) return rc;
+      inv_pending = true;
+    }
     if (P.syrk_n > 0) {
       KScope ks(h, CHOL_K_SYRK, st, P.syrk_flops, 8.0 * kTile * kTile * P.syrk_n);
       if (rlb)
@@ -907,6 +926,10 @@ int enqueue_factor_fp64(chol_handle* h, const double* values, cudaStream_t st) {
             D->asm_tasks + P.asm_b + P.asm_n, P.asmw_n, D->asm_segs, D->sn, D->rows, D->U, D->L);
     }
   }
+  if (inv_pending) {   // the inverses join the factor's stream before it ends
+    CHOL_CUDA_TRY(cudaEventRecord(D->iev[1], D->istream));
+    CHOL_CUDA_TRY(cudaStreamWaitEvent(st, D->iev[1], 0));
+  }
   if (st != caller) {
     CHOL_CUDA_TRY(cudaEventRecord(D->lev[2], st));
     CHOL_CUDA_TRY(cudaStreamWaitEvent(caller, D->lev[2], 0));
@@ -916,11 +939,11 @@ int enqueue_factor_fp64(chol_handle* h, const double* values, cudaStream_t st) {
 }
 
 int enqueue_factor(chol_handle* h, const double* values, cudaStream_t st) {
-  const int rc = h->opt.precision == CHOL_PREC_FP64 ? enqueue_factor_fp64(h, values, st)
-                                                    : chol_enqueue_factor_mixed(h, values, st);
+  if (h->opt.precision == CHOL_PREC_FP64) return enqueue_factor_fp64(h, values, st);   // inverses inside
+  const int rc = chol_enqueue_factor_mixed(h, values, st);
   if (rc) return rc;
-  // the triangle solves multiply by the diagonal blocks' inverses
-  return chol_diag_inv(h, st);
+  // the binary32 triangle solve multiplies by the diagonal blocks' inverses
+  return chol_diag_inv(h, 0, (int)h->tri_items.size(), st);
 }
 
 void drop_graph(chol_handle* h) {

@@ -23,6 +23,6 @@ int chol_tc_syrk(chol_handle* h, const TileTask* tasks, int n, cudaStream_t st);
 int chol_tc_status(chol_handle* h);
 void chol_adjoint_free(chol_handle* h);
 int chol_solve_status(chol_handle* h);
-int chol_diag_inv(chol_handle* h, cudaStream_t st);
+int chol_diag_inv(chol_handle* h, int b, int nitems, cudaStream_t st);
 int chol_bc_begin_mixed(const chol_handle* h);
 int chol_bc_read_mixed();

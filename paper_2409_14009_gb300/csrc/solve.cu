@@ -1489,13 +1489,13 @@ int chol_solve_mixed(chol_handle* h, double* b, int32_t nrhs, cudaStream_t st) {
 }
 
 // Inverses of the diagonal blocks the triangle solves multiply by, for the
-// factor just enqueued on st: binary64 (column-major panels) the inverse alone,
-// binary32 (row-major panels) the inverse and the two last-dependency products.
-int chol_diag_inv(chol_handle* h, cudaStream_t st) {
+// triangle items [b, b + nitems) of a factor enqueued on st (their blocks
+// final): binary64 (column-major panels) the inverse alone, binary32 (row-major
+// panels) the inverse and the two last-dependency products.
+int chol_diag_inv(chol_handle* h, int b, int nitems, cudaStream_t st) {
   DeviceState* D = h->dev;
-  const int nitems = (int)h->tri_items.size();
-  if (nitems == 0) return CHOL_OK;
-  const TriItem* items = reinterpret_cast<const TriItem*>(D->tri);
+  if (nitems <= 0) return CHOL_OK;
+  const TriItem* items = reinterpret_cast<const TriItem*>(D->tri) + b;
   if (h->opt.precision == CHOL_PREC_FP64) {
     // per block: the inverse by substitution, about 64^3 / 3 flops
     KScope ks(h, CHOL_K_SOLVE_DIAG, st, (double)nitems * 64.0 * 64.0 * 64.0 / 3.0,
