@@ -17,7 +17,6 @@
 namespace {
 
 constexpr int kT = 256;
-constexpr int kChunk = kSolveChunk;
 
 inline unsigned grid1d(int64_t n, int threads) {
   int64_t g = (n + threads - 1) / threads;
@@ -58,6 +57,28 @@ k_residual(const int64_t* __restrict__ rp, const int32_t* __restrict__ ci, const
         atomicMax(rmax + r, (unsigned long long)__double_as_longlong(fabs(v)));
       }
     }
+  }
+}
+
+// The same residual with a thread per row, for matrices with few entries per
+// row (at most 16 on average, e.g. 5-point grids): each row's sum in entry
+// order, the maxima reduced per warp before one atomic per warp and column.
+__global__ void __launch_bounds__(kT)
+k_residual_rows(const int64_t* __restrict__ rp, const int32_t* __restrict__ ci, const double* __restrict__ av,
+                const double* __restrict__ X, const double* __restrict__ B, int n, int nrhs,
+                double* __restrict__ R, unsigned long long* __restrict__ rmax) {
+  for (int r = 0; r < nrhs; ++r) {
+    const double* x = X + (int64_t)r * n;
+    double m = 0.0;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+      double s = 0.0;
+      for (int64_t t = rp[i]; t < rp[i + 1]; ++t) s = fma(av[t], x[ci[t]], s);
+      const double v = B[i + (int64_t)r * n] - s;
+      R[i + (int64_t)r * n] = v;
+      m = fmax(m, fabs(v));
+    }
+    for (int o = 16; o > 0; o >>= 1) m = fmax(m, __shfl_xor_sync(0xffffffffu, m, o));
+    if ((threadIdx.x & 31) == 0) atomicMax(rmax + r, (unsigned long long)__double_as_longlong(m));
   }
 }
 
@@ -209,6 +230,8 @@ extern "C" int chol_solve_refine(chol_handle* h, const double* b, double* x, int
   double* part = beta + nrhs;
   unsigned char* active = (unsigned char*)(part + kDotBlocks * nrhs);
   const unsigned gsp = grid1d((int64_t)n * 32, kT);
+  // a warp per row wastes most lanes on rows of a few entries
+  const bool few_per_row = h->csr_ptr[n] <= 16 * (int64_t)n;
 
   // ||A||_inf and ||b||_inf
   CHOL_CUDA_TRY(cudaMemsetAsync(red, 0, sizeof(double) * (3 * nrhs + 1), st));
@@ -223,7 +246,10 @@ extern "C" int chol_solve_refine(chol_handle* h, const double* b, double* x, int
   auto measure = [&]() -> int {
     // R = b - A x; eta = ||R|| / (||A|| ||x|| + ||b||)
     CHOL_CUDA_TRY(cudaMemsetAsync(rmax, 0, sizeof(double) * 2 * nrhs, st));
-    k_residual<<<gsp, kT, 0, st>>>(D->csr_ptr, D->csr_col, D->csr_val, x, b, n, nrhs, D->R, rmax);
+    if (few_per_row)
+      k_residual_rows<<<grid1d(n, kT), kT, 0, st>>>(D->csr_ptr, D->csr_col, D->csr_val, x, b, n, nrhs, D->R, rmax);
+    else
+      k_residual<<<gsp, kT, 0, st>>>(D->csr_ptr, D->csr_col, D->csr_val, x, b, n, nrhs, D->R, rmax);
     k_maxabs_cols<<<grid1d(n, 256), 256, 0, st>>>(x, n, nrhs, xmax);
     CHOL_CUDA_TRY(cudaMemcpyAsync(D->red_host, red, sizeof(double) * (3 * nrhs + 1), cudaMemcpyDeviceToHost, st));
     CHOL_CUDA_TRY(cudaStreamSynchronize(st));
