@@ -416,9 +416,9 @@ int chol_test_corrupt_plan(chol_handle* h, int32_t kind);
 int chol_autotune(chol_handle* h, const double* values, void* stream);
 
 /*
- * Analysis-level autotuner for batches (north star (2): tile shapes and
- * schedules picked by an autotuner; the paper's own choice is a fixed size
- * threshold between its CPU and GPU code paths, Sec. III-IV). Searches which
+ * Analysis-level autotuner for batches (the schedule of many small systems
+ * picked by measurement; the paper's own choice is a fixed size threshold
+ * between its CPU and GPU code paths, Sec. III-IV). Searches which
  * supernodes take the one-CTA kernel and how much relaxed merging to allow:
  * (small_max_cols, small_max_panel, small_max_rows) in {(64, 4096, 128),
  * (128, 16384, 256), (160, 24576, 512)} x merge_growth in {0, 0.1, 0.25}; for

@@ -8,7 +8,7 @@
 //
 // The limits and the error word are per translation unit (static), set by
 // bc_begin before a factorization and read by bc_read after it; one
-// factorization at a time per process in this build.
+// factorization at a time per process in the checked build.
 #pragma once
 #include <cstdint>
 

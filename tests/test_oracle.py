@@ -239,7 +239,7 @@ def test_logdet_2d_dirichlet_closed_form():
     s = 4 * np.sin(np.arange(1, k + 1) * np.pi / (2 * (k + 1))) ** 2
     exact = np.log(1e-3 + s[:, None] + s[None, :]).sum()
     assert abs(ref["fac"].logdet() - exact) <= 1e-12 * abs(exact)
-    # cross-check under the nested-dissection reading (same count as the survey's
+    # cross-check under the nested-dissection reading (the counts of an
     # independent symbolic run): nnz(L) = 88,130 and sum c_j^2 = 3,717,076
     assert ref["sym"].nnz == 88130 and ref["sym"].flops() == 3717076
 
